@@ -1,0 +1,360 @@
+"""FP64 CPU oracle for the collocation Lame single-layer H-matrix.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import this package.  It shares no
+code with the CUDA library in ``paper_2205_04752_gb300`` and never imports it.
+
+The C part (``hm_oracle.c``) follows the paper step by step (see its header
+for the passage behind each function); this module only marshals arguments and
+adds the pieces for which a library routine is the plain definition:
+
+* ``svd_rank`` / ``svd_truncate`` -- the truncated singular value
+  decomposition, the best rank-k approximation (Section 2, Eckart-Young),
+  computed with ``numpy.linalg.svd``;
+* ``dense_matvec`` -- y = A x with ``numpy`` on the dense Kelvin matrix.
+
+Parity unpinned: the absolute accuracy of the near-singular rule on badly
+shaped triangles (only its convergence on well-shaped ones is pinned).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libhm_oracle.so")
+_lib = None
+_lock = threading.Lock()
+
+ND = 32          # Gauss-Legendre points of the self term
+KERNELS = ("V_Delta", "V_11", "V_12", "V_13", "V_22", "V_23", "V_33")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP if available, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+            "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _L():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.c_void_p
+            I64 = ctypes.c_int64
+            I32 = ctypes.c_int32
+            D = ctypes.c_double
+            sig = {
+                "or_radon7": (None, [P, P]),
+                "or_gauss_legendre01": (None, [ctypes.c_int, P, P]),
+                "or_centroids": (None, [P, P, I64, P]),
+                "or_scalar_entry": (None, [P, P, P, ctypes.c_int, ctypes.c_int, P]),
+                "or_kelvin_entry": (None, [P, P, P, ctypes.c_int, ctypes.c_int, D, D, P]),
+                "or_scalar_rows": (None, [P, P, I64, P, I64, P]),
+                "or_kelvin_rows_matvec": (None, [P, P, I64, D, D, P, I64, P, I64, P]),
+                "or_kelvin_dense": (None, [P, P, I64, D, D, P]),
+                "or_aca_dense": (I32, [P, I64, I64, D, D, I32, P, P, P, P, P, P]),
+                "or_hmat_create": (P, [P, I64, P, I64, I64, D, D, D, I32]),
+                "or_hmat_free": (None, [P]),
+                "or_hmat_sizes": (None, [P, P]),
+                "or_hmat_tree": (None, [P, P, P, P]),
+                "or_hmat_blocks": (None, [P, P, P]),
+                "or_hmat_assemble": (None, [P, P, I64, P, I64]),
+                "or_hmat_rank": (I32, [P, I64, ctypes.c_int]),
+                "or_hmat_aca_flags": (I32, [P, I64, ctypes.c_int]),
+                "or_hmat_factors": (None, [P, I64, ctypes.c_int, P, P]),
+                "or_hmat_near_block": (None, [P, I64, P]),
+                "or_hmat_matvec": (None, [P, D, D, P, P, I64, P, I64, P, I64]),
+                "or_num_threads": (I32, []),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _i64(a):
+    return np.ascontiguousarray(a, dtype=np.int64)
+
+
+def num_threads() -> int:
+    return int(_L().or_num_threads())
+
+
+# --------------------------------------------------------------------------
+# quadrature and entries
+# --------------------------------------------------------------------------
+
+def radon7():
+    lam = np.zeros(21)
+    w = np.zeros(7)
+    _L().or_radon7(_p(lam), _p(w))
+    return lam.reshape(7, 3), w
+
+
+def gauss_legendre01(n: int):
+    x = np.zeros(n)
+    w = np.zeros(n)
+    _L().or_gauss_legendre01(n, _p(x), _p(w))
+    return x, w
+
+
+def centroids(V, T) -> np.ndarray:
+    V, T = _f64(V), _i32(T)
+    C = np.zeros((T.shape[0], 3))
+    _L().or_centroids(_p(V), _p(T), T.shape[0], _p(C))
+    return C
+
+
+def scalar_entry(x, V, tri, self_pair: bool, nd: int = ND) -> np.ndarray:
+    """Seven scalar kernels (Eq. (Vh), collocation, 1/(4 pi) prefactor) of
+    point x against triangle ``tri`` (3 vertex ids into V)."""
+    x, V, tri = _f64(x), _f64(V), _i32(tri)
+    out = np.zeros(7)
+    _L().or_scalar_entry(_p(x), _p(V), _p(tri), int(self_pair), nd, _p(out))
+    return out
+
+
+def kelvin_entry(x, V, tri, self_pair: bool, E: float, nu: float, nd: int = ND) -> np.ndarray:
+    """int_tau S_K(x - y) ds_y from Kelvin's tensor directly, 3 x 3."""
+    x, V, tri = _f64(x), _f64(V), _i32(tri)
+    out = np.zeros(9)
+    _L().or_kelvin_entry(_p(x), _p(V), _p(tri), int(self_pair), nd, E, nu, _p(out))
+    return out.reshape(3, 3)
+
+
+def scalar_rows(V, T, rows) -> np.ndarray:
+    """(7, len(rows), M) scalar-kernel matrix rows at the collocation points."""
+    V, T, rows = _f64(V), _i32(T), _i64(rows)
+    M = T.shape[0]
+    out = np.zeros((7, rows.shape[0], M))
+    _L().or_scalar_rows(_p(V), _p(T), M, _p(rows), rows.shape[0], _p(out))
+    return out
+
+
+def kelvin_dense(V, T, E: float, nu: float) -> np.ndarray:
+    """Dense 3M x 3M collocation matrix of the Lame single layer, dof 3 i + a."""
+    V, T = _f64(V), _i32(T)
+    M = T.shape[0]
+    A = np.zeros((3 * M, 3 * M))
+    _L().or_kelvin_dense(_p(V), _p(T), M, E, nu, _p(A))
+    return A
+
+
+def dense_matvec(A: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """y = A x for x of shape (nrhs, 3M) (library matmul)."""
+    return (A @ np.atleast_2d(x).T).T
+
+
+def kelvin_rows_matvec(V, T, E: float, nu: float, rows, x) -> np.ndarray:
+    """Exact rows (dofs 3 i + a, i in rows) of y = A x without forming A.
+    x: (nrhs, 3M).  Returns (nrhs, 3 * len(rows))."""
+    V, T, rows = _f64(V), _i32(T), _i64(rows)
+    x = _f64(np.atleast_2d(x))
+    M = T.shape[0]
+    y = np.zeros((x.shape[0], 3 * rows.shape[0]))
+    _L().or_kelvin_rows_matvec(_p(V), _p(T), M, E, nu, _p(rows), rows.shape[0], _p(x),
+                               x.shape[0], _p(y))
+    return y
+
+
+def lame_coefficients(E: float, nu: float):
+    """c1, c2 of Eq. (Vh) in collocation form: V_h = c1 diag(V_Delta) + c2 [V_kl]."""
+    c1 = (1.0 + nu) * (3.0 - 4.0 * nu) / (2.0 * E * (1.0 - nu))
+    c2 = (1.0 + nu) / (2.0 * E * (1.0 - nu))
+    return c1, c2
+
+
+# --------------------------------------------------------------------------
+# ACA (Algorithm 1) and SVD truncation
+# --------------------------------------------------------------------------
+
+def aca_dense(A, eps: float, eta_stop: float = 0.8, kmax: int = 256):
+    """Algorithm 1 on an explicit matrix.  Returns dict(U, V, rank, piv_i,
+    piv_j, steps, flags) with U (m x k), V (n x k) so that A ~ U V^T."""
+    A = _f64(A)
+    m, n = A.shape
+    kmax = int(kmax)
+    U = np.zeros((kmax, m))
+    Vv = np.zeros((kmax, n))
+    pi = np.zeros(kmax, dtype=np.int64)
+    pj = np.zeros(kmax, dtype=np.int64)
+    steps = ctypes.c_int32(0)
+    flags = ctypes.c_int32(0)
+    k = _L().or_aca_dense(_p(A), m, n, eps, eta_stop, kmax, _p(U), _p(Vv), _p(pi), _p(pj),
+                          ctypes.byref(steps), ctypes.byref(flags))
+    return dict(U=U[:k].T.copy(), V=Vv[:k].T.copy(), rank=int(k), piv_i=pi[:k].copy(),
+                piv_j=pj[:k].copy(), steps=int(steps.value), flags=int(flags.value))
+
+
+def svd_rank(A: np.ndarray, eps: float) -> int:
+    """Smallest r with ||A - A_r||_F <= eps ||A||_F (truncated SVD is the best
+    rank-r approximation, Section 2)."""
+    s = np.linalg.svd(A, compute_uv=False)
+    tot = float(np.sum(s * s))
+    if tot == 0.0:
+        return 0
+    tail = np.concatenate([np.cumsum((s * s)[::-1])[::-1], [0.0]])
+    for r in range(len(s) + 1):
+        if tail[r] <= eps * eps * tot:
+            return r
+    return len(s)
+
+
+def svd_truncate(U: np.ndarray, V: np.ndarray, eps: float):
+    """Recompress U V^T to the smallest rank r with relative Frobenius error
+    <= eps via QR of both factors and an SVD of the small core."""
+    if U.shape[1] == 0:
+        return U, V
+    qu, ru = np.linalg.qr(U)
+    qv, rv = np.linalg.qr(V)
+    w, s, zt = np.linalg.svd(ru @ rv.T)
+    tot = float(np.sum(s * s))
+    r = len(s)
+    tail = np.concatenate([np.cumsum((s * s)[::-1])[::-1], [0.0]])
+    for rr in range(len(s) + 1):
+        if tail[rr] <= eps * eps * tot:
+            r = rr
+            break
+    return (qu @ (w[:, :r] * s[:r])), (qv @ zt[:r].T)
+
+
+# --------------------------------------------------------------------------
+# the oracle's own H-matrix
+# --------------------------------------------------------------------------
+
+class HMatrix:
+    """Cluster tree, partition, ACA factors and near blocks built by the
+    oracle (FP64), and its H-matrix-vector product."""
+
+    def __init__(self, V, T, leaf: int, eta: float, eps: float, eta_stop: float = 0.8,
+                 kmax: int = 256):
+        self.V, self.T = _f64(V), _i32(T)
+        self.M = self.T.shape[0]
+        self.leaf, self.eta, self.eps, self.eta_stop, self.kmax = leaf, eta, eps, eta_stop, kmax
+        self._h = _L().or_hmat_create(_p(self.V), self.V.shape[0], _p(self.T), self.M, leaf,
+                                      eta, eps, eta_stop, kmax)
+        s = np.zeros(4, dtype=np.int64)
+        _L().or_hmat_sizes(self._h, _p(s))
+        self.nnodes, self.nadm, self.nnear = int(s[0]), int(s[1]), int(s[2])
+        self.perm = np.zeros(self.M, dtype=np.int64)
+        self.nodes = np.zeros((self.nnodes, 5), dtype=np.int64)
+        self.boxes = np.zeros((self.nnodes, 6))
+        _L().or_hmat_tree(self._h, _p(self.perm), _p(self.nodes), _p(self.boxes))
+        self.adm = np.zeros((self.nadm, 2), dtype=np.int64)
+        self.near = np.zeros((self.nnear, 2), dtype=np.int64)
+        _L().or_hmat_blocks(self._h, _p(self.adm), _p(self.near))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _L().or_hmat_free(h)
+            self._h = None
+
+    # block ranges in cluster order
+    def ranges(self, blocks: np.ndarray) -> np.ndarray:
+        t, s = blocks[:, 0], blocks[:, 1]
+        return np.stack([self.nodes[t, 0], self.nodes[t, 1], self.nodes[s, 0],
+                         self.nodes[s, 1]], 1)
+
+    @staticmethod
+    def _ids(ids):
+        """(pointer, count) with count -1 meaning 'all blocks'."""
+        if ids is None:
+            return None, -1, None
+        a = _i64(ids)
+        if a.size == 0:
+            a = np.zeros(1, dtype=np.int64)
+            return _p(a), 0, a
+        return _p(a), a.size, a
+
+    def assemble(self, adm_ids=None, near_ids=None):
+        """Assemble the listed blocks (all of a kind when its list is None)."""
+        pa, na, ka = self._ids(adm_ids)
+        pn, nn, kn = self._ids(near_ids)
+        _L().or_hmat_assemble(self._h, pa, na, pn, nn)
+
+    def rank(self, b: int, kern: int) -> int:
+        return int(_L().or_hmat_rank(self._h, b, kern))
+
+    def ranks(self) -> np.ndarray:
+        r = np.zeros((self.nadm, 7), dtype=np.int64)
+        for b in range(self.nadm):
+            for k in range(7):
+                r[b, k] = _L().or_hmat_rank(self._h, b, k)
+        return r
+
+    def aca_flags(self, b: int, kern: int) -> int:
+        return int(_L().or_hmat_aca_flags(self._h, b, kern))
+
+    def factors(self, b: int, kern: int):
+        t, s = self.adm[b]
+        m = int(self.nodes[t, 1] - self.nodes[t, 0])
+        n = int(self.nodes[s, 1] - self.nodes[s, 0])
+        k = self.rank(b, kern)
+        U = np.zeros((max(k, 0), m))
+        Vv = np.zeros((max(k, 0), n))
+        if k > 0:
+            _L().or_hmat_factors(self._h, b, kern, _p(U), _p(Vv))
+        return U.T.copy(), Vv.T.copy()
+
+    def near_block(self, b: int) -> np.ndarray:
+        t, s = self.near[b]
+        m = int(self.nodes[t, 1] - self.nodes[t, 0])
+        n = int(self.nodes[s, 1] - self.nodes[s, 0])
+        out = np.zeros((7, m, n))
+        _L().or_hmat_near_block(self._h, b, _p(out))
+        return out
+
+    def matvec(self, E: float, nu: float, x, adm_ids=None, near_ids=None) -> np.ndarray:
+        x = _f64(np.atleast_2d(x))
+        y = np.zeros_like(x)
+        pa, na, ka = self._ids(adm_ids)
+        pn, nn, kn = self._ids(near_ids)
+        _L().or_hmat_matvec(self._h, E, nu, _p(x), _p(y), x.shape[0], pa, na, pn, nn)
+        return y
+
+    def dense_block(self, b: int, kern: int) -> np.ndarray:
+        """The exact (quadrature-contract) scalar-kernel block of admissible
+        block b, computed entry by entry."""
+        t, s = self.adm[b]
+        lo_t, hi_t = self.nodes[t, :2]
+        lo_s, hi_s = self.nodes[s, :2]
+        rows = self.perm[lo_t:hi_t]
+        cols = self.perm[lo_s:hi_s]
+        R = scalar_rows(self.V, self.T, rows)[kern]
+        return R[:, cols]
