@@ -1,0 +1,190 @@
+/*
+ * hmat.h -- C ABI of the GB300 (sm_103a) H-matrix library for the collocation
+ * Lame single-layer operator (Bauer & Bebendorf, "Adaptive H-Matrix
+ * Computations in Linear Elasticity").
+ *
+ * Conventions for every entry point:
+ *   - Plain C types only.  A "device pointer" is memory of the current CUDA
+ *     device; a "host pointer" is ordinary (preferably pinned) host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Device work is stream ordered and asynchronous unless stated otherwise;
+ *     results are valid once the stream has been synchronised.
+ *   - Return value 0 (HM_OK) on success, a negative HM_E* code otherwise; the
+ *     text of the last error of the calling thread is hm_last_error().
+ *     Nothing throws across this boundary.
+ *   - Degrees of freedom are ordered dof = 3*i + a (triangle i in the mesh's
+ *     original order, component a in {0,1,2}).  Multi-RHS vectors are nrhs
+ *     rows of length >= 3M with leading dimension ld (elements).
+ *   - Objects (hm_tree, hm_matrix) are owned by the library; destroy them with
+ *     the matching *_destroy call.  Input arrays are copied and never retained.
+ */
+#ifndef HMAT_H
+#define HMAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define HM_OK 0
+#define HM_EINVAL (-1)    /* invalid argument: bad mesh, E <= 0, nu outside (0, 1/2), ... */
+#define HM_ENOMEM (-2)    /* device or host allocation failed */
+#define HM_ENOTCONV (-3)  /* iterative solve stopped before reaching the tolerance */
+#define HM_ETIMEOUT (-4)  /* a bounded device wait ran out; the context stays usable */
+#define HM_EDEVICE (-5)   /* a CUDA call failed */
+#define HM_ERANK (-6)     /* an ACA block reached the rank cap (result kept, flagged) */
+
+/* storage / arithmetic forms of the H-matrix-vector product */
+#define HM_FP64 0 /* factors and near field FP64, FP64 accumulation ("plain form") */
+#define HM_FP32 1 /* factors and near field FP32, FP32 accumulation */
+#define HM_BF16 2 /* factors BF16 with per-column FP32 scales, near field FP32, FP32 acc. */
+#define HM_FP16 3 /* factors FP16 with per-column FP32 scales, near field FP32, FP32 acc. */
+
+typedef struct hm_tree hm_tree;     /* cluster tree + block partition (host) */
+typedef struct hm_matrix hm_matrix; /* assembled H-matrix resident on the device */
+
+/* Optional device allocator.  alloc returns a device pointer of at least
+ * `bytes` (NULL on failure) usable on `stream`; free releases it.  When no
+ * allocator is given the library uses cudaMallocAsync / cudaFreeAsync. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* stream, void* user);
+    void (*free)(void* ptr, size_t bytes, void* stream, void* user);
+    void* user;
+} hm_allocator;
+
+/* ---------------------------------------------------------------------------
+ * hm_build_cluster_tree -- cluster tree T_I and block partition P (Section
+ * 2.1: binary tree of index sets, leaves of at most b_min = leaf indices;
+ * Eq. (adm): a block t x s is admissible iff
+ *     min(diam X_t, diam X_s) < eta * dist(X_t, X_s),
+ * evaluated on the bounding boxes of the clusters' triangle vertices).
+ * Host-only: touches no GPU.
+ *   verts  host, nv x 3 float64, row-major vertex coordinates
+ *   tris   host, nt x 3 int32, vertex ids of each flat triangle tau_i
+ *          (Section 4.2); the collocation point of tau_i is its centroid
+ *   leaf   b_min >= 1; eta > 0
+ *   out    receives a new tree (NULL on error)
+ * Split rule: longest axis of the box of the collocation points, median of a
+ * stable sort by (coordinate, triangle id), first son floor(n/2).
+ * Errors: HM_EINVAL (nv < 3, nt < 1, vertex id out of range, degenerate
+ * triangle, leaf < 1, eta <= 0, non-finite coordinate), HM_ENOMEM.
+ * ------------------------------------------------------------------------- */
+int hm_build_cluster_tree(const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                          int32_t leaf, double eta, hm_tree** out);
+
+/* sizes of a tree: counts[0..5] = M, nodes, admissible blocks, near blocks,
+ * leaves, depth */
+int hm_tree_sizes(const hm_tree* tree, int64_t counts[6]);
+
+/* Export for inspection and tests (host arrays sized from hm_tree_sizes):
+ *   perm[M]          cluster position -> original triangle id
+ *   nodes[nodes*5]   (lo, hi, son0, son1, level) per node, pre-order, sons -1
+ *                    for a leaf; [lo, hi) are cluster positions
+ *   adm[nadm*2]      (row node, column node) of each admissible block
+ *   near[nnear*2]    (row node, column node) of each near (dense) block
+ * Any pointer may be NULL to skip that array. */
+int hm_tree_export(const hm_tree* tree, int64_t* perm, int64_t* nodes, int64_t* adm,
+                   int64_t* near_blocks);
+
+void hm_tree_destroy(hm_tree* tree);
+
+/* Assembly parameters. */
+typedef struct {
+    double E;            /* Young modulus > 0 (Section 1) */
+    double nu;           /* Poisson ratio in (0, 1/2) */
+    double aca_eps;      /* eps_ACA > 0 (Algorithm 1) */
+    double aca_eta_stop; /* beta of Algorithm 1's stop factor eps(1-beta)/(1+eps); 0 = plain eps */
+    int32_t kmax;        /* rank cap per block and kernel, 1..256 (0 = 128) */
+    int32_t max_rhs;     /* largest nrhs a later hm_matvec may use, 1..64 (0 = 32) */
+} hm_params;
+
+/* ---------------------------------------------------------------------------
+ * hm_aca_assemble -- assemble the H-matrix of V_h on the device.
+ * Eq. (Vh) in collocation form with the prefactor read as 1/(4 pi):
+ *   V_h = c1 diag(V_Delta, V_Delta, V_Delta) + c2 [V_kl],
+ *   c1 = (1+nu)(3-4nu) / (2E(1-nu)),  c2 = (1+nu) / (2E(1-nu)),
+ *   V_Delta[i,j] = 1/(4pi) int_{tau_j} 1/|c_i - y| ds_y,
+ *   V_kl[i,j]    = 1/(4pi) int_{tau_j} (c_i-y)_k (c_i-y)_l / |c_i - y|^3 ds_y.
+ * Near (non-admissible) blocks are computed entry by entry (Section 2.2);
+ * every admissible block gets one ACA (Algorithm 1) per scalar kernel
+ * (V_Delta, V_11, V_12, V_13, V_22, V_23, V_33), in FP64.  The factors do not
+ * depend on E, nu; c1 and c2 are applied in the product.
+ *   tree   from hm_build_cluster_tree (not retained)
+ *   prm    parameters (validated; HM_EINVAL on a bad value)
+ *   alloc  optional device allocator (NULL: cudaMallocAsync)
+ *   stream stream for all device work; the call synchronises it before return
+ *   out    receives the matrix
+ * Returns HM_ERANK (matrix still valid) if a block hit the rank cap.
+ * ------------------------------------------------------------------------- */
+int hm_aca_assemble(const hm_tree* tree, const hm_params* prm, const hm_allocator* alloc,
+                    void* stream, hm_matrix** out);
+
+/* Change E, nu of an assembled matrix (the factors are material-free). */
+int hm_set_material(hm_matrix* H, double E, double nu);
+
+/* Build the packed copy used by the HM_FP32 / HM_BF16 / HM_FP16 product forms
+ * (HM_FP64 needs none).  Idempotent; synchronises `stream`. */
+int hm_pack(hm_matrix* H, int32_t form, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * hm_matvec -- y = V_h x (H-matrix-vector product, Section 2: each admissible
+ * block applies U (V^T x) at O(k(|t|+|s|)) cost, each near block its dense
+ * entries; the contributions of all blocks of a row are summed into y).
+ *   x, y    device pointers, nrhs rows of length 3M, leading dimension ld
+ *           (>= 3M); y is overwritten; x and y must not overlap
+ *   nrhs    1 .. max_rhs of the assembly
+ *   form    HM_FP64 or a packed form (hm_pack first)
+ * Deterministic: every output element is summed in a fixed order, so repeated
+ * calls give bitwise-identical results.  Asynchronous on `stream`; allocates
+ * nothing.  Calls on the same matrix must not overlap in time on the device
+ * (they share the matrix's workspace).
+ * ------------------------------------------------------------------------- */
+int hm_matvec(const hm_matrix* H, const double* x, double* y, int32_t nrhs, int64_t ld,
+              int32_t form, void* stream);
+
+/* Same product with HOST x and y: copies x in, runs hm_matvec, copies y back
+ * and synchronises `stream`.  Pinned host memory gives the fastest copies. */
+int hm_matvec_host(const hm_matrix* H, const double* x_host, double* y_host, int32_t nrhs,
+                   int64_t ld, int32_t form, void* stream);
+
+/* Statistics of an assembled matrix. */
+typedef struct {
+    int64_t M, nadm, nnear, nleaves;
+    int64_t near_pairs;         /* sum over near blocks of |t||s| */
+    int64_t far_entries;        /* sum over admissible blocks and kernels of k(|t|+|s|) */
+    int64_t rank_sum[7];        /* per scalar kernel */
+    int32_t rank_max[7];
+    int32_t rank_cap_hits;      /* block-kernel pairs that hit kmax */
+    int32_t csp;                /* sparsity constant: max blocks per row cluster */
+    int64_t bytes_fp64;         /* far + near bytes read by one FP64 product */
+    int64_t bytes_form[4];      /* same for each form (0 if not packed) */
+    double assemble_ms[3];      /* near-field quadrature, ACA, packing (device time) */
+} hm_stats;
+
+int hm_get_stats(const hm_matrix* H, hm_stats* st);
+
+/* Export one admissible block's FP64 factors for inspection: blk indexes the
+ * admissible list of hm_tree_export; kern 0..6 as above.  *rank receives k;
+ * U (|t| x k) and V (|s| x k) are host arrays in column-major order, cluster
+ * order within the block; pass NULL to query the rank only. */
+int hm_export_factors(const hm_matrix* H, int64_t blk, int32_t kern, int32_t* rank, double* U,
+                      double* V);
+
+/* Export one near block's FP64 entries: host array of 6 x |t| x |s|, values
+ * (V_11, V_12, V_13, V_22, V_23, V_33) row-major per value; V_Delta is their
+ * trace. */
+int hm_export_near(const hm_matrix* H, int64_t blk, double* out);
+
+void hm_matrix_destroy(hm_matrix* H);
+
+/* text of the calling thread's last error ("" if none) */
+const char* hm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HMAT_H */

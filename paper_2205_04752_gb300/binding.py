@@ -1,0 +1,287 @@
+"""Thin ctypes binding of the C ABI in ``include/hmat.h`` (argument marshalling
+only: every step of the hot path runs in the CUDA library).
+
+PyTorch supplies device memory (through the library's allocator hook, wired
+to the caching allocator) and streams.  If the compiled library is missing
+the import fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libhmat.so")
+
+HM_OK, HM_EINVAL, HM_ENOMEM, HM_ENOTCONV, HM_ETIMEOUT, HM_EDEVICE, HM_ERANK = 0, -1, -2, -3, -4, -5, -6
+FP64, FP32, BF16, FP16 = 0, 1, 2, 3
+FORMS = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "fp16": FP16}
+
+# every symbol the header declares
+SYMBOLS = (
+    "hm_build_cluster_tree", "hm_tree_sizes", "hm_tree_export", "hm_tree_destroy",
+    "hm_aca_assemble", "hm_set_material", "hm_pack", "hm_matvec", "hm_matvec_host",
+    "hm_get_stats", "hm_export_factors", "hm_export_near", "hm_matrix_destroy",
+    "hm_last_error",
+)
+
+
+class HMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"hmat error {code}: {msg}")
+        self.code = code
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_double), ("nu", ctypes.c_double), ("aca_eps", ctypes.c_double),
+                ("aca_eta_stop", ctypes.c_double), ("kmax", ctypes.c_int32),
+                ("max_rhs", ctypes.c_int32)]
+
+
+_ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class _Allocator(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_T), ("free", _FREE_T), ("user", ctypes.c_void_p)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int64), ("nadm", ctypes.c_int64), ("nnear", ctypes.c_int64),
+                ("nleaves", ctypes.c_int64), ("near_pairs", ctypes.c_int64),
+                ("far_entries", ctypes.c_int64), ("rank_sum", ctypes.c_int64 * 7),
+                ("rank_max", ctypes.c_int32 * 7), ("rank_cap_hits", ctypes.c_int32),
+                ("csp", ctypes.c_int32), ("bytes_fp64", ctypes.c_int64),
+                ("bytes_form", ctypes.c_int64 * 4), ("assemble_ms", ctypes.c_double * 3)]
+
+
+_lib = None
+
+
+def load():
+    """Load the in-tree library (build it with ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library not built: {LIB_PATH} is missing "
+                          "(run __graft_entry__.build()); there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    sig = {
+        "hm_build_cluster_tree": (ctypes.c_int, [P, I64, P, I64, I32, D, ctypes.POINTER(P)]),
+        "hm_tree_sizes": (ctypes.c_int, [P, P]),
+        "hm_tree_export": (ctypes.c_int, [P, P, P, P, P]),
+        "hm_tree_destroy": (None, [P]),
+        "hm_aca_assemble": (ctypes.c_int, [P, ctypes.POINTER(_Params), ctypes.POINTER(_Allocator),
+                                           P, ctypes.POINTER(P)]),
+        "hm_set_material": (ctypes.c_int, [P, D, D]),
+        "hm_pack": (ctypes.c_int, [P, I32, P]),
+        "hm_matvec": (ctypes.c_int, [P, P, P, I32, I64, I32, P]),
+        "hm_matvec_host": (ctypes.c_int, [P, P, P, I32, I64, I32, P]),
+        "hm_get_stats": (ctypes.c_int, [P, ctypes.POINTER(_Stats)]),
+        "hm_export_factors": (ctypes.c_int, [P, I64, I32, ctypes.POINTER(I32), P, P]),
+        "hm_export_near": (ctypes.c_int, [P, I64, P]),
+        "hm_matrix_destroy": (None, [P]),
+        "hm_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, ok=(HM_OK,)):
+    if rc not in ok:
+        raise HMError(rc, load().hm_last_error().decode())
+    return rc
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class ClusterTree:
+    """Cluster tree and block partition (host), ``hm_build_cluster_tree``."""
+
+    def __init__(self, verts, tris, leaf: int, eta: float):
+        lib = load()
+        self.verts = np.ascontiguousarray(verts, dtype=np.float64)
+        self.tris = np.ascontiguousarray(tris, dtype=np.int32)
+        h = ctypes.c_void_p()
+        _check(lib.hm_build_cluster_tree(_ptr(self.verts), self.verts.shape[0], _ptr(self.tris),
+                                         self.tris.shape[0], int(leaf), float(eta),
+                                         ctypes.byref(h)))
+        self._h = h
+        c = np.zeros(6, dtype=np.int64)
+        _check(lib.hm_tree_sizes(self._h, _ptr(c)))
+        self.M, self.nnodes, self.nadm, self.nnear, self.nleaves, self.depth = map(int, c)
+        self.leaf, self.eta = int(leaf), float(eta)
+
+    def export(self):
+        perm = np.zeros(self.M, dtype=np.int64)
+        nodes = np.zeros((self.nnodes, 5), dtype=np.int64)
+        adm = np.zeros((max(self.nadm, 1), 2), dtype=np.int64)
+        near = np.zeros((max(self.nnear, 1), 2), dtype=np.int64)
+        _check(load().hm_tree_export(self._h, _ptr(perm), _ptr(nodes), _ptr(adm), _ptr(near)))
+        return perm, nodes, adm[:self.nadm], near[:self.nnear]
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.hm_tree_destroy(h)
+            self._h = None
+
+
+def build_cluster_tree(verts, tris, leaf: int, eta: float) -> ClusterTree:
+    return ClusterTree(verts, tris, leaf, eta)
+
+
+def _torch_allocator(device: int):
+    import torch
+
+    def _a(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, int(stream or 0))
+        except Exception:  # reported to the library as a NULL allocation
+            return None
+
+    def _f(ptr, nbytes, stream, user):
+        if ptr:
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+    fa, ff = _ALLOC_T(_a), _FREE_T(_f)
+    return _Allocator(fa, ff, None), (fa, ff)
+
+
+@dataclass
+class Stats:
+    M: int
+    nadm: int
+    nnear: int
+    nleaves: int
+    near_pairs: int
+    far_entries: int
+    rank_sum: list
+    rank_max: list
+    rank_cap_hits: int
+    csp: int
+    bytes_fp64: int
+    bytes_form: list
+    assemble_ms: list
+
+
+class HMatrix:
+    """Assembled H-matrix resident on the device (``hm_aca_assemble``)."""
+
+    def __init__(self, tree: ClusterTree, E: float, nu: float, aca_eps: float,
+                 aca_eta_stop: float = 0.8, kmax: int = 128, max_rhs: int = 32, stream=None,
+                 torch_memory: bool = True):
+        import torch
+        lib = load()
+        self.M = tree.M
+        self.device = torch.cuda.current_device()
+        prm = _Params(float(E), float(nu), float(aca_eps), float(aca_eta_stop), int(kmax),
+                      int(max_rhs))
+        self._alloc_keep = None
+        ap = None
+        if torch_memory:
+            al, keep = _torch_allocator(self.device)
+            self._alloc_struct = al
+            self._alloc_keep = keep
+            ap = ctypes.byref(al)
+        h = ctypes.c_void_p()
+        rc = lib.hm_aca_assemble(tree._h, ctypes.byref(prm), ap, _stream_handle(stream),
+                                 ctypes.byref(h))
+        _check(rc, ok=(HM_OK, HM_ERANK))
+        self.rank_cap_hit = rc == HM_ERANK
+        self._h = h
+        self.max_rhs = int(max_rhs) if max_rhs else 32
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.hm_matrix_destroy(h)
+            self._h = None
+
+    def set_material(self, E: float, nu: float):
+        _check(load().hm_set_material(self._h, float(E), float(nu)))
+
+    def pack(self, form, stream=None):
+        f = FORMS[form] if isinstance(form, str) else int(form)
+        _check(load().hm_pack(self._h, f, _stream_handle(stream)))
+
+    def stats(self) -> Stats:
+        st = _Stats()
+        _check(load().hm_get_stats(self._h, ctypes.byref(st)))
+        return Stats(st.M, st.nadm, st.nnear, st.nleaves, st.near_pairs, st.far_entries,
+                     list(st.rank_sum), list(st.rank_max), st.rank_cap_hits, st.csp,
+                     st.bytes_fp64, list(st.bytes_form), list(st.assemble_ms))
+
+    def export_factors(self, blk: int, kern: int):
+        lib = load()
+        k = ctypes.c_int32(0)
+        _check(lib.hm_export_factors(self._h, int(blk), int(kern), ctypes.byref(k), None, None))
+        return int(k.value)
+
+    def factors(self, blk: int, kern: int, m: int, n: int):
+        lib = load()
+        k = self.export_factors(blk, kern)
+        U = np.zeros((max(k, 1), m))
+        V = np.zeros((max(k, 1), n))
+        kk = ctypes.c_int32(0)
+        _check(lib.hm_export_factors(self._h, int(blk), int(kern), ctypes.byref(kk), _ptr(U),
+                                     _ptr(V)))
+        return U[:k].T.copy(), V[:k].T.copy()
+
+    def near_block(self, blk: int, m: int, n: int):
+        out = np.zeros((6, m, n))
+        _check(load().hm_export_near(self._h, int(blk), _ptr(out)))
+        return out
+
+
+def aca_assemble(tree: ClusterTree, E: float, nu: float, aca_eps: float, **kw) -> HMatrix:
+    return HMatrix(tree, E, nu, aca_eps, **kw)
+
+
+def hmatvec(H: HMatrix, x, y, form="fp64", stream=None):
+    """y = V_h x on the device.  x, y: CUDA float64 tensors of shape (3M,) or
+    (nrhs, 3M) (row stride = ld)."""
+    import torch
+    f = FORMS[form] if isinstance(form, str) else int(form)
+    if not (x.is_cuda and y.is_cuda and x.dtype == torch.float64 and y.dtype == torch.float64):
+        raise TypeError("hmatvec: x and y must be CUDA float64 tensors")
+    nrhs = 1 if x.dim() == 1 else x.shape[0]
+    ld = x.shape[-1] if x.dim() == 1 else x.stride(0)
+    if (y.dim() == 1 and nrhs != 1) or (y.dim() == 2 and (y.shape[0] != nrhs or y.stride(0) != ld)):
+        raise ValueError("hmatvec: y must have the shape and row stride of x")
+    if x.shape[-1] != 3 * H.M or x.stride(-1) != 1 or y.stride(-1) != 1:
+        raise ValueError("hmatvec: rows must be contiguous of length 3M")
+    _check(load().hm_matvec(H._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                            nrhs, ld, f, _stream_handle(stream)))
+    return y
+
+
+def hmatvec_host(H: HMatrix, x: np.ndarray, y: np.ndarray, form="fp64", stream=None):
+    """Same product with host arrays (copies inside the call; synchronous)."""
+    f = FORMS[form] if isinstance(form, str) else int(form)
+    if x.dtype != np.float64 or y.dtype != np.float64:
+        raise TypeError("hmatvec_host: float64 arrays required")
+    nrhs = 1 if x.ndim == 1 else x.shape[0]
+    ld = x.shape[-1] if x.ndim == 1 else x.strides[0] // 8
+    _check(load().hm_matvec_host(H._h, _ptr(x), _ptr(y), nrhs, ld, f, _stream_handle(stream)))
+    return y

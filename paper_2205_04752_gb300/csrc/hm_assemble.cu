@@ -1,0 +1,1076 @@
+// hm_assemble.cu -- device assembly of the collocation Lame single-layer
+// H-matrix: quadrature points, near-field blocks computed entry by entry, and
+// batched ACA (Algorithm 1) over all admissible blocks and scalar kernels.
+//
+// Quadrature contract (the paper names no rule):
+//   * self pair: tau split at its centroid into three sub-triangles; Duffy
+//     map collapsing the apex, exact radial integral, 32 Gauss-Legendre
+//     points for the remaining 1-D integral per sub-triangle;
+//   * other pairs: Radon's 7-point degree-5 rule, on tau_j itself when
+//     |x - g_j|^2 >= 4 diam(tau_j)^2, otherwise on the leaves of a recursive
+//     4-way midpoint subdivision (same test per sub-triangle, depth < 8).
+// The subdivision decisions are taken with separately rounded operations
+// (no FMA) so that they do not depend on instruction selection.
+//
+// Scalar kernels, index kern: 0 V_Delta (1/r), 1 V_11, 2 V_12, 3 V_13, 4 V_22,
+// 5 V_23, 6 V_33 (d_k d_l / r^3, d = x - y), each with the factor 1/(4 pi)
+// (Eq. (Vh), prefactor read as 1/(4 pi)).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "hm_internal.h"
+
+namespace hm {
+namespace {
+
+constexpr int kGL = 32;         // Gauss-Legendre points of the self term
+constexpr int kMaxDepth = 8;    // subdivision depth cap
+constexpr int kStack = 3 * kMaxDepth + 1;
+constexpr int kAcaThreads = 256;
+constexpr int kAcaWarps = kAcaThreads / 32;
+constexpr int kKmaxLimit = 256;
+constexpr double kInv4Pi = 0.07957747154594767;  // 1 / (4 pi)
+constexpr double kAcaDelta = 1e-14;  // "v~ vanishes": max|v~| <= delta max|raw row|
+constexpr double kAcaTie = 1e-10;    // argmax ties: smallest index within this relative gap
+
+__constant__ double c_lam[21];  // Radon 7-point barycentric nodes
+__constant__ double c_w7[7];    // and weights (sum 1)
+__constant__ double c_glx[kGL]; // Gauss-Legendre nodes / weights on [0, 1]
+__constant__ double c_glw[kGL];
+
+struct Geom {
+    const double* coll;   // M x 3, cluster order: collocation points (centroids)
+    const double* tri;    // M x 9: vertices
+    const double* qp;     // M x 21: 7-point nodes
+    const double* qw;     // M x 7: weights * area / (4 pi)
+    const double* diam2;  // M: max squared edge length
+};
+
+// ---------------------------------------------------------------- host tables
+// Radon's rule (Stroud T2:5-1): centroid weight 9/40; nodes (a, a, 1-2a) with
+// a = (6 -+ sqrt 15)/21 and weights (155 -+ sqrt 15)/1200.
+void radon_table(double lam[21], double w[7])
+{
+    const double r15 = std::sqrt(15.0);
+    const double a[2] = {(6.0 - r15) / 21.0, (6.0 + r15) / 21.0};
+    const double wt[2] = {(155.0 - r15) / 1200.0, (155.0 + r15) / 1200.0};
+    lam[0] = lam[1] = lam[2] = 1.0 / 3.0;
+    w[0] = 9.0 / 40.0;
+    int q = 1;
+    for (int g = 0; g < 2; ++g) {
+        const double b = 1.0 - 2.0 * a[g];
+        const double pts[3][3] = {{a[g], a[g], b}, {a[g], b, a[g]}, {b, a[g], a[g]}};
+        for (int p = 0; p < 3; ++p, ++q) {
+            for (int c = 0; c < 3; ++c) lam[3 * q + c] = pts[p][c];
+            w[q] = wt[g];
+        }
+    }
+}
+
+// Gauss-Legendre on [0,1] from the Golub-Welsch view: Newton iteration on the
+// Legendre recurrence from Chebyshev-like starting points.
+void gauss_legendre_table(int n, double* x, double* w)
+{
+    for (int i = 0; i < n; ++i) {
+        double t = std::cos(M_PI * (n - i - 0.25) / (n + 0.5));  // ascending roots
+        double pn = 0.0, pn1 = 0.0;
+        for (int it = 0; it < 60; ++it) {
+            double p0 = 1.0, p1 = t;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2 * k - 1) * t * p1 - (k - 1) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            pn = p1;
+            pn1 = p0;
+            double d = n * (pn1 - t * pn) / (1.0 - t * t);
+            double step = pn / d;
+            t -= step;
+            if (std::fabs(step) < 1e-17) break;
+        }
+        double p0 = 1.0, p1 = t;
+        for (int k = 2; k <= n; ++k) {
+            double p2 = ((2 * k - 1) * t * p1 - (k - 1) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        double d = n * (p0 - t * p1) / (1.0 - t * t);
+        x[i] = 0.5 * (1.0 + t);
+        w[i] = 1.0 / ((1.0 - t * t) * d * d);  // = 0.5 * 2 / ((1-t^2) P_n'^2)
+    }
+}
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ double sq_dist_rn(const double* a, const double* b)
+{
+    double d0 = __dsub_rn(a[0], b[0]), d1 = __dsub_rn(a[1], b[1]), d2 = __dsub_rn(a[2], b[2]);
+    return __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
+}
+
+// x is close to the (sub-)triangle v[0..8] when |x - g|^2 < 4 diam^2
+__device__ __forceinline__ bool is_near_rn(const double* x, const double* v)
+{
+    double g[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[k] = __ddiv_rn(__dadd_rn(__dadd_rn(v[k], v[3 + k]), v[6 + k]), 3.0);
+    double e0 = sq_dist_rn(v, v + 3), e1 = sq_dist_rn(v + 3, v + 6), e2 = sq_dist_rn(v + 6, v);
+    double dm = fmax(fmax(e0, e1), e2);
+    return sq_dist_rn(x, g) < __dmul_rn(4.0, dm);
+}
+
+// accumulate the seven kernels of one source point with weight w (d = x - y)
+__device__ __forceinline__ void point7(double d0, double d1, double d2, double w, double* acc)
+{
+    double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+    double ir = rsqrt(r2);
+    double wir = w * ir;
+    double wir3 = wir * ir * ir;
+    acc[0] += wir;
+    acc[1] += wir3 * d0 * d0;
+    acc[2] += wir3 * d0 * d1;
+    acc[3] += wir3 * d0 * d2;
+    acc[4] += wir3 * d1 * d1;
+    acc[5] += wir3 * d1 * d2;
+    acc[6] += wir3 * d2 * d2;
+}
+
+// 7-point rule on one (sub-)triangle v, all kernels, weights include area
+__device__ void rule7_all(const double* x, const double* v, double* acc)
+{
+    double u[3], w[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        u[k] = v[3 + k] - v[k];
+        w[k] = v[6 + k] - v[k];
+    }
+    double n0 = u[1] * w[2] - u[2] * w[1], n1 = u[2] * w[0] - u[0] * w[2],
+           n2 = u[0] * w[1] - u[1] * w[0];
+    double area = 0.5 * sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+    double s[7] = {0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        double y[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            y[k] = c_lam[3 * q] * v[k] + c_lam[3 * q + 1] * v[3 + k] + c_lam[3 * q + 2] * v[6 + k];
+        point7(x[0] - y[0], x[1] - y[1], x[2] - y[2], c_w7[q], s);
+    }
+#pragma unroll
+    for (int c = 0; c < 7; ++c) acc[c] += area * s[c];
+}
+
+// adaptive rule for a point outside triangle v: depth-first over the midpoint
+// subdivision (children: corner 0, corner 1, corner 2, middle)
+__device__ void adaptive7(const double* x, const double* v0, double* acc)
+{
+    double st[kStack][9];
+    int dep[kStack];
+    int top = 0;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) st[0][c] = v0[c];
+    dep[0] = 0;
+    top = 1;
+    while (top > 0) {
+        --top;
+        double v[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) v[c] = st[top][c];
+        int d = dep[top];
+        if (d < kMaxDepth && is_near_rn(x, v)) {
+            double ab[3], bc[3], ca[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                ab[k] = __dmul_rn(__dadd_rn(v[k], v[3 + k]), 0.5);
+                bc[k] = __dmul_rn(__dadd_rn(v[3 + k], v[6 + k]), 0.5);
+                ca[k] = __dmul_rn(__dadd_rn(v[6 + k], v[k]), 0.5);
+            }
+            // push in reverse so that the pop order is corner 0, 1, 2, middle
+            const double* kids[4][3] = {{ab, bc, ca}, {ca, bc, v + 6}, {ab, v + 3, bc}, {v, ab, ca}};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+#pragma unroll
+                for (int p = 0; p < 3; ++p)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) st[top][3 * p + k] = kids[q][p][k];
+                dep[top] = d + 1;
+                ++top;
+            }
+        } else {
+            rule7_all(x, v, acc);
+        }
+    }
+}
+
+// self pair: x is the centroid of v; Duffy map per edge sub-triangle
+__device__ void self7(const double* x, const double* v, double* acc)
+{
+#pragma unroll 1
+    for (int e = 0; e < 3; ++e) {
+        const double* pa = v + 3 * e;
+        const double* pb = v + 3 * ((e + 1) % 3);
+        double a[3], b[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            a[k] = pa[k] - x[k];
+            b[k] = pb[k] - pa[k];
+        }
+        double n0 = a[1] * b[2] - a[2] * b[1], n1 = a[2] * b[0] - a[0] * b[2],
+               n2 = a[0] * b[1] - a[1] * b[0];
+        double cr = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+#pragma unroll 4
+        for (int q = 0; q < kGL; ++q) {
+            double t = c_glx[q];
+            point7(a[0] + t * b[0], a[1] + t * b[1], a[2] + t * b[2], c_glw[q] * cr, acc);
+        }
+    }
+}
+
+// all seven kernels of pair (i, j) (cluster positions), times 1/(4 pi)
+__device__ void entry7(const Geom& g, int i, int j, double* acc)
+{
+#pragma unroll
+    for (int c = 0; c < 7; ++c) acc[c] = 0.0;
+    const double* x = g.coll + 3 * (size_t)i;
+    const double* v = g.tri + 9 * (size_t)j;
+    if (i == j) {
+        self7(x, v, acc);
+    } else if (sq_dist_rn(x, g.coll + 3 * (size_t)j) < __dmul_rn(4.0, g.diam2[j])) {
+        adaptive7(x, v, acc);
+    } else {
+        const double* qp = g.qp + 21 * (size_t)j;
+        const double* qw = g.qw + 7 * (size_t)j;
+#pragma unroll
+        for (int q = 0; q < 7; ++q)
+            point7(x[0] - qp[3 * q], x[1] - qp[3 * q + 1], x[2] - qp[3 * q + 2], qw[q], acc);
+        return;  // qw already holds 1/(4 pi)
+    }
+#pragma unroll
+    for (int c = 0; c < 7; ++c) acc[c] *= kInv4Pi;
+}
+
+// one scalar kernel of pair (i, j): the far (7-point) path is specialised
+__device__ __forceinline__ double entry1(const Geom& g, int i, int j, int kern, int ka, int kb)
+{
+    const double* x = g.coll + 3 * (size_t)i;
+    if (i != j && !(sq_dist_rn(x, g.coll + 3 * (size_t)j) < __dmul_rn(4.0, g.diam2[j]))) {
+        const double* qp = g.qp + 21 * (size_t)j;
+        const double* qw = g.qw + 7 * (size_t)j;
+        double x0 = x[0], x1 = x[1], x2 = x[2];
+        double acc = 0.0;
+        if (kern == 0) {
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                double d0 = x0 - qp[3 * q], d1 = x1 - qp[3 * q + 1], d2 = x2 - qp[3 * q + 2];
+                acc += qw[q] * rsqrt(d0 * d0 + d1 * d1 + d2 * d2);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                double d0 = x0 - qp[3 * q], d1 = x1 - qp[3 * q + 1], d2 = x2 - qp[3 * q + 2];
+                double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+                double ir = rsqrt(r2);
+                double da = ka == 0 ? d0 : (ka == 1 ? d1 : d2);
+                double db = kb == 0 ? d0 : (kb == 1 ? d1 : d2);
+                acc += qw[q] * ir * ir * ir * (da * db);
+            }
+        }
+        return acc;
+    }
+    double a7[7];
+    entry7(g, i, j, a7);
+    return a7[kern];
+}
+
+// ---------------------------------------------------------------- geometry kernel
+__global__ void geom_kernel(int M, const int32_t* __restrict__ perm, const int32_t* __restrict__ T,
+                            const double* __restrict__ V, double* __restrict__ tri,
+                            double* __restrict__ qp, double* __restrict__ qw)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= M) return;
+    int t = perm[p];
+    double v[9];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v[3 * c + k] = V[3 * (size_t)T[3 * (size_t)t + c] + k];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) tri[9 * (size_t)p + c] = v[c];
+    double u[3], w[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        u[k] = v[3 + k] - v[k];
+        w[k] = v[6 + k] - v[k];
+    }
+    double n0 = u[1] * w[2] - u[2] * w[1], n1 = u[2] * w[0] - u[0] * w[2], n2 = u[0] * w[1] - u[1] * w[0];
+    double area = 0.5 * sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            qp[21 * (size_t)p + 3 * q + k] =
+                c_lam[3 * q] * v[k] + c_lam[3 * q + 1] * v[3 + k] + c_lam[3 * q + 2] * v[6 + k];
+        qw[7 * (size_t)p + q] = c_w7[q] * area * kInv4Pi;
+    }
+}
+
+// ---------------------------------------------------------------- near field
+// One CTA per near block; output per block [v][j][i] (i fastest), v = the six
+// kernels V_11..V_33 (V_Delta is their trace).
+__global__ void __launch_bounds__(128) near_kernel(Geom g, const Blk* __restrict__ blks,
+                                                   const int64_t* __restrict__ noff,
+                                                   double* __restrict__ N)
+{
+    Blk b = blks[blockIdx.x];
+    double* out = N + noff[blockIdx.x];
+    int pairs = b.m * b.n;
+    for (int e = threadIdx.x; e < pairs; e += blockDim.x) {
+        int j = e / b.m, i = e - j * b.m;
+        double a[7];
+        entry7(g, b.t0 + i, b.s0 + j, a);
+#pragma unroll
+        for (int v = 0; v < 6; ++v) out[(size_t)v * pairs + e] = a[1 + v];
+    }
+}
+
+// ---------------------------------------------------------------- batched ACA
+struct AcaTask {
+    int32_t blk, kern;
+};
+
+struct AcaParams {
+    double fac;        // eps (1 - eta_stop) / (1 + eps)
+    int32_t kmax;
+    int32_t kcap_all;  // columns reserved per CTA in scratch
+    int32_t mmax, nmax;
+};
+
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ int warp_min_i(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+struct AcaShared {
+    double su[kKmaxLimit];   // U[l][i_k] for the residual row
+    double sv[kKmaxLimit];   // V[l][j_k] for the residual column
+    double red[kAcaWarps][2 * kKmaxLimit + 2];
+    double bc[4];
+    int ibc[2];
+    int task;
+};
+
+__device__ double block_max(AcaShared& sh, double v)
+{
+    v = warp_max(v);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh.red[w][0] = v;
+    __syncthreads();
+    double r = sh.red[0][0];
+    for (int q = 1; q < kAcaWarps; ++q) r = fmax(r, sh.red[q][0]);
+    return r;
+}
+
+__device__ void block_max2(AcaShared& sh, double& a, double& b)
+{
+    a = warp_max(a);
+    b = warp_max(b);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) {
+        sh.red[w][0] = a;
+        sh.red[w][1] = b;
+    }
+    __syncthreads();
+    double ra = sh.red[0][0], rb = sh.red[0][1];
+    for (int q = 1; q < kAcaWarps; ++q) {
+        ra = fmax(ra, sh.red[q][0]);
+        rb = fmax(rb, sh.red[q][1]);
+    }
+    a = ra;
+    b = rb;
+}
+
+__device__ int block_min_i(AcaShared& sh, int v)
+{
+    v = warp_min_i(v);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh.red[w][0] = (double)v;
+    __syncthreads();
+    double r = sh.red[0][0];
+    for (int q = 1; q < kAcaWarps; ++q) r = fmin(r, sh.red[q][0]);
+    return (int)r;
+}
+
+// next pivot row: the smallest row outside Z whose |u| is within the tie gap
+// of the largest |u| outside Z; the smallest row outside Z if u vanishes there
+__device__ int next_row(AcaShared& sh, const double* u, const unsigned char* Z, int m)
+{
+    double mx = 0.0;
+    if (u)
+        for (int i = threadIdx.x; i < m; i += blockDim.x)
+            if (!Z[i]) mx = fmax(mx, fabs(u[i]));
+    mx = block_max(sh, mx);
+    int cand = INT_MAX;
+    if (mx > 0.0) {
+        double thr = mx * (1.0 - kAcaTie);
+        for (int i = threadIdx.x; i < m; i += blockDim.x)
+            if (!Z[i] && fabs(u[i]) >= thr) {
+                cand = i;
+                break;
+            }
+    } else {
+        for (int i = threadIdx.x; i < m; i += blockDim.x)
+            if (!Z[i]) {
+                cand = i;
+                break;
+            }
+    }
+    return block_min_i(sh, cand);
+}
+
+// Persistent batched ACA.  Each CTA takes tasks (admissible block, scalar
+// kernel) from a global counter, largest blocks first, and runs Algorithm 1
+// with its U / V columns in its own slice of `scratch`; the finished factors
+// (U: m x k, then V: n x k, both column-major) are appended to `arena` at an
+// offset taken with atomicAdd and repacked in block order afterwards.
+__global__ void __launch_bounds__(kAcaThreads) aca_kernel(
+    Geom g, const AcaTask* __restrict__ tasks, int ntask, const Blk* __restrict__ blks,
+    AcaParams prm, double* __restrict__ scratch, unsigned char* __restrict__ zscr,
+    int* __restrict__ counter, double* __restrict__ arena, unsigned long long* __restrict__ arena_top,
+    unsigned long long arena_cap, int32_t* __restrict__ out_rank, int64_t* __restrict__ out_off,
+    int32_t* __restrict__ out_flags)
+{
+    __shared__ AcaShared sh;
+    const int tid = threadIdx.x;
+    const int B = blockDim.x;
+    double* U = scratch + (size_t)blockIdx.x * (size_t)prm.kcap_all * (prm.mmax + prm.nmax);
+    double* Vf = U + (size_t)prm.kcap_all * prm.mmax;
+    unsigned char* Z = zscr + (size_t)blockIdx.x * prm.mmax;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) sh.task = atomicAdd(counter, 1);
+        __syncthreads();
+        const int task = sh.task;
+        if (task >= ntask) break;
+        const AcaTask tk = tasks[task];
+        const Blk b = blks[tk.blk];
+        const int m = b.m, n = b.n, kern = tk.kern;
+        const int ka = kern == 0 ? 0 : (kern <= 3 ? 0 : (kern <= 5 ? 1 : 2));
+        const int kb = kern == 0 ? 0 : (kern <= 3 ? kern - 1 : (kern <= 5 ? kern - 3 : 2));
+        int kcap = min(prm.kmax, min(m, n));
+        for (int i = tid; i < m; i += B) Z[i] = 0;
+        int k = 0, nz = 0, flags = 0, irow = 0;
+        double S2 = 0.0;
+        __syncthreads();
+        for (;;) {
+            if (k >= prm.kmax) {
+                flags |= 1;
+                break;
+            }
+            // residual row  v~ = A[i, s] - sum_{l<k} (u_l)_i v_l
+            for (int l = tid; l < k; l += B) sh.su[l] = U[(size_t)l * m + irow];
+            __syncthreads();
+            double* vk = Vf + (size_t)k * n;
+            double mraw = 0.0, mres = 0.0;
+            for (int j = tid; j < n; j += B) {
+                double a = entry1(g, b.t0 + irow, b.s0 + j, kern, ka, kb);
+                double s = a;
+                for (int l = 0; l < k; ++l) s -= sh.su[l] * Vf[(size_t)l * n + j];
+                vk[j] = s;
+                mraw = fmax(mraw, fabs(a));
+                mres = fmax(mres, fabs(s));
+            }
+            block_max2(sh, mraw, mres);
+            if (tid == 0) Z[irow] = 1;
+            ++nz;
+            if (!(mres > 0.0) || mres <= kAcaDelta * mraw) {
+                // vanishing row: try another one
+                if (nz == m) {
+                    flags |= 2;
+                    break;
+                }
+                __syncthreads();
+                irow = next_row(sh, k > 0 ? U + (size_t)(k - 1) * m : nullptr, Z, m);
+                if (irow >= m) {
+                    flags |= 16;
+                    break;
+                }
+                continue;
+            }
+            // pivot column: smallest j with |v~_j| >= (1 - tie) max
+            double thr = mres * (1.0 - kAcaTie);
+            int cand = INT_MAX;
+            for (int j = tid; j < n; j += B)
+                if (fabs(vk[j]) >= thr) {
+                    cand = j;
+                    break;
+                }
+            const int jk = block_min_i(sh, cand);
+            if (jk >= n) {  // no finite pivot (non-finite entries): give up on this block
+                flags |= 16;
+                break;
+            }
+            const double inv = 1.0 / vk[jk];
+            __syncthreads();  // everyone has read the pivot before it is scaled
+            double tvv = 0.0;
+            for (int j = tid; j < n; j += B) {
+                double s = vk[j] * inv;
+                vk[j] = s;
+                tvv += s * s;
+            }
+            for (int l = tid; l < k; l += B) sh.sv[l] = Vf[(size_t)l * n + jk];
+            __syncthreads();
+            // residual column  u_k = A[t, j_k] - sum_{l<k} (v_l)_{j_k} u_l
+            double* uk = U + (size_t)k * m;
+            double tuu = 0.0;
+            for (int i = tid; i < m; i += B) {
+                double a = entry1(g, b.t0 + i, b.s0 + jk, kern, ka, kb);
+                double s = a;
+                for (int l = 0; l < k; ++l) s -= sh.sv[l] * U[(size_t)l * m + i];
+                uk[i] = s;
+                tuu += s * s;
+            }
+            __syncthreads();
+            // ||S_k||_F^2 = ||S_{k-1}||^2 + 2 sum_l (u_k.u_l)(v_l.v_k) + |u_k|^2 |v_k|^2
+            const int w = tid >> 5, ln = tid & 31;
+            for (int l = 0; l < k; ++l) {
+                double pa = 0.0, pb = 0.0;
+                for (int i = tid; i < m; i += B) pa += uk[i] * U[(size_t)l * m + i];
+                for (int j = tid; j < n; j += B) pb += Vf[(size_t)l * n + j] * vk[j];
+                pa = warp_sum(pa);
+                pb = warp_sum(pb);
+                if (ln == 0) {
+                    sh.red[w][2 * l] = pa;
+                    sh.red[w][2 * l + 1] = pb;
+                }
+            }
+            tuu = warp_sum(tuu);
+            tvv = warp_sum(tvv);
+            if (ln == 0) {
+                sh.red[w][2 * k] = tuu;
+                sh.red[w][2 * k + 1] = tvv;
+            }
+            __syncthreads();
+            if (tid < 32) {
+                double cr = 0.0;
+                for (int l = tid; l < k; l += 32) {
+                    double a = 0.0, c = 0.0;
+                    for (int q = 0; q < kAcaWarps; ++q) {
+                        a += sh.red[q][2 * l];
+                        c += sh.red[q][2 * l + 1];
+                    }
+                    cr += a * c;
+                }
+                cr = warp_sum(cr);
+                if (tid == 0) {
+                    double uu = 0.0, vv = 0.0;
+                    for (int q = 0; q < kAcaWarps; ++q) {
+                        uu += sh.red[q][2 * k];
+                        vv += sh.red[q][2 * k + 1];
+                    }
+                    sh.bc[0] = cr;
+                    sh.bc[1] = uu;
+                    sh.bc[2] = vv;
+                }
+            }
+            __syncthreads();
+            const double uu = sh.bc[1], vv = sh.bc[2];
+            S2 = S2 + 2.0 * sh.bc[0] + uu * vv;
+            ++k;
+            if (sqrt(uu * vv) <= prm.fac * sqrt(fmax(S2, 0.0))) break;
+            if (nz == m) {
+                flags |= 2;
+                break;
+            }
+            if (k >= kcap) {
+                flags |= 4;
+                break;
+            }
+            __syncthreads();
+            irow = next_row(sh, uk, Z, m);
+            if (irow >= m) {
+                flags |= 16;
+                break;
+            }
+        }
+        // append the factors to the arena
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long need = (unsigned long long)k * (m + n);
+            unsigned long long off = atomicAdd(arena_top, need);
+            if (off + need > arena_cap) {
+                sh.ibc[0] = -1;
+            } else {
+                sh.ibc[0] = 0;
+                out_off[task] = (int64_t)off;
+            }
+            out_rank[task] = k;
+        }
+        __syncthreads();
+        if (sh.ibc[0] < 0) {
+            flags |= 8;
+        } else if (k > 0) {
+            double* dst = arena + out_off[task];
+            for (int l = 0; l < k; ++l) {
+                for (int i = tid; i < m; i += B) dst[(size_t)l * m + i] = U[(size_t)l * m + i];
+            }
+            double* dv = dst + (size_t)k * m;
+            for (int l = 0; l < k; ++l) {
+                for (int j = tid; j < n; j += B) dv[(size_t)l * n + j] = Vf[(size_t)l * n + j];
+            }
+        }
+        if (tid == 0) out_flags[task] = flags;
+    }
+}
+
+// copy finished factors from the arena into the block-ordered U / V arenas
+__global__ void repack_kernel(const AcaTask* __restrict__ tasks, int ntask,
+                              const Blk* __restrict__ blks, const int32_t* __restrict__ rank,
+                              const int64_t* __restrict__ off, const double* __restrict__ arena,
+                              const int64_t* __restrict__ uoff, const int64_t* __restrict__ voff,
+                              double* __restrict__ U, double* __restrict__ V)
+{
+    int task = blockIdx.x;
+    if (task >= ntask) return;
+    AcaTask tk = tasks[task];
+    int k = rank[task];
+    if (k == 0) return;
+    Blk b = blks[tk.blk];
+    const double* src = arena + off[task];
+    size_t q = (size_t)tk.blk * 7 + tk.kern;
+    double* du = U + uoff[q];
+    double* dv = V + voff[q];
+    size_t nu = (size_t)k * b.m, nv = (size_t)k * b.n;
+    for (size_t e = threadIdx.x; e < nu; e += blockDim.x) du[e] = src[e];
+    for (size_t e = threadIdx.x; e < nv; e += blockDim.x) dv[e] = src[nu + e];
+}
+
+int upload(hm_matrix& H, DevBuf& d, const void* src, size_t bytes)
+{
+    d.bytes = bytes;
+    d.p = H.alloc.alloc(bytes);
+    if (!d.p) return fail(HM_ENOMEM, "device allocation of %zu bytes failed", bytes);
+    if (bytes) HM_CUDA(cudaMemcpyAsync(d.p, src, bytes, cudaMemcpyHostToDevice, H.alloc.stream));
+    return HM_OK;
+}
+
+int dalloc(hm_matrix& H, DevBuf& d, size_t bytes)
+{
+    d.bytes = bytes;
+    d.p = H.alloc.alloc(bytes);
+    if (!d.p) return fail(HM_ENOMEM, "device allocation of %zu bytes failed", bytes);
+    return HM_OK;
+}
+
+struct TmpBuf {
+    hm_matrix& H;
+    DevBuf b;
+    explicit TmpBuf(hm_matrix& h) : H(h) {}
+    ~TmpBuf() { H.alloc.release(b.p, b.bytes); }
+};
+
+}  // namespace
+
+// ------------------------------------------------------------------------
+int assemble_device(const hm_tree& tr, hm_matrix& H)
+{
+    cudaStream_t s = H.alloc.stream;
+    const int64_t M = tr.M;
+    H.M = M;
+    {
+        double lam[21], w7[7], gx[kGL], gw[kGL];
+        radon_table(lam, w7);
+        gauss_legendre_table(kGL, gx, gw);
+        HM_CUDA(cudaMemcpyToSymbolAsync(c_lam, lam, sizeof lam, 0, cudaMemcpyHostToDevice, s));
+        HM_CUDA(cudaMemcpyToSymbolAsync(c_w7, w7, sizeof w7, 0, cudaMemcpyHostToDevice, s));
+        HM_CUDA(cudaMemcpyToSymbolAsync(c_glx, gx, sizeof gx, 0, cudaMemcpyHostToDevice, s));
+        HM_CUDA(cudaMemcpyToSymbolAsync(c_glw, gw, sizeof gw, 0, cudaMemcpyHostToDevice, s));
+    }
+    // ---- geometry in cluster order
+    std::vector<int32_t> perm32((size_t)M);
+    std::vector<double> coll((size_t)(3 * M)), diam2((size_t)M);
+    for (int64_t p = 0; p < M; ++p) {
+        int64_t t = tr.perm[(size_t)p];
+        perm32[(size_t)p] = (int32_t)t;
+        for (int k = 0; k < 3; ++k) coll[(size_t)(3 * p + k)] = tr.coll[(size_t)(3 * t + k)];
+        const double* v[3];
+        for (int c = 0; c < 3; ++c) v[c] = &tr.V[3 * (size_t)tr.T[(size_t)(3 * t + c)]];
+        double dm = 0.0;
+        for (int e = 0; e < 3; ++e) {
+            const double* a = v[e];
+            const double* b = v[(e + 1) % 3];
+            double d0 = a[0] - b[0], d1 = a[1] - b[1], d2 = a[2] - b[2];
+            double q = d0 * d0 + d1 * d1 + d2 * d2;  // host code: no contraction
+            dm = std::max(dm, q);
+        }
+        diam2[(size_t)p] = dm;
+    }
+    int rc;
+    if ((rc = upload(H, H.d_perm, perm32.data(), perm32.size() * 4))) return rc;
+    TmpBuf dV(H), dT(H), dcoll(H), dtri(H), dqp(H), dqw(H), ddiam(H);
+    if ((rc = upload(H, dV.b, tr.V.data(), tr.V.size() * 8))) return rc;
+    if ((rc = upload(H, dT.b, tr.T.data(), tr.T.size() * 4))) return rc;
+    if ((rc = upload(H, dcoll.b, coll.data(), coll.size() * 8))) return rc;
+    if ((rc = upload(H, ddiam.b, diam2.data(), diam2.size() * 8))) return rc;
+    if ((rc = dalloc(H, dtri.b, (size_t)M * 9 * 8))) return rc;
+    if ((rc = dalloc(H, dqp.b, (size_t)M * 21 * 8))) return rc;
+    if ((rc = dalloc(H, dqw.b, (size_t)M * 7 * 8))) return rc;
+    geom_kernel<<<(unsigned)((M + 127) / 128), 128, 0, s>>>((int)M, H.d_perm.as<int32_t>(),
+                                                            dT.b.as<int32_t>(), dV.b.as<double>(),
+                                                            dtri.b.as<double>(), dqp.b.as<double>(),
+                                                            dqw.b.as<double>());
+    HM_CUDA(cudaGetLastError());
+    Geom g{dcoll.b.as<double>(), dtri.b.as<double>(), dqp.b.as<double>(), dqw.b.as<double>(),
+           ddiam.b.as<double>()};
+
+    // ---- block lists
+    auto blk_of = [&](const std::array<int64_t, 2>& ts) {
+        const Node& a = tr.nodes[(size_t)ts[0]];
+        const Node& c = tr.nodes[(size_t)ts[1]];
+        return Blk{(int32_t)a.lo, (int32_t)(a.hi - a.lo), (int32_t)c.lo, (int32_t)(c.hi - c.lo)};
+    };
+    H.nadm = (int64_t)tr.adm.size();
+    H.nnear = (int64_t)tr.near_blocks.size();
+    H.adm_h.resize((size_t)H.nadm);
+    H.near_h.resize((size_t)H.nnear);
+    for (int64_t b = 0; b < H.nadm; ++b) H.adm_h[(size_t)b] = blk_of(tr.adm[(size_t)b]);
+    for (int64_t b = 0; b < H.nnear; ++b) H.near_h[(size_t)b] = blk_of(tr.near_blocks[(size_t)b]);
+    if ((rc = upload(H, H.d_adm, H.adm_h.data(), H.adm_h.size() * sizeof(Blk)))) return rc;
+    if ((rc = upload(H, H.d_near, H.near_h.data(), H.near_h.size() * sizeof(Blk)))) return rc;
+
+    cudaEvent_t ev[4];
+    for (auto& e : ev) HM_CUDA(cudaEventCreate(&e));
+    struct EvGuard {
+        cudaEvent_t* e;
+        ~EvGuard()
+        {
+            for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
+        }
+    } evg{ev};
+
+    // ---- near field
+    H.noff_h.resize((size_t)H.nnear);
+    int64_t ntot = 0;
+    for (int64_t b = 0; b < H.nnear; ++b) {
+        H.noff_h[(size_t)b] = ntot;
+        ntot += 6 * (int64_t)H.near_h[(size_t)b].m * H.near_h[(size_t)b].n;
+    }
+    H.n_total = ntot;
+    if ((rc = upload(H, H.d_noff, H.noff_h.data(), H.noff_h.size() * 8))) return rc;
+    if ((rc = dalloc(H, H.N64, (size_t)std::max<int64_t>(ntot, 1) * 8))) return rc;
+    HM_CUDA(cudaEventRecord(ev[0], s));
+    if (H.nnear > 0) {
+        near_kernel<<<(unsigned)H.nnear, 128, 0, s>>>(g, H.d_near.as<Blk>(), H.d_noff.as<int64_t>(),
+                                                      H.N64.as<double>());
+        HM_CUDA(cudaGetLastError());
+    }
+    HM_CUDA(cudaEventRecord(ev[1], s));
+
+    // ---- batched ACA
+    const int64_t ntask = H.nadm * 7;
+    H.rank_h.assign((size_t)ntask, 0);
+    H.flags_h.assign((size_t)ntask, 0);
+    std::vector<AcaTask> tasks((size_t)ntask);
+    for (int64_t b = 0; b < H.nadm; ++b)
+        for (int k = 0; k < 7; ++k) tasks[(size_t)(b * 7 + k)] = AcaTask{(int32_t)b, k};
+    std::stable_sort(tasks.begin(), tasks.end(), [&](const AcaTask& x, const AcaTask& y) {
+        const Blk& a = H.adm_h[(size_t)x.blk];
+        const Blk& c = H.adm_h[(size_t)y.blk];
+        return (int64_t)a.m + a.n > (int64_t)c.m + c.n;
+    });
+    std::vector<int32_t> trank((size_t)ntask, 0), tflags((size_t)ntask, 0);
+    std::vector<int64_t> toff((size_t)ntask, 0);
+    TmpBuf darena(H), dscr(H), dz(H), dtask(H), dcnt(H), dtop(H), drank(H), doff(H), dflag(H);
+    if (ntask > 0) {
+        int mmax = 0, nmax = 0, kc = 0;
+        double est = 0.0;
+        for (const Blk& b : H.adm_h) {
+            mmax = std::max(mmax, b.m);
+            nmax = std::max(nmax, b.n);
+            kc = std::max(kc, std::min(b.m, b.n));
+            est += 7.0 * (b.m + b.n) * std::min(24, std::min(b.m, b.n));
+        }
+        AcaParams prm;
+        double eps = H.prm.aca_eps;
+        prm.fac = eps * (1.0 - H.prm.aca_eta_stop) / (1.0 + eps);
+        prm.kmax = H.prm.kmax;
+        prm.kcap_all = std::max(1, std::min(kc, H.prm.kmax));
+        prm.mmax = mmax;
+        prm.nmax = nmax;
+        int dev = 0, nsm = 0, occ = 0;
+        HM_CUDA(cudaGetDevice(&dev));
+        HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, aca_kernel, kAcaThreads, 0));
+        int64_t grid = std::min<int64_t>(ntask, (int64_t)nsm * std::max(1, std::min(occ, 4)));
+        size_t per_cta = (size_t)prm.kcap_all * (mmax + nmax);
+        if ((rc = dalloc(H, dscr.b, (size_t)grid * per_cta * 8))) return rc;
+        if ((rc = dalloc(H, dz.b, (size_t)grid * mmax))) return rc;
+        if ((rc = upload(H, dtask.b, tasks.data(), tasks.size() * sizeof(AcaTask)))) return rc;
+        if ((rc = dalloc(H, dcnt.b, 64))) return rc;
+        if ((rc = dalloc(H, dtop.b, 64))) return rc;
+        if ((rc = dalloc(H, drank.b, (size_t)ntask * 4))) return rc;
+        if ((rc = dalloc(H, doff.b, (size_t)ntask * 8))) return rc;
+        if ((rc = dalloc(H, dflag.b, (size_t)ntask * 4))) return rc;
+        unsigned long long cap = (unsigned long long)(est * 1.25) + (1ull << 20);
+        if ((rc = dalloc(H, darena.b, (size_t)cap * 8))) return rc;
+        HM_CUDA(cudaMemsetAsync(dcnt.b.p, 0, 64, s));
+        HM_CUDA(cudaMemsetAsync(dtop.b.p, 0, 64, s));
+        aca_kernel<<<(unsigned)grid, kAcaThreads, 0, s>>>(
+            g, dtask.b.as<AcaTask>(), (int)ntask, H.d_adm.as<Blk>(), prm, dscr.b.as<double>(),
+            dz.b.as<unsigned char>(), dcnt.b.as<int>(), darena.b.as<double>(),
+            dtop.b.as<unsigned long long>(), cap, drank.b.as<int32_t>(), doff.b.as<int64_t>(),
+            dflag.b.as<int32_t>());
+        HM_CUDA(cudaGetLastError());
+        HM_CUDA(cudaMemcpyAsync(trank.data(), drank.b.p, (size_t)ntask * 4, cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaMemcpyAsync(toff.data(), doff.b.p, (size_t)ntask * 8, cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaMemcpyAsync(tflags.data(), dflag.b.p, (size_t)ntask * 4, cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaStreamSynchronize(s));
+        // tasks whose factors did not fit: run them again into an arena of the
+        // exact size (ACA is deterministic, so the result is the same)
+        std::vector<AcaTask> redo;
+        std::vector<int64_t> redo_idx;
+        unsigned long long need = 0;
+        for (int64_t q = 0; q < ntask; ++q)
+            if (tflags[(size_t)q] & 8) {
+                redo.push_back(tasks[(size_t)q]);
+                redo_idx.push_back(q);
+                const Blk& b = H.adm_h[(size_t)tasks[(size_t)q].blk];
+                need += (unsigned long long)trank[(size_t)q] * (b.m + b.n);
+            }
+        if (!redo.empty()) {
+            TmpBuf a2(H), t2(H), r2(H), o2(H), f2(H);
+            if ((rc = dalloc(H, a2.b, (size_t)(need + 1) * 8))) return rc;
+            if ((rc = upload(H, t2.b, redo.data(), redo.size() * sizeof(AcaTask)))) return rc;
+            if ((rc = dalloc(H, r2.b, redo.size() * 4))) return rc;
+            if ((rc = dalloc(H, o2.b, redo.size() * 8))) return rc;
+            if ((rc = dalloc(H, f2.b, redo.size() * 4))) return rc;
+            HM_CUDA(cudaMemsetAsync(dcnt.b.p, 0, 64, s));
+            HM_CUDA(cudaMemsetAsync(dtop.b.p, 0, 64, s));
+            int64_t g2 = std::min<int64_t>((int64_t)redo.size(), grid);
+            aca_kernel<<<(unsigned)g2, kAcaThreads, 0, s>>>(
+                g, t2.b.as<AcaTask>(), (int)redo.size(), H.d_adm.as<Blk>(), prm, dscr.b.as<double>(),
+                dz.b.as<unsigned char>(), dcnt.b.as<int>(), a2.b.as<double>(),
+                dtop.b.as<unsigned long long>(), need + 1, r2.b.as<int32_t>(), o2.b.as<int64_t>(),
+                f2.b.as<int32_t>());
+            HM_CUDA(cudaGetLastError());
+            // fold the re-run results into the main arena: grow it and append
+            std::vector<int32_t> rr(redo.size()), ff(redo.size());
+            std::vector<int64_t> oo(redo.size());
+            HM_CUDA(cudaMemcpyAsync(rr.data(), r2.b.p, rr.size() * 4, cudaMemcpyDeviceToHost, s));
+            HM_CUDA(cudaMemcpyAsync(oo.data(), o2.b.p, oo.size() * 8, cudaMemcpyDeviceToHost, s));
+            HM_CUDA(cudaMemcpyAsync(ff.data(), f2.b.p, ff.size() * 4, cudaMemcpyDeviceToHost, s));
+            HM_CUDA(cudaStreamSynchronize(s));
+            // new combined arena: old contents (first cap) + re-run contents
+            DevBuf big;
+            if ((rc = dalloc(H, big, (size_t)(cap + need + 1) * 8))) return rc;
+            HM_CUDA(cudaMemcpyAsync(big.p, darena.b.p, (size_t)cap * 8, cudaMemcpyDeviceToDevice, s));
+            HM_CUDA(cudaMemcpyAsync(big.as<double>() + cap, a2.b.p, (size_t)need * 8,
+                                    cudaMemcpyDeviceToDevice, s));
+            HM_CUDA(cudaStreamSynchronize(s));  // copies done before the sources are released
+            H.alloc.release(darena.b.p, darena.b.bytes);
+            darena.b = big;
+            for (size_t q = 0; q < redo.size(); ++q) {
+                size_t t = (size_t)redo_idx[q];
+                trank[t] = rr[q];
+                toff[t] = (int64_t)cap + oo[q];
+                tflags[t] = ff[q];
+            }
+            if ((rc = cuda_check(cudaMemcpyAsync(drank.b.p, trank.data(), (size_t)ntask * 4,
+                                                 cudaMemcpyHostToDevice, s), "rank upload")))
+                return rc;
+            if ((rc = cuda_check(cudaMemcpyAsync(doff.b.p, toff.data(), (size_t)ntask * 8,
+                                                 cudaMemcpyHostToDevice, s), "offset upload")))
+                return rc;
+            HM_CUDA(cudaStreamSynchronize(s));
+            for (int32_t f : ff)
+                if (f & 8) return fail(HM_EDEVICE, "ACA factor arena overflow on re-run");
+        }
+    }
+    HM_CUDA(cudaEventRecord(ev[2], s));
+
+    // ---- block-ordered FP64 factor arenas
+    for (int64_t q = 0; q < ntask; ++q) {
+        const AcaTask& tk = tasks[(size_t)q];
+        H.rank_h[(size_t)(tk.blk * 7 + tk.kern)] = trank[(size_t)q];
+        H.flags_h[(size_t)(tk.blk * 7 + tk.kern)] = tflags[(size_t)q];
+    }
+    H.uoff_h.resize((size_t)ntask);
+    H.voff_h.resize((size_t)ntask);
+    H.coff_h.resize((size_t)ntask);
+    H.woff_h.resize((size_t)ntask);
+    int64_t ut = 0, vt = 0, ct = 0, wt = 0;
+    for (int64_t b = 0; b < H.nadm; ++b)
+        for (int k = 0; k < 7; ++k) {
+            size_t q = (size_t)(b * 7 + k);
+            int32_t r = H.rank_h[q];
+            const Blk& bk = H.adm_h[(size_t)b];
+            H.uoff_h[q] = ut;
+            H.voff_h[q] = vt;
+            H.coff_h[q] = ct;
+            H.woff_h[q] = wt;
+            // keep every factor start 16-byte aligned for vector loads
+            ut += ((int64_t)r * bk.m + 7) & ~int64_t(7);
+            vt += ((int64_t)r * bk.n + 7) & ~int64_t(7);
+            ct += r;
+            wt += 3 * (int64_t)r;
+        }
+    H.u_total = ut;
+    H.v_total = vt;
+    H.c_total = ct;
+    H.w_total = wt;
+    if ((rc = dalloc(H, H.U64, (size_t)std::max<int64_t>(ut, 1) * 8))) return rc;
+    if ((rc = dalloc(H, H.V64, (size_t)std::max<int64_t>(vt, 1) * 8))) return rc;
+    if ((rc = upload(H, H.d_uoff, H.uoff_h.data(), (size_t)ntask * 8 + 8))) return rc;
+    if ((rc = upload(H, H.d_voff, H.voff_h.data(), (size_t)ntask * 8 + 8))) return rc;
+    if ((rc = upload(H, H.d_coff, H.coff_h.data(), (size_t)ntask * 8 + 8))) return rc;
+    if ((rc = upload(H, H.d_woff, H.woff_h.data(), (size_t)ntask * 8 + 8))) return rc;
+    if ((rc = upload(H, H.d_rank, H.rank_h.data(), (size_t)ntask * 4 + 4))) return rc;
+    if (ntask > 0) {
+        repack_kernel<<<(unsigned)ntask, 128, 0, s>>>(
+            dtask.b.as<AcaTask>(), (int)ntask, H.d_adm.as<Blk>(), drank.b.as<int32_t>(),
+            doff.b.as<int64_t>(), darena.b.as<double>(), H.d_uoff.as<int64_t>(),
+            H.d_voff.as<int64_t>(), H.U64.as<double>(), H.V64.as<double>());
+        HM_CUDA(cudaGetLastError());
+    }
+    HM_CUDA(cudaEventRecord(ev[3], s));
+
+    // ---- per-leaf work lists of the product
+    std::vector<int32_t> leafv;
+    std::vector<int32_t> far_ptr(1, 0), near_ptr(1, 0);
+    std::vector<FarItem> far_items;
+    std::vector<int32_t> near_items;
+    {
+        // admissible / near blocks grouped by row node
+        std::vector<std::vector<int32_t>> adm_by_row(tr.nodes.size()), near_by_row(tr.nodes.size());
+        for (int64_t b = 0; b < H.nadm; ++b) adm_by_row[(size_t)tr.adm[(size_t)b][0]].push_back((int32_t)b);
+        for (int64_t b = 0; b < H.nnear; ++b)
+            near_by_row[(size_t)tr.near_blocks[(size_t)b][0]].push_back((int32_t)b);
+        int32_t csp = 0;
+        for (size_t n = 0; n < tr.nodes.size(); ++n)
+            csp = std::max<int32_t>(csp, (int32_t)(adm_by_row[n].size() + near_by_row[n].size()));
+        H.csp = csp;
+        // ancestor chains: walk the tree from the root
+        std::vector<int64_t> parent(tr.nodes.size(), -1);
+        for (size_t n = 0; n < tr.nodes.size(); ++n)
+            for (int c = 0; c < 2; ++c)
+                if (tr.nodes[n].son[c] >= 0) parent[(size_t)tr.nodes[n].son[c]] = (int64_t)n;
+        int32_t maxleaf = 0;
+        for (int64_t lf : tr.leaves) {
+            const Node& L = tr.nodes[(size_t)lf];
+            leafv.push_back((int32_t)L.lo);
+            leafv.push_back((int32_t)(L.hi - L.lo));
+            maxleaf = std::max<int32_t>(maxleaf, (int32_t)(L.hi - L.lo));
+            std::vector<int64_t> chain;
+            for (int64_t n = lf; n >= 0; n = parent[(size_t)n]) chain.push_back(n);
+            std::reverse(chain.begin(), chain.end());  // root first
+            for (int64_t n : chain)
+                for (int32_t b : adm_by_row[(size_t)n])
+                    far_items.push_back(FarItem{b, (int32_t)(L.lo - tr.nodes[(size_t)n].lo)});
+            far_ptr.push_back((int32_t)far_items.size());
+            for (int32_t b : near_by_row[(size_t)lf]) near_items.push_back(b);
+            near_ptr.push_back((int32_t)near_items.size());
+        }
+        H.max_leaf = maxleaf;
+    }
+    H.nleaves = (int64_t)tr.leaves.size();
+    if ((rc = upload(H, H.d_leaf, leafv.data(), leafv.size() * 4))) return rc;
+    if ((rc = upload(H, H.d_far_ptr, far_ptr.data(), far_ptr.size() * 4))) return rc;
+    if ((rc = upload(H, H.d_far_items, far_items.data(), far_items.size() * sizeof(FarItem) + 8))) return rc;
+    if ((rc = upload(H, H.d_near_ptr, near_ptr.data(), near_ptr.size() * 4))) return rc;
+    if ((rc = upload(H, H.d_near_items, near_items.data(), near_items.size() * 4 + 4))) return rc;
+    {
+        // phase-1 order: blocks with the most factor data first
+        std::vector<int32_t> ord((size_t)H.nadm);
+        std::iota(ord.begin(), ord.end(), 0);
+        std::vector<int64_t> work((size_t)H.nadm, 0);
+        for (int64_t b = 0; b < H.nadm; ++b)
+            for (int k = 0; k < 7; ++k)
+                work[(size_t)b] += (int64_t)H.rank_h[(size_t)(b * 7 + k)] * H.adm_h[(size_t)b].n;
+        std::stable_sort(ord.begin(), ord.end(),
+                         [&](int32_t a, int32_t b) { return work[(size_t)a] > work[(size_t)b]; });
+        if ((rc = upload(H, H.d_p1_order, ord.data(), ord.size() * 4 + 4))) return rc;
+    }
+    // ---- workspace for the product
+    H.max_rhs = H.prm.max_rhs;
+    if ((rc = dalloc(H, H.xg, (size_t)H.max_rhs * 3 * M * 8))) return rc;
+    if ((rc = dalloc(H, H.wb, (size_t)H.max_rhs * std::max<int64_t>(H.w_total, 1) * 8))) return rc;
+    if ((rc = dalloc(H, H.xh, (size_t)H.max_rhs * 3 * M * 8))) return rc;
+    if ((rc = dalloc(H, H.yh, (size_t)H.max_rhs * 3 * M * 8))) return rc;
+    HM_CUDA(cudaStreamSynchronize(s));
+    float t01 = 0, t12 = 0, t23 = 0;
+    cudaEventElapsedTime(&t01, ev[0], ev[1]);
+    cudaEventElapsedTime(&t12, ev[1], ev[2]);
+    cudaEventElapsedTime(&t23, ev[2], ev[3]);
+    H.asm_ms[0] = t01;
+    H.asm_ms[1] = t12 + t23;
+    H.asm_ms[2] = 0.0;
+    return HM_OK;
+}
+
+}  // namespace hm
+
+extern "C" int hm_aca_assemble(const hm_tree* tree, const hm_params* prm, const hm_allocator* alloc,
+                               void* stream, hm_matrix** out)
+{
+    using namespace hm;
+    if (!out) return fail(HM_EINVAL, "hm_aca_assemble: out is NULL");
+    *out = nullptr;
+    if (!tree || !prm) return fail(HM_EINVAL, "hm_aca_assemble: NULL tree or params");
+    if (!(prm->E > 0.0) || !std::isfinite(prm->E)) return fail(HM_EINVAL, "hm_aca_assemble: E must be > 0");
+    if (!(prm->nu > 0.0 && prm->nu < 0.5)) return fail(HM_EINVAL, "hm_aca_assemble: nu must lie in (0, 1/2)");
+    if (!(prm->aca_eps > 0.0) || !(prm->aca_eps < 1.0))
+        return fail(HM_EINVAL, "hm_aca_assemble: aca_eps must lie in (0, 1)");
+    if (!(prm->aca_eta_stop >= 0.0 && prm->aca_eta_stop < 1.0))
+        return fail(HM_EINVAL, "hm_aca_assemble: aca_eta_stop must lie in [0, 1)");
+    if (prm->kmax < 0 || prm->kmax > kKmaxLimit)
+        return fail(HM_EINVAL, "hm_aca_assemble: kmax must lie in 0..%d", kKmaxLimit);
+    if (prm->max_rhs < 0 || prm->max_rhs > 64) return fail(HM_EINVAL, "hm_aca_assemble: max_rhs must lie in 0..64");
+    hm_matrix* H = new (std::nothrow) hm_matrix();
+    if (!H) return fail(HM_ENOMEM, "hm_aca_assemble: out of host memory");
+    H->prm = *prm;
+    if (H->prm.kmax == 0) H->prm.kmax = 128;
+    if (H->prm.max_rhs == 0) H->prm.max_rhs = 32;
+    H->E = prm->E;
+    H->nu = prm->nu;
+    H->alloc.stream = (cudaStream_t)stream;
+    if (alloc && alloc->alloc && alloc->free) {
+        H->alloc.user = *alloc;
+        H->alloc.has_user = true;
+    }
+    int rc;
+    try {
+        rc = assemble_device(*tree, *H);
+    } catch (const std::bad_alloc&) {
+        rc = fail(HM_ENOMEM, "hm_aca_assemble: out of host memory");
+    }
+    if (rc) {
+        hm_matrix_destroy(H);
+        return rc;
+    }
+    *out = H;
+    for (int32_t f : H->flags_h)
+        if (f & 1) {
+            set_error("hm_aca_assemble: a block reached the rank cap kmax=%d", H->prm.kmax);
+            return HM_ERANK;
+        }
+    return HM_OK;
+}

@@ -1,0 +1,411 @@
+// hm_host.cpp -- host side of the H-matrix library: error reporting, device
+// allocation, cluster tree and block partition (Section 2.1), and the ABI
+// entry points that need no kernel.
+//
+// Compiled with -ffp-contract=off: the geometric decisions (split axis,
+// admissibility) are made with separately rounded operations so that they
+// are reproducible on any host.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "hm_internal.h"
+
+namespace hm {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_check(cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return HM_OK;
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? HM_ENOMEM : HM_EDEVICE;
+}
+
+void* Allocator::alloc(size_t bytes)
+{
+    if (bytes == 0) bytes = 256;
+    void* p = nullptr;
+    if (has_user) {
+        p = user.alloc(bytes, (void*)stream, user.user);
+    } else if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+void Allocator::release(void* p, size_t bytes)
+{
+    if (!p) return;
+    if (has_user)
+        user.free(p, bytes, (void*)stream, user.user);
+    else
+        cudaFreeAsync(p, stream);
+}
+
+// ---------------------------------------------------------------- tree
+namespace {
+
+struct TreeBuilder {
+    hm_tree& tr;
+    std::vector<std::pair<double, int64_t>> keys;
+
+    int64_t build(int64_t lo, int64_t hi, int32_t level)
+    {
+        int64_t id = (int64_t)tr.nodes.size();
+        tr.nodes.emplace_back();
+        {
+            Node& nd = tr.nodes.back();
+            nd.lo = lo;
+            nd.hi = hi;
+            nd.level = level;
+            nd.son[0] = nd.son[1] = -1;
+            for (int k = 0; k < 3; ++k) {
+                nd.bmin[k] = INFINITY;
+                nd.bmax[k] = -INFINITY;
+            }
+            for (int64_t p = lo; p < hi; ++p) {
+                const int32_t* t = &tr.T[3 * tr.perm[p]];
+                for (int c = 0; c < 3; ++c)
+                    for (int k = 0; k < 3; ++k) {
+                        double v = tr.V[3 * (int64_t)t[c] + k];
+                        nd.bmin[k] = std::min(nd.bmin[k], v);
+                        nd.bmax[k] = std::max(nd.bmax[k], v);
+                    }
+            }
+        }
+        if (level > tr.depth) tr.depth = level;
+        if (hi - lo <= tr.leaf) return id;
+        double cmin[3] = {INFINITY, INFINITY, INFINITY};
+        double cmax[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int64_t p = lo; p < hi; ++p)
+            for (int k = 0; k < 3; ++k) {
+                double v = tr.coll[3 * tr.perm[p] + k];
+                cmin[k] = std::min(cmin[k], v);
+                cmax[k] = std::max(cmax[k], v);
+            }
+        // longest extent of the collocation-point box; lowest axis on ties
+        int ax = 0;
+        double ext = cmax[0] - cmin[0];
+        for (int k = 1; k < 3; ++k) {
+            double e = cmax[k] - cmin[k];
+            if (e > ext) {
+                ext = e;
+                ax = k;
+            }
+        }
+        keys.resize((size_t)(hi - lo));
+        for (int64_t p = lo; p < hi; ++p)
+            keys[(size_t)(p - lo)] = {tr.coll[3 * tr.perm[p] + ax], tr.perm[p]};
+        std::sort(keys.begin(), keys.end());  // (coordinate, id): unique keys
+        for (int64_t p = lo; p < hi; ++p) tr.perm[p] = keys[(size_t)(p - lo)].second;
+        int64_t mid = lo + (hi - lo) / 2;
+        int64_t s0 = build(lo, mid, level + 1);
+        int64_t s1 = build(mid, hi, level + 1);
+        tr.nodes[id].son[0] = s0;
+        tr.nodes[id].son[1] = s1;
+        return id;
+    }
+};
+
+double box_diam2(const Node& a)
+{
+    double s = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double e = a.bmax[k] - a.bmin[k];
+        s += e * e;
+    }
+    return s;
+}
+
+double box_dist2(const Node& a, const Node& b)
+{
+    double s = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double g = std::max(a.bmin[k] - b.bmax[k], b.bmin[k] - a.bmax[k]);
+        if (g < 0.0) g = 0.0;
+        s += g * g;
+    }
+    return s;
+}
+
+// block-cluster recursion (Section 2.1) with an explicit stack; the visiting
+// order is the recursive pre-order (sons in order (0,0), (0,1), (1,0), (1,1))
+void build_partition(hm_tree& tr)
+{
+    const double eta2 = tr.eta * tr.eta;
+    std::vector<std::array<int64_t, 2>> st;
+    st.push_back({0, 0});
+    while (!st.empty()) {
+        auto [t, s] = st.back();
+        st.pop_back();
+        const Node& a = tr.nodes[(size_t)t];
+        const Node& b = tr.nodes[(size_t)s];
+        double dmin = std::min(box_diam2(a), box_diam2(b));
+        if (dmin < eta2 * box_dist2(a, b)) {
+            tr.adm.push_back({t, s});
+            continue;
+        }
+        bool tl = a.son[0] < 0, sl = b.son[0] < 0;
+        if (!tl && !sl) {
+            st.push_back({a.son[1], b.son[1]});
+            st.push_back({a.son[1], b.son[0]});
+            st.push_back({a.son[0], b.son[1]});
+            st.push_back({a.son[0], b.son[0]});
+        } else if (!tl) {
+            st.push_back({a.son[1], s});
+            st.push_back({a.son[0], s});
+        } else if (!sl) {
+            st.push_back({t, b.son[1]});
+            st.push_back({t, b.son[0]});
+        } else {
+            tr.near_blocks.push_back({t, s});
+        }
+    }
+}
+
+}  // namespace
+}  // namespace hm
+
+using namespace hm;
+
+extern "C" {
+
+const char* hm_last_error(void) { return hm::g_err.c_str(); }
+
+int hm_build_cluster_tree(const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                          int32_t leaf, double eta, hm_tree** out)
+{
+    if (!out) return fail(HM_EINVAL, "hm_build_cluster_tree: out is NULL");
+    *out = nullptr;
+    if (!verts || !tris) return fail(HM_EINVAL, "hm_build_cluster_tree: NULL mesh array");
+    if (nv < 3 || nt < 1) return fail(HM_EINVAL, "hm_build_cluster_tree: empty mesh (nv=%lld, nt=%lld)",
+                                      (long long)nv, (long long)nt);
+    if (nt > (int64_t)INT32_MAX / 4)
+        return fail(HM_EINVAL, "hm_build_cluster_tree: too many triangles (%lld)", (long long)nt);
+    if (leaf < 1) return fail(HM_EINVAL, "hm_build_cluster_tree: leaf must be >= 1");
+    if (!(eta > 0.0) || !std::isfinite(eta)) return fail(HM_EINVAL, "hm_build_cluster_tree: eta must be > 0");
+    for (int64_t i = 0; i < 3 * nv; ++i)
+        if (!std::isfinite(verts[i]))
+            return fail(HM_EINVAL, "hm_build_cluster_tree: non-finite vertex coordinate");
+    hm_tree* tr = new (std::nothrow) hm_tree();
+    if (!tr) return fail(HM_ENOMEM, "hm_build_cluster_tree: out of host memory");
+    try {
+        tr->M = nt;
+        tr->nv = nv;
+        tr->leaf = leaf;
+        tr->eta = eta;
+        tr->V.assign(verts, verts + 3 * nv);
+        tr->T.assign(tris, tris + 3 * nt);
+        tr->coll.resize((size_t)(3 * nt));
+        for (int64_t i = 0; i < nt; ++i) {
+            const int32_t* t = &tr->T[(size_t)(3 * i)];
+            for (int c = 0; c < 3; ++c)
+                if (t[c] < 0 || t[c] >= nv) {
+                    delete tr;
+                    return fail(HM_EINVAL, "hm_build_cluster_tree: triangle %lld has vertex id %d out of range",
+                                (long long)i, t[c]);
+                }
+            const double* a = &tr->V[3 * (size_t)t[0]];
+            const double* b = &tr->V[3 * (size_t)t[1]];
+            const double* c = &tr->V[3 * (size_t)t[2]];
+            double u[3], v[3];
+            for (int k = 0; k < 3; ++k) {
+                u[k] = b[k] - a[k];
+                v[k] = c[k] - a[k];
+                tr->coll[(size_t)(3 * i + k)] = (a[k] + b[k] + c[k]) / 3.0;
+            }
+            double n0 = u[1] * v[2] - u[2] * v[1], n1 = u[2] * v[0] - u[0] * v[2],
+                   n2 = u[0] * v[1] - u[1] * v[0];
+            if (!(n0 * n0 + n1 * n1 + n2 * n2 > 0.0)) {
+                delete tr;
+                return fail(HM_EINVAL, "hm_build_cluster_tree: triangle %lld is degenerate", (long long)i);
+            }
+        }
+        tr->perm.resize((size_t)nt);
+        for (int64_t i = 0; i < nt; ++i) tr->perm[(size_t)i] = i;
+        tr->nodes.reserve((size_t)(2 * nt));
+        TreeBuilder tb{*tr, {}};
+        tb.build(0, nt, 0);
+        build_partition(*tr);
+        for (size_t n = 0; n < tr->nodes.size(); ++n)
+            if (tr->nodes[n].son[0] < 0) tr->leaves.push_back((int64_t)n);
+        std::sort(tr->leaves.begin(), tr->leaves.end(), [&](int64_t a, int64_t b) {
+            return tr->nodes[(size_t)a].lo < tr->nodes[(size_t)b].lo;
+        });
+    } catch (const std::bad_alloc&) {
+        delete tr;
+        return fail(HM_ENOMEM, "hm_build_cluster_tree: out of host memory");
+    }
+    *out = tr;
+    return HM_OK;
+}
+
+int hm_tree_sizes(const hm_tree* tr, int64_t counts[6])
+{
+    if (!tr || !counts) return fail(HM_EINVAL, "hm_tree_sizes: NULL argument");
+    counts[0] = tr->M;
+    counts[1] = (int64_t)tr->nodes.size();
+    counts[2] = (int64_t)tr->adm.size();
+    counts[3] = (int64_t)tr->near_blocks.size();
+    counts[4] = (int64_t)tr->leaves.size();
+    counts[5] = tr->depth;
+    return HM_OK;
+}
+
+int hm_tree_export(const hm_tree* tr, int64_t* perm, int64_t* nodes, int64_t* adm,
+                   int64_t* near_blocks)
+{
+    if (!tr) return fail(HM_EINVAL, "hm_tree_export: NULL tree");
+    if (perm) std::memcpy(perm, tr->perm.data(), (size_t)tr->M * sizeof(int64_t));
+    if (nodes)
+        for (size_t n = 0; n < tr->nodes.size(); ++n) {
+            const Node& nd = tr->nodes[n];
+            nodes[5 * n + 0] = nd.lo;
+            nodes[5 * n + 1] = nd.hi;
+            nodes[5 * n + 2] = nd.son[0];
+            nodes[5 * n + 3] = nd.son[1];
+            nodes[5 * n + 4] = nd.level;
+        }
+    if (adm)
+        for (size_t b = 0; b < tr->adm.size(); ++b) {
+            adm[2 * b] = tr->adm[b][0];
+            adm[2 * b + 1] = tr->adm[b][1];
+        }
+    if (near_blocks)
+        for (size_t b = 0; b < tr->near_blocks.size(); ++b) {
+            near_blocks[2 * b] = tr->near_blocks[b][0];
+            near_blocks[2 * b + 1] = tr->near_blocks[b][1];
+        }
+    return HM_OK;
+}
+
+void hm_tree_destroy(hm_tree* tr) { delete tr; }
+
+int hm_set_material(hm_matrix* H, double E, double nu)
+{
+    if (!H) return fail(HM_EINVAL, "hm_set_material: NULL matrix");
+    if (!(E > 0.0) || !std::isfinite(E)) return fail(HM_EINVAL, "hm_set_material: E must be > 0");
+    if (!(nu > 0.0 && nu < 0.5)) return fail(HM_EINVAL, "hm_set_material: nu must lie in (0, 1/2)");
+    H->E = E;
+    H->nu = nu;
+    return HM_OK;
+}
+
+int hm_get_stats(const hm_matrix* H, hm_stats* st)
+{
+    if (!H || !st) return fail(HM_EINVAL, "hm_get_stats: NULL argument");
+    std::memset(st, 0, sizeof *st);
+    st->M = H->M;
+    st->nadm = H->nadm;
+    st->nnear = H->nnear;
+    st->nleaves = H->nleaves;
+    for (const Blk& b : H->near_h) st->near_pairs += (int64_t)b.m * b.n;
+    int64_t far_cols = 0;
+    for (int64_t b = 0; b < H->nadm; ++b) {
+        const Blk& bk = H->adm_h[(size_t)b];
+        for (int k = 0; k < 7; ++k) {
+            int32_t r = H->rank_h[(size_t)(b * 7 + k)];
+            st->far_entries += (int64_t)r * (bk.m + bk.n);
+            st->rank_sum[k] += r;
+            st->rank_max[k] = std::max(st->rank_max[k], r);
+            far_cols += r;
+            if (H->flags_h[(size_t)(b * 7 + k)] & 1) st->rank_cap_hits++;
+        }
+    }
+    st->csp = H->csp;
+    int64_t near_vals = st->near_pairs * 6;
+    st->bytes_fp64 = (st->far_entries + near_vals) * 8;
+    st->bytes_form[0] = st->bytes_fp64;
+    if (H->packed[1]) st->bytes_form[1] = (st->far_entries + near_vals) * 4;
+    // packed 16-bit forms: 2-byte factors, one float scale per factor column
+    // (U and V), FP32 near field
+    if (H->packed[2]) st->bytes_form[2] = st->far_entries * 2 + far_cols * 8 + near_vals * 4;
+    if (H->packed[3]) st->bytes_form[3] = st->far_entries * 2 + far_cols * 8 + near_vals * 4;
+    for (int i = 0; i < 3; ++i) st->assemble_ms[i] = H->asm_ms[i];
+    return HM_OK;
+}
+
+int hm_export_factors(const hm_matrix* H, int64_t blk, int32_t kern, int32_t* rank, double* U,
+                      double* V)
+{
+    if (!H || !rank) return fail(HM_EINVAL, "hm_export_factors: NULL argument");
+    if (blk < 0 || blk >= H->nadm || kern < 0 || kern > 6)
+        return fail(HM_EINVAL, "hm_export_factors: block %lld kernel %d out of range",
+                    (long long)blk, kern);
+    size_t q = (size_t)(blk * 7 + kern);
+    int32_t k = H->rank_h[q];
+    *rank = k;
+    const Blk& b = H->adm_h[(size_t)blk];
+    if (U && k > 0)
+        HM_CUDA(cudaMemcpy(U, H->U64.as<double>() + H->uoff_h[q], (size_t)k * b.m * sizeof(double),
+                           cudaMemcpyDeviceToHost));
+    if (V && k > 0)
+        HM_CUDA(cudaMemcpy(V, H->V64.as<double>() + H->voff_h[q], (size_t)k * b.n * sizeof(double),
+                           cudaMemcpyDeviceToHost));
+    return HM_OK;
+}
+
+int hm_export_near(const hm_matrix* H, int64_t blk, double* out)
+{
+    if (!H || !out) return fail(HM_EINVAL, "hm_export_near: NULL argument");
+    if (blk < 0 || blk >= H->nnear) return fail(HM_EINVAL, "hm_export_near: block out of range");
+    const Blk& b = H->near_h[(size_t)blk];
+    // device layout per block: [v][j][i] (i fastest); exported as [v][i][j]
+    std::vector<double> tmp((size_t)6 * b.m * b.n);
+    HM_CUDA(cudaMemcpy(tmp.data(), H->N64.as<double>() + H->noff_h[(size_t)blk],
+                       tmp.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int v = 0; v < 6; ++v)
+        for (int i = 0; i < b.m; ++i)
+            for (int j = 0; j < b.n; ++j)
+                out[((size_t)v * b.m + i) * b.n + j] = tmp[((size_t)v * b.n + j) * b.m + i];
+    return HM_OK;
+}
+
+void hm_matrix_destroy(hm_matrix* H)
+{
+    if (!H) return;
+    hm::DevBuf* bufs[] = {&H->d_perm, &H->d_adm, &H->d_near, &H->d_rank, &H->d_uoff, &H->d_voff,
+                          &H->d_coff, &H->d_woff, &H->d_noff, &H->d_leaf, &H->d_far_ptr,
+                          &H->d_far_items, &H->d_near_ptr, &H->d_near_items, &H->d_p1_order,
+                          &H->U64, &H->V64, &H->N64, &H->U32, &H->V32, &H->N32, &H->U16b,
+                          &H->V16b, &H->U16h, &H->V16h, &H->SUb, &H->SVb, &H->SUh, &H->SVh,
+                          &H->xg, &H->wb, &H->xh, &H->yh};
+    // the assembly stream may be gone by now: drain the device and release
+    // on the legacy default stream
+    cudaDeviceSynchronize();
+    H->alloc.stream = nullptr;
+    for (hm::DevBuf* b : bufs) {
+        H->alloc.release(b->p, b->bytes);
+        b->p = nullptr;
+    }
+    cudaDeviceSynchronize();
+    delete H;
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+"""CPU-only checks of the C ABI: the library loads and exports every symbol
+of include/hmat.h, argument validation fails cleanly without a GPU, and the
+host-side cluster tree and block partition (Section 2.1) are identical to the
+oracle's, bit for bit."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2205_04752_gb300 import binding, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _header_functions():
+    src = open(os.path.join(ROOT, "include", "hmat.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_\s\*]*?\b(hm_[a-z0-9_]+)\s*\(",
+                       src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_header_symbol():
+    lib = binding.load()
+    names = _header_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(binding.SYMBOLS)
+
+
+def test_invalid_arguments_fail_cleanly():
+    V, T = inputs.icosphere(1)
+    with pytest.raises(binding.HMError) as e:
+        binding.build_cluster_tree(V, T, 0, 0.8)
+    assert e.value.code == binding.HM_EINVAL
+    with pytest.raises(binding.HMError):
+        binding.build_cluster_tree(V, T, 8, -1.0)
+    bad = T.copy()
+    bad[3, 1] = len(V) + 5
+    with pytest.raises(binding.HMError):
+        binding.build_cluster_tree(V, bad, 8, 0.8)
+    deg = T.copy()
+    deg[2] = [deg[2, 0], deg[2, 0], deg[2, 1]]
+    with pytest.raises(binding.HMError):
+        binding.build_cluster_tree(V, deg, 8, 0.8)
+    Vn = V.copy()
+    Vn[0, 0] = np.nan
+    with pytest.raises(binding.HMError):
+        binding.build_cluster_tree(Vn, T, 8, 0.8)
+    # NULL pointers through the raw ABI
+    lib = binding.load()
+    out = ctypes.c_void_p()
+    assert lib.hm_build_cluster_tree(None, 0, None, 0, 8, 0.8, ctypes.byref(out)) == binding.HM_EINVAL
+    assert b"NULL" in lib.hm_last_error() or b"empty" in lib.hm_last_error()
+    assert lib.hm_matvec(None, None, None, 1, 3, 0, None) == binding.HM_EINVAL
+    assert lib.hm_pack(None, 1, None) == binding.HM_EINVAL
+
+
+def _compare_tree(V, T, leaf, eta):
+    tr = binding.build_cluster_tree(V, T, leaf, eta)
+    perm, nodes, adm, near = tr.export()
+    Ho = oracle.HMatrix(V, T, leaf, eta, 1e-4)
+    np.testing.assert_array_equal(perm, Ho.perm)
+    np.testing.assert_array_equal(nodes, Ho.nodes)
+    np.testing.assert_array_equal(adm, Ho.adm)
+    np.testing.assert_array_equal(near, Ho.near)
+    return tr
+
+
+@pytest.mark.parametrize("mesh,leaf,eta", [
+    ("ico0", 4, 0.8), ("ico3", 32, 0.8), ("ico3", 7, 0.8), ("ico4", 64, 0.5),
+    ("cube6", 16, 0.8), ("ell", 32, 0.8), ("ico2", 10**6, 0.8)])
+def test_tree_and_partition_match_oracle(mesh, leaf, eta):
+    if mesh.startswith("ico"):
+        V, T = inputs.icosphere(int(mesh[3:]))
+    elif mesh == "cube6":
+        V, T = inputs.cube_surface(6)
+    else:
+        V, T = inputs.ellipsoid(9, 0.6, 1.7, 1.1)
+    tr = _compare_tree(V, T, leaf, eta)
+    if leaf >= len(T):
+        assert tr.nadm == 0 and tr.nnear == 1 and tr.nleaves == 1
+
+
+@pytest.mark.slow
+def test_tree_and_partition_match_oracle_level6():
+    """The level-6 icosphere of the benchmark (81,920 triangles, leaf 64)."""
+    V, T = inputs.icosphere(6)
+    tr = _compare_tree(V, T, 64, 0.8)
+    assert tr.nadm > 100000 and tr.nnear > 50000

@@ -1,0 +1,208 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle
+on the same seeded inputs.
+
+Tolerances: FP64 kernels against the oracle's same blocks 1e-12 (relative);
+the H-matrix product against the dense product 1e-4 (relative 2-norm); packed
+product forms against the FP64 form as stated per form.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2205_04752_gb300 import binding, inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+E, NU = 1.0, 0.3
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+class Case:
+    def __init__(self, V, T, leaf, eta=0.8, eps=1e-4, max_rhs=8):
+        self.V, self.T, self.leaf, self.eta, self.eps = V, T, leaf, eta, eps
+        self.M = len(T)
+        self.tree = binding.build_cluster_tree(V, T, leaf, eta)
+        self.H = binding.aca_assemble(self.tree, E, NU, eps, max_rhs=max_rhs)
+        self.Ho = oracle.HMatrix(V, T, leaf, eta, eps)
+        self.perm, self.nodes, self.adm, self.near = self.tree.export()
+
+    def matvec(self, x, form="fp64"):
+        xd = torch.tensor(np.atleast_2d(x), device="cuda")
+        yd = torch.full_like(xd, np.nan)
+        binding.hmatvec(self.H, xd, yd, form)
+        torch.cuda.synchronize()
+        return yd.cpu().numpy()
+
+    def size(self, node):
+        return int(self.nodes[node, 1] - self.nodes[node, 0])
+
+
+_cache = {}
+
+
+def c1():
+    if "c1" not in _cache:
+        V, T = inputs.icosphere(3)
+        _cache["c1"] = Case(V, T, 32)
+        _cache["c1"].Ho.assemble()
+    return _cache["c1"]
+
+
+def test_near_field_entries_match_oracle():
+    c = c1()
+    rng = np.random.default_rng(0)
+    ids = sorted(set(rng.choice(c.Ho.nnear, 60, replace=False).tolist()) |
+                 {b for b in range(c.Ho.nnear) if c.near[b, 0] == c.near[b, 1]})
+    for b in ids:
+        m, n = c.size(c.near[b, 0]), c.size(c.near[b, 1])
+        g = c.H.near_block(b, m, n)
+        o = c.Ho.near_block(b)
+        scale = np.abs(o[0]).max()
+        assert np.abs(g - o[1:]).max() <= 1e-12 * scale, b
+        assert np.abs(g[0] + g[3] + g[5] - o[0]).max() <= 1e-12 * scale, b
+
+
+def test_aca_factors_match_oracle_blocks():
+    """Every admissible block and scalar kernel of C1: same rank, and the
+    reconstructions U V^T agree to 1e-12 of the block's norm."""
+    c = c1()
+    worst = 0.0
+    for b in range(c.Ho.nadm):
+        m, n = c.size(c.adm[b, 0]), c.size(c.adm[b, 1])
+        for kern in range(7):
+            Uo, Vo = c.Ho.factors(b, kern)
+            Ug, Vg = c.H.factors(b, kern, m, n)
+            assert Ug.shape[1] == Uo.shape[1], (b, kern)
+            So = Uo @ Vo.T
+            d = np.linalg.norm(Ug @ Vg.T - So) / np.linalg.norm(So)
+            worst = max(worst, d)
+    assert worst <= 1e-12
+
+
+def test_hmatvec_fp64_matches_oracle_and_dense():
+    c = c1()
+    x = inputs.uniform_rhs(3 * c.M, 0, nrhs=3)
+    y = c.matvec(x)
+    yo = c.Ho.matvec(E, NU, x)
+    for r in range(3):
+        assert _rel(y[r], yo[r]) <= 1e-12
+    A = oracle.kelvin_dense(c.V, c.T, E, NU)
+    yd = oracle.dense_matvec(A, x)
+    for r in range(3):
+        assert _rel(y[r], yd[r]) <= 1e-4
+
+
+@pytest.mark.parametrize("form,tol", [("fp32", 1e-5), ("bf16", 1e-2), ("fp16", 2e-3)])
+def test_packed_forms_against_fp64_form(form, tol):
+    c = c1()
+    c.H.pack(form)
+    x = inputs.uniform_rhs(3 * c.M, 1, nrhs=2)
+    y64 = c.matvec(x)
+    y = c.matvec(x, form)
+    for r in range(2):
+        assert _rel(y[r], y64[r]) <= tol
+
+
+def test_deterministic_and_multi_rhs_consistent():
+    c = c1()
+    x = inputs.uniform_rhs(3 * c.M, 7, nrhs=5)
+    y1 = c.matvec(x)
+    y2 = c.matvec(x)
+    np.testing.assert_array_equal(y1, y2)
+    for r in (0, 4):
+        ys = c.matvec(x[r])
+        np.testing.assert_allclose(ys[0], y1[r], rtol=0, atol=1e-14 * np.abs(y1[r]).max())
+
+
+def test_host_entry_point_equals_device_entry_point():
+    c = c1()
+    x = inputs.uniform_rhs(3 * c.M, 3, nrhs=2)
+    y = np.zeros_like(x)
+    binding.hmatvec_host(c.H, x, y, "fp64")
+    np.testing.assert_array_equal(y, c.matvec(x))
+
+
+def test_set_material():
+    c = c1()
+    E2, nu2 = 2.5, 0.41
+    x = inputs.uniform_rhs(3 * c.M, 9)
+    c.H.set_material(E2, nu2)
+    try:
+        y = c.matvec(x)
+    finally:
+        c.H.set_material(E, NU)
+    yo = c.Ho.matvec(E2, nu2, x)
+    assert _rel(y[0], yo[0]) <= 1e-12
+
+
+@pytest.mark.parametrize("mesh,leaf", [("ico0", 3), ("ico1", 7), ("ico2", 1000), ("cube4", 12),
+                                       ("ell", 20)])
+def test_small_and_ragged_meshes(mesh, leaf):
+    """Tiny meshes, leaves of ragged size, a single dense leaf (leaf >= M), a
+    cube surface whose planar faces make some kernels vanish identically
+    (rank 0 blocks), and an ellipsoid."""
+    if mesh.startswith("ico"):
+        V, T = inputs.icosphere(int(mesh[3:]))
+    elif mesh == "cube4":
+        V, T = inputs.cube_surface(4)
+    else:
+        V, T = inputs.ellipsoid(7, 0.6, 1.7, 1.1)
+    c = Case(V, T, leaf, max_rhs=2)
+    c.Ho.assemble()
+    x = inputs.uniform_rhs(3 * c.M, 2, nrhs=2)
+    y = c.matvec(x)
+    yo = c.Ho.matvec(E, NU, x)
+    A = oracle.kelvin_dense(V, T, E, NU)
+    yd = oracle.dense_matvec(A, x)
+    for r in range(2):
+        assert _rel(y[r], yo[r]) <= 1e-12
+        assert _rel(y[r], yd[r]) <= 1e-4
+    if mesh == "cube4" and c.Ho.nadm:
+        assert (c.Ho.ranks() == 0).any()
+
+
+@pytest.mark.slow
+def test_level6_sampled_rows_and_blocks():
+    """The benchmark workload (level-6 icosphere, 245,760 dofs, leaf 64,
+    eta 0.8, eps 1e-4) in the configuration the benchmark times: the FP64
+    product against exact rows of the dense product at 384 sampled triangles
+    (relative error <= 1e-4), the FP32 form against the FP64 form on the full
+    vector (<= 1e-4), and ACA parity on 60 sampled admissible blocks."""
+    V, T = inputs.icosphere(6)
+    M = len(T)
+    tree = binding.build_cluster_tree(V, T, 64, 0.8)
+    H = binding.aca_assemble(tree, E, NU, 1e-4, max_rhs=1)
+    H.pack("fp32")
+    x = inputs.uniform_rhs(3 * M, 0)
+    xd = torch.tensor(x, device="cuda")
+    y64 = torch.empty_like(xd)
+    y32 = torch.empty_like(xd)
+    binding.hmatvec(H, xd[0], y64[0], "fp64")
+    binding.hmatvec(H, xd[0], y32[0], "fp32")
+    torch.cuda.synchronize()
+    y64, y32 = y64.cpu().numpy(), y32.cpu().numpy()
+    assert _rel(y32[0], y64[0]) <= 1e-4
+    rows = inputs.sample_rows(M, 384, 11)
+    yr = oracle.kelvin_rows_matvec(V, T, E, NU, rows, x)[0]
+    dofs = (3 * rows[:, None] + np.arange(3)[None, :]).ravel()
+    assert _rel(y64[0][dofs], yr) <= 1e-4
+    # ACA parity on sampled blocks
+    Ho = oracle.HMatrix(V, T, 64, 0.8, 1e-4)
+    perm, nodes, adm, near = tree.export()
+    rng = np.random.default_rng(4)
+    sizes = nodes[adm[:, 0], 1] - nodes[adm[:, 0], 0]
+    pick = list(rng.choice(len(adm), 50, replace=False)) + list(np.argsort(-sizes)[:10])
+    Ho.assemble(adm_ids=pick, near_ids=[])
+    for b in pick:
+        m = int(nodes[adm[b, 0], 1] - nodes[adm[b, 0], 0])
+        n = int(nodes[adm[b, 1], 1] - nodes[adm[b, 1], 0])
+        for kern in range(7):
+            Uo, Vo = Ho.factors(b, kern)
+            Ug, Vg = H.factors(b, kern, m, n)
+            assert Ug.shape[1] == Uo.shape[1], (b, kern)
+            So = Uo @ Vo.T
+            assert np.linalg.norm(Ug @ Vg.T - So) <= 1e-12 * np.linalg.norm(So), (b, kern)
