@@ -1,0 +1,352 @@
+"""Benchmark: H-matrix-vector products per second of the collocation Lame
+single layer on a level-6 icosphere (81,920 flat triangles, 245,760 dofs,
+E = 1, nu = 0.3, leaf 64, eta = 0.8, ACA eps = 1e-4), at <= 1e-4 relative
+error against the FP64 form.
+
+One step = one H-matrix-vector product y = V_h x (gather, far-field forward,
+per-leaf product with the near field).  The H-matrix (GBs) is far larger than
+L2, so every step streams it from HBM; no L2 flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--form fp16|fp32|...]
+  python bench.py --impl reference     # the FP64 CPU oracle on the host cores
+
+Under torchrun (N > 1) every rank runs its own replica (the product shards
+into independent problems; no collective on the data path): weak scaling,
+value = all ranks' products / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(workload="lame-single-layer-icosphere-L6", mesh="icosphere level 6",
+                triangles=81920, dofs=245760, E=1.0, nu=0.3, leaf=64, eta=0.8, aca_eps=1e-4,
+                nrhs=1)
+METRIC = "H-matvecs/s"
+UNIT = "matvec/s"
+MEAS_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def _peaks():
+    try:
+        with open(MEAS_PEAKS) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [s.strip() for s in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the oracle on a bounded sample of the same workload
+# --------------------------------------------------------------------------
+
+class OracleSample:
+    """The oracle's H-matrix-vector product over a seeded sample of the blocks
+    of the same workload (a fraction `frac` of the admissible and of the near
+    blocks, ACA-assembled by the oracle once, untimed), scaled to one full
+    product by the oracle's own FP64 storage bytes (the product streams every
+    stored value once)."""
+
+    def __init__(self, V, T, frac=0.01, seed=0):
+        import oracle
+        w = WORKLOAD
+        self.oracle = oracle
+        self.H = H = oracle.HMatrix(V, T, w["leaf"], w["eta"], w["aca_eps"])
+        rng = np.random.default_rng(seed)
+        self.na = max(1, int(round(frac * H.nadm)))
+        self.nn = max(1, int(round(frac * H.nnear)))
+        self.adm = np.sort(rng.choice(H.nadm, self.na, replace=False))
+        self.near = np.sort(rng.choice(H.nnear, self.nn, replace=False))
+        t0 = time.time()
+        H.assemble(adm_ids=self.adm, near_ids=self.near)
+        self.t_asm = time.time() - t0
+        ra = H.ranges(H.adm)
+        rn = H.ranges(H.near)
+        ma, na_ = ra[:, 1] - ra[:, 0], ra[:, 3] - ra[:, 2]
+        near_pairs = (rn[:, 1] - rn[:, 0]) * (rn[:, 3] - rn[:, 2])
+        # the oracle stores 7 values per near pair
+        near_all = float(np.sum(near_pairs)) * 7 * 8
+        near_s = float(np.sum(near_pairs[self.near])) * 7 * 8
+        ranks_s = np.array([[H.rank(b, k) for k in range(7)] for b in self.adm])
+        far_s = float(np.sum(ranks_s.sum(1) * (ma[self.adm] + na_[self.adm]))) * 8
+        # far field of all blocks at the sample's mean total rank per block
+        far_all = float(np.sum((ma + na_) * ranks_s.sum(1).mean())) * 8
+        self.scale = (far_all + near_all) / (far_s + near_s)
+        self.frac = frac
+        self.x = np.random.default_rng(1).uniform(-1, 1, (1, 3 * len(T)))
+
+    def step(self):
+        """Seconds of one full product, estimated from one timed sample product."""
+        t0 = time.perf_counter()
+        self.H.matvec(WORKLOAD["E"], WORKLOAD["nu"], self.x, adm_ids=self.adm,
+                      near_ids=self.near)
+        return (time.perf_counter() - t0) * self.scale
+
+    def describe(self, t_sample_ms, reps):
+        return (f"{self.frac:.1%} of the admissible ({self.na}) and near ({self.nn}) blocks of "
+                f"the level-6 workload (seeded), oracle ACA assembly of the sample "
+                f"{self.t_asm:.1f} s (untimed), sample product {t_sample_ms:.1f} ms (median of "
+                f"{reps}), scaled to a full product by FP64 storage bytes x{self.scale:.1f}")
+
+
+def cpu_baseline(V, T, reps=3):
+    s = OracleSample(V, T)
+    ts = [s.step() for _ in range(reps)]
+    t = float(np.median(ts))
+    return {"value": 1.0 / t, "unit": UNIT, "cores": s.oracle.num_threads(), "kind": "oracle",
+            "sample": s.describe(t / s.scale * 1e3, reps)}
+
+
+# --------------------------------------------------------------------------
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    from paper_2205_04752_gb300 import inputs
+    V, T = inputs.icosphere(6)
+    smp = OracleSample(V, T)
+    for _ in range(args.warmup):
+        smp.step()
+    ts = [smp.step() for _ in range(args.steps)]
+    t = float(np.median(ts))
+    v = 1.0 / t
+    info = {"value": v, "unit": UNIT, "cores": smp.oracle.num_threads(), "kind": "oracle",
+            "sample": smp.describe(t / smp.scale * 1e3, args.steps)}
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(WORKLOAD, form="fp64-cpu"),
+            "cpu_baseline": info,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2205_04752_gb300 import binding, inputs
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl" if dist.is_nccl_available() else "gloo")
+    w = WORKLOAD
+    V, T = inputs.icosphere(6)
+    M = len(T)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    tree = binding.build_cluster_tree(V, T, w["leaf"], w["eta"])
+    t_tree = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    H = binding.aca_assemble(tree, w["E"], w["nu"], w["aca_eps"], max_rhs=32)
+    torch.cuda.synchronize()
+    t_asm = time.perf_counter() - t0
+    form = args.form
+    H.pack(form)
+    st = H.stats()
+    x = torch.tensor(inputs.uniform_rhs(3 * M, 0), device="cuda")[0]
+    y = torch.empty_like(x)
+    y64 = torch.empty_like(x)
+    binding.hmatvec(H, x, y64, "fp64")
+    binding.hmatvec(H, x, y, form)
+    torch.cuda.synchronize()
+    err_mixed = float(torch.linalg.norm(y - y64) / torch.linalg.norm(y64))
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if ws > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # ---- headline: device-resident product in the chosen form
+    clk = ClockSampler(local)
+    clk.start()
+    ms_total = timed(lambda: binding.hmatvec(H, x, y, form), args.steps, args.warmup)
+    clocks = clk.stop()
+    ms_step = ms_total / args.steps
+    value = ws * 1e3 / ms_step
+
+    # ---- per-kernel device times (CUDA events on the launching stream)
+    H.profile(True)
+    for _ in range(args.steps):
+        binding.hmatvec(H, x, y, form)
+    kms, calls = H.profile_read()
+    H.profile(False)
+    kms = kms[:3] / max(calls, 1)
+    names = ["gather", "far_fwd", "leaf_near"]
+    dom = int(np.argmax(kms))
+    wf = {"fp64": 8, "fp32": 4, "bf16": 2, "fp16": 2}[form]
+    wn = 8 if form == "fp64" else 4
+    wa = 8 if form == "fp64" else 4
+    scales = 0 if wf >= 4 else st.factor_columns * 4
+    nvals = st.near_pairs * 6
+    vec = 3 * M * wa
+    alg = {
+        "gather": 3 * M * 8 + M * 4 + vec,
+        "far_fwd": st.far_v_entries * wf + scales + vec + 3 * st.factor_columns * wa,
+        "leaf_near": st.far_u_entries * wf + scales + nvals * wn + 3 * st.factor_columns * wa
+        + vec + 3 * M * 8,
+    }
+    peak, peak_kind = _peaks()
+    achieved = alg[names[dom]] / (kms[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "kernel": names[dom],
+                "peak_kind": peak_kind,
+                "kernel_ms": {n: round(float(k), 4) for n, k in zip(names, kms)},
+                "alg_bytes": {n: int(b) for n, b in alg.items()}}
+    total_alg = sum(alg.values())
+
+    # ---- end to end through the public API with host buffers
+    xh = torch.empty(3 * M, dtype=torch.float64, pin_memory=True)
+    xh.copy_(x.cpu())
+    yh = torch.empty(3 * M, dtype=torch.float64, pin_memory=True)
+    xn, yn = xh.numpy(), yh.numpy()
+    ms_e2e = timed(lambda: binding.hmatvec_host(H, xn, yn, form), args.steps, args.warmup)
+    e2e = {"value": ws * 1e3 * args.steps / ms_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": 3 * M * 8, "d2h_bytes_per_step": 3 * M * 8}
+
+    # ---- context: FP64 plain form and 32 right-hand sides
+    ms64 = timed(lambda: binding.hmatvec(H, x, y64, "fp64"), max(2, args.steps // 4), 1) \
+        / max(2, args.steps // 4)
+    X = torch.tensor(inputs.uniform_rhs(3 * M, 0, nrhs=32), device="cuda")
+    Y = torch.empty_like(X)
+    ms32 = timed(lambda: binding.hmatvec(H, X, Y, form), max(2, args.steps // 4), 1) \
+        / max(2, args.steps // 4)
+
+    line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16+f32", "fp16": "f16+f32"}[form],
+            "data": "synthetic",
+            "config": dict(WORKLOAD, form=form, l2="inputs larger than L2 (H-matrix "
+                           f"{total_alg/1e9:.2f} GB per product)", parallelism=f"replicas{ws}"),
+            "roofline": roofline, "clocks": clocks, "e2e": e2e,
+            "gpu_launches": 3 * args.steps,
+            "rel_err_vs_fp64_form": err_mixed,
+            "fp64_form": {"ms_per_matvec": round(ms64, 4), "value": round(1e3 / ms64, 3)},
+            "nrhs32": {"ms_per_call": round(ms32, 4), "vectors_per_s": round(32e3 / ms32, 2)},
+            "assembly": {"tree_s": round(t_tree, 3), "assemble_s": round(t_asm, 3),
+                         "near_ms": round(st.assemble_ms[0], 1),
+                         "aca_ms": round(st.assemble_ms[1], 1),
+                         "rank_mean": [round(r / max(st.nadm, 1), 2) for r in st.rank_sum],
+                         "bytes_per_form": st.bytes_form}}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from paper_2205_04752_gb300 import inputs as _in
+        line["cpu_baseline"] = {k: v for k, v in cpu_baseline(V, T).items()
+                                if k in ("value", "unit", "cores", "kind", "sample")}
+    elif rank == 0:
+        line["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="fp16", choices=["fp64", "fp32", "bf16", "fp16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -155,6 +155,9 @@ typedef struct {
     int64_t M, nadm, nnear, nleaves;
     int64_t near_pairs;         /* sum over near blocks of |t||s| */
     int64_t far_entries;        /* sum over admissible blocks and kernels of k(|t|+|s|) */
+    int64_t far_u_entries;      /* sum of k|t| (U factors) */
+    int64_t far_v_entries;      /* sum of k|s| (V factors) */
+    int64_t factor_columns;     /* sum of k over admissible blocks and kernels */
     int64_t rank_sum[7];        /* per scalar kernel */
     int32_t rank_max[7];
     int32_t rank_cap_hits;      /* block-kernel pairs that hit kmax */
@@ -165,6 +168,16 @@ typedef struct {
 } hm_stats;
 
 int hm_get_stats(const hm_matrix* H, hm_stats* st);
+
+/* Measurement hook.  While enabled, hm_matvec records CUDA events around each
+ * of its kernels on the launching stream (no synchronisation is added);
+ * hm_profile_read synchronises on those events, returns the summed device
+ * time per kernel in ms (ms[0] gather, ms[1] far-field forward, ms[2]
+ * per-leaf product with the near field, ms[3] unused), the number of
+ * profiled calls, and resets the sums.  At most 4096 calls are kept between
+ * two reads (later ones are not profiled).  Not thread safe. */
+int hm_profile_enable(hm_matrix* H, int32_t on);
+int hm_profile_read(hm_matrix* H, double ms[4], int64_t* calls);
 
 /* Export one admissible block's FP64 factors for inspection: blk indexes the
  * admissible list of hm_tree_export; kern 0..6 as above.  *rank receives k;

@@ -25,7 +25,7 @@ SYMBOLS = (
     "hm_build_cluster_tree", "hm_tree_sizes", "hm_tree_export", "hm_tree_destroy",
     "hm_aca_assemble", "hm_set_material", "hm_pack", "hm_matvec", "hm_matvec_host",
     "hm_get_stats", "hm_export_factors", "hm_export_near", "hm_matrix_destroy",
-    "hm_last_error",
+    "hm_last_error", "hm_profile_enable", "hm_profile_read",
 )
 
 
@@ -52,7 +52,9 @@ class _Allocator(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int64), ("nadm", ctypes.c_int64), ("nnear", ctypes.c_int64),
                 ("nleaves", ctypes.c_int64), ("near_pairs", ctypes.c_int64),
-                ("far_entries", ctypes.c_int64), ("rank_sum", ctypes.c_int64 * 7),
+                ("far_entries", ctypes.c_int64), ("far_u_entries", ctypes.c_int64),
+                ("far_v_entries", ctypes.c_int64), ("factor_columns", ctypes.c_int64),
+                ("rank_sum", ctypes.c_int64 * 7),
                 ("rank_max", ctypes.c_int32 * 7), ("rank_cap_hits", ctypes.c_int32),
                 ("csp", ctypes.c_int32), ("bytes_fp64", ctypes.c_int64),
                 ("bytes_form", ctypes.c_int64 * 4), ("assemble_ms", ctypes.c_double * 3)]
@@ -87,6 +89,8 @@ def load():
         "hm_export_near": (ctypes.c_int, [P, I64, P]),
         "hm_matrix_destroy": (None, [P]),
         "hm_last_error": (ctypes.c_char_p, []),
+        "hm_profile_enable": (ctypes.c_int, [P, I32]),
+        "hm_profile_read": (ctypes.c_int, [P, P, ctypes.POINTER(I64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -176,6 +180,9 @@ class Stats:
     nleaves: int
     near_pairs: int
     far_entries: int
+    far_u_entries: int
+    far_v_entries: int
+    factor_columns: int
     rank_sum: list
     rank_max: list
     rank_cap_hits: int
@@ -229,8 +236,18 @@ class HMatrix:
         st = _Stats()
         _check(load().hm_get_stats(self._h, ctypes.byref(st)))
         return Stats(st.M, st.nadm, st.nnear, st.nleaves, st.near_pairs, st.far_entries,
-                     list(st.rank_sum), list(st.rank_max), st.rank_cap_hits, st.csp,
+                     st.far_u_entries, st.far_v_entries, st.factor_columns, list(st.rank_sum), list(st.rank_max), st.rank_cap_hits, st.csp,
                      st.bytes_fp64, list(st.bytes_form), list(st.assemble_ms))
+
+    def profile(self, on: bool):
+        _check(load().hm_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self):
+        """(ms per kernel [gather, far forward, leaf product, -], calls)."""
+        ms = np.zeros(4)
+        n = ctypes.c_int64(0)
+        _check(load().hm_profile_read(self._h, _ptr(ms), ctypes.byref(n)))
+        return ms, int(n.value)
 
     def export_factors(self, blk: int, kern: int):
         lib = load()
@@ -266,8 +283,10 @@ def hmatvec(H: HMatrix, x, y, form="fp64", stream=None):
     if not (x.is_cuda and y.is_cuda and x.dtype == torch.float64 and y.dtype == torch.float64):
         raise TypeError("hmatvec: x and y must be CUDA float64 tensors")
     nrhs = 1 if x.dim() == 1 else x.shape[0]
-    ld = x.shape[-1] if x.dim() == 1 else x.stride(0)
-    if (y.dim() == 1 and nrhs != 1) or (y.dim() == 2 and (y.shape[0] != nrhs or y.stride(0) != ld)):
+    # the stride of a single row is irrelevant (and may be anything)
+    ld = x.shape[-1] if nrhs == 1 else x.stride(0)
+    if (y.dim() == 1 and nrhs != 1) or (y.dim() == 2 and (y.shape[0] != nrhs or
+                                                          (nrhs > 1 and y.stride(0) != ld))):
         raise ValueError("hmatvec: y must have the shape and row stride of x")
     if x.shape[-1] != 3 * H.M or x.stride(-1) != 1 or y.stride(-1) != 1:
         raise ValueError("hmatvec: rows must be contiguous of length 3M")
@@ -282,6 +301,10 @@ def hmatvec_host(H: HMatrix, x: np.ndarray, y: np.ndarray, form="fp64", stream=N
     if x.dtype != np.float64 or y.dtype != np.float64:
         raise TypeError("hmatvec_host: float64 arrays required")
     nrhs = 1 if x.ndim == 1 else x.shape[0]
-    ld = x.shape[-1] if x.ndim == 1 else x.strides[0] // 8
+    ld = x.shape[-1] if nrhs == 1 else x.strides[0] // 8
+    if nrhs > 1 and (y.shape != x.shape or y.strides != x.strides):
+        raise ValueError("hmatvec_host: y must have the shape and strides of x")
+    if x.strides[-1] != 8 or y.strides[-1] != 8:
+        raise ValueError("hmatvec_host: rows must be contiguous")
     _check(load().hm_matvec_host(H._h, _ptr(x), _ptr(y), nrhs, ld, f, _stream_handle(stream)))
     return y

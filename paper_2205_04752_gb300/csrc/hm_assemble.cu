@@ -664,11 +664,13 @@ __global__ void repack_kernel(const AcaTask* __restrict__ tasks, int ntask,
     for (size_t e = threadIdx.x; e < nv; e += blockDim.x) dv[e] = src[nu + e];
 }
 
+// allocate max(bytes, 16) and copy exactly `bytes` (an empty list is a valid,
+// never-read device buffer)
 int upload(hm_matrix& H, DevBuf& d, const void* src, size_t bytes)
 {
-    d.bytes = bytes;
-    d.p = H.alloc.alloc(bytes);
-    if (!d.p) return fail(HM_ENOMEM, "device allocation of %zu bytes failed", bytes);
+    d.bytes = std::max<size_t>(bytes, 16);
+    d.p = H.alloc.alloc(d.bytes);
+    if (!d.p) return fail(HM_ENOMEM, "device allocation of %zu bytes failed", d.bytes);
     if (bytes) HM_CUDA(cudaMemcpyAsync(d.p, src, bytes, cudaMemcpyHostToDevice, H.alloc.stream));
     return HM_OK;
 }
@@ -939,11 +941,11 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
     H.w_total = wt;
     if ((rc = dalloc(H, H.U64, (size_t)std::max<int64_t>(ut, 1) * 8))) return rc;
     if ((rc = dalloc(H, H.V64, (size_t)std::max<int64_t>(vt, 1) * 8))) return rc;
-    if ((rc = upload(H, H.d_uoff, H.uoff_h.data(), (size_t)ntask * 8 + 8))) return rc;
-    if ((rc = upload(H, H.d_voff, H.voff_h.data(), (size_t)ntask * 8 + 8))) return rc;
-    if ((rc = upload(H, H.d_coff, H.coff_h.data(), (size_t)ntask * 8 + 8))) return rc;
-    if ((rc = upload(H, H.d_woff, H.woff_h.data(), (size_t)ntask * 8 + 8))) return rc;
-    if ((rc = upload(H, H.d_rank, H.rank_h.data(), (size_t)ntask * 4 + 4))) return rc;
+    if ((rc = upload(H, H.d_uoff, H.uoff_h.data(), (size_t)ntask * 8))) return rc;
+    if ((rc = upload(H, H.d_voff, H.voff_h.data(), (size_t)ntask * 8))) return rc;
+    if ((rc = upload(H, H.d_coff, H.coff_h.data(), (size_t)ntask * 8))) return rc;
+    if ((rc = upload(H, H.d_woff, H.woff_h.data(), (size_t)ntask * 8))) return rc;
+    if ((rc = upload(H, H.d_rank, H.rank_h.data(), (size_t)ntask * 4))) return rc;
     if (ntask > 0) {
         repack_kernel<<<(unsigned)ntask, 128, 0, s>>>(
             dtask.b.as<AcaTask>(), (int)ntask, H.d_adm.as<Blk>(), drank.b.as<int32_t>(),
@@ -994,9 +996,9 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
     H.nleaves = (int64_t)tr.leaves.size();
     if ((rc = upload(H, H.d_leaf, leafv.data(), leafv.size() * 4))) return rc;
     if ((rc = upload(H, H.d_far_ptr, far_ptr.data(), far_ptr.size() * 4))) return rc;
-    if ((rc = upload(H, H.d_far_items, far_items.data(), far_items.size() * sizeof(FarItem) + 8))) return rc;
+    if ((rc = upload(H, H.d_far_items, far_items.data(), far_items.size() * sizeof(FarItem)))) return rc;
     if ((rc = upload(H, H.d_near_ptr, near_ptr.data(), near_ptr.size() * 4))) return rc;
-    if ((rc = upload(H, H.d_near_items, near_items.data(), near_items.size() * 4 + 4))) return rc;
+    if ((rc = upload(H, H.d_near_items, near_items.data(), near_items.size() * 4))) return rc;
     {
         // phase-1 order: blocks with the most factor data first
         std::vector<int32_t> ord((size_t)H.nadm);
@@ -1007,7 +1009,7 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
                 work[(size_t)b] += (int64_t)H.rank_h[(size_t)(b * 7 + k)] * H.adm_h[(size_t)b].n;
         std::stable_sort(ord.begin(), ord.end(),
                          [&](int32_t a, int32_t b) { return work[(size_t)a] > work[(size_t)b]; });
-        if ((rc = upload(H, H.d_p1_order, ord.data(), ord.size() * 4 + 4))) return rc;
+        if ((rc = upload(H, H.d_p1_order, ord.data(), ord.size() * 4))) return rc;
     }
     // ---- workspace for the product
     H.max_rhs = H.prm.max_rhs;

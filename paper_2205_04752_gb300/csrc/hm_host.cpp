@@ -68,6 +68,25 @@ void Allocator::release(void* p, size_t bytes)
         cudaFreeAsync(p, stream);
 }
 
+void prof_mark(const hm_matrix& H, int which, cudaStream_t s)
+{
+    if (!H.prof_on) return;
+    if (which == 0 && H.prof_calls >= 4096) return;
+    int64_t c = which == 0 ? H.prof_calls : H.prof_calls - 1;
+    if (which == 0) {
+        if ((size_t)(4 * (c + 1)) > H.prof_ev.size()) {
+            for (int k = 0; k < 4; ++k) {
+                cudaEvent_t e;
+                if (cudaEventCreate(&e) != cudaSuccess) return;
+                H.prof_ev.push_back(e);
+            }
+        }
+        ++H.prof_calls;
+    }
+    if (c < 0 || (size_t)(4 * c + which) >= H.prof_ev.size()) return;
+    cudaEventRecord(H.prof_ev[(size_t)(4 * c + which)], s);
+}
+
 // ---------------------------------------------------------------- tree
 namespace {
 
@@ -332,12 +351,15 @@ int hm_get_stats(const hm_matrix* H, hm_stats* st)
         for (int k = 0; k < 7; ++k) {
             int32_t r = H->rank_h[(size_t)(b * 7 + k)];
             st->far_entries += (int64_t)r * (bk.m + bk.n);
+            st->far_u_entries += (int64_t)r * bk.m;
+            st->far_v_entries += (int64_t)r * bk.n;
             st->rank_sum[k] += r;
             st->rank_max[k] = std::max(st->rank_max[k], r);
             far_cols += r;
             if (H->flags_h[(size_t)(b * 7 + k)] & 1) st->rank_cap_hits++;
         }
     }
+    st->factor_columns = far_cols;
     st->csp = H->csp;
     int64_t near_vals = st->near_pairs * 6;
     st->bytes_fp64 = (st->far_entries + near_vals) * 8;
@@ -387,9 +409,36 @@ int hm_export_near(const hm_matrix* H, int64_t blk, double* out)
     return HM_OK;
 }
 
+int hm_profile_enable(hm_matrix* H, int32_t on)
+{
+    if (!H) return fail(HM_EINVAL, "hm_profile_enable: NULL matrix");
+    H->prof_on = on != 0;
+    return HM_OK;
+}
+
+int hm_profile_read(hm_matrix* H, double ms[4], int64_t* calls)
+{
+    if (!H || !ms) return fail(HM_EINVAL, "hm_profile_read: NULL argument");
+    for (int i = 0; i < 4; ++i) ms[i] = 0.0;
+    int64_t n = H->prof_calls;
+    for (int64_t c = 0; c < n; ++c) {
+        cudaEvent_t* e = &H->prof_ev[(size_t)(4 * c)];
+        HM_CUDA(cudaEventSynchronize(e[3]));
+        for (int k = 0; k < 3; ++k) {
+            float t = 0.0f;
+            HM_CUDA(cudaEventElapsedTime(&t, e[k], e[k + 1]));
+            ms[k] += t;
+        }
+    }
+    if (calls) *calls = n;
+    H->prof_calls = 0;
+    return HM_OK;
+}
+
 void hm_matrix_destroy(hm_matrix* H)
 {
     if (!H) return;
+    for (cudaEvent_t e : H->prof_ev) cudaEventDestroy(e);
     hm::DevBuf* bufs[] = {&H->d_perm, &H->d_adm, &H->d_near, &H->d_rank, &H->d_uoff, &H->d_voff,
                           &H->d_coff, &H->d_woff, &H->d_noff, &H->d_leaf, &H->d_far_ptr,
                           &H->d_far_items, &H->d_near_ptr, &H->d_near_items, &H->d_p1_order,

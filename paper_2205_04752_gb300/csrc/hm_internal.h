@@ -122,9 +122,16 @@ struct hm_matrix {
     hm::DevBuf xg;  // max_rhs x 3 x M doubles (gathered x, cluster order)
     hm::DevBuf wb;  // max_rhs x w_total doubles
     hm::DevBuf xh, yh;  // device staging for hm_matvec_host (max_rhs x 3M doubles)
+
+    // measurement hook (hm_profile_enable / hm_profile_read)
+    bool prof_on = false;
+    mutable std::vector<cudaEvent_t> prof_ev;  // 4 per profiled call
+    mutable int64_t prof_calls = 0;
 };
 
 namespace hm {
+// record event `which` (0..3) of the current profiled call, if profiling
+void prof_mark(const hm_matrix& H, int which, cudaStream_t s);
 // kernels launchers (implemented in the .cu files)
 int assemble_device(const hm_tree& tr, hm_matrix& H);
 int matvec_device(const hm_matrix& H, const double* x, double* y, int32_t nrhs, int64_t ld,

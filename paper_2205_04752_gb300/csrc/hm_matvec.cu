@@ -319,9 +319,11 @@ int run_matvec(const hm_matrix& H, const TF* U, const TF* V, const TN* N, const 
     const TA c1 = (TA)((1.0 + H.nu) * (3.0 - 4.0 * H.nu) / (2.0 * H.E * (1.0 - H.nu)));
     const TA c2 = (TA)((1.0 + H.nu) / (2.0 * H.E * (1.0 - H.nu)));
     dim3 gg((unsigned)((M + 255) / 256), (unsigned)nrhs);
+    prof_mark(H, 0, s);
     gather_kernel<TA><<<gg, 256, 0, s>>>(M, nrhs, x, ld, H.d_perm.as<int32_t>(), xg);
     HM_CUDA(cudaGetLastError());
     const bool multi = nrhs > 1;
+    prof_mark(H, 1, s);
     if (H.nadm > 0) {
         if (multi)
             far_fwd_kernel<TF, TA, 4><<<(unsigned)H.nadm, kFwdThreads, 0, s>>>(
@@ -335,6 +337,7 @@ int run_matvec(const hm_matrix& H, const TF* U, const TF* V, const TN* N, const 
                 M, nrhs, H.w_total, c1, c2);
         HM_CUDA(cudaGetLastError());
     }
+    prof_mark(H, 2, s);
     int bdim = H.max_leaf <= 128 ? 128 : ((H.max_leaf + 31) / 32) * 32;
     const int RCm = multi ? 4 : 1;
     size_t smem = (size_t)RCm * 3 * bdim * sizeof(TA);
@@ -351,6 +354,7 @@ int run_matvec(const hm_matrix& H, const TF* U, const TF* V, const TN* N, const 
             H.d_near.as<Blk>(), H.d_rank.as<int32_t>(), H.d_uoff.as<int64_t>(), H.d_woff.as<int64_t>(),
             H.d_noff.as<int64_t>(), U, N, xg, w, H.d_perm.as<int32_t>(), y, ld, M, nrhs, H.w_total, c1, c2);
     HM_CUDA(cudaGetLastError());
+    prof_mark(H, 3, s);
     return HM_OK;
 }
 

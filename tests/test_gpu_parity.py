@@ -31,7 +31,7 @@ class Case:
         self.perm, self.nodes, self.adm, self.near = self.tree.export()
 
     def matvec(self, x, form="fp64"):
-        xd = torch.tensor(np.atleast_2d(x), device="cuda")
+        xd = torch.tensor(np.ascontiguousarray(np.atleast_2d(x)), device="cuda")
         yd = torch.full_like(xd, np.nan)
         binding.hmatvec(self.H, xd, yd, form)
         torch.cuda.synchronize()
