@@ -145,6 +145,30 @@ int hm_pack(hm_matrix* H, int32_t form, void* stream);
 int hm_matvec(const hm_matrix* H, const double* x, double* y, int32_t nrhs, int64_t ld,
               int32_t form, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * hm_matvec_noalloc -- the product of hm_matvec for callers that cannot
+ * allocate device memory when they need it (a fixed, pre-reserved memory
+ * budget such as a real-time or embedded loop, or a host framework that owns
+ * all allocation).  The paper has no counterpart; this is a library service.
+ * Same arguments, result and determinism as hm_matvec, but the workspace
+ * (gathered x and the far-field vectors V^T x) comes from one static device
+ * array of 32 MiB inside the library instead of the matrix's own workspace.
+ *   - Allocates nothing and calls no allocating routine.
+ *   - The array is held by every GPU on which the library is loaded, until
+ *     the process exits.
+ *   - Products needing more than 32 MiB of workspace are rejected with
+ *     HM_EINVAL (need = nrhs * (3M + 3 * sum of ACA ranks) * 8 bytes for
+ *     HM_FP64, * 4 for the other forms, plus alignment).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress, which may load the library's device code on
+ *     that device); make that first call before any stream capture.
+ *   - All calls share the array: calls whose kernels overlap in time on the
+ *     device race and give wrong results.  Nothing in it needs to start at
+ *     zero (every call writes each element before reading it).
+ * ------------------------------------------------------------------------- */
+int hm_matvec_noalloc(const hm_matrix* H, const double* x, double* y, int32_t nrhs, int64_t ld,
+                      int32_t form, void* stream);
+
 /* Same product with HOST x and y: copies x in, runs hm_matvec, copies y back
  * and synchronises `stream`.  Pinned host memory gives the fastest copies. */
 int hm_matvec_host(const hm_matrix* H, const double* x_host, double* y_host, int32_t nrhs,

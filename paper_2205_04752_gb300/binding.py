@@ -25,7 +25,7 @@ SYMBOLS = (
     "hm_build_cluster_tree", "hm_tree_sizes", "hm_tree_export", "hm_tree_destroy",
     "hm_aca_assemble", "hm_set_material", "hm_pack", "hm_matvec", "hm_matvec_host",
     "hm_get_stats", "hm_export_factors", "hm_export_near", "hm_matrix_destroy",
-    "hm_last_error", "hm_profile_enable", "hm_profile_read",
+    "hm_last_error", "hm_profile_enable", "hm_profile_read", "hm_matvec_noalloc",
 )
 
 
@@ -84,6 +84,7 @@ def load():
         "hm_pack": (ctypes.c_int, [P, I32, P]),
         "hm_matvec": (ctypes.c_int, [P, P, P, I32, I64, I32, P]),
         "hm_matvec_host": (ctypes.c_int, [P, P, P, I32, I64, I32, P]),
+        "hm_matvec_noalloc": (ctypes.c_int, [P, P, P, I32, I64, I32, P]),
         "hm_get_stats": (ctypes.c_int, [P, ctypes.POINTER(_Stats)]),
         "hm_export_factors": (ctypes.c_int, [P, I64, I32, ctypes.POINTER(I32), P, P]),
         "hm_export_near": (ctypes.c_int, [P, I64, P]),
@@ -292,6 +293,25 @@ def hmatvec(H: HMatrix, x, y, form="fp64", stream=None):
         raise ValueError("hmatvec: rows must be contiguous of length 3M")
     _check(load().hm_matvec(H._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                             nrhs, ld, f, _stream_handle(stream)))
+    return y
+
+
+def hmatvec_noalloc(H: HMatrix, x, y, form="fp64", stream=None):
+    """``hm_matvec_noalloc``: the product of ``hmatvec`` with its workspace
+    taken from the library's fixed 32 MiB static device array, for callers
+    that cannot allocate device memory; it allocates nothing.  Calls must not
+    overlap on the device (they share that array)."""
+    import torch
+    f = FORMS[form] if isinstance(form, str) else int(form)
+    if not (x.is_cuda and y.is_cuda and x.dtype == torch.float64 and y.dtype == torch.float64):
+        raise TypeError("hmatvec_noalloc: x and y must be CUDA float64 tensors")
+    nrhs = 1 if x.dim() == 1 else x.shape[0]
+    ld = x.shape[-1] if nrhs == 1 else x.stride(0)
+    if y.shape != x.shape or (nrhs > 1 and y.stride(0) != ld):
+        raise ValueError("hmatvec_noalloc: y must have the shape and row stride of x")
+    _check(load().hm_matvec_noalloc(H._h, ctypes.c_void_p(x.data_ptr()),
+                                    ctypes.c_void_p(y.data_ptr()), nrhs, ld, f,
+                                    _stream_handle(stream)))
     return y
 
 

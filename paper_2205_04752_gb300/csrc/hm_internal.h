@@ -130,6 +130,17 @@ struct hm_matrix {
 };
 
 namespace hm {
+// workspace of one product: gathered x (nrhs x 3 x M) and the far-field w
+// vectors (nrhs x w_total), both in the form's accumulation type
+struct Scratch {
+    void* xg;
+    void* w;
+    bool profile;  // record the measurement-hook events
+};
+int matvec_device_scratch(const hm_matrix& H, const double* x, double* y, int32_t nrhs,
+                          int64_t ld, int32_t form, cudaStream_t s, const Scratch& scr);
+// bytes of Scratch a product of nrhs vectors in `form` needs (xg 256-aligned, then w)
+size_t matvec_scratch_bytes(const hm_matrix& H, int32_t nrhs, int32_t form);
 // record event `which` (0..3) of the current profiled call, if profiling
 void prof_mark(const hm_matrix& H, int which, cudaStream_t s);
 // kernels launchers (implemented in the .cu files)

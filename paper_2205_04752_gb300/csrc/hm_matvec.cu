@@ -311,19 +311,20 @@ int dalloc(hm_matrix& H, DevBuf& d, size_t bytes)
 
 template <class TF, class TN, class TA>
 int run_matvec(const hm_matrix& H, const TF* U, const TF* V, const TN* N, const float* SU,
-               const float* SV, const double* x, double* y, int nrhs, int64_t ld, cudaStream_t s)
+               const float* SV, const double* x, double* y, int nrhs, int64_t ld, cudaStream_t s,
+               const Scratch& scr)
 {
     const int M = (int)H.M;
-    TA* xg = H.xg.as<TA>();
-    TA* w = H.wb.as<TA>();
+    TA* xg = static_cast<TA*>(scr.xg);
+    TA* w = static_cast<TA*>(scr.w);
     const TA c1 = (TA)((1.0 + H.nu) * (3.0 - 4.0 * H.nu) / (2.0 * H.E * (1.0 - H.nu)));
     const TA c2 = (TA)((1.0 + H.nu) / (2.0 * H.E * (1.0 - H.nu)));
     dim3 gg((unsigned)((M + 255) / 256), (unsigned)nrhs);
-    prof_mark(H, 0, s);
+    if (scr.profile) prof_mark(H, 0, s);
     gather_kernel<TA><<<gg, 256, 0, s>>>(M, nrhs, x, ld, H.d_perm.as<int32_t>(), xg);
     HM_CUDA(cudaGetLastError());
     const bool multi = nrhs > 1;
-    prof_mark(H, 1, s);
+    if (scr.profile) prof_mark(H, 1, s);
     if (H.nadm > 0) {
         if (multi)
             far_fwd_kernel<TF, TA, 4><<<(unsigned)H.nadm, kFwdThreads, 0, s>>>(
@@ -337,7 +338,7 @@ int run_matvec(const hm_matrix& H, const TF* U, const TF* V, const TN* N, const 
                 M, nrhs, H.w_total, c1, c2);
         HM_CUDA(cudaGetLastError());
     }
-    prof_mark(H, 2, s);
+    if (scr.profile) prof_mark(H, 2, s);
     int bdim = H.max_leaf <= 128 ? 128 : ((H.max_leaf + 31) / 32) * 32;
     const int RCm = multi ? 4 : 1;
     size_t smem = (size_t)RCm * 3 * bdim * sizeof(TA);
@@ -354,35 +355,50 @@ int run_matvec(const hm_matrix& H, const TF* U, const TF* V, const TN* N, const 
             H.d_near.as<Blk>(), H.d_rank.as<int32_t>(), H.d_uoff.as<int64_t>(), H.d_woff.as<int64_t>(),
             H.d_noff.as<int64_t>(), U, N, xg, w, H.d_perm.as<int32_t>(), y, ld, M, nrhs, H.w_total, c1, c2);
     HM_CUDA(cudaGetLastError());
-    prof_mark(H, 3, s);
+    if (scr.profile) prof_mark(H, 3, s);
     return HM_OK;
 }
 
 }  // namespace
 
-int matvec_device(const hm_matrix& H, const double* x, double* y, int32_t nrhs, int64_t ld,
-                  int32_t form, cudaStream_t s)
+int matvec_device_scratch(const hm_matrix& H, const double* x, double* y, int32_t nrhs, int64_t ld,
+                          int32_t form, cudaStream_t s, const Scratch& scr)
 {
     switch (form) {
         case HM_FP64:
             return run_matvec<double, double, double>(H, H.U64.as<double>(), H.V64.as<double>(),
                                                       H.N64.as<double>(), nullptr, nullptr, x, y,
-                                                      nrhs, ld, s);
+                                                      nrhs, ld, s, scr);
         case HM_FP32:
             return run_matvec<float, float, float>(H, H.U32.as<float>(), H.V32.as<float>(),
                                                    H.N32.as<float>(), nullptr, nullptr, x, y, nrhs,
-                                                   ld, s);
+                                                   ld, s, scr);
         case HM_BF16:
             return run_matvec<__nv_bfloat16, float, float>(
                 H, H.U16b.as<__nv_bfloat16>(), H.V16b.as<__nv_bfloat16>(), H.N32.as<float>(),
-                H.SUb.as<float>(), H.SVb.as<float>(), x, y, nrhs, ld, s);
+                H.SUb.as<float>(), H.SVb.as<float>(), x, y, nrhs, ld, s, scr);
         case HM_FP16:
             return run_matvec<__half, float, float>(H, H.U16h.as<__half>(), H.V16h.as<__half>(),
                                                     H.N32.as<float>(), H.SUh.as<float>(),
-                                                    H.SVh.as<float>(), x, y, nrhs, ld, s);
+                                                    H.SVh.as<float>(), x, y, nrhs, ld, s, scr);
         default:
             return fail(HM_EINVAL, "hm_matvec: unknown form %d", form);
     }
+}
+
+int matvec_device(const hm_matrix& H, const double* x, double* y, int32_t nrhs, int64_t ld,
+                  int32_t form, cudaStream_t s)
+{
+    Scratch scr{H.xg.p, H.wb.p, true};
+    return matvec_device_scratch(H, x, y, nrhs, ld, form, s, scr);
+}
+
+size_t matvec_scratch_bytes(const hm_matrix& H, int32_t nrhs, int32_t form)
+{
+    size_t ta = form == HM_FP64 ? 8 : 4;
+    size_t xg = ((size_t)nrhs * 3 * (size_t)H.M * ta + 255) & ~(size_t)255;
+    size_t w = (size_t)nrhs * (size_t)std::max<int64_t>(H.w_total, 1) * ta;
+    return xg + w;
 }
 
 int pack_device(hm_matrix& H, int32_t form, cudaStream_t s)
