@@ -174,6 +174,11 @@ int hm_matvec_noalloc(const hm_matrix* H, const double* x, double* y, int32_t nr
 int hm_matvec_host(const hm_matrix* H, const double* x_host, double* y_host, int32_t nrhs,
                    int64_t ld, int32_t form, void* stream);
 
+/* Status of the asynchronous products of H: HM_ETIMEOUT if a bounded device
+ * wait inside an earlier hm_matvec ran out (its result is then invalid; the
+ * flag is cleared), HM_OK otherwise.  Synchronises the device. */
+int hm_check(const hm_matrix* H);
+
 /* Statistics of an assembled matrix. */
 typedef struct {
     int64_t M, nadm, nnear, nleaves;

@@ -25,7 +25,7 @@ SYMBOLS = (
     "hm_build_cluster_tree", "hm_tree_sizes", "hm_tree_export", "hm_tree_destroy",
     "hm_aca_assemble", "hm_set_material", "hm_pack", "hm_matvec", "hm_matvec_host",
     "hm_get_stats", "hm_export_factors", "hm_export_near", "hm_matrix_destroy",
-    "hm_last_error", "hm_profile_enable", "hm_profile_read", "hm_matvec_noalloc",
+    "hm_last_error", "hm_profile_enable", "hm_profile_read", "hm_matvec_noalloc", "hm_check",
 )
 
 
@@ -85,6 +85,7 @@ def load():
         "hm_matvec": (ctypes.c_int, [P, P, P, I32, I64, I32, P]),
         "hm_matvec_host": (ctypes.c_int, [P, P, P, I32, I64, I32, P]),
         "hm_matvec_noalloc": (ctypes.c_int, [P, P, P, I32, I64, I32, P]),
+        "hm_check": (ctypes.c_int, [P]),
         "hm_get_stats": (ctypes.c_int, [P, ctypes.POINTER(_Stats)]),
         "hm_export_factors": (ctypes.c_int, [P, I64, I32, ctypes.POINTER(I32), P, P]),
         "hm_export_near": (ctypes.c_int, [P, I64, P]),
@@ -239,6 +240,10 @@ class HMatrix:
         return Stats(st.M, st.nadm, st.nnear, st.nleaves, st.near_pairs, st.far_entries,
                      st.far_u_entries, st.far_v_entries, st.factor_columns, list(st.rank_sum), list(st.rank_max), st.rank_cap_hits, st.csp,
                      st.bytes_fp64, list(st.bytes_form), list(st.assemble_ms))
+
+    def check(self):
+        """Raise if a bounded device wait in an earlier product ran out."""
+        _check(load().hm_check(self._h))
 
     def profile(self, on: bool):
         _check(load().hm_profile_enable(self._h, 1 if on else 0))

@@ -918,8 +918,7 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
     H.uoff_h.resize((size_t)ntask);
     H.voff_h.resize((size_t)ntask);
     H.coff_h.resize((size_t)ntask);
-    H.woff_h.resize((size_t)ntask);
-    int64_t ut = 0, vt = 0, ct = 0, wt = 0;
+    int64_t ut = 0, vt = 0, ct = 0;
     for (int64_t b = 0; b < H.nadm; ++b)
         for (int k = 0; k < 7; ++k) {
             size_t q = (size_t)(b * 7 + k);
@@ -928,23 +927,20 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
             H.uoff_h[q] = ut;
             H.voff_h[q] = vt;
             H.coff_h[q] = ct;
-            H.woff_h[q] = wt;
             // keep every factor start 16-byte aligned for vector loads
             ut += ((int64_t)r * bk.m + 7) & ~int64_t(7);
             vt += ((int64_t)r * bk.n + 7) & ~int64_t(7);
             ct += r;
-            wt += 3 * (int64_t)r;
         }
     H.u_total = ut;
     H.v_total = vt;
     H.c_total = ct;
-    H.w_total = wt;
+    H.w_total = 4 * ct;  // w holds one 4-vector per factor column
     if ((rc = dalloc(H, H.U64, (size_t)std::max<int64_t>(ut, 1) * 8))) return rc;
     if ((rc = dalloc(H, H.V64, (size_t)std::max<int64_t>(vt, 1) * 8))) return rc;
     if ((rc = upload(H, H.d_uoff, H.uoff_h.data(), (size_t)ntask * 8))) return rc;
     if ((rc = upload(H, H.d_voff, H.voff_h.data(), (size_t)ntask * 8))) return rc;
     if ((rc = upload(H, H.d_coff, H.coff_h.data(), (size_t)ntask * 8))) return rc;
-    if ((rc = upload(H, H.d_woff, H.woff_h.data(), (size_t)ntask * 8))) return rc;
     if ((rc = upload(H, H.d_rank, H.rank_h.data(), (size_t)ntask * 4))) return rc;
     if (ntask > 0) {
         repack_kernel<<<(unsigned)ntask, 128, 0, s>>>(
@@ -955,13 +951,15 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
     }
     HM_CUDA(cudaEventRecord(ev[3], s));
 
-    // ---- per-leaf work lists of the product
-    std::vector<int32_t> leafv;
-    std::vector<int32_t> far_ptr(1, 0), near_ptr(1, 0);
-    std::vector<FarItem> far_items;
-    std::vector<int32_t> near_items;
+    // ---- streaming layouts of the product (element offsets; the arenas of
+    // each form are filled by pack_device)
+    //   U, per leaf tau: for every admissible block t x s with t containing
+    //     tau (root first) and every kernel with k > 0, the k columns of
+    //     U[rows of tau, :] as segments of mp = roundup(|tau|, 8) elements;
+    //   near field, per leaf: for every near block tau x sigma and column j,
+    //     six segments (V_11, V_12, V_13, V_22, V_23, V_33) of mp elements;
+    //   V, per admissible block: row-major |s| x Cp, Cp = roundup(sum k, 8).
     {
-        // admissible / near blocks grouped by row node
         std::vector<std::vector<int32_t>> adm_by_row(tr.nodes.size()), near_by_row(tr.nodes.size());
         for (int64_t b = 0; b < H.nadm; ++b) adm_by_row[(size_t)tr.adm[(size_t)b][0]].push_back((int32_t)b);
         for (int64_t b = 0; b < H.nnear; ++b)
@@ -970,37 +968,101 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
         for (size_t n = 0; n < tr.nodes.size(); ++n)
             csp = std::max<int32_t>(csp, (int32_t)(adm_by_row[n].size() + near_by_row[n].size()));
         H.csp = csp;
-        // ancestor chains: walk the tree from the root
         std::vector<int64_t> parent(tr.nodes.size(), -1);
         for (size_t n = 0; n < tr.nodes.size(); ++n)
             for (int c = 0; c < 2; ++c)
                 if (tr.nodes[n].son[c] >= 0) parent[(size_t)tr.nodes[n].son[c]] = (int64_t)n;
+        std::vector<int32_t> leafv, lf_ptr(1, 0), ln_ptr(1, 0);
+        std::vector<int64_t> lf_base, ln_base;
+        std::vector<LeafFarItem> lf_items;
+        std::vector<PackSrc> lf_src;
+        std::vector<LeafNearItem> ln_items;
+        std::vector<NearSrc> ln_src;
+        int64_t ul = 0, nl = 0;
         int32_t maxleaf = 0;
         for (int64_t lf : tr.leaves) {
             const Node& L = tr.nodes[(size_t)lf];
+            const int32_t mt = (int32_t)(L.hi - L.lo);
+            const int64_t mp = (mt + 7) & ~7;
             leafv.push_back((int32_t)L.lo);
-            leafv.push_back((int32_t)(L.hi - L.lo));
-            maxleaf = std::max<int32_t>(maxleaf, (int32_t)(L.hi - L.lo));
+            leafv.push_back(mt);
+            maxleaf = std::max(maxleaf, mt);
             std::vector<int64_t> chain;
             for (int64_t n = lf; n >= 0; n = parent[(size_t)n]) chain.push_back(n);
             std::reverse(chain.begin(), chain.end());  // root first
+            int32_t seg = 0;
+            lf_base.push_back(ul);
             for (int64_t n : chain)
-                for (int32_t b : adm_by_row[(size_t)n])
-                    far_items.push_back(FarItem{b, (int32_t)(L.lo - tr.nodes[(size_t)n].lo)});
-            far_ptr.push_back((int32_t)far_items.size());
-            for (int32_t b : near_by_row[(size_t)lf]) near_items.push_back(b);
-            near_ptr.push_back((int32_t)near_items.size());
+                for (int32_t b : adm_by_row[(size_t)n]) {
+                    const int32_t off = (int32_t)(L.lo - tr.nodes[(size_t)n].lo);
+                    for (int k = 0; k < 7; ++k) {
+                        const size_t q = (size_t)b * 7 + k;
+                        const int32_t r = H.rank_h[q];
+                        if (r == 0) continue;
+                        lf_items.push_back(LeafFarItem{seg, (int32_t)H.coff_h[q]});
+                        lf_src.push_back(PackSrc{H.uoff_h[q] + off, H.adm_h[(size_t)b].m, r});
+                        seg += r;
+                    }
+                }
+            lf_items.push_back(LeafFarItem{seg, 0});  // sentinel: number of segments
+            lf_src.push_back(PackSrc{0, 0, 0});
+            lf_ptr.push_back((int32_t)lf_items.size());
+            ul += (int64_t)seg * mp;
+            int32_t col = 0;
+            ln_base.push_back(nl);
+            for (int32_t b : near_by_row[(size_t)lf]) {
+                const Blk& bk = H.near_h[(size_t)b];
+                ln_items.push_back(LeafNearItem{col, bk.s0});
+                ln_src.push_back(NearSrc{H.noff_h[(size_t)b], bk.n, 0});
+                col += bk.n;
+            }
+            ln_items.push_back(LeafNearItem{col, 0});  // sentinel: number of columns
+            ln_src.push_back(NearSrc{0, 0, 0});
+            ln_ptr.push_back((int32_t)ln_items.size());
+            nl += (int64_t)col * 6 * mp;
         }
         H.max_leaf = maxleaf;
+        H.ul_total = ul;
+        H.nl_total = nl;
+        std::vector<int64_t> vb_base((size_t)H.nadm + 1);
+        int64_t vr = 0;
+        for (int64_t b = 0; b < H.nadm; ++b) {
+            int64_t C = 0;
+            for (int k = 0; k < 7; ++k) C += H.rank_h[(size_t)(b * 7 + k)];
+            vb_base[(size_t)b] = vr;
+            vr += (int64_t)H.adm_h[(size_t)b].n * ((C + 7) & ~int64_t(7));
+        }
+        vb_base[(size_t)H.nadm] = vr;
+        H.vr_total = vr;
+        H.nleaves = (int64_t)tr.leaves.size();
+        {
+            // streamed kernel: leaves with the most bytes first
+            std::vector<int64_t> bytes(tr.leaves.size());
+            for (size_t l = 0; l < tr.leaves.size(); ++l) {
+                const int64_t mp = (leafv[2 * l + 1] + 7) & ~7;
+                bytes[l] = (int64_t)lf_items[(size_t)lf_ptr[l + 1] - 1].seg_start * mp +
+                           (int64_t)ln_items[(size_t)ln_ptr[l + 1] - 1].col_start * 6 * mp;
+            }
+            std::vector<int32_t> order(tr.leaves.size());
+            std::iota(order.begin(), order.end(), 0);
+            std::stable_sort(order.begin(), order.end(),
+                             [&](int32_t a, int32_t b) { return bytes[(size_t)a] > bytes[(size_t)b]; });
+            if ((rc = upload(H, H.d_leaf_order, order.data(), order.size() * 4))) return rc;
+        }
+        if ((rc = upload(H, H.d_leaf, leafv.data(), leafv.size() * 4))) return rc;
+        if ((rc = upload(H, H.d_lf_base, lf_base.data(), lf_base.size() * 8))) return rc;
+        if ((rc = upload(H, H.d_lf_ptr, lf_ptr.data(), lf_ptr.size() * 4))) return rc;
+        if ((rc = upload(H, H.d_lf_items, lf_items.data(), lf_items.size() * sizeof(LeafFarItem)))) return rc;
+        if ((rc = upload(H, H.d_lf_src, lf_src.data(), lf_src.size() * sizeof(PackSrc)))) return rc;
+        if ((rc = upload(H, H.d_ln_base, ln_base.data(), ln_base.size() * 8))) return rc;
+        if ((rc = upload(H, H.d_ln_ptr, ln_ptr.data(), ln_ptr.size() * 4))) return rc;
+        if ((rc = upload(H, H.d_ln_items, ln_items.data(), ln_items.size() * sizeof(LeafNearItem)))) return rc;
+        if ((rc = upload(H, H.d_ln_src, ln_src.data(), ln_src.size() * sizeof(NearSrc)))) return rc;
+        if ((rc = upload(H, H.d_vb_base, vb_base.data(), vb_base.size() * 8))) return rc;
     }
-    H.nleaves = (int64_t)tr.leaves.size();
-    if ((rc = upload(H, H.d_leaf, leafv.data(), leafv.size() * 4))) return rc;
-    if ((rc = upload(H, H.d_far_ptr, far_ptr.data(), far_ptr.size() * 4))) return rc;
-    if ((rc = upload(H, H.d_far_items, far_items.data(), far_items.size() * sizeof(FarItem)))) return rc;
-    if ((rc = upload(H, H.d_near_ptr, near_ptr.data(), near_ptr.size() * 4))) return rc;
-    if ((rc = upload(H, H.d_near_items, near_items.data(), near_items.size() * 4))) return rc;
     {
-        // phase-1 order: blocks with the most factor data first
+        // forward-pass records: blocks with |s| <= 128 (one warp each) and
+        // larger ones (one CTA each), each list with the most data first
         std::vector<int32_t> ord((size_t)H.nadm);
         std::iota(ord.begin(), ord.end(), 0);
         std::vector<int64_t> work((size_t)H.nadm, 0);
@@ -1009,14 +1071,55 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
                 work[(size_t)b] += (int64_t)H.rank_h[(size_t)(b * 7 + k)] * H.adm_h[(size_t)b].n;
         std::stable_sort(ord.begin(), ord.end(),
                          [&](int32_t a, int32_t b) { return work[(size_t)a] > work[(size_t)b]; });
-        if ((rc = upload(H, H.d_p1_order, ord.data(), ord.size() * 4))) return rc;
+        std::vector<FwdRec> small, big;
+        std::vector<int64_t> vb((size_t)H.nadm + 1);
+        {
+            int64_t vr = 0;
+            for (int64_t b = 0; b < H.nadm; ++b) {
+                int64_t C = 0;
+                for (int k = 0; k < 7; ++k) C += H.rank_h[(size_t)(b * 7 + k)];
+                vb[(size_t)b] = vr;
+                vr += (int64_t)H.adm_h[(size_t)b].n * ((C + 7) & ~int64_t(7));
+            }
+        }
+        for (int32_t b : ord) {
+            FwdRec r{};
+            const Blk& bk = H.adm_h[(size_t)b];
+            r.s0 = bk.s0;
+            r.n = bk.n;
+            r.col0 = (int32_t)H.coff_h[(size_t)b * 7];
+            r.C = 0;
+            for (int k = 0; k < 7; ++k) {
+                const int32_t kk = H.rank_h[(size_t)(b * 7 + k)];
+                if (kk > 255) return fail(HM_EINVAL, "rank %d above 255 is not supported", kk);
+                r.kpack |= (uint64_t)kk << (8 * k);
+                r.C += kk;
+            }
+            r.vbase = vb[(size_t)b];
+            if (r.C == 0) continue;
+            (bk.n <= 128 ? small : big).push_back(r);
+        }
+        H.n_fwd_small = (int64_t)small.size();
+        H.n_fwd_big = (int64_t)big.size();
+        if ((rc = upload(H, H.d_fwd_small, small.data(), small.size() * sizeof(FwdRec)))) return rc;
+        if ((rc = upload(H, H.d_fwd_big, big.data(), big.size() * sizeof(FwdRec)))) return rc;
+        if (H.c_total > INT32_MAX / 4) return fail(HM_EINVAL, "too many factor columns");
     }
     // ---- workspace for the product
     H.max_rhs = H.prm.max_rhs;
-    if ((rc = dalloc(H, H.xg, (size_t)H.max_rhs * 3 * M * 8))) return rc;
+    if ((rc = dalloc(H, H.xg, (size_t)H.max_rhs * 4 * M * 8))) return rc;
     if ((rc = dalloc(H, H.wb, (size_t)H.max_rhs * std::max<int64_t>(H.w_total, 1) * 8))) return rc;
+    if ((rc = dalloc(H, H.yn, (size_t)H.max_rhs * 3 * M * 8))) return rc;
+    if ((rc = dalloc(H, H.d_counters, (size_t)H.max_rhs * sizeof(int)))) return rc;
+    if ((rc = dalloc(H, H.d_err, 64))) return rc;
+    HM_CUDA(cudaMemsetAsync(H.d_err.p, 0, 64, s));
+    HM_CUDA(cudaStreamCreateWithFlags(&H.side, cudaStreamNonBlocking));
+    HM_CUDA(cudaEventCreateWithFlags(&H.ev_fork, cudaEventDisableTiming));
+    HM_CUDA(cudaEventCreateWithFlags(&H.ev_join, cudaEventDisableTiming));
     if ((rc = dalloc(H, H.xh, (size_t)H.max_rhs * 3 * M * 8))) return rc;
     if ((rc = dalloc(H, H.yh, (size_t)H.max_rhs * 3 * M * 8))) return rc;
+    // the FP64 form is always available
+    if ((rc = pack_device(H, HM_FP64, s))) return rc;
     HM_CUDA(cudaStreamSynchronize(s));
     float t01 = 0, t12 = 0, t23 = 0;
     cudaEventElapsedTime(&t01, ev[0], ev[1]);

@@ -363,12 +363,15 @@ int hm_get_stats(const hm_matrix* H, hm_stats* st)
     st->csp = H->csp;
     int64_t near_vals = st->near_pairs * 6;
     st->bytes_fp64 = (st->far_entries + near_vals) * 8;
-    st->bytes_form[0] = st->bytes_fp64;
-    if (H->packed[1]) st->bytes_form[1] = (st->far_entries + near_vals) * 4;
-    // packed 16-bit forms: 2-byte factors, one float scale per factor column
-    // (U and V), FP32 near field
-    if (H->packed[2]) st->bytes_form[2] = st->far_entries * 2 + far_cols * 8 + near_vals * 4;
-    if (H->packed[3]) st->bytes_form[3] = st->far_entries * 2 + far_cols * 8 + near_vals * 4;
+    // bytes one product streams in each packed form (padded layouts; the
+    // 16-bit forms add one float scale per factor column of U and of V)
+    const int64_t stream_elems = H->ul_total + H->vr_total;
+    for (int f = 0; f < 4; ++f) {
+        if (!H->packed[f]) continue;
+        int64_t wf = f == HM_FP64 ? 8 : (f == HM_FP32 ? 4 : 2);
+        int64_t wn = f == HM_FP64 ? 8 : 4;
+        st->bytes_form[f] = stream_elems * wf + H->nl_total * wn + (wf == 2 ? far_cols * 8 : 0);
+    }
     for (int i = 0; i < 3; ++i) st->assemble_ms[i] = H->asm_ms[i];
     return HM_OK;
 }
@@ -409,6 +412,19 @@ int hm_export_near(const hm_matrix* H, int64_t blk, double* out)
     return HM_OK;
 }
 
+int hm_check(const hm_matrix* H)
+{
+    if (!H) return fail(HM_EINVAL, "hm_check: NULL matrix");
+    int flag = 0;
+    HM_CUDA(cudaMemcpy(&flag, H->d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        const int zero = 0;
+        HM_CUDA(cudaMemcpy(H->d_err.p, &zero, sizeof(int), cudaMemcpyHostToDevice));
+        return fail(HM_ETIMEOUT, "hm_check: a bounded device wait ran out in an earlier product");
+    }
+    return HM_OK;
+}
+
 int hm_profile_enable(hm_matrix* H, int32_t on)
 {
     if (!H) return fail(HM_EINVAL, "hm_profile_enable: NULL matrix");
@@ -439,12 +455,19 @@ void hm_matrix_destroy(hm_matrix* H)
 {
     if (!H) return;
     for (cudaEvent_t e : H->prof_ev) cudaEventDestroy(e);
+    if (H->ev_fork) cudaEventDestroy(H->ev_fork);
+    if (H->ev_join) cudaEventDestroy(H->ev_join);
+    if (H->side) {
+        cudaStreamSynchronize(H->side);
+        cudaStreamDestroy(H->side);
+    }
     hm::DevBuf* bufs[] = {&H->d_perm, &H->d_adm, &H->d_near, &H->d_rank, &H->d_uoff, &H->d_voff,
-                          &H->d_coff, &H->d_woff, &H->d_noff, &H->d_leaf, &H->d_far_ptr,
-                          &H->d_far_items, &H->d_near_ptr, &H->d_near_items, &H->d_p1_order,
-                          &H->U64, &H->V64, &H->N64, &H->U32, &H->V32, &H->N32, &H->U16b,
-                          &H->V16b, &H->U16h, &H->V16h, &H->SUb, &H->SVb, &H->SUh, &H->SVh,
-                          &H->xg, &H->wb, &H->xh, &H->yh};
+                          &H->d_coff, &H->d_noff, &H->d_leaf, &H->d_lf_base, &H->d_lf_ptr,
+                          &H->d_lf_items, &H->d_lf_src, &H->d_ln_base, &H->d_ln_ptr, &H->d_ln_items,
+                          &H->d_ln_src, &H->d_vb_base, &H->d_fwd_small, &H->d_fwd_big, &H->d_leaf_order, &H->d_counters, &H->d_err, &H->U64, &H->V64, &H->N64,
+                          &H->Ul[0], &H->Ul[1], &H->Ul[2], &H->Ul[3], &H->Vr[0], &H->Vr[1],
+                          &H->Vr[2], &H->Vr[3], &H->Nl64, &H->Nl32, &H->SU, &H->SV, &H->xg, &H->wb,
+                          &H->yn, &H->xh, &H->yh};
     // the assembly stream may be gone by now: drain the device and release
     // on the legacy default stream
     cudaDeviceSynchronize();

@@ -71,9 +71,34 @@ struct Blk {
     int32_t t0, m, s0, n;
 };
 
-// matvec work item of a leaf: admissible block b, row offset of the leaf in t
-struct FarItem {
-    int32_t b, off;
+// far-field stream of a leaf: item = one (admissible block, kernel) with its
+// first segment in the leaf's stream and its first global factor column; each
+// leaf's list ends with a sentinel whose seg_start is the segment count
+struct LeafFarItem {
+    int32_t seg_start, col;
+};
+// source of a far item in the block-ordered FP64 U arena (used by packing):
+// element offset of (first row of the leaf, column 0), leading dimension, rank
+struct PackSrc {
+    int64_t src;
+    int32_t ld, k;
+};
+// near-field stream of a leaf: item = one near block with its first column in
+// the stream and its first column cluster position; sentinel as above
+struct LeafNearItem {
+    int32_t col_start, s0;
+};
+struct NearSrc {
+    int64_t src;  // element offset of the block in the block-ordered FP64 near arena
+    int32_t n, pad;
+};
+// one admissible block of the far-field forward pass (32 bytes): column
+// cluster start and size, first global factor column, total rank, offset of
+// its row-major V, and the rank of each of the seven kernels
+struct FwdRec {
+    int32_t s0, n, col0, C;
+    int64_t vbase;
+    uint64_t kpack;  // rank of kernel q in bits 8q .. 8q+7
 };
 
 }  // namespace hm
@@ -90,7 +115,6 @@ struct hm_matrix {
     std::vector<int32_t> flags_h;         // nadm * 7
     std::vector<int64_t> uoff_h, voff_h;  // element offsets in the U / V arenas (nadm*7)
     std::vector<int64_t> coff_h;          // column offsets (per-column scales), nadm*7
-    std::vector<int64_t> woff_h;          // offsets in the w workspace (nadm*7), 3k each
     std::vector<int64_t> noff_h;          // element offsets in the near arena (nnear)
     int64_t u_total = 0, v_total = 0, c_total = 0, w_total = 0, n_total = 0;
     int32_t csp = 0;
@@ -102,25 +126,35 @@ struct hm_matrix {
     hm::DevBuf d_adm;    // Blk nadm
     hm::DevBuf d_near;   // Blk nnear
     hm::DevBuf d_rank;   // int32 nadm*7
-    hm::DevBuf d_uoff, d_voff, d_coff, d_woff;  // int64 nadm*7
+    hm::DevBuf d_uoff, d_voff, d_coff;  // int64 nadm*7
     hm::DevBuf d_noff;   // int64 nnear
     hm::DevBuf d_leaf;   // int32 2*nleaves (t0, m)
-    hm::DevBuf d_far_ptr, d_far_items;    // CSR per leaf
-    hm::DevBuf d_near_ptr, d_near_items;  // CSR per leaf (near block ids)
-    hm::DevBuf d_p1_order;                // int32 nadm: phase-1 block order (largest first)
+    hm::DevBuf d_lf_base, d_lf_ptr, d_lf_items, d_lf_src;  // far stream per leaf
+    hm::DevBuf d_ln_base, d_ln_ptr, d_ln_items, d_ln_src;  // near stream per leaf
+    hm::DevBuf d_vb_base;                 // int64 nadm+1: row-major V of each block
+    hm::DevBuf d_fwd_small, d_fwd_big;   // FwdRec: blocks with |s| <= 128 / larger ones
+    hm::DevBuf d_leaf_order;             // int32 nleaves: leaves by decreasing streamed bytes
+    hm::DevBuf d_counters;               // int32 max_rhs: work counters of the streamed kernel
+    hm::DevBuf d_err;                    // int32: set by a device wait that ran out
+    int64_t n_fwd_small = 0, n_fwd_big = 0;
+    int64_t ul_total = 0, nl_total = 0, vr_total = 0;
+    // the near field runs on a second stream, concurrently with the far field
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
-    // FP64 arenas
+    // FP64 factor and near arenas in block order (ACA output, export)
     hm::DevBuf U64, V64, N64;
-    // packed arenas
-    hm::DevBuf U32, V32, N32;          // FP32 (N32 also serves BF16/FP16 forms)
-    hm::DevBuf U16b, V16b, U16h, V16h;  // BF16 / FP16 factors
-    hm::DevBuf SUb, SVb, SUh, SVh;     // per-column scales (float) for BF16 / FP16
-    bool packed[4] = {true, false, false, false};
+    // streaming arenas of each form (index = form): U leaf-major, V row-major
+    hm::DevBuf Ul[4], Vr[4];
+    hm::DevBuf Nl64, Nl32;  // near field leaf-major: FP64 form / all other forms
+    hm::DevBuf SU, SV;      // per-column scales of the 16-bit forms (float, c_total)
+    bool packed[4] = {false, false, false, false};
 
     // workspace
     int32_t max_rhs = 32;
-    hm::DevBuf xg;  // max_rhs x 3 x M doubles (gathered x, cluster order)
-    hm::DevBuf wb;  // max_rhs x w_total doubles
+    hm::DevBuf xg;  // max_rhs x M x 4 doubles (gathered x, cluster order, padded 4-vectors)
+    hm::DevBuf wb;  // max_rhs x w_total doubles (one 4-vector per factor column)
+    hm::DevBuf yn;  // max_rhs x 3 x M doubles (near-field part of y, cluster order)
     hm::DevBuf xh, yh;  // device staging for hm_matvec_host (max_rhs x 3M doubles)
 
     // measurement hook (hm_profile_enable / hm_profile_read)
@@ -130,16 +164,19 @@ struct hm_matrix {
 };
 
 namespace hm {
-// workspace of one product: gathered x (nrhs x 3 x M) and the far-field w
-// vectors (nrhs x w_total), both in the form's accumulation type
+// workspace of one product: gathered x (nrhs x M x 4), the far-field w
+// vectors (nrhs x c_total x 4) and the near-field part of y (nrhs x 3 x M),
+// all in the form's accumulation type
 struct Scratch {
     void* xg;
     void* w;
+    void* yn;
     bool profile;  // record the measurement-hook events
 };
 int matvec_device_scratch(const hm_matrix& H, const double* x, double* y, int32_t nrhs,
                           int64_t ld, int32_t form, cudaStream_t s, const Scratch& scr);
-// bytes of Scratch a product of nrhs vectors in `form` needs (xg 256-aligned, then w)
+// bytes of Scratch a product of nrhs vectors in `form` needs (xg, yn, w; each
+// part 256-byte aligned)
 size_t matvec_scratch_bytes(const hm_matrix& H, int32_t nrhs, int32_t form);
 // record event `which` (0..3) of the current profiled call, if profiling
 void prof_mark(const hm_matrix& H, int which, cudaStream_t s);

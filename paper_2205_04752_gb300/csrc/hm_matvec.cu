@@ -5,16 +5,26 @@
 // blocks of a row are summed into y.  With Eq. (Vh),
 //   y_a(t) += c1 U_Delta (V_Delta^T x_a(s)) + c2 sum_b U_ab (V_ab^T x_b(s)).
 //
+// The product is memory bound: every stored factor and near-field value is
+// read once per product.  The factors are therefore stored in the order the
+// kernels stream them (built once by pack_device):
+//   V  per admissible block, row-major |s| x Cp (all seven kernels' columns
+//      side by side, Cp = sum k rounded up to 8): 16-byte loads along a row;
+//   U  per leaf row cluster tau, one contiguous stream of segments (a segment
+//      is one column of U restricted to the rows of tau, padded to a multiple
+//      of 8) over all admissible blocks t x s with t containing tau;
+//   near field per leaf, one contiguous stream: for each near block and
+//      column j, six segments (V_11, V_12, V_13, V_22, V_23, V_33).
 // Three launches, all stream ordered and deterministic (fixed summation order,
 // no atomics):
-//   1. gather   x (original dof order) -> xg[r][a][p] (cluster order, SoA)
-//   2. far_fwd  one CTA per admissible block: w = coefficient * V^T xg, i.e.
-//               for every kernel and column l the three values that multiply
-//               column l of U for the outputs a = 0, 1, 2
-//   3. leaf     one CTA per leaf row cluster tau: for every row i of tau,
-//               sum over all admissible blocks t x s with t containing tau of
-//               U[i, :] . w(a) plus its near blocks' dense rows, then the
-//               scatter to the original dof order.
+//   1. gather   x (original dof order) -> xg[r][p][a] (cluster order, a padded to 4)
+//   2. fwd      one CTA per admissible block: z = V^T xg, and for every factor
+//               column c the three values w[c][a] that multiply column c of U
+//               for output component a (c1, c2 and the column scales folded in)
+//   3. leaf     one CTA per leaf: its threads split the leaf's U and near
+//               streams into contiguous, equal ranges, accumulate U w and the
+//               dense near rows, sum the ranges in a fixed order and scatter y
+//               to the original dof order.
 // Forms: FP64 (factors, near field, accumulation); FP32; BF16 / FP16 factors
 // with one FP32 scale per factor column (folded into w) and an FP32 near field.
 #include <cuda_bf16.h>
@@ -24,26 +34,97 @@
 #include <cmath>
 
 #include "hm_internal.h"
+#include "hm_stream.cuh"
 
 namespace hm {
 namespace {
 
-template <class T>
-__device__ __forceinline__ float to_f(T v);
-template <>
-__device__ __forceinline__ float to_f<float>(float v) { return v; }
-template <>
-__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
-template <>
-__device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
+constexpr int kThreads = 128;
 
-template <class TF, class TA>
-__device__ __forceinline__ TA load_f(const TF* p)
+// ---------------------------------------------------------------- 16-byte loads
+// load N = 16 / sizeof(T) consecutive values (16-byte aligned, streaming) as TA
+template <class T, class TA>
+struct Vec16;
+
+template <class TA>
+struct Vec16<double, TA> {
+    static constexpr int N = 2;
+    __device__ __forceinline__ static void load(const double* p, TA* o)
+    {
+        double2 v = __ldcs(reinterpret_cast<const double2*>(p));
+        o[0] = (TA)v.x;
+        o[1] = (TA)v.y;
+    }
+};
+template <class TA>
+struct Vec16<float, TA> {
+    static constexpr int N = 4;
+    __device__ __forceinline__ static void load(const float* p, TA* o)
+    {
+        float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+        o[0] = (TA)v.x;
+        o[1] = (TA)v.y;
+        o[2] = (TA)v.z;
+        o[3] = (TA)v.w;
+    }
+};
+template <class TA>
+struct Vec16<__half, TA> {
+    static constexpr int N = 8;
+    __device__ __forceinline__ static void load(const __half* p, TA* o)
+    {
+        uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+        const __half2* h = reinterpret_cast<const __half2*>(&v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float2 f = __half22float2(h[q]);
+            o[2 * q] = (TA)f.x;
+            o[2 * q + 1] = (TA)f.y;
+        }
+    }
+};
+template <class TA>
+struct Vec16<__nv_bfloat16, TA> {
+    static constexpr int N = 8;
+    __device__ __forceinline__ static void load(const __nv_bfloat16* p, TA* o)
+    {
+        uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float2 f = __bfloat1622float2(h[q]);
+            o[2 * q] = (TA)f.x;
+            o[2 * q + 1] = (TA)f.y;
+        }
+    }
+};
+
+// R consecutive values of type T (R * sizeof(T) a multiple of 16)
+template <class T, class TA, int R>
+__device__ __forceinline__ void load_rows(const T* p, TA* o)
 {
-    return (TA)to_f<TF>(*p);
+    constexpr int N = Vec16<T, TA>::N;
+#pragma unroll
+    for (int q = 0; q < R / N; ++q) Vec16<T, TA>::load(p + q * N, o + q * N);
 }
-template <>
-__device__ __forceinline__ double load_f<double, double>(const double* p) { return __ldg(p); }
+
+// x and w are stored as 4-vectors (the 4th entry is zero): one position of x
+// (components 0..2) or one factor column of w (outputs 0..2) per 16 bytes
+// (FP32) or 32 bytes (FP64)
+__device__ __forceinline__ void load3(const float* p, float& a, float& b, float& c)
+{
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a = v.x;
+    b = v.y;
+    c = v.z;
+}
+__device__ __forceinline__ void load3(const double* p, double& a, double& b, double& c)
+{
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    a = v.x;
+    b = v.y;
+    c = p[2];
+}
 
 // kernel -> (p, q) component pair; kernel 0 is V_Delta
 __device__ __forceinline__ void kern_pq(int kern, int& p, int& q)
@@ -60,302 +141,592 @@ __global__ void gather_kernel(int M, int nrhs, const double* __restrict__ x, int
     int r = blockIdx.y;
     if (p >= M || r >= nrhs) return;
     size_t src = (size_t)r * ld + 3 * (size_t)perm[p];
+    TA* d = xg + ((size_t)r * M + p) * 4;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) xg[((size_t)r * 3 + a) * M + p] = (TA)x[src + a];
+    for (int a = 0; a < 3; ++a) d[a] = (TA)x[src + a];
+    d[3] = (TA)0;
 }
 
+// ---------------------------------------------------------------- phase 1
+// w for every factor column c of block `rec` from its reduced z = V^T x
+// (three components), with c1 / c2 and the column scales folded in
 template <class TA>
-__device__ __forceinline__ TA warp_sum(TA v)
+__device__ __forceinline__ void write_w(const FwdRec& rec, int c, const TA* z, const float* __restrict__ SU,
+                                        const float* __restrict__ SV, TA* __restrict__ wr, TA c1, TA c2)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-constexpr int kFwdThreads = 128;
-
-// Phase 1: one CTA per admissible block (largest first); warp w takes the
-// block's factor columns c = w, w + 4, ... (all seven kernels concatenated).
-template <class TF, class TA, int RC>
-__global__ void __launch_bounds__(kFwdThreads) far_fwd_kernel(
-    const int32_t* __restrict__ order, const Blk* __restrict__ blks, const int32_t* __restrict__ rank,
-    const int64_t* __restrict__ voff, const int64_t* __restrict__ woff,
-    const int64_t* __restrict__ coff, const TF* __restrict__ V, const float* __restrict__ SU,
-    const float* __restrict__ SV, const TA* __restrict__ xg, TA* __restrict__ w, int M, int nrhs,
-    int64_t wtot, TA c1, TA c2)
-{
-    const int b = order[blockIdx.x];
-    const Blk bk = blks[b];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nw = blockDim.x >> 5;
-    int kk[7];
-    int ctot = 0;
-#pragma unroll
-    for (int k = 0; k < 7; ++k) {
-        kk[k] = rank[(size_t)b * 7 + k];
-        ctot += kk[k];
+    int kern = 0, l = c;
+    for (;;) {
+        const int k = (int)((rec.kpack >> (8 * kern)) & 0xff);
+        if (l < k) break;
+        l -= k;
+        ++kern;
     }
-    for (int c = warp; c < ctot; c += nw) {
-        int kern = 0, l = c;
-        while (l >= kk[kern]) {
-            l -= kk[kern];
-            ++kern;
-        }
-        const size_t q = (size_t)b * 7 + kern;
-        const int k = kk[kern];
-        const TF* v = V + voff[q] + (size_t)l * bk.n;
-        const TA sv = SV ? (TA)SV[coff[q] + l] : (TA)1;
-        const TA su = SU ? (TA)SU[coff[q] + l] : (TA)1;
+    const int64_t col = (int64_t)rec.col0 + c;
+    const TA sv = SV ? (TA)SV[col] : (TA)1;
+    const TA su = SU ? (TA)SU[col] : (TA)1;
+    TA o[3];
+    if (kern == 0) {
+        const TA f = c1 * su * sv;
+        o[0] = f * z[0];
+        o[1] = f * z[1];
+        o[2] = f * z[2];
+    } else {
         int p, pq;
         kern_pq(kern, p, pq);
-        for (int r0 = 0; r0 < nrhs; r0 += RC) {
-            TA z[RC][3];
+        const TA f = c2 * su * sv;
+        o[0] = o[1] = o[2] = (TA)0;
+        o[p] = f * z[pq];
+        if (p != pq) o[pq] = f * z[p];
+    }
+    wr[col * 4] = o[0];
+    wr[col * 4 + 1] = o[1];
+    wr[col * 4 + 2] = o[2];
+    wr[col * 4 + 3] = (TA)0;
+}
+
+// Small blocks (|s| <= 128): one warp per block.  Lane (q, g): column vector
+// q (VEC consecutive columns of the row-major V), rows g, g + G, ...
+template <class TF, class TA>
+__global__ void __launch_bounds__(kThreads) fwd_small_kernel(
+    const FwdRec* __restrict__ recs, int nrec, const TF* __restrict__ Vr, const float* __restrict__ SU,
+    const float* __restrict__ SV, const TA* __restrict__ xg, TA* __restrict__ w, int M, int64_t ctot,
+    TA c1, TA c2)
+{
+    constexpr int VEC = Vec16<TF, TA>::N;
+    __shared__ TA red[kThreads / 32][32 * VEC * 3];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.y;
+    const int bi = blockIdx.x * (kThreads / 32) + warp;
+    if (bi >= nrec) return;
+    TA* wr = w + (size_t)r * 4 * ctot;
+    TA* rw = red[warp];
+    const FwdRec rec = recs[bi];
+    const int Cp = (rec.C + 7) & ~7, Q = Cp / VEC;
+    const TF* Vb = Vr + rec.vbase;
+    const TA* x0 = xg + ((size_t)r * M + rec.s0) * 4;
+    for (int cq0 = 0; cq0 < Q; cq0 += 32) {
+        const int QT = min(Q - cq0, 32), G = 32 / QT;
+        const int q = lane % QT, g = lane / QT;
+        TA acc[VEC][3];
 #pragma unroll
-            for (int rr = 0; rr < RC; ++rr) z[rr][0] = z[rr][1] = z[rr][2] = (TA)0;
-            for (int j = lane; j < bk.n; j += 32) {
-                TA vj = load_f<TF, TA>(v + j);
+        for (int e = 0; e < VEC; ++e) acc[e][0] = acc[e][1] = acc[e][2] = (TA)0;
+        if (g < G) {
+            const TF* vp = Vb + (size_t)(cq0 + q) * VEC;
+#pragma unroll 4
+            for (int j = g; j < rec.n; j += G) {
+                TA v[VEC];
+                Vec16<TF, TA>::load(vp + (size_t)j * Cp, v);
+                TA xa, xb, xc;
+                load3(x0 + (size_t)j * 4, xa, xb, xc);
 #pragma unroll
-                for (int rr = 0; rr < RC; ++rr) {
-                    if (r0 + rr < nrhs) {
-                        const TA* xr = xg + (size_t)(r0 + rr) * 3 * M + bk.s0 + j;
-                        z[rr][0] += vj * xr[0];
-                        z[rr][1] += vj * xr[M];
-                        z[rr][2] += vj * xr[2 * (size_t)M];
-                    }
+                for (int e = 0; e < VEC; ++e) {
+                    acc[e][0] += v[e] * xa;
+                    acc[e][1] += v[e] * xb;
+                    acc[e][2] += v[e] * xc;
                 }
             }
 #pragma unroll
-            for (int rr = 0; rr < RC; ++rr) {
-                if (r0 + rr >= nrhs) break;
-                TA z0 = warp_sum(z[rr][0]) * sv, z1 = warp_sum(z[rr][1]) * sv,
-                   z2 = warp_sum(z[rr][2]) * sv;
-                if (lane == 0) {
-                    TA* wo = w + (size_t)(r0 + rr) * wtot + woff[q];
-                    TA o[3];
-                    if (kern == 0) {
-                        o[0] = c1 * su * z0;
-                        o[1] = c1 * su * z1;
-                        o[2] = c1 * su * z2;
-                    } else {
-                        TA zz[3] = {z0, z1, z2};
-                        o[0] = o[1] = o[2] = (TA)0;
-                        o[p] = c2 * su * zz[pq];
-                        if (p != pq) o[pq] = c2 * su * zz[p];
-                    }
-                    wo[l] = o[0];
-                    wo[k + l] = o[1];
-                    wo[2 * k + l] = o[2];
+            for (int e = 0; e < VEC; ++e)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) rw[((g * QT + q) * VEC + e) * 3 + a] = acc[e][a];
+        }
+        __syncwarp();
+        if (g == 0) {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                const int c = (cq0 + q) * VEC + e;
+                if (c < rec.C) {
+                    TA z[3] = {(TA)0, (TA)0, (TA)0};
+                    for (int gg = 0; gg < G; ++gg)
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) z[a] += rw[((gg * QT + q) * VEC + e) * 3 + a];
+                    write_w<TA>(rec, c, z, SU, SV, wr, c1, c2);
                 }
             }
         }
+        __syncwarp();
     }
 }
 
-// Phase 2 (+ near field): one CTA per leaf.  Thread (i, h): row i of the leaf,
-// group h of H = blockDim / |tau| groups; the groups split the factor columns
-// and near-block columns round robin and are summed at the end.
-template <class TF, class TN, class TA, int RC>
-__global__ void leaf_kernel(const int32_t* __restrict__ leaf, const int32_t* __restrict__ far_ptr,
-                            const FarItem* __restrict__ far_items, const int32_t* __restrict__ near_ptr,
-                            const int32_t* __restrict__ near_items, const Blk* __restrict__ adm,
-                            const Blk* __restrict__ nearb, const int32_t* __restrict__ rank,
-                            const int64_t* __restrict__ uoff, const int64_t* __restrict__ woff,
-                            const int64_t* __restrict__ noff, const TF* __restrict__ U,
-                            const TN* __restrict__ N, const TA* __restrict__ xg,
-                            const TA* __restrict__ w, const int32_t* __restrict__ perm,
-                            double* __restrict__ y, int64_t ld, int M, int nrhs, int64_t wtot,
-                            TA c1, TA c2)
+// Larger blocks: one CTA per block.  Thread (q, g) as above with G row
+// groups over the whole CTA, reduced through shared memory.
+template <class TF, class TA>
+__global__ void __launch_bounds__(kThreads) fwd_big_kernel(
+    const FwdRec* __restrict__ recs, const TF* __restrict__ Vr, const float* __restrict__ SU,
+    const float* __restrict__ SV, const TA* __restrict__ xg, TA* __restrict__ w, int M, int64_t ctot,
+    TA c1, TA c2)
 {
-    extern __shared__ unsigned char smem_raw[];
-    TA* red = reinterpret_cast<TA*>(smem_raw);
-    const int lf = blockIdx.x;
+    constexpr int VEC = Vec16<TF, TA>::N;
+    __shared__ TA red[kThreads * VEC * 3];
+    const FwdRec rec = recs[blockIdx.x];
+    const int r = blockIdx.y;
+    const int Cp = (rec.C + 7) & ~7, Q = Cp / VEC;
+    const TF* Vb = Vr + rec.vbase;
+    const TA* x0 = xg + ((size_t)r * M + rec.s0) * 4;
+    TA* wr = w + (size_t)r * 4 * ctot;
+    const int tid = threadIdx.x;
+    for (int cq0 = 0; cq0 < Q; cq0 += kThreads) {
+        const int QT = min(Q - cq0, kThreads);
+        const int G = kThreads / QT;
+        const int q = tid % QT, g = tid / QT;
+        TA acc[VEC][3];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) acc[e][0] = acc[e][1] = acc[e][2] = (TA)0;
+        if (g < G) {
+            const TF* vp = Vb + (size_t)(cq0 + q) * VEC;
+#pragma unroll 4
+            for (int j = g; j < rec.n; j += G) {
+                TA v[VEC];
+                Vec16<TF, TA>::load(vp + (size_t)j * Cp, v);
+                TA xa, xb, xc;
+                load3(x0 + (size_t)j * 4, xa, xb, xc);
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    acc[e][0] += v[e] * xa;
+                    acc[e][1] += v[e] * xb;
+                    acc[e][2] += v[e] * xc;
+                }
+            }
+        }
+        __syncthreads();
+        if (g < G) {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) red[((g * QT + q) * VEC + e) * 3 + a] = acc[e][a];
+        }
+        __syncthreads();
+        for (int idx = tid; idx < QT * VEC; idx += kThreads) {
+            const int c = cq0 * VEC + idx;
+            if (c >= rec.C) continue;
+            TA z[3] = {(TA)0, (TA)0, (TA)0};
+            for (int gg = 0; gg < G; ++gg)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) z[a] += red[(gg * QT * VEC + idx) * 3 + a];
+            write_w<TA>(rec, c, z, SU, SV, wr, c1, c2);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- phase 2
+// Rows of a leaf are handled in chunks of at most kThreads row blocks of R
+// rows (one chunk unless the leaf has more than kThreads * R rows).  Thread
+// (p, h): rows of row block p, group h of H = kThreads / P; group h takes the
+// contiguous range [S h / H, S (h+1) / H) of the leaf's S stream entries.
+
+// near field: one CTA per (leaf, rhs); yn[r][a][cluster position] =
+// sum over near blocks of the dense 3 x 3 Kelvin blocks c1 delta V_Delta + c2 V_ab
+template <class TN, class TA>
+__global__ void __launch_bounds__(kThreads) near_leaf_kernel(
+    const int32_t* __restrict__ leaf, const int64_t* __restrict__ ln_base,
+    const int32_t* __restrict__ ln_ptr, const LeafNearItem* __restrict__ ln_items,
+    const TN* __restrict__ Nl, const TA* __restrict__ xg, TA* __restrict__ yn, int M, TA c1, TA c2)
+{
+    constexpr int R = Vec16<TN, TA>::N;
+    __shared__ TA red[kThreads * R * 3];
+    const int lf = blockIdx.x, r = blockIdx.y;
     const int t0 = leaf[2 * lf], mt = leaf[2 * lf + 1];
-    const int H = blockDim.x / mt;
-    const int i = threadIdx.x % mt, h = threadIdx.x / mt;
-    const bool active = h < H;
-    const int f0 = far_ptr[lf], f1 = far_ptr[lf + 1];
-    const int n0 = near_ptr[lf], n1 = near_ptr[lf + 1];
-    for (int r0 = 0; r0 < nrhs; r0 += RC) {
-        const int rc = min(RC, nrhs - r0);
-        TA acc[RC][3];
+    const int mp = (mt + 7) & ~7;
+    const int Ptot = mp / R;
+    const int tid = threadIdx.x;
+    const int j0 = ln_ptr[lf], j1 = ln_ptr[lf + 1];
+    const int Sn = ln_items[j1 - 1].col_start;
+    const TA* xr = xg + (size_t)r * 4 * M;
+    for (int pb0 = 0; pb0 < Ptot; pb0 += kThreads) {
+        const int P = min(Ptot - pb0, kThreads);
+        const int H = kThreads / P;
+        const int p = tid % P, h = tid / P;
+        const int row0 = (pb0 + p) * R;
+        TA acc[R][3];
 #pragma unroll
-        for (int rr = 0; rr < RC; ++rr) acc[rr][0] = acc[rr][1] = acc[rr][2] = (TA)0;
-        if (active) {
-            int rot = 0;  // global column counter mod H
-            for (int it = f0; it < f1; ++it) {
-                const FarItem fi = far_items[it];
-                const int m = adm[fi.b].m;
-#pragma unroll 1
-                for (int kern = 0; kern < 7; ++kern) {
-                    const size_t q = (size_t)fi.b * 7 + kern;
-                    const int k = rank[q];
-                    if (k == 0) continue;
-                    const TF* ub = U + uoff[q] + fi.off + i;
-                    const TA* wb = w + woff[q];
-                    int l = h - rot;
-                    l = ((l % H) + H) % H;
-                    for (; l < k; l += H) {
-                        const TA u = load_f<TF, TA>(ub + (size_t)l * m);
+        for (int e = 0; e < R; ++e) acc[e][0] = acc[e][1] = acc[e][2] = (TA)0;
+        if (h < H) {
+            const int n0 = (int)(((int64_t)Sn * h) / H), n1 = (int)(((int64_t)Sn * (h + 1)) / H);
+            if (n0 < n1) {
+                int lo = j0, hi = j1 - 2;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (ln_items[mid].col_start <= n0) lo = mid;
+                    else hi = mid - 1;
+                }
+                int q = lo;
+                int nxt = ln_items[q + 1].col_start;
+                int sbase = ln_items[q].s0 - ln_items[q].col_start;
+                const TN* base = Nl + ln_base[lf] + row0;
+                for (int g = n0; g < n1; ++g) {
+                    while (g >= nxt) {
+                        ++q;
+                        nxt = ln_items[q + 1].col_start;
+                        sbase = ln_items[q].s0 - ln_items[q].col_start;
+                    }
+                    const int sj = sbase + g;
+                    TA x0, x1, x2;
+                    load3(xr + (size_t)sj * 4, x0, x1, x2);
+                    const TN* e0 = base + (size_t)g * 6 * mp;
+                    TA v11[R], v12[R], v13[R], v22[R], v23[R], v33[R];
+                    Vec16<TN, TA>::load(e0, v11);
+                    Vec16<TN, TA>::load(e0 + mp, v12);
+                    Vec16<TN, TA>::load(e0 + 2 * mp, v13);
+                    Vec16<TN, TA>::load(e0 + 3 * mp, v22);
+                    Vec16<TN, TA>::load(e0 + 4 * mp, v23);
+                    Vec16<TN, TA>::load(e0 + 5 * mp, v33);
 #pragma unroll
-                        for (int rr = 0; rr < RC; ++rr) {
-                            if (rr < rc) {
-                                const TA* wr = wb + (size_t)(r0 + rr) * wtot;
-                                acc[rr][0] += u * wr[l];
-                                acc[rr][1] += u * wr[k + l];
-                                acc[rr][2] += u * wr[2 * k + l];
+                    for (int e = 0; e < R; ++e) {
+                        const TA vd = c1 * (v11[e] + v22[e] + v33[e]);
+                        acc[e][0] += vd * x0 + c2 * (v11[e] * x0 + v12[e] * x1 + v13[e] * x2);
+                        acc[e][1] += vd * x1 + c2 * (v12[e] * x0 + v22[e] * x1 + v23[e] * x2);
+                        acc[e][2] += vd * x2 + c2 * (v13[e] * x0 + v23[e] * x1 + v33[e] * x2);
+                    }
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < R; ++e)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) red[((h * P + p) * R + e) * 3 + a] = acc[e][a];
+        }
+        __syncthreads();
+        const int rows = min(P * R, mt - pb0 * R);
+        for (int idx = tid; idx < rows * 3; idx += kThreads) {
+            const int i = idx / 3, a = idx - 3 * i;
+            TA sum = (TA)0;
+            for (int g = 0; g < H; ++g) sum += red[((g * P) * R + i) * 3 + a];
+            yn[((size_t)r * 3 + a) * M + t0 + pb0 * R + i] = sum;
+        }
+        __syncthreads();
+    }
+}
+
+// far field: one CTA per (leaf, rhs); y = sum over the leaf's U segments of
+// U_seg[rows] * w[col(seg)] plus the near-field part yn, scattered to the
+// original dof order
+template <class TF, class TA>
+__global__ void __launch_bounds__(kThreads) far_leaf_kernel(
+    const int32_t* __restrict__ leaf, const int64_t* __restrict__ lf_base,
+    const int32_t* __restrict__ lf_ptr, const LeafFarItem* __restrict__ lf_items,
+    const TF* __restrict__ Ul, const TA* __restrict__ w, const TA* __restrict__ yn,
+    const int32_t* __restrict__ perm, double* __restrict__ y, int64_t ld, int M, int64_t ctot)
+{
+    constexpr int R = Vec16<TF, TA>::N;
+    constexpr int U4 = 4;  // segments in flight per thread
+    __shared__ TA red[kThreads * R * 3];
+    const int lf = blockIdx.x, r = blockIdx.y;
+    const int t0 = leaf[2 * lf], mt = leaf[2 * lf + 1];
+    const int mp = (mt + 7) & ~7;
+    const int Ptot = mp / R;
+    const int tid = threadIdx.x;
+    const int i0 = lf_ptr[lf], i1 = lf_ptr[lf + 1];
+    const int S = lf_items[i1 - 1].seg_start;
+    const TA* wr = w + (size_t)r * 4 * ctot;
+    for (int pb0 = 0; pb0 < Ptot; pb0 += kThreads) {
+        const int P = min(Ptot - pb0, kThreads);
+        const int H = kThreads / P;
+        const int p = tid % P, h = tid / P;
+        const int row0 = (pb0 + p) * R;
+        TA acc[R][3];
+#pragma unroll
+        for (int e = 0; e < R; ++e) acc[e][0] = acc[e][1] = acc[e][2] = (TA)0;
+        if (h < H) {
+            const int g0 = (int)(((int64_t)S * h) / H), g1 = (int)(((int64_t)S * (h + 1)) / H);
+            if (g0 < g1) {
+                int lo = i0, hi = i1 - 2;  // item containing g0: last with seg_start <= g0
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (lf_items[mid].seg_start <= g0) lo = mid;
+                    else hi = mid - 1;
+                }
+                int q = lo;
+                int nxt = lf_items[q + 1].seg_start;
+                int cbase = lf_items[q].col - lf_items[q].seg_start;
+                const TF* base = Ul + lf_base[lf] + row0;
+                for (int g = g0; g < g1; g += U4) {
+                    TA u[U4][R];
+                    int col[U4];
+#pragma unroll
+                    for (int t = 0; t < U4; ++t) {
+                        if (g + t < g1) {
+                            while (g + t >= nxt) {
+                                ++q;
+                                nxt = lf_items[q + 1].seg_start;
+                                cbase = lf_items[q].col - lf_items[q].seg_start;
+                            }
+                            col[t] = cbase + g + t;
+                            Vec16<TF, TA>::load(base + (size_t)(g + t) * mp, u[t]);
+                        }
+                    }
+#pragma unroll
+                    for (int t = 0; t < U4; ++t) {
+                        if (g + t < g1) {
+                            TA w0, w1, w2;
+                            load3(wr + (size_t)col[t] * 4, w0, w1, w2);
+#pragma unroll
+                            for (int e = 0; e < R; ++e) {
+                                acc[e][0] += u[t][e] * w0;
+                                acc[e][1] += u[t][e] * w1;
+                                acc[e][2] += u[t][e] * w2;
                             }
                         }
                     }
-                    rot = (rot + k) % H;
                 }
             }
-            for (int it = n0; it < n1; ++it) {
-                const int nb = near_items[it];
-                const Blk bk = nearb[nb];
-                const int n = bk.n;
-                const size_t pairs = (size_t)mt * n;
-                const TN* Nb = N + noff[nb] + i;
-                int j = h - rot;
-                j = ((j % H) + H) % H;
-                for (; j < n; j += H) {
-                    const TN* e = Nb + (size_t)j * mt;
-                    const TA v11 = (TA)e[0], v12 = (TA)e[pairs], v13 = (TA)e[2 * pairs];
-                    const TA v22 = (TA)e[3 * pairs], v23 = (TA)e[4 * pairs], v33 = (TA)e[5 * pairs];
-                    const TA vd = c1 * (v11 + v22 + v33);
 #pragma unroll
-                    for (int rr = 0; rr < RC; ++rr) {
-                        if (rr < rc) {
-                            const TA* xr = xg + (size_t)(r0 + rr) * 3 * M + bk.s0 + j;
-                            const TA x0 = xr[0], x1 = xr[M], x2 = xr[2 * (size_t)M];
-                            acc[rr][0] += vd * x0 + c2 * (v11 * x0 + v12 * x1 + v13 * x2);
-                            acc[rr][1] += vd * x1 + c2 * (v12 * x0 + v22 * x1 + v23 * x2);
-                            acc[rr][2] += vd * x2 + c2 * (v13 * x0 + v23 * x1 + v33 * x2);
-                        }
-                    }
-                }
-                rot = (rot + n) % H;
-            }
-        }
-        // sum the H partial results of every row in a fixed order
-        __syncthreads();
-        if (active) {
+            for (int e = 0; e < R; ++e)
 #pragma unroll
-            for (int rr = 0; rr < RC; ++rr)
-#pragma unroll
-                for (int a = 0; a < 3; ++a) red[((size_t)(rr * 3 + a) * H + h) * mt + i] = acc[rr][a];
+                for (int a = 0; a < 3; ++a) red[((h * P + p) * R + e) * 3 + a] = acc[e][a];
         }
         __syncthreads();
-        if (active && h == 0) {
-            const size_t dst = 3 * (size_t)perm[t0 + i];
-            for (int rr = 0; rr < rc; ++rr)
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    TA s = (TA)0;
-                    for (int g = 0; g < H; ++g) s += red[((size_t)(rr * 3 + a) * H + g) * mt + i];
-                    y[(size_t)(r0 + rr) * ld + dst + a] = (double)s;
-                }
+        const int rows = min(P * R, mt - pb0 * R);
+        for (int idx = tid; idx < rows * 3; idx += kThreads) {
+            const int i = idx / 3, a = idx - 3 * i;
+            const int pos = t0 + pb0 * R + i;
+            TA sum = (TA)0;
+            for (int g = 0; g < H; ++g) sum += red[((g * P) * R + i) * 3 + a];
+            sum += yn[((size_t)r * 3 + a) * M + pos];
+            y[(size_t)r * ld + 3 * (size_t)perm[pos] + a] = (double)sum;
         }
+        __syncthreads();
     }
 }
 
 // ---------------------------------------------------------------- packing
-template <class TO>
-__global__ void convert_kernel(const double* __restrict__ src, TO* __restrict__ dst, size_t n)
-{
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
-         e += (size_t)gridDim.x * blockDim.x)
-        dst[e] = (TO)src[e];
-}
-
-template <class T16>
-__device__ __forceinline__ T16 from_f(float v);
+template <class T>
+__device__ __forceinline__ T cvt(double v);
 template <>
-__device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+__device__ __forceinline__ double cvt<double>(double v) { return v; }
 template <>
-__device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
+__device__ __forceinline__ float cvt<float>(double v) { return (float)v; }
+template <>
+__device__ __forceinline__ __half cvt<__half>(double v) { return __float2half_rn((float)v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
 
-// 16-bit factors with one scale per column: column / max|column|
-template <class T16>
-__global__ void pack16_kernel(int ntask, const Blk* __restrict__ blks, const int32_t* __restrict__ rank,
-                              const int64_t* __restrict__ off, const int64_t* __restrict__ coff,
-                              int rows_is_m, const double* __restrict__ src, T16* __restrict__ dst,
-                              float* __restrict__ scale)
+// per-column scale of the 16-bit forms: max |column| (1 for a zero column)
+__global__ void colscale_kernel(int ntask, const Blk* __restrict__ blks, const int32_t* __restrict__ rank,
+                                const int64_t* __restrict__ uoff, const int64_t* __restrict__ voff,
+                                const int64_t* __restrict__ coff, const double* __restrict__ U,
+                                const double* __restrict__ V, float* __restrict__ SU,
+                                float* __restrict__ SV)
 {
     const int q = blockIdx.x;
     if (q >= ntask) return;
     const int k = rank[q];
     const Blk bk = blks[q / 7];
-    const int len = rows_is_m ? bk.m : bk.n;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int l = warp; l < k; l += nw) {
-        const double* c = src + off[q] + (size_t)l * len;
+    for (int task = warp; task < 2 * k; task += nw) {
+        const int l = task % k;
+        const bool isu = task < k;
+        const int len = isu ? bk.m : bk.n;
+        const double* c = (isu ? U + uoff[q] : V + voff[q]) + (size_t)l * len;
         double mx = 0.0;
         for (int e = lane; e < len; e += 32) mx = fmax(mx, fabs(c[e]));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        const float sc = mx > 0.0 ? (float)mx : 1.0f;
-        const double inv = 1.0 / (double)sc;
-        T16* d = dst + off[q] + (size_t)l * len;
-        for (int e = lane; e < len; e += 32) d[e] = from_f<T16>((float)(c[e] * inv));
-        if (lane == 0) scale[coff[q] + l] = sc;
+        if (lane == 0) (isu ? SU : SV)[coff[q] + l] = mx > 0.0 ? (float)mx : 1.0f;
+    }
+}
+
+// U leaf-major: one CTA per leaf
+template <class T>
+__global__ void pack_ul_kernel(const int32_t* __restrict__ leaf, const int64_t* __restrict__ lf_base,
+                               const int32_t* __restrict__ lf_ptr, const LeafFarItem* __restrict__ items,
+                               const PackSrc* __restrict__ src, const double* __restrict__ U,
+                               const float* __restrict__ SU, T* __restrict__ Ul)
+{
+    const int lf = blockIdx.x;
+    const int mt = leaf[2 * lf + 1], mp = (mt + 7) & ~7;
+    T* dst = Ul + lf_base[lf];
+    for (int q = lf_ptr[lf]; q < lf_ptr[lf + 1] - 1; ++q) {
+        const PackSrc ps = src[q];
+        const LeafFarItem it = items[q];
+        const int n = ps.k * mp;
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+            const int l = e / mp, i = e - l * mp;
+            double v = 0.0;
+            if (i < mt) {
+                v = U[ps.src + (size_t)l * ps.ld + i];
+                if (SU) v /= (double)SU[it.col + l];
+            }
+            dst[(size_t)(it.seg_start + l) * mp + i] = cvt<T>(v);
+        }
+    }
+}
+
+// V row-major per block: one CTA per block
+template <class T>
+__global__ void pack_vr_kernel(const Blk* __restrict__ blks, const int32_t* __restrict__ rank,
+                               const int64_t* __restrict__ voff, const int64_t* __restrict__ coff,
+                               const int64_t* __restrict__ vb_base, const double* __restrict__ V,
+                               const float* __restrict__ SV, T* __restrict__ Vr)
+{
+    const int b = blockIdx.x;
+    const Blk bk = blks[b];
+    int kk[7], kp[8];
+    kp[0] = 0;
+    for (int k = 0; k < 7; ++k) {
+        kk[k] = rank[(size_t)b * 7 + k];
+        kp[k + 1] = kp[k] + kk[k];
+    }
+    const int C = kp[7], Cp = (C + 7) & ~7;
+    T* dst = Vr + vb_base[b];
+    const int64_t col0 = coff[(size_t)b * 7];
+    for (int64_t e = threadIdx.x; e < (int64_t)bk.n * Cp; e += blockDim.x) {
+        const int j = (int)(e / Cp), c = (int)(e - (int64_t)j * Cp);
+        double v = 0.0;
+        if (c < C) {
+            int kern = 0;
+            while (c >= kp[kern + 1]) ++kern;
+            const int l = c - kp[kern];
+            v = V[voff[(size_t)b * 7 + kern] + (size_t)l * bk.n + j];
+            if (SV) v /= (double)SV[col0 + c];
+        }
+        dst[e] = cvt<T>(v);
+    }
+}
+
+// near field leaf-major: one CTA per leaf
+template <class T>
+__global__ void pack_nl_kernel(const int32_t* __restrict__ leaf, const int64_t* __restrict__ ln_base,
+                               const int32_t* __restrict__ ln_ptr, const LeafNearItem* __restrict__ items,
+                               const NearSrc* __restrict__ src, const double* __restrict__ N,
+                               T* __restrict__ Nl)
+{
+    const int lf = blockIdx.x;
+    const int mt = leaf[2 * lf + 1], mp = (mt + 7) & ~7;
+    T* dst = Nl + ln_base[lf];
+    for (int q = ln_ptr[lf]; q < ln_ptr[lf + 1] - 1; ++q) {
+        const NearSrc ns = src[q];
+        const int c0 = items[q].col_start;
+        const int n = ns.n * 6 * mp;
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+            const int jv = e / mp, i = e - jv * mp;
+            const int j = jv / 6, v = jv - 6 * j;
+            double val = 0.0;
+            if (i < mt) val = N[ns.src + ((size_t)v * ns.n + j) * mt + i];
+            dst[((size_t)(c0 + j) * 6 + v) * mp + i] = cvt<T>(val);
+        }
     }
 }
 
 int dalloc(hm_matrix& H, DevBuf& d, size_t bytes)
 {
-    d.bytes = bytes;
-    d.p = H.alloc.alloc(bytes);
-    if (!d.p) return fail(HM_ENOMEM, "device allocation of %zu bytes failed", bytes);
+    d.bytes = std::max<size_t>(bytes, 256);
+    d.p = H.alloc.alloc(d.bytes);
+    if (!d.p) return fail(HM_ENOMEM, "device allocation of %zu bytes failed", d.bytes);
     return HM_OK;
 }
 
 template <class TF, class TN, class TA>
-int run_matvec(const hm_matrix& H, const TF* U, const TF* V, const TN* N, const float* SU,
-               const float* SV, const double* x, double* y, int nrhs, int64_t ld, cudaStream_t s,
-               const Scratch& scr)
+int run_matvec(const hm_matrix& H, int form, const TN* N, const float* SU, const float* SV,
+               const double* x, double* y, int nrhs, int64_t ld, cudaStream_t s, const Scratch& scr)
 {
     const int M = (int)H.M;
     TA* xg = static_cast<TA*>(scr.xg);
     TA* w = static_cast<TA*>(scr.w);
+    TA* yn = static_cast<TA*>(scr.yn);
+    const TF* Ul = H.Ul[form].as<TF>();
+    const TF* Vr = H.Vr[form].as<TF>();
     const TA c1 = (TA)((1.0 + H.nu) * (3.0 - 4.0 * H.nu) / (2.0 * H.E * (1.0 - H.nu)));
     const TA c2 = (TA)((1.0 + H.nu) / (2.0 * H.E * (1.0 - H.nu)));
-    dim3 gg((unsigned)((M + 255) / 256), (unsigned)nrhs);
+    const unsigned nr = (unsigned)nrhs;
+    dim3 gg((unsigned)((M + 255) / 256), nr);
     if (scr.profile) prof_mark(H, 0, s);
     gather_kernel<TA><<<gg, 256, 0, s>>>(M, nrhs, x, ld, H.d_perm.as<int32_t>(), xg);
     HM_CUDA(cudaGetLastError());
-    const bool multi = nrhs > 1;
     if (scr.profile) prof_mark(H, 1, s);
-    if (H.nadm > 0) {
-        if (multi)
-            far_fwd_kernel<TF, TA, 4><<<(unsigned)H.nadm, kFwdThreads, 0, s>>>(
-                H.d_p1_order.as<int32_t>(), H.d_adm.as<Blk>(), H.d_rank.as<int32_t>(),
-                H.d_voff.as<int64_t>(), H.d_woff.as<int64_t>(), H.d_coff.as<int64_t>(), V, SU, SV, xg, w,
-                M, nrhs, H.w_total, c1, c2);
-        else
-            far_fwd_kernel<TF, TA, 1><<<(unsigned)H.nadm, kFwdThreads, 0, s>>>(
-                H.d_p1_order.as<int32_t>(), H.d_adm.as<Blk>(), H.d_rank.as<int32_t>(),
-                H.d_voff.as<int64_t>(), H.d_woff.as<int64_t>(), H.d_coff.as<int64_t>(), V, SU, SV, xg, w,
-                M, nrhs, H.w_total, c1, c2);
+    // the streamed per-leaf kernel handles leaves of up to kConsumers * R rows
+    constexpr int Rs = stream::Smem16<TF, TA>::N;
+    const bool streamed = ((H.max_leaf + 7) & ~7) / Rs <= stream::kConsumers;
+    if (!streamed) {
+        // fork: the near field on the side stream, concurrently with the forward pass
+        HM_CUDA(cudaEventRecord(H.ev_fork, s));
+        HM_CUDA(cudaStreamWaitEvent(H.side, H.ev_fork, 0));
+        near_leaf_kernel<TN, TA><<<dim3((unsigned)H.nleaves, nr), kThreads, 0, H.side>>>(
+            H.d_leaf.as<int32_t>(), H.d_ln_base.as<int64_t>(), H.d_ln_ptr.as<int32_t>(),
+            H.d_ln_items.as<LeafNearItem>(), N, xg, yn, M, c1, c2);
+        HM_CUDA(cudaGetLastError());
+        HM_CUDA(cudaEventRecord(H.ev_join, H.side));
+    }
+    if (H.n_fwd_big > 0) {
+        fwd_big_kernel<TF, TA><<<dim3((unsigned)H.n_fwd_big, nr), kThreads, 0, s>>>(
+            H.d_fwd_big.as<FwdRec>(), Vr, SU, SV, xg, w, M, H.c_total, c1, c2);
+        HM_CUDA(cudaGetLastError());
+    }
+    if (H.n_fwd_small > 0) {
+        const unsigned nb = (unsigned)((H.n_fwd_small + kThreads / 32 - 1) / (kThreads / 32));
+        fwd_small_kernel<TF, TA><<<dim3(nb, nr), kThreads, 0, s>>>(
+            H.d_fwd_small.as<FwdRec>(), (int)H.n_fwd_small, Vr, SU, SV, xg, w, M, H.c_total, c1, c2);
         HM_CUDA(cudaGetLastError());
     }
     if (scr.profile) prof_mark(H, 2, s);
-    int bdim = H.max_leaf <= 128 ? 128 : ((H.max_leaf + 31) / 32) * 32;
-    const int RCm = multi ? 4 : 1;
-    size_t smem = (size_t)RCm * 3 * bdim * sizeof(TA);
-    if (multi)
-        leaf_kernel<TF, TN, TA, 4><<<(unsigned)H.nleaves, bdim, smem, s>>>(
-            H.d_leaf.as<int32_t>(), H.d_far_ptr.as<int32_t>(), H.d_far_items.as<FarItem>(),
-            H.d_near_ptr.as<int32_t>(), H.d_near_items.as<int32_t>(), H.d_adm.as<Blk>(),
-            H.d_near.as<Blk>(), H.d_rank.as<int32_t>(), H.d_uoff.as<int64_t>(), H.d_woff.as<int64_t>(),
-            H.d_noff.as<int64_t>(), U, N, xg, w, H.d_perm.as<int32_t>(), y, ld, M, nrhs, H.w_total, c1, c2);
-    else
-        leaf_kernel<TF, TN, TA, 1><<<(unsigned)H.nleaves, bdim, smem, s>>>(
-            H.d_leaf.as<int32_t>(), H.d_far_ptr.as<int32_t>(), H.d_far_items.as<FarItem>(),
-            H.d_near_ptr.as<int32_t>(), H.d_near_items.as<int32_t>(), H.d_adm.as<Blk>(),
-            H.d_near.as<Blk>(), H.d_rank.as<int32_t>(), H.d_uoff.as<int64_t>(), H.d_woff.as<int64_t>(),
-            H.d_noff.as<int64_t>(), U, N, xg, w, H.d_perm.as<int32_t>(), y, ld, M, nrhs, H.w_total, c1, c2);
-    HM_CUDA(cudaGetLastError());
+    if (streamed) {
+        auto kern = stream::leaf_stream_kernel<TF, TN, TA>;
+        const size_t smem = stream::smem_bytes<TA>(Rs);
+        static bool attr_set = false;  // per template instance
+        if (!attr_set) {
+            HM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr_set = true;
+        }
+        int dev = 0, nsm = 0, occ = 0;
+        HM_CUDA(cudaGetDevice(&dev));
+        HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, stream::kThreads, smem));
+        const int64_t ncta = std::min<int64_t>(H.nleaves, (int64_t)nsm * std::max(occ, 1));
+        HM_CUDA(cudaMemsetAsync(H.d_counters.p, 0, (size_t)nrhs * sizeof(int), s));
+        stream::LeafTables tb{H.d_leaf.as<int32_t>(),    H.d_leaf_order.as<int32_t>(),
+                              H.d_lf_base.as<int64_t>(), H.d_lf_ptr.as<int32_t>(),
+                              H.d_lf_items.as<LeafFarItem>(), H.d_ln_base.as<int64_t>(),
+                              H.d_ln_ptr.as<int32_t>(),  H.d_ln_items.as<LeafNearItem>(),
+                              H.d_perm.as<int32_t>()};
+        kern<<<dim3((unsigned)ncta, nr), stream::kThreads, smem, s>>>(
+            (int)H.nleaves, tb, H.d_counters.as<int>(), H.d_err.as<int>(), Ul, N, xg, w, y, ld, M,
+            H.c_total, c1, c2);
+        HM_CUDA(cudaGetLastError());
+    } else {
+        // join, then the far-field product per leaf (adds the near part)
+        HM_CUDA(cudaStreamWaitEvent(s, H.ev_join, 0));
+        far_leaf_kernel<TF, TA><<<dim3((unsigned)H.nleaves, nr), kThreads, 0, s>>>(
+            H.d_leaf.as<int32_t>(), H.d_lf_base.as<int64_t>(), H.d_lf_ptr.as<int32_t>(),
+            H.d_lf_items.as<LeafFarItem>(), Ul, w, yn, H.d_perm.as<int32_t>(), y, ld, M, H.c_total);
+        HM_CUDA(cudaGetLastError());
+    }
     if (scr.profile) prof_mark(H, 3, s);
+    return HM_OK;
+}
+
+template <class T>
+int pack_form(hm_matrix& H, int form, const float* SU, const float* SV, cudaStream_t s)
+{
+    int rc;
+    if ((rc = dalloc(H, H.Ul[form], (size_t)H.ul_total * sizeof(T)))) return rc;
+    if ((rc = dalloc(H, H.Vr[form], (size_t)H.vr_total * sizeof(T)))) return rc;
+    if (H.nleaves > 0) {
+        pack_ul_kernel<T><<<(unsigned)H.nleaves, 256, 0, s>>>(
+            H.d_leaf.as<int32_t>(), H.d_lf_base.as<int64_t>(), H.d_lf_ptr.as<int32_t>(),
+            H.d_lf_items.as<LeafFarItem>(), H.d_lf_src.as<PackSrc>(), H.U64.as<double>(), SU,
+            H.Ul[form].as<T>());
+        HM_CUDA(cudaGetLastError());
+    }
+    if (H.nadm > 0) {
+        pack_vr_kernel<T><<<(unsigned)H.nadm, 256, 0, s>>>(
+            H.d_adm.as<Blk>(), H.d_rank.as<int32_t>(), H.d_voff.as<int64_t>(), H.d_coff.as<int64_t>(),
+            H.d_vb_base.as<int64_t>(), H.V64.as<double>(), SV, H.Vr[form].as<T>());
+        HM_CUDA(cudaGetLastError());
+    }
+    return HM_OK;
+}
+
+template <class T>
+int pack_near(hm_matrix& H, DevBuf& dst, cudaStream_t s)
+{
+    int rc;
+    if ((rc = dalloc(H, dst, (size_t)H.nl_total * sizeof(T)))) return rc;
+    if (H.nleaves > 0) {
+        pack_nl_kernel<T><<<(unsigned)H.nleaves, 256, 0, s>>>(
+            H.d_leaf.as<int32_t>(), H.d_ln_base.as<int64_t>(), H.d_ln_ptr.as<int32_t>(),
+            H.d_ln_items.as<LeafNearItem>(), H.d_ln_src.as<NearSrc>(), H.N64.as<double>(),
+            dst.as<T>());
+        HM_CUDA(cudaGetLastError());
+    }
     return HM_OK;
 }
 
@@ -366,21 +737,18 @@ int matvec_device_scratch(const hm_matrix& H, const double* x, double* y, int32_
 {
     switch (form) {
         case HM_FP64:
-            return run_matvec<double, double, double>(H, H.U64.as<double>(), H.V64.as<double>(),
-                                                      H.N64.as<double>(), nullptr, nullptr, x, y,
-                                                      nrhs, ld, s, scr);
+            return run_matvec<double, double, double>(H, form, H.Nl64.as<double>(), nullptr, nullptr,
+                                                      x, y, nrhs, ld, s, scr);
         case HM_FP32:
-            return run_matvec<float, float, float>(H, H.U32.as<float>(), H.V32.as<float>(),
-                                                   H.N32.as<float>(), nullptr, nullptr, x, y, nrhs,
-                                                   ld, s, scr);
+            return run_matvec<float, float, float>(H, form, H.Nl32.as<float>(), nullptr, nullptr, x,
+                                                   y, nrhs, ld, s, scr);
         case HM_BF16:
-            return run_matvec<__nv_bfloat16, float, float>(
-                H, H.U16b.as<__nv_bfloat16>(), H.V16b.as<__nv_bfloat16>(), H.N32.as<float>(),
-                H.SUb.as<float>(), H.SVb.as<float>(), x, y, nrhs, ld, s, scr);
+            return run_matvec<__nv_bfloat16, float, float>(H, form, H.Nl32.as<float>(),
+                                                           H.SU.as<float>(), H.SV.as<float>(), x, y,
+                                                           nrhs, ld, s, scr);
         case HM_FP16:
-            return run_matvec<__half, float, float>(H, H.U16h.as<__half>(), H.V16h.as<__half>(),
-                                                    H.N32.as<float>(), H.SUh.as<float>(),
-                                                    H.SVh.as<float>(), x, y, nrhs, ld, s, scr);
+            return run_matvec<__half, float, float>(H, form, H.Nl32.as<float>(), H.SU.as<float>(),
+                                                    H.SV.as<float>(), x, y, nrhs, ld, s, scr);
         default:
             return fail(HM_EINVAL, "hm_matvec: unknown form %d", form);
     }
@@ -389,61 +757,51 @@ int matvec_device_scratch(const hm_matrix& H, const double* x, double* y, int32_
 int matvec_device(const hm_matrix& H, const double* x, double* y, int32_t nrhs, int64_t ld,
                   int32_t form, cudaStream_t s)
 {
-    Scratch scr{H.xg.p, H.wb.p, true};
+    Scratch scr{H.xg.p, H.wb.p, H.yn.p, true};
     return matvec_device_scratch(H, x, y, nrhs, ld, form, s, scr);
 }
 
 size_t matvec_scratch_bytes(const hm_matrix& H, int32_t nrhs, int32_t form)
 {
     size_t ta = form == HM_FP64 ? 8 : 4;
-    size_t xg = ((size_t)nrhs * 3 * (size_t)H.M * ta + 255) & ~(size_t)255;
+    size_t vec = ((size_t)nrhs * 4 * (size_t)H.M * ta + 255) & ~(size_t)255;
     size_t w = (size_t)nrhs * (size_t)std::max<int64_t>(H.w_total, 1) * ta;
-    return xg + w;
+    return 2 * vec + w;
 }
 
 int pack_device(hm_matrix& H, int32_t form, cudaStream_t s)
 {
     int rc;
     const int ntask = (int)(H.nadm * 7);
-    auto convert = [&](const DevBuf& src, DevBuf& dst, int64_t n) -> int {
-        if ((rc = dalloc(H, dst, (size_t)std::max<int64_t>(n, 1) * 4))) return rc;
-        if (n > 0) {
-            convert_kernel<float><<<1216, 256, 0, s>>>(src.as<double>(), dst.as<float>(), (size_t)n);
-            HM_CUDA(cudaGetLastError());
-        }
+    if (form == HM_FP64) {
+        if ((rc = pack_form<double>(H, HM_FP64, nullptr, nullptr, s))) return rc;
+        if ((rc = pack_near<double>(H, H.Nl64, s))) return rc;
+        H.packed[HM_FP64] = true;
         return HM_OK;
-    };
-    if (!H.N32.p && form != HM_FP64)
-        if ((rc = convert(H.N64, H.N32, H.n_total))) return rc;
-    if (form == HM_FP32) {
-        if ((rc = convert(H.U64, H.U32, H.u_total))) return rc;
-        if ((rc = convert(H.V64, H.V32, H.v_total))) return rc;
-    } else if (form == HM_BF16 || form == HM_FP16) {
-        DevBuf &Ud = form == HM_BF16 ? H.U16b : H.U16h, &Vd = form == HM_BF16 ? H.V16b : H.V16h;
-        DevBuf &Su = form == HM_BF16 ? H.SUb : H.SUh, &Sv = form == HM_BF16 ? H.SVb : H.SVh;
-        if ((rc = dalloc(H, Ud, (size_t)std::max<int64_t>(H.u_total, 1) * 2))) return rc;
-        if ((rc = dalloc(H, Vd, (size_t)std::max<int64_t>(H.v_total, 1) * 2))) return rc;
-        if ((rc = dalloc(H, Su, (size_t)std::max<int64_t>(H.c_total, 1) * 4))) return rc;
-        if ((rc = dalloc(H, Sv, (size_t)std::max<int64_t>(H.c_total, 1) * 4))) return rc;
-        if (ntask > 0) {
-            if (form == HM_BF16) {
-                pack16_kernel<__nv_bfloat16><<<ntask, 128, 0, s>>>(
-                    ntask, H.d_adm.as<Blk>(), H.d_rank.as<int32_t>(), H.d_uoff.as<int64_t>(),
-                    H.d_coff.as<int64_t>(), 1, H.U64.as<double>(), Ud.as<__nv_bfloat16>(), Su.as<float>());
-                pack16_kernel<__nv_bfloat16><<<ntask, 128, 0, s>>>(
-                    ntask, H.d_adm.as<Blk>(), H.d_rank.as<int32_t>(), H.d_voff.as<int64_t>(),
-                    H.d_coff.as<int64_t>(), 0, H.V64.as<double>(), Vd.as<__nv_bfloat16>(), Sv.as<float>());
-            } else {
-                pack16_kernel<__half><<<ntask, 128, 0, s>>>(
-                    ntask, H.d_adm.as<Blk>(), H.d_rank.as<int32_t>(), H.d_uoff.as<int64_t>(),
-                    H.d_coff.as<int64_t>(), 1, H.U64.as<double>(), Ud.as<__half>(), Su.as<float>());
-                pack16_kernel<__half><<<ntask, 128, 0, s>>>(
-                    ntask, H.d_adm.as<Blk>(), H.d_rank.as<int32_t>(), H.d_voff.as<int64_t>(),
-                    H.d_coff.as<int64_t>(), 0, H.V64.as<double>(), Vd.as<__half>(), Sv.as<float>());
-            }
-            HM_CUDA(cudaGetLastError());
-        }
     }
+    if (!H.Nl32.p)
+        if ((rc = pack_near<float>(H, H.Nl32, s))) return rc;
+    if (form == HM_FP32) {
+        if ((rc = pack_form<float>(H, HM_FP32, nullptr, nullptr, s))) return rc;
+    } else {
+        if (!H.SU.p) {
+            if ((rc = dalloc(H, H.SU, (size_t)std::max<int64_t>(H.c_total, 1) * 4))) return rc;
+            if ((rc = dalloc(H, H.SV, (size_t)std::max<int64_t>(H.c_total, 1) * 4))) return rc;
+            if (ntask > 0) {
+                colscale_kernel<<<ntask, 128, 0, s>>>(
+                    ntask, H.d_adm.as<Blk>(), H.d_rank.as<int32_t>(), H.d_uoff.as<int64_t>(),
+                    H.d_voff.as<int64_t>(), H.d_coff.as<int64_t>(), H.U64.as<double>(),
+                    H.V64.as<double>(), H.SU.as<float>(), H.SV.as<float>());
+                HM_CUDA(cudaGetLastError());
+            }
+        }
+        if (form == HM_BF16)
+            rc = pack_form<__nv_bfloat16>(H, HM_BF16, H.SU.as<float>(), H.SV.as<float>(), s);
+        else
+            rc = pack_form<__half>(H, HM_FP16, H.SU.as<float>(), H.SV.as<float>(), s);
+        if (rc) return rc;
+    }
+    H.packed[form] = true;
     return HM_OK;
 }
 

@@ -81,7 +81,8 @@ extern "C" int hm_matvec_noalloc(const hm_matrix* H, const double* x, double* y,
     int rc = scratch_address(&base);
     if (rc) return rc;
     const size_t ta = form == HM_FP64 ? 8 : 4;
-    const size_t xg_bytes = ((size_t)nrhs * 3 * (size_t)H->M * ta + 255) & ~(size_t)255;
-    Scratch scr{base, static_cast<unsigned char*>(base) + xg_bytes, false};
+    const size_t vec = ((size_t)nrhs * 4 * (size_t)H->M * ta + 255) & ~(size_t)255;
+    unsigned char* b = static_cast<unsigned char*>(base);
+    Scratch scr{b, b + 2 * vec, b + vec, false};
     return matvec_device_scratch(*H, x, y, nrhs, ld, form, (cudaStream_t)stream, scr);
 }

@@ -1,0 +1,454 @@
+// hm_stream.cuh -- per-leaf product of the far and near field streamed through
+// shared memory with bulk asynchronous copies (cp.async.bulk + mbarrier).
+//
+// For every leaf row cluster tau the factor segments (columns of U restricted
+// to the rows of tau) and the near-field columns are contiguous in memory
+// (see hm_matvec.cu).  A persistent CTA takes leaves from a global counter
+// (largest first).  Warp 0 is the producer: for every slot of a ring of
+// kStages shared-memory slots it copies up to kStageBytes of the current
+// leaf's stream and, next to it, the 4-vector each segment needs: w of the
+// segment's factor column (far field) or x at the segment's source position
+// (near field).  Consecutive segments of one (block, kernel) item have
+// consecutive factor columns (and of one near block consecutive positions),
+// so these are a few contiguous bulk copies per slot, one per item and lane.
+// Warps 1..7 consume the slots from shared memory only: thread (p, h) owns R
+// rows (16 bytes of U) and every H-th segment of a slot; at the end of a leaf
+// the H partial sums of each row are added in a fixed order and y is written
+// in the original dof order.  Deterministic.
+//
+// Every mbarrier wait is bounded (kWaitCycles); on expiry the thread records
+// an error in *err, the producer drains its own copies in flight (again
+// bounded) and the CTA returns.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <climits>
+#include <cstdint>
+
+namespace hm {
+namespace stream {
+
+constexpr int kThreads = 256;             // warp 0 producer + 7 consumer warps
+constexpr int kConsumers = kThreads - 32;
+constexpr int kStages = 4;
+constexpr int kStageBytes = 16384;
+constexpr int kMaxSeg = 256;              // segments / columns per stage at most
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+struct StageMeta {
+    int32_t leaf;   // leaf index (into the leaf table)
+    int32_t kind;   // 0 far segments, 1 near columns, 2 no more work
+    int32_t first;  // first segment / column of the stage within the leaf's stream
+    int32_t count;  // segments / columns in the stage
+    int32_t last;   // 1 if this is the last stage of the leaf
+    int32_t pad[3];
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait for the phase with the given parity; false (and *err set) on expiry
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (clock64() - t0 > kWaitCycles) {
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+}
+
+// bulk copy global -> shared (16-byte aligned, size a multiple of 16), with
+// completion counted on the mbarrier
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void named_barrier_consumers()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory");
+}
+
+// 16 bytes from shared memory as N values
+template <class T, class TA>
+struct Smem16;
+template <class TA>
+struct Smem16<double, TA> {
+    static constexpr int N = 2;
+    __device__ __forceinline__ static void load(const double* p, TA* o)
+    {
+        double2 v = *reinterpret_cast<const double2*>(p);
+        o[0] = (TA)v.x;
+        o[1] = (TA)v.y;
+    }
+};
+template <class TA>
+struct Smem16<float, TA> {
+    static constexpr int N = 4;
+    __device__ __forceinline__ static void load(const float* p, TA* o)
+    {
+        float4 v = *reinterpret_cast<const float4*>(p);
+        o[0] = (TA)v.x;
+        o[1] = (TA)v.y;
+        o[2] = (TA)v.z;
+        o[3] = (TA)v.w;
+    }
+};
+template <class TA>
+struct Smem16<__half, TA> {
+    static constexpr int N = 8;
+    __device__ __forceinline__ static void load(const __half* p, TA* o)
+    {
+        uint4 v = *reinterpret_cast<const uint4*>(p);
+        const __half2* h = reinterpret_cast<const __half2*>(&v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float2 f = __half22float2(h[q]);
+            o[2 * q] = (TA)f.x;
+            o[2 * q + 1] = (TA)f.y;
+        }
+    }
+};
+template <class TA>
+struct Smem16<__nv_bfloat16, TA> {
+    static constexpr int N = 8;
+    __device__ __forceinline__ static void load(const __nv_bfloat16* p, TA* o)
+    {
+        uint4 v = *reinterpret_cast<const uint4*>(p);
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float2 f = __bfloat1622float2(h[q]);
+            o[2 * q] = (TA)f.x;
+            o[2 * q + 1] = (TA)f.y;
+        }
+    }
+};
+
+__device__ __forceinline__ void load3(const float* p, float& a, float& b, float& c)
+{
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a = v.x;
+    b = v.y;
+    c = v.z;
+}
+__device__ __forceinline__ void load3(const double* p, double& a, double& b, double& c)
+{
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    a = v.x;
+    b = v.y;
+    c = p[2];
+}
+
+// R consecutive values (R * sizeof(T) a multiple of 16) from shared memory
+template <class T, class TA, int R>
+__device__ __forceinline__ void smem_rows(const T* p, TA* o)
+{
+    constexpr int N = Smem16<T, TA>::N;
+#pragma unroll
+    for (int q = 0; q < R / N; ++q) Smem16<T, TA>::load(p + q * N, o + q * N);
+}
+
+template <class TA>
+size_t smem_bytes(int R)
+{
+    return (size_t)kStages * kStageBytes + (size_t)kStages * kMaxSeg * 4 * sizeof(TA) +
+           (size_t)kConsumers * R * 3 * sizeof(TA);
+}
+
+struct LeafTables {
+    const int32_t* leaf;      // (t0, mt) per leaf
+    const int32_t* order;     // leaves in processing order
+    const int64_t* lf_base;
+    const int32_t* lf_ptr;
+    const LeafFarItem* lf_items;
+    const int64_t* ln_base;
+    const int32_t* ln_ptr;
+    const LeafNearItem* ln_items;
+    const int32_t* perm;
+};
+
+template <class TF, class TN, class TA>
+__global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
+    int nleaves, LeafTables tb, int* __restrict__ counters, int* __restrict__ err,
+    const TF* __restrict__ Ul, const TN* __restrict__ Nl, const TA* __restrict__ xg,
+    const TA* __restrict__ w, double* __restrict__ y, int64_t ld, int M, int64_t ctot, TA c1, TA c2)
+{
+    constexpr int R = Smem16<TF, TA>::N;  // rows per consumer thread: 16 bytes of U
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* sbuf = smem;
+    TA* aux = reinterpret_cast<TA*>(smem + kStages * kStageBytes);  // kStages x kMaxSeg x 4
+    TA* red = aux + kStages * kMaxSeg * 4;
+    __shared__ __align__(8) uint64_t full[kStages];
+    __shared__ __align__(8) uint64_t empty[kStages];
+    __shared__ StageMeta meta[kStages];
+    __shared__ int abort_flag;
+
+    const int r = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kConsumers / 32);
+        }
+        abort_flag = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        int it = 0;
+        bool ok = true;
+        // One stage: [first, first + count) of the current stream.  `items`
+        // are the stream's (start, vector index) records (sentinel last, ni
+        // records); *cur is the item containing `first` and is advanced to
+        // the item containing first + count.  vec: the 4-vectors the stream
+        // reads (w for the far field, x for the near field).
+        auto emit = [&](int lf, int kind, int first, int count, int last, const void* src,
+                        uint32_t bytes, const int2* items, int ni, int* cur, const TA* vec) -> bool {
+            const int slot = it % kStages;
+            if (it >= kStages) {
+                if (!mbar_wait(&empty[slot], (uint32_t)((it / kStages) - 1) & 1u, err)) return false;
+            }
+            if (lane == 0) {
+                StageMeta m;
+                m.leaf = lf;
+                m.kind = kind;
+                m.first = first;
+                m.count = count;
+                m.last = last;
+                meta[slot] = m;
+                if (kind < 2)
+                    mbar_arrive_expect_tx(&full[slot], bytes + (uint32_t)(count * 4 * sizeof(TA)));
+            }
+            __syncwarp();
+            if (kind < 2) {
+                TA* av = aux + (size_t)slot * kMaxSeg * 4;
+                const int end = first + count;
+                int q0 = *cur;
+                for (;;) {
+                    // lane l looks at item q0 + l; its end is the next item's start
+                    const int q = q0 + lane;
+                    int2 a = make_int2(INT_MAX, 0);
+                    if (q < ni - 1) a = items[q];
+                    int b = __shfl_down_sync(0xffffffffu, a.x, 1);
+                    if (lane == 31) b = (q + 1 < ni) ? items[q + 1].x : INT_MAX;
+                    const bool overlap = a.x < end;  // items are sorted; all start < end at most
+                    if (overlap) {
+                        const int g0 = max(a.x, first), g1 = min(b, end);
+                        if (g0 < g1)
+                            bulk_g2s(av + (size_t)(g0 - first) * 4, vec + (size_t)(a.y + (g0 - a.x)) * 4,
+                                     (uint32_t)((g1 - g0) * 4 * sizeof(TA)), &full[slot]);
+                    }
+                    const unsigned ov = __ballot_sync(0xffffffffu, overlap);
+                    const int nov = __popc(ov);  // overlapping items are a prefix of the lanes
+                    const int lastq = q0 + nov - 1;  // last overlapping item
+                    const int lastb = __shfl_sync(0xffffffffu, b, (nov - 1) & 31);
+                    if (nov < 32 || lastb >= end) {
+                        // the item containing `end` (or the last item) is the next cursor
+                        *cur = lastb > end ? lastq : lastq + 1;
+                        break;
+                    }
+                    q0 += 32;
+                }
+                if (lane == 0) bulk_g2s(sbuf + (size_t)slot * kStageBytes, src, bytes, &full[slot]);
+            } else if (lane == 0) {
+                mbar_arrive(&full[slot]);
+            }
+            ++it;
+            return true;
+        };
+        const TA* wvec = w + (size_t)r * 4 * ctot;
+        const TA* xvec = xg + (size_t)r * 4 * M;
+        for (;;) {
+            int idx = 0;
+            if (lane == 0) idx = atomicAdd(&counters[r], 1);
+            idx = __shfl_sync(0xffffffffu, idx, 0);
+            if (idx >= nleaves || !ok) break;
+            const int lf = tb.order[idx];
+            const int mt = tb.leaf[2 * lf + 1];
+            const int mp = (mt + 7) & ~7;
+            const int fi0 = tb.lf_ptr[lf], fi1 = tb.lf_ptr[lf + 1];
+            const int ni0 = tb.ln_ptr[lf], ni1 = tb.ln_ptr[lf + 1];
+            const int S = tb.lf_items[fi1 - 1].seg_start;
+            const int Sn = tb.ln_items[ni1 - 1].col_start;
+            const int segB = mp * (int)sizeof(TF);
+            const int perF = min(kStageBytes / segB, kMaxSeg);
+            const int2* fitems = reinterpret_cast<const int2*>(tb.lf_items + fi0);
+            const int2* nitems = reinterpret_cast<const int2*>(tb.ln_items + ni0);
+            int cur = 0;
+            for (int g = 0; g < S && ok; g += perF) {
+                const int cnt = min(perF, S - g);
+                const TF* src = Ul + tb.lf_base[lf] + (size_t)g * mp;
+                ok = emit(lf, 0, g, cnt, (g + cnt == S && Sn == 0) ? 1 : 0, src, (uint32_t)(cnt * segB),
+                          fitems, fi1 - fi0, &cur, wvec);
+            }
+            const int colB = 6 * mp * (int)sizeof(TN);
+            const int perN = min(kStageBytes / colB, kMaxSeg);
+            cur = 0;
+            for (int g = 0; g < Sn && ok; g += perN) {
+                const int cnt = min(perN, Sn - g);
+                const TN* src = Nl + tb.ln_base[lf] + (size_t)g * 6 * mp;
+                ok = emit(lf, 1, g, cnt, (g + cnt == Sn) ? 1 : 0, src, (uint32_t)(cnt * colB), nitems,
+                          ni1 - ni0, &cur, xvec);
+            }
+        }
+        if (ok) ok = emit(-1, 2, 0, 0, 0, nullptr, 0, nullptr, 0, nullptr, nullptr);
+        if (!ok) {
+            // drain this CTA's own copies in flight before returning (bounded)
+            if (lane == 0) abort_flag = 1;
+            for (int k = 1; k <= kStages && k <= it; ++k) {
+                const int j = it - k;
+                mbar_wait(&full[j % kStages], (uint32_t)(j / kStages) & 1u, err);
+            }
+        }
+        return;
+    }
+
+    // ---------------------------------------------------------------- consumers
+    const int ctid = threadIdx.x - 32;
+    int cur = -1, P = 1, H = 0, p = 0, h = 0, t0 = 0, mt = 0, mp = 8;
+    TA acc[R][3];
+    for (int it = 0;; ++it) {
+        const int slot = it % kStages;
+        if (!mbar_wait(&full[slot], (uint32_t)(it / kStages) & 1u, err)) break;
+        const StageMeta m = meta[slot];
+        if (m.kind == 2) break;
+        if (m.leaf != cur) {
+            cur = m.leaf;
+            t0 = tb.leaf[2 * cur];
+            mt = tb.leaf[2 * cur + 1];
+            mp = (mt + 7) & ~7;
+            P = mp / R;
+            H = kConsumers / P;
+            p = ctid % P;
+            h = ctid / P;
+#pragma unroll
+            for (int e = 0; e < R; ++e) acc[e][0] = acc[e][1] = acc[e][2] = (TA)0;
+        }
+        const TA* av = aux + (size_t)slot * kMaxSeg * 4;
+        if (h < H) {
+            if (m.kind == 0) {
+                const TF* sb = reinterpret_cast<const TF*>(sbuf + (size_t)slot * kStageBytes) + p * R;
+                int s = h;
+                for (; s + H < m.count; s += 2 * H) {
+                    TA wa0, wa1, wa2, wb0, wb1, wb2;
+                    load3(av + (size_t)s * 4, wa0, wa1, wa2);
+                    load3(av + (size_t)(s + H) * 4, wb0, wb1, wb2);
+                    TA ua[R], ub[R];
+                    smem_rows<TF, TA, R>(sb + (size_t)s * mp, ua);
+                    smem_rows<TF, TA, R>(sb + (size_t)(s + H) * mp, ub);
+#pragma unroll
+                    for (int e = 0; e < R; ++e) {
+                        acc[e][0] += ua[e] * wa0 + ub[e] * wb0;
+                        acc[e][1] += ua[e] * wa1 + ub[e] * wb1;
+                        acc[e][2] += ua[e] * wa2 + ub[e] * wb2;
+                    }
+                }
+                if (s < m.count) {
+                    TA wa0, wa1, wa2;
+                    load3(av + (size_t)s * 4, wa0, wa1, wa2);
+                    TA ua[R];
+                    smem_rows<TF, TA, R>(sb + (size_t)s * mp, ua);
+#pragma unroll
+                    for (int e = 0; e < R; ++e) {
+                        acc[e][0] += ua[e] * wa0;
+                        acc[e][1] += ua[e] * wa1;
+                        acc[e][2] += ua[e] * wa2;
+                    }
+                }
+            } else {
+                const TN* sb = reinterpret_cast<const TN*>(sbuf + (size_t)slot * kStageBytes) + p * R;
+                for (int s = h; s < m.count; s += H) {
+                    TA x0, x1, x2;
+                    load3(av + (size_t)s * 4, x0, x1, x2);
+                    const TN* e0 = sb + (size_t)s * 6 * mp;
+                    TA v11[R], v12[R], v13[R], v22[R], v23[R], v33[R];
+                    smem_rows<TN, TA, R>(e0, v11);
+                    smem_rows<TN, TA, R>(e0 + mp, v12);
+                    smem_rows<TN, TA, R>(e0 + 2 * mp, v13);
+                    smem_rows<TN, TA, R>(e0 + 3 * mp, v22);
+                    smem_rows<TN, TA, R>(e0 + 4 * mp, v23);
+                    smem_rows<TN, TA, R>(e0 + 5 * mp, v33);
+#pragma unroll
+                    for (int e = 0; e < R; ++e) {
+                        const TA vd = c1 * (v11[e] + v22[e] + v33[e]);
+                        acc[e][0] += vd * x0 + c2 * (v11[e] * x0 + v12[e] * x1 + v13[e] * x2);
+                        acc[e][1] += vd * x1 + c2 * (v12[e] * x0 + v22[e] * x1 + v23[e] * x2);
+                        acc[e][2] += vd * x2 + c2 * (v13[e] * x0 + v23[e] * x1 + v33[e] * x2);
+                    }
+                }
+            }
+        }
+        // the slot may be refilled once every consumer warp is done with it
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+        if (m.last) {
+            if (h < H) {
+#pragma unroll
+                for (int e = 0; e < R; ++e)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) red[((h * P + p) * R + e) * 3 + a] = acc[e][a];
+            }
+            named_barrier_consumers();
+            for (int idx = ctid; idx < mt * 3; idx += kConsumers) {
+                const int i = idx / 3, a = idx - 3 * i;
+                TA sum = (TA)0;
+                for (int g = 0; g < H; ++g) sum += red[((g * P) * R + i) * 3 + a];
+                y[(size_t)r * ld + 3 * (size_t)tb.perm[t0 + i] + a] = (double)sum;
+            }
+            named_barrier_consumers();
+        }
+    }
+}
+
+}  // namespace stream
+}  // namespace hm
