@@ -157,7 +157,7 @@ int hm_matvec(const hm_matrix* H, const double* x, double* y, int32_t nrhs, int6
  *   - The array is held by every GPU on which the library is loaded, until
  *     the process exits.
  *   - Products needing more than 32 MiB of workspace are rejected with
- *     HM_EINVAL (need = nrhs * (3M + 3 * sum of ACA ranks) * 8 bytes for
+ *     HM_EINVAL (need = nrhs * (8M + 4 * sum of ACA ranks) * 8 bytes for
  *     HM_FP64, * 4 for the other forms, plus alignment).
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress, which may load the library's device code on

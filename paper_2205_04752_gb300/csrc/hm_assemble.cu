@@ -1024,16 +1024,6 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
         H.max_leaf = maxleaf;
         H.ul_total = ul;
         H.nl_total = nl;
-        std::vector<int64_t> vb_base((size_t)H.nadm + 1);
-        int64_t vr = 0;
-        for (int64_t b = 0; b < H.nadm; ++b) {
-            int64_t C = 0;
-            for (int k = 0; k < 7; ++k) C += H.rank_h[(size_t)(b * 7 + k)];
-            vb_base[(size_t)b] = vr;
-            vr += (int64_t)H.adm_h[(size_t)b].n * ((C + 7) & ~int64_t(7));
-        }
-        vb_base[(size_t)H.nadm] = vr;
-        H.vr_total = vr;
         H.nleaves = (int64_t)tr.leaves.size();
         {
             // streamed kernel: leaves with the most bytes first
@@ -1058,7 +1048,6 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
         if ((rc = upload(H, H.d_ln_ptr, ln_ptr.data(), ln_ptr.size() * 4))) return rc;
         if ((rc = upload(H, H.d_ln_items, ln_items.data(), ln_items.size() * sizeof(LeafNearItem)))) return rc;
         if ((rc = upload(H, H.d_ln_src, ln_src.data(), ln_src.size() * sizeof(NearSrc)))) return rc;
-        if ((rc = upload(H, H.d_vb_base, vb_base.data(), vb_base.size() * 8))) return rc;
     }
     {
         // forward-pass records: blocks with |s| <= 128 (one warp each) and
@@ -1071,38 +1060,39 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
                 work[(size_t)b] += (int64_t)H.rank_h[(size_t)(b * 7 + k)] * H.adm_h[(size_t)b].n;
         std::stable_sort(ord.begin(), ord.end(),
                          [&](int32_t a, int32_t b) { return work[(size_t)a] > work[(size_t)b]; });
-        std::vector<FwdRec> small, big;
-        std::vector<int64_t> vb((size_t)H.nadm + 1);
-        {
-            int64_t vr = 0;
-            for (int64_t b = 0; b < H.nadm; ++b) {
-                int64_t C = 0;
-                for (int k = 0; k < 7; ++k) C += H.rank_h[(size_t)(b * 7 + k)];
-                vb[(size_t)b] = vr;
-                vr += (int64_t)H.adm_h[(size_t)b].n * ((C + 7) & ~int64_t(7));
+        // stream order: blocks with |s| > 128 first, then the others, each
+        // with the most data first; the row-major V arena follows this order
+        std::vector<int32_t> big_ids, small_ids;
+        for (int32_t b : ord) (H.adm_h[(size_t)b].n <= 128 ? small_ids : big_ids).push_back(b);
+        std::vector<int64_t> vb_base((size_t)H.nadm + 1, 0);
+        std::vector<FwdRec> recs;
+        int64_t vr = 0;
+        for (const auto* lst : {&big_ids, &small_ids})
+            for (int32_t b : *lst) {
+                FwdRec r{};
+                const Blk& bk = H.adm_h[(size_t)b];
+                r.s0 = bk.s0;
+                r.n = bk.n;
+                r.col0 = (int32_t)H.coff_h[(size_t)b * 7];
+                r.C = 0;
+                for (int k = 0; k < 7; ++k) {
+                    const int32_t kk = H.rank_h[(size_t)(b * 7 + k)];
+                    if (kk > 255) return fail(HM_EINVAL, "rank %d above 255 is not supported", kk);
+                    r.kpack |= (uint64_t)kk << (8 * k);
+                    r.C += kk;
+                }
+                vb_base[(size_t)b] = vr;
+                r.vbase = vr;
+                vr += (int64_t)bk.n * ((r.C + 7) & ~int64_t(7));
+                if (r.C == 0) continue;
+                (bk.n <= 128 ? H.n_fwd_small : H.n_fwd_big) += 1;
+                recs.push_back(r);
             }
-        }
-        for (int32_t b : ord) {
-            FwdRec r{};
-            const Blk& bk = H.adm_h[(size_t)b];
-            r.s0 = bk.s0;
-            r.n = bk.n;
-            r.col0 = (int32_t)H.coff_h[(size_t)b * 7];
-            r.C = 0;
-            for (int k = 0; k < 7; ++k) {
-                const int32_t kk = H.rank_h[(size_t)(b * 7 + k)];
-                if (kk > 255) return fail(HM_EINVAL, "rank %d above 255 is not supported", kk);
-                r.kpack |= (uint64_t)kk << (8 * k);
-                r.C += kk;
-            }
-            r.vbase = vb[(size_t)b];
-            if (r.C == 0) continue;
-            (bk.n <= 128 ? small : big).push_back(r);
-        }
-        H.n_fwd_small = (int64_t)small.size();
-        H.n_fwd_big = (int64_t)big.size();
-        if ((rc = upload(H, H.d_fwd_small, small.data(), small.size() * sizeof(FwdRec)))) return rc;
-        if ((rc = upload(H, H.d_fwd_big, big.data(), big.size() * sizeof(FwdRec)))) return rc;
+        vb_base[(size_t)H.nadm] = vr;
+        H.vr_total = vr;
+        H.fwd_h = recs;
+        if ((rc = upload(H, H.d_fwd_all, recs.data(), recs.size() * sizeof(FwdRec)))) return rc;
+        if ((rc = upload(H, H.d_vb_base, vb_base.data(), vb_base.size() * 8))) return rc;
         if (H.c_total > INT32_MAX / 4) return fail(HM_EINVAL, "too many factor columns");
     }
     // ---- workspace for the product
@@ -1110,7 +1100,7 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
     if ((rc = dalloc(H, H.xg, (size_t)H.max_rhs * 4 * M * 8))) return rc;
     if ((rc = dalloc(H, H.wb, (size_t)H.max_rhs * std::max<int64_t>(H.w_total, 1) * 8))) return rc;
     if ((rc = dalloc(H, H.yn, (size_t)H.max_rhs * 3 * M * 8))) return rc;
-    if ((rc = dalloc(H, H.d_counters, (size_t)H.max_rhs * sizeof(int)))) return rc;
+    if ((rc = dalloc(H, H.d_counters, (size_t)2 * H.max_rhs * sizeof(int)))) return rc;
     if ((rc = dalloc(H, H.d_err, 64))) return rc;
     HM_CUDA(cudaMemsetAsync(H.d_err.p, 0, 64, s));
     HM_CUDA(cudaStreamCreateWithFlags(&H.side, cudaStreamNonBlocking));

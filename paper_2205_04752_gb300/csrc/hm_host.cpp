@@ -364,13 +364,13 @@ int hm_get_stats(const hm_matrix* H, hm_stats* st)
     int64_t near_vals = st->near_pairs * 6;
     st->bytes_fp64 = (st->far_entries + near_vals) * 8;
     // bytes one product streams in each packed form (padded layouts; the
-    // 16-bit forms add one float scale per factor column of U and of V)
+    // 16-bit forms add one float scale per factor column of U)
     const int64_t stream_elems = H->ul_total + H->vr_total;
     for (int f = 0; f < 4; ++f) {
         if (!H->packed[f]) continue;
         int64_t wf = f == HM_FP64 ? 8 : (f == HM_FP32 ? 4 : 2);
         int64_t wn = f == HM_FP64 ? 8 : 4;
-        st->bytes_form[f] = stream_elems * wf + H->nl_total * wn + (wf == 2 ? far_cols * 8 : 0);
+        st->bytes_form[f] = stream_elems * wf + H->nl_total * wn + (wf == 2 ? far_cols * 4 : 0);
     }
     for (int i = 0; i < 3; ++i) st->assemble_ms[i] = H->asm_ms[i];
     return HM_OK;
@@ -464,7 +464,7 @@ void hm_matrix_destroy(hm_matrix* H)
     hm::DevBuf* bufs[] = {&H->d_perm, &H->d_adm, &H->d_near, &H->d_rank, &H->d_uoff, &H->d_voff,
                           &H->d_coff, &H->d_noff, &H->d_leaf, &H->d_lf_base, &H->d_lf_ptr,
                           &H->d_lf_items, &H->d_lf_src, &H->d_ln_base, &H->d_ln_ptr, &H->d_ln_items,
-                          &H->d_ln_src, &H->d_vb_base, &H->d_fwd_small, &H->d_fwd_big, &H->d_leaf_order, &H->d_counters, &H->d_err, &H->U64, &H->V64, &H->N64,
+                          &H->d_ln_src, &H->d_vb_base, &H->d_fwd_all, &H->d_leaf_order, &H->d_counters, &H->d_err, &H->U64, &H->V64, &H->N64,
                           &H->Ul[0], &H->Ul[1], &H->Ul[2], &H->Ul[3], &H->Vr[0], &H->Vr[1],
                           &H->Vr[2], &H->Vr[3], &H->Nl64, &H->Nl32, &H->SU, &H->SV, &H->xg, &H->wb,
                           &H->yn, &H->xh, &H->yh};

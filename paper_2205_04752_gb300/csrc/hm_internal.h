@@ -101,6 +101,7 @@ struct FwdRec {
     uint64_t kpack;  // rank of kernel q in bits 8q .. 8q+7
 };
 
+
 }  // namespace hm
 
 struct hm_matrix {
@@ -132,7 +133,9 @@ struct hm_matrix {
     hm::DevBuf d_lf_base, d_lf_ptr, d_lf_items, d_lf_src;  // far stream per leaf
     hm::DevBuf d_ln_base, d_ln_ptr, d_ln_items, d_ln_src;  // near stream per leaf
     hm::DevBuf d_vb_base;                 // int64 nadm+1: row-major V of each block
-    hm::DevBuf d_fwd_small, d_fwd_big;   // FwdRec: blocks with |s| <= 128 / larger ones
+    hm::DevBuf d_fwd_all;                // FwdRec in stream order: |s| > 128 first, then the rest
+    std::vector<hm::FwdRec> fwd_h;       // host copy of d_fwd_all
+
     hm::DevBuf d_leaf_order;             // int32 nleaves: leaves by decreasing streamed bytes
     hm::DevBuf d_counters;               // int32 max_rhs: work counters of the streamed kernel
     hm::DevBuf d_err;                    // int32: set by a device wait that ran out

@@ -646,16 +646,19 @@ int run_matvec(const hm_matrix& H, int form, const TN* N, const float* SU, const
         HM_CUDA(cudaGetLastError());
         HM_CUDA(cudaEventRecord(H.ev_join, H.side));
     }
-    if (H.n_fwd_big > 0) {
-        fwd_big_kernel<TF, TA><<<dim3((unsigned)H.n_fwd_big, nr), kThreads, 0, s>>>(
-            H.d_fwd_big.as<FwdRec>(), Vr, SU, SV, xg, w, M, H.c_total, c1, c2);
-        HM_CUDA(cudaGetLastError());
-    }
-    if (H.n_fwd_small > 0) {
-        const unsigned nb = (unsigned)((H.n_fwd_small + kThreads / 32 - 1) / (kThreads / 32));
-        fwd_small_kernel<TF, TA><<<dim3(nb, nr), kThreads, 0, s>>>(
-            H.d_fwd_small.as<FwdRec>(), (int)H.n_fwd_small, Vr, SU, SV, xg, w, M, H.c_total, c1, c2);
-        HM_CUDA(cudaGetLastError());
+    {
+        const FwdRec* recs = H.d_fwd_all.as<FwdRec>();
+        if (H.n_fwd_big > 0) {
+            fwd_big_kernel<TF, TA><<<dim3((unsigned)H.n_fwd_big, nr), kThreads, 0, s>>>(
+                recs, Vr, SU, SV, xg, w, M, H.c_total, c1, c2);
+            HM_CUDA(cudaGetLastError());
+        }
+        if (H.n_fwd_small > 0) {
+            const unsigned nb = (unsigned)((H.n_fwd_small + kThreads / 32 - 1) / (kThreads / 32));
+            fwd_small_kernel<TF, TA><<<dim3(nb, nr), kThreads, 0, s>>>(
+                recs + H.n_fwd_big, (int)H.n_fwd_small, Vr, SU, SV, xg, w, M, H.c_total, c1, c2);
+            HM_CUDA(cudaGetLastError());
+        }
     }
     if (scr.profile) prof_mark(H, 2, s);
     if (streamed) {
@@ -744,11 +747,11 @@ int matvec_device_scratch(const hm_matrix& H, const double* x, double* y, int32_
                                                    y, nrhs, ld, s, scr);
         case HM_BF16:
             return run_matvec<__nv_bfloat16, float, float>(H, form, H.Nl32.as<float>(),
-                                                           H.SU.as<float>(), H.SV.as<float>(), x, y,
-                                                           nrhs, ld, s, scr);
+                                                           H.SU.as<float>(), nullptr, x, y, nrhs, ld,
+                                                           s, scr);
         case HM_FP16:
             return run_matvec<__half, float, float>(H, form, H.Nl32.as<float>(), H.SU.as<float>(),
-                                                    H.SV.as<float>(), x, y, nrhs, ld, s, scr);
+                                                    nullptr, x, y, nrhs, ld, s, scr);
         default:
             return fail(HM_EINVAL, "hm_matvec: unknown form %d", form);
     }
@@ -769,6 +772,9 @@ size_t matvec_scratch_bytes(const hm_matrix& H, int32_t nrhs, int32_t form)
     return 2 * vec + w;
 }
 
+// units of the streamed forward pass for a form with factor element size `sz`:
+// chunked blocks (the large ones, and any block too big for one stage) and
+// runs of up to 32 consecutive small blocks that fit one stage together
 int pack_device(hm_matrix& H, int32_t form, cudaStream_t s)
 {
     int rc;
@@ -795,10 +801,13 @@ int pack_device(hm_matrix& H, int32_t form, cudaStream_t s)
                 HM_CUDA(cudaGetLastError());
             }
         }
+        // V columns are normalised by their ACA pivot (max |v| = 1), so V is
+        // stored without a scale; U carries the magnitudes and gets one scale
+        // per column
         if (form == HM_BF16)
-            rc = pack_form<__nv_bfloat16>(H, HM_BF16, H.SU.as<float>(), H.SV.as<float>(), s);
+            rc = pack_form<__nv_bfloat16>(H, HM_BF16, H.SU.as<float>(), nullptr, s);
         else
-            rc = pack_form<__half>(H, HM_FP16, H.SU.as<float>(), H.SV.as<float>(), s);
+            rc = pack_form<__half>(H, HM_FP16, H.SU.as<float>(), nullptr, s);
         if (rc) return rc;
     }
     H.packed[form] = true;
