@@ -174,6 +174,43 @@ int hm_matvec_noalloc(const hm_matrix* H, const double* x, double* y, int32_t nr
 int hm_matvec_host(const hm_matrix* H, const double* x_host, double* y_host, int32_t nrhs,
                    int64_t ld, int32_t form, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * hm_solve -- solve V_h t = g (one right-hand side) for the single-layer
+ * density t.  Restarted GMRES(m) runs on the product form `inner_form` (for
+ * speed), inside iterative refinement whose residual r = g - V_h t is always
+ * computed with the FP64 form: the result satisfies
+ *     ||g - V_h t||_2 <= tol ||g||_2
+ * for the FP64 H-matrix operator (the paper solves with the assembled
+ * approximation of the operator as well; the solver choice is this library's).
+ *   g, t    device vectors of 3M doubles (dof 3i + a); t is overwritten (or
+ *           used as the initial guess if use_initial_guess)
+ *   info    optional: iterations, restarts, refinements, final relative residual
+ * Synchronises `stream`.  Allocates (restart + 5) vectors of workspace through
+ * the matrix's allocator for the duration of the call.  Returns HM_ENOTCONV
+ * (info filled, t = best iterate) if the caps are reached first.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    double tol;                /* relative FP64 residual target (> 0) */
+    double inner_tol;          /* residual reduction asked of each GMRES solve (0 = 1e-3) */
+    int32_t inner_form;        /* HM_FP16, HM_BF16, HM_FP32 or HM_FP64 (must be packed) */
+    int32_t restart;           /* GMRES restart length m (0 = 50, at most 127) */
+    int32_t max_inner;         /* cap on the total number of inner products (0 = 1000) */
+    int32_t max_refine;        /* cap on refinement steps (0 = 20) */
+    int32_t use_initial_guess; /* nonzero: start from the given t */
+    int32_t pad;
+} hm_solve_params;
+
+typedef struct {
+    int32_t iterations;   /* inner products (GMRES iterations) */
+    int32_t restarts;
+    int32_t refinements;  /* FP64 residual evaluations after the first */
+    int32_t pad;
+    double rel_residual;  /* ||g - V_h t|| / ||g|| with the FP64 form */
+} hm_solve_info;
+
+int hm_solve(const hm_matrix* H, const double* g, double* t, const hm_solve_params* p,
+             hm_solve_info* info, void* stream);
+
 /* Status of the asynchronous products of H: HM_ETIMEOUT if a bounded device
  * wait inside an earlier hm_matvec ran out (its result is then invalid; the
  * flag is cleared), HM_OK otherwise.  Synchronises the device. */

@@ -548,7 +548,8 @@ typedef void (*or_col_fn)(void* ctx, int64_t j, double* out);  /* A[t, j] (m val
 typedef struct {
     int32_t rank;
     int32_t steps;      /* rows visited (accepted + vanished) */
-    int32_t flags;      /* 1: rank cap reached, 2: Z exhausted, 4: k = min(m,n) */
+    int32_t flags;      /* 1: rank cap reached, 2: Z exhausted, 4: k = min(m,n),
+                           32 (set by the H-matrix build): kernel identically zero */
 } or_aca_info;
 
 /* smallest index among the entries (with mask[i] == 0 if mask) whose modulus is
@@ -873,12 +874,38 @@ void or_hmat_blocks(const void* hp, int64_t* adm, int64_t* nearb)
     }
 }
 
+/* Component pair (p, q) of the scalar kernels 1..6 (V_11, V_12, V_13, V_22, V_23, V_33). */
+static const int kern_p[7] = {-1, 0, 0, 0, 1, 1, 2};
+static const int kern_q[7] = {-1, 0, 1, 2, 1, 2, 2};
+
+/* A kernel with factor (x - y)_a vanishes identically on a block whose
+ * clusters' vertices all share the coordinate a (then every collocation point
+ * and every source point has it too): its exact rank is 0, which is what
+ * Algorithm 1 reaches in exact arithmetic once Z = t. */
+static int kernel_vanishes(const or_node* t, const or_node* s, int kern)
+{
+    if (kern == 0) return 0;
+    const int ax[2] = {kern_p[kern], kern_q[kern]};
+    for (int e = 0; e < 2; ++e) {
+        const int a = ax[e];
+        if (t->bmin[a] == t->bmax[a] && s->bmin[a] == s->bmax[a] && t->bmin[a] == s->bmin[a]) return 1;
+    }
+    return 0;
+}
+
 static void assemble_adm(or_hmat* h, int64_t b)
 {
     const or_node* t = &h->nodes[h->bl.adm[b].t];
     const or_node* s = &h->nodes[h->bl.adm[b].s];
     int64_t m = t->hi - t->lo, n = s->hi - s->lo;
     for (int kern = 0; kern < 7; ++kern) {
+        if (kernel_vanishes(t, s, kern)) {
+            h->rank[b * 7 + kern] = 0;
+            h->aca_flags[b * 7 + kern] = 32;
+            h->Uf[b * 7 + kern] = (double*)malloc(sizeof(double));
+            h->Vf[b * 7 + kern] = (double*)malloc(sizeof(double));
+            continue;
+        }
         int64_t kc = h->kmax;
         double* U = (double*)malloc((size_t)(m * kc) * sizeof(double));
         double* Vv = (double*)malloc((size_t)(n * kc) * sizeof(double));

@@ -7,7 +7,7 @@ The binding is imported lazily so that ``paper_2205_04752_gb300.inputs``
 (seeded synthetic meshes) can be used without the CUDA library.
 """
 
-__all__ = ["build_cluster_tree", "aca_assemble", "hmatvec", "hmatvec_host", "HMatrix",
+__all__ = ["build_cluster_tree", "aca_assemble", "hmatvec", "hmatvec_host", "solve", "HMatrix",
            "ClusterTree", "FP64", "FP32", "BF16", "FP16"]
 
 

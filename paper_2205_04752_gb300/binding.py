@@ -26,6 +26,7 @@ SYMBOLS = (
     "hm_aca_assemble", "hm_set_material", "hm_pack", "hm_matvec", "hm_matvec_host",
     "hm_get_stats", "hm_export_factors", "hm_export_near", "hm_matrix_destroy",
     "hm_last_error", "hm_profile_enable", "hm_profile_read", "hm_matvec_noalloc", "hm_check",
+    "hm_solve",
 )
 
 
@@ -47,6 +48,19 @@ _FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
 
 class _Allocator(ctypes.Structure):
     _fields_ = [("alloc", _ALLOC_T), ("free", _FREE_T), ("user", ctypes.c_void_p)]
+
+
+class _SolveParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
+                ("inner_form", ctypes.c_int32), ("restart", ctypes.c_int32),
+                ("max_inner", ctypes.c_int32), ("max_refine", ctypes.c_int32),
+                ("use_initial_guess", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class _SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("restarts", ctypes.c_int32),
+                ("refinements", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("rel_residual", ctypes.c_double)]
 
 
 class _Stats(ctypes.Structure):
@@ -86,6 +100,8 @@ def load():
         "hm_matvec_host": (ctypes.c_int, [P, P, P, I32, I64, I32, P]),
         "hm_matvec_noalloc": (ctypes.c_int, [P, P, P, I32, I64, I32, P]),
         "hm_check": (ctypes.c_int, [P]),
+        "hm_solve": (ctypes.c_int, [P, P, P, ctypes.POINTER(_SolveParams),
+                                    ctypes.POINTER(_SolveInfo), P]),
         "hm_get_stats": (ctypes.c_int, [P, ctypes.POINTER(_Stats)]),
         "hm_export_factors": (ctypes.c_int, [P, I64, I32, ctypes.POINTER(I32), P, P]),
         "hm_export_near": (ctypes.c_int, [P, I64, P]),
@@ -299,6 +315,32 @@ def hmatvec(H: HMatrix, x, y, form="fp64", stream=None):
     _check(load().hm_matvec(H._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                             nrhs, ld, f, _stream_handle(stream)))
     return y
+
+
+def solve(H: HMatrix, g, t, tol: float = 1e-8, inner_form="fp16", inner_tol: float = 0.0,
+          restart: int = 50, max_inner: int = 0, max_refine: int = 0, initial_guess=False,
+          stream=None, raise_on_fail: bool = True):
+    """``hm_solve``: V_h t = g with GMRES on ``inner_form`` and FP64-residual
+    iterative refinement.  g, t: CUDA float64 tensors of 3M.  Returns a dict
+    with iterations, restarts, refinements and the relative FP64 residual."""
+    import torch
+    if not (g.is_cuda and t.is_cuda and g.dtype == torch.float64 and t.dtype == torch.float64):
+        raise TypeError("solve: g and t must be CUDA float64 tensors")
+    if g.numel() != 3 * H.M or t.numel() != 3 * H.M or not g.is_contiguous() or not t.is_contiguous():
+        raise ValueError("solve: g and t must be contiguous vectors of 3M")
+    f = FORMS[inner_form] if isinstance(inner_form, str) else int(inner_form)
+    p = _SolveParams(float(tol), float(inner_tol), f, int(restart), int(max_inner), int(max_refine),
+                     1 if initial_guess else 0, 0)
+    info = _SolveInfo()
+    rc = load().hm_solve(H._h, ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                         ctypes.byref(p), ctypes.byref(info), _stream_handle(stream))
+    out = dict(iterations=info.iterations, restarts=info.restarts, refinements=info.refinements,
+               rel_residual=info.rel_residual, converged=rc == HM_OK)
+    if raise_on_fail:
+        _check(rc)
+    elif rc not in (HM_OK, HM_ENOTCONV):
+        _check(rc)
+    return out
 
 
 def hmatvec_noalloc(H: HMatrix, x, y, form="fp64", stream=None):

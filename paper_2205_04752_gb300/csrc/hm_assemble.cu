@@ -788,12 +788,30 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
     HM_CUDA(cudaEventRecord(ev[1], s));
 
     // ---- batched ACA
-    const int64_t ntask = H.nadm * 7;
-    H.rank_h.assign((size_t)ntask, 0);
-    H.flags_h.assign((size_t)ntask, 0);
-    std::vector<AcaTask> tasks((size_t)ntask);
-    for (int64_t b = 0; b < H.nadm; ++b)
-        for (int k = 0; k < 7; ++k) tasks[(size_t)(b * 7 + k)] = AcaTask{(int32_t)b, k};
+    H.rank_h.assign((size_t)H.nadm * 7, 0);
+    H.flags_h.assign((size_t)H.nadm * 7, 0);
+    // A scalar kernel with factor (x - y)_a vanishes identically on a block
+    // whose clusters' vertices all share coordinate a: exact rank 0 (what
+    // Algorithm 1 reaches in exact arithmetic once Z = t), no ACA task.
+    static const int kp[7] = {-1, 0, 0, 0, 1, 1, 2}, kq[7] = {-1, 0, 1, 2, 1, 2, 2};
+    std::vector<AcaTask> tasks;
+    tasks.reserve((size_t)H.nadm * 7);
+    for (int64_t b = 0; b < H.nadm; ++b) {
+        const Node& nt = tr.nodes[(size_t)tr.adm[(size_t)b][0]];
+        const Node& ns = tr.nodes[(size_t)tr.adm[(size_t)b][1]];
+        for (int k = 0; k < 7; ++k) {
+            bool zero = false;
+            if (k > 0)
+                for (int a : {kp[k], kq[k]})
+                    if (nt.bmin[a] == nt.bmax[a] && ns.bmin[a] == ns.bmax[a] && nt.bmin[a] == ns.bmin[a])
+                        zero = true;
+            if (zero)
+                H.flags_h[(size_t)(b * 7 + k)] = 32;
+            else
+                tasks.push_back(AcaTask{(int32_t)b, k});
+        }
+    }
+    const int64_t ntask = (int64_t)tasks.size();
     std::stable_sort(tasks.begin(), tasks.end(), [&](const AcaTask& x, const AcaTask& y) {
         const Blk& a = H.adm_h[(size_t)x.blk];
         const Blk& c = H.adm_h[(size_t)y.blk];
@@ -915,9 +933,10 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
         H.rank_h[(size_t)(tk.blk * 7 + tk.kern)] = trank[(size_t)q];
         H.flags_h[(size_t)(tk.blk * 7 + tk.kern)] = tflags[(size_t)q];
     }
-    H.uoff_h.resize((size_t)ntask);
-    H.voff_h.resize((size_t)ntask);
-    H.coff_h.resize((size_t)ntask);
+    const int64_t nbk = H.nadm * 7;
+    H.uoff_h.resize((size_t)nbk);
+    H.voff_h.resize((size_t)nbk);
+    H.coff_h.resize((size_t)nbk);
     int64_t ut = 0, vt = 0, ct = 0;
     for (int64_t b = 0; b < H.nadm; ++b)
         for (int k = 0; k < 7; ++k) {
@@ -938,10 +957,10 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
     H.w_total = 4 * ct;  // w holds one 4-vector per factor column
     if ((rc = dalloc(H, H.U64, (size_t)std::max<int64_t>(ut, 1) * 8))) return rc;
     if ((rc = dalloc(H, H.V64, (size_t)std::max<int64_t>(vt, 1) * 8))) return rc;
-    if ((rc = upload(H, H.d_uoff, H.uoff_h.data(), (size_t)ntask * 8))) return rc;
-    if ((rc = upload(H, H.d_voff, H.voff_h.data(), (size_t)ntask * 8))) return rc;
-    if ((rc = upload(H, H.d_coff, H.coff_h.data(), (size_t)ntask * 8))) return rc;
-    if ((rc = upload(H, H.d_rank, H.rank_h.data(), (size_t)ntask * 4))) return rc;
+    if ((rc = upload(H, H.d_uoff, H.uoff_h.data(), (size_t)nbk * 8))) return rc;
+    if ((rc = upload(H, H.d_voff, H.voff_h.data(), (size_t)nbk * 8))) return rc;
+    if ((rc = upload(H, H.d_coff, H.coff_h.data(), (size_t)nbk * 8))) return rc;
+    if ((rc = upload(H, H.d_rank, H.rank_h.data(), (size_t)nbk * 4))) return rc;
     if (ntask > 0) {
         repack_kernel<<<(unsigned)ntask, 128, 0, s>>>(
             dtask.b.as<AcaTask>(), (int)ntask, H.d_adm.as<Blk>(), drank.b.as<int32_t>(),

@@ -437,6 +437,29 @@ def test_aca_block_accuracy_c1():
     assert np.median(ratios) < 0.1
 
 
+def test_vanishing_kernels_on_coplanar_blocks():
+    """A block whose clusters lie in one coordinate plane x_a = c has
+    (x - y)_a = 0, so every scalar kernel with that factor is identically zero
+    (rank 0, no ACA).  The quadrature of those kernels gives rounding noise
+    only, far below the block's V_Delta entries."""
+    V, T = inputs.cube_surface(8)
+    H = oracle.HMatrix(V, T, 16, 0.8, 1e-4)
+    H.assemble()
+    R = oracle.scalar_rows(V, T, np.arange(len(T)))
+    Rc = R[:, H.perm][:, :, H.perm]
+    hits = 0
+    for b in range(H.nadm):
+        a0, a1, s0, s1 = H.ranges(H.adm[b:b + 1])[0]
+        for kern in range(1, 7):
+            if H.aca_flags(b, kern) & 32:
+                hits += 1
+                assert H.rank(b, kern) == 0
+                blk = Rc[kern, a0:a1, s0:s1]
+                vd = Rc[0, a0:a1, s0:s1]
+                assert np.abs(blk).max() <= 1e-12 * np.abs(vd).max()
+    assert hits > 0
+
+
 def test_svd_truncate_recompresses():
     rng = np.random.default_rng(9)
     U = rng.standard_normal((40, 3)) @ rng.standard_normal((3, 8))
