@@ -442,21 +442,22 @@ def test_vanishing_kernels_on_coplanar_blocks():
     (x - y)_a = 0, so every scalar kernel with that factor is identically zero
     (rank 0, no ACA).  The quadrature of those kernels gives rounding noise
     only, far below the block's V_Delta entries."""
-    V, T = inputs.cube_surface(8)
+    V, T = inputs.cube_surface(16)
     H = oracle.HMatrix(V, T, 16, 0.8, 1e-4)
     H.assemble()
-    R = oracle.scalar_rows(V, T, np.arange(len(T)))
-    Rc = R[:, H.perm][:, :, H.perm]
     hits = 0
     for b in range(H.nadm):
+        flagged = [k for k in range(1, 7) if H.aca_flags(b, k) & 32]
+        if not flagged or hits >= 12:
+            continue
         a0, a1, s0, s1 = H.ranges(H.adm[b:b + 1])[0]
-        for kern in range(1, 7):
-            if H.aca_flags(b, kern) & 32:
-                hits += 1
-                assert H.rank(b, kern) == 0
-                blk = Rc[kern, a0:a1, s0:s1]
-                vd = Rc[0, a0:a1, s0:s1]
-                assert np.abs(blk).max() <= 1e-12 * np.abs(vd).max()
+        R = oracle.scalar_rows(V, T, H.perm[a0:a1])[:, :, H.perm[s0:s1]]
+        for kern in flagged:
+            hits += 1
+            assert H.rank(b, kern) == 0
+            assert np.abs(R[kern]).max() <= 1e-12 * np.abs(R[0]).max()
+        for kern in set(range(1, 7)) - set(flagged):
+            assert H.rank(b, kern) > 0
     assert hits > 0
 
 
