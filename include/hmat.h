@@ -43,6 +43,9 @@ extern "C" {
 #define HM_BF16 2 /* factors BF16 with per-column FP32 scales, near field FP32, FP32 acc. */
 #define HM_FP16 3 /* factors FP16 with per-column FP32 scales, near field FP32, FP32 acc. */
 
+/* largest leaf size b_min of a cluster tree (see hm_build_cluster_tree) */
+#define HM_MAX_LEAF 336
+
 typedef struct hm_tree hm_tree;     /* cluster tree + block partition (host) */
 typedef struct hm_matrix hm_matrix; /* assembled H-matrix resident on the device */
 
@@ -65,12 +68,15 @@ typedef struct {
  *   verts  host, nv x 3 float64, row-major vertex coordinates
  *   tris   host, nt x 3 int32, vertex ids of each flat triangle tau_i
  *          (Section 4.2); the collocation point of tau_i is its centroid
- *   leaf   b_min >= 1; eta > 0
+ *   leaf   b_min, 1 <= b_min <= HM_MAX_LEAF (the streamed product keeps the
+ *          rows of one leaf in one CTA and one near-field column of a leaf,
+ *          6 x 336 FP64 values, in one 16 KB shared-memory stage); eta > 0
  *   out    receives a new tree (NULL on error)
  * Split rule: longest axis of the box of the collocation points, median of a
  * stable sort by (coordinate, triangle id), first son floor(n/2).
  * Errors: HM_EINVAL (nv < 3, nt < 1, vertex id out of range, degenerate
- * triangle, leaf < 1, eta <= 0, non-finite coordinate), HM_ENOMEM.
+ * triangle, leaf outside 1..HM_MAX_LEAF, eta <= 0, non-finite coordinate),
+ * HM_ENOMEM.
  * ------------------------------------------------------------------------- */
 int hm_build_cluster_tree(const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
                           int32_t leaf, double eta, hm_tree** out);

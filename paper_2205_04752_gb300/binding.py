@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libhmat.so")
 HM_OK, HM_EINVAL, HM_ENOMEM, HM_ENOTCONV, HM_ETIMEOUT, HM_EDEVICE, HM_ERANK = 0, -1, -2, -3, -4, -5, -6
 FP64, FP32, BF16, FP16 = 0, 1, 2, 3
 FORMS = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "fp16": FP16}
+MAX_LEAF = 336  # HM_MAX_LEAF
 
 # every symbol the header declares
 SYMBOLS = (

@@ -1056,7 +1056,13 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
             std::iota(order.begin(), order.end(), 0);
             std::stable_sort(order.begin(), order.end(),
                              [&](int32_t a, int32_t b) { return bytes[(size_t)a] > bytes[(size_t)b]; });
-            if ((rc = upload(H, H.d_leaf_order, order.data(), order.size() * 4))) return rc;
+            std::vector<int2> work(order.size());
+            for (size_t q = 0; q < order.size(); ++q) work[q] = make_int2(0, order[q]);
+            H.leaf_order_h = order;
+            H.leaf_bytes_h = bytes;
+            if ((rc = upload(H, H.d_work, work.data(), work.size() * sizeof(int2)))) return rc;
+            const int64_t pp[2] = {0, M};
+            if ((rc = upload(H, H.d_pos_prefix, pp, sizeof pp))) return rc;
         }
         if ((rc = upload(H, H.d_leaf, leafv.data(), leafv.size() * 4))) return rc;
         if ((rc = upload(H, H.d_lf_base, lf_base.data(), lf_base.size() * 8))) return rc;
@@ -1093,13 +1099,15 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
                 r.s0 = bk.s0;
                 r.n = bk.n;
                 r.col0 = (int32_t)H.coff_h[(size_t)b * 7];
-                r.C = 0;
+                r.mesh = 0;
+                int32_t Csum = 0;
                 for (int k = 0; k < 7; ++k) {
                     const int32_t kk = H.rank_h[(size_t)(b * 7 + k)];
                     if (kk > 255) return fail(HM_EINVAL, "rank %d above 255 is not supported", kk);
                     r.kpack |= (uint64_t)kk << (8 * k);
-                    r.C += kk;
+                    Csum += kk;
                 }
+                r.C = (int16_t)Csum;
                 vb_base[(size_t)b] = vr;
                 r.vbase = vr;
                 vr += (int64_t)bk.n * ((r.C + 7) & ~int64_t(7));
@@ -1118,13 +1126,10 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
     H.max_rhs = H.prm.max_rhs;
     if ((rc = dalloc(H, H.xg, (size_t)H.max_rhs * 4 * M * 8))) return rc;
     if ((rc = dalloc(H, H.wb, (size_t)H.max_rhs * std::max<int64_t>(H.w_total, 1) * 8))) return rc;
-    if ((rc = dalloc(H, H.yn, (size_t)H.max_rhs * 3 * M * 8))) return rc;
     if ((rc = dalloc(H, H.d_counters, (size_t)2 * H.max_rhs * sizeof(int)))) return rc;
     if ((rc = dalloc(H, H.d_err, 64))) return rc;
     HM_CUDA(cudaMemsetAsync(H.d_err.p, 0, 64, s));
-    HM_CUDA(cudaStreamCreateWithFlags(&H.side, cudaStreamNonBlocking));
-    HM_CUDA(cudaEventCreateWithFlags(&H.ev_fork, cudaEventDisableTiming));
-    HM_CUDA(cudaEventCreateWithFlags(&H.ev_join, cudaEventDisableTiming));
+
     if ((rc = dalloc(H, H.xh, (size_t)H.max_rhs * 3 * M * 8))) return rc;
     if ((rc = dalloc(H, H.yh, (size_t)H.max_rhs * 3 * M * 8))) return rc;
     // the FP64 form is always available

@@ -227,7 +227,8 @@ int hm_build_cluster_tree(const double* verts, int64_t nv, const int32_t* tris, 
                                       (long long)nv, (long long)nt);
     if (nt > (int64_t)INT32_MAX / 4)
         return fail(HM_EINVAL, "hm_build_cluster_tree: too many triangles (%lld)", (long long)nt);
-    if (leaf < 1) return fail(HM_EINVAL, "hm_build_cluster_tree: leaf must be >= 1");
+    if (leaf < 1 || leaf > HM_MAX_LEAF)
+        return fail(HM_EINVAL, "hm_build_cluster_tree: leaf must lie in 1..%d", HM_MAX_LEAF);
     if (!(eta > 0.0) || !std::isfinite(eta)) return fail(HM_EINVAL, "hm_build_cluster_tree: eta must be > 0");
     for (int64_t i = 0; i < 3 * nv; ++i)
         if (!std::isfinite(verts[i]))
@@ -333,7 +334,12 @@ int hm_set_material(hm_matrix* H, double E, double nu)
     if (!(nu > 0.0 && nu < 0.5)) return fail(HM_EINVAL, "hm_set_material: nu must lie in (0, 1/2)");
     H->E = E;
     H->nu = nu;
-    return HM_OK;
+    for (int f = 0; f < 4; ++f)
+        if (H->packed[f]) {
+            int rc = write_mesh_table(*H, f, nullptr);
+            if (rc) return rc;
+        }
+    return cuda_check(cudaDeviceSynchronize(), "hm_set_material");
 }
 
 int hm_get_stats(const hm_matrix* H, hm_stats* st)
@@ -420,6 +426,7 @@ int hm_check(const hm_matrix* H)
     if (flag) {
         const int zero = 0;
         HM_CUDA(cudaMemcpy(H->d_err.p, &zero, sizeof(int), cudaMemcpyHostToDevice));
+        if (flag == 2) return fail(HM_EINVAL, "hm_check: an earlier product met a leaf larger than a stage");
         return fail(HM_ETIMEOUT, "hm_check: a bounded device wait ran out in an earlier product");
     }
     return HM_OK;
@@ -455,19 +462,15 @@ void hm_matrix_destroy(hm_matrix* H)
 {
     if (!H) return;
     for (cudaEvent_t e : H->prof_ev) cudaEventDestroy(e);
-    if (H->ev_fork) cudaEventDestroy(H->ev_fork);
-    if (H->ev_join) cudaEventDestroy(H->ev_join);
-    if (H->side) {
-        cudaStreamSynchronize(H->side);
-        cudaStreamDestroy(H->side);
-    }
+
     hm::DevBuf* bufs[] = {&H->d_perm, &H->d_adm, &H->d_near, &H->d_rank, &H->d_uoff, &H->d_voff,
                           &H->d_coff, &H->d_noff, &H->d_leaf, &H->d_lf_base, &H->d_lf_ptr,
                           &H->d_lf_items, &H->d_lf_src, &H->d_ln_base, &H->d_ln_ptr, &H->d_ln_items,
-                          &H->d_ln_src, &H->d_vb_base, &H->d_fwd_all, &H->d_leaf_order, &H->d_counters, &H->d_err, &H->U64, &H->V64, &H->N64,
+                          &H->d_ln_src, &H->d_vb_base, &H->d_fwd_all, &H->d_work, &H->d_pos_prefix, &H->d_mesh[0], &H->d_mesh[1], &H->d_mesh[2],
+                          &H->d_mesh[3], &H->d_counters, &H->d_err, &H->U64, &H->V64, &H->N64,
                           &H->Ul[0], &H->Ul[1], &H->Ul[2], &H->Ul[3], &H->Vr[0], &H->Vr[1],
                           &H->Vr[2], &H->Vr[3], &H->Nl64, &H->Nl32, &H->SU, &H->SV, &H->xg, &H->wb,
-                          &H->yn, &H->xh, &H->yh};
+                          &H->xh, &H->yh};
     // the assembly stream may be gone by now: drain the device and release
     // on the legacy default stream
     cudaDeviceSynchronize();

@@ -93,12 +93,54 @@ struct NearSrc {
     int32_t n, pad;
 };
 // one admissible block of the far-field forward pass (32 bytes): column
-// cluster start and size, first global factor column, total rank, offset of
-// its row-major V, and the rank of each of the seven kernels
+// cluster start and size, first factor column, total rank, mesh, offset of its
+// row-major V, and the rank of each of the seven kernels
 struct FwdRec {
-    int32_t s0, n, col0, C;
+    int32_t s0, n, col0;
+    int16_t C;
+    uint16_t mesh;
     int64_t vbase;
     uint64_t kpack;  // rank of kernel q in bits 8q .. 8q+7
+};
+
+// Device-side description of one mesh taking part in a product (a single
+// matrix is a product over one mesh; a batch concatenates several).  Stream
+// and table pointers are the mesh's own; the vectors live in shared arrays:
+// x and y rows hold the mesh's dofs at xoff, the gathered x (4-vectors) at
+// xgoff and w (4-vectors) at woff.
+struct MeshDev {
+    const void* Ul;   // leaf-major U stream (factor type of the form)
+    const void* Vr;   // row-major V of every block
+    const void* Nl;   // leaf-major near-field stream
+    const float* SU;  // per-column U scales (16-bit forms) or null
+    const int32_t* leaf;
+    const int64_t* lf_base;
+    const int32_t* lf_ptr;
+    const LeafFarItem* lf_items;
+    const int64_t* ln_base;
+    const int32_t* ln_ptr;
+    const LeafNearItem* ln_items;
+    const int32_t* perm;
+    int64_t xoff, xgoff, woff;
+    int32_t M, max_leaf;
+    double c1, c2;
+};
+
+// A product over one or more meshes: device tables and work lists.
+struct Plan {
+    const MeshDev* meshes;      // nmesh entries (form specific)
+    MeshDev mesh0;              // host copy of the only mesh when nmesh == 1
+    int32_t nmesh;
+    const int64_t* pos_prefix;  // nmesh + 1: cluster positions before each mesh
+    int64_t npos;
+    const FwdRec* fwd;          // nbig blocks with |s| > 128, then nsmall others
+    int64_t nbig, nsmall;
+    const int2* work;           // (mesh, leaf) in processing order
+    int64_t nwork;
+    int32_t max_leaf;
+    int* counters;              // >= nrhs ints of device memory
+    int* err;
+    int64_t xg_ld, w_ld;        // per-RHS stride of the gathered x and of w (elements)
 };
 
 
@@ -136,14 +178,15 @@ struct hm_matrix {
     hm::DevBuf d_fwd_all;                // FwdRec in stream order: |s| > 128 first, then the rest
     std::vector<hm::FwdRec> fwd_h;       // host copy of d_fwd_all
 
-    hm::DevBuf d_leaf_order;             // int32 nleaves: leaves by decreasing streamed bytes
-    hm::DevBuf d_counters;               // int32 max_rhs: work counters of the streamed kernel
+    hm::DevBuf d_work;                   // int2 (0, leaf): leaves by decreasing streamed bytes
+    std::vector<int32_t> leaf_order_h;   // host copy of the order
+    std::vector<int64_t> leaf_bytes_h;   // streamed elements per leaf (U + near)
+    hm::DevBuf d_pos_prefix;             // int64 {0, M}
+    hm::DevBuf d_mesh[4];                // MeshDev of this matrix, per packed form
+    hm::DevBuf d_counters;               // int32 2*max_rhs: work counters of the streamed kernel
     hm::DevBuf d_err;                    // int32: set by a device wait that ran out
     int64_t n_fwd_small = 0, n_fwd_big = 0;
     int64_t ul_total = 0, nl_total = 0, vr_total = 0;
-    // the near field runs on a second stream, concurrently with the far field
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     // FP64 factor and near arenas in block order (ACA output, export)
     hm::DevBuf U64, V64, N64;
@@ -157,7 +200,6 @@ struct hm_matrix {
     int32_t max_rhs = 32;
     hm::DevBuf xg;  // max_rhs x M x 4 doubles (gathered x, cluster order, padded 4-vectors)
     hm::DevBuf wb;  // max_rhs x w_total doubles (one 4-vector per factor column)
-    hm::DevBuf yn;  // max_rhs x 3 x M doubles (near-field part of y, cluster order)
     hm::DevBuf xh, yh;  // device staging for hm_matvec_host (max_rhs x 3M doubles)
 
     // measurement hook (hm_profile_enable / hm_profile_read)
@@ -167,20 +209,28 @@ struct hm_matrix {
 };
 
 namespace hm {
-// workspace of one product: gathered x (nrhs x M x 4), the far-field w
-// vectors (nrhs x c_total x 4) and the near-field part of y (nrhs x 3 x M),
-// all in the form's accumulation type
+// workspace of one product: gathered x (nrhs x M x 4) and the far-field w
+// vectors (nrhs x c_total x 4), in the form's accumulation type, and nrhs
+// work counters of the streamed leaf kernel
 struct Scratch {
     void* xg;
     void* w;
-    void* yn;
+    int* counters;
     bool profile;  // record the measurement-hook events
 };
 int matvec_device_scratch(const hm_matrix& H, const double* x, double* y, int32_t nrhs,
                           int64_t ld, int32_t form, cudaStream_t s, const Scratch& scr);
-// bytes of Scratch a product of nrhs vectors in `form` needs (xg, yn, w; each
-// part 256-byte aligned)
+// bytes of Scratch a product of nrhs vectors in `form` needs (xg, w and the
+// counters, each part 256-byte aligned)
 size_t matvec_scratch_bytes(const hm_matrix& H, int32_t nrhs, int32_t form);
+// the product over the meshes of a plan: x, y rows of length >= total dofs
+// with leading dimension ld; xg / w workspace with the plan's strides
+int run_product(const Plan& P, int32_t form, const double* x, double* y, int32_t nrhs, int64_t ld,
+                void* xg, void* w, cudaStream_t s, const hm_matrix* prof);
+// (re)write the single-mesh table of a packed form (after packing or a
+// change of material)
+int write_mesh_table(hm_matrix& H, int32_t form, cudaStream_t s);
+MeshDev mesh_desc(const hm_matrix& H, int32_t form);
 // record event `which` (0..3) of the current profiled call, if profiling
 void prof_mark(const hm_matrix& H, int which, cudaStream_t s);
 // kernels launchers (implemented in the .cu files)

@@ -15,16 +15,21 @@
 //      of 8) over all admissible blocks t x s with t containing tau;
 //   near field per leaf, one contiguous stream: for each near block and
 //      column j, six segments (V_11, V_12, V_13, V_22, V_23, V_33).
-// Three launches, all stream ordered and deterministic (fixed summation order,
-// no atomics):
-//   1. gather   x (original dof order) -> xg[r][p][a] (cluster order, a padded to 4)
-//   2. fwd      one CTA per admissible block: z = V^T xg, and for every factor
-//               column c the three values w[c][a] that multiply column c of U
-//               for output component a (c1, c2 and the column scales folded in)
-//   3. leaf     one CTA per leaf: its threads split the leaf's U and near
-//               streams into contiguous, equal ranges, accumulate U w and the
-//               dense near rows, sum the ranges in a fixed order and scatter y
-//               to the original dof order.
+// The product runs over a Plan: one or more meshes (a single matrix is a plan
+// over one mesh), each with its own streams, tables and material
+// coefficients, whose vectors sit side by side in shared x / y rows.  Three
+// phases, stream ordered and deterministic (fixed summation order, no
+// floating-point atomics):
+//   1. gather   x (original dof order) -> xg[r][p][a] (cluster order of every
+//               mesh, a padded to 4)
+//   2. fwd      one CTA per admissible block with |s| > 128, one warp per
+//               smaller block: z = V^T xg, and for every factor column c the
+//               three values w[c][a] that multiply column c of U for output
+//               component a (c1, c2 and the column scale folded in)
+//   3. leaf     persistent CTAs take (mesh, leaf) items from a counter and
+//               stream the leaf's U and near field through shared memory
+//               (hm_stream.cuh), sum U w and the dense near rows in a fixed
+//               order and scatter y to the original dof order.
 // Forms: FP64 (factors, near field, accumulation); FP32; BF16 / FP16 factors
 // with one FP32 scale per factor column (folded into w) and an FP32 near field.
 #include <cuda_bf16.h>
@@ -133,15 +138,31 @@ __device__ __forceinline__ void kern_pq(int kern, int& p, int& q)
     q = kern == 0 ? -1 : (kern <= 3 ? kern - 1 : (kern <= 5 ? kern - 3 : 2));
 }
 
-template <class TA>
-__global__ void gather_kernel(int M, int nrhs, const double* __restrict__ x, int64_t ld,
-                              const int32_t* __restrict__ perm, TA* __restrict__ xg)
+// mesh of cluster position p of the product: the largest m with pos_prefix[m] <= p
+__device__ __forceinline__ int mesh_of(const int64_t* __restrict__ pos_prefix, int nmesh, int64_t p)
 {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    int r = blockIdx.y;
-    if (p >= M || r >= nrhs) return;
-    size_t src = (size_t)r * ld + 3 * (size_t)perm[p];
-    TA* d = xg + ((size_t)r * M + p) * 4;
+    int lo = 0, hi = nmesh - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pos_prefix[mid] <= p) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// x (original dof order of every mesh) -> xg[r][p][a] (cluster order, a padded to 4)
+template <class TA>
+__global__ void gather_kernel(const MeshDev* __restrict__ meshes, int nmesh, const int64_t* __restrict__ pos_prefix,
+                              int64_t npos, const double* __restrict__ x, int64_t ld, TA* __restrict__ xg,
+                              int64_t xg_ld)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (p >= npos) return;
+    const int m = mesh_of(pos_prefix, nmesh, p);
+    const MeshDev& md = meshes[m];
+    const size_t src = (size_t)r * ld + md.xoff + 3 * (size_t)md.perm[p - pos_prefix[m]];
+    TA* d = xg + (size_t)r * xg_ld + (size_t)p * 4;
 #pragma unroll
     for (int a = 0; a < 3; ++a) d[a] = (TA)x[src + a];
     d[3] = (TA)0;
@@ -149,10 +170,10 @@ __global__ void gather_kernel(int M, int nrhs, const double* __restrict__ x, int
 
 // ---------------------------------------------------------------- phase 1
 // w for every factor column c of block `rec` from its reduced z = V^T x
-// (three components), with c1 / c2 and the column scales folded in
+// (three components), with c1 / c2 and the column scale of U folded in
 template <class TA>
 __device__ __forceinline__ void write_w(const FwdRec& rec, int c, const TA* z, const float* __restrict__ SU,
-                                        const float* __restrict__ SV, TA* __restrict__ wr, TA c1, TA c2)
+                                        TA* __restrict__ wr, TA c1, TA c2)
 {
     int kern = 0, l = c;
     for (;;) {
@@ -162,18 +183,17 @@ __device__ __forceinline__ void write_w(const FwdRec& rec, int c, const TA* z, c
         ++kern;
     }
     const int64_t col = (int64_t)rec.col0 + c;
-    const TA sv = SV ? (TA)SV[col] : (TA)1;
     const TA su = SU ? (TA)SU[col] : (TA)1;
     TA o[3];
     if (kern == 0) {
-        const TA f = c1 * su * sv;
+        const TA f = c1 * su;
         o[0] = f * z[0];
         o[1] = f * z[1];
         o[2] = f * z[2];
     } else {
         int p, pq;
         kern_pq(kern, p, pq);
-        const TA f = c2 * su * sv;
+        const TA f = c2 * su;
         o[0] = o[1] = o[2] = (TA)0;
         o[p] = f * z[pq];
         if (p != pq) o[pq] = f * z[p];
@@ -184,26 +204,46 @@ __device__ __forceinline__ void write_w(const FwdRec& rec, int c, const TA* z, c
     wr[col * 4 + 3] = (TA)0;
 }
 
+// pointers of block `rec` of its mesh for right-hand side r.  ONE: the plan
+// has a single mesh, passed by value as a kernel parameter (no dependent load
+// of the mesh table before the first load of V).
+template <class TF, class TA, bool ONE>
+struct FwdArgs {
+    const TF* Vb;
+    const TA* x0;
+    TA* wr;
+    const float* SU;
+    TA c1, c2;
+    __device__ __forceinline__ FwdArgs(const FwdRec& rec, const MeshDev& m0, const MeshDev* __restrict__ meshes,
+                                       const TA* xg, TA* w, int r, int64_t xg_ld, int64_t w_ld)
+    {
+        const MeshDev& md = ONE ? m0 : meshes[rec.mesh];
+        Vb = static_cast<const TF*>(md.Vr) + rec.vbase;
+        x0 = xg + (size_t)r * xg_ld + md.xgoff + (size_t)rec.s0 * 4;
+        wr = w + (size_t)r * w_ld + md.woff;
+        SU = md.SU;
+        c1 = (TA)md.c1;
+        c2 = (TA)md.c2;
+    }
+};
+
 // Small blocks (|s| <= 128): one warp per block.  Lane (q, g): column vector
 // q (VEC consecutive columns of the row-major V), rows g, g + G, ...
-template <class TF, class TA>
+template <class TF, class TA, bool ONE>
 __global__ void __launch_bounds__(kThreads) fwd_small_kernel(
-    const FwdRec* __restrict__ recs, int nrec, const TF* __restrict__ Vr, const float* __restrict__ SU,
-    const float* __restrict__ SV, const TA* __restrict__ xg, TA* __restrict__ w, int M, int64_t ctot,
-    TA c1, TA c2)
+    const FwdRec* __restrict__ recs, int64_t nrec, const __grid_constant__ MeshDev m0,
+    const MeshDev* __restrict__ meshes, const TA* __restrict__ xg, TA* __restrict__ w, int64_t xg_ld, int64_t w_ld)
 {
     constexpr int VEC = Vec16<TF, TA>::N;
     __shared__ TA red[kThreads / 32][32 * VEC * 3];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r = blockIdx.y;
-    const int bi = blockIdx.x * (kThreads / 32) + warp;
+    const int64_t bi = (int64_t)blockIdx.x * (kThreads / 32) + warp;
     if (bi >= nrec) return;
-    TA* wr = w + (size_t)r * 4 * ctot;
     TA* rw = red[warp];
     const FwdRec rec = recs[bi];
+    const FwdArgs<TF, TA, ONE> fa(rec, m0, meshes, xg, w, r, xg_ld, w_ld);
     const int Cp = (rec.C + 7) & ~7, Q = Cp / VEC;
-    const TF* Vb = Vr + rec.vbase;
-    const TA* x0 = xg + ((size_t)r * M + rec.s0) * 4;
     for (int cq0 = 0; cq0 < Q; cq0 += 32) {
         const int QT = min(Q - cq0, 32), G = 32 / QT;
         const int q = lane % QT, g = lane / QT;
@@ -211,13 +251,13 @@ __global__ void __launch_bounds__(kThreads) fwd_small_kernel(
 #pragma unroll
         for (int e = 0; e < VEC; ++e) acc[e][0] = acc[e][1] = acc[e][2] = (TA)0;
         if (g < G) {
-            const TF* vp = Vb + (size_t)(cq0 + q) * VEC;
+            const TF* vp = fa.Vb + (size_t)(cq0 + q) * VEC;
 #pragma unroll 4
             for (int j = g; j < rec.n; j += G) {
                 TA v[VEC];
                 Vec16<TF, TA>::load(vp + (size_t)j * Cp, v);
                 TA xa, xb, xc;
-                load3(x0 + (size_t)j * 4, xa, xb, xc);
+                load3(fa.x0 + (size_t)j * 4, xa, xb, xc);
 #pragma unroll
                 for (int e = 0; e < VEC; ++e) {
                     acc[e][0] += v[e] * xa;
@@ -240,7 +280,7 @@ __global__ void __launch_bounds__(kThreads) fwd_small_kernel(
                     for (int gg = 0; gg < G; ++gg)
 #pragma unroll
                         for (int a = 0; a < 3; ++a) z[a] += rw[((gg * QT + q) * VEC + e) * 3 + a];
-                    write_w<TA>(rec, c, z, SU, SV, wr, c1, c2);
+                    write_w<TA>(rec, c, z, fa.SU, fa.wr, fa.c1, fa.c2);
                 }
             }
         }
@@ -250,20 +290,17 @@ __global__ void __launch_bounds__(kThreads) fwd_small_kernel(
 
 // Larger blocks: one CTA per block.  Thread (q, g) as above with G row
 // groups over the whole CTA, reduced through shared memory.
-template <class TF, class TA>
+template <class TF, class TA, bool ONE>
 __global__ void __launch_bounds__(kThreads) fwd_big_kernel(
-    const FwdRec* __restrict__ recs, const TF* __restrict__ Vr, const float* __restrict__ SU,
-    const float* __restrict__ SV, const TA* __restrict__ xg, TA* __restrict__ w, int M, int64_t ctot,
-    TA c1, TA c2)
+    const FwdRec* __restrict__ recs, const __grid_constant__ MeshDev m0, const MeshDev* __restrict__ meshes,
+    const TA* __restrict__ xg, TA* __restrict__ w, int64_t xg_ld, int64_t w_ld)
 {
     constexpr int VEC = Vec16<TF, TA>::N;
     __shared__ TA red[kThreads * VEC * 3];
     const FwdRec rec = recs[blockIdx.x];
     const int r = blockIdx.y;
+    const FwdArgs<TF, TA, ONE> fa(rec, m0, meshes, xg, w, r, xg_ld, w_ld);
     const int Cp = (rec.C + 7) & ~7, Q = Cp / VEC;
-    const TF* Vb = Vr + rec.vbase;
-    const TA* x0 = xg + ((size_t)r * M + rec.s0) * 4;
-    TA* wr = w + (size_t)r * 4 * ctot;
     const int tid = threadIdx.x;
     for (int cq0 = 0; cq0 < Q; cq0 += kThreads) {
         const int QT = min(Q - cq0, kThreads);
@@ -273,13 +310,13 @@ __global__ void __launch_bounds__(kThreads) fwd_big_kernel(
 #pragma unroll
         for (int e = 0; e < VEC; ++e) acc[e][0] = acc[e][1] = acc[e][2] = (TA)0;
         if (g < G) {
-            const TF* vp = Vb + (size_t)(cq0 + q) * VEC;
+            const TF* vp = fa.Vb + (size_t)(cq0 + q) * VEC;
 #pragma unroll 4
             for (int j = g; j < rec.n; j += G) {
                 TA v[VEC];
                 Vec16<TF, TA>::load(vp + (size_t)j * Cp, v);
                 TA xa, xb, xc;
-                load3(x0 + (size_t)j * 4, xa, xb, xc);
+                load3(fa.x0 + (size_t)j * 4, xa, xb, xc);
 #pragma unroll
                 for (int e = 0; e < VEC; ++e) {
                     acc[e][0] += v[e] * xa;
@@ -303,186 +340,7 @@ __global__ void __launch_bounds__(kThreads) fwd_big_kernel(
             for (int gg = 0; gg < G; ++gg)
 #pragma unroll
                 for (int a = 0; a < 3; ++a) z[a] += red[(gg * QT * VEC + idx) * 3 + a];
-            write_w<TA>(rec, c, z, SU, SV, wr, c1, c2);
-        }
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------- phase 2
-// Rows of a leaf are handled in chunks of at most kThreads row blocks of R
-// rows (one chunk unless the leaf has more than kThreads * R rows).  Thread
-// (p, h): rows of row block p, group h of H = kThreads / P; group h takes the
-// contiguous range [S h / H, S (h+1) / H) of the leaf's S stream entries.
-
-// near field: one CTA per (leaf, rhs); yn[r][a][cluster position] =
-// sum over near blocks of the dense 3 x 3 Kelvin blocks c1 delta V_Delta + c2 V_ab
-template <class TN, class TA>
-__global__ void __launch_bounds__(kThreads) near_leaf_kernel(
-    const int32_t* __restrict__ leaf, const int64_t* __restrict__ ln_base,
-    const int32_t* __restrict__ ln_ptr, const LeafNearItem* __restrict__ ln_items,
-    const TN* __restrict__ Nl, const TA* __restrict__ xg, TA* __restrict__ yn, int M, TA c1, TA c2)
-{
-    constexpr int R = Vec16<TN, TA>::N;
-    __shared__ TA red[kThreads * R * 3];
-    const int lf = blockIdx.x, r = blockIdx.y;
-    const int t0 = leaf[2 * lf], mt = leaf[2 * lf + 1];
-    const int mp = (mt + 7) & ~7;
-    const int Ptot = mp / R;
-    const int tid = threadIdx.x;
-    const int j0 = ln_ptr[lf], j1 = ln_ptr[lf + 1];
-    const int Sn = ln_items[j1 - 1].col_start;
-    const TA* xr = xg + (size_t)r * 4 * M;
-    for (int pb0 = 0; pb0 < Ptot; pb0 += kThreads) {
-        const int P = min(Ptot - pb0, kThreads);
-        const int H = kThreads / P;
-        const int p = tid % P, h = tid / P;
-        const int row0 = (pb0 + p) * R;
-        TA acc[R][3];
-#pragma unroll
-        for (int e = 0; e < R; ++e) acc[e][0] = acc[e][1] = acc[e][2] = (TA)0;
-        if (h < H) {
-            const int n0 = (int)(((int64_t)Sn * h) / H), n1 = (int)(((int64_t)Sn * (h + 1)) / H);
-            if (n0 < n1) {
-                int lo = j0, hi = j1 - 2;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (ln_items[mid].col_start <= n0) lo = mid;
-                    else hi = mid - 1;
-                }
-                int q = lo;
-                int nxt = ln_items[q + 1].col_start;
-                int sbase = ln_items[q].s0 - ln_items[q].col_start;
-                const TN* base = Nl + ln_base[lf] + row0;
-                for (int g = n0; g < n1; ++g) {
-                    while (g >= nxt) {
-                        ++q;
-                        nxt = ln_items[q + 1].col_start;
-                        sbase = ln_items[q].s0 - ln_items[q].col_start;
-                    }
-                    const int sj = sbase + g;
-                    TA x0, x1, x2;
-                    load3(xr + (size_t)sj * 4, x0, x1, x2);
-                    const TN* e0 = base + (size_t)g * 6 * mp;
-                    TA v11[R], v12[R], v13[R], v22[R], v23[R], v33[R];
-                    Vec16<TN, TA>::load(e0, v11);
-                    Vec16<TN, TA>::load(e0 + mp, v12);
-                    Vec16<TN, TA>::load(e0 + 2 * mp, v13);
-                    Vec16<TN, TA>::load(e0 + 3 * mp, v22);
-                    Vec16<TN, TA>::load(e0 + 4 * mp, v23);
-                    Vec16<TN, TA>::load(e0 + 5 * mp, v33);
-#pragma unroll
-                    for (int e = 0; e < R; ++e) {
-                        const TA vd = c1 * (v11[e] + v22[e] + v33[e]);
-                        acc[e][0] += vd * x0 + c2 * (v11[e] * x0 + v12[e] * x1 + v13[e] * x2);
-                        acc[e][1] += vd * x1 + c2 * (v12[e] * x0 + v22[e] * x1 + v23[e] * x2);
-                        acc[e][2] += vd * x2 + c2 * (v13[e] * x0 + v23[e] * x1 + v33[e] * x2);
-                    }
-                }
-            }
-#pragma unroll
-            for (int e = 0; e < R; ++e)
-#pragma unroll
-                for (int a = 0; a < 3; ++a) red[((h * P + p) * R + e) * 3 + a] = acc[e][a];
-        }
-        __syncthreads();
-        const int rows = min(P * R, mt - pb0 * R);
-        for (int idx = tid; idx < rows * 3; idx += kThreads) {
-            const int i = idx / 3, a = idx - 3 * i;
-            TA sum = (TA)0;
-            for (int g = 0; g < H; ++g) sum += red[((g * P) * R + i) * 3 + a];
-            yn[((size_t)r * 3 + a) * M + t0 + pb0 * R + i] = sum;
-        }
-        __syncthreads();
-    }
-}
-
-// far field: one CTA per (leaf, rhs); y = sum over the leaf's U segments of
-// U_seg[rows] * w[col(seg)] plus the near-field part yn, scattered to the
-// original dof order
-template <class TF, class TA>
-__global__ void __launch_bounds__(kThreads) far_leaf_kernel(
-    const int32_t* __restrict__ leaf, const int64_t* __restrict__ lf_base,
-    const int32_t* __restrict__ lf_ptr, const LeafFarItem* __restrict__ lf_items,
-    const TF* __restrict__ Ul, const TA* __restrict__ w, const TA* __restrict__ yn,
-    const int32_t* __restrict__ perm, double* __restrict__ y, int64_t ld, int M, int64_t ctot)
-{
-    constexpr int R = Vec16<TF, TA>::N;
-    constexpr int U4 = 4;  // segments in flight per thread
-    __shared__ TA red[kThreads * R * 3];
-    const int lf = blockIdx.x, r = blockIdx.y;
-    const int t0 = leaf[2 * lf], mt = leaf[2 * lf + 1];
-    const int mp = (mt + 7) & ~7;
-    const int Ptot = mp / R;
-    const int tid = threadIdx.x;
-    const int i0 = lf_ptr[lf], i1 = lf_ptr[lf + 1];
-    const int S = lf_items[i1 - 1].seg_start;
-    const TA* wr = w + (size_t)r * 4 * ctot;
-    for (int pb0 = 0; pb0 < Ptot; pb0 += kThreads) {
-        const int P = min(Ptot - pb0, kThreads);
-        const int H = kThreads / P;
-        const int p = tid % P, h = tid / P;
-        const int row0 = (pb0 + p) * R;
-        TA acc[R][3];
-#pragma unroll
-        for (int e = 0; e < R; ++e) acc[e][0] = acc[e][1] = acc[e][2] = (TA)0;
-        if (h < H) {
-            const int g0 = (int)(((int64_t)S * h) / H), g1 = (int)(((int64_t)S * (h + 1)) / H);
-            if (g0 < g1) {
-                int lo = i0, hi = i1 - 2;  // item containing g0: last with seg_start <= g0
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (lf_items[mid].seg_start <= g0) lo = mid;
-                    else hi = mid - 1;
-                }
-                int q = lo;
-                int nxt = lf_items[q + 1].seg_start;
-                int cbase = lf_items[q].col - lf_items[q].seg_start;
-                const TF* base = Ul + lf_base[lf] + row0;
-                for (int g = g0; g < g1; g += U4) {
-                    TA u[U4][R];
-                    int col[U4];
-#pragma unroll
-                    for (int t = 0; t < U4; ++t) {
-                        if (g + t < g1) {
-                            while (g + t >= nxt) {
-                                ++q;
-                                nxt = lf_items[q + 1].seg_start;
-                                cbase = lf_items[q].col - lf_items[q].seg_start;
-                            }
-                            col[t] = cbase + g + t;
-                            Vec16<TF, TA>::load(base + (size_t)(g + t) * mp, u[t]);
-                        }
-                    }
-#pragma unroll
-                    for (int t = 0; t < U4; ++t) {
-                        if (g + t < g1) {
-                            TA w0, w1, w2;
-                            load3(wr + (size_t)col[t] * 4, w0, w1, w2);
-#pragma unroll
-                            for (int e = 0; e < R; ++e) {
-                                acc[e][0] += u[t][e] * w0;
-                                acc[e][1] += u[t][e] * w1;
-                                acc[e][2] += u[t][e] * w2;
-                            }
-                        }
-                    }
-                }
-            }
-#pragma unroll
-            for (int e = 0; e < R; ++e)
-#pragma unroll
-                for (int a = 0; a < 3; ++a) red[((h * P + p) * R + e) * 3 + a] = acc[e][a];
-        }
-        __syncthreads();
-        const int rows = min(P * R, mt - pb0 * R);
-        for (int idx = tid; idx < rows * 3; idx += kThreads) {
-            const int i = idx / 3, a = idx - 3 * i;
-            const int pos = t0 + pb0 * R + i;
-            TA sum = (TA)0;
-            for (int g = 0; g < H; ++g) sum += red[((g * P) * R + i) * 3 + a];
-            sum += yn[((size_t)r * 3 + a) * M + pos];
-            y[(size_t)r * ld + 3 * (size_t)perm[pos] + a] = (double)sum;
+            write_w<TA>(rec, c, z, fa.SU, fa.wr, fa.c1, fa.c2);
         }
         __syncthreads();
     }
@@ -615,84 +473,78 @@ int dalloc(hm_matrix& H, DevBuf& d, size_t bytes)
     return HM_OK;
 }
 
+// per-device launch data of the streamed leaf kernel of one form
+struct StreamLaunch {
+    int ctas_per_sm = 0;
+    int nsm = 0;
+};
+
 template <class TF, class TN, class TA>
-int run_matvec(const hm_matrix& H, int form, const TN* N, const float* SU, const float* SV,
-               const double* x, double* y, int nrhs, int64_t ld, cudaStream_t s, const Scratch& scr)
+int stream_launch(StreamLaunch& out)
 {
-    const int M = (int)H.M;
-    TA* xg = static_cast<TA*>(scr.xg);
-    TA* w = static_cast<TA*>(scr.w);
-    TA* yn = static_cast<TA*>(scr.yn);
-    const TF* Ul = H.Ul[form].as<TF>();
-    const TF* Vr = H.Vr[form].as<TF>();
-    const TA c1 = (TA)((1.0 + H.nu) * (3.0 - 4.0 * H.nu) / (2.0 * H.E * (1.0 - H.nu)));
-    const TA c2 = (TA)((1.0 + H.nu) / (2.0 * H.E * (1.0 - H.nu)));
-    const unsigned nr = (unsigned)nrhs;
-    dim3 gg((unsigned)((M + 255) / 256), nr);
-    if (scr.profile) prof_mark(H, 0, s);
-    gather_kernel<TA><<<gg, 256, 0, s>>>(M, nrhs, x, ld, H.d_perm.as<int32_t>(), xg);
-    HM_CUDA(cudaGetLastError());
-    if (scr.profile) prof_mark(H, 1, s);
-    // the streamed per-leaf kernel handles leaves of up to kConsumers * R rows
+    constexpr int kMaxDevices = 64;
+    static StreamLaunch cache[kMaxDevices];  // per template instance and device
+    int dev = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    if (dev < kMaxDevices && cache[dev].nsm > 0) {
+        out = cache[dev];
+        return HM_OK;
+    }
+    auto kern = stream::leaf_stream_kernel<TF, TN, TA>;
+    const size_t smem = stream::smem_bytes<TA>(stream::Smem16<TF, TA>::N);
+    HM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    StreamLaunch l;
+    HM_CUDA(cudaDeviceGetAttribute(&l.nsm, cudaDevAttrMultiProcessorCount, dev));
+    HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&l.ctas_per_sm, kern, stream::kThreads, smem));
+    l.ctas_per_sm = std::max(l.ctas_per_sm, 1);
+    if (dev < kMaxDevices) cache[dev] = l;
+    out = l;
+    return HM_OK;
+}
+
+// The three phases of the product over every mesh of the plan.
+template <class TF, class TN, class TA>
+int run_product_t(const Plan& P, const double* x, double* y, int nrhs, int64_t ld, TA* xg, TA* w,
+                  cudaStream_t s, const hm_matrix* prof)
+{
     constexpr int Rs = stream::Smem16<TF, TA>::N;
-    const bool streamed = ((H.max_leaf + 7) & ~7) / Rs <= stream::kConsumers;
-    if (!streamed) {
-        // fork: the near field on the side stream, concurrently with the forward pass
-        HM_CUDA(cudaEventRecord(H.ev_fork, s));
-        HM_CUDA(cudaStreamWaitEvent(H.side, H.ev_fork, 0));
-        near_leaf_kernel<TN, TA><<<dim3((unsigned)H.nleaves, nr), kThreads, 0, H.side>>>(
-            H.d_leaf.as<int32_t>(), H.d_ln_base.as<int64_t>(), H.d_ln_ptr.as<int32_t>(),
-            H.d_ln_items.as<LeafNearItem>(), N, xg, yn, M, c1, c2);
+    const int mpmax = (P.max_leaf + 7) & ~7;
+    if (mpmax / Rs > stream::kConsumers || 6 * mpmax * (int)sizeof(TN) > stream::kStageBytes)
+        return fail(HM_EINVAL, "product: a leaf of %d rows does not fit the streamed kernel", P.max_leaf);
+    const unsigned nr = (unsigned)nrhs;
+    if (prof) prof_mark(*prof, 0, s);
+    if (P.npos > 0) {
+        gather_kernel<TA><<<dim3((unsigned)((P.npos + 255) / 256), nr), 256, 0, s>>>(
+            P.meshes, P.nmesh, P.pos_prefix, P.npos, x, ld, xg, P.xg_ld);
         HM_CUDA(cudaGetLastError());
-        HM_CUDA(cudaEventRecord(H.ev_join, H.side));
     }
-    {
-        const FwdRec* recs = H.d_fwd_all.as<FwdRec>();
-        if (H.n_fwd_big > 0) {
-            fwd_big_kernel<TF, TA><<<dim3((unsigned)H.n_fwd_big, nr), kThreads, 0, s>>>(
-                recs, Vr, SU, SV, xg, w, M, H.c_total, c1, c2);
-            HM_CUDA(cudaGetLastError());
-        }
-        if (H.n_fwd_small > 0) {
-            const unsigned nb = (unsigned)((H.n_fwd_small + kThreads / 32 - 1) / (kThreads / 32));
-            fwd_small_kernel<TF, TA><<<dim3(nb, nr), kThreads, 0, s>>>(
-                recs + H.n_fwd_big, (int)H.n_fwd_small, Vr, SU, SV, xg, w, M, H.c_total, c1, c2);
-            HM_CUDA(cudaGetLastError());
-        }
+    if (prof) prof_mark(*prof, 1, s);
+    const bool one = P.nmesh == 1;
+    const MeshDev m0 = one ? P.mesh0 : MeshDev{};
+    if (P.nbig > 0) {
+        auto kb = one ? fwd_big_kernel<TF, TA, true> : fwd_big_kernel<TF, TA, false>;
+        kb<<<dim3((unsigned)P.nbig, nr), kThreads, 0, s>>>(P.fwd, m0, P.meshes, xg, w, P.xg_ld, P.w_ld);
+        HM_CUDA(cudaGetLastError());
     }
-    if (scr.profile) prof_mark(H, 2, s);
-    if (streamed) {
-        auto kern = stream::leaf_stream_kernel<TF, TN, TA>;
+    if (P.nsmall > 0) {
+        const unsigned nb = (unsigned)((P.nsmall + kThreads / 32 - 1) / (kThreads / 32));
+        auto ks = one ? fwd_small_kernel<TF, TA, true> : fwd_small_kernel<TF, TA, false>;
+        ks<<<dim3(nb, nr), kThreads, 0, s>>>(P.fwd + P.nbig, P.nsmall, m0, P.meshes, xg, w, P.xg_ld, P.w_ld);
+        HM_CUDA(cudaGetLastError());
+    }
+    if (prof) prof_mark(*prof, 2, s);
+    if (P.nwork > 0) {
+        StreamLaunch l;
+        int rc = stream_launch<TF, TN, TA>(l);
+        if (rc) return rc;
         const size_t smem = stream::smem_bytes<TA>(Rs);
-        static bool attr_set = false;  // per template instance
-        if (!attr_set) {
-            HM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr_set = true;
-        }
-        int dev = 0, nsm = 0, occ = 0;
-        HM_CUDA(cudaGetDevice(&dev));
-        HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, stream::kThreads, smem));
-        const int64_t ncta = std::min<int64_t>(H.nleaves, (int64_t)nsm * std::max(occ, 1));
-        HM_CUDA(cudaMemsetAsync(H.d_counters.p, 0, (size_t)nrhs * sizeof(int), s));
-        stream::LeafTables tb{H.d_leaf.as<int32_t>(),    H.d_leaf_order.as<int32_t>(),
-                              H.d_lf_base.as<int64_t>(), H.d_lf_ptr.as<int32_t>(),
-                              H.d_lf_items.as<LeafFarItem>(), H.d_ln_base.as<int64_t>(),
-                              H.d_ln_ptr.as<int32_t>(),  H.d_ln_items.as<LeafNearItem>(),
-                              H.d_perm.as<int32_t>()};
-        kern<<<dim3((unsigned)ncta, nr), stream::kThreads, smem, s>>>(
-            (int)H.nleaves, tb, H.d_counters.as<int>(), H.d_err.as<int>(), Ul, N, xg, w, y, ld, M,
-            H.c_total, c1, c2);
-        HM_CUDA(cudaGetLastError());
-    } else {
-        // join, then the far-field product per leaf (adds the near part)
-        HM_CUDA(cudaStreamWaitEvent(s, H.ev_join, 0));
-        far_leaf_kernel<TF, TA><<<dim3((unsigned)H.nleaves, nr), kThreads, 0, s>>>(
-            H.d_leaf.as<int32_t>(), H.d_lf_base.as<int64_t>(), H.d_lf_ptr.as<int32_t>(),
-            H.d_lf_items.as<LeafFarItem>(), Ul, w, yn, H.d_perm.as<int32_t>(), y, ld, M, H.c_total);
+        const int64_t ncta = std::min<int64_t>(P.nwork, (int64_t)l.nsm * l.ctas_per_sm);
+        HM_CUDA(cudaMemsetAsync(P.counters, 0, (size_t)nrhs * sizeof(int), s));
+        stream::leaf_stream_kernel<TF, TN, TA><<<dim3((unsigned)ncta, nr), stream::kThreads, smem, s>>>(
+            P.work, (int)P.nwork, P.meshes, P.counters, P.err, xg, w, P.xg_ld, P.w_ld, y, ld);
         HM_CUDA(cudaGetLastError());
     }
-    if (scr.profile) prof_mark(H, 3, s);
+    if (prof) prof_mark(*prof, 3, s);
     return HM_OK;
 }
 
@@ -735,46 +587,102 @@ int pack_near(hm_matrix& H, DevBuf& dst, cudaStream_t s)
 
 }  // namespace
 
-int matvec_device_scratch(const hm_matrix& H, const double* x, double* y, int32_t nrhs, int64_t ld,
-                          int32_t form, cudaStream_t s, const Scratch& scr)
+int run_product(const Plan& P, int32_t form, const double* x, double* y, int32_t nrhs, int64_t ld, void* xg,
+                void* w, cudaStream_t s, const hm_matrix* prof)
 {
     switch (form) {
         case HM_FP64:
-            return run_matvec<double, double, double>(H, form, H.Nl64.as<double>(), nullptr, nullptr,
-                                                      x, y, nrhs, ld, s, scr);
+            return run_product_t<double, double, double>(P, x, y, nrhs, ld, static_cast<double*>(xg),
+                                                         static_cast<double*>(w), s, prof);
         case HM_FP32:
-            return run_matvec<float, float, float>(H, form, H.Nl32.as<float>(), nullptr, nullptr, x,
-                                                   y, nrhs, ld, s, scr);
+            return run_product_t<float, float, float>(P, x, y, nrhs, ld, static_cast<float*>(xg),
+                                                      static_cast<float*>(w), s, prof);
         case HM_BF16:
-            return run_matvec<__nv_bfloat16, float, float>(H, form, H.Nl32.as<float>(),
-                                                           H.SU.as<float>(), nullptr, x, y, nrhs, ld,
-                                                           s, scr);
+            return run_product_t<__nv_bfloat16, float, float>(P, x, y, nrhs, ld, static_cast<float*>(xg),
+                                                              static_cast<float*>(w), s, prof);
         case HM_FP16:
-            return run_matvec<__half, float, float>(H, form, H.Nl32.as<float>(), H.SU.as<float>(),
-                                                    nullptr, x, y, nrhs, ld, s, scr);
+            return run_product_t<__half, float, float>(P, x, y, nrhs, ld, static_cast<float*>(xg),
+                                                       static_cast<float*>(w), s, prof);
         default:
-            return fail(HM_EINVAL, "hm_matvec: unknown form %d", form);
+            return fail(HM_EINVAL, "product: unknown form %d", form);
     }
+}
+
+MeshDev mesh_desc(const hm_matrix& H, int32_t form)
+{
+    MeshDev m{};
+    m.Ul = H.Ul[form].p;
+    m.Vr = H.Vr[form].p;
+    m.Nl = form == HM_FP64 ? H.Nl64.p : H.Nl32.p;
+    m.SU = (form == HM_BF16 || form == HM_FP16) ? H.SU.as<float>() : nullptr;
+    m.leaf = H.d_leaf.as<int32_t>();
+    m.lf_base = H.d_lf_base.as<int64_t>();
+    m.lf_ptr = H.d_lf_ptr.as<int32_t>();
+    m.lf_items = H.d_lf_items.as<LeafFarItem>();
+    m.ln_base = H.d_ln_base.as<int64_t>();
+    m.ln_ptr = H.d_ln_ptr.as<int32_t>();
+    m.ln_items = H.d_ln_items.as<LeafNearItem>();
+    m.perm = H.d_perm.as<int32_t>();
+    m.xoff = m.xgoff = m.woff = 0;
+    m.M = (int32_t)H.M;
+    m.max_leaf = H.max_leaf;
+    m.c1 = (1.0 + H.nu) * (3.0 - 4.0 * H.nu) / (2.0 * H.E * (1.0 - H.nu));
+    m.c2 = (1.0 + H.nu) / (2.0 * H.E * (1.0 - H.nu));
+    return m;
+}
+
+int write_mesh_table(hm_matrix& H, int32_t form, cudaStream_t s)
+{
+    int rc;
+    if (!H.d_mesh[form].p)
+        if ((rc = dalloc(H, H.d_mesh[form], sizeof(MeshDev)))) return rc;
+    // a product in flight may still read the old table
+    HM_CUDA(cudaDeviceSynchronize());
+    const MeshDev m = mesh_desc(H, form);
+    HM_CUDA(cudaMemcpy(H.d_mesh[form].p, &m, sizeof m, cudaMemcpyHostToDevice));
+    (void)s;
+    return HM_OK;
+}
+
+int matvec_device_scratch(const hm_matrix& H, const double* x, double* y, int32_t nrhs, int64_t ld,
+                          int32_t form, cudaStream_t s, const Scratch& scr)
+{
+    Plan P{};
+    P.meshes = H.d_mesh[form].as<MeshDev>();
+    P.mesh0 = mesh_desc(H, form);
+    P.nmesh = 1;
+    P.pos_prefix = H.d_pos_prefix.as<int64_t>();
+    P.npos = H.M;
+    P.fwd = H.d_fwd_all.as<FwdRec>();
+    P.nbig = H.n_fwd_big;
+    P.nsmall = H.n_fwd_small;
+    P.work = H.d_work.as<int2>();
+    P.nwork = H.nleaves;
+    P.max_leaf = H.max_leaf;
+    P.counters = scr.counters;
+    P.err = H.d_err.as<int>();
+    P.xg_ld = 4 * H.M;
+    P.w_ld = H.w_total;
+    return run_product(P, form, x, y, nrhs, ld, scr.xg, scr.w, s, scr.profile ? &H : nullptr);
 }
 
 int matvec_device(const hm_matrix& H, const double* x, double* y, int32_t nrhs, int64_t ld,
                   int32_t form, cudaStream_t s)
 {
-    Scratch scr{H.xg.p, H.wb.p, H.yn.p, true};
+    Scratch scr{H.xg.p, H.wb.p, H.d_counters.as<int>(), true};
     return matvec_device_scratch(H, x, y, nrhs, ld, form, s, scr);
 }
 
 size_t matvec_scratch_bytes(const hm_matrix& H, int32_t nrhs, int32_t form)
 {
-    size_t ta = form == HM_FP64 ? 8 : 4;
-    size_t vec = ((size_t)nrhs * 4 * (size_t)H.M * ta + 255) & ~(size_t)255;
-    size_t w = (size_t)nrhs * (size_t)std::max<int64_t>(H.w_total, 1) * ta;
-    return 2 * vec + w;
+    const size_t ta = form == HM_FP64 ? 8 : 4;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    return up((size_t)nrhs * 4 * (size_t)H.M * ta) + up((size_t)nrhs * (size_t)std::max<int64_t>(H.w_total, 1) * ta) +
+           up((size_t)nrhs * sizeof(int));
 }
 
-// units of the streamed forward pass for a form with factor element size `sz`:
-// chunked blocks (the large ones, and any block too big for one stage) and
-// runs of up to 32 consecutive small blocks that fit one stage together
+// the streaming layouts of one form (and the FP32 near field and the column
+// scales it shares with the other reduced forms), then the form's mesh table
 int pack_device(hm_matrix& H, int32_t form, cudaStream_t s)
 {
     int rc;
@@ -782,6 +690,7 @@ int pack_device(hm_matrix& H, int32_t form, cudaStream_t s)
     if (form == HM_FP64) {
         if ((rc = pack_form<double>(H, HM_FP64, nullptr, nullptr, s))) return rc;
         if ((rc = pack_near<double>(H, H.Nl64, s))) return rc;
+        if ((rc = write_mesh_table(H, HM_FP64, s))) return rc;
         H.packed[HM_FP64] = true;
         return HM_OK;
     }
@@ -810,6 +719,7 @@ int pack_device(hm_matrix& H, int32_t form, cudaStream_t s)
             rc = pack_form<__half>(H, HM_FP16, H.SU.as<float>(), nullptr, s);
         if (rc) return rc;
     }
+    if ((rc = write_mesh_table(H, form, s))) return rc;
     H.packed[form] = true;
     return HM_OK;
 }

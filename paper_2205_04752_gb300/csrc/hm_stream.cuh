@@ -3,10 +3,11 @@
 //
 // For every leaf row cluster tau the factor segments (columns of U restricted
 // to the rows of tau) and the near-field columns are contiguous in memory
-// (see hm_matvec.cu).  A persistent CTA takes leaves from a global counter
-// (largest first).  Warp 0 is the producer: for every slot of a ring of
-// kStages shared-memory slots it copies up to kStageBytes of the current
-// leaf's stream and, next to it, the 4-vector each segment needs: w of the
+// (see hm_matvec.cu).  A persistent CTA takes (mesh, leaf) work items from a
+// global counter (largest first, over every mesh of the product).  Warp 0 is
+// the producer: for every slot of a ring of kStages shared-memory slots it
+// copies up to kStageBytes of the current leaf's stream and, next to it, the
+// 4-vector each segment needs: w of the
 // segment's factor column (far field) or x at the segment's source position
 // (near field).  Consecutive segments of one (block, kernel) item have
 // consecutive factor columns (and of one near block consecutive positions),
@@ -38,12 +39,12 @@ constexpr int kMaxSeg = 256;              // segments / columns per stage at mos
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 struct StageMeta {
-    int32_t leaf;   // leaf index (into the leaf table)
+    int32_t leaf;   // leaf index (into its mesh's leaf table)
     int32_t kind;   // 0 far segments, 1 near columns, 2 no more work
     int32_t first;  // first segment / column of the stage within the leaf's stream
     int32_t count;  // segments / columns in the stage
     int32_t last;   // 1 if this is the last stage of the leaf
-    int32_t pad[3];
+    int32_t pad[3]; // pad[0]: mesh of the leaf
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p)
@@ -203,23 +204,11 @@ size_t smem_bytes(int R)
            (size_t)kConsumers * R * 3 * sizeof(TA);
 }
 
-struct LeafTables {
-    const int32_t* leaf;      // (t0, mt) per leaf
-    const int32_t* order;     // leaves in processing order
-    const int64_t* lf_base;
-    const int32_t* lf_ptr;
-    const LeafFarItem* lf_items;
-    const int64_t* ln_base;
-    const int32_t* ln_ptr;
-    const LeafNearItem* ln_items;
-    const int32_t* perm;
-};
-
 template <class TF, class TN, class TA>
 __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
-    int nleaves, LeafTables tb, int* __restrict__ counters, int* __restrict__ err,
-    const TF* __restrict__ Ul, const TN* __restrict__ Nl, const TA* __restrict__ xg,
-    const TA* __restrict__ w, double* __restrict__ y, int64_t ld, int M, int64_t ctot, TA c1, TA c2)
+    const int2* __restrict__ work, int nwork, const MeshDev* __restrict__ meshes, int* __restrict__ counters,
+    int* __restrict__ err, const TA* __restrict__ xg_base, const TA* __restrict__ w_base, int64_t xg_ld,
+    int64_t w_ld, double* __restrict__ y, int64_t ld)
 {
     constexpr int R = Smem16<TF, TA>::N;  // rows per consumer thread: 16 bytes of U
     extern __shared__ __align__(128) unsigned char smem[];
@@ -229,7 +218,6 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
     __shared__ __align__(8) uint64_t full[kStages];
     __shared__ __align__(8) uint64_t empty[kStages];
     __shared__ StageMeta meta[kStages];
-    __shared__ int abort_flag;
 
     const int r = blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -238,7 +226,6 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], kConsumers / 32);
         }
-        abort_flag = 0;
         mbar_fence_init();
     }
     __syncthreads();
@@ -252,7 +239,7 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
         // records); *cur is the item containing `first` and is advanced to
         // the item containing first + count.  vec: the 4-vectors the stream
         // reads (w for the far field, x for the near field).
-        auto emit = [&](int lf, int kind, int first, int count, int last, const void* src,
+        auto emit = [&](int mesh, int lf, int kind, int first, int count, int last, const void* src,
                         uint32_t bytes, const int2* items, int ni, int* cur, const TA* vec) -> bool {
             const int slot = it % kStages;
             if (it >= kStages) {
@@ -265,6 +252,7 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
                 m.first = first;
                 m.count = count;
                 m.last = last;
+                m.pad[0] = mesh;
                 meta[slot] = m;
                 if (kind < 2)
                     mbar_arrive_expect_tx(&full[slot], bytes + (uint32_t)(count * 4 * sizeof(TA)));
@@ -281,7 +269,7 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
                     if (q < ni - 1) a = items[q];
                     int b = __shfl_down_sync(0xffffffffu, a.x, 1);
                     if (lane == 31) b = (q + 1 < ni) ? items[q + 1].x : INT_MAX;
-                    const bool overlap = a.x < end;  // items are sorted; all start < end at most
+                    const bool overlap = a.x < end;  // items are sorted by start
                     if (overlap) {
                         const int g0 = max(a.x, first), g1 = min(b, end);
                         if (g0 < g1)
@@ -290,10 +278,9 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
                     }
                     const unsigned ov = __ballot_sync(0xffffffffu, overlap);
                     const int nov = __popc(ov);  // overlapping items are a prefix of the lanes
-                    const int lastq = q0 + nov - 1;  // last overlapping item
+                    const int lastq = q0 + nov - 1;
                     const int lastb = __shfl_sync(0xffffffffu, b, (nov - 1) & 31);
                     if (nov < 32 || lastb >= end) {
-                        // the item containing `end` (or the last item) is the next cursor
                         *cur = lastb > end ? lastq : lastq + 1;
                         break;
                     }
@@ -306,45 +293,54 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
             ++it;
             return true;
         };
-        const TA* wvec = w + (size_t)r * 4 * ctot;
-        const TA* xvec = xg + (size_t)r * 4 * M;
         for (;;) {
             int idx = 0;
             if (lane == 0) idx = atomicAdd(&counters[r], 1);
             idx = __shfl_sync(0xffffffffu, idx, 0);
-            if (idx >= nleaves || !ok) break;
-            const int lf = tb.order[idx];
-            const int mt = tb.leaf[2 * lf + 1];
+            if (idx >= nwork || !ok) break;
+            const int2 wk = work[idx];
+            const MeshDev& md = meshes[wk.x];
+            const int lf = wk.y;
+            const int mt = md.leaf[2 * lf + 1];
             const int mp = (mt + 7) & ~7;
-            const int fi0 = tb.lf_ptr[lf], fi1 = tb.lf_ptr[lf + 1];
-            const int ni0 = tb.ln_ptr[lf], ni1 = tb.ln_ptr[lf + 1];
-            const int S = tb.lf_items[fi1 - 1].seg_start;
-            const int Sn = tb.ln_items[ni1 - 1].col_start;
+            const int fi0 = md.lf_ptr[lf], fi1 = md.lf_ptr[lf + 1];
+            const int ni0 = md.ln_ptr[lf], ni1 = md.ln_ptr[lf + 1];
+            const int S = md.lf_items[fi1 - 1].seg_start;
+            const int Sn = md.ln_items[ni1 - 1].col_start;
+            const TF* Ul = static_cast<const TF*>(md.Ul);
+            const TN* Nl = static_cast<const TN*>(md.Nl);
+            const TA* wvec = w_base + (size_t)r * w_ld + md.woff;
+            const TA* xvec = xg_base + (size_t)r * xg_ld + md.xgoff;
             const int segB = mp * (int)sizeof(TF);
             const int perF = min(kStageBytes / segB, kMaxSeg);
-            const int2* fitems = reinterpret_cast<const int2*>(tb.lf_items + fi0);
-            const int2* nitems = reinterpret_cast<const int2*>(tb.ln_items + ni0);
+            const int colB = 6 * mp * (int)sizeof(TN);
+            const int perN = min(kStageBytes / colB, kMaxSeg);
+            if (perF < 1 || perN < 1) {
+                // a segment or a near column larger than a stage (the host
+                // rejects such leaves before the launch): stop producing
+                if (lane == 0) atomicExch(err, 2);
+                break;
+            }
+            const int2* fitems = reinterpret_cast<const int2*>(md.lf_items + fi0);
+            const int2* nitems = reinterpret_cast<const int2*>(md.ln_items + ni0);
             int cur = 0;
             for (int g = 0; g < S && ok; g += perF) {
                 const int cnt = min(perF, S - g);
-                const TF* src = Ul + tb.lf_base[lf] + (size_t)g * mp;
-                ok = emit(lf, 0, g, cnt, (g + cnt == S && Sn == 0) ? 1 : 0, src, (uint32_t)(cnt * segB),
+                const TF* src = Ul + md.lf_base[lf] + (size_t)g * mp;
+                ok = emit(wk.x, lf, 0, g, cnt, (g + cnt == S && Sn == 0) ? 1 : 0, src, (uint32_t)(cnt * segB),
                           fitems, fi1 - fi0, &cur, wvec);
             }
-            const int colB = 6 * mp * (int)sizeof(TN);
-            const int perN = min(kStageBytes / colB, kMaxSeg);
             cur = 0;
             for (int g = 0; g < Sn && ok; g += perN) {
                 const int cnt = min(perN, Sn - g);
-                const TN* src = Nl + tb.ln_base[lf] + (size_t)g * 6 * mp;
-                ok = emit(lf, 1, g, cnt, (g + cnt == Sn) ? 1 : 0, src, (uint32_t)(cnt * colB), nitems,
+                const TN* src = Nl + md.ln_base[lf] + (size_t)g * 6 * mp;
+                ok = emit(wk.x, lf, 1, g, cnt, (g + cnt == Sn) ? 1 : 0, src, (uint32_t)(cnt * colB), nitems,
                           ni1 - ni0, &cur, xvec);
             }
         }
-        if (ok) ok = emit(-1, 2, 0, 0, 0, nullptr, 0, nullptr, 0, nullptr, nullptr);
+        if (ok) ok = emit(0, -1, 2, 0, 0, 0, nullptr, 0, nullptr, 0, nullptr, nullptr);
         if (!ok) {
             // drain this CTA's own copies in flight before returning (bounded)
-            if (lane == 0) abort_flag = 1;
             for (int k = 1; k <= kStages && k <= it; ++k) {
                 const int j = it - k;
                 mbar_wait(&full[j % kStages], (uint32_t)(j / kStages) & 1u, err);
@@ -355,17 +351,26 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
 
     // ---------------------------------------------------------------- consumers
     const int ctid = threadIdx.x - 32;
-    int cur = -1, P = 1, H = 0, p = 0, h = 0, t0 = 0, mt = 0, mp = 8;
+    int cur = -1, cur_mesh = -1, P = 1, H = 0, p = 0, h = 0, t0 = 0, mt = 0, mp = 8;
+    const int32_t* perm = nullptr;
+    int64_t xoff = 0;
+    TA c1 = (TA)0, c2 = (TA)0;
     TA acc[R][3];
     for (int it = 0;; ++it) {
         const int slot = it % kStages;
         if (!mbar_wait(&full[slot], (uint32_t)(it / kStages) & 1u, err)) break;
         const StageMeta m = meta[slot];
         if (m.kind == 2) break;
-        if (m.leaf != cur) {
+        if (m.leaf != cur || m.pad[0] != cur_mesh) {
             cur = m.leaf;
-            t0 = tb.leaf[2 * cur];
-            mt = tb.leaf[2 * cur + 1];
+            cur_mesh = m.pad[0];
+            const MeshDev& md = meshes[cur_mesh];
+            t0 = md.leaf[2 * cur];
+            mt = md.leaf[2 * cur + 1];
+            perm = md.perm;
+            xoff = md.xoff;
+            c1 = (TA)md.c1;
+            c2 = (TA)md.c2;
             mp = (mt + 7) & ~7;
             P = mp / R;
             H = kConsumers / P;
@@ -443,7 +448,7 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
                 const int i = idx / 3, a = idx - 3 * i;
                 TA sum = (TA)0;
                 for (int g = 0; g < H; ++g) sum += red[((g * P) * R + i) * 3 + a];
-                y[(size_t)r * ld + 3 * (size_t)tb.perm[t0 + i] + a] = (double)sum;
+                y[(size_t)r * ld + xoff + 3 * (size_t)perm[t0 + i] + a] = (double)sum;
             }
             named_barrier_consumers();
         }

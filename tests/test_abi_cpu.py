@@ -32,11 +32,27 @@ def test_library_exports_every_header_symbol():
     assert set(names) == set(binding.SYMBOLS)
 
 
+def test_binding_constants_match_header():
+    src = open(os.path.join(ROOT, "include", "hmat.h")).read()
+    defs = dict(re.findall(r"^#define (HM_[A-Z0-9_]+) \(?(-?\d+)\)?", src, flags=re.M))
+    assert int(defs["HM_MAX_LEAF"]) == binding.MAX_LEAF
+    for name in ("HM_OK", "HM_EINVAL", "HM_ENOMEM", "HM_ENOTCONV", "HM_ETIMEOUT", "HM_EDEVICE", "HM_ERANK"):
+        assert int(defs[name]) == getattr(binding, name), name
+    for name, key in (("HM_FP64", "fp64"), ("HM_FP32", "fp32"), ("HM_BF16", "bf16"), ("HM_FP16", "fp16")):
+        assert int(defs[name]) == binding.FORMS[key], name
+
+
 def test_invalid_arguments_fail_cleanly():
     V, T = inputs.icosphere(1)
     with pytest.raises(binding.HMError) as e:
         binding.build_cluster_tree(V, T, 0, 0.8)
     assert e.value.code == binding.HM_EINVAL
+    # the streamed product holds a leaf's rows in one CTA and one FP64
+    # near-field column (6 x 336 values) in one 16 KB stage: at most 336
+    binding.build_cluster_tree(V, T, 336, 0.8)
+    with pytest.raises(binding.HMError) as e:
+        binding.build_cluster_tree(V, T, 337, 0.8)
+    assert b"336" in binding.load().hm_last_error()
     with pytest.raises(binding.HMError):
         binding.build_cluster_tree(V, T, 8, -1.0)
     bad = T.copy()
@@ -73,7 +89,7 @@ def _compare_tree(V, T, leaf, eta):
 
 @pytest.mark.parametrize("mesh,leaf,eta", [
     ("ico0", 4, 0.8), ("ico3", 32, 0.8), ("ico3", 7, 0.8), ("ico4", 64, 0.5),
-    ("cube6", 16, 0.8), ("ell", 32, 0.8), ("ico2", 10**6, 0.8)])
+    ("cube6", 16, 0.8), ("ell", 32, 0.8), ("ico2", 336, 0.8)])
 def test_tree_and_partition_match_oracle(mesh, leaf, eta):
     if mesh.startswith("ico"):
         V, T = inputs.icosphere(int(mesh[3:]))

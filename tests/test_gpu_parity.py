@@ -139,16 +139,19 @@ def test_set_material():
     assert _rel(y[0], yo[0]) <= 1e-12
 
 
-@pytest.mark.parametrize("mesh,leaf", [("ico0", 3), ("ico1", 7), ("ico2", 1000), ("cube4", 12),
-                                       ("ell", 20)])
+@pytest.mark.parametrize("mesh,leaf", [("ico0", 3), ("ico1", 7), ("ico2", 336), ("cube4", 12),
+                                       ("ell", 20), ("ell10", 336)])
 def test_small_and_ragged_meshes(mesh, leaf):
     """Tiny meshes, leaves of ragged size, a single dense leaf (leaf >= M), a
     cube surface whose planar faces make some kernels vanish identically
-    (rank 0 blocks), and an ellipsoid."""
+    (rank 0 blocks), an ellipsoid, and leaves of 300 rows near the largest
+    leaf the library takes (336): one FP64 near-field column per stage."""
     if mesh.startswith("ico"):
         V, T = inputs.icosphere(int(mesh[3:]))
     elif mesh == "cube4":
         V, T = inputs.cube_surface(4)
+    elif mesh == "ell10":
+        V, T = inputs.ellipsoid(10, 0.6, 1.7, 1.1)
     else:
         V, T = inputs.ellipsoid(7, 0.6, 1.7, 1.1)
     c = Case(V, T, leaf, max_rhs=2)
