@@ -181,6 +181,62 @@ int hm_matvec_host(const hm_matrix* H, const double* x_host, double* y_host, int
                    int64_t ld, int32_t form, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * hm_batch -- the product of hm_matvec over many resident matrices at once
+ * (meshes of different sizes and materials).  The paper treats one mesh at
+ * a time; the batch is a library service for many independent problems: it
+ * runs each phase of the product (Section 2: V^T x per admissible block, then
+ * U w and the near field per row cluster) as ONE launch over every block of
+ * every member, with one work list of (mesh, leaf) items for the persistent
+ * per-leaf kernel.
+ *   mats     nmat (1..65535) distinct assembled matrices, each with `form`
+ *            packed.  The batch refers to their device data: they must
+ *            outlive it and must not change (hm_set_material on a member
+ *            after hm_batch_create is not seen by the batch; create a new one).
+ *   max_rhs  largest nrhs of hm_batch_matvec (sizes the batch's workspace)
+ * Vector layout: member m's dofs (3 M_m, dof 3i + a in its own original
+ * order) sit at offsets dof_offsets[m] .. dof_offsets[m+1] of each row of x
+ * and y; hm_batch_layout returns the nmat + 1 offsets and sizes[0..3] =
+ * members, total dofs, admissible blocks, leaves.
+ * Result: member m's part of y is bitwise equal to hm_matvec(mats[m], ...)
+ * on its part of x, under every schedule.
+ * Allocates its workspace through the first member's allocator.
+ * ------------------------------------------------------------------------- */
+typedef struct hm_batch hm_batch;
+
+/* Launch schedule of a batched product.  No knob changes any result. */
+typedef struct {
+    int32_t leaf_ctas_per_sm; /* CTAs per SM of the per-leaf kernel (0 = as many as fit) */
+    int32_t work_order;       /* 0: all (mesh, leaf) items by decreasing bytes; 1: member by member */
+    int32_t fork_forward;     /* 1: large- and small-block forward kernels on two streams */
+    int32_t pad;
+} hm_schedule;
+
+int hm_batch_create(const hm_matrix* const* mats, int32_t nmat, int32_t form, int32_t max_rhs,
+                    hm_batch** out);
+int hm_batch_layout(const hm_batch* B, int64_t* dof_offsets, int64_t sizes[4]);
+
+/* y = V_h x for every member: x, y device pointers, nrhs (1..max_rhs) rows
+ * of length >= total dofs, leading dimension ld; must not overlap.
+ * use_graph != 0: the product is captured once into a CUDA graph (per x, y,
+ * nrhs, ld and schedule; a change of any of them captures a new one) and
+ * replayed with one cudaGraphLaunch on `stream`.  Asynchronous; calls on the
+ * same batch must not overlap on the device (shared workspace). */
+int hm_batch_matvec(hm_batch* B, const double* x, double* y, int32_t nrhs, int64_t ld,
+                    int32_t use_graph, void* stream);
+
+/* Time every candidate schedule (CTAs per SM in {max, 1}, both work orders,
+ * forward on one or two streams) over `reps` products of nrhs right-hand
+ * sides on `stream` and keep the fastest; returns it and its ms per product.
+ * Allocates two temporary vectors; synchronises `stream`. */
+int hm_batch_autotune(hm_batch* B, int32_t nrhs, int32_t reps, hm_schedule* chosen, double* ms,
+                      void* stream);
+int hm_batch_set_schedule(hm_batch* B, const hm_schedule* s);
+int hm_batch_get_schedule(const hm_batch* B, hm_schedule* s);
+/* as hm_check, for the batch's own products */
+int hm_batch_check(const hm_batch* B);
+void hm_batch_destroy(hm_batch* B);
+
+/* ---------------------------------------------------------------------------
  * hm_solve -- solve V_h t = g (one right-hand side) for the single-layer
  * density t.  Restarted GMRES(m) runs on the product form `inner_form` (for
  * speed), inside iterative refinement whose residual r = g - V_h t is always

@@ -27,7 +27,8 @@ SYMBOLS = (
     "hm_aca_assemble", "hm_set_material", "hm_pack", "hm_matvec", "hm_matvec_host",
     "hm_get_stats", "hm_export_factors", "hm_export_near", "hm_matrix_destroy",
     "hm_last_error", "hm_profile_enable", "hm_profile_read", "hm_matvec_noalloc", "hm_check",
-    "hm_solve",
+    "hm_solve", "hm_batch_create", "hm_batch_layout", "hm_batch_matvec", "hm_batch_autotune",
+    "hm_batch_set_schedule", "hm_batch_get_schedule", "hm_batch_check", "hm_batch_destroy",
 )
 
 
@@ -62,6 +63,11 @@ class _SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("restarts", ctypes.c_int32),
                 ("refinements", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("rel_residual", ctypes.c_double)]
+
+
+class _Schedule(ctypes.Structure):
+    _fields_ = [("leaf_ctas_per_sm", ctypes.c_int32), ("work_order", ctypes.c_int32),
+                ("fork_forward", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -110,6 +116,15 @@ def load():
         "hm_last_error": (ctypes.c_char_p, []),
         "hm_profile_enable": (ctypes.c_int, [P, I32]),
         "hm_profile_read": (ctypes.c_int, [P, P, ctypes.POINTER(I64)]),
+        "hm_batch_create": (ctypes.c_int, [P, I32, I32, I32, ctypes.POINTER(P)]),
+        "hm_batch_layout": (ctypes.c_int, [P, P, P]),
+        "hm_batch_matvec": (ctypes.c_int, [P, P, P, I32, I64, I32, P]),
+        "hm_batch_autotune": (ctypes.c_int, [P, I32, I32, ctypes.POINTER(_Schedule),
+                                             ctypes.POINTER(D), P]),
+        "hm_batch_set_schedule": (ctypes.c_int, [P, ctypes.POINTER(_Schedule)]),
+        "hm_batch_get_schedule": (ctypes.c_int, [P, ctypes.POINTER(_Schedule)]),
+        "hm_batch_check": (ctypes.c_int, [P]),
+        "hm_batch_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -376,3 +391,74 @@ def hmatvec_host(H: HMatrix, x: np.ndarray, y: np.ndarray, form="fp64", stream=N
         raise ValueError("hmatvec_host: rows must be contiguous")
     _check(load().hm_matvec_host(H._h, _ptr(x), _ptr(y), nrhs, ld, f, _stream_handle(stream)))
     return y
+
+
+class Batch:
+    """``hm_batch``: one product over several resident matrices (each with
+    ``form`` packed).  Rows of x and y hold every member's dofs side by side
+    at ``offsets[m] .. offsets[m+1]``.  The members must stay alive and
+    unchanged while the batch exists."""
+
+    def __init__(self, mats, form="fp16", max_rhs: int = 16):
+        lib = load()
+        self.mats = list(mats)  # keeps the members alive
+        self.form = FORMS[form] if isinstance(form, str) else int(form)
+        arr = (ctypes.c_void_p * len(self.mats))(*[m._h.value for m in self.mats])
+        h = ctypes.c_void_p()
+        _check(lib.hm_batch_create(arr, len(self.mats), self.form, int(max_rhs), ctypes.byref(h)))
+        self._h = h
+        self.max_rhs = int(max_rhs)
+        off = np.zeros(len(self.mats) + 1, dtype=np.int64)
+        sz = np.zeros(4, dtype=np.int64)
+        _check(lib.hm_batch_layout(self._h, _ptr(off), _ptr(sz)))
+        self.offsets = off
+        self.ndof = int(sz[1])
+        self.nblocks, self.nleaves = int(sz[2]), int(sz[3])
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.hm_batch_destroy(h)
+            self._h = None
+
+    def matvec(self, x, y, graph: bool = False, stream=None):
+        """y = V_h x for every member; x, y CUDA float64 tensors (ndof,) or
+        (nrhs, ndof) with the same row stride."""
+        import torch
+        if not (x.is_cuda and y.is_cuda and x.dtype == torch.float64 and y.dtype == torch.float64):
+            raise TypeError("Batch.matvec: x and y must be CUDA float64 tensors")
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        ld = x.shape[-1] if nrhs == 1 else x.stride(0)
+        if y.shape != x.shape or (nrhs > 1 and y.stride(0) != ld):
+            raise ValueError("Batch.matvec: y must have the shape and row stride of x")
+        if x.shape[-1] < self.ndof or x.stride(-1) != 1 or y.stride(-1) != 1:
+            raise ValueError("Batch.matvec: rows must be contiguous of length >= ndof")
+        _check(load().hm_batch_matvec(self._h, ctypes.c_void_p(x.data_ptr()),
+                                      ctypes.c_void_p(y.data_ptr()), nrhs, ld, 1 if graph else 0,
+                                      _stream_handle(stream)))
+        return y
+
+    def autotune(self, nrhs: int = 1, reps: int = 3, stream=None):
+        """Time every schedule, keep the fastest; returns (schedule dict, ms)."""
+        sc = _Schedule()
+        ms = ctypes.c_double(0.0)
+        _check(load().hm_batch_autotune(self._h, int(nrhs), int(reps), ctypes.byref(sc),
+                                        ctypes.byref(ms), _stream_handle(stream)))
+        return self._sched_dict(sc), float(ms.value)
+
+    @staticmethod
+    def _sched_dict(sc):
+        return dict(leaf_ctas_per_sm=sc.leaf_ctas_per_sm, work_order=sc.work_order,
+                    fork_forward=sc.fork_forward)
+
+    def schedule(self):
+        sc = _Schedule()
+        _check(load().hm_batch_get_schedule(self._h, ctypes.byref(sc)))
+        return self._sched_dict(sc)
+
+    def set_schedule(self, leaf_ctas_per_sm=0, work_order=0, fork_forward=0):
+        sc = _Schedule(int(leaf_ctas_per_sm), int(work_order), int(fork_forward), 0)
+        _check(load().hm_batch_set_schedule(self._h, ctypes.byref(sc)))
+
+    def check(self):
+        _check(load().hm_batch_check(self._h))

@@ -223,10 +223,17 @@ int matvec_device_scratch(const hm_matrix& H, const double* x, double* y, int32_
 // bytes of Scratch a product of nrhs vectors in `form` needs (xg, w and the
 // counters, each part 256-byte aligned)
 size_t matvec_scratch_bytes(const hm_matrix& H, int32_t nrhs, int32_t form);
+// Launch schedule of a product.  None of these change the arithmetic: every
+// output element is summed in the same order under every schedule.
+struct Sched {
+    int32_t ctas_per_sm = 0;        // streamed leaf kernel: CTAs per SM (0 = as many as fit)
+    cudaStream_t side = nullptr;    // non-null: the large-block forward kernel runs on `side`
+    cudaEvent_t fork = nullptr, join = nullptr;  // (with these two events) beside the small-block one
+};
 // the product over the meshes of a plan: x, y rows of length >= total dofs
 // with leading dimension ld; xg / w workspace with the plan's strides
 int run_product(const Plan& P, int32_t form, const double* x, double* y, int32_t nrhs, int64_t ld,
-                void* xg, void* w, cudaStream_t s, const hm_matrix* prof);
+                void* xg, void* w, cudaStream_t s, const hm_matrix* prof, const Sched* sched = nullptr);
 // (re)write the single-mesh table of a packed form (after packing or a
 // change of material)
 int write_mesh_table(hm_matrix& H, int32_t form, cudaStream_t s);

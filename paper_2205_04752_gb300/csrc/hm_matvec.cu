@@ -505,7 +505,7 @@ int stream_launch(StreamLaunch& out)
 // The three phases of the product over every mesh of the plan.
 template <class TF, class TN, class TA>
 int run_product_t(const Plan& P, const double* x, double* y, int nrhs, int64_t ld, TA* xg, TA* w,
-                  cudaStream_t s, const hm_matrix* prof)
+                  cudaStream_t s, const hm_matrix* prof, const Sched& sc)
 {
     constexpr int Rs = stream::Smem16<TF, TA>::N;
     const int mpmax = (P.max_leaf + 7) & ~7;
@@ -521,9 +521,15 @@ int run_product_t(const Plan& P, const double* x, double* y, int nrhs, int64_t l
     if (prof) prof_mark(*prof, 1, s);
     const bool one = P.nmesh == 1;
     const MeshDev m0 = one ? P.mesh0 : MeshDev{};
+    const bool fork = sc.side && P.nbig > 0 && P.nsmall > 0;
+    if (fork) {
+        HM_CUDA(cudaEventRecord(sc.fork, s));
+        HM_CUDA(cudaStreamWaitEvent(sc.side, sc.fork, 0));
+    }
     if (P.nbig > 0) {
         auto kb = one ? fwd_big_kernel<TF, TA, true> : fwd_big_kernel<TF, TA, false>;
-        kb<<<dim3((unsigned)P.nbig, nr), kThreads, 0, s>>>(P.fwd, m0, P.meshes, xg, w, P.xg_ld, P.w_ld);
+        kb<<<dim3((unsigned)P.nbig, nr), kThreads, 0, fork ? sc.side : s>>>(P.fwd, m0, P.meshes, xg, w, P.xg_ld,
+                                                                          P.w_ld);
         HM_CUDA(cudaGetLastError());
     }
     if (P.nsmall > 0) {
@@ -532,13 +538,18 @@ int run_product_t(const Plan& P, const double* x, double* y, int nrhs, int64_t l
         ks<<<dim3(nb, nr), kThreads, 0, s>>>(P.fwd + P.nbig, P.nsmall, m0, P.meshes, xg, w, P.xg_ld, P.w_ld);
         HM_CUDA(cudaGetLastError());
     }
+    if (fork) {
+        HM_CUDA(cudaEventRecord(sc.join, sc.side));
+        HM_CUDA(cudaStreamWaitEvent(s, sc.join, 0));
+    }
     if (prof) prof_mark(*prof, 2, s);
     if (P.nwork > 0) {
         StreamLaunch l;
         int rc = stream_launch<TF, TN, TA>(l);
         if (rc) return rc;
         const size_t smem = stream::smem_bytes<TA>(Rs);
-        const int64_t ncta = std::min<int64_t>(P.nwork, (int64_t)l.nsm * l.ctas_per_sm);
+        const int per_sm = sc.ctas_per_sm > 0 ? std::min(sc.ctas_per_sm, l.ctas_per_sm) : l.ctas_per_sm;
+        const int64_t ncta = std::min<int64_t>(P.nwork, (int64_t)l.nsm * per_sm);
         HM_CUDA(cudaMemsetAsync(P.counters, 0, (size_t)nrhs * sizeof(int), s));
         stream::leaf_stream_kernel<TF, TN, TA><<<dim3((unsigned)ncta, nr), stream::kThreads, smem, s>>>(
             P.work, (int)P.nwork, P.meshes, P.counters, P.err, xg, w, P.xg_ld, P.w_ld, y, ld);
@@ -587,22 +598,39 @@ int pack_near(hm_matrix& H, DevBuf& dst, cudaStream_t s)
 
 }  // namespace
 
-int run_product(const Plan& P, int32_t form, const double* x, double* y, int32_t nrhs, int64_t ld, void* xg,
-                void* w, cudaStream_t s, const hm_matrix* prof)
+int product_prepare(int32_t form, int* ctas_per_sm)
 {
+    StreamLaunch l;
+    int rc;
+    switch (form) {
+        case HM_FP64: rc = stream_launch<double, double, double>(l); break;
+        case HM_FP32: rc = stream_launch<float, float, float>(l); break;
+        case HM_BF16: rc = stream_launch<__nv_bfloat16, float, float>(l); break;
+        case HM_FP16: rc = stream_launch<__half, float, float>(l); break;
+        default: return fail(HM_EINVAL, "product: unknown form %d", form);
+    }
+    if (rc) return rc;
+    if (ctas_per_sm) *ctas_per_sm = l.ctas_per_sm;
+    return HM_OK;
+}
+
+int run_product(const Plan& P, int32_t form, const double* x, double* y, int32_t nrhs, int64_t ld, void* xg,
+                void* w, cudaStream_t s, const hm_matrix* prof, const Sched* sched)
+{
+    const Sched sc = sched ? *sched : Sched{};
     switch (form) {
         case HM_FP64:
             return run_product_t<double, double, double>(P, x, y, nrhs, ld, static_cast<double*>(xg),
-                                                         static_cast<double*>(w), s, prof);
+                                                         static_cast<double*>(w), s, prof, sc);
         case HM_FP32:
             return run_product_t<float, float, float>(P, x, y, nrhs, ld, static_cast<float*>(xg),
-                                                      static_cast<float*>(w), s, prof);
+                                                      static_cast<float*>(w), s, prof, sc);
         case HM_BF16:
             return run_product_t<__nv_bfloat16, float, float>(P, x, y, nrhs, ld, static_cast<float*>(xg),
-                                                              static_cast<float*>(w), s, prof);
+                                                              static_cast<float*>(w), s, prof, sc);
         case HM_FP16:
             return run_product_t<__half, float, float>(P, x, y, nrhs, ld, static_cast<float*>(xg),
-                                                       static_cast<float*>(w), s, prof);
+                                                       static_cast<float*>(w), s, prof, sc);
         default:
             return fail(HM_EINVAL, "product: unknown form %d", form);
     }
