@@ -319,6 +319,17 @@ int hm_export_factors(const hm_matrix* H, int64_t blk, int32_t kern, int32_t* ra
  * trace. */
 int hm_export_near(const hm_matrix* H, int64_t blk, double* out);
 
+/* Release the FP64 data of H (the block-ordered FP64 factors and near field,
+ * the FP64 product form and the pack sources) once the reduced forms it will
+ * serve are packed: it keeps only what the packed forms read, typically a
+ * third of the assembled footprint or less.  Afterwards hm_matvec in
+ * HM_FP64, hm_solve, hm_pack and the exports return HM_EINVAL.  At least one
+ * of HM_FP32 / HM_BF16 / HM_FP16 must be packed.  Synchronises the device. */
+int hm_compact(hm_matrix* H);
+
+/* Device bytes H currently holds (all its buffers and workspace). */
+int hm_footprint(const hm_matrix* H, int64_t* bytes);
+
 void hm_matrix_destroy(hm_matrix* H);
 
 /* text of the calling thread's last error ("" if none) */

@@ -29,6 +29,7 @@ SYMBOLS = (
     "hm_last_error", "hm_profile_enable", "hm_profile_read", "hm_matvec_noalloc", "hm_check",
     "hm_solve", "hm_batch_create", "hm_batch_layout", "hm_batch_matvec", "hm_batch_autotune",
     "hm_batch_set_schedule", "hm_batch_get_schedule", "hm_batch_check", "hm_batch_destroy",
+    "hm_compact", "hm_footprint",
 )
 
 
@@ -125,6 +126,8 @@ def load():
         "hm_batch_get_schedule": (ctypes.c_int, [P, ctypes.POINTER(_Schedule)]),
         "hm_batch_check": (ctypes.c_int, [P]),
         "hm_batch_destroy": (None, [P]),
+        "hm_compact": (ctypes.c_int, [P]),
+        "hm_footprint": (ctypes.c_int, [P, ctypes.POINTER(I64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -276,6 +279,16 @@ class HMatrix:
     def check(self):
         """Raise if a bounded device wait in an earlier product ran out."""
         _check(load().hm_check(self._h))
+
+    def compact(self):
+        """``hm_compact``: release the FP64 data, keep the packed reduced forms."""
+        _check(load().hm_compact(self._h))
+
+    def footprint(self) -> int:
+        """Device bytes held by the matrix (``hm_footprint``)."""
+        b = ctypes.c_int64(0)
+        _check(load().hm_footprint(self._h, ctypes.byref(b)))
+        return int(b.value)
 
     def profile(self, on: bool):
         _check(load().hm_profile_enable(self._h, 1 if on else 0))

@@ -97,8 +97,6 @@ Plan make_plan(const hm_batch& B)
     P.max_leaf = B.max_leaf;
     P.counters = B.counters.as<int>();
     P.err = B.err.as<int>();
-    P.xg_ld = 4 * B.npos;
-    P.w_ld = B.w_total;
     return P;
 }
 
@@ -185,8 +183,8 @@ int hm_batch_create(const hm_matrix* const* mats, int32_t nmat, int32_t form, in
     for (int32_t m = 0; m < nmat; ++m) {
         MeshDev d = mesh_desc(*mats[m], form);
         d.xoff = 3 * B->pos_prefix[(size_t)m];
-        d.xgoff = 4 * B->pos_prefix[(size_t)m];
-        d.woff = woff[(size_t)m];
+        d.xgoff = B->pos_prefix[(size_t)m];
+        d.woff = woff[(size_t)m] / 4;  // in factor columns
         B->mesh_h.push_back(d);
     }
 

@@ -386,6 +386,7 @@ int hm_export_factors(const hm_matrix* H, int64_t blk, int32_t kern, int32_t* ra
                       double* V)
 {
     if (!H || !rank) return fail(HM_EINVAL, "hm_export_factors: NULL argument");
+    if (H->compacted && (U || V)) return fail(HM_EINVAL, "hm_export_factors: FP64 factors released (hm_compact)");
     if (blk < 0 || blk >= H->nadm || kern < 0 || kern > 6)
         return fail(HM_EINVAL, "hm_export_factors: block %lld kernel %d out of range",
                     (long long)blk, kern);
@@ -405,6 +406,7 @@ int hm_export_factors(const hm_matrix* H, int64_t blk, int32_t kern, int32_t* ra
 int hm_export_near(const hm_matrix* H, int64_t blk, double* out)
 {
     if (!H || !out) return fail(HM_EINVAL, "hm_export_near: NULL argument");
+    if (H->compacted) return fail(HM_EINVAL, "hm_export_near: FP64 near field released (hm_compact)");
     if (blk < 0 || blk >= H->nnear) return fail(HM_EINVAL, "hm_export_near: block out of range");
     const Blk& b = H->near_h[(size_t)blk];
     // device layout per block: [v][j][i] (i fastest); exported as [v][i][j]
@@ -455,6 +457,46 @@ int hm_profile_read(hm_matrix* H, double ms[4], int64_t* calls)
     }
     if (calls) *calls = n;
     H->prof_calls = 0;
+    return HM_OK;
+}
+
+int hm_compact(hm_matrix* H)
+{
+    if (!H) return fail(HM_EINVAL, "hm_compact: NULL matrix");
+    if (H->compacted) return HM_OK;
+    if (!H->packed[HM_FP32] && !H->packed[HM_BF16] && !H->packed[HM_FP16])
+        return fail(HM_EINVAL, "hm_compact: pack a reduced form first (hm_pack)");
+    HM_CUDA(cudaDeviceSynchronize());
+    hm::DevBuf* bufs[] = {&H->U64, &H->V64, &H->N64, &H->SV, &H->Ul[HM_FP64], &H->Vr[HM_FP64], &H->Nl64,
+                          &H->d_lf_src, &H->d_ln_src, &H->d_mesh[HM_FP64]};
+    cudaStream_t saved = H->alloc.stream;
+    H->alloc.stream = nullptr;
+    for (hm::DevBuf* b : bufs) {
+        H->alloc.release(b->p, b->bytes);
+        b->p = nullptr;
+        b->bytes = 0;
+    }
+    H->alloc.stream = saved;
+    H->packed[HM_FP64] = false;
+    H->compacted = true;
+    return cuda_check(cudaDeviceSynchronize(), "hm_compact");
+}
+
+int hm_footprint(const hm_matrix* H, int64_t* bytes)
+{
+    if (!H || !bytes) return fail(HM_EINVAL, "hm_footprint: NULL argument");
+    const hm::DevBuf* bufs[] = {&H->d_perm, &H->d_adm, &H->d_near, &H->d_rank, &H->d_uoff, &H->d_voff,
+                                &H->d_coff, &H->d_noff, &H->d_leaf, &H->d_lf_base, &H->d_lf_ptr,
+                                &H->d_lf_items, &H->d_lf_src, &H->d_ln_base, &H->d_ln_ptr, &H->d_ln_items,
+                                &H->d_ln_src, &H->d_vb_base, &H->d_fwd_all, &H->d_work, &H->d_pos_prefix,
+                                &H->d_mesh[0], &H->d_mesh[1], &H->d_mesh[2], &H->d_mesh[3], &H->d_counters,
+                                &H->d_err, &H->U64, &H->V64, &H->N64, &H->Ul[0], &H->Ul[1], &H->Ul[2],
+                                &H->Ul[3], &H->Vr[0], &H->Vr[1], &H->Vr[2], &H->Vr[3], &H->Nl64, &H->Nl32,
+                                &H->SU, &H->SV, &H->xg, &H->wb, &H->xh, &H->yh};
+    int64_t t = 0;
+    for (const hm::DevBuf* b : bufs)
+        if (b->p) t += (int64_t)b->bytes;
+    *bytes = t;
     return HM_OK;
 }
 

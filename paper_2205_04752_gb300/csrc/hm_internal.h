@@ -106,8 +106,9 @@ struct FwdRec {
 // Device-side description of one mesh taking part in a product (a single
 // matrix is a product over one mesh; a batch concatenates several).  Stream
 // and table pointers are the mesh's own; the vectors live in shared arrays:
-// x and y rows hold the mesh's dofs at xoff, the gathered x (4-vectors) at
-// xgoff and w (4-vectors) at woff.
+// x and y rows hold the mesh's dofs at element offset xoff; the gathered x
+// and w hold G interleaved 4-vectors per cluster position / factor column,
+// the mesh's first position at xgoff and first column at woff.
 struct MeshDev {
     const void* Ul;   // leaf-major U stream (factor type of the form)
     const void* Vr;   // row-major V of every block
@@ -140,7 +141,6 @@ struct Plan {
     int32_t max_leaf;
     int* counters;              // >= nrhs ints of device memory
     int* err;
-    int64_t xg_ld, w_ld;        // per-RHS stride of the gathered x and of w (elements)
 };
 
 
@@ -195,6 +195,7 @@ struct hm_matrix {
     hm::DevBuf Nl64, Nl32;  // near field leaf-major: FP64 form / all other forms
     hm::DevBuf SU, SV;      // per-column scales of the 16-bit forms (float, c_total)
     bool packed[4] = {false, false, false, false};
+    bool compacted = false;  // FP64 data released (hm_compact)
 
     // workspace
     int32_t max_rhs = 32;

@@ -150,19 +150,20 @@ __device__ __forceinline__ int mesh_of(const int64_t* __restrict__ pos_prefix, i
     return lo;
 }
 
-// x (original dof order of every mesh) -> xg[r][p][a] (cluster order, a padded to 4)
+// x (original dof order of every mesh) -> xg[p][r][a] (cluster order, G
+// right-hand sides interleaved, a padded to 4)
 template <class TA>
 __global__ void gather_kernel(const MeshDev* __restrict__ meshes, int nmesh, const int64_t* __restrict__ pos_prefix,
-                              int64_t npos, const double* __restrict__ x, int64_t ld, TA* __restrict__ xg,
-                              int64_t xg_ld)
+                              int64_t npos, const double* __restrict__ x, int64_t ld, TA* __restrict__ xg, int G)
 {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int r = blockIdx.y;
-    if (p >= npos) return;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= npos * G) return;
+    const int64_t p = idx / G;
+    const int r = (int)(idx - p * G);
     const int m = mesh_of(pos_prefix, nmesh, p);
     const MeshDev& md = meshes[m];
     const size_t src = (size_t)r * ld + md.xoff + 3 * (size_t)md.perm[p - pos_prefix[m]];
-    TA* d = xg + (size_t)r * xg_ld + (size_t)p * 4;
+    TA* d = xg + (size_t)idx * 4;
 #pragma unroll
     for (int a = 0; a < 3; ++a) d[a] = (TA)x[src + a];
     d[3] = (TA)0;
@@ -172,8 +173,8 @@ __global__ void gather_kernel(const MeshDev* __restrict__ meshes, int nmesh, con
 // w for every factor column c of block `rec` from its reduced z = V^T x
 // (three components), with c1 / c2 and the column scale of U folded in
 template <class TA>
-__device__ __forceinline__ void write_w(const FwdRec& rec, int c, const TA* z, const float* __restrict__ SU,
-                                        TA* __restrict__ wr, TA c1, TA c2)
+__device__ __forceinline__ void write_w(const FwdRec& rec, int c, TA z0, TA z1, TA z2, const float* __restrict__ SU,
+                                        TA* __restrict__ wr, TA c1, TA c2, int G, int r)
 {
     int kern = 0, l = c;
     for (;;) {
@@ -187,24 +188,28 @@ __device__ __forceinline__ void write_w(const FwdRec& rec, int c, const TA* z, c
     TA o[3];
     if (kern == 0) {
         const TA f = c1 * su;
-        o[0] = f * z[0];
-        o[1] = f * z[1];
-        o[2] = f * z[2];
+        o[0] = f * z0;
+        o[1] = f * z1;
+        o[2] = f * z2;
     } else {
+        // V_pq enters y_p with x_q and (p != q) y_q with x_p; selects keep
+        // everything in registers
         int p, pq;
         kern_pq(kern, p, pq);
         const TA f = c2 * su;
-        o[0] = o[1] = o[2] = (TA)0;
-        o[p] = f * z[pq];
-        if (p != pq) o[pq] = f * z[p];
+        const TA zp = p == 0 ? z0 : (p == 1 ? z1 : z2);
+        const TA zq = pq == 0 ? z0 : (pq == 1 ? z1 : z2);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) o[a] = a == p ? f * zq : (a == pq ? f * zp : (TA)0);
     }
-    wr[col * 4] = o[0];
-    wr[col * 4 + 1] = o[1];
-    wr[col * 4 + 2] = o[2];
-    wr[col * 4 + 3] = (TA)0;
+    TA* d = wr + ((size_t)col * G + r) * 4;
+    d[0] = o[0];
+    d[1] = o[1];
+    d[2] = o[2];
+    d[3] = (TA)0;
 }
 
-// pointers of block `rec` of its mesh for right-hand side r.  ONE: the plan
+// pointers of block `rec` of its mesh.  ONE: the plan
 // has a single mesh, passed by value as a kernel parameter (no dependent load
 // of the mesh table before the first load of V).
 template <class TF, class TA, bool ONE>
@@ -215,45 +220,45 @@ struct FwdArgs {
     const float* SU;
     TA c1, c2;
     __device__ __forceinline__ FwdArgs(const FwdRec& rec, const MeshDev& m0, const MeshDev* __restrict__ meshes,
-                                       const TA* xg, TA* w, int r, int64_t xg_ld, int64_t w_ld)
+                                       const TA* xg, TA* w, int G)
     {
         const MeshDev& md = ONE ? m0 : meshes[rec.mesh];
         Vb = static_cast<const TF*>(md.Vr) + rec.vbase;
-        x0 = xg + (size_t)r * xg_ld + md.xgoff + (size_t)rec.s0 * 4;
-        wr = w + (size_t)r * w_ld + md.woff;
+        x0 = xg + ((size_t)md.xgoff + rec.s0) * G * 4;
+        wr = w + (size_t)md.woff * G * 4;
         SU = md.SU;
         c1 = (TA)md.c1;
         c2 = (TA)md.c2;
     }
 };
 
-// Small blocks (|s| <= 128): one warp per block.  Lane (q, g): column vector
-// q (VEC consecutive columns of the row-major V), rows g, g + G, ...
+// Single vector, small blocks (|s| <= 128): one warp per block.  Lane (q, g):
+// column vector q (VEC consecutive columns of the row-major V), rows g, g +
+// GG, ...; the GG partial sums are added in a fixed order.
 template <class TF, class TA, bool ONE>
 __global__ void __launch_bounds__(kThreads) fwd_small_kernel(
     const FwdRec* __restrict__ recs, int64_t nrec, const __grid_constant__ MeshDev m0,
-    const MeshDev* __restrict__ meshes, const TA* __restrict__ xg, TA* __restrict__ w, int64_t xg_ld, int64_t w_ld)
+    const MeshDev* __restrict__ meshes, const TA* __restrict__ xg, TA* __restrict__ w)
 {
     constexpr int VEC = Vec16<TF, TA>::N;
     __shared__ TA red[kThreads / 32][32 * VEC * 3];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r = blockIdx.y;
     const int64_t bi = (int64_t)blockIdx.x * (kThreads / 32) + warp;
     if (bi >= nrec) return;
     TA* rw = red[warp];
     const FwdRec rec = recs[bi];
-    const FwdArgs<TF, TA, ONE> fa(rec, m0, meshes, xg, w, r, xg_ld, w_ld);
+    const FwdArgs<TF, TA, ONE> fa(rec, m0, meshes, xg, w, 1);
     const int Cp = (rec.C + 7) & ~7, Q = Cp / VEC;
     for (int cq0 = 0; cq0 < Q; cq0 += 32) {
-        const int QT = min(Q - cq0, 32), G = 32 / QT;
+        const int QT = min(Q - cq0, 32), GG = 32 / QT;
         const int q = lane % QT, g = lane / QT;
         TA acc[VEC][3];
 #pragma unroll
         for (int e = 0; e < VEC; ++e) acc[e][0] = acc[e][1] = acc[e][2] = (TA)0;
-        if (g < G) {
+        if (g < GG) {
             const TF* vp = fa.Vb + (size_t)(cq0 + q) * VEC;
 #pragma unroll 4
-            for (int j = g; j < rec.n; j += G) {
+            for (int j = g; j < rec.n; j += GG) {
                 TA v[VEC];
                 Vec16<TF, TA>::load(vp + (size_t)j * Cp, v);
                 TA xa, xb, xc;
@@ -277,10 +282,10 @@ __global__ void __launch_bounds__(kThreads) fwd_small_kernel(
                 const int c = (cq0 + q) * VEC + e;
                 if (c < rec.C) {
                     TA z[3] = {(TA)0, (TA)0, (TA)0};
-                    for (int gg = 0; gg < G; ++gg)
+                    for (int gg = 0; gg < GG; ++gg)
 #pragma unroll
                         for (int a = 0; a < 3; ++a) z[a] += rw[((gg * QT + q) * VEC + e) * 3 + a];
-                    write_w<TA>(rec, c, z, fa.SU, fa.wr, fa.c1, fa.c2);
+                    write_w<TA>(rec, c, z[0], z[1], z[2], fa.SU, fa.wr, fa.c1, fa.c2, 1, 0);
                 }
             }
         }
@@ -288,31 +293,30 @@ __global__ void __launch_bounds__(kThreads) fwd_small_kernel(
     }
 }
 
-// Larger blocks: one CTA per block.  Thread (q, g) as above with G row
-// groups over the whole CTA, reduced through shared memory.
+// Single vector, larger blocks: one CTA per block.  Thread (q, g) as above
+// with GG row groups over the whole CTA, reduced through shared memory.
 template <class TF, class TA, bool ONE>
 __global__ void __launch_bounds__(kThreads) fwd_big_kernel(
     const FwdRec* __restrict__ recs, const __grid_constant__ MeshDev m0, const MeshDev* __restrict__ meshes,
-    const TA* __restrict__ xg, TA* __restrict__ w, int64_t xg_ld, int64_t w_ld)
+    const TA* __restrict__ xg, TA* __restrict__ w)
 {
     constexpr int VEC = Vec16<TF, TA>::N;
     __shared__ TA red[kThreads * VEC * 3];
     const FwdRec rec = recs[blockIdx.x];
-    const int r = blockIdx.y;
-    const FwdArgs<TF, TA, ONE> fa(rec, m0, meshes, xg, w, r, xg_ld, w_ld);
+    const FwdArgs<TF, TA, ONE> fa(rec, m0, meshes, xg, w, 1);
     const int Cp = (rec.C + 7) & ~7, Q = Cp / VEC;
     const int tid = threadIdx.x;
     for (int cq0 = 0; cq0 < Q; cq0 += kThreads) {
         const int QT = min(Q - cq0, kThreads);
-        const int G = kThreads / QT;
+        const int GG = kThreads / QT;
         const int q = tid % QT, g = tid / QT;
         TA acc[VEC][3];
 #pragma unroll
         for (int e = 0; e < VEC; ++e) acc[e][0] = acc[e][1] = acc[e][2] = (TA)0;
-        if (g < G) {
+        if (g < GG) {
             const TF* vp = fa.Vb + (size_t)(cq0 + q) * VEC;
 #pragma unroll 4
-            for (int j = g; j < rec.n; j += G) {
+            for (int j = g; j < rec.n; j += GG) {
                 TA v[VEC];
                 Vec16<TF, TA>::load(vp + (size_t)j * Cp, v);
                 TA xa, xb, xc;
@@ -326,7 +330,7 @@ __global__ void __launch_bounds__(kThreads) fwd_big_kernel(
             }
         }
         __syncthreads();
-        if (g < G) {
+        if (g < GG) {
 #pragma unroll
             for (int e = 0; e < VEC; ++e)
 #pragma unroll
@@ -337,13 +341,132 @@ __global__ void __launch_bounds__(kThreads) fwd_big_kernel(
             const int c = cq0 * VEC + idx;
             if (c >= rec.C) continue;
             TA z[3] = {(TA)0, (TA)0, (TA)0};
-            for (int gg = 0; gg < G; ++gg)
+            for (int gg = 0; gg < GG; ++gg)
 #pragma unroll
                 for (int a = 0; a < 3; ++a) z[a] += red[(gg * QT * VEC + idx) * 3 + a];
-            write_w<TA>(rec, c, z, fa.SU, fa.wr, fa.c1, fa.c2);
+            write_w<TA>(rec, c, z[0], z[1], z[2], fa.SU, fa.wr, fa.c1, fa.c2, 1, 0);
         }
         __syncthreads();
     }
+}
+
+// Several (G) interleaved right-hand sides.  A block's work is the pairs
+// (column vector q, RHS chunk c of RC vectors); T threads (a warp, or the
+// CTA for a large block) take one pair each, with GG = T / pairs row groups
+// when there are fewer pairs than threads (partial sums added in a fixed
+// order through shared memory), else rounds of pairs over all rows.
+template <class TF, class TA, int RC, int T>
+__device__ __forceinline__ void fwd_multi_block(const FwdRec& rec, const FwdArgs<TF, TA, true>& fa, int G, int tid,
+                                                TA* red)
+{
+    constexpr int VEC = Vec16<TF, TA>::N;
+    constexpr int kPer = VEC * RC * 3;
+    const int Cp = (rec.C + 7) & ~7, Q = Cp / VEC;
+    const int NRC = (G + RC - 1) / RC;
+    const int pairs = Q * NRC;
+    const int GG = pairs >= T ? 1 : T / pairs;
+    for (int pr0 = 0; pr0 < pairs; pr0 += T) {
+        const int pr = pr0 + tid % min(pairs, T);
+        const int g = GG > 1 ? tid / pairs : (tid < pairs - pr0 ? 0 : GG);
+        const int q = pr % Q, c = pr / Q;
+        const int nq = min(RC, G - c * RC);
+        TA acc[VEC][RC][3];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e)
+#pragma unroll
+            for (int k = 0; k < RC; ++k) acc[e][k][0] = acc[e][k][1] = acc[e][k][2] = (TA)0;
+        if (g < GG) {
+            const TF* vp = fa.Vb + (size_t)q * VEC;
+            const TA* xp = fa.x0 + (size_t)c * RC * 4;
+#pragma unroll 2
+            for (int j = g; j < rec.n; j += GG) {
+                TA v[VEC];
+                Vec16<TF, TA>::load(vp + (size_t)j * Cp, v);
+                const TA* xr = xp + (size_t)j * G * 4;
+#pragma unroll
+                for (int k = 0; k < RC; ++k) {
+                    if (k >= nq) break;
+                    TA xa, xb, xc;
+                    load3(xr + k * 4, xa, xb, xc);
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) {
+                        acc[e][k][0] += v[e] * xa;
+                        acc[e][k][1] += v[e] * xb;
+                        acc[e][k][2] += v[e] * xc;
+                    }
+                }
+            }
+        }
+        if (GG == 1) {
+            if (g < GG) {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    const int col = q * VEC + e;
+                    if (col >= rec.C) continue;
+#pragma unroll
+                    for (int k = 0; k < RC; ++k) {
+                        if (k >= nq) break;
+                        write_w<TA>(rec, col, acc[e][k][0], acc[e][k][1], acc[e][k][2], fa.SU, fa.wr, fa.c1, fa.c2, G, c * RC + k);
+                    }
+                }
+            }
+        } else {
+            if (g < GG) {
+                TA* rp = red + (size_t)(g * pairs + pr) * kPer;
+#pragma unroll
+                for (int e = 0; e < VEC; ++e)
+#pragma unroll
+                    for (int k = 0; k < RC; ++k)
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) rp[(e * RC + k) * 3 + a] = acc[e][k][a];
+            }
+            if (T == 32) __syncwarp();
+            else __syncthreads();
+            for (int idx = tid; idx < pairs * VEC * RC; idx += T) {
+                const int pp = idx / (VEC * RC), rem = idx - pp * (VEC * RC);
+                const int e = rem / RC, k = rem - e * RC;
+                const int qq = pp % Q, cc = pp / Q;
+                const int col = qq * VEC + e, r = cc * RC + k;
+                if (col >= rec.C || r >= G) continue;
+                TA z[3] = {(TA)0, (TA)0, (TA)0};
+                for (int gg = 0; gg < GG; ++gg)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) z[a] += red[(size_t)(gg * pairs + pp) * kPer + (e * RC + k) * 3 + a];
+                write_w<TA>(rec, col, z[0], z[1], z[2], fa.SU, fa.wr, fa.c1, fa.c2, G, r);
+            }
+            if (T == 32) __syncwarp();
+            else __syncthreads();
+        }
+    }
+}
+
+template <class TF, class TA, bool ONE, int RC>
+__global__ void __launch_bounds__(kThreads) fwd_small_multi_kernel(
+    const FwdRec* __restrict__ recs, int64_t nrec, const __grid_constant__ MeshDev m0,
+    const MeshDev* __restrict__ meshes, const TA* __restrict__ xg, TA* __restrict__ w, int G)
+{
+    constexpr int kPer = Vec16<TF, TA>::N * RC * 3;
+    __shared__ TA red[kThreads / 32][32 * kPer];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t bi = (int64_t)blockIdx.x * (kThreads / 32) + warp;
+    if (bi >= nrec) return;
+    const FwdRec rec = recs[bi];
+    const FwdArgs<TF, TA, ONE> fa0(rec, m0, meshes, xg, w, G);
+    const FwdArgs<TF, TA, true>& fa = reinterpret_cast<const FwdArgs<TF, TA, true>&>(fa0);
+    fwd_multi_block<TF, TA, RC, 32>(rec, fa, G, lane, red[warp]);
+}
+
+template <class TF, class TA, bool ONE, int RC>
+__global__ void __launch_bounds__(kThreads) fwd_big_multi_kernel(
+    const FwdRec* __restrict__ recs, const __grid_constant__ MeshDev m0, const MeshDev* __restrict__ meshes,
+    const TA* __restrict__ xg, TA* __restrict__ w, int G)
+{
+    constexpr int kPer = Vec16<TF, TA>::N * RC * 3;
+    __shared__ TA red[kThreads * kPer];
+    const FwdRec rec = recs[blockIdx.x];
+    const FwdArgs<TF, TA, ONE> fa0(rec, m0, meshes, xg, w, G);
+    const FwdArgs<TF, TA, true>& fa = reinterpret_cast<const FwdArgs<TF, TA, true>&>(fa0);
+    fwd_multi_block<TF, TA, RC, kThreads>(rec, fa, G, threadIdx.x, red);
 }
 
 // ---------------------------------------------------------------- packing
@@ -473,13 +596,22 @@ int dalloc(hm_matrix& H, DevBuf& d, size_t bytes)
     return HM_OK;
 }
 
+// right-hand sides per consumer thread of the multi-vector kernels (the
+// fwd kernels use the same chunk): 16 accumulated rows x vectors for FP32
+// accumulation, 8 for FP64
+template <class TF, class TA>
+constexpr int multi_rc()
+{
+    return (sizeof(TA) == 8 ? 8 : 16) / Vec16<TF, TA>::N;
+}
+
 // per-device launch data of the streamed leaf kernel of one form
 struct StreamLaunch {
     int ctas_per_sm = 0;
     int nsm = 0;
 };
 
-template <class TF, class TN, class TA>
+template <class TF, class TN, class TA, int RC>
 int stream_launch(StreamLaunch& out)
 {
     constexpr int kMaxDevices = 64;
@@ -490,8 +622,8 @@ int stream_launch(StreamLaunch& out)
         out = cache[dev];
         return HM_OK;
     }
-    auto kern = stream::leaf_stream_kernel<TF, TN, TA>;
-    const size_t smem = stream::smem_bytes<TA>(stream::Smem16<TF, TA>::N);
+    auto kern = stream::leaf_stream_kernel<TF, TN, TA, RC>;
+    const size_t smem = stream::LeafCfg<TF, TA, RC>::smem();
     HM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     StreamLaunch l;
     HM_CUDA(cudaDeviceGetAttribute(&l.nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -502,20 +634,17 @@ int stream_launch(StreamLaunch& out)
     return HM_OK;
 }
 
-// The three phases of the product over every mesh of the plan.
-template <class TF, class TN, class TA>
-int run_product_t(const Plan& P, const double* x, double* y, int nrhs, int64_t ld, TA* xg, TA* w,
-                  cudaStream_t s, const hm_matrix* prof, const Sched& sc)
+// One launch of each phase for G right-hand sides (rows of x and y at
+// stride ld), with RC vectors per thread chunk.
+template <class TF, class TN, class TA, int RC>
+int run_phases(const Plan& P, const double* x, double* y, int G, int64_t ld, TA* xg, TA* w, int* counter,
+               cudaStream_t s, const hm_matrix* prof, const Sched& sc)
 {
-    constexpr int Rs = stream::Smem16<TF, TA>::N;
-    const int mpmax = (P.max_leaf + 7) & ~7;
-    if (mpmax / Rs > stream::kConsumers || 6 * mpmax * (int)sizeof(TN) > stream::kStageBytes)
-        return fail(HM_EINVAL, "product: a leaf of %d rows does not fit the streamed kernel", P.max_leaf);
-    const unsigned nr = (unsigned)nrhs;
     if (prof) prof_mark(*prof, 0, s);
     if (P.npos > 0) {
-        gather_kernel<TA><<<dim3((unsigned)((P.npos + 255) / 256), nr), 256, 0, s>>>(
-            P.meshes, P.nmesh, P.pos_prefix, P.npos, x, ld, xg, P.xg_ld);
+        const int64_t n = P.npos * G;
+        gather_kernel<TA><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P.meshes, P.nmesh, P.pos_prefix, P.npos, x,
+                                                                      ld, xg, G);
         HM_CUDA(cudaGetLastError());
     }
     if (prof) prof_mark(*prof, 1, s);
@@ -527,15 +656,26 @@ int run_product_t(const Plan& P, const double* x, double* y, int nrhs, int64_t l
         HM_CUDA(cudaStreamWaitEvent(sc.side, sc.fork, 0));
     }
     if (P.nbig > 0) {
-        auto kb = one ? fwd_big_kernel<TF, TA, true> : fwd_big_kernel<TF, TA, false>;
-        kb<<<dim3((unsigned)P.nbig, nr), kThreads, 0, fork ? sc.side : s>>>(P.fwd, m0, P.meshes, xg, w, P.xg_ld,
-                                                                          P.w_ld);
+        const unsigned nb = (unsigned)P.nbig;
+        cudaStream_t sb = fork ? sc.side : s;
+        if (RC == 1) {
+            auto kb = one ? fwd_big_kernel<TF, TA, true> : fwd_big_kernel<TF, TA, false>;
+            kb<<<nb, kThreads, 0, sb>>>(P.fwd, m0, P.meshes, xg, w);
+        } else {
+            auto kb = one ? fwd_big_multi_kernel<TF, TA, true, RC> : fwd_big_multi_kernel<TF, TA, false, RC>;
+            kb<<<nb, kThreads, 0, sb>>>(P.fwd, m0, P.meshes, xg, w, G);
+        }
         HM_CUDA(cudaGetLastError());
     }
     if (P.nsmall > 0) {
         const unsigned nb = (unsigned)((P.nsmall + kThreads / 32 - 1) / (kThreads / 32));
-        auto ks = one ? fwd_small_kernel<TF, TA, true> : fwd_small_kernel<TF, TA, false>;
-        ks<<<dim3(nb, nr), kThreads, 0, s>>>(P.fwd + P.nbig, P.nsmall, m0, P.meshes, xg, w, P.xg_ld, P.w_ld);
+        if (RC == 1) {
+            auto ks = one ? fwd_small_kernel<TF, TA, true> : fwd_small_kernel<TF, TA, false>;
+            ks<<<nb, kThreads, 0, s>>>(P.fwd + P.nbig, P.nsmall, m0, P.meshes, xg, w);
+        } else {
+            auto ks = one ? fwd_small_multi_kernel<TF, TA, true, RC> : fwd_small_multi_kernel<TF, TA, false, RC>;
+            ks<<<nb, kThreads, 0, s>>>(P.fwd + P.nbig, P.nsmall, m0, P.meshes, xg, w, G);
+        }
         HM_CUDA(cudaGetLastError());
     }
     if (fork) {
@@ -545,17 +685,42 @@ int run_product_t(const Plan& P, const double* x, double* y, int nrhs, int64_t l
     if (prof) prof_mark(*prof, 2, s);
     if (P.nwork > 0) {
         StreamLaunch l;
-        int rc = stream_launch<TF, TN, TA>(l);
+        int rc = stream_launch<TF, TN, TA, RC>(l);
         if (rc) return rc;
-        const size_t smem = stream::smem_bytes<TA>(Rs);
+        const size_t smem = stream::LeafCfg<TF, TA, RC>::smem();
         const int per_sm = sc.ctas_per_sm > 0 ? std::min(sc.ctas_per_sm, l.ctas_per_sm) : l.ctas_per_sm;
         const int64_t ncta = std::min<int64_t>(P.nwork, (int64_t)l.nsm * per_sm);
-        HM_CUDA(cudaMemsetAsync(P.counters, 0, (size_t)nrhs * sizeof(int), s));
-        stream::leaf_stream_kernel<TF, TN, TA><<<dim3((unsigned)ncta, nr), stream::kThreads, smem, s>>>(
-            P.work, (int)P.nwork, P.meshes, P.counters, P.err, xg, w, P.xg_ld, P.w_ld, y, ld);
+        stream::leaf_stream_kernel<TF, TN, TA, RC><<<(unsigned)ncta, stream::kThreads, smem, s>>>(
+            P.work, (int)P.nwork, P.meshes, counter, P.err, xg, w, G, y, ld);
         HM_CUDA(cudaGetLastError());
     }
     if (prof) prof_mark(*prof, 3, s);
+    return HM_OK;
+}
+
+// The product over every mesh of the plan: one vector with the single-vector
+// kernels, several in launches of up to Gmax interleaved vectors each.
+template <class TF, class TN, class TA>
+int run_product_t(const Plan& P, const double* x, double* y, int nrhs, int64_t ld, TA* xg, TA* w,
+                  cudaStream_t s, const hm_matrix* prof, const Sched& sc)
+{
+    constexpr int Rr = stream::Smem16<TF, TA>::N;
+    constexpr int RC = multi_rc<TF, TA>();
+    const int mpmax = std::max((P.max_leaf + 7) & ~7, 8);
+    if (mpmax / Rr > stream::kConsumers || 6 * mpmax * (int)sizeof(TN) > stream::kStageBytes)
+        return fail(HM_EINVAL, "product: a leaf of %d rows does not fit the streamed kernel", P.max_leaf);
+    if (P.nwork > 0) HM_CUDA(cudaMemsetAsync(P.counters, 0, (size_t)nrhs * sizeof(int), s));
+    if (nrhs == 1) return run_phases<TF, TN, TA, 1>(P, x, y, 1, ld, xg, w, P.counters, s, prof, sc);
+    // every (row block, RHS chunk) pair of the largest leaf needs a consumer
+    // thread; at most 32 vectors keep at least 16 segments per slot
+    const int Gmax = std::min(32, RC * (stream::kConsumers / (mpmax / Rr)));
+    int k = 0;
+    for (int r0 = 0; r0 < nrhs; r0 += Gmax, ++k) {
+        const int G = std::min(Gmax, nrhs - r0);
+        int rc = run_phases<TF, TN, TA, RC>(P, x + (size_t)r0 * ld, y + (size_t)r0 * ld, G, ld, xg, w,
+                                            P.counters + k, s, k == 0 ? prof : nullptr, sc);
+        if (rc) return rc;
+    }
     return HM_OK;
 }
 
@@ -598,20 +763,25 @@ int pack_near(hm_matrix& H, DevBuf& dst, cudaStream_t s)
 
 }  // namespace
 
+template <class TF, class TN, class TA>
+int prepare_t(int* ctas_per_sm)
+{
+    StreamLaunch l1, lm;
+    int rc = stream_launch<TF, TN, TA, 1>(l1);
+    if (!rc) rc = stream_launch<TF, TN, TA, multi_rc<TF, TA>()>(lm);
+    if (!rc && ctas_per_sm) *ctas_per_sm = std::max(l1.ctas_per_sm, lm.ctas_per_sm);
+    return rc;
+}
+
 int product_prepare(int32_t form, int* ctas_per_sm)
 {
-    StreamLaunch l;
-    int rc;
     switch (form) {
-        case HM_FP64: rc = stream_launch<double, double, double>(l); break;
-        case HM_FP32: rc = stream_launch<float, float, float>(l); break;
-        case HM_BF16: rc = stream_launch<__nv_bfloat16, float, float>(l); break;
-        case HM_FP16: rc = stream_launch<__half, float, float>(l); break;
+        case HM_FP64: return prepare_t<double, double, double>(ctas_per_sm);
+        case HM_FP32: return prepare_t<float, float, float>(ctas_per_sm);
+        case HM_BF16: return prepare_t<__nv_bfloat16, float, float>(ctas_per_sm);
+        case HM_FP16: return prepare_t<__half, float, float>(ctas_per_sm);
         default: return fail(HM_EINVAL, "product: unknown form %d", form);
     }
-    if (rc) return rc;
-    if (ctas_per_sm) *ctas_per_sm = l.ctas_per_sm;
-    return HM_OK;
 }
 
 int run_product(const Plan& P, int32_t form, const double* x, double* y, int32_t nrhs, int64_t ld, void* xg,
@@ -689,8 +859,6 @@ int matvec_device_scratch(const hm_matrix& H, const double* x, double* y, int32_
     P.max_leaf = H.max_leaf;
     P.counters = scr.counters;
     P.err = H.d_err.as<int>();
-    P.xg_ld = 4 * H.M;
-    P.w_ld = H.w_total;
     return run_product(P, form, x, y, nrhs, ld, scr.xg, scr.w, s, scr.profile ? &H : nullptr);
 }
 
@@ -763,6 +931,7 @@ int hm_pack(hm_matrix* H, int32_t form, void* stream)
     if (!H) return fail(HM_EINVAL, "hm_pack: NULL matrix");
     if (form < HM_FP64 || form > HM_FP16) return fail(HM_EINVAL, "hm_pack: unknown form %d", form);
     if (H->packed[form]) return HM_OK;
+    if (H->compacted) return fail(HM_EINVAL, "hm_pack: FP64 data released (hm_compact); pack before compacting");
     cudaStream_t s = (cudaStream_t)stream;
     cudaStream_t saved = H->alloc.stream;
     H->alloc.stream = s;

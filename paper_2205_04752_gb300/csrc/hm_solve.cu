@@ -138,6 +138,8 @@ extern "C" int hm_solve(const hm_matrix* H, const double* g, double* t, const hm
     if (p.inner_tol <= 0.0) p.inner_tol = 1e-3;
     if (p.max_inner <= 0) p.max_inner = 1000;
     if (p.max_refine <= 0) p.max_refine = 20;
+    if (!H->packed[HM_FP64])
+        return fail(HM_EINVAL, "hm_solve: the FP64 form (residuals) was released by hm_compact");
     if (p.inner_form < HM_FP64 || p.inner_form > HM_FP16 || !H->packed[p.inner_form])
         return fail(HM_EINVAL, "hm_solve: inner form %d not available (hm_pack first)", p.inner_form);
     if (info) std::memset(info, 0, sizeof *info);

@@ -12,10 +12,13 @@
 // (near field).  Consecutive segments of one (block, kernel) item have
 // consecutive factor columns (and of one near block consecutive positions),
 // so these are a few contiguous bulk copies per slot, one per item and lane.
-// Warps 1..7 consume the slots from shared memory only: thread (p, h) owns R
-// rows (16 bytes of U) and every H-th segment of a slot; at the end of a leaf
-// the H partial sums of each row are added in a fixed order and y is written
-// in the original dof order.  Deterministic.
+// Warps 1..7 consume the slots from shared memory only: thread (p, c, h) owns
+// Rr rows (16 bytes of U), a chunk of RC right-hand sides and every H-th
+// segment of a slot; at the end of a leaf the H partial sums of each row are
+// added in a fixed order and y is written in the original dof order.
+// Deterministic for a given number G of right-hand sides per launch (H, the
+// segment split, depends on G, so the same vector applied in launches of
+// different width agrees to the rounding of the accumulation type).
 //
 // Every mbarrier wait is bounded (kWaitCycles); on expiry the thread records
 // an error in *err, the producer drains its own copies in flight (again
@@ -197,30 +200,40 @@ __device__ __forceinline__ void smem_rows(const T* p, TA* o)
     for (int q = 0; q < R / N; ++q) Smem16<T, TA>::load(p + q * N, o + q * N);
 }
 
-template <class TA>
-size_t smem_bytes(int R)
-{
-    return (size_t)kStages * kStageBytes + (size_t)kStages * kMaxSeg * 4 * sizeof(TA) +
-           (size_t)kConsumers * R * 3 * sizeof(TA);
-}
+// Right-hand sides: a launch serves G of them at once (the vectors are
+// interleaved, 4-vector (position or column, r) at index pos * G + r).  A
+// consumer thread holds Rr rows (16 bytes of U) for RC right-hand sides.
+// RC = 1 is the single-vector kernel; RC * Rr = 16 otherwise.
+template <class TF, class TA, int RC>
+struct LeafCfg {
+    static constexpr int Rr = Smem16<TF, TA>::N;
+    // 4-vectors of w / x staged beside each slot
+    static constexpr int kAuxBytes = RC == 1 ? kMaxSeg * 4 * (int)sizeof(TA) : 16384;
+    static constexpr size_t smem()
+    {
+        return (size_t)kStages * kStageBytes + (size_t)kStages * kAuxBytes +
+               (size_t)kConsumers * Rr * RC * 3 * sizeof(TA);
+    }
+};
 
-template <class TF, class TN, class TA>
+template <class TF, class TN, class TA, int RC>
 __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
-    const int2* __restrict__ work, int nwork, const MeshDev* __restrict__ meshes, int* __restrict__ counters,
-    int* __restrict__ err, const TA* __restrict__ xg_base, const TA* __restrict__ w_base, int64_t xg_ld,
-    int64_t w_ld, double* __restrict__ y, int64_t ld)
+    const int2* __restrict__ work, int nwork, const MeshDev* __restrict__ meshes, int* __restrict__ counter,
+    int* __restrict__ err, const TA* __restrict__ xg_base, const TA* __restrict__ w_base, int G,
+    double* __restrict__ y, int64_t ld)
 {
-    constexpr int R = Smem16<TF, TA>::N;  // rows per consumer thread: 16 bytes of U
+    using Cfg = LeafCfg<TF, TA, RC>;
+    constexpr int Rr = Cfg::Rr;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* sbuf = smem;
-    TA* aux = reinterpret_cast<TA*>(smem + kStages * kStageBytes);  // kStages x kMaxSeg x 4
-    TA* red = aux + kStages * kMaxSeg * 4;
+    unsigned char* auxb = smem + kStages * kStageBytes;  // kStages x kAuxBytes
+    TA* red = reinterpret_cast<TA*>(auxb + kStages * Cfg::kAuxBytes);
     __shared__ __align__(8) uint64_t full[kStages];
     __shared__ __align__(8) uint64_t empty[kStages];
     __shared__ StageMeta meta[kStages];
 
-    const int r = blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int vecG = 4 * G;  // TA values per segment / column in the staged vectors
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
@@ -238,7 +251,7 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
         // are the stream's (start, vector index) records (sentinel last, ni
         // records); *cur is the item containing `first` and is advanced to
         // the item containing first + count.  vec: the 4-vectors the stream
-        // reads (w for the far field, x for the near field).
+        // reads (w for the far field, x for the near field), G per index.
         auto emit = [&](int mesh, int lf, int kind, int first, int count, int last, const void* src,
                         uint32_t bytes, const int2* items, int ni, int* cur, const TA* vec) -> bool {
             const int slot = it % kStages;
@@ -255,11 +268,11 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
                 m.pad[0] = mesh;
                 meta[slot] = m;
                 if (kind < 2)
-                    mbar_arrive_expect_tx(&full[slot], bytes + (uint32_t)(count * 4 * sizeof(TA)));
+                    mbar_arrive_expect_tx(&full[slot], bytes + (uint32_t)(count * vecG * sizeof(TA)));
             }
             __syncwarp();
             if (kind < 2) {
-                TA* av = aux + (size_t)slot * kMaxSeg * 4;
+                TA* av = reinterpret_cast<TA*>(auxb + (size_t)slot * Cfg::kAuxBytes);
                 const int end = first + count;
                 int q0 = *cur;
                 for (;;) {
@@ -273,8 +286,8 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
                     if (overlap) {
                         const int g0 = max(a.x, first), g1 = min(b, end);
                         if (g0 < g1)
-                            bulk_g2s(av + (size_t)(g0 - first) * 4, vec + (size_t)(a.y + (g0 - a.x)) * 4,
-                                     (uint32_t)((g1 - g0) * 4 * sizeof(TA)), &full[slot]);
+                            bulk_g2s(av + (size_t)(g0 - first) * vecG, vec + (size_t)(a.y + (g0 - a.x)) * vecG,
+                                     (uint32_t)((g1 - g0) * vecG * sizeof(TA)), &full[slot]);
                     }
                     const unsigned ov = __ballot_sync(0xffffffffu, overlap);
                     const int nov = __popc(ov);  // overlapping items are a prefix of the lanes
@@ -293,9 +306,10 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
             ++it;
             return true;
         };
+        const int perV = min(kMaxSeg, Cfg::kAuxBytes / (vecG * (int)sizeof(TA)));
         for (;;) {
             int idx = 0;
-            if (lane == 0) idx = atomicAdd(&counters[r], 1);
+            if (lane == 0) idx = atomicAdd(counter, 1);
             idx = __shfl_sync(0xffffffffu, idx, 0);
             if (idx >= nwork || !ok) break;
             const int2 wk = work[idx];
@@ -309,12 +323,12 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
             const int Sn = md.ln_items[ni1 - 1].col_start;
             const TF* Ul = static_cast<const TF*>(md.Ul);
             const TN* Nl = static_cast<const TN*>(md.Nl);
-            const TA* wvec = w_base + (size_t)r * w_ld + md.woff;
-            const TA* xvec = xg_base + (size_t)r * xg_ld + md.xgoff;
+            const TA* wvec = w_base + (size_t)md.woff * vecG;
+            const TA* xvec = xg_base + (size_t)md.xgoff * vecG;
             const int segB = mp * (int)sizeof(TF);
-            const int perF = min(kStageBytes / segB, kMaxSeg);
+            const int perF = min(kStageBytes / segB, perV);
             const int colB = 6 * mp * (int)sizeof(TN);
-            const int perN = min(kStageBytes / colB, kMaxSeg);
+            const int perN = min(kStageBytes / colB, perV);
             if (perF < 1 || perN < 1) {
                 // a segment or a near column larger than a stage (the host
                 // rejects such leaves before the launch): stop producing
@@ -350,12 +364,15 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
     }
 
     // ---------------------------------------------------------------- consumers
+    // thread (p, c, h): row block p (Rr rows), RHS chunk c (RC vectors),
+    // segment group h (every H-th segment / column of each slot)
     const int ctid = threadIdx.x - 32;
-    int cur = -1, cur_mesh = -1, P = 1, H = 0, p = 0, h = 0, t0 = 0, mt = 0, mp = 8;
+    const int NRC = (G + RC - 1) / RC;
+    int cur = -1, cur_mesh = -1, P = 1, H = 0, p = 0, c = 0, h = 0, t0 = 0, mt = 0, mp = 8;
     const int32_t* perm = nullptr;
     int64_t xoff = 0;
     TA c1 = (TA)0, c2 = (TA)0;
-    TA acc[R][3];
+    TA acc[Rr][RC][3];
     for (int it = 0;; ++it) {
         const int slot = it % kStages;
         if (!mbar_wait(&full[slot], (uint32_t)(it / kStages) & 1u, err)) break;
@@ -372,63 +389,90 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
             c1 = (TA)md.c1;
             c2 = (TA)md.c2;
             mp = (mt + 7) & ~7;
-            P = mp / R;
-            H = kConsumers / P;
+            P = mp / Rr;
+            H = kConsumers / (P * NRC);
             p = ctid % P;
-            h = ctid / P;
+            c = (ctid / P) % NRC;
+            h = ctid / (P * NRC);
 #pragma unroll
-            for (int e = 0; e < R; ++e) acc[e][0] = acc[e][1] = acc[e][2] = (TA)0;
+            for (int e = 0; e < Rr; ++e)
+#pragma unroll
+                for (int q = 0; q < RC; ++q) acc[e][q][0] = acc[e][q][1] = acc[e][q][2] = (TA)0;
         }
-        const TA* av = aux + (size_t)slot * kMaxSeg * 4;
+        const TA* av = reinterpret_cast<const TA*>(auxb + (size_t)slot * Cfg::kAuxBytes) + (size_t)c * RC * 4;
         if (h < H) {
             if (m.kind == 0) {
-                const TF* sb = reinterpret_cast<const TF*>(sbuf + (size_t)slot * kStageBytes) + p * R;
-                int s = h;
-                for (; s + H < m.count; s += 2 * H) {
-                    TA wa0, wa1, wa2, wb0, wb1, wb2;
-                    load3(av + (size_t)s * 4, wa0, wa1, wa2);
-                    load3(av + (size_t)(s + H) * 4, wb0, wb1, wb2);
-                    TA ua[R], ub[R];
-                    smem_rows<TF, TA, R>(sb + (size_t)s * mp, ua);
-                    smem_rows<TF, TA, R>(sb + (size_t)(s + H) * mp, ub);
+                const TF* sb = reinterpret_cast<const TF*>(sbuf + (size_t)slot * kStageBytes) + p * Rr;
+                if (RC == 1 && G == 1) {
+                    // single vector: two segments per iteration
+                    int s = h;
+                    for (; s + H < m.count; s += 2 * H) {
+                        TA wa0, wa1, wa2, wb0, wb1, wb2;
+                        load3(av + (size_t)s * 4, wa0, wa1, wa2);
+                        load3(av + (size_t)(s + H) * 4, wb0, wb1, wb2);
+                        TA ua[Rr], ub[Rr];
+                        smem_rows<TF, TA, Rr>(sb + (size_t)s * mp, ua);
+                        smem_rows<TF, TA, Rr>(sb + (size_t)(s + H) * mp, ub);
 #pragma unroll
-                    for (int e = 0; e < R; ++e) {
-                        acc[e][0] += ua[e] * wa0 + ub[e] * wb0;
-                        acc[e][1] += ua[e] * wa1 + ub[e] * wb1;
-                        acc[e][2] += ua[e] * wa2 + ub[e] * wb2;
+                        for (int e = 0; e < Rr; ++e) {
+                            acc[e][0][0] += ua[e] * wa0 + ub[e] * wb0;
+                            acc[e][0][1] += ua[e] * wa1 + ub[e] * wb1;
+                            acc[e][0][2] += ua[e] * wa2 + ub[e] * wb2;
+                        }
                     }
-                }
-                if (s < m.count) {
-                    TA wa0, wa1, wa2;
-                    load3(av + (size_t)s * 4, wa0, wa1, wa2);
-                    TA ua[R];
-                    smem_rows<TF, TA, R>(sb + (size_t)s * mp, ua);
+                    if (s < m.count) {
+                        TA wa0, wa1, wa2;
+                        load3(av + (size_t)s * 4, wa0, wa1, wa2);
+                        TA ua[Rr];
+                        smem_rows<TF, TA, Rr>(sb + (size_t)s * mp, ua);
 #pragma unroll
-                    for (int e = 0; e < R; ++e) {
-                        acc[e][0] += ua[e] * wa0;
-                        acc[e][1] += ua[e] * wa1;
-                        acc[e][2] += ua[e] * wa2;
+                        for (int e = 0; e < Rr; ++e) {
+                            acc[e][0][0] += ua[e] * wa0;
+                            acc[e][0][1] += ua[e] * wa1;
+                            acc[e][0][2] += ua[e] * wa2;
+                        }
+                    }
+                } else {
+                    for (int s = h; s < m.count; s += H) {
+                        TA ua[Rr];
+                        smem_rows<TF, TA, Rr>(sb + (size_t)s * mp, ua);
+#pragma unroll
+                        for (int q = 0; q < RC; ++q) {
+                            if (RC > 1 && c * RC + q >= G) break;
+                            TA w0, w1, w2;
+                            load3(av + ((size_t)s * G + q) * 4, w0, w1, w2);
+#pragma unroll
+                            for (int e = 0; e < Rr; ++e) {
+                                acc[e][q][0] += ua[e] * w0;
+                                acc[e][q][1] += ua[e] * w1;
+                                acc[e][q][2] += ua[e] * w2;
+                            }
+                        }
                     }
                 }
             } else {
-                const TN* sb = reinterpret_cast<const TN*>(sbuf + (size_t)slot * kStageBytes) + p * R;
+                const TN* sb = reinterpret_cast<const TN*>(sbuf + (size_t)slot * kStageBytes) + p * Rr;
                 for (int s = h; s < m.count; s += H) {
-                    TA x0, x1, x2;
-                    load3(av + (size_t)s * 4, x0, x1, x2);
                     const TN* e0 = sb + (size_t)s * 6 * mp;
-                    TA v11[R], v12[R], v13[R], v22[R], v23[R], v33[R];
-                    smem_rows<TN, TA, R>(e0, v11);
-                    smem_rows<TN, TA, R>(e0 + mp, v12);
-                    smem_rows<TN, TA, R>(e0 + 2 * mp, v13);
-                    smem_rows<TN, TA, R>(e0 + 3 * mp, v22);
-                    smem_rows<TN, TA, R>(e0 + 4 * mp, v23);
-                    smem_rows<TN, TA, R>(e0 + 5 * mp, v33);
+                    TA v11[Rr], v12[Rr], v13[Rr], v22[Rr], v23[Rr], v33[Rr];
+                    smem_rows<TN, TA, Rr>(e0, v11);
+                    smem_rows<TN, TA, Rr>(e0 + mp, v12);
+                    smem_rows<TN, TA, Rr>(e0 + 2 * mp, v13);
+                    smem_rows<TN, TA, Rr>(e0 + 3 * mp, v22);
+                    smem_rows<TN, TA, Rr>(e0 + 4 * mp, v23);
+                    smem_rows<TN, TA, Rr>(e0 + 5 * mp, v33);
 #pragma unroll
-                    for (int e = 0; e < R; ++e) {
-                        const TA vd = c1 * (v11[e] + v22[e] + v33[e]);
-                        acc[e][0] += vd * x0 + c2 * (v11[e] * x0 + v12[e] * x1 + v13[e] * x2);
-                        acc[e][1] += vd * x1 + c2 * (v12[e] * x0 + v22[e] * x1 + v23[e] * x2);
-                        acc[e][2] += vd * x2 + c2 * (v13[e] * x0 + v23[e] * x1 + v33[e] * x2);
+                    for (int q = 0; q < RC; ++q) {
+                        if (RC > 1 && c * RC + q >= G) break;
+                        TA x0, x1, x2;
+                        load3(av + ((size_t)s * G + q) * 4, x0, x1, x2);
+#pragma unroll
+                        for (int e = 0; e < Rr; ++e) {
+                            const TA vd = c1 * (v11[e] + v22[e] + v33[e]);
+                            acc[e][q][0] += vd * x0 + c2 * (v11[e] * x0 + v12[e] * x1 + v13[e] * x2);
+                            acc[e][q][1] += vd * x1 + c2 * (v12[e] * x0 + v22[e] * x1 + v23[e] * x2);
+                            acc[e][q][2] += vd * x2 + c2 * (v13[e] * x0 + v23[e] * x1 + v33[e] * x2);
+                        }
                     }
                 }
             }
@@ -437,17 +481,26 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[slot]);
         if (m.last) {
+            // red[((h * P + p) * NRC + c)][e][q][a]
+            constexpr int kPer = Rr * RC * 3;
             if (h < H) {
+                TA* rp = red + (size_t)((h * P + p) * NRC + c) * kPer;
 #pragma unroll
-                for (int e = 0; e < R; ++e)
+                for (int e = 0; e < Rr; ++e)
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) red[((h * P + p) * R + e) * 3 + a] = acc[e][a];
+                    for (int q = 0; q < RC; ++q)
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) rp[(e * RC + q) * 3 + a] = acc[e][q][a];
             }
             named_barrier_consumers();
-            for (int idx = ctid; idx < mt * 3; idx += kConsumers) {
-                const int i = idx / 3, a = idx - 3 * i;
+            const int per_row = 3 * G;
+            for (int idx = ctid; idx < mt * per_row; idx += kConsumers) {
+                const int i = idx / per_row, rem = idx - i * per_row;
+                const int r = rem / 3, a = rem - 3 * r;
+                const int pp = i / Rr, e = i - pp * Rr, cc = r / RC, q = r - cc * RC;
                 TA sum = (TA)0;
-                for (int g = 0; g < H; ++g) sum += red[((g * P) * R + i) * 3 + a];
+                for (int g = 0; g < H; ++g)
+                    sum += red[(size_t)((g * P + pp) * NRC + cc) * kPer + (e * RC + q) * 3 + a];
                 y[(size_t)r * ld + xoff + 3 * (size_t)perm[t0 + i] + a] = (double)sum;
             }
             named_barrier_consumers();

@@ -148,3 +148,34 @@ def test_batch_argument_errors():
         B.matvec(x, torch.zeros_like(x))  # nrhs above max_rhs
     with pytest.raises(binding.HMError):
         B.set_schedule(work_order=2)
+
+
+def test_compact_keeps_the_packed_form_and_releases_fp64():
+    V, T = inputs.icosphere(3)
+    tr = binding.build_cluster_tree(V, T, 32, 0.8)
+    H = binding.aca_assemble(tr, 1.0, 0.3, 1e-4, max_rhs=1)
+    H.pack("fp16")
+    x = torch.tensor(inputs.uniform_rhs(3 * len(T), 4), device="cuda")[0]
+    y0 = _alone(H, x, "fp16")
+    torch.cuda.synchronize()
+    before = H.footprint()
+    H.compact()
+    after = H.footprint()
+    assert after < 0.6 * before, (before, after)
+    y1 = _alone(H, x, "fp16")
+    torch.cuda.synchronize()
+    assert torch.equal(y0, y1)
+    with pytest.raises(binding.HMError):
+        _alone(H, x, "fp64")
+    with pytest.raises(binding.HMError):
+        H.pack("fp32")
+    with pytest.raises(binding.HMError):
+        H.near_block(0, 1, 1)
+    with pytest.raises(binding.HMError):
+        binding.solve(H, x, torch.zeros_like(x))
+    # a compacted matrix still joins a batch in its packed form
+    B = binding.Batch([H], "fp16", max_rhs=1)
+    y2 = torch.empty_like(x)
+    B.matvec(x, y2)
+    torch.cuda.synchronize()
+    assert torch.equal(y0, y2)

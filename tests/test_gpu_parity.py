@@ -118,6 +118,42 @@ def test_deterministic_and_multi_rhs_consistent():
         np.testing.assert_allclose(ys[0], y1[r], rtol=0, atol=1e-14 * np.abs(y1[r]).max())
 
 
+@pytest.mark.parametrize("form", ["fp16", "fp32", "bf16", "fp64"])
+def test_multi_rhs_launches_match_single_vector_products(form):
+    """Several right-hand sides share one pass over the factors (interleaved
+    vectors, up to 32 per launch): each row agrees with the single-vector
+    product to the rounding of the accumulation type, and repeats are bitwise
+    equal."""
+    if "c32" not in _cache:
+        V, T = inputs.icosphere(3)
+        _cache["c32"] = Case(V, T, 32, max_rhs=32)
+    c = _cache["c32"]
+    if form != "fp64":
+        c.H.pack(form)
+    tol = 1e-13 if form == "fp64" else 2e-6
+    for nrhs in (2, 7, 32):
+        x = inputs.uniform_rhs(3 * c.M, 40 + nrhs, nrhs=nrhs)
+        y = c.matvec(x, form)
+        np.testing.assert_array_equal(y, c.matvec(x, form))
+        for r in sorted({0, nrhs // 2, nrhs - 1}):
+            ys = c.matvec(x[r], form)[0]
+            assert _rel(y[r], ys) <= tol, (nrhs, r)
+
+
+def test_multi_rhs_split_into_several_launches():
+    """Leaves of 300 rows in FP64 leave room for only 4 vectors per launch:
+    10 right-hand sides run as launches of 4, 4 and 2; every row matches the
+    oracle's H-matrix product."""
+    V, T = inputs.ellipsoid(10, 0.6, 1.7, 1.1)
+    c = Case(V, T, 336, max_rhs=10)
+    c.Ho.assemble()
+    x = inputs.uniform_rhs(3 * c.M, 9, nrhs=10)
+    y = c.matvec(x)
+    yo = c.Ho.matvec(E, NU, x)
+    for r in range(10):
+        assert _rel(y[r], yo[r]) <= 1e-12, r
+
+
 def test_host_entry_point_equals_device_entry_point():
     c = c1()
     x = inputs.uniform_rhs(3 * c.M, 3, nrhs=2)
