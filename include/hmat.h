@@ -36,6 +36,7 @@ extern "C" {
 #define HM_ETIMEOUT (-4)  /* a bounded device wait ran out; the context stays usable */
 #define HM_EDEVICE (-5)   /* a CUDA call failed */
 #define HM_ERANK (-6)     /* an ACA block reached the rank cap (result kept, flagged) */
+#define HM_EBUSY (-7)     /* request rejected by admission (queue full or footprint too large) */
 
 /* storage / arithmetic forms of the H-matrix-vector product */
 #define HM_FP64 0 /* factors and near field FP64, FP64 accumulation ("plain form") */
@@ -237,12 +238,79 @@ int hm_batch_check(const hm_batch* B);
 void hm_batch_destroy(hm_batch* B);
 
 /* ---------------------------------------------------------------------------
+ * hm_server -- a request loop over resident H-matrices (a library service;
+ * the paper solves one problem at a time).  Matvec requests (y = V_h x for
+ * 1..32 vectors, Section 2's product) and solve requests (hm_solve's GMRES
+ * with iterative refinement) on any of the server's matrices arrive over
+ * time.  A request is admitted, in arrival order, as soon as one of `slots`
+ * worker streams is free AND its device footprint fits in the free part of
+ * a fixed arena of budget_bytes (its vectors, the product workspace and, for
+ * a solve, the Krylov basis); admitted requests run concurrently on their
+ * own streams, so their kernels overlap on the device while later arrivals
+ * keep being admitted.  Arrivals that find queue_cap requests waiting, or
+ * whose footprint exceeds the arena, are rejected (HM_EBUSY).
+ * Every request runs the kernels it would run alone, with its own
+ * workspace: its result is bitwise the same alone and in any mix.
+ * The matrices must stay alive and unchanged while the server exists; the
+ * arena is allocated once through the first matrix's allocator.
+ * ------------------------------------------------------------------------- */
+typedef struct hm_server hm_server;
+
+#define HM_REQ_MATVEC 0
+#define HM_REQ_SOLVE 1
+
+typedef struct {
+    int32_t slots;          /* requests in flight at most (1..64 worker streams) */
+    int32_t queue_cap;      /* waiting requests at most; later arrivals are rejected */
+    int64_t budget_bytes;   /* device arena for the footprints of requests in flight */
+    int32_t matvec_form;    /* packed form of matvec requests */
+    int32_t inner_form;     /* solve: GMRES product form */
+    int32_t residual_form;  /* solve: refinement residual form */
+    int32_t restart;        /* solve: GMRES restart (0 = 30) */
+    double inner_tol;       /* solve: residual reduction per GMRES solve (0 = 1e-3) */
+    int32_t max_inner;      /* solve: cap on inner products (0 = 1000) */
+    int32_t pad;
+} hm_server_params;
+
+typedef struct {
+    double arrival_s;      /* seconds after the start of hm_server_run */
+    int32_t mesh;          /* index into the server's matrices */
+    int32_t kind;          /* HM_REQ_MATVEC or HM_REQ_SOLVE */
+    int32_t nrhs;          /* matvec: 1..32 vectors; solve: ignored (1) */
+    int32_t seed;          /* inputs drawn on the device when x_host is NULL */
+    double tol;            /* solve: relative residual target (0 = 1e-6) */
+    const double* x_host;  /* nrhs x 3M inputs (matvec x, solve g) or NULL */
+    double* y_host;        /* nrhs x 3M results (matvec y, solve t) or NULL */
+} hm_request;
+
+typedef struct {
+    int32_t status;        /* HM_OK, HM_ENOTCONV (solve), HM_EBUSY (rejected), other errors */
+    int32_t iterations;    /* solve: inner GMRES iterations */
+    double arrival_s;      /* request arrival (0 when not replayed in real time) */
+    double start_s;        /* admission */
+    double done_s;         /* completion, results copied back */
+    double rel_residual;   /* solve: final relative residual in residual_form */
+} hm_result;
+
+int hm_server_create(const hm_matrix* const* mats, int32_t nmat, const hm_server_params* p,
+                     hm_server** out);
+/* device bytes request q would hold while in flight */
+int hm_server_footprint(const hm_server* S, const hm_request* q, int64_t* bytes);
+/* Serve n requests and return when all are finished or rejected.
+ * realtime != 0: request i arrives at reqs[i].arrival_s (sorted); otherwise
+ * all arrive at once.  Inputs with x_host == NULL are uniform[-1, 1) values
+ * from a counter-based generator (splitmix64 of the seed and the index).
+ * Blocks the calling thread (which schedules); one worker thread per slot. */
+int hm_server_run(hm_server* S, const hm_request* reqs, int32_t n, int32_t realtime, hm_result* out);
+void hm_server_destroy(hm_server* S);
+
+/* ---------------------------------------------------------------------------
  * hm_solve -- solve V_h t = g (one right-hand side) for the single-layer
  * density t.  Restarted GMRES(m) runs on the product form `inner_form` (for
- * speed), inside iterative refinement whose residual r = g - V_h t is always
- * computed with the FP64 form: the result satisfies
+ * speed), inside iterative refinement whose residual r = g - V_h t is
+ * computed with `residual_form` (FP64 by default): the result satisfies
  *     ||g - V_h t||_2 <= tol ||g||_2
- * for the FP64 H-matrix operator (the paper solves with the assembled
+ * for the H-matrix operator in that form (FP64 by default) (the paper solves with the assembled
  * approximation of the operator as well; the solver choice is this library's).
  *   g, t    device vectors of 3M doubles (dof 3i + a); t is overwritten (or
  *           used as the initial guess if use_initial_guess)
@@ -259,7 +327,8 @@ typedef struct {
     int32_t max_inner;         /* cap on the total number of inner products (0 = 1000) */
     int32_t max_refine;        /* cap on refinement steps (0 = 20) */
     int32_t use_initial_guess; /* nonzero: start from the given t */
-    int32_t pad;
+    int32_t residual_form;     /* form of the refinement residual: HM_FP64 (0, the default) or,
+                                  on a compacted matrix, a packed reduced form */
 } hm_solve_params;
 
 typedef struct {

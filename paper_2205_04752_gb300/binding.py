@@ -16,7 +16,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libhmat.so")
 
-HM_OK, HM_EINVAL, HM_ENOMEM, HM_ENOTCONV, HM_ETIMEOUT, HM_EDEVICE, HM_ERANK = 0, -1, -2, -3, -4, -5, -6
+HM_OK, HM_EINVAL, HM_ENOMEM, HM_ENOTCONV, HM_ETIMEOUT, HM_EDEVICE, HM_ERANK, HM_EBUSY = \
+    0, -1, -2, -3, -4, -5, -6, -7
+HM_REQ_MATVEC, HM_REQ_SOLVE = 0, 1
 FP64, FP32, BF16, FP16 = 0, 1, 2, 3
 FORMS = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "fp16": FP16}
 MAX_LEAF = 336  # HM_MAX_LEAF
@@ -29,7 +31,8 @@ SYMBOLS = (
     "hm_last_error", "hm_profile_enable", "hm_profile_read", "hm_matvec_noalloc", "hm_check",
     "hm_solve", "hm_batch_create", "hm_batch_layout", "hm_batch_matvec", "hm_batch_autotune",
     "hm_batch_set_schedule", "hm_batch_get_schedule", "hm_batch_check", "hm_batch_destroy",
-    "hm_compact", "hm_footprint",
+    "hm_compact", "hm_footprint", "hm_server_create", "hm_server_footprint", "hm_server_run",
+    "hm_server_destroy",
 )
 
 
@@ -57,7 +60,7 @@ class _SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
                 ("inner_form", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("max_inner", ctypes.c_int32), ("max_refine", ctypes.c_int32),
-                ("use_initial_guess", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("use_initial_guess", ctypes.c_int32), ("residual_form", ctypes.c_int32)]
 
 
 class _SolveInfo(ctypes.Structure):
@@ -69,6 +72,26 @@ class _SolveInfo(ctypes.Structure):
 class _Schedule(ctypes.Structure):
     _fields_ = [("leaf_ctas_per_sm", ctypes.c_int32), ("work_order", ctypes.c_int32),
                 ("fork_forward", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class _ServerParams(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("queue_cap", ctypes.c_int32),
+                ("budget_bytes", ctypes.c_int64), ("matvec_form", ctypes.c_int32),
+                ("inner_form", ctypes.c_int32), ("residual_form", ctypes.c_int32),
+                ("restart", ctypes.c_int32), ("inner_tol", ctypes.c_double),
+                ("max_inner", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("arrival_s", ctypes.c_double), ("mesh", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("nrhs", ctypes.c_int32), ("seed", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("x_host", ctypes.c_void_p), ("y_host", ctypes.c_void_p)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("arrival_s", ctypes.c_double), ("start_s", ctypes.c_double),
+                ("done_s", ctypes.c_double), ("rel_residual", ctypes.c_double)]
 
 
 class _Stats(ctypes.Structure):
@@ -128,6 +151,10 @@ def load():
         "hm_batch_destroy": (None, [P]),
         "hm_compact": (ctypes.c_int, [P]),
         "hm_footprint": (ctypes.c_int, [P, ctypes.POINTER(I64)]),
+        "hm_server_create": (ctypes.c_int, [P, I32, ctypes.POINTER(_ServerParams), ctypes.POINTER(P)]),
+        "hm_server_footprint": (ctypes.c_int, [P, ctypes.POINTER(_Request), ctypes.POINTER(I64)]),
+        "hm_server_run": (ctypes.c_int, [P, P, I32, I32, P]),
+        "hm_server_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -348,7 +375,7 @@ def hmatvec(H: HMatrix, x, y, form="fp64", stream=None):
 
 def solve(H: HMatrix, g, t, tol: float = 1e-8, inner_form="fp16", inner_tol: float = 0.0,
           restart: int = 50, max_inner: int = 0, max_refine: int = 0, initial_guess=False,
-          stream=None, raise_on_fail: bool = True):
+          stream=None, raise_on_fail: bool = True, residual_form="fp64"):
     """``hm_solve``: V_h t = g with GMRES on ``inner_form`` and FP64-residual
     iterative refinement.  g, t: CUDA float64 tensors of 3M.  Returns a dict
     with iterations, restarts, refinements and the relative FP64 residual."""
@@ -358,8 +385,9 @@ def solve(H: HMatrix, g, t, tol: float = 1e-8, inner_form="fp16", inner_tol: flo
     if g.numel() != 3 * H.M or t.numel() != 3 * H.M or not g.is_contiguous() or not t.is_contiguous():
         raise ValueError("solve: g and t must be contiguous vectors of 3M")
     f = FORMS[inner_form] if isinstance(inner_form, str) else int(inner_form)
+    fr = FORMS[residual_form] if isinstance(residual_form, str) else int(residual_form)
     p = _SolveParams(float(tol), float(inner_tol), f, int(restart), int(max_inner), int(max_refine),
-                     1 if initial_guess else 0, 0)
+                     1 if initial_guess else 0, fr)
     info = _SolveInfo()
     rc = load().hm_solve(H._h, ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(t.data_ptr()),
                          ctypes.byref(p), ctypes.byref(info), _stream_handle(stream))
@@ -475,3 +503,56 @@ class Batch:
 
     def check(self):
         _check(load().hm_batch_check(self._h))
+
+
+class Server:
+    """``hm_server``: a request loop over resident matrices (each with the
+    forms it serves packed).  ``run`` replays a list of requests (dicts with
+    arrival_s, mesh, kind 'matvec' / 'solve', nrhs, seed, tol and optional
+    host arrays x / y) and returns one result dict per request."""
+
+    def __init__(self, mats, slots=8, queue_cap=1024, budget_bytes=8 << 30, matvec_form="fp16",
+                 inner_form="fp16", residual_form="fp32", restart=30, inner_tol=1e-3, max_inner=0):
+        lib = load()
+        self.mats = list(mats)
+        f = lambda v: FORMS[v] if isinstance(v, str) else int(v)
+        p = _ServerParams(int(slots), int(queue_cap), int(budget_bytes), f(matvec_form), f(inner_form),
+                          f(residual_form), int(restart), float(inner_tol), int(max_inner), 0)
+        arr = (ctypes.c_void_p * len(self.mats))(*[m._h.value for m in self.mats])
+        h = ctypes.c_void_p()
+        _check(lib.hm_server_create(arr, len(self.mats), ctypes.byref(p), ctypes.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.hm_server_destroy(h)
+            self._h = None
+
+    @staticmethod
+    def _request(r):
+        x = r.get("x")
+        y = r.get("y")
+        for a in (x, y):
+            if a is not None and (a.dtype != np.float64 or not a.flags.c_contiguous):
+                raise TypeError("Server: x / y must be C-contiguous float64 arrays")
+        kind = r.get("kind", "matvec")
+        kind = HM_REQ_SOLVE if kind in ("solve", HM_REQ_SOLVE) else HM_REQ_MATVEC
+        return _Request(float(r.get("arrival_s", 0.0)), int(r["mesh"]), kind, int(r.get("nrhs", 1)),
+                        int(r.get("seed", 0)), float(r.get("tol", 0.0)),
+                        x.ctypes.data if x is not None else None, y.ctypes.data if y is not None else None)
+
+    def footprint(self, r) -> int:
+        b = ctypes.c_int64(0)
+        q = self._request(r)
+        _check(load().hm_server_footprint(self._h, ctypes.byref(q), ctypes.byref(b)))
+        return int(b.value)
+
+    def run(self, requests, realtime=True):
+        n = len(requests)
+        reqs = (_Request * max(n, 1))(*[self._request(r) for r in requests])
+        res = (_Result * max(n, 1))()
+        _check(load().hm_server_run(self._h, reqs, n, 1 if realtime else 0, res))
+        return [dict(status=r.status, iterations=r.iterations, arrival_s=r.arrival_s,
+                     start_s=r.start_s, done_s=r.done_s, rel_residual=r.rel_residual)
+                for r in res[:n]]

@@ -42,11 +42,6 @@ struct hm_batch {
     hm_schedule gsched{};
 };
 
-namespace hm {
-// in hm_matvec.cu
-int product_prepare(int32_t form, int* ctas_per_sm);
-}
-
 namespace {
 
 using namespace hm;

@@ -224,6 +224,8 @@ int matvec_device_scratch(const hm_matrix& H, const double* x, double* y, int32_
 // bytes of Scratch a product of nrhs vectors in `form` needs (xg, w and the
 // counters, each part 256-byte aligned)
 size_t matvec_scratch_bytes(const hm_matrix& H, int32_t nrhs, int32_t form);
+// a Scratch laid out in the matvec_scratch_bytes(H, nrhs, form) bytes at base
+Scratch make_scratch(const hm_matrix& H, int32_t nrhs, int32_t form, void* base);
 // Launch schedule of a product.  None of these change the arithmetic: every
 // output element is summed in the same order under every schedule.
 struct Sched {
@@ -246,4 +248,11 @@ int assemble_device(const hm_tree& tr, hm_matrix& H);
 int matvec_device(const hm_matrix& H, const double* x, double* y, int32_t nrhs, int64_t ld,
                   int32_t form, cudaStream_t s);
 int pack_device(hm_matrix& H, int32_t form, cudaStream_t s);
+// fill the launch caches of a form's kernels (call before capture or threads)
+int product_prepare(int32_t form, int* ctas_per_sm);
+// the solver on caller-provided memory (hm_solve.cu)
+size_t solve_workspace_bytes(int64_t n, int32_t restart);
+int solve_check_params(const hm_matrix* H, hm_solve_params& p);
+int solve_device(const hm_matrix& H, const double* g, double* t, const hm_solve_params& p, hm_solve_info* info,
+                 cudaStream_t s, void* ws, void* scratch);
 }  // namespace hm

@@ -869,6 +869,17 @@ int matvec_device(const hm_matrix& H, const double* x, double* y, int32_t nrhs, 
     return matvec_device_scratch(H, x, y, nrhs, ld, form, s, scr);
 }
 
+Scratch make_scratch(const hm_matrix& H, int32_t nrhs, int32_t form, void* base)
+{
+    // the layout matvec_scratch_bytes counts: xg, w, counters
+    const size_t ta = form == HM_FP64 ? 8 : 4;
+    auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    const size_t vec = up((size_t)nrhs * 4 * (size_t)H.M * ta);
+    const size_t wb = up((size_t)nrhs * (size_t)std::max<int64_t>(H.w_total, 1) * ta);
+    unsigned char* b = static_cast<unsigned char*>(base);
+    return Scratch{b, b + vec, reinterpret_cast<int*>(b + vec + wb), false};
+}
+
 size_t matvec_scratch_bytes(const hm_matrix& H, int32_t nrhs, int32_t form)
 {
     const size_t ta = form == HM_FP64 ? 8 : 4;

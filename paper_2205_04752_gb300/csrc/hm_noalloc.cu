@@ -81,12 +81,6 @@ extern "C" int hm_matvec_noalloc(const hm_matrix* H, const double* x, double* y,
     void* base = nullptr;
     int rc = scratch_address(&base);
     if (rc) return rc;
-    // the layout matvec_scratch_bytes counts: xg, w, counters
-    const size_t ta = form == HM_FP64 ? 8 : 4;
-    auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
-    const size_t vec = up((size_t)nrhs * 4 * (size_t)H->M * ta);
-    const size_t wb = up((size_t)nrhs * (size_t)std::max<int64_t>(H->w_total, 1) * ta);
-    unsigned char* b = static_cast<unsigned char*>(base);
-    Scratch scr{b, b + vec, reinterpret_cast<int*>(b + vec + wb), false};
+    const Scratch scr = make_scratch(*H, nrhs, form, base);
     return matvec_device_scratch(*H, x, y, nrhs, ld, form, (cudaStream_t)stream, scr);
 }

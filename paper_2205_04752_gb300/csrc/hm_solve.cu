@@ -125,44 +125,44 @@ struct Solver {
 }  // namespace
 }  // namespace hm
 
-using namespace hm;
+namespace hm {
 
-extern "C" int hm_solve(const hm_matrix* H, const double* g, double* t, const hm_solve_params* sp,
-                        hm_solve_info* info, void* stream)
+size_t solve_workspace_bytes(int64_t n, int32_t restart)
 {
-    if (!H || !g || !t || !sp) return fail(HM_EINVAL, "hm_solve: NULL argument");
-    hm_solve_params p = *sp;
+    return ((size_t)(restart + 1) * n + 3 * (size_t)n + (size_t)kRedBlocks * kMaxBasis + 2 * kMaxBasis) * 8;
+}
+
+int solve_check_params(const hm_matrix* H, hm_solve_params& p)
+{
     if (p.restart <= 0) p.restart = 50;
     if (p.restart > kMaxBasis - 1) return fail(HM_EINVAL, "hm_solve: restart above %d", kMaxBasis - 1);
     if (!(p.tol > 0.0)) return fail(HM_EINVAL, "hm_solve: tol must be > 0");
     if (p.inner_tol <= 0.0) p.inner_tol = 1e-3;
     if (p.max_inner <= 0) p.max_inner = 1000;
     if (p.max_refine <= 0) p.max_refine = 20;
-    if (!H->packed[HM_FP64])
-        return fail(HM_EINVAL, "hm_solve: the FP64 form (residuals) was released by hm_compact");
+    if (p.residual_form < HM_FP64 || p.residual_form > HM_FP16 || !H->packed[p.residual_form])
+        return fail(HM_EINVAL, "hm_solve: residual form %d not available (FP64 released by hm_compact, or not packed)",
+                    p.residual_form);
     if (p.inner_form < HM_FP64 || p.inner_form > HM_FP16 || !H->packed[p.inner_form])
         return fail(HM_EINVAL, "hm_solve: inner form %d not available (hm_pack first)", p.inner_form);
+    return HM_OK;
+}
+
+// The solve on caller-provided memory: `ws` of solve_workspace_bytes(3M,
+// restart) bytes; products use `scratch` (matvec_scratch_bytes(H, 1, form)
+// bytes for the larger of the two forms) or, if null, the matrix's own
+// workspace.  `p` must have passed solve_check_params.
+int solve_device(const hm_matrix& Hm, const double* g, double* t, const hm_solve_params& p, hm_solve_info* info,
+                 cudaStream_t s, void* ws, void* scratch)
+{
+    const hm_matrix* H = &Hm;
     if (info) std::memset(info, 0, sizeof *info);
-    cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = 3 * H->M;
     const int m = p.restart;
-    // workspace, through the matrix's allocator
-    Allocator al = H->alloc;
-    al.stream = s;
-    const size_t bytes = ((size_t)(m + 1) * n + 3 * (size_t)n + (size_t)kRedBlocks * kMaxBasis + 2 * kMaxBasis) * 8;
-    void* ws = al.alloc(bytes);
-    if (!ws) return fail(HM_ENOMEM, "hm_solve: workspace of %zu bytes", bytes);
-    struct Release {
-        Allocator& a;
-        void* p;
-        size_t b;
-        cudaStream_t s;
-        ~Release()
-        {
-            cudaStreamSynchronize(s);
-            a.release(p, b);
-        }
-    } rel{al, ws, bytes, s};
+    auto mv = [&](const double* x, double* y, int32_t form) -> int {
+        if (!scratch) return matvec_device(*H, x, y, 1, n, form, s);
+        return matvec_device_scratch(*H, x, y, 1, n, form, s, make_scratch(*H, 1, form, scratch));
+    };
     double* base = static_cast<double*>(ws);
     Solver S{*H, s, n, base, base + (size_t)(m + 1) * n, base + (size_t)(m + 2) * n,
              base + (size_t)(m + 3) * n, base + (size_t)(m + 4) * n,
@@ -180,8 +180,8 @@ extern "C" int hm_solve(const hm_matrix* H, const double* g, double* t, const hm
     }
     if (!p.use_initial_guess) HM_CUDA(cudaMemsetAsync(t, 0, (size_t)n * 8, s));
     auto residual = [&]() -> int {
-        // r = g - V_h t with the FP64 form
-        int e = matvec_device(*H, t, S.r, 1, n, HM_FP64, s);
+        // r = g - V_h t with the residual form (FP64 unless asked otherwise)
+        int e = mv(t, S.r, p.residual_form);
         if (e) return e;
         return S.axpby(1.0, g, -1.0, S.r);
     };
@@ -203,7 +203,7 @@ extern "C" int hm_solve(const hm_matrix* H, const double* g, double* t, const hm
             if (first_cycle) {
                 if ((rc = S.axpby(1.0 / beta, rhs, 0.0, S.basis))) return rc;
             } else {
-                if ((rc = matvec_device(*H, S.d, S.w, 1, n, p.inner_form, s))) return rc;
+                if ((rc = mv(S.d, S.w, p.inner_form))) return rc;
                 if ((rc = S.axpby(1.0, rhs, -1.0, S.w))) return rc;
                 if ((rc = S.norm(S.w, &beta))) return rc;
                 if (beta <= target) break;
@@ -217,7 +217,7 @@ extern "C" int hm_solve(const hm_matrix* H, const double* g, double* t, const hm
             for (; k < m && total_inner < p.max_inner; ++k) {
                 double* vk = S.basis + (size_t)k * n;
                 double* vk1 = S.basis + (size_t)(k + 1) * n;
-                if ((rc = matvec_device(*H, vk, vk1, 1, n, p.inner_form, s))) return rc;
+                if ((rc = mv(vk, vk1, p.inner_form))) return rc;
                 ++total_inner;
                 // classical Gram-Schmidt, two passes
                 std::vector<double> h(k + 2, 0.0);
@@ -280,7 +280,31 @@ extern "C" int hm_solve(const hm_matrix* H, const double* g, double* t, const hm
         info->rel_residual = rnorm / gnorm;
     }
     if (rnorm > p.tol * gnorm)
-        return fail(HM_ENOTCONV, "hm_solve: relative FP64 residual %.3e above tol %.3e after %d inner iterations",
+        return fail(HM_ENOTCONV, "hm_solve: relative residual %.3e above tol %.3e after %d inner iterations",
                     rnorm / gnorm, p.tol, total_inner);
     return HM_OK;
+}
+
+}  // namespace hm
+
+using namespace hm;
+
+extern "C" int hm_solve(const hm_matrix* H, const double* g, double* t, const hm_solve_params* sp,
+                        hm_solve_info* info, void* stream)
+{
+    if (!H || !g || !t || !sp) return fail(HM_EINVAL, "hm_solve: NULL argument");
+    hm_solve_params p = *sp;
+    int rc = solve_check_params(H, p);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    // workspace, through the matrix's allocator
+    Allocator al = H->alloc;
+    al.stream = s;
+    const size_t bytes = solve_workspace_bytes(3 * H->M, p.restart);
+    void* ws = al.alloc(bytes);
+    if (!ws) return fail(HM_ENOMEM, "hm_solve: workspace of %zu bytes", bytes);
+    rc = solve_device(*H, g, t, p, info, s, ws, nullptr);
+    cudaStreamSynchronize(s);
+    al.release(ws, bytes);
+    return rc;
 }
