@@ -10,6 +10,12 @@ L2, so every step streams it from HBM; no L2 flush is needed.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--form fp16|fp32|...]
   python bench.py --impl reference     # the FP64 CPU oracle on the host cores
 
+Besides the headline the JSON line carries, as context: the FP64 form, 32
+right-hand sides, end-to-end products with host buffers, "batch64" (batched
+products over 64 ellipsoid meshes with 1 and 16 right-hand sides) and
+"serving" (the request loop over 16 resident meshes at swept Poisson rates,
+p50 / p99 latency); --no-batch / --no-serve skip the last two.
+
 Under torchrun (N > 1) every rank runs its own replica (the product shards
 into independent problems; no collective on the data path): weak scaling,
 value = all ranks' products / the slowest rank's time.
@@ -343,7 +349,7 @@ def run_ours(args):
             "config": dict(w, form=form, l2="inputs larger than L2 (H-matrix "
                            f"{total_alg/1e9:.2f} GB per product)", parallelism=f"replicas{ws}"),
             "roofline": roofline, "clocks": clocks, "e2e": e2e,
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": 4 * args.steps,
             "rel_err_vs_fp64_form": err_mixed,
             "fp64_form": {"ms_per_matvec": round(ms64, 4), "value": round(1e3 / ms64, 3)},
             "nrhs32": {"ms_per_call": round(ms32, 4), "vectors_per_s": round(32e3 / ms32, 2)},
@@ -353,17 +359,140 @@ def run_ours(args):
                          "rank_mean": [round(r / max(st.nadm, 1), 2) for r in st.rank_sum],
                          "bytes_per_form": st.bytes_form}}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        from paper_2205_04752_gb300 import inputs as _in
         line["cpu_baseline"] = {k: v for k, v in cpu_baseline(V, T).items()
                                 if k in ("value", "unit", "cores", "kind", "sample")}
     elif rank == 0:
         line["cpu_baseline"] = None
+    # ---- batched and served workloads (their own matrices; free this one first)
+    del H, X, Y
+    torch.cuda.empty_cache()
+    for key, skip, fn in (("batch64", args.no_batch, bench_batch), ("serving", args.no_serve, bench_serving)):
+        if skip or rank != 0 or ws != 1:
+            continue
+        try:
+            line[key] = fn(args)
+        except Exception as e:  # reported, the headline still prints
+            line[key] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def bench_batch(args):
+    """Batched products over 64 ellipsoid meshes (2k-40k triangles each, leaf
+    32, nu uniform[0.2, 0.45]): one launch per phase over all members, the
+    schedule chosen by the autotuner, replayed as a CUDA graph; FP16 form."""
+    import torch
+    from paper_2205_04752_gb300 import binding, inputs
+    specs = inputs.ellipsoid_batch_specs(64, 3, 2000.0, 40000.0)
+    mats, t0, resident, tri = [], time.perf_counter(), 0, 0
+    for sp in specs:
+        V, T = inputs.ellipsoid(sp["n"], sp["a"], sp["b"], sp["c"])
+        tr = binding.build_cluster_tree(V, T, 32, 0.8)
+        H = binding.aca_assemble(tr, sp["E"], sp["nu"], 1e-4, max_rhs=1, defer_fp64=True)
+        H.pack("fp16")
+        H.compact()
+        resident += H.footprint()
+        tri += len(T)
+        mats.append(H)
+    torch.cuda.synchronize()
+    t_asm = time.perf_counter() - t0
+    R = 16
+    B = binding.Batch(mats, "fp16", max_rhs=R)
+    out = {"workload": "64 ellipsoids, 2k-40k triangles (log-uniform), leaf 32, eta 0.8, eps 1e-4",
+           "meshes": len(mats), "triangles": tri, "dofs": B.ndof, "admissible_blocks": B.nblocks,
+           "leaves": B.nleaves, "assemble_s": round(t_asm, 2), "resident_gb": round(resident / 1e9, 2)}
+    bytes_prod = sum(m.stats().bytes_form[3] for m in mats)
+    stream = torch.cuda.current_stream()
+    for nrhs in (1, R):
+        sched, _ = B.autotune(nrhs=nrhs, reps=3)
+        x = torch.tensor(inputs.uniform_rhs(B.ndof, 1000, nrhs=nrhs), device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(3):
+            B.matvec(x, y, graph=True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        n = 10
+        e0.record(stream)
+        for _ in range(n):
+            B.matvec(x, y, graph=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        out[f"nrhs{nrhs}"] = {"ms_per_batch_product": round(ms, 3),
+                              "mesh_vector_products_per_s": round(len(mats) * nrhs * 1e3 / ms, 1),
+                              "factor_gb_per_s": round(bytes_prod / (ms * 1e-3) / 1e9, 1),
+                              "schedule": sched}
+    B.check()
+    out["bytes_per_product_gb"] = round(bytes_prod / 1e9, 2)
+    del B, mats
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_serving(args):
+    """Request loop over a pool of 16 resident meshes (icospheres of levels
+    3-6 and 12 ellipsoids of 1k-200k triangles): Poisson arrivals at swept
+    rates, 80% matvec (1-32 vectors, FP16 form) / 20% solve (tol 1e-6, GMRES
+    on FP16 with FP32-residual refinement), mesh uniform over the pool."""
+    import torch
+    from paper_2205_04752_gb300 import binding, inputs
+    meshes = [(inputs.icosphere(l), 64, 0.3) for l in (3, 4, 5, 6)]
+    for sp in inputs.ellipsoid_batch_specs(12, 5, 1000.0, 200000.0):
+        meshes.append((inputs.ellipsoid(sp["n"], sp["a"], sp["b"], sp["c"]), 64, sp["nu"]))
+    mats, t0, resident, tri = [], time.perf_counter(), 0, []
+    for (V, T), leaf, nu in meshes:
+        tr = binding.build_cluster_tree(V, T, leaf, 0.8)
+        H = binding.aca_assemble(tr, 1.0, nu, 1e-4, max_rhs=1, defer_fp64=True)
+        H.pack("fp16")
+        H.pack("fp32")
+        H.compact()
+        resident += H.footprint()
+        tri.append(len(T))
+        mats.append(H)
+    torch.cuda.synchronize()
+    t_asm = time.perf_counter() - t0
+    srv = binding.Server(mats, slots=8, queue_cap=256, budget_bytes=24 << 30, matvec_form="fp16",
+                         inner_form="fp16", residual_form="fp32", restart=30)
+    out = {"workload": "16 resident meshes (icosphere L3-L6, 12 ellipsoids 1k-200k triangles), "
+                       "Poisson arrivals, 80% matvec (1-32 RHS, fp16) / 20% solve (tol 1e-6)",
+           "triangles": tri, "assemble_s": round(t_asm, 2), "resident_gb": round(resident / 1e9, 2),
+           "slots": 8, "budget_gb": 24, "rates": []}
+    # warm the kernels of every form once
+    srv.run([dict(mesh=m, kind="matvec", nrhs=1, seed=m) for m in range(len(mats))], realtime=False)
+    rng = np.random.default_rng(5)
+    for rate in args.serve_rates:
+        n = max(20, int(rate * args.serve_seconds))
+        t = np.cumsum(rng.exponential(1.0 / rate, n))
+        reqs = []
+        for i in range(n):
+            solve = rng.random() < 0.2
+            reqs.append(dict(arrival_s=float(t[i]), mesh=int(rng.integers(len(mats))),
+                             kind="solve" if solve else "matvec",
+                             nrhs=1 if solve else int(rng.integers(1, 33)), seed=i, tol=1e-6))
+        w0 = time.perf_counter()
+        res = srv.run(reqs, realtime=True)
+        wall = time.perf_counter() - w0
+        ok = [r for r in res if r["status"] in (binding.HM_OK, binding.HM_ENOTCONV)]
+        lat = np.array([r["done_s"] - r["arrival_s"] for r in ok]) * 1e3
+        vec = sum(q["nrhs"] for q, r in zip(reqs, res) if r["status"] == binding.HM_OK and q["kind"] == "matvec")
+        sres = [r["rel_residual"] for q, r in zip(reqs, res) if q["kind"] == "solve" and r["status"] == binding.HM_OK]
+        out["rates"].append({
+            "rate_rps": rate, "requests": n, "completed": len(ok),
+            "rejected": sum(r["status"] == binding.HM_EBUSY for r in res),
+            "not_converged": sum(r["status"] == binding.HM_ENOTCONV for r in res),
+            "p50_ms": round(float(np.percentile(lat, 50)), 2) if len(lat) else None,
+            "p99_ms": round(float(np.percentile(lat, 99)), 2) if len(lat) else None,
+            "throughput_rps": round(len(ok) / wall, 1),
+            "matvec_vectors_per_s": round(vec / wall, 1),
+            "solve_max_rel_residual": float(max(sres)) if sres else None})
+    del srv, mats
+    torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -374,6 +503,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="fp16", choices=["fp64", "fp32", "bf16", "fp16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-mesh batched products")
+    ap.add_argument("--no-serve", action="store_true", help="skip the request-loop measurement")
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[10.0, 30.0, 100.0])
+    ap.add_argument("--serve-seconds", type=float, default=4.0)
     ap.add_argument("--minimal", action="store_true",
                     help="profiling runs: assemble, pack and time the headline product only "
                          "(no e2e, context forms, clock sampling or CPU baseline)")

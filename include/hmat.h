@@ -106,7 +106,14 @@ typedef struct {
     double aca_eta_stop; /* beta of Algorithm 1's stop factor eps(1-beta)/(1+eps); 0 = plain eps */
     int32_t kmax;        /* rank cap per block and kernel, 1..256 (0 = 128) */
     int32_t max_rhs;     /* largest nrhs a later hm_matvec may use, 1..64 (0 = 32) */
+    int32_t flags;       /* HM_DEFER_FP64: do not build the FP64 product form at assembly */
+    int32_t pad;
 } hm_params;
+
+/* hm_params.flags: build the FP64 product form only on hm_pack(H, HM_FP64)
+ * (saves its memory while a matrix is assembled only to be packed into a
+ * reduced form and compacted) */
+#define HM_DEFER_FP64 1
 
 /* ---------------------------------------------------------------------------
  * hm_aca_assemble -- assemble the H-matrix of V_h on the device.
@@ -124,6 +131,7 @@ typedef struct {
  *   alloc  optional device allocator (NULL: cudaMallocAsync)
  *   stream stream for all device work; the call synchronises it before return
  *   out    receives the matrix
+ * The FP64 product form is built too unless prm->flags has HM_DEFER_FP64.
  * Returns HM_ERANK (matrix still valid) if a block hit the rank cap.
  * ------------------------------------------------------------------------- */
 int hm_aca_assemble(const hm_tree* tree, const hm_params* prm, const hm_allocator* alloc,
@@ -132,8 +140,8 @@ int hm_aca_assemble(const hm_tree* tree, const hm_params* prm, const hm_allocato
 /* Change E, nu of an assembled matrix (the factors are material-free). */
 int hm_set_material(hm_matrix* H, double E, double nu);
 
-/* Build the packed copy used by the HM_FP32 / HM_BF16 / HM_FP16 product forms
- * (HM_FP64 needs none).  Idempotent; synchronises `stream`. */
+/* Build the streaming copy used by a product form (HM_FP64 is built at
+ * assembly unless deferred).  Idempotent; synchronises `stream`. */
 int hm_pack(hm_matrix* H, int32_t form, void* stream);
 
 /* ---------------------------------------------------------------------------

@@ -45,7 +45,7 @@ class HMError(RuntimeError):
 class _Params(ctypes.Structure):
     _fields_ = [("E", ctypes.c_double), ("nu", ctypes.c_double), ("aca_eps", ctypes.c_double),
                 ("aca_eta_stop", ctypes.c_double), ("kmax", ctypes.c_int32),
-                ("max_rhs", ctypes.c_int32)]
+                ("max_rhs", ctypes.c_int32), ("flags", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 _ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -261,13 +261,13 @@ class HMatrix:
 
     def __init__(self, tree: ClusterTree, E: float, nu: float, aca_eps: float,
                  aca_eta_stop: float = 0.8, kmax: int = 128, max_rhs: int = 32, stream=None,
-                 torch_memory: bool = True):
+                 torch_memory: bool = True, defer_fp64: bool = False):
         import torch
         lib = load()
         self.M = tree.M
         self.device = torch.cuda.current_device()
         prm = _Params(float(E), float(nu), float(aca_eps), float(aca_eta_stop), int(kmax),
-                      int(max_rhs))
+                      int(max_rhs), 1 if defer_fp64 else 0, 0)
         self._alloc_keep = None
         ap = None
         if torch_memory:

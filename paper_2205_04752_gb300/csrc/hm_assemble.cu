@@ -340,6 +340,10 @@ struct AcaTask {
     int32_t blk, kern;
 };
 
+// device bytes of per-CTA ACA scratch per launch (the grid of a launch over
+// very large blocks is reduced to stay within it)
+constexpr size_t kAcaScratchBytes = size_t(4) << 30;
+
 struct AcaParams {
     double fac;        // eps (1 - eta_stop) / (1 + eps)
     int32_t kmax;
@@ -646,6 +650,7 @@ __global__ void __launch_bounds__(kAcaThreads) aca_kernel(
 __global__ void repack_kernel(const AcaTask* __restrict__ tasks, int ntask,
                               const Blk* __restrict__ blks, const int32_t* __restrict__ rank,
                               const int64_t* __restrict__ off, const double* __restrict__ arena,
+                              int64_t cap, const double* __restrict__ arena2,
                               const int64_t* __restrict__ uoff, const int64_t* __restrict__ voff,
                               double* __restrict__ U, double* __restrict__ V)
 {
@@ -655,7 +660,8 @@ __global__ void repack_kernel(const AcaTask* __restrict__ tasks, int ntask,
     int k = rank[task];
     if (k == 0) return;
     Blk b = blks[tk.blk];
-    const double* src = arena + off[task];
+    const int64_t o = off[task];
+    const double* src = o < cap ? arena + o : arena2 + (o - cap);
     size_t q = (size_t)tk.blk * 7 + tk.kern;
     double* du = U + uoff[q];
     double* dv = V + voff[q];
@@ -819,53 +825,102 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
     });
     std::vector<int32_t> trank((size_t)ntask, 0), tflags((size_t)ntask, 0);
     std::vector<int64_t> toff((size_t)ntask, 0);
-    TmpBuf darena(H), dscr(H), dz(H), dtask(H), dcnt(H), dtop(H), drank(H), doff(H), dflag(H);
+    TmpBuf darena(H), darena2(H), dscr(H), dz(H), dtask(H), dcnt(H), dtop(H), drank(H), doff(H), dflag(H);
+    unsigned long long cap = 0;  // elements of darena; offsets >= cap lie in darena2
     if (ntask > 0) {
-        int mmax = 0, nmax = 0, kc = 0;
         double est = 0.0;
-        for (const Blk& b : H.adm_h) {
-            mmax = std::max(mmax, b.m);
-            nmax = std::max(nmax, b.n);
-            kc = std::max(kc, std::min(b.m, b.n));
-            est += 7.0 * (b.m + b.n) * std::min(24, std::min(b.m, b.n));
+        // first guess of the factor arena: rank 12 per block and kernel (the
+        // measured means are 6-9 at eps 1e-4), at most 60% of the free
+        // device memory; tasks that do not fit are re-run into an arena of
+        // the exact size below
+        for (const Blk& b : H.adm_h) est += 7.0 * (b.m + b.n) * std::min(12, std::min(b.m, b.n));
+        {
+            size_t fr = 0, tot = 0;
+            if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) est = std::min(est, 0.6 * (double)fr / 8.0 / 1.1);
+            else cudaGetLastError();
         }
-        AcaParams prm;
-        double eps = H.prm.aca_eps;
-        prm.fac = eps * (1.0 - H.prm.aca_eta_stop) / (1.0 + eps);
-        prm.kmax = H.prm.kmax;
-        prm.kcap_all = std::max(1, std::min(kc, H.prm.kmax));
-        prm.mmax = mmax;
-        prm.nmax = nmax;
+        const double eps = H.prm.aca_eps;
+        const double fac = eps * (1.0 - H.prm.aca_eta_stop) / (1.0 + eps);
         int dev = 0, nsm = 0, occ = 0;
         HM_CUDA(cudaGetDevice(&dev));
         HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, aca_kernel, kAcaThreads, 0));
-        int64_t grid = std::min<int64_t>(ntask, (int64_t)nsm * std::max(1, std::min(occ, 4)));
-        size_t per_cta = (size_t)prm.kcap_all * (mmax + nmax);
-        if ((rc = dalloc(H, dscr.b, (size_t)grid * per_cta * 8))) return rc;
-        if ((rc = dalloc(H, dz.b, (size_t)grid * mmax))) return rc;
+        const int64_t full_grid = (int64_t)nsm * std::max(1, std::min(occ, 4));
+        // Launch classes over the tasks (sorted by decreasing |t| + |s|): a
+        // class ends where blocks are half the size of its first one.  Each
+        // CTA's scratch holds the largest block of its class, and a class's
+        // grid is bounded so that all its scratch fits kAcaScratchBytes.
+        struct AcaClass {
+            int64_t i0, i1, grid;
+            AcaParams prm;
+        };
+        std::vector<AcaClass> classes;
+        size_t scr_bytes = 0, z_bytes = 0;
+        auto make_class = [&](const std::vector<AcaTask>& tl, int64_t i0, int64_t i1) {
+            AcaClass c;
+            c.i0 = i0;
+            c.i1 = i1;
+            int mmax = 1, nmax = 1, kc = 1;
+            for (int64_t q = i0; q < i1; ++q) {
+                const Blk& b = H.adm_h[(size_t)tl[(size_t)q].blk];
+                mmax = std::max(mmax, b.m);
+                nmax = std::max(nmax, b.n);
+                kc = std::max(kc, std::min(b.m, b.n));
+            }
+            c.prm.fac = fac;
+            c.prm.kmax = H.prm.kmax;
+            c.prm.kcap_all = std::max(1, std::min(kc, H.prm.kmax));
+            c.prm.mmax = mmax;
+            c.prm.nmax = nmax;
+            const size_t per_cta = (size_t)c.prm.kcap_all * (size_t)(mmax + nmax) * 8;
+            c.grid = std::max<int64_t>(1, std::min<int64_t>({full_grid, i1 - i0, (int64_t)(kAcaScratchBytes / per_cta)}));
+            scr_bytes = std::max(scr_bytes, (size_t)c.grid * per_cta);
+            z_bytes = std::max(z_bytes, (size_t)c.grid * (size_t)mmax);
+            return c;
+        };
+        auto split = [&](const std::vector<AcaTask>& tl, std::vector<AcaClass>& out) {
+            int64_t i0 = 0;
+            const int64_t nt = (int64_t)tl.size();
+            while (i0 < nt) {
+                const Blk& b0 = H.adm_h[(size_t)tl[(size_t)i0].blk];
+                const int64_t half = ((int64_t)b0.m + b0.n) / 2;
+                int64_t i1 = i0 + 1;
+                while (i1 < nt) {
+                    const Blk& b = H.adm_h[(size_t)tl[(size_t)i1].blk];
+                    if ((int64_t)b.m + b.n <= half) break;
+                    ++i1;
+                }
+                out.push_back(make_class(tl, i0, i1));
+                i0 = i1;
+            }
+        };
+        split(tasks, classes);
+        if ((rc = dalloc(H, dscr.b, scr_bytes))) return rc;
+        if ((rc = dalloc(H, dz.b, z_bytes))) return rc;
         if ((rc = upload(H, dtask.b, tasks.data(), tasks.size() * sizeof(AcaTask)))) return rc;
         if ((rc = dalloc(H, dcnt.b, 64))) return rc;
         if ((rc = dalloc(H, dtop.b, 64))) return rc;
         if ((rc = dalloc(H, drank.b, (size_t)ntask * 4))) return rc;
         if ((rc = dalloc(H, doff.b, (size_t)ntask * 8))) return rc;
         if ((rc = dalloc(H, dflag.b, (size_t)ntask * 4))) return rc;
-        unsigned long long cap = (unsigned long long)(est * 1.25) + (1ull << 20);
+        cap = (unsigned long long)(est * 1.1) + (1ull << 20);
         if ((rc = dalloc(H, darena.b, (size_t)cap * 8))) return rc;
-        HM_CUDA(cudaMemsetAsync(dcnt.b.p, 0, 64, s));
         HM_CUDA(cudaMemsetAsync(dtop.b.p, 0, 64, s));
-        aca_kernel<<<(unsigned)grid, kAcaThreads, 0, s>>>(
-            g, dtask.b.as<AcaTask>(), (int)ntask, H.d_adm.as<Blk>(), prm, dscr.b.as<double>(),
-            dz.b.as<unsigned char>(), dcnt.b.as<int>(), darena.b.as<double>(),
-            dtop.b.as<unsigned long long>(), cap, drank.b.as<int32_t>(), doff.b.as<int64_t>(),
-            dflag.b.as<int32_t>());
-        HM_CUDA(cudaGetLastError());
+        for (const AcaClass& c : classes) {
+            HM_CUDA(cudaMemsetAsync(dcnt.b.p, 0, 64, s));
+            aca_kernel<<<(unsigned)c.grid, kAcaThreads, 0, s>>>(
+                g, dtask.b.as<AcaTask>() + c.i0, (int)(c.i1 - c.i0), H.d_adm.as<Blk>(), c.prm,
+                dscr.b.as<double>(), dz.b.as<unsigned char>(), dcnt.b.as<int>(), darena.b.as<double>(),
+                dtop.b.as<unsigned long long>(), cap, drank.b.as<int32_t>() + c.i0, doff.b.as<int64_t>() + c.i0,
+                dflag.b.as<int32_t>() + c.i0);
+            HM_CUDA(cudaGetLastError());
+        }
         HM_CUDA(cudaMemcpyAsync(trank.data(), drank.b.p, (size_t)ntask * 4, cudaMemcpyDeviceToHost, s));
         HM_CUDA(cudaMemcpyAsync(toff.data(), doff.b.p, (size_t)ntask * 8, cudaMemcpyDeviceToHost, s));
         HM_CUDA(cudaMemcpyAsync(tflags.data(), dflag.b.p, (size_t)ntask * 4, cudaMemcpyDeviceToHost, s));
         HM_CUDA(cudaStreamSynchronize(s));
-        // tasks whose factors did not fit: run them again into an arena of the
-        // exact size (ACA is deterministic, so the result is the same)
+        // tasks whose factors did not fit: run them again into a second arena
+        // of the exact size (ACA is deterministic, so the result is the same)
         std::vector<AcaTask> redo;
         std::vector<int64_t> redo_idx;
         unsigned long long need = 0;
@@ -877,37 +932,36 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
                 need += (unsigned long long)trank[(size_t)q] * (b.m + b.n);
             }
         if (!redo.empty()) {
-            TmpBuf a2(H), t2(H), r2(H), o2(H), f2(H);
-            if ((rc = dalloc(H, a2.b, (size_t)(need + 1) * 8))) return rc;
+            TmpBuf t2(H), r2(H), o2(H), f2(H);
+            DevBuf& a2 = darena2.b;
+            if ((rc = dalloc(H, a2, (size_t)(need + 1) * 8))) return rc;
             if ((rc = upload(H, t2.b, redo.data(), redo.size() * sizeof(AcaTask)))) return rc;
             if ((rc = dalloc(H, r2.b, redo.size() * 4))) return rc;
             if ((rc = dalloc(H, o2.b, redo.size() * 8))) return rc;
             if ((rc = dalloc(H, f2.b, redo.size() * 4))) return rc;
-            HM_CUDA(cudaMemsetAsync(dcnt.b.p, 0, 64, s));
             HM_CUDA(cudaMemsetAsync(dtop.b.p, 0, 64, s));
-            int64_t g2 = std::min<int64_t>((int64_t)redo.size(), grid);
-            aca_kernel<<<(unsigned)g2, kAcaThreads, 0, s>>>(
-                g, t2.b.as<AcaTask>(), (int)redo.size(), H.d_adm.as<Blk>(), prm, dscr.b.as<double>(),
-                dz.b.as<unsigned char>(), dcnt.b.as<int>(), a2.b.as<double>(),
-                dtop.b.as<unsigned long long>(), need + 1, r2.b.as<int32_t>(), o2.b.as<int64_t>(),
-                f2.b.as<int32_t>());
-            HM_CUDA(cudaGetLastError());
-            // fold the re-run results into the main arena: grow it and append
+            // the re-run tasks keep their decreasing size order; classes as above,
+            // each grid bounded by the scratch already allocated
+            std::vector<AcaClass> rcl;
+            split(redo, rcl);
+            for (AcaClass& c : rcl) {
+                const size_t per_cta = (size_t)c.prm.kcap_all * (size_t)(c.prm.mmax + c.prm.nmax) * 8;
+                c.grid = std::max<int64_t>(1, std::min<int64_t>({c.grid, (int64_t)(dscr.b.bytes / per_cta),
+                                                                 (int64_t)(dz.b.bytes / (size_t)c.prm.mmax)}));
+                HM_CUDA(cudaMemsetAsync(dcnt.b.p, 0, 64, s));
+                aca_kernel<<<(unsigned)c.grid, kAcaThreads, 0, s>>>(
+                    g, t2.b.as<AcaTask>() + c.i0, (int)(c.i1 - c.i0), H.d_adm.as<Blk>(), c.prm, dscr.b.as<double>(),
+                    dz.b.as<unsigned char>(), dcnt.b.as<int>(), a2.as<double>(), dtop.b.as<unsigned long long>(),
+                    need + 1, r2.b.as<int32_t>() + c.i0, o2.b.as<int64_t>() + c.i0, f2.b.as<int32_t>() + c.i0);
+                HM_CUDA(cudaGetLastError());
+            }
+            // the re-run results: offsets past `cap` address the second arena
             std::vector<int32_t> rr(redo.size()), ff(redo.size());
             std::vector<int64_t> oo(redo.size());
             HM_CUDA(cudaMemcpyAsync(rr.data(), r2.b.p, rr.size() * 4, cudaMemcpyDeviceToHost, s));
             HM_CUDA(cudaMemcpyAsync(oo.data(), o2.b.p, oo.size() * 8, cudaMemcpyDeviceToHost, s));
             HM_CUDA(cudaMemcpyAsync(ff.data(), f2.b.p, ff.size() * 4, cudaMemcpyDeviceToHost, s));
             HM_CUDA(cudaStreamSynchronize(s));
-            // new combined arena: old contents (first cap) + re-run contents
-            DevBuf big;
-            if ((rc = dalloc(H, big, (size_t)(cap + need + 1) * 8))) return rc;
-            HM_CUDA(cudaMemcpyAsync(big.p, darena.b.p, (size_t)cap * 8, cudaMemcpyDeviceToDevice, s));
-            HM_CUDA(cudaMemcpyAsync(big.as<double>() + cap, a2.b.p, (size_t)need * 8,
-                                    cudaMemcpyDeviceToDevice, s));
-            HM_CUDA(cudaStreamSynchronize(s));  // copies done before the sources are released
-            H.alloc.release(darena.b.p, darena.b.bytes);
-            darena.b = big;
             for (size_t q = 0; q < redo.size(); ++q) {
                 size_t t = (size_t)redo_idx[q];
                 trank[t] = rr[q];
@@ -964,7 +1018,7 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
     if (ntask > 0) {
         repack_kernel<<<(unsigned)ntask, 128, 0, s>>>(
             dtask.b.as<AcaTask>(), (int)ntask, H.d_adm.as<Blk>(), drank.b.as<int32_t>(),
-            doff.b.as<int64_t>(), darena.b.as<double>(), H.d_uoff.as<int64_t>(),
+            doff.b.as<int64_t>(), darena.b.as<double>(), (int64_t)cap, darena2.b.as<double>(), H.d_uoff.as<int64_t>(),
             H.d_voff.as<int64_t>(), H.U64.as<double>(), H.V64.as<double>());
         HM_CUDA(cudaGetLastError());
     }
@@ -1132,8 +1186,9 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
 
     if ((rc = dalloc(H, H.xh, (size_t)H.max_rhs * 3 * M * 8))) return rc;
     if ((rc = dalloc(H, H.yh, (size_t)H.max_rhs * 3 * M * 8))) return rc;
-    // the FP64 form is always available
-    if ((rc = pack_device(H, HM_FP64, s))) return rc;
+    // the FP64 form, unless deferred to hm_pack
+    if (!(H.prm.flags & HM_DEFER_FP64))
+        if ((rc = pack_device(H, HM_FP64, s))) return rc;
     HM_CUDA(cudaStreamSynchronize(s));
     float t01 = 0, t12 = 0, t23 = 0;
     cudaEventElapsedTime(&t01, ev[0], ev[1]);
@@ -1163,6 +1218,7 @@ extern "C" int hm_aca_assemble(const hm_tree* tree, const hm_params* prm, const 
     if (prm->kmax < 0 || prm->kmax > kKmaxLimit)
         return fail(HM_EINVAL, "hm_aca_assemble: kmax must lie in 0..%d", kKmaxLimit);
     if (prm->max_rhs < 0 || prm->max_rhs > 64) return fail(HM_EINVAL, "hm_aca_assemble: max_rhs must lie in 0..64");
+    if (prm->flags & ~HM_DEFER_FP64) return fail(HM_EINVAL, "hm_aca_assemble: unknown flags 0x%x", prm->flags);
     hm_matrix* H = new (std::nothrow) hm_matrix();
     if (!H) return fail(HM_ENOMEM, "hm_aca_assemble: out of host memory");
     H->prm = *prm;

@@ -79,7 +79,6 @@ class Arena {
         }
     }
     size_t size() const { return size_; }
-    size_t used() const { return used_; }
 
   private:
     std::map<size_t, size_t> free_;

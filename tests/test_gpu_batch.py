@@ -179,3 +179,17 @@ def test_compact_keeps_the_packed_form_and_releases_fp64():
     B.matvec(x, y2)
     torch.cuda.synchronize()
     assert torch.equal(y0, y2)
+
+
+def test_deferred_fp64_form_is_built_on_request():
+    V, T = inputs.icosphere(2)
+    tr = binding.build_cluster_tree(V, T, 16, 0.8)
+    Hd = binding.aca_assemble(tr, 1.0, 0.3, 1e-4, max_rhs=1, defer_fp64=True)
+    H = binding.aca_assemble(tr, 1.0, 0.3, 1e-4, max_rhs=1)
+    x = torch.tensor(inputs.uniform_rhs(3 * len(T), 6), device="cuda")[0]
+    with pytest.raises(binding.HMError):
+        _alone(Hd, x, "fp64")
+    Hd.pack("fp64")
+    a, b = _alone(Hd, x, "fp64"), _alone(H, x, "fp64")
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
