@@ -12,9 +12,10 @@ L2, so every step streams it from HBM; no L2 flush is needed.
 
 Besides the headline the JSON line carries, as context: the FP64 form, 32
 right-hand sides, end-to-end products with host buffers, "batch64" (batched
-products over 64 ellipsoid meshes with 1 and 16 right-hand sides) and
+products over 64 ellipsoid meshes with 1 and 16 right-hand sides), "solve"
+(GMRES with FP64-residual refinement to 1e-8 on a 196,608-triangle cube) and
 "serving" (the request loop over 16 resident meshes at swept Poisson rates,
-p50 / p99 latency); --no-batch / --no-serve skip the last two.
+p50 / p99 latency); --no-batch / --no-solve / --no-serve skip them.
 
 Under torchrun (N > 1) every rank runs its own replica (the product shards
 into independent problems; no collective on the data path): weak scaling,
@@ -366,7 +367,8 @@ def run_ours(args):
     # ---- batched and served workloads (their own matrices; free this one first)
     del H, X, Y
     torch.cuda.empty_cache()
-    for key, skip, fn in (("batch64", args.no_batch, bench_batch), ("serving", args.no_serve, bench_serving)):
+    for key, skip, fn in (("batch64", args.no_batch, bench_batch), ("solve", args.no_solve, bench_solve),
+                          ("serving", args.no_serve, bench_serving)):
         if skip or rank != 0 or ws != 1:
             continue
         try:
@@ -430,6 +432,53 @@ def bench_batch(args):
     B.check()
     out["bytes_per_product_gb"] = round(bytes_prod / 1e9, 2)
     del B, mats
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_solve(args):
+    """The Dirichlet solve on the cube surface [-1,1]^3 with 128 x 128
+    squares per face (196,608 triangles, 589,824 dofs), nu = 0.3, leaf 64:
+    GMRES(50) on the BF16 form inside FP64-residual iterative refinement to
+    ||g - V_h t|| <= 1e-8 ||g||; g = (1, 0, 0) + uniform[-1, 1] per dof."""
+    import torch
+    from paper_2205_04752_gb300 import binding, inputs
+    V, T = inputs.cube_surface(128)
+    M = len(T)
+    t0 = time.perf_counter()
+    tr = binding.build_cluster_tree(V, T, 64, 0.8)
+    H = binding.aca_assemble(tr, 1.0, 0.3, 1e-4, max_rhs=1)
+    H.pack("bf16")
+    torch.cuda.synchronize()
+    t_asm = time.perf_counter() - t0
+    g = (np.array([1.0, 0.0, 0.0])[None, :] + np.random.default_rng(2).uniform(-1, 1, (M, 3))).ravel()
+    gd = torch.tensor(g, device="cuda")
+    td = torch.zeros_like(gd)
+    out = {"workload": "cube surface 6x128x128x2 = 196,608 triangles, 589,824 dofs, nu 0.3, leaf 64",
+           "assemble_s": round(t_asm, 2)}
+    stream = torch.cuda.current_stream()
+    for f in ("bf16", "fp64"):
+        binding.hmatvec(H, gd, td, f)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            binding.hmatvec(H, gd, td, f)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[f"{f}_matvec_ms"] = round(e0.elapsed_time(e1) / 5, 3)
+    td.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = binding.solve(H, gd, td, tol=1e-8, inner_form="bf16", restart=50, max_inner=5000,
+                         raise_on_fail=False)
+    torch.cuda.synchronize()
+    out["solve_s"] = round(time.perf_counter() - t0, 3)
+    out.update({k: info[k] for k in ("iterations", "restarts", "refinements", "rel_residual", "converged")})
+    # what the same iteration count would cost on the plain FP64 form
+    out["fp64_inner_estimate_s"] = round(info["iterations"] * out["fp64_matvec_ms"] * 1e-3, 2)
+    del H
     torch.cuda.empty_cache()
     return out
 
@@ -505,6 +554,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-mesh batched products")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-loop measurement")
+    ap.add_argument("--no-solve", action="store_true", help="skip the 196,608-triangle cube solve")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[10.0, 30.0, 100.0])
     ap.add_argument("--serve-seconds", type=float, default=4.0)
     ap.add_argument("--minimal", action="store_true",
