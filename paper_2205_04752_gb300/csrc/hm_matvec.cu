@@ -351,10 +351,12 @@ __global__ void __launch_bounds__(kThreads) fwd_big_kernel(
 }
 
 // Several (G) interleaved right-hand sides.  A block's work is the pairs
-// (column vector q, RHS chunk c of RC vectors); T threads (a warp, or the
-// CTA for a large block) take one pair each, with GG = T / pairs row groups
-// when there are fewer pairs than threads (partial sums added in a fixed
-// order through shared memory), else rounds of pairs over all rows.
+// (column vector q, RHS chunk c of RC vectors).  T threads (a warp, or the CTA
+// for a large block) split the rows into GG groups and take the pairs in
+// rounds of PR = T / GG; the GG partial sums are added in a fixed order
+// through shared memory.  A warp uses GG = 32 / pairs when the pairs fit a
+// warp (else GG = 1, rounds of 32); a CTA keeps at most 32 pairs per round so
+// that every large block has at least 4 row groups.
 template <class TF, class TA, int RC, int T>
 __device__ __forceinline__ void fwd_multi_block(const FwdRec& rec, const FwdArgs<TF, TA, true>& fa, int G, int tid,
                                                 TA* red)
@@ -364,10 +366,13 @@ __device__ __forceinline__ void fwd_multi_block(const FwdRec& rec, const FwdArgs
     const int Cp = (rec.C + 7) & ~7, Q = Cp / VEC;
     const int NRC = (G + RC - 1) / RC;
     const int pairs = Q * NRC;
-    const int GG = pairs >= T ? 1 : T / pairs;
-    for (int pr0 = 0; pr0 < pairs; pr0 += T) {
-        const int pr = pr0 + tid % min(pairs, T);
-        const int g = GG > 1 ? tid / pairs : (tid < pairs - pr0 ? 0 : GG);
+    const int GG = T == 32 ? max(1, 32 / pairs) : max(1, T / min(pairs, T / 4));
+    const int PR = T / GG;
+    const int pl = tid % PR, g = tid / PR;
+    for (int pr0 = 0; pr0 < pairs; pr0 += PR) {
+        const int nr = min(PR, pairs - pr0);
+        const bool active = g < GG && pl < nr;
+        const int pr = pr0 + pl;
         const int q = pr % Q, c = pr / Q;
         const int nq = min(RC, G - c * RC);
         TA acc[VEC][RC][3];
@@ -375,7 +380,7 @@ __device__ __forceinline__ void fwd_multi_block(const FwdRec& rec, const FwdArgs
         for (int e = 0; e < VEC; ++e)
 #pragma unroll
             for (int k = 0; k < RC; ++k) acc[e][k][0] = acc[e][k][1] = acc[e][k][2] = (TA)0;
-        if (g < GG) {
+        if (active) {
             const TF* vp = fa.Vb + (size_t)q * VEC;
             const TA* xp = fa.x0 + (size_t)c * RC * 4;
 #pragma unroll 2
@@ -398,7 +403,7 @@ __device__ __forceinline__ void fwd_multi_block(const FwdRec& rec, const FwdArgs
             }
         }
         if (GG == 1) {
-            if (g < GG) {
+            if (active) {
 #pragma unroll
                 for (int e = 0; e < VEC; ++e) {
                     const int col = q * VEC + e;
@@ -406,13 +411,14 @@ __device__ __forceinline__ void fwd_multi_block(const FwdRec& rec, const FwdArgs
 #pragma unroll
                     for (int k = 0; k < RC; ++k) {
                         if (k >= nq) break;
-                        write_w<TA>(rec, col, acc[e][k][0], acc[e][k][1], acc[e][k][2], fa.SU, fa.wr, fa.c1, fa.c2, G, c * RC + k);
+                        write_w<TA>(rec, col, acc[e][k][0], acc[e][k][1], acc[e][k][2], fa.SU, fa.wr, fa.c1, fa.c2, G,
+                                    c * RC + k);
                     }
                 }
             }
         } else {
-            if (g < GG) {
-                TA* rp = red + (size_t)(g * pairs + pr) * kPer;
+            if (active) {
+                TA* rp = red + (size_t)(g * PR + pl) * kPer;
 #pragma unroll
                 for (int e = 0; e < VEC; ++e)
 #pragma unroll
@@ -422,16 +428,16 @@ __device__ __forceinline__ void fwd_multi_block(const FwdRec& rec, const FwdArgs
             }
             if (T == 32) __syncwarp();
             else __syncthreads();
-            for (int idx = tid; idx < pairs * VEC * RC; idx += T) {
+            for (int idx = tid; idx < nr * VEC * RC; idx += T) {
                 const int pp = idx / (VEC * RC), rem = idx - pp * (VEC * RC);
                 const int e = rem / RC, k = rem - e * RC;
-                const int qq = pp % Q, cc = pp / Q;
+                const int qq = (pr0 + pp) % Q, cc = (pr0 + pp) / Q;
                 const int col = qq * VEC + e, r = cc * RC + k;
                 if (col >= rec.C || r >= G) continue;
                 TA z[3] = {(TA)0, (TA)0, (TA)0};
                 for (int gg = 0; gg < GG; ++gg)
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) z[a] += red[(size_t)(gg * pairs + pp) * kPer + (e * RC + k) * 3 + a];
+                    for (int a = 0; a < 3; ++a) z[a] += red[(size_t)(gg * PR + pp) * kPer + (e * RC + k) * 3 + a];
                 write_w<TA>(rec, col, z[0], z[1], z[2], fa.SU, fa.wr, fa.c1, fa.c2, G, r);
             }
             if (T == 32) __syncwarp();

@@ -204,16 +204,21 @@ __device__ __forceinline__ void smem_rows(const T* p, TA* o)
 // interleaved, 4-vector (position or column, r) at index pos * G + r).  A
 // consumer thread holds Rr rows (16 bytes of U) for RC right-hand sides.
 // RC = 1 is the single-vector kernel; RC * Rr = 16 otherwise.
+// A slot is kStageBytes of stream data followed by kAuxBytes of staged 4-vectors.
+// The single-vector kernel keeps 4 slots and a separate reduction area
+// (about 100 KB, two CTAs per SM); the multi-vector kernel keeps 3 slots of
+// 32 KB and reduces a finished leaf inside the slot of its last stage, one
+// RHS-chunk position at a time, so that it too fits two CTAs per SM.
 template <class TF, class TA, int RC>
 struct LeafCfg {
     static constexpr int Rr = Smem16<TF, TA>::N;
-    // 4-vectors of w / x staged beside each slot
+    static constexpr int kS = RC == 1 ? 4 : 3;
     static constexpr int kAuxBytes = RC == 1 ? kMaxSeg * 4 * (int)sizeof(TA) : 16384;
-    static constexpr size_t smem()
-    {
-        return (size_t)kStages * kStageBytes + (size_t)kStages * kAuxBytes +
-               (size_t)kConsumers * Rr * RC * 3 * sizeof(TA);
-    }
+    static constexpr int kSlotBytes = kStageBytes + kAuxBytes;
+    static constexpr int kRedBytes = kConsumers * Rr * 3 * (int)sizeof(TA) * (RC == 1 ? 1 : 0);
+    static_assert(RC == 1 || kConsumers * Rr * 3 * (int)sizeof(TA) <= kSlotBytes,
+                  "one RHS position of the leaf reduction must fit a slot");
+    static constexpr size_t smem() { return (size_t)kS * kSlotBytes + (size_t)kRedBytes; }
 };
 
 template <class TF, class TN, class TA, int RC>
@@ -224,10 +229,12 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
 {
     using Cfg = LeafCfg<TF, TA, RC>;
     constexpr int Rr = Cfg::Rr;
+    constexpr int NS = Cfg::kS;
     extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char* sbuf = smem;
-    unsigned char* auxb = smem + kStages * kStageBytes;  // kStages x kAuxBytes
-    TA* red = reinterpret_cast<TA*>(auxb + kStages * Cfg::kAuxBytes);
+    // slot q: stream data at smem + q * kSlotBytes, its 4-vectors kStageBytes later
+    auto sdata = [&](int q) { return smem + (size_t)q * Cfg::kSlotBytes; };
+    auto saux = [&](int q) { return smem + (size_t)q * Cfg::kSlotBytes + kStageBytes; };
+    TA* red1 = reinterpret_cast<TA*>(smem + (size_t)NS * Cfg::kSlotBytes);  // single-vector kernel only
     __shared__ __align__(8) uint64_t full[kStages];
     __shared__ __align__(8) uint64_t empty[kStages];
     __shared__ StageMeta meta[kStages];
@@ -235,7 +242,7 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int vecG = 4 * G;  // TA values per segment / column in the staged vectors
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < NS; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], kConsumers / 32);
         }
@@ -254,9 +261,9 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
         // reads (w for the far field, x for the near field), G per index.
         auto emit = [&](int mesh, int lf, int kind, int first, int count, int last, const void* src,
                         uint32_t bytes, const int2* items, int ni, int* cur, const TA* vec) -> bool {
-            const int slot = it % kStages;
-            if (it >= kStages) {
-                if (!mbar_wait(&empty[slot], (uint32_t)((it / kStages) - 1) & 1u, err)) return false;
+            const int slot = it % NS;
+            if (it >= NS) {
+                if (!mbar_wait(&empty[slot], (uint32_t)((it / NS) - 1) & 1u, err)) return false;
             }
             if (lane == 0) {
                 StageMeta m;
@@ -272,7 +279,7 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
             }
             __syncwarp();
             if (kind < 2) {
-                TA* av = reinterpret_cast<TA*>(auxb + (size_t)slot * Cfg::kAuxBytes);
+                TA* av = reinterpret_cast<TA*>(saux(slot));
                 const int end = first + count;
                 int q0 = *cur;
                 for (;;) {
@@ -299,7 +306,7 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
                     }
                     q0 += 32;
                 }
-                if (lane == 0) bulk_g2s(sbuf + (size_t)slot * kStageBytes, src, bytes, &full[slot]);
+                if (lane == 0) bulk_g2s(sdata(slot), src, bytes, &full[slot]);
             } else if (lane == 0) {
                 mbar_arrive(&full[slot]);
             }
@@ -355,9 +362,9 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
         if (ok) ok = emit(0, -1, 2, 0, 0, 0, nullptr, 0, nullptr, 0, nullptr, nullptr);
         if (!ok) {
             // drain this CTA's own copies in flight before returning (bounded)
-            for (int k = 1; k <= kStages && k <= it; ++k) {
+            for (int k = 1; k <= NS && k <= it; ++k) {
                 const int j = it - k;
-                mbar_wait(&full[j % kStages], (uint32_t)(j / kStages) & 1u, err);
+                mbar_wait(&full[j % NS], (uint32_t)(j / NS) & 1u, err);
             }
         }
         return;
@@ -374,8 +381,8 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
     TA c1 = (TA)0, c2 = (TA)0;
     TA acc[Rr][RC][3];
     for (int it = 0;; ++it) {
-        const int slot = it % kStages;
-        if (!mbar_wait(&full[slot], (uint32_t)(it / kStages) & 1u, err)) break;
+        const int slot = it % NS;
+        if (!mbar_wait(&full[slot], (uint32_t)(it / NS) & 1u, err)) break;
         const StageMeta m = meta[slot];
         if (m.kind == 2) break;
         if (m.leaf != cur || m.pad[0] != cur_mesh) {
@@ -399,10 +406,10 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
 #pragma unroll
                 for (int q = 0; q < RC; ++q) acc[e][q][0] = acc[e][q][1] = acc[e][q][2] = (TA)0;
         }
-        const TA* av = reinterpret_cast<const TA*>(auxb + (size_t)slot * Cfg::kAuxBytes) + (size_t)c * RC * 4;
+        const TA* av = reinterpret_cast<const TA*>(saux(slot)) + (size_t)c * RC * 4;
         if (h < H) {
             if (m.kind == 0) {
-                const TF* sb = reinterpret_cast<const TF*>(sbuf + (size_t)slot * kStageBytes) + p * Rr;
+                const TF* sb = reinterpret_cast<const TF*>(sdata(slot)) + p * Rr;
                 if (RC == 1 && G == 1) {
                     // single vector: two segments per iteration
                     int s = h;
@@ -450,8 +457,8 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
                         }
                     }
                 }
-            } else {
-                const TN* sb = reinterpret_cast<const TN*>(sbuf + (size_t)slot * kStageBytes) + p * Rr;
+            } else if (RC == 1) {
+                const TN* sb = reinterpret_cast<const TN*>(sdata(slot)) + p * Rr;
                 for (int s = h; s < m.count; s += H) {
                     const TN* e0 = sb + (size_t)s * 6 * mp;
                     TA v11[Rr], v12[Rr], v13[Rr], v22[Rr], v23[Rr], v33[Rr];
@@ -461,49 +468,104 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
                     smem_rows<TN, TA, Rr>(e0 + 3 * mp, v22);
                     smem_rows<TN, TA, Rr>(e0 + 4 * mp, v23);
                     smem_rows<TN, TA, Rr>(e0 + 5 * mp, v33);
+                    TA x0, x1, x2;
+                    load3(av + (size_t)s * G * 4, x0, x1, x2);
+#pragma unroll
+                    for (int e = 0; e < Rr; ++e) {
+                        const TA vd = c1 * (v11[e] + v22[e] + v33[e]);
+                        acc[e][0][0] += vd * x0 + c2 * (v11[e] * x0 + v12[e] * x1 + v13[e] * x2);
+                        acc[e][0][1] += vd * x1 + c2 * (v12[e] * x0 + v22[e] * x1 + v23[e] * x2);
+                        acc[e][0][2] += vd * x2 + c2 * (v13[e] * x0 + v23[e] * x1 + v33[e] * x2);
+                    }
+                }
+            } else {
+                // several vectors: the six values of a column one at a time
+                // (few live registers); per vector the products c x_b that
+                // multiply each value: V_aa enters y_a with (c1 + c2) x_a and the
+                // other two components with c1 x_b; V_ab (a != b) enters y_a with
+                // c2 x_b and y_b with c2 x_a
+                const TN* sb = reinterpret_cast<const TN*>(sdata(slot)) + p * Rr;
+                const TA c12 = c1 + c2;
+                for (int s = h; s < m.count; s += H) {
+                    const TN* e0 = sb + (size_t)s * 6 * mp;
+                    TA xs[RC][3];
 #pragma unroll
                     for (int q = 0; q < RC; ++q) {
-                        if (RC > 1 && c * RC + q >= G) break;
-                        TA x0, x1, x2;
-                        load3(av + ((size_t)s * G + q) * 4, x0, x1, x2);
+                        if (c * RC + q < G) load3(av + ((size_t)s * G + q) * 4, xs[q][0], xs[q][1], xs[q][2]);
+                        else xs[q][0] = xs[q][1] = xs[q][2] = (TA)0;
+                    }
 #pragma unroll
-                        for (int e = 0; e < Rr; ++e) {
-                            const TA vd = c1 * (v11[e] + v22[e] + v33[e]);
-                            acc[e][q][0] += vd * x0 + c2 * (v11[e] * x0 + v12[e] * x1 + v13[e] * x2);
-                            acc[e][q][1] += vd * x1 + c2 * (v12[e] * x0 + v22[e] * x1 + v23[e] * x2);
-                            acc[e][q][2] += vd * x2 + c2 * (v13[e] * x0 + v23[e] * x1 + v33[e] * x2);
+                    for (int v = 0; v < 6; ++v) {
+                        // (a, b) of value v: 11, 12, 13, 22, 23, 33
+                        const int va = v < 3 ? 0 : (v < 5 ? 1 : 2);
+                        const int vb = v < 3 ? v : (v < 5 ? v - 2 : 2);
+                        TA val[Rr];
+                        smem_rows<TN, TA, Rr>(e0 + v * mp, val);
+#pragma unroll
+                        for (int q = 0; q < RC; ++q) {
+                            if (va == vb) {
+                                const TA f0 = (va == 0 ? c12 : c1) * xs[q][0];
+                                const TA f1 = (va == 1 ? c12 : c1) * xs[q][1];
+                                const TA f2 = (va == 2 ? c12 : c1) * xs[q][2];
+#pragma unroll
+                                for (int e = 0; e < Rr; ++e) {
+                                    acc[e][q][0] += f0 * val[e];
+                                    acc[e][q][1] += f1 * val[e];
+                                    acc[e][q][2] += f2 * val[e];
+                                }
+                            } else {
+                                const TA fa = c2 * xs[q][vb], fb = c2 * xs[q][va];
+#pragma unroll
+                                for (int e = 0; e < Rr; ++e) {
+                                    acc[e][q][va] += fa * val[e];
+                                    acc[e][q][vb] += fb * val[e];
+                                }
+                            }
                         }
                     }
                 }
             }
         }
-        // the slot may be refilled once every consumer warp is done with it
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[slot]);
+        if (RC == 1 || !m.last) {
+            // the slot may be refilled once every consumer warp is done with it
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[slot]);
+        }
         if (m.last) {
-            // red[((h * P + p) * NRC + c)][e][q][a]
-            constexpr int kPer = Rr * RC * 3;
-            if (h < H) {
-                TA* rp = red + (size_t)((h * P + p) * NRC + c) * kPer;
+            // the H partial sums of every (row, vector, component), added in a
+            // fixed order; red[((h * P + p) * NRC + c)][e][a] for one position q
+            // of the RHS chunk at a time (the multi-vector kernel reuses the
+            // slot of this last stage, released afterwards)
+            TA* red = RC == 1 ? red1 : reinterpret_cast<TA*>(sdata(slot));
+            constexpr int kPer = Rr * 3;
+            if (RC > 1) named_barrier_consumers();  // everyone is done reading the slot
 #pragma unroll
-                for (int e = 0; e < Rr; ++e)
+            for (int q = 0; q < RC; ++q) {
+                if (h < H) {
+                    TA* rp = red + (size_t)((h * P + p) * NRC + c) * kPer;
 #pragma unroll
-                    for (int q = 0; q < RC; ++q)
+                    for (int e = 0; e < Rr; ++e)
 #pragma unroll
-                        for (int a = 0; a < 3; ++a) rp[(e * RC + q) * 3 + a] = acc[e][q][a];
+                        for (int a = 0; a < 3; ++a) rp[e * 3 + a] = acc[e][q][a];
+                }
+                named_barrier_consumers();
+                const int nvec = (G - q + RC - 1) / RC;  // vectors r = cc * RC + q < G
+                const int per_row = 3 * nvec;
+                for (int idx = ctid; idx < mt * per_row; idx += kConsumers) {
+                    const int i = idx / per_row, rem = idx - i * per_row;
+                    const int cc = rem / 3, a = rem - 3 * cc;
+                    const int pp = i / Rr, e = i - pp * Rr;
+                    TA sum = (TA)0;
+                    for (int g = 0; g < H; ++g) sum += red[(size_t)((g * P + pp) * NRC + cc) * kPer + e * 3 + a];
+                    const int r = cc * RC + q;
+                    y[(size_t)r * ld + xoff + 3 * (size_t)perm[t0 + i] + a] = (double)sum;
+                }
+                named_barrier_consumers();
             }
-            named_barrier_consumers();
-            const int per_row = 3 * G;
-            for (int idx = ctid; idx < mt * per_row; idx += kConsumers) {
-                const int i = idx / per_row, rem = idx - i * per_row;
-                const int r = rem / 3, a = rem - 3 * r;
-                const int pp = i / Rr, e = i - pp * Rr, cc = r / RC, q = r - cc * RC;
-                TA sum = (TA)0;
-                for (int g = 0; g < H; ++g)
-                    sum += red[(size_t)((g * P + pp) * NRC + cc) * kPer + (e * RC + q) * 3 + a];
-                y[(size_t)r * ld + xoff + 3 * (size_t)perm[t0 + i] + a] = (double)sum;
+            if (RC > 1) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
             }
-            named_barrier_consumers();
         }
     }
 }
