@@ -1080,7 +1080,9 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
             lf_items.push_back(LeafFarItem{seg, 0});  // sentinel: number of segments
             lf_src.push_back(PackSrc{0, 0, 0});
             lf_ptr.push_back((int32_t)lf_items.size());
-            ul += (int64_t)seg * mp;
+            // the 16-bit forms take segments 16 at a time (one tensor-core K step):
+            // every leaf's U stream holds a multiple of 16 segments, zero padded
+            ul += (int64_t)((seg + 15) & ~15) * mp;
             int32_t col = 0;
             ln_base.push_back(nl);
             for (int32_t b : near_by_row[(size_t)lf]) {

@@ -391,12 +391,14 @@ int hm_batch_autotune(hm_batch* B, int32_t nrhs, int32_t reps, hm_schedule* chos
 int hm_batch_check(const hm_batch* B)
 {
     if (!B) return fail(HM_EINVAL, "hm_batch_check: NULL batch");
-    int flag = 0;
-    HM_CUDA(cudaMemcpy(&flag, B->err.p, sizeof(int), cudaMemcpyDeviceToHost));
-    if (flag) {
-        const int zero = 0;
-        HM_CUDA(cudaMemcpy(B->err.p, &zero, sizeof(int), cudaMemcpyHostToDevice));
-        return fail(HM_ETIMEOUT, "hm_batch_check: a bounded device wait ran out in an earlier product");
+    int e[4] = {0, 0, 0, 0};
+    HM_CUDA(cudaMemcpy(e, B->err.p, sizeof e, cudaMemcpyDeviceToHost));
+    if (e[0]) {
+        const int zero[4] = {0, 0, 0, 0};
+        HM_CUDA(cudaMemcpy(B->err.p, zero, sizeof zero, cudaMemcpyHostToDevice));
+        return fail(HM_ETIMEOUT,
+                    "hm_batch_check: a bounded device wait ran out in an earlier product (site %d, stage %d, CTA %d)",
+                    e[1], e[2], e[3]);
     }
     return HM_OK;
 }

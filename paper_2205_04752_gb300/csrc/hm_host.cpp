@@ -423,13 +423,15 @@ int hm_export_near(const hm_matrix* H, int64_t blk, double* out)
 int hm_check(const hm_matrix* H)
 {
     if (!H) return fail(HM_EINVAL, "hm_check: NULL matrix");
-    int flag = 0;
-    HM_CUDA(cudaMemcpy(&flag, H->d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
-    if (flag) {
-        const int zero = 0;
-        HM_CUDA(cudaMemcpy(H->d_err.p, &zero, sizeof(int), cudaMemcpyHostToDevice));
-        if (flag == 2) return fail(HM_EINVAL, "hm_check: an earlier product met a leaf larger than a stage");
-        return fail(HM_ETIMEOUT, "hm_check: a bounded device wait ran out in an earlier product");
+    int e[4] = {0, 0, 0, 0};
+    HM_CUDA(cudaMemcpy(e, H->d_err.p, sizeof e, cudaMemcpyDeviceToHost));
+    if (e[0]) {
+        const int zero[4] = {0, 0, 0, 0};
+        HM_CUDA(cudaMemcpy(H->d_err.p, zero, sizeof zero, cudaMemcpyHostToDevice));
+        if (e[0] == 2) return fail(HM_EINVAL, "hm_check: an earlier product met a leaf larger than a stage");
+        return fail(HM_ETIMEOUT,
+                    "hm_check: a bounded device wait ran out in an earlier product (site %d, stage %d, CTA %d)",
+                    e[1], e[2], e[3]);
     }
     return HM_OK;
 }

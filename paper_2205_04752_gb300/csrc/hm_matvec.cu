@@ -512,7 +512,11 @@ __global__ void colscale_kernel(int ntask, const Blk* __restrict__ blks, const i
     }
 }
 
-// U leaf-major: one CTA per leaf
+// U leaf-major: one CTA per leaf.  The 16-bit forms store each leaf's stream
+// in 8 x 8 tiles, segment group g = s / 8 and row block b = i / 8 at
+// ((g * mp / 8 + b) * 64 + (s % 8) * 8 + i % 8): eight rows of one segment
+// stay 16 contiguous bytes, and the tiles are the core matrices of an
+// MN-major tensor-core operand.  Other forms: segment-major, s * mp + i.
 template <class T>
 __global__ void pack_ul_kernel(const int32_t* __restrict__ leaf, const int64_t* __restrict__ lf_base,
                                const int32_t* __restrict__ lf_ptr, const LeafFarItem* __restrict__ items,
@@ -533,7 +537,10 @@ __global__ void pack_ul_kernel(const int32_t* __restrict__ leaf, const int64_t* 
                 v = U[ps.src + (size_t)l * ps.ld + i];
                 if (SU) v /= (double)SU[it.col + l];
             }
-            dst[(size_t)(it.seg_start + l) * mp + i] = cvt<T>(v);
+            const size_t sg = (size_t)it.seg_start + l;
+            const size_t o = sizeof(T) == 2 ? ((sg / 8) * (size_t)(mp / 8) + (size_t)(i / 8)) * 64 + (sg % 8) * 8 + i % 8
+                                            : sg * mp + i;
+            dst[o] = cvt<T>(v);
         }
     }
 }
@@ -736,6 +743,8 @@ int pack_form(hm_matrix& H, int form, const float* SU, const float* SV, cudaStre
     int rc;
     if ((rc = dalloc(H, H.Ul[form], (size_t)H.ul_total * sizeof(T)))) return rc;
     if ((rc = dalloc(H, H.Vr[form], (size_t)H.vr_total * sizeof(T)))) return rc;
+    // padding segments are zero
+    HM_CUDA(cudaMemsetAsync(H.Ul[form].p, 0, (size_t)H.ul_total * sizeof(T), s));
     if (H.nleaves > 0) {
         pack_ul_kernel<T><<<(unsigned)H.nleaves, 256, 0, s>>>(
             H.d_leaf.as<int32_t>(), H.d_lf_base.as<int64_t>(), H.d_lf_ptr.as<int32_t>(),

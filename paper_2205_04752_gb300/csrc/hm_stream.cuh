@@ -90,14 +90,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
-// bounded wait for the phase with the given parity; false (and *err set) on expiry
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err)
+// bounded wait for the phase with the given parity; false on expiry, with
+// err[0] = 1 and the first expiry's site, stage and CTA in err[1..3]
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int site = 0, int stage = 0)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
         if (clock64() - t0 > kWaitCycles) {
+            if (atomicCAS(err + 1, 0, site) == 0) {
+                err[2] = stage;
+                err[3] = (int)blockIdx.x;
+            }
             atomicExch(err, 1);
             return false;
         }
@@ -113,6 +118,18 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
             smem_addr(dst)),
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
+}
+
+// 16 KB of zeros: the staged w of the padding segments of a 16-bit U stream
+__device__ __align__(128) unsigned char g_zeros[16384] = {};
+
+// element offset of rows [Rr p, Rr p + Rr) of segment s in a stage whose
+// first segment is a multiple of 8 (tiled 16-bit streams) or any segment
+template <class TF>
+__device__ __forceinline__ size_t useg(int s, int p, int mp)
+{
+    if (sizeof(TF) == 2) return ((size_t)(s >> 3) * (size_t)(mp >> 3) + (size_t)p) * 64 + (size_t)(s & 7) * 8;
+    return (size_t)s * mp + (size_t)p * (16 / sizeof(TF));
 }
 
 __device__ __forceinline__ void named_barrier_consumers()
@@ -259,11 +276,12 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
         // records); *cur is the item containing `first` and is advanced to
         // the item containing first + count.  vec: the 4-vectors the stream
         // reads (w for the far field, x for the near field), G per index.
+        int sreal = 0;  // real segments of the current leaf's U stream
         auto emit = [&](int mesh, int lf, int kind, int first, int count, int last, const void* src,
                         uint32_t bytes, const int2* items, int ni, int* cur, const TA* vec) -> bool {
             const int slot = it % NS;
             if (it >= NS) {
-                if (!mbar_wait(&empty[slot], (uint32_t)((it / NS) - 1) & 1u, err)) return false;
+                if (!mbar_wait(&empty[slot], (uint32_t)((it / NS) - 1) & 1u, err, 1, it)) return false;
             }
             if (lane == 0) {
                 StageMeta m;
@@ -284,12 +302,13 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
                 int q0 = *cur;
                 for (;;) {
                     // lane l looks at item q0 + l; its end is the next item's start
+                    // (the sentinel's start for the last real item)
                     const int q = q0 + lane;
                     int2 a = make_int2(INT_MAX, 0);
-                    if (q < ni - 1) a = items[q];
+                    if (q < ni) a = items[q];
                     int b = __shfl_down_sync(0xffffffffu, a.x, 1);
                     if (lane == 31) b = (q + 1 < ni) ? items[q + 1].x : INT_MAX;
-                    const bool overlap = a.x < end;  // items are sorted by start
+                    const bool overlap = q < ni - 1 && a.x < end;  // items are sorted by start
                     if (overlap) {
                         const int g0 = max(a.x, first), g1 = min(b, end);
                         if (g0 < g1)
@@ -306,7 +325,15 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
                     }
                     q0 += 32;
                 }
-                if (lane == 0) bulk_g2s(sdata(slot), src, bytes, &full[slot]);
+                if (lane == 0) {
+                    bulk_g2s(sdata(slot), src, bytes, &full[slot]);
+                    // padding segments of a 16-bit U stream: zero w
+                    if (kind == 0 && end > sreal) {
+                        const int z0 = max(first, sreal);
+                        bulk_g2s(av + (size_t)(z0 - first) * vecG, g_zeros,
+                                 (uint32_t)((end - z0) * vecG * sizeof(TA)), &full[slot]);
+                    }
+                }
             } else if (lane == 0) {
                 mbar_arrive(&full[slot]);
             }
@@ -326,14 +353,20 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
             const int mp = (mt + 7) & ~7;
             const int fi0 = md.lf_ptr[lf], fi1 = md.lf_ptr[lf + 1];
             const int ni0 = md.ln_ptr[lf], ni1 = md.ln_ptr[lf + 1];
-            const int S = md.lf_items[fi1 - 1].seg_start;
+            sreal = md.lf_items[fi1 - 1].seg_start;
+            // 16-bit streams are tiled in groups of 8 segments (and stored padded
+            // to 16, the tensor-core K step); the single-vector kernel takes
+            // stages in whole tiles, the multi-vector one in K steps
+            constexpr bool kTiled = sizeof(TF) == 2;
+            constexpr int kGran = RC == 1 ? 8 : 16;
+            const int S = kTiled ? (sreal + kGran - 1) & ~(kGran - 1) : sreal;
             const int Sn = md.ln_items[ni1 - 1].col_start;
             const TF* Ul = static_cast<const TF*>(md.Ul);
             const TN* Nl = static_cast<const TN*>(md.Nl);
             const TA* wvec = w_base + (size_t)md.woff * vecG;
             const TA* xvec = xg_base + (size_t)md.xgoff * vecG;
             const int segB = mp * (int)sizeof(TF);
-            const int perF = min(kStageBytes / segB, perV);
+            const int perF = kTiled ? min(kStageBytes / segB, perV) & ~(kGran - 1) : min(kStageBytes / segB, perV);
             const int colB = 6 * mp * (int)sizeof(TN);
             const int perN = min(kStageBytes / colB, perV);
             if (perF < 1 || perN < 1) {
@@ -364,7 +397,7 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
             // drain this CTA's own copies in flight before returning (bounded)
             for (int k = 1; k <= NS && k <= it; ++k) {
                 const int j = it - k;
-                mbar_wait(&full[j % NS], (uint32_t)(j / NS) & 1u, err);
+                mbar_wait(&full[j % NS], (uint32_t)(j / NS) & 1u, err, 2, j);
             }
         }
         return;
@@ -382,7 +415,7 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
     TA acc[Rr][RC][3];
     for (int it = 0;; ++it) {
         const int slot = it % NS;
-        if (!mbar_wait(&full[slot], (uint32_t)(it / NS) & 1u, err)) break;
+        if (!mbar_wait(&full[slot], (uint32_t)(it / NS) & 1u, err, 3, it)) break;
         const StageMeta m = meta[slot];
         if (m.kind == 2) break;
         if (m.leaf != cur || m.pad[0] != cur_mesh) {
@@ -409,7 +442,7 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
         const TA* av = reinterpret_cast<const TA*>(saux(slot)) + (size_t)c * RC * 4;
         if (h < H) {
             if (m.kind == 0) {
-                const TF* sb = reinterpret_cast<const TF*>(sdata(slot)) + p * Rr;
+                const TF* sb = reinterpret_cast<const TF*>(sdata(slot));
                 if (RC == 1 && G == 1) {
                     // single vector: two segments per iteration
                     int s = h;
@@ -418,8 +451,8 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
                         load3(av + (size_t)s * 4, wa0, wa1, wa2);
                         load3(av + (size_t)(s + H) * 4, wb0, wb1, wb2);
                         TA ua[Rr], ub[Rr];
-                        smem_rows<TF, TA, Rr>(sb + (size_t)s * mp, ua);
-                        smem_rows<TF, TA, Rr>(sb + (size_t)(s + H) * mp, ub);
+                        smem_rows<TF, TA, Rr>(sb + useg<TF>(s, p, mp), ua);
+                        smem_rows<TF, TA, Rr>(sb + useg<TF>(s + H, p, mp), ub);
 #pragma unroll
                         for (int e = 0; e < Rr; ++e) {
                             acc[e][0][0] += ua[e] * wa0 + ub[e] * wb0;
@@ -431,7 +464,7 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
                         TA wa0, wa1, wa2;
                         load3(av + (size_t)s * 4, wa0, wa1, wa2);
                         TA ua[Rr];
-                        smem_rows<TF, TA, Rr>(sb + (size_t)s * mp, ua);
+                        smem_rows<TF, TA, Rr>(sb + useg<TF>(s, p, mp), ua);
 #pragma unroll
                         for (int e = 0; e < Rr; ++e) {
                             acc[e][0][0] += ua[e] * wa0;
@@ -442,7 +475,7 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
                 } else {
                     for (int s = h; s < m.count; s += H) {
                         TA ua[Rr];
-                        smem_rows<TF, TA, Rr>(sb + (size_t)s * mp, ua);
+                        smem_rows<TF, TA, Rr>(sb + useg<TF>(s, p, mp), ua);
 #pragma unroll
                         for (int q = 0; q < RC; ++q) {
                             if (RC > 1 && c * RC + q >= G) break;
