@@ -1182,7 +1182,7 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
     H.max_rhs = H.prm.max_rhs;
     if ((rc = dalloc(H, H.xg, (size_t)H.max_rhs * 4 * M * 8))) return rc;
     if ((rc = dalloc(H, H.wb, (size_t)H.max_rhs * std::max<int64_t>(H.w_total, 1) * 8))) return rc;
-    if ((rc = dalloc(H, H.d_counters, (size_t)2 * H.max_rhs * sizeof(int)))) return rc;
+    if ((rc = dalloc(H, H.d_counters, (size_t)kCounterInts * sizeof(int)))) return rc;
     if ((rc = dalloc(H, H.d_err, 64))) return rc;
     HM_CUDA(cudaMemsetAsync(H.d_err.p, 0, 64, s));
 

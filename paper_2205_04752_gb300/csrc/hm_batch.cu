@@ -232,7 +232,7 @@ int hm_batch_create(const hm_matrix* const* mats, int32_t nmat, int32_t form, in
         (rc = bupload(*B, B->d_work[1], w1.data(), w1.size() * sizeof(int2))) ||
         (rc = balloc(*B, B->xg, (size_t)max_rhs * 4 * (size_t)B->npos * ta)) ||
         (rc = balloc(*B, B->w, (size_t)max_rhs * (size_t)std::max<int64_t>(B->w_total, 1) * ta)) ||
-        (rc = balloc(*B, B->counters, (size_t)max_rhs * sizeof(int))) || (rc = balloc(*B, B->err, 64))) {
+        (rc = balloc(*B, B->counters, (size_t)kCounterInts * sizeof(int))) || (rc = balloc(*B, B->err, 64))) {
         batch_free(B);
         return rc;
     }

@@ -125,6 +125,8 @@ struct MeshDev {
     int64_t xoff, xgoff, woff;
     int32_t M, max_leaf;
     double c1, c2;
+    float wbound;  // 16-bit forms: bound of |w| / max|x| over the factor columns
+    float pad;
 };
 
 // A product over one or more meshes: device tables and work lists.
@@ -139,9 +141,12 @@ struct Plan {
     const int2* work;           // (mesh, leaf) in processing order
     int64_t nwork;
     int32_t max_leaf;
-    int* counters;              // >= nrhs ints of device memory
+    int* counters;              // kCounterInts ints of device memory (work counters, max|x| per vector)
     int* err;
 };
+// device ints of the counter region of a product: one work counter per
+// launch (at most 64) and the max|x| words of a launch at offset 64
+constexpr int kCounterInts = 128;
 
 
 }  // namespace hm
@@ -195,6 +200,7 @@ struct hm_matrix {
     hm::DevBuf Nl64, Nl32;  // near field leaf-major: FP64 form / all other forms
     hm::DevBuf SU, SV;      // per-column scales of the 16-bit forms (float, c_total)
     bool packed[4] = {false, false, false, false};
+    float wbound_su = 0.0f;  // max over factor columns of (U column scale x |s| of its block)
     bool compacted = false;  // FP64 data released (hm_compact)
 
     // workspace

@@ -1,0 +1,427 @@
+// hm_leaf_tc.cuh -- per-leaf product for several right-hand sides with the
+// far field on the tensor cores (tcgen05), for the FP16 / BF16 forms.
+//
+// For a leaf tau and G <= 16 right-hand sides the far field is
+//   Y[i, (r, a)] = sum_s U[i, s] W[s, (r, a)]
+// over the leaf's U segments s (Section 2: the U factors of every admissible
+// block whose row cluster contains tau, with w = c V^T x of the block).  One
+// tcgen05.mma computes D[m, i] += A[m, k] B[k, i] for M = 128, K = 16 and N =
+// the leaf's rows (rounded up to 16), accumulating in tensor memory:
+//   B = U of 16 segments, straight from the stage (the stream is stored in
+//       8 x 8 core-matrix tiles, an MN-major operand);
+//   A = 128 rows (split, r, a): W scaled by a power of two t_r and split into
+//       hi = fp16(W t_r) (split 0) and lo = fp16(W t_r - hi) (split 1), so
+//       that D[(0, r, a)] + D[(1, r, a)] = t_r (U W) to about 2^-22 relative;
+//       rows of vectors r >= G are zero.  The consumer warps build it in a
+//       K-major core-matrix layout from the staged FP32 w.
+// t_r = 2^floor(log2(2^15 / (wbound x max|x_r|))): wbound bounds |w| / max|x|
+// for the mesh (|v| <= 1 after pivot normalisation, so |V^T x| <= |s| max|x|),
+// which keeps every scaled value inside the FP16 range.
+// One thread issues the MMAs of a stage and commits them to the barriers that
+// release the A buffer and the stage.  The near field stays on the CUDA cores
+// (as in the multi-vector kernel) and is added to the far result at the end of
+// the leaf, in a fixed order.  Every wait is bounded.
+#pragma once
+
+#include <type_traits>
+
+#include "hm_stream.cuh"
+
+namespace hm {
+namespace stream {
+
+constexpr int kTcStage = 12288;  // bytes of stream data per slot
+constexpr int kTcAux = 12288;    // bytes of staged 4-vectors per slot
+constexpr int kTcSlots = 3;
+constexpr int kTcSlotBytes = kTcStage + kTcAux;
+constexpr int kTcK = 48;                   // segments per far stage at most (three K steps)
+constexpr int kTcABytes = 128 * kTcK * 2;  // one A tile
+constexpr int kTcSbo = (kTcK / 8) * 128;   // M-direction core stride of an A tile
+constexpr int kTcMaxG = 16;
+constexpr size_t tc_smem() { return (size_t)kTcSlots * kTcSlotBytes + 2 * (size_t)kTcABytes; }
+static_assert(kConsumers * 8 * 3 * 4 <= kTcSlotBytes, "the near reduction must fit a slot");
+static_assert(64 * 64 * 4 <= kTcSlotBytes, "the far epilogue exchange must fit a slot");
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    // SWIZZLE_NONE shared-memory matrix descriptor: start, leading (K-direction)
+    // and stride (M/N-direction) core-matrix offsets in 16-byte units, version 1
+    return (uint64_t)((saddr >> 4) & 0x3fff) | ((uint64_t)((lbo >> 4) & 0x3fff) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3fff) << 32) | ((uint64_t)1 << 46);
+}
+
+// kind::f16, D FP32, A K-major, B MN-major, M = 128
+__device__ __forceinline__ uint32_t tc_idesc(int n, bool bf16)
+{
+    const uint32_t f = bf16 ? 1u : 0u;
+    return (1u << 4) | (f << 7) | (f << 10) | (0u << 15) | (1u << 16) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 8 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tc_ld8(uint32_t addr, float* v)
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(addr)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+template <class T>
+__device__ __forceinline__ unsigned short tc_bits(float v);
+template <>
+__device__ __forceinline__ unsigned short tc_bits<__half>(float v)
+{
+    return __half_as_ushort(__float2half_rn(v));
+}
+template <>
+__device__ __forceinline__ unsigned short tc_bits<__nv_bfloat16>(float v)
+{
+    return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+template <class T>
+__device__ __forceinline__ float tc_back(unsigned short b);
+template <>
+__device__ __forceinline__ float tc_back<__half>(unsigned short b)
+{
+    return __half2float(__ushort_as_half(b));
+}
+template <>
+__device__ __forceinline__ float tc_back<__nv_bfloat16>(unsigned short b)
+{
+    return __bfloat162float(__ushort_as_bfloat16(b));
+}
+
+// the power-of-two scale of vector r's far-field values on a mesh
+__device__ __forceinline__ float tc_scale(float wbound, const int* xmax, int r)
+{
+    const float xm = __int_as_float(xmax[r]);
+    const float b = wbound * xm;
+    if (!(b > 0.0f) || !isfinite(b)) return 1.0f;
+    return exp2f(floorf(log2f(32768.0f / b)));
+}
+
+template <class TF>
+__global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
+    const int2* __restrict__ work, int nwork, const MeshDev* __restrict__ meshes, int* __restrict__ counter,
+    int* __restrict__ err, const float* __restrict__ xg_base, const float* __restrict__ w_base, int G,
+    const int* __restrict__ xmax, uint32_t tmem_cols, double* __restrict__ y, int64_t ld)
+{
+    using TA = float;
+    using TN = float;
+    constexpr int Rr = 8;  // rows per consumer thread in the near field (as for 16-bit U)
+    constexpr int RC = 2;
+    constexpr bool kBf16 = sizeof(TF) == 2 && !std::is_same<TF, __half>::value;
+    extern __shared__ __align__(128) unsigned char smem[];
+    auto sdata = [&](int q) { return smem + (size_t)q * kTcSlotBytes; };
+    auto saux = [&](int q) { return smem + (size_t)q * kTcSlotBytes + kTcStage; };
+    unsigned char* abuf = smem + (size_t)kTcSlots * kTcSlotBytes;  // two A tiles
+    __shared__ __align__(8) uint64_t full[kTcSlots];
+    __shared__ __align__(8) uint64_t empty[kTcSlots];      // near stages: one arrival per consumer warp
+    __shared__ __align__(8) uint64_t empty_far[kTcSlots];  // far stages: the MMA commit
+    __shared__ __align__(8) uint64_t abar[2];
+    __shared__ __align__(8) uint64_t dbar;
+    __shared__ __align__(8) uint64_t fbar;
+    __shared__ StageMeta meta[kTcSlots];
+    __shared__ uint32_t tmem_slot;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTcSlots; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kConsumers / 32);
+            mbar_init(&empty_far[s], 1);
+        }
+        mbar_init(&abar[0], 1);
+        mbar_init(&abar[1], 1);
+        mbar_init(&dbar, 1);
+        mbar_init(&fbar, 1);
+        mbar_fence_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(&tmem_slot)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        leaf_producer<TF, TN, TA, kTcSlots, kTcStage, kTcAux, 16, kTcK>(work, nwork, meshes, counter, err, xg_base,
+                                                                        w_base, G, smem, full, empty, meta, empty_far);
+        return;
+    }
+
+    // ---------------------------------------------------------------- consumers
+    // warps 1..3 build the A tiles of the far stages and thread 0 of warp 1
+    // issues the MMAs; warps 4..7 go on to the near stages meanwhile and read
+    // the accumulators (TMEM lane quarters 0..3) in the epilogue
+    constexpr int kBuilders = 96;
+    const int ctid = threadIdx.x - 32;
+    const bool builder = ctid < kBuilders;
+    const int NRC = (G + RC - 1) / RC;
+    int cur = -1, cur_mesh = -1, P = 1, H = 0, p = 0, c = 0, h = 0, t0 = 0, mt = 0, mp = 8, mp16 = 16;
+    const int32_t* perm = nullptr;
+    int64_t xoff = 0;
+    TA c1 = 0.f, c2 = 0.f;
+    float wbound = 0.f;
+    int fs = 0;   // far stages seen (A buffer, phase of its barrier)
+    int nfl = 0;  // leaves with a far field finished (phase of dbar)
+    bool far_started = false;
+    TA acc[Rr][RC][3];
+    for (int it = 0;; ++it) {
+        const int slot = it % kTcSlots;
+        if (!mbar_wait(&full[slot], (uint32_t)(it / kTcSlots) & 1u, err, 3, it)) break;
+        const StageMeta m = meta[slot];
+        if (m.kind == 2) break;
+        if (m.leaf != cur || m.pad[0] != cur_mesh) {
+            cur = m.leaf;
+            cur_mesh = m.pad[0];
+            const MeshDev& md = meshes[cur_mesh];
+            t0 = md.leaf[2 * cur];
+            mt = md.leaf[2 * cur + 1];
+            perm = md.perm;
+            xoff = md.xoff;
+            c1 = (TA)md.c1;
+            c2 = (TA)md.c2;
+            wbound = md.wbound;
+            mp = (mt + 7) & ~7;
+            mp16 = (mt + 15) & ~15;
+            P = mp / Rr;
+            H = kConsumers / (P * NRC);
+            p = ctid % P;
+            c = (ctid / P) % NRC;
+            h = ctid / (P * NRC);
+            far_started = false;
+#pragma unroll
+            for (int e = 0; e < Rr; ++e)
+#pragma unroll
+                for (int q = 0; q < RC; ++q) acc[e][q][0] = acc[e][q][1] = acc[e][q][2] = (TA)0;
+        }
+        if (m.kind == 0) {
+            // ---- far stage on the tensor cores
+            const int buf = fs & 1;
+            const bool first_far = !far_started;
+            far_started = true;
+            ++fs;
+            if (!builder) continue;
+            if (fs > 2 && !mbar_wait(&abar[buf], (uint32_t)(((fs - 1) >> 1) - 1) & 1u, err, 4, it)) break;
+            unsigned char* A = abuf + (size_t)buf * kTcABytes;
+            const float* av = reinterpret_cast<const float*>(saux(slot));
+            const int nkb = m.count >> 3;  // core columns of this stage
+            // item (mb, kb, rr): vector r = 2 mb + rr, rows 8 mb + 4 rr + a (hi)
+            // and 64 + 8 mb + 4 rr + a (lo), segments 8 kb .. 8 kb + 7
+            for (int itm = ctid; itm < 16 * nkb; itm += kBuilders) {
+                const int rr = itm & 1, mb = (itm >> 1) & 7, kb = itm >> 4;
+                const int r = 2 * mb + rr;
+                const float t = r < G ? tc_scale(wbound, xmax, r) : 0.0f;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    // one row of the hi core and of the lo core: 8 segments of (r, a)
+                    uint32_t hw[4] = {0u, 0u, 0u, 0u}, lw[4] = {0u, 0u, 0u, 0u};
+                    if (r < G) {
+#pragma unroll
+                        for (int s2 = 0; s2 < 4; ++s2) {
+                            const float v0 = av[((size_t)(kb * 8 + 2 * s2) * G + r) * 4 + a] * t;
+                            const float v1 = av[((size_t)(kb * 8 + 2 * s2 + 1) * G + r) * 4 + a] * t;
+                            const uint32_t h0 = tc_bits<TF>(v0), h1 = tc_bits<TF>(v1);
+                            const uint32_t l0 = tc_bits<TF>(v0 - tc_back<TF>((unsigned short)h0));
+                            const uint32_t l1 = tc_bits<TF>(v1 - tc_back<TF>((unsigned short)h1));
+                            hw[s2] = h0 | (h1 << 16);
+                            lw[s2] = l0 | (l1 << 16);
+                        }
+                    }
+                    *reinterpret_cast<uint4*>(A + (size_t)(mb * (kTcK / 8) + kb) * 128 + (4 * rr + a) * 16) =
+                        make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4*>(A + (size_t)((mb + 8) * (kTcK / 8) + kb) * 128 + (4 * rr + a) * 16) =
+                        make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc_fence_before();
+            asm volatile("bar.sync 2, %0;" ::"n"(kBuilders) : "memory");
+            if (ctid == 0) {
+                tc_fence_after();
+                const uint32_t a0 = smem_addr(A), b0 = smem_addr(sdata(slot));
+                const uint32_t kstride = (uint32_t)(mp >> 3) * 128;  // K-direction core stride of U
+                for (int ks = 0; ks < (m.count >> 4); ++ks) {
+                    for (int n0 = 0; n0 < mp16; n0 += 256) {
+                        const int n = min(256, mp16 - n0);
+                        const uint64_t ad = tc_desc(a0 + (uint32_t)ks * 256, 128, kTcSbo);
+                        const uint64_t bd = tc_desc(b0 + (uint32_t)ks * 2 * kstride + (uint32_t)(n0 >> 3) * 128,
+                                                    kstride, 128);
+                        tc_mma(tmem + (uint32_t)n0, ad, bd, tc_idesc(n, kBf16), (!first_far || ks > 0) ? 1u : 0u);
+                    }
+                }
+                tc_commit(&abar[buf]);
+                tc_commit(&empty_far[slot]);
+                if (m.pad[1]) tc_commit(&dbar);
+            }
+            continue;
+        }
+        // ---- near stage on the CUDA cores (as in the multi-vector kernel)
+        const TA* av = reinterpret_cast<const TA*>(saux(slot)) + (size_t)c * RC * 4;
+        if (h < H) {
+            const TN* sb = reinterpret_cast<const TN*>(sdata(slot)) + p * Rr;
+            const TA c12 = c1 + c2;
+            for (int s = h; s < m.count; s += H) {
+                const TN* e0 = sb + (size_t)s * 6 * mp;
+                TA xs[RC][3];
+#pragma unroll
+                for (int q = 0; q < RC; ++q) {
+                    if (c * RC + q < G) load3(av + ((size_t)s * G + q) * 4, xs[q][0], xs[q][1], xs[q][2]);
+                    else xs[q][0] = xs[q][1] = xs[q][2] = (TA)0;
+                }
+#pragma unroll
+                for (int v = 0; v < 6; ++v) {
+                    const int va = v < 3 ? 0 : (v < 5 ? 1 : 2);
+                    const int vb = v < 3 ? v : (v < 5 ? v - 2 : 2);
+                    TA val[Rr];
+                    smem_rows<TN, TA, Rr>(e0 + v * mp, val);
+#pragma unroll
+                    for (int q = 0; q < RC; ++q) {
+                        if (va == vb) {
+                            const TA f0 = (va == 0 ? c12 : c1) * xs[q][0];
+                            const TA f1 = (va == 1 ? c12 : c1) * xs[q][1];
+                            const TA f2 = (va == 2 ? c12 : c1) * xs[q][2];
+#pragma unroll
+                            for (int e = 0; e < Rr; ++e) {
+                                acc[e][q][0] += f0 * val[e];
+                                acc[e][q][1] += f1 * val[e];
+                                acc[e][q][2] += f2 * val[e];
+                            }
+                        } else {
+                            const TA fa = c2 * xs[q][vb], fb = c2 * xs[q][va];
+#pragma unroll
+                            for (int e = 0; e < Rr; ++e) {
+                                acc[e][q][va] += fa * val[e];
+                                acc[e][q][vb] += fb * val[e];
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (m.last) {
+            named_barrier_consumers();  // everyone is done reading the slot
+            const bool has_far = far_started;
+            if (has_far) {
+                // ---- far epilogue: D (TMEM) -> y, hi + lo rows added, t_r removed
+                if (!mbar_wait(&dbar, (uint32_t)nfl & 1u, err, 5, it)) break;
+                ++nfl;
+                tc_fence_after();
+                float* X = reinterpret_cast<float*>(sdata(slot));  // lo rows [64][64 columns]
+                const int q4 = warp & 3;                          // TMEM lane quarter of this warp
+                const bool reader = warp >= 4;                    // warps 4..7 cover lanes 0..127
+                for (int c0 = 0; c0 < mp16; c0 += 64) {
+                    const int nc = min(64, mp16 - c0);
+                    if (reader && q4 >= 2) {
+                        const int row = 32 * q4 + lane - 64;
+                        for (int cc = 0; cc < nc; cc += 8) {
+                            float v[8];
+                            tc_ld8(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(c0 + cc), v);
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) X[row * 64 + cc + q] = v[q];
+                        }
+                    }
+                    named_barrier_consumers();
+                    if (reader && q4 < 2) {
+                        const int row = 32 * q4 + lane;
+                        const int r = row >> 2, a = row & 3;
+                        const float inv = 1.0f / tc_scale(wbound, xmax, min(r, kTcMaxG - 1));
+                        for (int cc = 0; cc < nc; cc += 8) {
+                            float v[8];
+                            tc_ld8(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(c0 + cc), v);
+                            if (a < 3 && r < G) {
+#pragma unroll
+                                for (int q = 0; q < 8; ++q) {
+                                    const int i = c0 + cc + q;
+                                    if (i < mt)
+                                        y[(size_t)r * ld + xoff + 3 * (size_t)perm[t0 + i] + a] =
+                                            (double)((v[q] + X[row * 64 + cc + q]) * inv);
+                                }
+                            }
+                        }
+                    }
+                    __threadfence_block();
+                    tc_fence_before();
+                    named_barrier_consumers();
+                }
+                tc_fence_after();
+            }
+            // ---- near field: the H partial sums, added to the far result
+            TA* red = reinterpret_cast<TA*>(sdata(slot));
+            constexpr int kPer = Rr * 3;
+#pragma unroll
+            for (int q = 0; q < RC; ++q) {
+                if (h < H) {
+                    TA* rp = red + (size_t)((h * P + p) * NRC + c) * kPer;
+#pragma unroll
+                    for (int e = 0; e < Rr; ++e)
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) rp[e * 3 + a] = acc[e][q][a];
+                }
+                named_barrier_consumers();
+                const int nvec = (G - q + RC - 1) / RC;
+                const int per_row = 3 * nvec;
+                for (int idx = ctid; idx < mt * per_row; idx += kConsumers) {
+                    const int i = idx / per_row, rem = idx - i * per_row;
+                    const int cc = rem / 3, a = rem - 3 * cc;
+                    const int pp = i / Rr, e = i - pp * Rr;
+                    TA sum = (TA)0;
+                    for (int g = 0; g < H; ++g) sum += red[(size_t)((g * P + pp) * NRC + cc) * kPer + e * 3 + a];
+                    const int r = cc * RC + q;
+                    double* yp = y + (size_t)r * ld + xoff + 3 * (size_t)perm[t0 + i] + a;
+                    *yp = has_far ? *yp + (double)sum : (double)sum;
+                }
+                named_barrier_consumers();
+            }
+        }
+        // the slot may be refilled once every consumer warp is done with it
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+    }
+    // ---- drain: no MMA may still run when the tensor memory is released
+    tc_fence_before();
+    named_barrier_consumers();
+    if (ctid == 0 && fs > 0) {
+        tc_fence_after();
+        tc_commit(&fbar);
+        mbar_wait(&fbar, 0u, err, 6, 0);
+    }
+    tc_fence_before();
+    named_barrier_consumers();
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
+}  // namespace stream
+}  // namespace hm

@@ -36,10 +36,14 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cstring>
 #include <cmath>
+
+#include <type_traits>
 
 #include "hm_internal.h"
 #include "hm_stream.cuh"
+#include "hm_leaf_tc.cuh"
 
 namespace hm {
 namespace {
@@ -475,6 +479,44 @@ __global__ void __launch_bounds__(kThreads) fwd_big_multi_kernel(
     fwd_multi_block<TF, TA, RC, kThreads>(rec, fa, G, threadIdx.x, red);
 }
 
+// max |x| of each of the G vectors of a launch (rows of n dofs at stride ld),
+// as the bits of a non-negative float (ordered like the values)
+__global__ void absmax_kernel(const double* __restrict__ x, int64_t ld, int64_t n, int* __restrict__ out)
+{
+    const int r = blockIdx.y;
+    double mx = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        mx = fmax(mx, fabs(x[(size_t)r * ld + i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+        // rounded up to FP32 so that the bound stays a bound
+        float f = (float)mx;
+        if ((double)f < mx) f = nextafterf(f, INFINITY);
+        atomicMax(out + r, __float_as_int(f));
+    }
+}
+
+// max over the factor columns of (column scale of U) x |s| of the column's block
+__global__ void wbound_kernel(const FwdRec* __restrict__ recs, int64_t nrec, const float* __restrict__ SU,
+                              int* __restrict__ out)
+{
+    float mx = 0.0f;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nrec; b += (int64_t)gridDim.x * blockDim.x) {
+        const FwdRec rec = recs[b];
+        float s = 0.0f;
+        for (int c = 0; c < rec.C; ++c) s = fmaxf(s, SU[rec.col0 + c]);
+        mx = fmaxf(mx, s * (float)rec.n);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_int(mx));
+}
+
 // ---------------------------------------------------------------- packing
 template <class T>
 __device__ __forceinline__ T cvt(double v);
@@ -711,6 +753,94 @@ int run_phases(const Plan& P, const double* x, double* y, int G, int64_t ld, TA*
     return HM_OK;
 }
 
+// fewest vectors of a launch that takes the far field to the tensor cores
+constexpr int kTcMinG = 12;
+
+// per-device launch data of the tensor-core leaf kernel
+template <class TF>
+int tc_launch(StreamLaunch& out)
+{
+    constexpr int kMaxDevices = 64;
+    static StreamLaunch cache[kMaxDevices];
+    int dev = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    if (dev < kMaxDevices && cache[dev].nsm > 0) {
+        out = cache[dev];
+        return HM_OK;
+    }
+    auto kern = stream::leaf_tc_kernel<TF>;
+    const size_t smem = stream::tc_smem();
+    HM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    StreamLaunch l;
+    HM_CUDA(cudaDeviceGetAttribute(&l.nsm, cudaDevAttrMultiProcessorCount, dev));
+    HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&l.ctas_per_sm, kern, stream::kThreads, smem));
+    l.ctas_per_sm = std::max(l.ctas_per_sm, 1);
+    if (dev < kMaxDevices) cache[dev] = l;
+    out = l;
+    return HM_OK;
+}
+
+// One launch of each phase for G <= 16 vectors with the tensor-core leaf kernel.
+template <class TF>
+int run_phases_tc(const Plan& P, const double* x, double* y, int G, int64_t ld, float* xg, float* w, int* counter,
+                  int* xmax, cudaStream_t s, const hm_matrix* prof, const Sched& sc)
+{
+    constexpr int RC = multi_rc<TF, float>();
+    if (prof) prof_mark(*prof, 0, s);
+    HM_CUDA(cudaMemsetAsync(xmax, 0, (size_t)G * sizeof(int), s));
+    absmax_kernel<<<dim3(64, (unsigned)G), 256, 0, s>>>(x, ld, 3 * P.npos, xmax);
+    HM_CUDA(cudaGetLastError());
+    if (P.npos > 0) {
+        const int64_t n = P.npos * G;
+        gather_kernel<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P.meshes, P.nmesh, P.pos_prefix, P.npos, x,
+                                                                         ld, xg, G);
+        HM_CUDA(cudaGetLastError());
+    }
+    if (prof) prof_mark(*prof, 1, s);
+    const bool one = P.nmesh == 1;
+    const MeshDev m0 = one ? P.mesh0 : MeshDev{};
+    const bool fork = sc.side && P.nbig > 0 && P.nsmall > 0;
+    if (fork) {
+        HM_CUDA(cudaEventRecord(sc.fork, s));
+        HM_CUDA(cudaStreamWaitEvent(sc.side, sc.fork, 0));
+    }
+    if (P.nbig > 0) {
+        auto kb = one ? fwd_big_multi_kernel<TF, float, true, RC> : fwd_big_multi_kernel<TF, float, false, RC>;
+        kb<<<(unsigned)P.nbig, kThreads, 0, fork ? sc.side : s>>>(P.fwd, m0, P.meshes, xg, w, G);
+        HM_CUDA(cudaGetLastError());
+    }
+    if (P.nsmall > 0) {
+        const unsigned nb = (unsigned)((P.nsmall + kThreads / 32 - 1) / (kThreads / 32));
+        auto ks = one ? fwd_small_multi_kernel<TF, float, true, RC> : fwd_small_multi_kernel<TF, float, false, RC>;
+        ks<<<nb, kThreads, 0, s>>>(P.fwd + P.nbig, P.nsmall, m0, P.meshes, xg, w, G);
+        HM_CUDA(cudaGetLastError());
+    }
+    if (fork) {
+        HM_CUDA(cudaEventRecord(sc.join, sc.side));
+        HM_CUDA(cudaStreamWaitEvent(s, sc.join, 0));
+    }
+    if (prof) prof_mark(*prof, 2, s);
+    if (P.nwork > 0) {
+        StreamLaunch l;
+        int rc = tc_launch<TF>(l);
+        if (rc) return rc;
+        // tensor memory: the leaf's rows (rounded up to 16) as FP32 columns
+        const int mp16 = (std::max(P.max_leaf, 1) + 15) & ~15;
+        uint32_t cols = 32;
+        while ((int)cols < mp16) cols <<= 1;
+        // two CTAs per SM fit by registers and shared memory (a persistent CTA
+        // that does not become resident at once finds the work taken and exits)
+        int per_sm = sc.ctas_per_sm > 0 ? std::min(sc.ctas_per_sm, 2) : 2;
+        per_sm = std::min(per_sm, (int)(512 / cols));  // never wait for another CTA's columns
+        const int64_t ncta = std::min<int64_t>(P.nwork, (int64_t)l.nsm * std::max(per_sm, 1));
+        stream::leaf_tc_kernel<TF><<<(unsigned)ncta, stream::kThreads, stream::tc_smem(), s>>>(
+            P.work, (int)P.nwork, P.meshes, counter, P.err, xg, w, G, xmax, cols, y, ld);
+        HM_CUDA(cudaGetLastError());
+    }
+    if (prof) prof_mark(*prof, 3, s);
+    return HM_OK;
+}
+
 // The product over every mesh of the plan: one vector with the single-vector
 // kernels, several in launches of up to Gmax interleaved vectors each.
 template <class TF, class TN, class TA>
@@ -722,13 +852,29 @@ int run_product_t(const Plan& P, const double* x, double* y, int nrhs, int64_t l
     const int mpmax = std::max((P.max_leaf + 7) & ~7, 8);
     if (mpmax / Rr > stream::kConsumers || 6 * mpmax * (int)sizeof(TN) > stream::kStageBytes)
         return fail(HM_EINVAL, "product: a leaf of %d rows does not fit the streamed kernel", P.max_leaf);
-    if (P.nwork > 0) HM_CUDA(cudaMemsetAsync(P.counters, 0, (size_t)nrhs * sizeof(int), s));
+    if (P.nwork > 0) HM_CUDA(cudaMemsetAsync(P.counters, 0, 64 * sizeof(int), s));
     if (nrhs == 1) return run_phases<TF, TN, TA, 1>(P, x, y, 1, ld, xg, w, P.counters, s, prof, sc);
+    int k = 0, r0 = 0;
+    if constexpr (sizeof(TF) == 2 && std::is_same<TA, float>::value) {
+        // 16-bit factors: launches of 16 vectors (at least kTcMinG) take the
+        // far field to the tensor cores; fewer vectors stay on the CUDA cores,
+        // where the per-stage latency of the tensor-core pipeline does not pay
+        for (; nrhs - r0 >= kTcMinG; r0 += std::min(stream::kTcMaxG, nrhs - r0), ++k) {
+            const int G = std::min(stream::kTcMaxG, nrhs - r0);
+            int rc = run_phases_tc<TF>(P, x + (size_t)r0 * ld, y + (size_t)r0 * ld, G, ld, reinterpret_cast<float*>(xg),
+                                       reinterpret_cast<float*>(w), P.counters + k, P.counters + 64, s,
+                                       k == 0 ? prof : nullptr, sc);
+            if (rc) return rc;
+        }
+        if (r0 == nrhs) return HM_OK;
+        if (nrhs - r0 == 1)
+            return run_phases<TF, TN, TA, 1>(P, x + (size_t)r0 * ld, y + (size_t)r0 * ld, 1, ld, xg, w,
+                                             P.counters + k, s, k == 0 ? prof : nullptr, sc);
+    }
     // every (row block, RHS chunk) pair of the largest leaf needs a consumer
     // thread; at most 32 vectors keep at least 16 segments per slot
     const int Gmax = std::min(32, RC * (stream::kConsumers / (mpmax / Rr)));
-    int k = 0;
-    for (int r0 = 0; r0 < nrhs; r0 += Gmax, ++k) {
+    for (; r0 < nrhs; r0 += Gmax, ++k) {
         const int G = std::min(Gmax, nrhs - r0);
         int rc = run_phases<TF, TN, TA, RC>(P, x + (size_t)r0 * ld, y + (size_t)r0 * ld, G, ld, xg, w,
                                             P.counters + k, s, k == 0 ? prof : nullptr, sc);
@@ -841,6 +987,9 @@ MeshDev mesh_desc(const hm_matrix& H, int32_t form)
     m.max_leaf = H.max_leaf;
     m.c1 = (1.0 + H.nu) * (3.0 - 4.0 * H.nu) / (2.0 * H.E * (1.0 - H.nu));
     m.c2 = (1.0 + H.nu) / (2.0 * H.E * (1.0 - H.nu));
+    // |w| <= max(c1, c2) x column scale x |s| x max|x| (|v| <= 1); rounded up
+    m.wbound = (form == HM_BF16 || form == HM_FP16) ? (float)(std::max(m.c1, m.c2) * (double)H.wbound_su) * 1.0001f
+                                                    : 0.0f;
     return m;
 }
 
@@ -892,7 +1041,7 @@ Scratch make_scratch(const hm_matrix& H, int32_t nrhs, int32_t form, void* base)
     const size_t vec = up((size_t)nrhs * 4 * (size_t)H.M * ta);
     const size_t wb = up((size_t)nrhs * (size_t)std::max<int64_t>(H.w_total, 1) * ta);
     unsigned char* b = static_cast<unsigned char*>(base);
-    return Scratch{b, b + vec, reinterpret_cast<int*>(b + vec + wb), false};
+    return Scratch{b, b + vec, reinterpret_cast<int*>(b + vec + wb), false};  // counters: kCounterInts
 }
 
 size_t matvec_scratch_bytes(const hm_matrix& H, int32_t nrhs, int32_t form)
@@ -900,7 +1049,7 @@ size_t matvec_scratch_bytes(const hm_matrix& H, int32_t nrhs, int32_t form)
     const size_t ta = form == HM_FP64 ? 8 : 4;
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
     return up((size_t)nrhs * 4 * (size_t)H.M * ta) + up((size_t)nrhs * (size_t)std::max<int64_t>(H.w_total, 1) * ta) +
-           up((size_t)nrhs * sizeof(int));
+           up((size_t)kCounterInts * sizeof(int));
 }
 
 // the streaming layouts of one form (and the FP32 near field and the column
@@ -931,6 +1080,23 @@ int pack_device(hm_matrix& H, int32_t form, cudaStream_t s)
                     H.V64.as<double>(), H.SU.as<float>(), H.SV.as<float>());
                 HM_CUDA(cudaGetLastError());
             }
+        }
+        if (H.wbound_su == 0.0f) {
+            DevBuf wb;
+            if ((rc = dalloc(H, wb, 256))) return rc;
+            HM_CUDA(cudaMemsetAsync(wb.p, 0, 4, s));
+            const int64_t nrec = H.n_fwd_big + H.n_fwd_small;
+            if (nrec > 0) {
+                wbound_kernel<<<256, 256, 0, s>>>(H.d_fwd_all.as<FwdRec>(), nrec, H.SU.as<float>(), wb.as<int>());
+                HM_CUDA(cudaGetLastError());
+            }
+            int bits = 0;
+            HM_CUDA(cudaMemcpyAsync(&bits, wb.p, 4, cudaMemcpyDeviceToHost, s));
+            HM_CUDA(cudaStreamSynchronize(s));
+            H.alloc.release(wb.p, wb.bytes);
+            float f;
+            std::memcpy(&f, &bits, 4);
+            H.wbound_su = f;
         }
         // V columns are normalised by their ACA pivot (max |v| = 1), so V is
         // stored without a scale; U carries the magnitudes and gets one scale

@@ -238,36 +238,32 @@ struct LeafCfg {
     static constexpr size_t smem() { return (size_t)kS * kSlotBytes + (size_t)kRedBytes; }
 };
 
-template <class TF, class TN, class TA, int RC>
-__global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
-    const int2* __restrict__ work, int nwork, const MeshDev* __restrict__ meshes, int* __restrict__ counter,
-    int* __restrict__ err, const TA* __restrict__ xg_base, const TA* __restrict__ w_base, int G,
-    double* __restrict__ y, int64_t ld)
+// ---------------------------------------------------------------- producer
+// Warp 0 of a leaf kernel: takes (mesh, leaf) items from the counter and
+// fills the NS slots (stream data + staged 4-vectors) with bulk copies; each
+// slot is handed over through full[slot] and taken back through empty[slot]
+// (whatever count that barrier was initialised with).  kGran: stage
+// granularity of a tiled 16-bit U stream (8 for the single-vector kernel,
+// 16, the tensor-core K step, otherwise).
+// empty_far (optional): far stages are taken back through this second set of
+// barriers instead (the tensor-core kernel releases them by MMA commit).
+template <class TF, class TN, class TA, int NS, int kStage, int kAuxBytes, int kGran, int kFarCap = 1 << 20>
+__device__ __forceinline__ void leaf_producer(const int2* __restrict__ work, int nwork,
+                                              const MeshDev* __restrict__ meshes, int* __restrict__ counter,
+                                              int* __restrict__ err, const TA* __restrict__ xg_base,
+                                              const TA* __restrict__ w_base, int G, unsigned char* smem,
+                                              uint64_t* full, uint64_t* empty, StageMeta* meta,
+                                              uint64_t* empty_far = nullptr)
 {
-    using Cfg = LeafCfg<TF, TA, RC>;
-    constexpr int Rr = Cfg::Rr;
-    constexpr int NS = Cfg::kS;
-    extern __shared__ __align__(128) unsigned char smem[];
-    // slot q: stream data at smem + q * kSlotBytes, its 4-vectors kStageBytes later
-    auto sdata = [&](int q) { return smem + (size_t)q * Cfg::kSlotBytes; };
-    auto saux = [&](int q) { return smem + (size_t)q * Cfg::kSlotBytes + kStageBytes; };
-    TA* red1 = reinterpret_cast<TA*>(smem + (size_t)NS * Cfg::kSlotBytes);  // single-vector kernel only
-    __shared__ __align__(8) uint64_t full[kStages];
-    __shared__ __align__(8) uint64_t empty[kStages];
-    __shared__ StageMeta meta[kStages];
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int vecG = 4 * G;  // TA values per segment / column in the staged vectors
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < NS; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kConsumers / 32);
-        }
-        mbar_fence_init();
-    }
-    __syncthreads();
-
-    if (warp == 0) {
+    // per slot: kind of its last stage and the uses of each release barrier
+    int prev_kind[NS], uses_far[NS], uses_near[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) prev_kind[q] = uses_far[q] = uses_near[q] = 0;
+    constexpr int kSlotBytes = kStage + kAuxBytes;
+    const int lane = threadIdx.x & 31;
+    const int vecG = 4 * G;
+    auto sdata = [&](int q) { return smem + (size_t)q * kSlotBytes; };
+    auto saux = [&](int q) { return smem + (size_t)q * kSlotBytes + kStage; };
         // ------------------------------------------------------------ producer
         int it = 0;
         bool ok = true;
@@ -277,12 +273,23 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
         // the item containing first + count.  vec: the 4-vectors the stream
         // reads (w for the far field, x for the near field), G per index.
         int sreal = 0;  // real segments of the current leaf's U stream
+        // lastfar: the stage ends the leaf's far stream (meta pad[1])
         auto emit = [&](int mesh, int lf, int kind, int first, int count, int last, const void* src,
-                        uint32_t bytes, const int2* items, int ni, int* cur, const TA* vec) -> bool {
+                        uint32_t bytes, const int2* items, int ni, int* cur, const TA* vec, int lastfar) -> bool {
             const int slot = it % NS;
             if (it >= NS) {
-                if (!mbar_wait(&empty[slot], (uint32_t)((it / NS) - 1) & 1u, err, 1, it)) return false;
+                bool got;
+                if (empty_far && prev_kind[slot] == 0)
+                    got = mbar_wait(&empty_far[slot], (uint32_t)(uses_far[slot] - 1) & 1u, err, 1, it);
+                else if (empty_far)
+                    got = mbar_wait(&empty[slot], (uint32_t)(uses_near[slot] - 1) & 1u, err, 1, it);
+                else
+                    got = mbar_wait(&empty[slot], (uint32_t)((it / NS) - 1) & 1u, err, 1, it);
+                if (!got) return false;
             }
+            prev_kind[slot] = kind;
+            if (kind == 0) ++uses_far[slot];
+            else ++uses_near[slot];
             if (lane == 0) {
                 StageMeta m;
                 m.leaf = lf;
@@ -291,6 +298,7 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
                 m.count = count;
                 m.last = last;
                 m.pad[0] = mesh;
+                m.pad[1] = lastfar;
                 meta[slot] = m;
                 if (kind < 2)
                     mbar_arrive_expect_tx(&full[slot], bytes + (uint32_t)(count * vecG * sizeof(TA)));
@@ -340,7 +348,7 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
             ++it;
             return true;
         };
-        const int perV = min(kMaxSeg, Cfg::kAuxBytes / (vecG * (int)sizeof(TA)));
+        const int perV = min(kMaxSeg, kAuxBytes / (vecG * (int)sizeof(TA)));
         for (;;) {
             int idx = 0;
             if (lane == 0) idx = atomicAdd(counter, 1);
@@ -358,7 +366,6 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
             // to 16, the tensor-core K step); the single-vector kernel takes
             // stages in whole tiles, the multi-vector one in K steps
             constexpr bool kTiled = sizeof(TF) == 2;
-            constexpr int kGran = RC == 1 ? 8 : 16;
             const int S = kTiled ? (sreal + kGran - 1) & ~(kGran - 1) : sreal;
             const int Sn = md.ln_items[ni1 - 1].col_start;
             const TF* Ul = static_cast<const TF*>(md.Ul);
@@ -366,9 +373,9 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
             const TA* wvec = w_base + (size_t)md.woff * vecG;
             const TA* xvec = xg_base + (size_t)md.xgoff * vecG;
             const int segB = mp * (int)sizeof(TF);
-            const int perF = kTiled ? min(kStageBytes / segB, perV) & ~(kGran - 1) : min(kStageBytes / segB, perV);
+            const int perF = kTiled ? min(min(kStage / segB, perV), kFarCap) & ~(kGran - 1) : min(kStage / segB, perV);
             const int colB = 6 * mp * (int)sizeof(TN);
-            const int perN = min(kStageBytes / colB, perV);
+            const int perN = min(kStage / colB, perV);
             if (perF < 1 || perN < 1) {
                 // a segment or a near column larger than a stage (the host
                 // rejects such leaves before the launch): stop producing
@@ -382,17 +389,17 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
                 const int cnt = min(perF, S - g);
                 const TF* src = Ul + md.lf_base[lf] + (size_t)g * mp;
                 ok = emit(wk.x, lf, 0, g, cnt, (g + cnt == S && Sn == 0) ? 1 : 0, src, (uint32_t)(cnt * segB),
-                          fitems, fi1 - fi0, &cur, wvec);
+                          fitems, fi1 - fi0, &cur, wvec, g + cnt == S ? 1 : 0);
             }
             cur = 0;
             for (int g = 0; g < Sn && ok; g += perN) {
                 const int cnt = min(perN, Sn - g);
                 const TN* src = Nl + md.ln_base[lf] + (size_t)g * 6 * mp;
                 ok = emit(wk.x, lf, 1, g, cnt, (g + cnt == Sn) ? 1 : 0, src, (uint32_t)(cnt * colB), nitems,
-                          ni1 - ni0, &cur, xvec);
+                          ni1 - ni0, &cur, xvec, 0);
             }
         }
-        if (ok) ok = emit(0, -1, 2, 0, 0, 0, nullptr, 0, nullptr, 0, nullptr, nullptr);
+        if (ok) ok = emit(0, -1, 2, 0, 0, 0, nullptr, 0, nullptr, 0, nullptr, nullptr, 0);
         if (!ok) {
             // drain this CTA's own copies in flight before returning (bounded)
             for (int k = 1; k <= NS && k <= it; ++k) {
@@ -400,6 +407,39 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
                 mbar_wait(&full[j % NS], (uint32_t)(j / NS) & 1u, err, 2, j);
             }
         }
+}
+
+template <class TF, class TN, class TA, int RC>
+__global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
+    const int2* __restrict__ work, int nwork, const MeshDev* __restrict__ meshes, int* __restrict__ counter,
+    int* __restrict__ err, const TA* __restrict__ xg_base, const TA* __restrict__ w_base, int G,
+    double* __restrict__ y, int64_t ld)
+{
+    using Cfg = LeafCfg<TF, TA, RC>;
+    constexpr int Rr = Cfg::Rr;
+    constexpr int NS = Cfg::kS;
+    extern __shared__ __align__(128) unsigned char smem[];
+    // slot q: stream data at smem + q * kSlotBytes, its 4-vectors kStageBytes later
+    auto sdata = [&](int q) { return smem + (size_t)q * Cfg::kSlotBytes; };
+    auto saux = [&](int q) { return smem + (size_t)q * Cfg::kSlotBytes + kStageBytes; };
+    TA* red1 = reinterpret_cast<TA*>(smem + (size_t)NS * Cfg::kSlotBytes);  // single-vector kernel only
+    __shared__ __align__(8) uint64_t full[kStages];
+    __shared__ __align__(8) uint64_t empty[kStages];
+    __shared__ StageMeta meta[kStages];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kConsumers / 32);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    if (warp == 0) {
+        leaf_producer<TF, TN, TA, NS, kStageBytes, Cfg::kAuxBytes, RC == 1 ? 8 : 16>(
+            work, nwork, meshes, counter, err, xg_base, w_base, G, smem, full, empty, meta);
         return;
     }
 
