@@ -405,7 +405,7 @@ def bench_batch(args):
     R = 16
     B = binding.Batch(mats, "fp16", max_rhs=R)
     out = {"workload": "64 ellipsoids, 2k-40k triangles (log-uniform), leaf 32, eta 0.8, eps 1e-4",
-           "meshes": len(mats), "triangles": tri, "dofs": B.ndof, "admissible_blocks": B.nblocks,
+           "meshes": len(mats), "triangles": tri, "dofs": B.ndof, "forward_groups": B.ngroups,
            "leaves": B.nleaves, "assemble_s": round(t_asm, 2), "resident_gb": round(resident / 1e9, 2)}
     bytes_prod = sum(m.stats().bytes_form[3] for m in mats)
     stream = torch.cuda.current_stream()

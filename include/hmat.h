@@ -205,7 +205,8 @@ int hm_matvec_host(const hm_matrix* H, const double* x_host, double* y_host, int
  * Vector layout: member m's dofs (3 M_m, dof 3i + a in its own original
  * order) sit at offsets dof_offsets[m] .. dof_offsets[m+1] of each row of x
  * and y; hm_batch_layout returns the nmat + 1 offsets and sizes[0..3] =
- * members, total dofs, admissible blocks, leaves.
+ * members, total dofs, forward groups (admissible blocks sharing a column
+ * cluster), leaves.
  * Result: member m's part of y is bitwise equal to hm_matvec(mats[m], ...)
  * on its part of x, under every schedule.
  * Allocates its workspace through the first member's allocator.

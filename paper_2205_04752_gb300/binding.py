@@ -454,7 +454,7 @@ class Batch:
         _check(lib.hm_batch_layout(self._h, _ptr(off), _ptr(sz)))
         self.offsets = off
         self.ndof = int(sz[1])
-        self.nblocks, self.nleaves = int(sz[2]), int(sz[3])
+        self.ngroups, self.nleaves = int(sz[2]), int(sz[3])
 
     def __del__(self):
         h = getattr(self, "_h", None)

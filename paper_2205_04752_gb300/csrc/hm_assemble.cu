@@ -1131,25 +1131,51 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
         if ((rc = upload(H, H.d_ln_src, ln_src.data(), ln_src.size() * sizeof(NearSrc)))) return rc;
     }
     {
-        // forward-pass records: blocks with |s| <= 128 (one warp each) and
-        // larger ones (one CTA each), each list with the most data first
-        std::vector<int32_t> ord((size_t)H.nadm);
-        std::iota(ord.begin(), ord.end(), 0);
-        std::vector<int64_t> work((size_t)H.nadm, 0);
-        for (int64_t b = 0; b < H.nadm; ++b)
-            for (int k = 0; k < 7; ++k)
-                work[(size_t)b] += (int64_t)H.rank_h[(size_t)(b * 7 + k)] * H.adm_h[(size_t)b].n;
-        std::stable_sort(ord.begin(), ord.end(),
-                         [&](int32_t a, int32_t b) { return work[(size_t)a] > work[(size_t)b]; });
-        // stream order: blocks with |s| > 128 first, then the others, each
-        // with the most data first; the row-major V arena follows this order
-        std::vector<int32_t> big_ids, small_ids;
-        for (int32_t b : ord) (H.adm_h[(size_t)b].n <= 128 ? small_ids : big_ids).push_back(b);
-        std::vector<int64_t> vb_base((size_t)H.nadm + 1, 0);
+        // forward-pass groups: the admissible blocks that share a column
+        // cluster s (at most kMaxGroupRecs each) store their row-major V side
+        // by side, one |s| x Cs matrix per group (block b's Cp_b = sum of its
+        // ranks rounded up to 8 columns at column offset coff_b), so that the
+        // forward pass reads x(s) once per group; groups with the most data
+        // first
+        std::vector<std::vector<int32_t>> by_col(tr.nodes.size());
+        for (int64_t b = 0; b < H.nadm; ++b) {
+            int32_t Csum = 0;
+            for (int k = 0; k < 7; ++k) Csum += H.rank_h[(size_t)(b * 7 + k)];
+            if (Csum > 0) by_col[(size_t)tr.adm[(size_t)b][1]].push_back((int32_t)b);
+        }
+        struct G0 {
+            int64_t work;
+            std::vector<int32_t> blocks;
+        };
+        std::vector<G0> gl;
+        for (size_t nd = 0; nd < tr.nodes.size(); ++nd) {
+            const auto& L = by_col[nd];
+            for (size_t i0 = 0; i0 < L.size(); i0 += kMaxGroupRecs) {
+                G0 g;
+                g.blocks.assign(L.begin() + (int64_t)i0, L.begin() + (int64_t)std::min(L.size(), i0 + kMaxGroupRecs));
+                g.work = 0;
+                for (int32_t b : g.blocks)
+                    for (int k = 0; k < 7; ++k)
+                        g.work += (int64_t)H.rank_h[(size_t)(b * 7 + k)] * H.adm_h[(size_t)b].n;
+                gl.push_back(std::move(g));
+            }
+        }
+        std::stable_sort(gl.begin(), gl.end(), [](const G0& a, const G0& b) { return a.work > b.work; });
+        std::vector<int64_t> vb_base((size_t)H.nadm + 1, 0), vb_ld((size_t)H.nadm + 1, 0);
         std::vector<FwdRec> recs;
+        std::vector<FwdGroup> groups;
         int64_t vr = 0;
-        for (const auto* lst : {&big_ids, &small_ids})
-            for (int32_t b : *lst) {
+        for (const G0& g0 : gl) {
+            FwdGroup g{};
+            const Blk& b0 = H.adm_h[(size_t)g0.blocks[0]];
+            g.vbase = vr;
+            g.s0 = b0.s0;
+            g.n = b0.n;
+            g.first = (int32_t)recs.size();
+            g.nrec = (int16_t)g0.blocks.size();
+            g.mesh = 0;
+            int64_t cs = 0;
+            for (int32_t b : g0.blocks) {
                 FwdRec r{};
                 const Blk& bk = H.adm_h[(size_t)b];
                 r.s0 = bk.s0;
@@ -1164,24 +1190,70 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
                     Csum += kk;
                 }
                 r.C = (int16_t)Csum;
-                vb_base[(size_t)b] = vr;
-                r.vbase = vr;
-                vr += (int64_t)bk.n * ((r.C + 7) & ~int64_t(7));
-                if (r.C == 0) continue;
-                (bk.n <= 128 ? H.n_fwd_small : H.n_fwd_big) += 1;
+                r.coff = (int32_t)cs;  // column offset in the group
+                r.grp = (int32_t)groups.size();
+                vb_base[(size_t)b] = vr + cs;
+                cs += (Csum + 7) & ~7;
                 recs.push_back(r);
             }
+            if (cs > INT32_MAX / 8) return fail(HM_EINVAL, "forward group too wide");
+            g.Cs = (int32_t)cs;
+            for (int32_t b : g0.blocks) vb_ld[(size_t)b] = cs;
+            vr += (int64_t)g.n * cs;
+            groups.push_back(g);
+        }
         vb_base[(size_t)H.nadm] = vr;
         H.vr_total = vr;
+        // units: one CTA per kFwdUnitRows rows of a group, the most data first
+        std::vector<FwdUnit> units;
+        std::vector<FwdMulti> multi;
+        int64_t zc = 0;
+        for (size_t gi = 0; gi < groups.size(); ++gi) {
+            const FwdGroup& g = groups[gi];
+            const int32_t nch = (g.n + kFwdUnitRows - 1) / kFwdUnitRows;
+            const int64_t z0 = nch > 1 ? zc : -1;
+            if (nch > 1) {
+                multi.push_back(FwdMulti{(int32_t)gi, nch, zc});
+                zc += (int64_t)nch * g.Cs;
+            }
+            for (int32_t k = 0; k < nch; ++k)
+                units.push_back(FwdUnit{(int32_t)gi, k * kFwdUnitRows, std::min(kFwdUnitRows, g.n - k * kFwdUnitRows), k, z0});
+        }
+        std::stable_sort(units.begin(), units.end(), [&](const FwdUnit& a, const FwdUnit& b) {
+            return (int64_t)a.nrows * groups[(size_t)a.group].Cs > (int64_t)b.nrows * groups[(size_t)b.group].Cs;
+        });
+        H.zcols = zc;
+        H.unit_h = units;
+        H.multi_h = multi;
         H.fwd_h = recs;
+        H.grp_h = groups;
+        // per-block lists for the several-vector forward kernels
+        std::vector<int32_t> bigv, smallv;
+        {
+            std::vector<int32_t> ord(recs.size());
+            std::iota(ord.begin(), ord.end(), 0);
+            std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) {
+                return (int64_t)recs[(size_t)a].n * recs[(size_t)a].C > (int64_t)recs[(size_t)b].n * recs[(size_t)b].C;
+            });
+            for (int32_t q : ord) (recs[(size_t)q].n > 128 ? bigv : smallv).push_back(q);
+        }
+        H.big_h = bigv;
+        H.small_h = smallv;
+        if ((rc = upload(H, H.d_big, bigv.data(), bigv.size() * 4))) return rc;
+        if ((rc = upload(H, H.d_small, smallv.data(), smallv.size() * 4))) return rc;
+        if ((rc = upload(H, H.d_units, units.data(), units.size() * sizeof(FwdUnit)))) return rc;
+        if ((rc = upload(H, H.d_multi, multi.data(), multi.size() * sizeof(FwdMulti)))) return rc;
         if ((rc = upload(H, H.d_fwd_all, recs.data(), recs.size() * sizeof(FwdRec)))) return rc;
+        if ((rc = upload(H, H.d_groups, groups.data(), groups.size() * sizeof(FwdGroup)))) return rc;
         if ((rc = upload(H, H.d_vb_base, vb_base.data(), vb_base.size() * 8))) return rc;
+        if ((rc = upload(H, H.d_vb_ld, vb_ld.data(), vb_ld.size() * 8))) return rc;
         if (H.c_total > INT32_MAX / 4) return fail(HM_EINVAL, "too many factor columns");
     }
     // ---- workspace for the product
     H.max_rhs = H.prm.max_rhs;
     if ((rc = dalloc(H, H.xg, (size_t)H.max_rhs * 4 * M * 8))) return rc;
     if ((rc = dalloc(H, H.wb, (size_t)H.max_rhs * std::max<int64_t>(H.w_total, 1) * 8))) return rc;
+    if ((rc = dalloc(H, H.zb, (size_t)H.max_rhs * std::max<int64_t>(H.zcols, 1) * 4 * 8))) return rc;
     if ((rc = dalloc(H, H.d_counters, (size_t)kCounterInts * sizeof(int)))) return rc;
     if ((rc = dalloc(H, H.d_err, 64))) return rc;
     HM_CUDA(cudaMemsetAsync(H.d_err.p, 0, 64, s));

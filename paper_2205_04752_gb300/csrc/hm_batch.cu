@@ -23,13 +23,14 @@
 struct hm_batch {
     std::vector<const hm_matrix*> mats;
     int32_t form = 0, max_rhs = 0;
-    int64_t npos = 0, w_total = 0, nbig = 0, nsmall = 0, nwork = 0;
+    int64_t npos = 0, w_total = 0, ngroups = 0, nunits = 0, nmulti = 0, zcols = 0, nwork = 0, nbig = 0, nsmall = 0;
     int32_t max_leaf = 0;
     int ctas_max = 1;  // CTAs per SM of the streamed kernel that fit
     std::vector<int64_t> pos_prefix;  // nmat + 1 cluster positions
     std::vector<hm::MeshDev> mesh_h;
     hm::Allocator alloc;
-    hm::DevBuf d_mesh, d_pos_prefix, d_fwd, d_work[2], xg, w, counters, err;
+    hm::DevBuf d_mesh, d_pos_prefix, d_fwd, d_groups, d_units, d_multi, d_big, d_small, d_work[2], xg, w, z, counters,
+        err;
     hm_schedule sched{};
     cudaStream_t side = nullptr, cap = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
@@ -66,7 +67,9 @@ void batch_free(hm_batch* B)
 {
     if (!B) return;
     if (B->gexec) cudaGraphExecDestroy(B->gexec);
-    for (DevBuf* b : {&B->d_mesh, &B->d_pos_prefix, &B->d_fwd, &B->d_work[0], &B->d_work[1], &B->xg, &B->w,
+    for (DevBuf* b : {&B->d_mesh, &B->d_pos_prefix, &B->d_fwd, &B->d_groups, &B->d_units, &B->d_multi, &B->d_big,
+                      &B->d_small, &B->d_work[0],
+                      &B->d_work[1], &B->xg, &B->w, &B->z,
                       &B->counters, &B->err})
         if (b->p) B->alloc.release(b->p, b->bytes);
     if (B->side) cudaStreamDestroy(B->side);
@@ -85,7 +88,16 @@ Plan make_plan(const hm_batch& B)
     P.pos_prefix = B.d_pos_prefix.as<int64_t>();
     P.npos = B.npos;
     P.fwd = B.d_fwd.as<FwdRec>();
+    P.groups = B.d_groups.as<FwdGroup>();
+    P.units = B.d_units.as<FwdUnit>();
+    P.nunits = B.nunits;
+    P.multi = B.d_multi.as<FwdMulti>();
+    P.nmulti = B.nmulti;
+    P.zcols = B.zcols;
+    P.z = B.z.p;
+    P.big = B.d_big.as<int32_t>();
     P.nbig = B.nbig;
+    P.small = B.d_small.as<int32_t>();
     P.nsmall = B.nsmall;
     P.work = B.d_work[B.sched.work_order ? 1 : 0].as<int2>();
     P.nwork = B.nwork;
@@ -183,22 +195,56 @@ int hm_batch_create(const hm_matrix* const* mats, int32_t nmat, int32_t form, in
         B->mesh_h.push_back(d);
     }
 
-    // forward records: the large blocks of every member, then the small ones
-    // (a block's class is its own matrix's, so its arithmetic is unchanged)
+    // forward groups, units and tall groups of every member (indices shifted
+    // into the concatenated lists; a block's group and its arithmetic are its
+    // own matrix's), the units with the most data first across members
     std::vector<FwdRec> fwd;
-    for (int pass = 0; pass < 2; ++pass)
-        for (int32_t m = 0; m < nmat; ++m) {
-            const hm_matrix& H = *mats[m];
-            const int64_t a = pass == 0 ? 0 : H.n_fwd_big;
-            const int64_t b = pass == 0 ? H.n_fwd_big : H.n_fwd_big + H.n_fwd_small;
-            for (int64_t q = a; q < b; ++q) {
-                FwdRec r = H.fwd_h[(size_t)q];
-                r.mesh = (uint16_t)m;
-                fwd.push_back(r);
-            }
-            if (pass == 0) B->nbig += b - a;
-            else B->nsmall += b - a;
+    std::vector<FwdGroup> groups;
+    std::vector<FwdUnit> units;
+    std::vector<FwdMulti> multi;
+    std::vector<int32_t> bigv, smallv;
+    int64_t zc = 0;
+    for (int32_t m = 0; m < nmat; ++m) {
+        const hm_matrix& H = *mats[m];
+        const int32_t rbase = (int32_t)fwd.size(), gbase = (int32_t)groups.size();
+        for (FwdRec r : H.fwd_h) {
+            r.mesh = (uint16_t)m;
+            r.grp += gbase;
+            fwd.push_back(r);
         }
+        for (int32_t q : H.big_h) bigv.push_back(q + rbase);
+        for (int32_t q : H.small_h) smallv.push_back(q + rbase);
+        for (FwdGroup g : H.grp_h) {
+            g.first += rbase;
+            g.mesh = (uint16_t)m;
+            groups.push_back(g);
+        }
+        for (FwdUnit u : H.unit_h) {
+            u.group += gbase;
+            if (u.zcol0 >= 0) u.zcol0 += zc;
+            units.push_back(u);
+        }
+        for (FwdMulti mu : H.multi_h) {
+            mu.group += gbase;
+            mu.zcol0 += zc;
+            multi.push_back(mu);
+        }
+        zc += H.zcols;
+    }
+    std::stable_sort(units.begin(), units.end(), [&](const FwdUnit& a, const FwdUnit& b) {
+        return (int64_t)a.nrows * groups[(size_t)a.group].Cs > (int64_t)b.nrows * groups[(size_t)b.group].Cs;
+    });
+    auto by_work = [&](int32_t a, int32_t b) {
+        return (int64_t)fwd[(size_t)a].n * fwd[(size_t)a].C > (int64_t)fwd[(size_t)b].n * fwd[(size_t)b].C;
+    };
+    std::stable_sort(bigv.begin(), bigv.end(), by_work);
+    std::stable_sort(smallv.begin(), smallv.end(), by_work);
+    B->nbig = (int64_t)bigv.size();
+    B->nsmall = (int64_t)smallv.size();
+    B->ngroups = (int64_t)groups.size();
+    B->nunits = (int64_t)units.size();
+    B->nmulti = (int64_t)multi.size();
+    B->zcols = zc;
 
     // work lists: 0 = every (mesh, leaf) by decreasing streamed elements (a
     // longest-processing-time order over the whole batch); 1 = member by
@@ -228,6 +274,12 @@ int hm_batch_create(const hm_matrix* const* mats, int32_t nmat, int32_t form, in
     if ((rc = bupload(*B, B->d_mesh, B->mesh_h.data(), B->mesh_h.size() * sizeof(MeshDev))) ||
         (rc = bupload(*B, B->d_pos_prefix, B->pos_prefix.data(), B->pos_prefix.size() * 8)) ||
         (rc = bupload(*B, B->d_fwd, fwd.data(), fwd.size() * sizeof(FwdRec))) ||
+        (rc = bupload(*B, B->d_groups, groups.data(), groups.size() * sizeof(FwdGroup))) ||
+        (rc = bupload(*B, B->d_units, units.data(), units.size() * sizeof(FwdUnit))) ||
+        (rc = bupload(*B, B->d_multi, multi.data(), multi.size() * sizeof(FwdMulti))) ||
+        (rc = bupload(*B, B->d_big, bigv.data(), bigv.size() * 4)) ||
+        (rc = bupload(*B, B->d_small, smallv.data(), smallv.size() * 4)) ||
+        (rc = balloc(*B, B->z, (size_t)max_rhs * (size_t)std::max<int64_t>(B->zcols, 1) * 4 * ta)) ||
         (rc = bupload(*B, B->d_work[0], w0.data(), w0.size() * sizeof(int2))) ||
         (rc = bupload(*B, B->d_work[1], w1.data(), w1.size() * sizeof(int2))) ||
         (rc = balloc(*B, B->xg, (size_t)max_rhs * 4 * (size_t)B->npos * ta)) ||
@@ -259,7 +311,7 @@ int hm_batch_layout(const hm_batch* B, int64_t* dof_offsets, int64_t* sizes)
     if (sizes) {
         sizes[0] = (int64_t)B->mats.size();
         sizes[1] = 3 * B->npos;
-        sizes[2] = B->nbig + B->nsmall;
+        sizes[2] = B->ngroups;
         sizes[3] = B->nwork;
     }
     return HM_OK;

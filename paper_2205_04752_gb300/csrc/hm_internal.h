@@ -93,15 +93,40 @@ struct NearSrc {
     int32_t n, pad;
 };
 // one admissible block of the far-field forward pass (32 bytes): column
-// cluster start and size, first factor column, total rank, mesh, offset of its
-// row-major V, and the rank of each of the seven kernels
+// cluster start and size, first factor column, total rank, mesh, column offset
+// of its V inside its group's row-major matrix, the group, and the rank of
+// each of the seven kernels
 struct FwdRec {
     int32_t s0, n, col0;
     int16_t C;
     uint16_t mesh;
-    int64_t vbase;
+    int32_t coff, grp;
     uint64_t kpack;  // rank of kernel q in bits 8q .. 8q+7
 };
+// the blocks that share a column cluster: V of all of them as one row-major
+// n x Cs matrix at element offset vbase; records first .. first + nrec - 1
+struct FwdGroup {
+    int64_t vbase;
+    int32_t s0, n, Cs, first;
+    int16_t nrec;
+    uint16_t mesh;
+    int32_t pad;
+};
+constexpr int kMaxGroupRecs = 64;
+// a CTA's share of a forward group: rows j0 .. j0 + nrows of group `group`;
+// a group taller than kFwdUnitRows has several units whose partial sums go
+// to the z workspace (column zcol0 + chunk * Cs of the group's slice) and are
+// added by a second pass in chunk order; zcol0 < 0 for a one-unit group
+struct FwdUnit {
+    int32_t group, j0, nrows, chunk;
+    int64_t zcol0;
+};
+// the groups with several units: group, units, first z column
+struct FwdMulti {
+    int32_t group, nchunk;
+    int64_t zcol0;
+};
+constexpr int kFwdUnitRows = 256;
 
 // Device-side description of one mesh taking part in a product (a single
 // matrix is a product over one mesh; a batch concatenates several).  Stream
@@ -136,13 +161,23 @@ struct Plan {
     int32_t nmesh;
     const int64_t* pos_prefix;  // nmesh + 1: cluster positions before each mesh
     int64_t npos;
-    const FwdRec* fwd;          // nbig blocks with |s| > 128, then nsmall others
-    int64_t nbig, nsmall;
+    const FwdRec* fwd;          // the block records of every group
+    const FwdGroup* groups;     // forward groups (records indexed over all meshes)
+    const FwdUnit* units;       // nunits CTAs of the forward pass
+    int64_t nunits;
+    const FwdMulti* multi;      // nmulti groups added by the second pass
+    int64_t nmulti;
+    const int32_t* big;         // records of the blocks with |s| > 128 (several vectors: CTA per block)
+    int64_t nbig;
+    const int32_t* small;       // the other records (several vectors: warp per block)
+    int64_t nsmall;
+    int64_t zcols;              // z workspace columns (4-vectors per vector)
     const int2* work;           // (mesh, leaf) in processing order
     int64_t nwork;
     int32_t max_leaf;
     int* counters;              // kCounterInts ints of device memory (work counters, max|x| per vector)
     int* err;
+    void* z;                    // forward partial sums: nrhs x zcols 4-vectors
 };
 // device ints of the counter region of a product: one work counter per
 // launch (at most 64) and the max|x| words of a launch at offset 64
@@ -179,9 +214,18 @@ struct hm_matrix {
     hm::DevBuf d_leaf;   // int32 2*nleaves (t0, m)
     hm::DevBuf d_lf_base, d_lf_ptr, d_lf_items, d_lf_src;  // far stream per leaf
     hm::DevBuf d_ln_base, d_ln_ptr, d_ln_items, d_ln_src;  // near stream per leaf
-    hm::DevBuf d_vb_base;                 // int64 nadm+1: row-major V of each block
-    hm::DevBuf d_fwd_all;                // FwdRec in stream order: |s| > 128 first, then the rest
-    std::vector<hm::FwdRec> fwd_h;       // host copy of d_fwd_all
+    hm::DevBuf d_vb_base;                 // int64 nadm+1: V of each block (first row) in its group
+    hm::DevBuf d_vb_ld;                   // int64 nadm+1: row stride of that V (its group's Cs)
+    hm::DevBuf d_fwd_all;                // FwdRec of every block, group by group
+    hm::DevBuf d_groups;                 // FwdGroup
+    hm::DevBuf d_units, d_multi;         // FwdUnit (the most data first), FwdMulti
+    hm::DevBuf d_big, d_small;           // record indices by block height, the most data first
+    std::vector<int32_t> big_h, small_h;
+    std::vector<hm::FwdUnit> unit_h;
+    std::vector<hm::FwdMulti> multi_h;
+    int64_t zcols = 0;
+    std::vector<hm::FwdRec> fwd_h;       // host copies
+    std::vector<hm::FwdGroup> grp_h;
 
     hm::DevBuf d_work;                   // int2 (0, leaf): leaves by decreasing streamed bytes
     std::vector<int32_t> leaf_order_h;   // host copy of the order
@@ -190,7 +234,6 @@ struct hm_matrix {
     hm::DevBuf d_mesh[4];                // MeshDev of this matrix, per packed form
     hm::DevBuf d_counters;               // int32 2*max_rhs: work counters of the streamed kernel
     hm::DevBuf d_err;                    // int32: set by a device wait that ran out
-    int64_t n_fwd_small = 0, n_fwd_big = 0;
     int64_t ul_total = 0, nl_total = 0, vr_total = 0;
 
     // FP64 factor and near arenas in block order (ACA output, export)
@@ -207,6 +250,7 @@ struct hm_matrix {
     int32_t max_rhs = 32;
     hm::DevBuf xg;  // max_rhs x M x 4 doubles (gathered x, cluster order, padded 4-vectors)
     hm::DevBuf wb;  // max_rhs x w_total doubles (one 4-vector per factor column)
+    hm::DevBuf zb;  // max_rhs x zcols x 4 doubles (forward partial sums of the tall groups)
     hm::DevBuf xh, yh;  // device staging for hm_matvec_host (max_rhs x 3M doubles)
 
     // measurement hook (hm_profile_enable / hm_profile_read)
@@ -216,14 +260,15 @@ struct hm_matrix {
 };
 
 namespace hm {
-// workspace of one product: gathered x (nrhs x M x 4) and the far-field w
-// vectors (nrhs x c_total x 4), in the form's accumulation type, and nrhs
-// work counters of the streamed leaf kernel
+// workspace of one product: gathered x (nrhs x M x 4), the far-field w
+// vectors (nrhs x c_total x 4) and the forward partial sums (nrhs x zcols x
+// 4), in the form's accumulation type, and the counters of the launches
 struct Scratch {
     void* xg;
     void* w;
     int* counters;
     bool profile;  // record the measurement-hook events
+    void* z = nullptr;
 };
 int matvec_device_scratch(const hm_matrix& H, const double* x, double* y, int32_t nrhs,
                           int64_t ld, int32_t form, cudaStream_t s, const Scratch& scr);

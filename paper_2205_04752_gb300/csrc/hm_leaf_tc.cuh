@@ -174,8 +174,8 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
     const uint32_t tmem = tmem_slot;
 
     if (warp == 0) {
-        leaf_producer<TF, TN, TA, kTcSlots, kTcStage, kTcAux, 16, kTcK>(work, nwork, meshes, counter, err, xg_base,
-                                                                        w_base, G, smem, full, empty, meta, empty_far);
+        leaf_producer<TF, TN, TA, kTcSlots, kTcStage, kTcAux, 16, kTcK, true>(
+            work, nwork, meshes, counter, err, xg_base, w_base, G, smem, full, empty, meta, empty_far);
         return;
     }
 

@@ -48,7 +48,7 @@
 namespace hm {
 namespace {
 
-constexpr int kThreads = 128;
+
 
 // ---------------------------------------------------------------- 16-byte loads
 // load N = 16 / sizeof(T) consecutive values (16-byte aligned, streaming) as TA
@@ -213,21 +213,187 @@ __device__ __forceinline__ void write_w(const FwdRec& rec, int c, TA z0, TA z1, 
     d[3] = (TA)0;
 }
 
+// ---------------------------------------------------------------- forward groups
+// z = V^T x for every admissible block, a group of blocks that share the
+// column cluster s at a time (their V side by side, one n x Cs row-major
+// matrix), so that x(s) is read once per group.  One CTA per group.  The work
+// is the pairs (column vector q = VEC consecutive columns, RHS chunk c of RC
+// vectors); the T threads split the rows into GG groups and take the pairs in
+// rounds of PR = T / GG (GG = T / pairs when the pairs are fewer than the
+// threads).  x(s) is staged in shared memory kFwdRows rows at a time; V is
+// read once, 16 bytes per row and column vector.  The GG partial sums are
+// added in a fixed order through shared memory, then w is written for every
+// column (c1 / c2 and the U column scale folded in).  Deterministic.
+constexpr int kFwdThreads = 128;
+constexpr int kFwdXsBytes = 8192;
+
+template <class TF, class TA, int RC, bool ONE>
+__global__ void __launch_bounds__(kFwdThreads) fwd_group_kernel(
+    const FwdUnit* __restrict__ units, const FwdGroup* __restrict__ groups, const FwdRec* __restrict__ recs,
+    const __grid_constant__ MeshDev m0, const MeshDev* __restrict__ meshes, const TA* __restrict__ xg,
+    TA* __restrict__ w, TA* __restrict__ z, int G)
+{
+    constexpr int VEC = Vec16<TF, TA>::N;
+    constexpr int T = kFwdThreads;
+    constexpr int kPer = VEC * RC * 3;
+    __shared__ __align__(16) TA xs[kFwdXsBytes / sizeof(TA)];
+    __shared__ __align__(16) TA red[T * kPer];
+    __shared__ FwdRec srec[kMaxGroupRecs];
+    const FwdUnit un = units[blockIdx.x];
+    const FwdGroup gp = groups[un.group];
+    const MeshDev& md = ONE ? m0 : meshes[gp.mesh];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < gp.nrec; i += T) srec[i] = recs[gp.first + i];
+    const TF* Vg = static_cast<const TF*>(md.Vr) + gp.vbase + (size_t)un.j0 * gp.Cs;
+    const TA* x0 = xg + ((size_t)md.xgoff + gp.s0 + un.j0) * G * 4;
+    TA* wr = w + (size_t)md.woff * G * 4;
+    const float* SU = md.SU;
+    const TA c1 = (TA)md.c1, c2 = (TA)md.c2;
+    const int Cs = gp.Cs, n = un.nrows;
+    const int Q = Cs / VEC;
+    const int NRC = (G + RC - 1) / RC;
+    const int pairs = Q * NRC;
+    const int rows = max(1, (int)(kFwdXsBytes / sizeof(TA)) / (G * 4));  // x rows per staged chunk
+    const int GG = pairs >= T ? 1 : min(T / pairs, rows);
+    const int PR = T / GG;
+    const int pl = tid % PR, g = tid / PR;
+    __syncthreads();
+    for (int pr0 = 0; pr0 < pairs; pr0 += PR) {
+        const int nr = min(PR, pairs - pr0);
+        const bool active = g < GG && pl < nr;
+        const int pr = pr0 + pl;
+        const int q = pr % Q, c = pr / Q;
+        const int nq = min(RC, G - c * RC);
+        TA acc[VEC][RC][3];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e)
+#pragma unroll
+            for (int k = 0; k < RC; ++k) acc[e][k][0] = acc[e][k][1] = acc[e][k][2] = (TA)0;
+        const TF* vp = Vg + (size_t)q * VEC;
+        for (int j0 = 0; j0 < n; j0 += rows) {
+            const int nrows = min(rows, n - j0);
+            __syncthreads();  // the previous chunk is consumed
+            // stage x rows j0 .. j0 + nrows (4-vectors, G per row), 16 bytes a thread
+            {
+                constexpr int E16 = 16 / sizeof(TA);
+                const int nv = nrows * G * 4 / E16;
+                const uint4* src = reinterpret_cast<const uint4*>(x0 + (size_t)j0 * G * 4);
+                uint4* dst = reinterpret_cast<uint4*>(xs);
+                for (int e = tid; e < nv; e += T) dst[e] = src[e];
+            }
+            __syncthreads();
+            if (active) {
+#pragma unroll 2
+                for (int jj = g; jj < nrows; jj += GG) {
+                    TA v[VEC];
+                    Vec16<TF, TA>::load(vp + (size_t)(j0 + jj) * Cs, v);
+                    const TA* xr = xs + ((size_t)jj * G + c * RC) * 4;
+#pragma unroll
+                    for (int k = 0; k < RC; ++k) {
+                        if (RC > 1 && k >= nq) break;
+                        TA xa, xb, xc;
+                        load3(xr + k * 4, xa, xb, xc);
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e) {
+                            acc[e][k][0] += v[e] * xa;
+                            acc[e][k][1] += v[e] * xb;
+                            acc[e][k][2] += v[e] * xc;
+                        }
+                    }
+                }
+            }
+        }
+        // the partial sums of the GG row groups, in a fixed order
+        if (GG > 1) {
+            __syncthreads();
+            if (active) {
+                TA* rp = red + (size_t)(g * PR + pl) * kPer;
+#pragma unroll
+                for (int e = 0; e < VEC; ++e)
+#pragma unroll
+                    for (int k = 0; k < RC; ++k)
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) rp[(e * RC + k) * 3 + a] = acc[e][k][a];
+            }
+            __syncthreads();
+        }
+        for (int idx = (GG > 1 ? tid : (active ? 0 : 1 << 30)); idx < (GG > 1 ? nr * VEC * RC : 1);
+             idx += (GG > 1 ? T : 1)) {
+            // GG == 1: this thread's own pair; GG > 1: (pair, column, vector) items
+            const int pp = GG > 1 ? idx / (VEC * RC) : pl;
+            const int q2 = (pr0 + pp) % Q, c2i = (pr0 + pp) / Q;
+            // the block of column vector q2: the last record with offset <= q2 VEC
+            int lo = 0, hi = gp.nrec - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (srec[mid].coff <= q2 * VEC) lo = mid;
+                else hi = mid - 1;
+            }
+            const FwdRec& rec = srec[lo];
+            const int cb0 = q2 * VEC - rec.coff;  // first column of the vector in the block
+            // one-unit groups write w; the units of taller groups write their
+            // partial sums for the second pass
+            TA* zp = un.zcol0 >= 0 ? z + ((size_t)(un.zcol0 + (int64_t)un.chunk * Cs) * G) * 4 : nullptr;
+            if (GG > 1) {
+                const int rem = idx - pp * (VEC * RC);
+                const int e = rem / RC, k = rem - e * RC;
+                const int r = c2i * RC + k;
+                if (cb0 + e >= rec.C || r >= G) continue;
+                TA zz[3] = {(TA)0, (TA)0, (TA)0};
+                for (int gg = 0; gg < GG; ++gg)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) zz[a] += red[(size_t)(gg * PR + pp) * kPer + (e * RC + k) * 3 + a];
+                if (zp) {
+                    TA* d = zp + ((size_t)(q2 * VEC + e) * G + r) * 4;
+                    d[0] = zz[0];
+                    d[1] = zz[1];
+                    d[2] = zz[2];
+                } else {
+                    write_w<TA>(rec, cb0 + e, zz[0], zz[1], zz[2], SU, wr, c1, c2, G, r);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    if (cb0 + e >= rec.C) continue;
+#pragma unroll
+                    for (int k = 0; k < RC; ++k) {
+                        if (k >= nq) break;
+                        if (zp) {
+                            TA* d = zp + ((size_t)(q2 * VEC + e) * G + c * RC + k) * 4;
+                            d[0] = acc[e][k][0];
+                            d[1] = acc[e][k][1];
+                            d[2] = acc[e][k][2];
+                        } else {
+                            write_w<TA>(rec, cb0 + e, acc[e][k][0], acc[e][k][1], acc[e][k][2], SU, wr, c1, c2, G,
+                                        c * RC + k);
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+constexpr int kThreads = 128;  // per-block forward kernels
+
 // pointers of block `rec` of its mesh.  ONE: the plan
 // has a single mesh, passed by value as a kernel parameter (no dependent load
 // of the mesh table before the first load of V).
 template <class TF, class TA, bool ONE>
 struct FwdArgs {
     const TF* Vb;
+    int64_t ld;  // row stride of V (the group's Cs)
     const TA* x0;
     TA* wr;
     const float* SU;
     TA c1, c2;
-    __device__ __forceinline__ FwdArgs(const FwdRec& rec, const MeshDev& m0, const MeshDev* __restrict__ meshes,
-                                       const TA* xg, TA* w, int G)
+    __device__ __forceinline__ FwdArgs(const FwdRec& rec, const FwdGroup* __restrict__ groups, const MeshDev& m0,
+                                       const MeshDev* __restrict__ meshes, const TA* xg, TA* w, int G)
     {
         const MeshDev& md = ONE ? m0 : meshes[rec.mesh];
-        Vb = static_cast<const TF*>(md.Vr) + rec.vbase;
+        const FwdGroup gp = groups[rec.grp];
+        Vb = static_cast<const TF*>(md.Vr) + gp.vbase + rec.coff;
+        ld = gp.Cs;
         x0 = xg + ((size_t)md.xgoff + rec.s0) * G * 4;
         wr = w + (size_t)md.woff * G * 4;
         SU = md.SU;
@@ -235,124 +401,6 @@ struct FwdArgs {
         c2 = (TA)md.c2;
     }
 };
-
-// Single vector, small blocks (|s| <= 128): one warp per block.  Lane (q, g):
-// column vector q (VEC consecutive columns of the row-major V), rows g, g +
-// GG, ...; the GG partial sums are added in a fixed order.
-template <class TF, class TA, bool ONE>
-__global__ void __launch_bounds__(kThreads) fwd_small_kernel(
-    const FwdRec* __restrict__ recs, int64_t nrec, const __grid_constant__ MeshDev m0,
-    const MeshDev* __restrict__ meshes, const TA* __restrict__ xg, TA* __restrict__ w)
-{
-    constexpr int VEC = Vec16<TF, TA>::N;
-    __shared__ TA red[kThreads / 32][32 * VEC * 3];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t bi = (int64_t)blockIdx.x * (kThreads / 32) + warp;
-    if (bi >= nrec) return;
-    TA* rw = red[warp];
-    const FwdRec rec = recs[bi];
-    const FwdArgs<TF, TA, ONE> fa(rec, m0, meshes, xg, w, 1);
-    const int Cp = (rec.C + 7) & ~7, Q = Cp / VEC;
-    for (int cq0 = 0; cq0 < Q; cq0 += 32) {
-        const int QT = min(Q - cq0, 32), GG = 32 / QT;
-        const int q = lane % QT, g = lane / QT;
-        TA acc[VEC][3];
-#pragma unroll
-        for (int e = 0; e < VEC; ++e) acc[e][0] = acc[e][1] = acc[e][2] = (TA)0;
-        if (g < GG) {
-            const TF* vp = fa.Vb + (size_t)(cq0 + q) * VEC;
-#pragma unroll 4
-            for (int j = g; j < rec.n; j += GG) {
-                TA v[VEC];
-                Vec16<TF, TA>::load(vp + (size_t)j * Cp, v);
-                TA xa, xb, xc;
-                load3(fa.x0 + (size_t)j * 4, xa, xb, xc);
-#pragma unroll
-                for (int e = 0; e < VEC; ++e) {
-                    acc[e][0] += v[e] * xa;
-                    acc[e][1] += v[e] * xb;
-                    acc[e][2] += v[e] * xc;
-                }
-            }
-#pragma unroll
-            for (int e = 0; e < VEC; ++e)
-#pragma unroll
-                for (int a = 0; a < 3; ++a) rw[((g * QT + q) * VEC + e) * 3 + a] = acc[e][a];
-        }
-        __syncwarp();
-        if (g == 0) {
-#pragma unroll
-            for (int e = 0; e < VEC; ++e) {
-                const int c = (cq0 + q) * VEC + e;
-                if (c < rec.C) {
-                    TA z[3] = {(TA)0, (TA)0, (TA)0};
-                    for (int gg = 0; gg < GG; ++gg)
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) z[a] += rw[((gg * QT + q) * VEC + e) * 3 + a];
-                    write_w<TA>(rec, c, z[0], z[1], z[2], fa.SU, fa.wr, fa.c1, fa.c2, 1, 0);
-                }
-            }
-        }
-        __syncwarp();
-    }
-}
-
-// Single vector, larger blocks: one CTA per block.  Thread (q, g) as above
-// with GG row groups over the whole CTA, reduced through shared memory.
-template <class TF, class TA, bool ONE>
-__global__ void __launch_bounds__(kThreads) fwd_big_kernel(
-    const FwdRec* __restrict__ recs, const __grid_constant__ MeshDev m0, const MeshDev* __restrict__ meshes,
-    const TA* __restrict__ xg, TA* __restrict__ w)
-{
-    constexpr int VEC = Vec16<TF, TA>::N;
-    __shared__ TA red[kThreads * VEC * 3];
-    const FwdRec rec = recs[blockIdx.x];
-    const FwdArgs<TF, TA, ONE> fa(rec, m0, meshes, xg, w, 1);
-    const int Cp = (rec.C + 7) & ~7, Q = Cp / VEC;
-    const int tid = threadIdx.x;
-    for (int cq0 = 0; cq0 < Q; cq0 += kThreads) {
-        const int QT = min(Q - cq0, kThreads);
-        const int GG = kThreads / QT;
-        const int q = tid % QT, g = tid / QT;
-        TA acc[VEC][3];
-#pragma unroll
-        for (int e = 0; e < VEC; ++e) acc[e][0] = acc[e][1] = acc[e][2] = (TA)0;
-        if (g < GG) {
-            const TF* vp = fa.Vb + (size_t)(cq0 + q) * VEC;
-#pragma unroll 4
-            for (int j = g; j < rec.n; j += GG) {
-                TA v[VEC];
-                Vec16<TF, TA>::load(vp + (size_t)j * Cp, v);
-                TA xa, xb, xc;
-                load3(fa.x0 + (size_t)j * 4, xa, xb, xc);
-#pragma unroll
-                for (int e = 0; e < VEC; ++e) {
-                    acc[e][0] += v[e] * xa;
-                    acc[e][1] += v[e] * xb;
-                    acc[e][2] += v[e] * xc;
-                }
-            }
-        }
-        __syncthreads();
-        if (g < GG) {
-#pragma unroll
-            for (int e = 0; e < VEC; ++e)
-#pragma unroll
-                for (int a = 0; a < 3; ++a) red[((g * QT + q) * VEC + e) * 3 + a] = acc[e][a];
-        }
-        __syncthreads();
-        for (int idx = tid; idx < QT * VEC; idx += kThreads) {
-            const int c = cq0 * VEC + idx;
-            if (c >= rec.C) continue;
-            TA z[3] = {(TA)0, (TA)0, (TA)0};
-            for (int gg = 0; gg < GG; ++gg)
-#pragma unroll
-                for (int a = 0; a < 3; ++a) z[a] += red[(gg * QT * VEC + idx) * 3 + a];
-            write_w<TA>(rec, c, z[0], z[1], z[2], fa.SU, fa.wr, fa.c1, fa.c2, 1, 0);
-        }
-        __syncthreads();
-    }
-}
 
 // Several (G) interleaved right-hand sides.  A block's work is the pairs
 // (column vector q, RHS chunk c of RC vectors).  T threads (a warp, or the CTA
@@ -390,7 +438,7 @@ __device__ __forceinline__ void fwd_multi_block(const FwdRec& rec, const FwdArgs
 #pragma unroll 2
             for (int j = g; j < rec.n; j += GG) {
                 TA v[VEC];
-                Vec16<TF, TA>::load(vp + (size_t)j * Cp, v);
+                Vec16<TF, TA>::load(vp + (size_t)j * fa.ld, v);
                 const TA* xr = xp + (size_t)j * G * 4;
 #pragma unroll
                 for (int k = 0; k < RC; ++k) {
@@ -452,31 +500,72 @@ __device__ __forceinline__ void fwd_multi_block(const FwdRec& rec, const FwdArgs
 
 template <class TF, class TA, bool ONE, int RC>
 __global__ void __launch_bounds__(kThreads) fwd_small_multi_kernel(
-    const FwdRec* __restrict__ recs, int64_t nrec, const __grid_constant__ MeshDev m0,
-    const MeshDev* __restrict__ meshes, const TA* __restrict__ xg, TA* __restrict__ w, int G)
+    const int32_t* __restrict__ ids, int64_t nrec, const FwdRec* __restrict__ recs, const FwdGroup* __restrict__ groups,
+    const __grid_constant__ MeshDev m0, const MeshDev* __restrict__ meshes, const TA* __restrict__ xg,
+    TA* __restrict__ w, int G)
 {
     constexpr int kPer = Vec16<TF, TA>::N * RC * 3;
     __shared__ TA red[kThreads / 32][32 * kPer];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t bi = (int64_t)blockIdx.x * (kThreads / 32) + warp;
     if (bi >= nrec) return;
-    const FwdRec rec = recs[bi];
-    const FwdArgs<TF, TA, ONE> fa0(rec, m0, meshes, xg, w, G);
+    const FwdRec rec = recs[ids[bi]];
+    const FwdArgs<TF, TA, ONE> fa0(rec, groups, m0, meshes, xg, w, G);
     const FwdArgs<TF, TA, true>& fa = reinterpret_cast<const FwdArgs<TF, TA, true>&>(fa0);
     fwd_multi_block<TF, TA, RC, 32>(rec, fa, G, lane, red[warp]);
 }
 
 template <class TF, class TA, bool ONE, int RC>
 __global__ void __launch_bounds__(kThreads) fwd_big_multi_kernel(
-    const FwdRec* __restrict__ recs, const __grid_constant__ MeshDev m0, const MeshDev* __restrict__ meshes,
-    const TA* __restrict__ xg, TA* __restrict__ w, int G)
+    const int32_t* __restrict__ ids, const FwdRec* __restrict__ recs, const FwdGroup* __restrict__ groups,
+    const __grid_constant__ MeshDev m0, const MeshDev* __restrict__ meshes, const TA* __restrict__ xg,
+    TA* __restrict__ w, int G)
 {
     constexpr int kPer = Vec16<TF, TA>::N * RC * 3;
     __shared__ TA red[kThreads * kPer];
-    const FwdRec rec = recs[blockIdx.x];
-    const FwdArgs<TF, TA, ONE> fa0(rec, m0, meshes, xg, w, G);
+    const FwdRec rec = recs[ids[blockIdx.x]];
+    const FwdArgs<TF, TA, ONE> fa0(rec, groups, m0, meshes, xg, w, G);
     const FwdArgs<TF, TA, true>& fa = reinterpret_cast<const FwdArgs<TF, TA, true>&>(fa0);
     fwd_multi_block<TF, TA, RC, kThreads>(rec, fa, G, threadIdx.x, red);
+}
+
+// Second pass for the groups taller than one unit: z of every (column,
+// vector) as the sum of the units' partial sums in chunk order, then w.
+template <class TA, bool ONE>
+__global__ void __launch_bounds__(kFwdThreads) fwd_reduce_kernel(
+    const FwdMulti* __restrict__ multi, const FwdGroup* __restrict__ groups, const FwdRec* __restrict__ recs,
+    const __grid_constant__ MeshDev m0, const MeshDev* __restrict__ meshes, const TA* __restrict__ z,
+    TA* __restrict__ w, int G)
+{
+    __shared__ FwdRec srec[kMaxGroupRecs];
+    const FwdMulti mu = multi[blockIdx.x];
+    const FwdGroup gp = groups[mu.group];
+    const MeshDev& md = ONE ? m0 : meshes[gp.mesh];
+    for (int i = threadIdx.x; i < gp.nrec; i += blockDim.x) srec[i] = recs[gp.first + i];
+    __syncthreads();
+    TA* wr = w + (size_t)md.woff * G * 4;
+    const TA c1 = (TA)md.c1, c2 = (TA)md.c2;
+    const int Cs = gp.Cs;
+    for (int idx = threadIdx.x; idx < Cs * G; idx += blockDim.x) {
+        const int col = idx / G, r = idx - col * G;
+        int lo = 0, hi = gp.nrec - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (srec[mid].coff <= col) lo = mid;
+            else hi = mid - 1;
+        }
+        const FwdRec& rec = srec[lo];
+        const int cb = col - rec.coff;
+        if (cb >= rec.C) continue;
+        TA zz[3] = {(TA)0, (TA)0, (TA)0};
+        for (int k = 0; k < mu.nchunk; ++k) {
+            const TA* d = z + ((size_t)(mu.zcol0 + (int64_t)k * Cs + col) * G + r) * 4;
+            zz[0] += d[0];
+            zz[1] += d[1];
+            zz[2] += d[2];
+        }
+        write_w<TA>(rec, cb, zz[0], zz[1], zz[2], md.SU, wr, c1, c2, G, r);
+    }
 }
 
 // max |x| of each of the G vectors of a launch (rows of n dofs at stride ld),
@@ -587,12 +676,12 @@ __global__ void pack_ul_kernel(const int32_t* __restrict__ leaf, const int64_t* 
     }
 }
 
-// V row-major per block: one CTA per block
+// V row-major in its forward group (row stride ld[b]): one CTA per block
 template <class T>
 __global__ void pack_vr_kernel(const Blk* __restrict__ blks, const int32_t* __restrict__ rank,
                                const int64_t* __restrict__ voff, const int64_t* __restrict__ coff,
-                               const int64_t* __restrict__ vb_base, const double* __restrict__ V,
-                               const float* __restrict__ SV, T* __restrict__ Vr)
+                               const int64_t* __restrict__ vb_base, const int64_t* __restrict__ vb_ld,
+                               const double* __restrict__ V, const float* __restrict__ SV, T* __restrict__ Vr)
 {
     const int b = blockIdx.x;
     const Blk bk = blks[b];
@@ -603,7 +692,9 @@ __global__ void pack_vr_kernel(const Blk* __restrict__ blks, const int32_t* __re
         kp[k + 1] = kp[k] + kk[k];
     }
     const int C = kp[7], Cp = (C + 7) & ~7;
+    if (C == 0) return;
     T* dst = Vr + vb_base[b];
+    const int64_t ld = vb_ld[b];
     const int64_t col0 = coff[(size_t)b * 7];
     for (int64_t e = threadIdx.x; e < (int64_t)bk.n * Cp; e += blockDim.x) {
         const int j = (int)(e / Cp), c = (int)(e - (int64_t)j * Cp);
@@ -615,7 +706,7 @@ __global__ void pack_vr_kernel(const Blk* __restrict__ blks, const int32_t* __re
             v = V[voff[(size_t)b * 7 + kern] + (size_t)l * bk.n + j];
             if (SV) v /= (double)SV[col0 + c];
         }
-        dst[e] = cvt<T>(v);
+        dst[(size_t)j * ld + c] = cvt<T>(v);
     }
 }
 
@@ -689,6 +780,63 @@ int stream_launch(StreamLaunch& out)
     return HM_OK;
 }
 
+// The forward pass over every unit of the plan (with a fork schedule the
+// unit list is split in two halves on two streams), then the second pass of
+// the tall groups.
+template <class TF, class TA, int RC>
+int run_forward(const Plan& P, TA* xg, TA* w, TA* z, int G, cudaStream_t s, const Sched& sc)
+{
+    if (P.nunits <= 0) return HM_OK;
+    const bool one = P.nmesh == 1;
+    const MeshDev m0 = one ? P.mesh0 : MeshDev{};
+    if (RC > 1) {
+        // several vectors: one CTA per tall block, one warp per other block
+        const bool fork = sc.side && P.nbig > 0 && P.nsmall > 0;
+        if (fork) {
+            HM_CUDA(cudaEventRecord(sc.fork, s));
+            HM_CUDA(cudaStreamWaitEvent(sc.side, sc.fork, 0));
+        }
+        if (P.nbig > 0) {
+            auto kb = one ? fwd_big_multi_kernel<TF, TA, true, RC> : fwd_big_multi_kernel<TF, TA, false, RC>;
+            kb<<<(unsigned)P.nbig, kThreads, 0, fork ? sc.side : s>>>(P.big, P.fwd, P.groups, m0, P.meshes, xg, w, G);
+            HM_CUDA(cudaGetLastError());
+        }
+        if (P.nsmall > 0) {
+            const unsigned nb = (unsigned)((P.nsmall + kThreads / 32 - 1) / (kThreads / 32));
+            auto ks = one ? fwd_small_multi_kernel<TF, TA, true, RC> : fwd_small_multi_kernel<TF, TA, false, RC>;
+            ks<<<nb, kThreads, 0, s>>>(P.small, P.nsmall, P.fwd, P.groups, m0, P.meshes, xg, w, G);
+            HM_CUDA(cudaGetLastError());
+        }
+        if (fork) {
+            HM_CUDA(cudaEventRecord(sc.join, sc.side));
+            HM_CUDA(cudaStreamWaitEvent(s, sc.join, 0));
+        }
+        return HM_OK;
+    }
+    auto kern = one ? fwd_group_kernel<TF, TA, RC, true> : fwd_group_kernel<TF, TA, RC, false>;
+    const bool fork = sc.side && P.nunits > 1;
+    const int64_t half = fork ? P.nunits / 2 : P.nunits;
+    if (fork) {
+        HM_CUDA(cudaEventRecord(sc.fork, s));
+        HM_CUDA(cudaStreamWaitEvent(sc.side, sc.fork, 0));
+        kern<<<(unsigned)(P.nunits - half), kFwdThreads, 0, sc.side>>>(P.units + half, P.groups, P.fwd, m0, P.meshes,
+                                                                       xg, w, z, G);
+        HM_CUDA(cudaGetLastError());
+    }
+    kern<<<(unsigned)half, kFwdThreads, 0, s>>>(P.units, P.groups, P.fwd, m0, P.meshes, xg, w, z, G);
+    HM_CUDA(cudaGetLastError());
+    if (fork) {
+        HM_CUDA(cudaEventRecord(sc.join, sc.side));
+        HM_CUDA(cudaStreamWaitEvent(s, sc.join, 0));
+    }
+    if (P.nmulti > 0) {
+        auto red = one ? fwd_reduce_kernel<TA, true> : fwd_reduce_kernel<TA, false>;
+        red<<<(unsigned)P.nmulti, kFwdThreads, 0, s>>>(P.multi, P.groups, P.fwd, m0, P.meshes, z, w, G);
+        HM_CUDA(cudaGetLastError());
+    }
+    return HM_OK;
+}
+
 // One launch of each phase for G right-hand sides (rows of x and y at
 // stride ld), with RC vectors per thread chunk.
 template <class TF, class TN, class TA, int RC>
@@ -703,39 +851,9 @@ int run_phases(const Plan& P, const double* x, double* y, int G, int64_t ld, TA*
         HM_CUDA(cudaGetLastError());
     }
     if (prof) prof_mark(*prof, 1, s);
-    const bool one = P.nmesh == 1;
-    const MeshDev m0 = one ? P.mesh0 : MeshDev{};
-    const bool fork = sc.side && P.nbig > 0 && P.nsmall > 0;
-    if (fork) {
-        HM_CUDA(cudaEventRecord(sc.fork, s));
-        HM_CUDA(cudaStreamWaitEvent(sc.side, sc.fork, 0));
-    }
-    if (P.nbig > 0) {
-        const unsigned nb = (unsigned)P.nbig;
-        cudaStream_t sb = fork ? sc.side : s;
-        if (RC == 1) {
-            auto kb = one ? fwd_big_kernel<TF, TA, true> : fwd_big_kernel<TF, TA, false>;
-            kb<<<nb, kThreads, 0, sb>>>(P.fwd, m0, P.meshes, xg, w);
-        } else {
-            auto kb = one ? fwd_big_multi_kernel<TF, TA, true, RC> : fwd_big_multi_kernel<TF, TA, false, RC>;
-            kb<<<nb, kThreads, 0, sb>>>(P.fwd, m0, P.meshes, xg, w, G);
-        }
-        HM_CUDA(cudaGetLastError());
-    }
-    if (P.nsmall > 0) {
-        const unsigned nb = (unsigned)((P.nsmall + kThreads / 32 - 1) / (kThreads / 32));
-        if (RC == 1) {
-            auto ks = one ? fwd_small_kernel<TF, TA, true> : fwd_small_kernel<TF, TA, false>;
-            ks<<<nb, kThreads, 0, s>>>(P.fwd + P.nbig, P.nsmall, m0, P.meshes, xg, w);
-        } else {
-            auto ks = one ? fwd_small_multi_kernel<TF, TA, true, RC> : fwd_small_multi_kernel<TF, TA, false, RC>;
-            ks<<<nb, kThreads, 0, s>>>(P.fwd + P.nbig, P.nsmall, m0, P.meshes, xg, w, G);
-        }
-        HM_CUDA(cudaGetLastError());
-    }
-    if (fork) {
-        HM_CUDA(cudaEventRecord(sc.join, sc.side));
-        HM_CUDA(cudaStreamWaitEvent(s, sc.join, 0));
+    {
+        int rc = run_forward<TF, TA, RC>(P, xg, w, static_cast<TA*>(P.z), G, s, sc);
+        if (rc) return rc;
     }
     if (prof) prof_mark(*prof, 2, s);
     if (P.nwork > 0) {
@@ -797,27 +915,9 @@ int run_phases_tc(const Plan& P, const double* x, double* y, int G, int64_t ld, 
         HM_CUDA(cudaGetLastError());
     }
     if (prof) prof_mark(*prof, 1, s);
-    const bool one = P.nmesh == 1;
-    const MeshDev m0 = one ? P.mesh0 : MeshDev{};
-    const bool fork = sc.side && P.nbig > 0 && P.nsmall > 0;
-    if (fork) {
-        HM_CUDA(cudaEventRecord(sc.fork, s));
-        HM_CUDA(cudaStreamWaitEvent(sc.side, sc.fork, 0));
-    }
-    if (P.nbig > 0) {
-        auto kb = one ? fwd_big_multi_kernel<TF, float, true, RC> : fwd_big_multi_kernel<TF, float, false, RC>;
-        kb<<<(unsigned)P.nbig, kThreads, 0, fork ? sc.side : s>>>(P.fwd, m0, P.meshes, xg, w, G);
-        HM_CUDA(cudaGetLastError());
-    }
-    if (P.nsmall > 0) {
-        const unsigned nb = (unsigned)((P.nsmall + kThreads / 32 - 1) / (kThreads / 32));
-        auto ks = one ? fwd_small_multi_kernel<TF, float, true, RC> : fwd_small_multi_kernel<TF, float, false, RC>;
-        ks<<<nb, kThreads, 0, s>>>(P.fwd + P.nbig, P.nsmall, m0, P.meshes, xg, w, G);
-        HM_CUDA(cudaGetLastError());
-    }
-    if (fork) {
-        HM_CUDA(cudaEventRecord(sc.join, sc.side));
-        HM_CUDA(cudaStreamWaitEvent(s, sc.join, 0));
+    {
+        int rc = run_forward<TF, float, RC>(P, xg, w, static_cast<float*>(P.z), G, s, sc);
+        if (rc) return rc;
     }
     if (prof) prof_mark(*prof, 2, s);
     if (P.nwork > 0) {
@@ -901,7 +1001,7 @@ int pack_form(hm_matrix& H, int form, const float* SU, const float* SV, cudaStre
     if (H.nadm > 0) {
         pack_vr_kernel<T><<<(unsigned)H.nadm, 256, 0, s>>>(
             H.d_adm.as<Blk>(), H.d_rank.as<int32_t>(), H.d_voff.as<int64_t>(), H.d_coff.as<int64_t>(),
-            H.d_vb_base.as<int64_t>(), H.V64.as<double>(), SV, H.Vr[form].as<T>());
+            H.d_vb_base.as<int64_t>(), H.d_vb_ld.as<int64_t>(), H.V64.as<double>(), SV, H.Vr[form].as<T>());
         HM_CUDA(cudaGetLastError());
     }
     return HM_OK;
@@ -1016,8 +1116,17 @@ int matvec_device_scratch(const hm_matrix& H, const double* x, double* y, int32_
     P.pos_prefix = H.d_pos_prefix.as<int64_t>();
     P.npos = H.M;
     P.fwd = H.d_fwd_all.as<FwdRec>();
-    P.nbig = H.n_fwd_big;
-    P.nsmall = H.n_fwd_small;
+    P.groups = H.d_groups.as<FwdGroup>();
+    P.units = H.d_units.as<FwdUnit>();
+    P.nunits = (int64_t)H.unit_h.size();
+    P.multi = H.d_multi.as<FwdMulti>();
+    P.nmulti = (int64_t)H.multi_h.size();
+    P.zcols = H.zcols;
+    P.z = scr.z;
+    P.big = H.d_big.as<int32_t>();
+    P.nbig = (int64_t)H.big_h.size();
+    P.small = H.d_small.as<int32_t>();
+    P.nsmall = (int64_t)H.small_h.size();
     P.work = H.d_work.as<int2>();
     P.nwork = H.nleaves;
     P.max_leaf = H.max_leaf;
@@ -1029,7 +1138,7 @@ int matvec_device_scratch(const hm_matrix& H, const double* x, double* y, int32_
 int matvec_device(const hm_matrix& H, const double* x, double* y, int32_t nrhs, int64_t ld,
                   int32_t form, cudaStream_t s)
 {
-    Scratch scr{H.xg.p, H.wb.p, H.d_counters.as<int>(), true};
+    Scratch scr{H.xg.p, H.wb.p, H.d_counters.as<int>(), true, H.zb.p};
     return matvec_device_scratch(H, x, y, nrhs, ld, form, s, scr);
 }
 
@@ -1041,7 +1150,8 @@ Scratch make_scratch(const hm_matrix& H, int32_t nrhs, int32_t form, void* base)
     const size_t vec = up((size_t)nrhs * 4 * (size_t)H.M * ta);
     const size_t wb = up((size_t)nrhs * (size_t)std::max<int64_t>(H.w_total, 1) * ta);
     unsigned char* b = static_cast<unsigned char*>(base);
-    return Scratch{b, b + vec, reinterpret_cast<int*>(b + vec + wb), false};  // counters: kCounterInts
+    const size_t cnt = up((size_t)kCounterInts * sizeof(int));
+    return Scratch{b, b + vec, reinterpret_cast<int*>(b + vec + wb), false, b + vec + wb + cnt};
 }
 
 size_t matvec_scratch_bytes(const hm_matrix& H, int32_t nrhs, int32_t form)
@@ -1049,7 +1159,7 @@ size_t matvec_scratch_bytes(const hm_matrix& H, int32_t nrhs, int32_t form)
     const size_t ta = form == HM_FP64 ? 8 : 4;
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
     return up((size_t)nrhs * 4 * (size_t)H.M * ta) + up((size_t)nrhs * (size_t)std::max<int64_t>(H.w_total, 1) * ta) +
-           up((size_t)kCounterInts * sizeof(int));
+           up((size_t)kCounterInts * sizeof(int)) + up((size_t)nrhs * (size_t)std::max<int64_t>(H.zcols, 1) * 4 * ta);
 }
 
 // the streaming layouts of one form (and the FP32 near field and the column
@@ -1085,7 +1195,7 @@ int pack_device(hm_matrix& H, int32_t form, cudaStream_t s)
             DevBuf wb;
             if ((rc = dalloc(H, wb, 256))) return rc;
             HM_CUDA(cudaMemsetAsync(wb.p, 0, 4, s));
-            const int64_t nrec = H.n_fwd_big + H.n_fwd_small;
+            const int64_t nrec = (int64_t)H.fwd_h.size();
             if (nrec > 0) {
                 wbound_kernel<<<256, 256, 0, s>>>(H.d_fwd_all.as<FwdRec>(), nrec, H.SU.as<float>(), wb.as<int>());
                 HM_CUDA(cudaGetLastError());

@@ -247,7 +247,8 @@ struct LeafCfg {
 // 16, the tensor-core K step, otherwise).
 // empty_far (optional): far stages are taken back through this second set of
 // barriers instead (the tensor-core kernel releases them by MMA commit).
-template <class TF, class TN, class TA, int NS, int kStage, int kAuxBytes, int kGran, int kFarCap = 1 << 20>
+template <class TF, class TN, class TA, int NS, int kStage, int kAuxBytes, int kGran, int kFarCap = 1 << 20,
+          bool kTwoRelease = false>
 __device__ __forceinline__ void leaf_producer(const int2* __restrict__ work, int nwork,
                                               const MeshDev* __restrict__ meshes, int* __restrict__ counter,
                                               int* __restrict__ err, const TA* __restrict__ xg_base,
@@ -255,10 +256,11 @@ __device__ __forceinline__ void leaf_producer(const int2* __restrict__ work, int
                                               uint64_t* full, uint64_t* empty, StageMeta* meta,
                                               uint64_t* empty_far = nullptr)
 {
-    // per slot: kind of its last stage and the uses of each release barrier
-    int prev_kind[NS], uses_far[NS], uses_near[NS];
-#pragma unroll
-    for (int q = 0; q < NS; ++q) prev_kind[q] = uses_far[q] = uses_near[q] = 0;
+    // per slot (two release barriers only): kind of its last stage and the
+    // uses of each release barrier, as bit fields of registers
+    uint32_t far_mask = 0u;      // bit q: slot q last held a far stage
+    uint32_t far_parity = 0u;    // bit q: parity of the next far release of slot q
+    uint32_t near_parity = 0u;   // bit q: parity of the next near release of slot q
     constexpr int kSlotBytes = kStage + kAuxBytes;
     const int lane = threadIdx.x & 31;
     const int vecG = 4 * G;
@@ -279,17 +281,26 @@ __device__ __forceinline__ void leaf_producer(const int2* __restrict__ work, int
             const int slot = it % NS;
             if (it >= NS) {
                 bool got;
-                if (empty_far && prev_kind[slot] == 0)
-                    got = mbar_wait(&empty_far[slot], (uint32_t)(uses_far[slot] - 1) & 1u, err, 1, it);
-                else if (empty_far)
-                    got = mbar_wait(&empty[slot], (uint32_t)(uses_near[slot] - 1) & 1u, err, 1, it);
-                else
+                if (kTwoRelease) {
+                    // wait for the release of the slot's previous stage, then
+                    // flip that barrier's expected parity
+                    const uint32_t bit = 1u << slot;
+                    if (far_mask & bit) {
+                        got = mbar_wait(&empty_far[slot], (far_parity & bit) ? 1u : 0u, err, 1, it);
+                        far_parity ^= bit;
+                    } else {
+                        got = mbar_wait(&empty[slot], (near_parity & bit) ? 1u : 0u, err, 1, it);
+                        near_parity ^= bit;
+                    }
+                } else {
                     got = mbar_wait(&empty[slot], (uint32_t)((it / NS) - 1) & 1u, err, 1, it);
+                }
                 if (!got) return false;
             }
-            prev_kind[slot] = kind;
-            if (kind == 0) ++uses_far[slot];
-            else ++uses_near[slot];
+            if (kTwoRelease) {
+                const uint32_t bit = 1u << slot;
+                far_mask = kind == 0 ? (far_mask | bit) : (far_mask & ~bit);
+            }
             if (lane == 0) {
                 StageMeta m;
                 m.leaf = lf;
