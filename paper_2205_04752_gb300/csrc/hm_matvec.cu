@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_group_kernel(
             }
             __syncthreads();
             if (active) {
-#pragma unroll 2
+#pragma unroll 4
                 for (int jj = g; jj < nrows; jj += GG) {
                     TA v[VEC];
                     Vec16<TF, TA>::load(vp + (size_t)(j0 + jj) * Cs, v);

@@ -120,6 +120,23 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared through the load/store path
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+// the mbarrier's current phase also waits for this thread's cp.async copies
+// (its pending count is raised now and lowered when they have landed)
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// aux ranges up to this many bytes go through cp.async, larger ones through
+// the bulk copy engine
+constexpr int kSmallCopy = 256;
+
 // 16 KB of zeros: the staged w of the padding segments of a 16-bit U stream
 __device__ __align__(128) unsigned char g_zeros[16384] = {};
 
@@ -275,6 +292,11 @@ __device__ __forceinline__ void leaf_producer(const int2* __restrict__ work, int
         // the item containing first + count.  vec: the 4-vectors the stream
         // reads (w for the far field, x for the near field), G per index.
         int sreal = 0;  // real segments of the current leaf's U stream
+        // the items of the next stage's scan, loaded at the end of the previous
+        // one so that their latency overlaps the wait for a free slot
+        const int2* pre_items = nullptr;
+        int pre_q0 = -1, pre_b31 = INT_MAX;
+        int2 pre_a = make_int2(INT_MAX, 0);
         // lastfar: the stage ends the leaf's far stream (meta pad[1])
         auto emit = [&](int mesh, int lf, int kind, int first, int count, int last, const void* src,
                         uint32_t bytes, const int2* items, int ni, int* cur, const TA* vec, int lastfar) -> bool {
@@ -311,11 +333,21 @@ __device__ __forceinline__ void leaf_producer(const int2* __restrict__ work, int
                 m.pad[0] = mesh;
                 m.pad[1] = lastfar;
                 meta[slot] = m;
-                if (kind < 2)
-                    mbar_arrive_expect_tx(&full[slot], bytes + (uint32_t)(count * vecG * sizeof(TA)));
             }
             __syncwarp();
             if (kind < 2) {
+                // bytes of this lane's copies that go through the bulk engine
+                uint32_t bulk = 0;
+                auto copy = [&](TA* dst, const TA* srcp, uint32_t nb) {
+                    if (nb <= (uint32_t)kSmallCopy) {
+                        for (uint32_t o = 0; o < nb; o += 16)
+                            cp_async16(reinterpret_cast<unsigned char*>(dst) + o,
+                                       reinterpret_cast<const unsigned char*>(srcp) + o);
+                    } else {
+                        bulk_g2s(dst, srcp, nb, &full[slot]);
+                        bulk += nb;
+                    }
+                };
                 TA* av = reinterpret_cast<TA*>(saux(slot));
                 const int end = first + count;
                 int q0 = *cur;
@@ -324,15 +356,22 @@ __device__ __forceinline__ void leaf_producer(const int2* __restrict__ work, int
                     // (the sentinel's start for the last real item)
                     const int q = q0 + lane;
                     int2 a = make_int2(INT_MAX, 0);
-                    if (q < ni) a = items[q];
+                    int b31 = INT_MAX;
+                    if (pre_items == items && pre_q0 == q0) {
+                        a = pre_a;
+                        b31 = pre_b31;
+                    } else {
+                        if (q < ni) a = items[q];
+                        if (lane == 31 && q + 1 < ni) b31 = items[q + 1].x;
+                    }
                     int b = __shfl_down_sync(0xffffffffu, a.x, 1);
-                    if (lane == 31) b = (q + 1 < ni) ? items[q + 1].x : INT_MAX;
+                    if (lane == 31) b = b31;
                     const bool overlap = q < ni - 1 && a.x < end;  // items are sorted by start
                     if (overlap) {
                         const int g0 = max(a.x, first), g1 = min(b, end);
                         if (g0 < g1)
-                            bulk_g2s(av + (size_t)(g0 - first) * vecG, vec + (size_t)(a.y + (g0 - a.x)) * vecG,
-                                     (uint32_t)((g1 - g0) * vecG * sizeof(TA)), &full[slot]);
+                            copy(av + (size_t)(g0 - first) * vecG, vec + (size_t)(a.y + (g0 - a.x)) * vecG,
+                                 (uint32_t)((g1 - g0) * vecG * sizeof(TA)));
                     }
                     const unsigned ov = __ballot_sync(0xffffffffu, overlap);
                     const int nov = __popc(ov);  // overlapping items are a prefix of the lanes
@@ -344,14 +383,29 @@ __device__ __forceinline__ void leaf_producer(const int2* __restrict__ work, int
                     }
                     q0 += 32;
                 }
+                {
+                    // issue the next scan's loads now
+                    const int qn = *cur + lane;
+                    pre_items = items;
+                    pre_q0 = *cur;
+                    pre_a = qn < ni ? items[qn] : make_int2(INT_MAX, 0);
+                    pre_b31 = (lane == 31 && qn + 1 < ni) ? items[qn + 1].x : INT_MAX;
+                }
+                // padding segments of a 16-bit U stream: zero w
+                if (lane == 0 && kind == 0 && end > sreal) {
+                    const int z0 = max(first, sreal);
+                    copy(av + (size_t)(z0 - first) * vecG, reinterpret_cast<const TA*>(g_zeros),
+                         (uint32_t)((end - z0) * vecG * sizeof(TA)));
+                }
+                // the phase waits for every lane's cp.async copies, then for the
+                // bulk bytes that lane 0 announces with its arrival
+                cp_async_arrive(&full[slot]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) bulk += __shfl_xor_sync(0xffffffffu, bulk, o);
+                __syncwarp();
                 if (lane == 0) {
+                    mbar_arrive_expect_tx(&full[slot], bytes + bulk);
                     bulk_g2s(sdata(slot), src, bytes, &full[slot]);
-                    // padding segments of a 16-bit U stream: zero w
-                    if (kind == 0 && end > sreal) {
-                        const int z0 = max(first, sreal);
-                        bulk_g2s(av + (size_t)(z0 - first) * vecG, g_zeros,
-                                 (uint32_t)((end - z0) * vecG * sizeof(TA)), &full[slot]);
-                    }
                 }
             } else if (lane == 0) {
                 mbar_arrive(&full[slot]);
