@@ -1161,10 +1161,11 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
             }
         }
         std::stable_sort(gl.begin(), gl.end(), [](const G0& a, const G0& b) { return a.work > b.work; });
-        std::vector<int64_t> vb_base((size_t)H.nadm + 1, 0), vb_ld((size_t)H.nadm + 1, 0);
+        std::vector<int64_t> vb_base((size_t)H.nadm + 1, 0), vb_ld((size_t)H.nadm + 1, 0),
+            vb_coff((size_t)H.nadm + 1, 0);
         std::vector<FwdRec> recs;
         std::vector<FwdGroup> groups;
-        int64_t vr = 0;
+        int64_t vr = 0, dcols = 0;
         for (const G0& g0 : gl) {
             FwdGroup g{};
             const Blk& b0 = H.adm_h[(size_t)g0.blocks[0]];
@@ -1192,18 +1193,25 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
                 r.C = (int16_t)Csum;
                 r.coff = (int32_t)cs;  // column offset in the group
                 r.grp = (int32_t)groups.size();
-                vb_base[(size_t)b] = vr + cs;
+                vb_base[(size_t)b] = vr;
+                vb_coff[(size_t)b] = cs;
                 cs += (Csum + 7) & ~7;
                 recs.push_back(r);
             }
             if (cs > INT32_MAX / 8) return fail(HM_EINVAL, "forward group too wide");
             g.Cs = (int32_t)cs;
+            if (dcols + cs > INT32_MAX) return fail(HM_EINVAL, "too many forward-group columns");
+            g.dbase = (int32_t)dcols;
+            dcols += cs;
             for (int32_t b : g0.blocks) vb_ld[(size_t)b] = cs;
-            vr += (int64_t)g.n * cs;
+            // rows padded to 16 (a tensor-core K step; the 16-bit forms store V
+            // in 8 x 8 tiles, see pack_vr_kernel)
+            vr += (int64_t)((g.n + 15) & ~15) * cs;
             groups.push_back(g);
         }
         vb_base[(size_t)H.nadm] = vr;
         H.vr_total = vr;
+        H.dcols = dcols;
         // units: one CTA per kFwdUnitRows rows of a group, the most data first
         std::vector<FwdUnit> units;
         std::vector<FwdMulti> multi;
@@ -1217,10 +1225,12 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
                 zc += (int64_t)nch * g.Cs;
             }
             for (int32_t k = 0; k < nch; ++k)
-                units.push_back(FwdUnit{(int32_t)gi, k * kFwdUnitRows, std::min(kFwdUnitRows, g.n - k * kFwdUnitRows), k, z0});
+                for (int32_t c0 = 0; c0 < g.Cs; c0 += kFwdUnitCols)
+                    units.push_back(FwdUnit{(int32_t)gi, k * kFwdUnitRows, std::min(kFwdUnitRows, g.n - k * kFwdUnitRows),
+                                            k, c0, std::min(kFwdUnitCols, g.Cs - c0), z0});
         }
         std::stable_sort(units.begin(), units.end(), [&](const FwdUnit& a, const FwdUnit& b) {
-            return (int64_t)a.nrows * groups[(size_t)a.group].Cs > (int64_t)b.nrows * groups[(size_t)b.group].Cs;
+            return (int64_t)a.nrows * a.ncols > (int64_t)b.nrows * b.ncols;
         });
         H.zcols = zc;
         H.unit_h = units;
@@ -1247,6 +1257,7 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
         if ((rc = upload(H, H.d_groups, groups.data(), groups.size() * sizeof(FwdGroup)))) return rc;
         if ((rc = upload(H, H.d_vb_base, vb_base.data(), vb_base.size() * 8))) return rc;
         if ((rc = upload(H, H.d_vb_ld, vb_ld.data(), vb_ld.size() * 8))) return rc;
+        if ((rc = upload(H, H.d_vb_coff, vb_coff.data(), vb_coff.size() * 8))) return rc;
         if (H.c_total > INT32_MAX / 4) return fail(HM_EINVAL, "too many factor columns");
     }
     // ---- workspace for the product

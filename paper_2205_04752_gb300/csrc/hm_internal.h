@@ -103,15 +103,23 @@ struct FwdRec {
     int32_t coff, grp;
     uint64_t kpack;  // rank of kernel q in bits 8q .. 8q+7
 };
-// the blocks that share a column cluster: V of all of them as one row-major
-// n x Cs matrix at element offset vbase; records first .. first + nrec - 1
+// the blocks that share a column cluster: V of all of them as one n x Cs
+// matrix at element offset vbase (row-major, or 8 x 8 tiles for the 16-bit
+// forms); records first .. first + nrec - 1; the column descriptors of the
+// 16-bit tensor-core forward pass at dbase .. dbase + Cs - 1
 struct FwdGroup {
     int64_t vbase;
     int32_t s0, n, Cs, first;
     int16_t nrec;
     uint16_t mesh;
-    int32_t pad;
+    int32_t dbase;
 };
+// column descriptor (x, y) of a forward-group column for the tensor-core
+// forward pass: x = factor column | p << 28 | q << 30 with the block's kernel
+// V_pq (p = q = 3: the c1 kernel), y = the bits of c1 su or c2 su; kFdSkip
+// marks a padding column
+constexpr uint32_t kFdSkip = 0xffffffffu;
+constexpr int64_t kFdMaxCol = (1 << 28) - 1;
 constexpr int kMaxGroupRecs = 64;
 // a CTA's share of a forward group: rows j0 .. j0 + nrows of group `group`;
 // a group taller than kFwdUnitRows has several units whose partial sums go
@@ -119,6 +127,7 @@ constexpr int kMaxGroupRecs = 64;
 // added by a second pass in chunk order; zcol0 < 0 for a one-unit group
 struct FwdUnit {
     int32_t group, j0, nrows, chunk;
+    int32_t c0, ncols;  // the unit's columns of the group (at most kFwdUnitCols)
     int64_t zcol0;
 };
 // the groups with several units: group, units, first z column
@@ -127,6 +136,7 @@ struct FwdMulti {
     int64_t zcol0;
 };
 constexpr int kFwdUnitRows = 256;
+constexpr int kFwdUnitCols = 256;
 
 // Device-side description of one mesh taking part in a product (a single
 // matrix is a product over one mesh; a batch concatenates several).  Stream
@@ -139,6 +149,7 @@ struct MeshDev {
     const void* Vr;   // row-major V of every block
     const void* Nl;   // leaf-major near-field stream
     const float* SU;  // per-column U scales (16-bit forms) or null
+    const uint2* fdesc;  // 16-bit forms: column descriptors of the forward groups
     const int32_t* leaf;
     const int64_t* lf_base;
     const int32_t* lf_ptr;
@@ -216,6 +227,9 @@ struct hm_matrix {
     hm::DevBuf d_ln_base, d_ln_ptr, d_ln_items, d_ln_src;  // near stream per leaf
     hm::DevBuf d_vb_base;                 // int64 nadm+1: V of each block (first row) in its group
     hm::DevBuf d_vb_ld;                   // int64 nadm+1: row stride of that V (its group's Cs)
+    hm::DevBuf d_vb_coff;                 // int64 nadm+1: column offset of the block in its group
+    hm::DevBuf fdesc;                     // uint2 per forward-group column (16-bit forms)
+    int64_t dcols = 0;                    // forward-group columns (sum of Cs)
     hm::DevBuf d_fwd_all;                // FwdRec of every block, group by group
     hm::DevBuf d_groups;                 // FwdGroup
     hm::DevBuf d_units, d_multi;         // FwdUnit (the most data first), FwdMulti

@@ -108,6 +108,18 @@ struct Vec16<__nv_bfloat16, TA> {
     }
 };
 
+// element offset of V[j, c] (c a multiple of 8) in a forward group of Cs
+// columns: row-major for FP64 / FP32, 8 x 8 tiles (row j / 8, column c / 8)
+// for the 16-bit forms, the layout of a tensor-core operand
+template <class TF>
+__device__ __forceinline__ size_t vel(int j, int c, int Cs)
+{
+    if constexpr (sizeof(TF) == 2)
+        return ((size_t)(j >> 3) * (size_t)(Cs >> 3) + (size_t)(c >> 3)) * 64 + (size_t)(j & 7) * 8;
+    else
+        return (size_t)j * (size_t)Cs + (size_t)c;
+}
+
 // R consecutive values of type T (R * sizeof(T) a multiple of 16)
 template <class T, class TA, int R>
 __device__ __forceinline__ void load_rows(const T* p, TA* o)
@@ -155,22 +167,39 @@ __device__ __forceinline__ int mesh_of(const int64_t* __restrict__ pos_prefix, i
 }
 
 // x (original dof order of every mesh) -> xg[p][r][a] (cluster order, G
-// right-hand sides interleaved, a padded to 4)
+// right-hand sides interleaved, a padded to 4).  With xmax (G <= 32), also
+// max |xg| of each vector, as the bits of a non-negative float (ordered like
+// the values), for the power-of-two scales of the tensor-core kernels.
 template <class TA>
 __global__ void gather_kernel(const MeshDev* __restrict__ meshes, int nmesh, const int64_t* __restrict__ pos_prefix,
-                              int64_t npos, const double* __restrict__ x, int64_t ld, TA* __restrict__ xg, int G)
+                              int64_t npos, const double* __restrict__ x, int64_t ld, TA* __restrict__ xg, int G,
+                              int* __restrict__ xmax)
 {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= npos * G) return;
+    const bool in = idx < npos * G;
     const int64_t p = idx / G;
     const int r = (int)(idx - p * G);
-    const int m = mesh_of(pos_prefix, nmesh, p);
-    const MeshDev& md = meshes[m];
-    const size_t src = (size_t)r * ld + md.xoff + 3 * (size_t)md.perm[p - pos_prefix[m]];
-    TA* d = xg + (size_t)idx * 4;
+    float mx = 0.0f;
+    if (in) {
+        const int m = mesh_of(pos_prefix, nmesh, p);
+        const MeshDev& md = meshes[m];
+        const size_t src = (size_t)r * ld + md.xoff + 3 * (size_t)md.perm[p - pos_prefix[m]];
+        TA* d = xg + (size_t)idx * 4;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) d[a] = (TA)x[src + a];
-    d[3] = (TA)0;
+        for (int a = 0; a < 3; ++a) {
+            const TA v = (TA)x[src + a];
+            d[a] = v;
+            mx = fmaxf(mx, fabsf((float)v));
+        }
+        d[3] = (TA)0;
+    }
+    if (xmax == nullptr) return;
+    __shared__ int smx[32];
+    if (threadIdx.x < 32) smx[threadIdx.x] = 0;
+    __syncthreads();
+    if (in && mx > 0.0f) atomicMax(&smx[r], __float_as_int(mx));
+    __syncthreads();
+    if ((int)threadIdx.x < G && smx[threadIdx.x] > 0) atomicMax(xmax + threadIdx.x, smx[threadIdx.x]);
 }
 
 // ---------------------------------------------------------------- phase 1
@@ -244,13 +273,13 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_group_kernel(
     const MeshDev& md = ONE ? m0 : meshes[gp.mesh];
     const int tid = threadIdx.x;
     for (int i = tid; i < gp.nrec; i += T) srec[i] = recs[gp.first + i];
-    const TF* Vg = static_cast<const TF*>(md.Vr) + gp.vbase + (size_t)un.j0 * gp.Cs;
+    const TF* Vg = static_cast<const TF*>(md.Vr) + gp.vbase;
     const TA* x0 = xg + ((size_t)md.xgoff + gp.s0 + un.j0) * G * 4;
     TA* wr = w + (size_t)md.woff * G * 4;
     const float* SU = md.SU;
     const TA c1 = (TA)md.c1, c2 = (TA)md.c2;
     const int Cs = gp.Cs, n = un.nrows;
-    const int Q = Cs / VEC;
+    const int Q = un.ncols / VEC;  // column vectors of this unit (from column un.c0)
     const int NRC = (G + RC - 1) / RC;
     const int pairs = Q * NRC;
     const int rows = max(1, (int)(kFwdXsBytes / sizeof(TA)) / (G * 4));  // x rows per staged chunk
@@ -269,7 +298,7 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_group_kernel(
         for (int e = 0; e < VEC; ++e)
 #pragma unroll
             for (int k = 0; k < RC; ++k) acc[e][k][0] = acc[e][k][1] = acc[e][k][2] = (TA)0;
-        const TF* vp = Vg + (size_t)q * VEC;
+        const int cq = un.c0 + q * VEC;
         for (int j0 = 0; j0 < n; j0 += rows) {
             const int nrows = min(rows, n - j0);
             __syncthreads();  // the previous chunk is consumed
@@ -286,7 +315,7 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_group_kernel(
 #pragma unroll 4
                 for (int jj = g; jj < nrows; jj += GG) {
                     TA v[VEC];
-                    Vec16<TF, TA>::load(vp + (size_t)(j0 + jj) * Cs, v);
+                    Vec16<TF, TA>::load(Vg + vel<TF>(un.j0 + j0 + jj, cq, Cs), v);
                     const TA* xr = xs + ((size_t)jj * G + c * RC) * 4;
 #pragma unroll
                     for (int k = 0; k < RC; ++k) {
@@ -321,7 +350,7 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_group_kernel(
              idx += (GG > 1 ? T : 1)) {
             // GG == 1: this thread's own pair; GG > 1: (pair, column, vector) items
             const int pp = GG > 1 ? idx / (VEC * RC) : pl;
-            const int q2 = (pr0 + pp) % Q, c2i = (pr0 + pp) / Q;
+            const int q2 = (pr0 + pp) % Q + un.c0 / VEC, c2i = (pr0 + pp) / Q;
             // the block of column vector q2: the last record with offset <= q2 VEC
             int lo = 0, hi = gp.nrec - 1;
             while (lo < hi) {
@@ -376,13 +405,22 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_group_kernel(
 
 constexpr int kThreads = 128;  // per-block forward kernels
 
+}  // namespace
+}  // namespace hm
+
+#include "hm_fwd_tc.cuh"
+
+namespace hm {
+namespace {
+
 // pointers of block `rec` of its mesh.  ONE: the plan
 // has a single mesh, passed by value as a kernel parameter (no dependent load
 // of the mesh table before the first load of V).
 template <class TF, class TA, bool ONE>
 struct FwdArgs {
-    const TF* Vb;
-    int64_t ld;  // row stride of V (the group's Cs)
+    const TF* Vb;  // V of the block's group
+    int coff;      // first column of the block in the group
+    int ld;        // columns of the group (Cs)
     const TA* x0;
     TA* wr;
     const float* SU;
@@ -392,7 +430,8 @@ struct FwdArgs {
     {
         const MeshDev& md = ONE ? m0 : meshes[rec.mesh];
         const FwdGroup gp = groups[rec.grp];
-        Vb = static_cast<const TF*>(md.Vr) + gp.vbase + rec.coff;
+        Vb = static_cast<const TF*>(md.Vr) + gp.vbase;
+        coff = rec.coff;
         ld = gp.Cs;
         x0 = xg + ((size_t)md.xgoff + rec.s0) * G * 4;
         wr = w + (size_t)md.woff * G * 4;
@@ -433,12 +472,12 @@ __device__ __forceinline__ void fwd_multi_block(const FwdRec& rec, const FwdArgs
 #pragma unroll
             for (int k = 0; k < RC; ++k) acc[e][k][0] = acc[e][k][1] = acc[e][k][2] = (TA)0;
         if (active) {
-            const TF* vp = fa.Vb + (size_t)q * VEC;
+            const int cq = fa.coff + q * VEC;
             const TA* xp = fa.x0 + (size_t)c * RC * 4;
 #pragma unroll 2
             for (int j = g; j < rec.n; j += GG) {
                 TA v[VEC];
-                Vec16<TF, TA>::load(vp + (size_t)j * fa.ld, v);
+                Vec16<TF, TA>::load(fa.Vb + vel<TF>(j, cq, fa.ld), v);
                 const TA* xr = xp + (size_t)j * G * 4;
 #pragma unroll
                 for (int k = 0; k < RC; ++k) {
@@ -568,28 +607,6 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_reduce_kernel(
     }
 }
 
-// max |x| of each of the G vectors of a launch (rows of n dofs at stride ld),
-// as the bits of a non-negative float (ordered like the values)
-__global__ void absmax_kernel(const double* __restrict__ x, int64_t ld, int64_t n, int* __restrict__ out)
-{
-    const int r = blockIdx.y;
-    double mx = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        mx = fmax(mx, fabs(x[(size_t)r * ld + i]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    __shared__ double red[32];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
-        // rounded up to FP32 so that the bound stays a bound
-        float f = (float)mx;
-        if ((double)f < mx) f = nextafterf(f, INFINITY);
-        atomicMax(out + r, __float_as_int(f));
-    }
-}
-
 // max over the factor columns of (column scale of U) x |s| of the column's block
 __global__ void wbound_kernel(const FwdRec* __restrict__ recs, int64_t nrec, const float* __restrict__ SU,
                               int* __restrict__ out)
@@ -604,6 +621,40 @@ __global__ void wbound_kernel(const FwdRec* __restrict__ recs, int64_t nrec, con
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_int(mx));
+}
+
+// Column descriptors of the tensor-core forward pass (one warp per block
+// record): for every column of a forward group the factor column it feeds,
+// the components of z its kernel takes (as write_w) and the factor c su;
+// padding columns are marked kFdSkip
+__global__ void fdesc_kernel(const FwdRec* __restrict__ recs, int64_t nrec, const FwdGroup* __restrict__ groups,
+                             const float* __restrict__ SU, float c1, float c2, uint2* __restrict__ desc)
+{
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= nrec) return;
+    const FwdRec rec = recs[b];
+    const int64_t base = (int64_t)groups[rec.grp].dbase + rec.coff;
+    const int Cp = (rec.C + 7) & ~7;
+    for (int c = lane; c < Cp; c += 32) {
+        uint2 d = make_uint2(kFdSkip, 0u);
+        if (c < rec.C) {
+            int kern = 0, l = c;
+            for (;;) {
+                const int k = (int)((rec.kpack >> (8 * kern)) & 0xff);
+                if (l < k) break;
+                l -= k;
+                ++kern;
+            }
+            const int64_t col = (int64_t)rec.col0 + c;
+            int p, pq;
+            kern_pq(kern, p, pq);
+            const float f = (kern == 0 ? c1 : c2) * SU[col];
+            const uint32_t pp = kern == 0 ? 3u : (uint32_t)p, qq = kern == 0 ? 3u : (uint32_t)pq;
+            d = make_uint2((uint32_t)col | (pp << 28) | (qq << 30), __float_as_uint(f));
+        }
+        desc[base + c] = d;
+    }
 }
 
 // ---------------------------------------------------------------- packing
@@ -676,12 +727,18 @@ __global__ void pack_ul_kernel(const int32_t* __restrict__ leaf, const int64_t* 
     }
 }
 
-// V row-major in its forward group (row stride ld[b]): one CTA per block
+// V in its forward group (ld[b] = the group's Cs columns, the block at
+// column vb_coff[b]): one CTA per block.  16-bit forms: 8 x 8 tiles, row group
+// j / 8 and column group c / 8 at ((j / 8) * Cs / 8 + c / 8) * 64 + (j % 8) * 8
+// + c % 8 (eight columns of one row stay 16 contiguous bytes; the tiles are
+// the core matrices of an MN-major tensor-core operand).  Other forms:
+// row-major, j * Cs + c.
 template <class T>
 __global__ void pack_vr_kernel(const Blk* __restrict__ blks, const int32_t* __restrict__ rank,
                                const int64_t* __restrict__ voff, const int64_t* __restrict__ coff,
                                const int64_t* __restrict__ vb_base, const int64_t* __restrict__ vb_ld,
-                               const double* __restrict__ V, const float* __restrict__ SV, T* __restrict__ Vr)
+                               const int64_t* __restrict__ vb_coff, const double* __restrict__ V,
+                               const float* __restrict__ SV, T* __restrict__ Vr)
 {
     const int b = blockIdx.x;
     const Blk bk = blks[b];
@@ -694,7 +751,7 @@ __global__ void pack_vr_kernel(const Blk* __restrict__ blks, const int32_t* __re
     const int C = kp[7], Cp = (C + 7) & ~7;
     if (C == 0) return;
     T* dst = Vr + vb_base[b];
-    const int64_t ld = vb_ld[b];
+    const int64_t ld = vb_ld[b], cb = vb_coff[b];
     const int64_t col0 = coff[(size_t)b * 7];
     for (int64_t e = threadIdx.x; e < (int64_t)bk.n * Cp; e += blockDim.x) {
         const int j = (int)(e / Cp), c = (int)(e - (int64_t)j * Cp);
@@ -706,7 +763,10 @@ __global__ void pack_vr_kernel(const Blk* __restrict__ blks, const int32_t* __re
             v = V[voff[(size_t)b * 7 + kern] + (size_t)l * bk.n + j];
             if (SV) v /= (double)SV[col0 + c];
         }
-        dst[(size_t)j * ld + c] = cvt<T>(v);
+        const int64_t cc = cb + c;
+        const size_t o = sizeof(T) == 2 ? ((size_t)(j >> 3) * (size_t)(ld >> 3) + (size_t)(cc >> 3)) * 64 + (j & 7) * 8 + (cc & 7)
+                                        : (size_t)j * ld + cc;
+        dst[o] = cvt<T>(v);
     }
 }
 
@@ -780,13 +840,60 @@ int stream_launch(StreamLaunch& out)
     return HM_OK;
 }
 
+// fewest vectors of a launch that take the forward pass of the 16-bit forms
+// to the tensor cores
+constexpr int kFwdTcMinG = 2;
+
+template <class TF>
+constexpr bool fwd_on_tc(int G)
+{
+    return sizeof(TF) == 2 && G >= kFwdTcMinG;
+}
+
+// The forward pass of the 16-bit forms on the tensor cores: one persistent
+// launch over every unit per 16 vectors, then the second pass of the tall
+// groups.  xmax holds max |xg| of each vector (from the gather).
+template <class TF>
+int run_forward_tc(const Plan& P, const float* xg, float* w, float* z, int G, const int* xmax, cudaStream_t s)
+{
+    constexpr int kMaxDevices = 64;
+    static int nsm_cache[kMaxDevices][2];
+    int dev = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    const bool one = P.nmesh == 1;
+    auto kern = one ? stream::fwd_tc_kernel<TF, true> : stream::fwd_tc_kernel<TF, false>;
+    int nsm = dev < kMaxDevices ? nsm_cache[dev][one] : 0;
+    if (nsm == 0) {
+        HM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stream::fp_smem()));
+        HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        if (dev < kMaxDevices) nsm_cache[dev][one] = nsm;
+    }
+    if (P.nunits > INT32_MAX) return fail(HM_EINVAL, "forward pass: too many units");
+    const MeshDev m0 = one ? P.mesh0 : MeshDev{};
+    const unsigned grid = (unsigned)std::min<int64_t>(P.nunits, nsm);  // one CTA per SM (all of its TMEM)
+    for (int r0 = 0; r0 < G; r0 += stream::kTcMaxG) {
+        kern<<<grid, stream::kFpThreads, stream::fp_smem(), s>>>(P.units, (int)P.nunits, P.groups, m0, P.meshes, xg,
+                                                                 w, z, G, r0, xmax, P.err);
+        HM_CUDA(cudaGetLastError());
+    }
+    if (P.nmulti > 0) {
+        auto red = one ? fwd_reduce_kernel<float, true> : fwd_reduce_kernel<float, false>;
+        red<<<(unsigned)P.nmulti, kFwdThreads, 0, s>>>(P.multi, P.groups, P.fwd, m0, P.meshes, z, w, G);
+        HM_CUDA(cudaGetLastError());
+    }
+    return HM_OK;
+}
+
 // The forward pass over every unit of the plan (with a fork schedule the
 // unit list is split in two halves on two streams), then the second pass of
-// the tall groups.
+// the tall groups.  Several vectors of a 16-bit form go to the tensor cores.
 template <class TF, class TA, int RC>
-int run_forward(const Plan& P, TA* xg, TA* w, TA* z, int G, cudaStream_t s, const Sched& sc)
+int run_forward(const Plan& P, TA* xg, TA* w, TA* z, int G, const int* xmax, cudaStream_t s, const Sched& sc)
 {
     if (P.nunits <= 0) return HM_OK;
+    if constexpr (sizeof(TF) == 2 && std::is_same<TA, float>::value) {
+        if (fwd_on_tc<TF>(G)) return run_forward_tc<TF>(P, xg, w, z, G, xmax, s);
+    }
     const bool one = P.nmesh == 1;
     const MeshDev m0 = one ? P.mesh0 : MeshDev{};
     if (RC > 1) {
@@ -844,15 +951,17 @@ int run_phases(const Plan& P, const double* x, double* y, int G, int64_t ld, TA*
                cudaStream_t s, const hm_matrix* prof, const Sched& sc)
 {
     if (prof) prof_mark(*prof, 0, s);
+    int* xmax = fwd_on_tc<TF>(G) ? P.counters + 64 : nullptr;
+    if (xmax) HM_CUDA(cudaMemsetAsync(xmax, 0, (size_t)G * sizeof(int), s));
     if (P.npos > 0) {
         const int64_t n = P.npos * G;
         gather_kernel<TA><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P.meshes, P.nmesh, P.pos_prefix, P.npos, x,
-                                                                      ld, xg, G);
+                                                                      ld, xg, G, xmax);
         HM_CUDA(cudaGetLastError());
     }
     if (prof) prof_mark(*prof, 1, s);
     {
-        int rc = run_forward<TF, TA, RC>(P, xg, w, static_cast<TA*>(P.z), G, s, sc);
+        int rc = run_forward<TF, TA, RC>(P, xg, w, static_cast<TA*>(P.z), G, xmax, s, sc);
         if (rc) return rc;
     }
     if (prof) prof_mark(*prof, 2, s);
@@ -906,17 +1015,15 @@ int run_phases_tc(const Plan& P, const double* x, double* y, int G, int64_t ld, 
     constexpr int RC = multi_rc<TF, float>();
     if (prof) prof_mark(*prof, 0, s);
     HM_CUDA(cudaMemsetAsync(xmax, 0, (size_t)G * sizeof(int), s));
-    absmax_kernel<<<dim3(64, (unsigned)G), 256, 0, s>>>(x, ld, 3 * P.npos, xmax);
-    HM_CUDA(cudaGetLastError());
     if (P.npos > 0) {
         const int64_t n = P.npos * G;
         gather_kernel<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P.meshes, P.nmesh, P.pos_prefix, P.npos, x,
-                                                                         ld, xg, G);
+                                                                         ld, xg, G, xmax);
         HM_CUDA(cudaGetLastError());
     }
     if (prof) prof_mark(*prof, 1, s);
     {
-        int rc = run_forward<TF, float, RC>(P, xg, w, static_cast<float*>(P.z), G, s, sc);
+        int rc = run_forward<TF, float, RC>(P, xg, w, static_cast<float*>(P.z), G, xmax, s, sc);
         if (rc) return rc;
     }
     if (prof) prof_mark(*prof, 2, s);
@@ -989,6 +1096,7 @@ int pack_form(hm_matrix& H, int form, const float* SU, const float* SV, cudaStre
     int rc;
     if ((rc = dalloc(H, H.Ul[form], (size_t)H.ul_total * sizeof(T)))) return rc;
     if ((rc = dalloc(H, H.Vr[form], (size_t)H.vr_total * sizeof(T)))) return rc;
+    HM_CUDA(cudaMemsetAsync(H.Vr[form].p, 0, (size_t)H.vr_total * sizeof(T), s));  // padding rows and columns
     // padding segments are zero
     HM_CUDA(cudaMemsetAsync(H.Ul[form].p, 0, (size_t)H.ul_total * sizeof(T), s));
     if (H.nleaves > 0) {
@@ -1001,7 +1109,8 @@ int pack_form(hm_matrix& H, int form, const float* SU, const float* SV, cudaStre
     if (H.nadm > 0) {
         pack_vr_kernel<T><<<(unsigned)H.nadm, 256, 0, s>>>(
             H.d_adm.as<Blk>(), H.d_rank.as<int32_t>(), H.d_voff.as<int64_t>(), H.d_coff.as<int64_t>(),
-            H.d_vb_base.as<int64_t>(), H.d_vb_ld.as<int64_t>(), H.V64.as<double>(), SV, H.Vr[form].as<T>());
+            H.d_vb_base.as<int64_t>(), H.d_vb_ld.as<int64_t>(), H.d_vb_coff.as<int64_t>(), H.V64.as<double>(), SV,
+            H.Vr[form].as<T>());
         HM_CUDA(cudaGetLastError());
     }
     return HM_OK;
@@ -1074,6 +1183,7 @@ MeshDev mesh_desc(const hm_matrix& H, int32_t form)
     m.Vr = H.Vr[form].p;
     m.Nl = form == HM_FP64 ? H.Nl64.p : H.Nl32.p;
     m.SU = (form == HM_BF16 || form == HM_FP16) ? H.SU.as<float>() : nullptr;
+    m.fdesc = (form == HM_BF16 || form == HM_FP16) ? H.fdesc.as<uint2>() : nullptr;
     m.leaf = H.d_leaf.as<int32_t>();
     m.lf_base = H.d_lf_base.as<int64_t>();
     m.lf_ptr = H.d_lf_ptr.as<int32_t>();
@@ -1188,6 +1298,19 @@ int pack_device(hm_matrix& H, int32_t form, cudaStream_t s)
                     ntask, H.d_adm.as<Blk>(), H.d_rank.as<int32_t>(), H.d_uoff.as<int64_t>(),
                     H.d_voff.as<int64_t>(), H.d_coff.as<int64_t>(), H.U64.as<double>(),
                     H.V64.as<double>(), H.SU.as<float>(), H.SV.as<float>());
+                HM_CUDA(cudaGetLastError());
+            }
+        }
+        if (!H.fdesc.p) {
+            if (H.c_total > kFdMaxCol) return fail(HM_EINVAL, "16-bit forms: more than %lld factor columns", (long long)kFdMaxCol);
+            if ((rc = dalloc(H, H.fdesc, (size_t)std::max<int64_t>(H.dcols, 1) * sizeof(uint2)))) return rc;
+            const int64_t nrec = (int64_t)H.fwd_h.size();
+            if (nrec > 0) {
+                const MeshDev m = mesh_desc(H, HM_FP64);
+                fdesc_kernel<<<(unsigned)((nrec + 7) / 8), 256, 0, s>>>(H.d_fwd_all.as<FwdRec>(), nrec,
+                                                                        H.d_groups.as<FwdGroup>(), H.SU.as<float>(),
+                                                                        (float)m.c1, (float)m.c2,
+                                                                        H.fdesc.as<uint2>());
                 HM_CUDA(cudaGetLastError());
             }
         }
