@@ -699,6 +699,28 @@ struct TmpBuf {
 }  // namespace
 
 // ------------------------------------------------------------------------
+std::vector<FwdTcUnit> tc_units(const std::vector<FwdUnit>& units, const std::vector<FwdGroup>& groups)
+{
+    std::vector<FwdTcUnit> out(units.size());
+    for (size_t i = 0; i < units.size(); ++i) {
+        const FwdUnit& u = units[i];
+        const FwdGroup& g = groups[(size_t)u.group];
+        FwdTcUnit t{};
+        // the unit's tiles are contiguous: after the full row chunks above it
+        // and the units to its left in its row chunk (16-bit layout of V)
+        t.v0 = g.vbase + (int64_t)u.j0 * g.Cs + (int64_t)((u.nrows + 15) & ~15) * u.c0;
+        t.z0 = u.zcol0 >= 0 ? u.zcol0 + (int64_t)u.chunk * g.Cs + u.c0 : -1;
+        t.x0 = g.s0 + u.j0;
+        t.d0 = g.dbase + u.c0;
+        t.ld8 = u.ncols * 8;
+        t.nrows = (int16_t)u.nrows;
+        t.ncols = (int16_t)u.ncols;
+        t.mesh = g.mesh;
+        out[i] = t;
+    }
+    return out;
+}
+
 int assemble_device(const hm_tree& tr, hm_matrix& H)
 {
     cudaStream_t s = H.alloc.stream;
@@ -1252,6 +1274,10 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
         if ((rc = upload(H, H.d_big, bigv.data(), bigv.size() * 4))) return rc;
         if ((rc = upload(H, H.d_small, smallv.data(), smallv.size() * 4))) return rc;
         if ((rc = upload(H, H.d_units, units.data(), units.size() * sizeof(FwdUnit)))) return rc;
+        {
+            const std::vector<FwdTcUnit> tcu = tc_units(units, groups);
+            if ((rc = upload(H, H.d_tcunits, tcu.data(), tcu.size() * sizeof(FwdTcUnit)))) return rc;
+        }
         if ((rc = upload(H, H.d_multi, multi.data(), multi.size() * sizeof(FwdMulti)))) return rc;
         if ((rc = upload(H, H.d_fwd_all, recs.data(), recs.size() * sizeof(FwdRec)))) return rc;
         if ((rc = upload(H, H.d_groups, groups.data(), groups.size() * sizeof(FwdGroup)))) return rc;

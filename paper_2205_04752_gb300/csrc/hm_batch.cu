@@ -29,7 +29,7 @@ struct hm_batch {
     std::vector<int64_t> pos_prefix;  // nmat + 1 cluster positions
     std::vector<hm::MeshDev> mesh_h;
     hm::Allocator alloc;
-    hm::DevBuf d_mesh, d_pos_prefix, d_fwd, d_groups, d_units, d_multi, d_big, d_small, d_work[2], xg, w, z, counters,
+    hm::DevBuf d_mesh, d_pos_prefix, d_fwd, d_groups, d_units, d_tcunits, d_multi, d_big, d_small, d_work[2], xg, w, z, counters,
         err;
     hm_schedule sched{};
     cudaStream_t side = nullptr, cap = nullptr;
@@ -67,7 +67,7 @@ void batch_free(hm_batch* B)
 {
     if (!B) return;
     if (B->gexec) cudaGraphExecDestroy(B->gexec);
-    for (DevBuf* b : {&B->d_mesh, &B->d_pos_prefix, &B->d_fwd, &B->d_groups, &B->d_units, &B->d_multi, &B->d_big,
+    for (DevBuf* b : {&B->d_mesh, &B->d_pos_prefix, &B->d_fwd, &B->d_groups, &B->d_units, &B->d_tcunits, &B->d_multi, &B->d_big,
                       &B->d_small, &B->d_work[0],
                       &B->d_work[1], &B->xg, &B->w, &B->z,
                       &B->counters, &B->err})
@@ -90,6 +90,7 @@ Plan make_plan(const hm_batch& B)
     P.fwd = B.d_fwd.as<FwdRec>();
     P.groups = B.d_groups.as<FwdGroup>();
     P.units = B.d_units.as<FwdUnit>();
+    P.tcu = B.d_tcunits.as<FwdTcUnit>();
     P.nunits = B.nunits;
     P.multi = B.d_multi.as<FwdMulti>();
     P.nmulti = B.nmulti;
@@ -243,6 +244,7 @@ int hm_batch_create(const hm_matrix* const* mats, int32_t nmat, int32_t form, in
     B->nsmall = (int64_t)smallv.size();
     B->ngroups = (int64_t)groups.size();
     B->nunits = (int64_t)units.size();
+    const std::vector<FwdTcUnit> tcu = tc_units(units, groups);
     B->nmulti = (int64_t)multi.size();
     B->zcols = zc;
 
@@ -276,6 +278,7 @@ int hm_batch_create(const hm_matrix* const* mats, int32_t nmat, int32_t form, in
         (rc = bupload(*B, B->d_fwd, fwd.data(), fwd.size() * sizeof(FwdRec))) ||
         (rc = bupload(*B, B->d_groups, groups.data(), groups.size() * sizeof(FwdGroup))) ||
         (rc = bupload(*B, B->d_units, units.data(), units.size() * sizeof(FwdUnit))) ||
+        (rc = bupload(*B, B->d_tcunits, tcu.data(), tcu.size() * sizeof(FwdTcUnit))) ||
         (rc = bupload(*B, B->d_multi, multi.data(), multi.size() * sizeof(FwdMulti))) ||
         (rc = bupload(*B, B->d_big, bigv.data(), bigv.size() * 4)) ||
         (rc = bupload(*B, B->d_small, smallv.data(), smallv.size() * 4)) ||

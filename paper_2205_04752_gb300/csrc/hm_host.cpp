@@ -490,7 +490,7 @@ int hm_footprint(const hm_matrix* H, int64_t* bytes)
     const hm::DevBuf* bufs[] = {&H->d_perm, &H->d_adm, &H->d_near, &H->d_rank, &H->d_uoff, &H->d_voff,
                                 &H->d_coff, &H->d_noff, &H->d_leaf, &H->d_lf_base, &H->d_lf_ptr,
                                 &H->d_lf_items, &H->d_lf_src, &H->d_ln_base, &H->d_ln_ptr, &H->d_ln_items,
-                                &H->d_ln_src, &H->d_vb_base, &H->d_vb_ld, &H->d_vb_coff, &H->fdesc, &H->d_groups, &H->d_units, &H->d_multi, &H->d_big, &H->d_small, &H->d_fwd_all, &H->d_work, &H->d_pos_prefix,
+                                &H->d_ln_src, &H->d_vb_base, &H->d_vb_ld, &H->d_vb_coff, &H->fdesc, &H->d_groups, &H->d_units, &H->d_tcunits, &H->d_multi, &H->d_big, &H->d_small, &H->d_fwd_all, &H->d_work, &H->d_pos_prefix,
                                 &H->d_mesh[0], &H->d_mesh[1], &H->d_mesh[2], &H->d_mesh[3], &H->d_counters,
                                 &H->d_err, &H->U64, &H->V64, &H->N64, &H->Ul[0], &H->Ul[1], &H->Ul[2],
                                 &H->Ul[3], &H->Vr[0], &H->Vr[1], &H->Vr[2], &H->Vr[3], &H->Nl64, &H->Nl32,
@@ -510,7 +510,7 @@ void hm_matrix_destroy(hm_matrix* H)
     hm::DevBuf* bufs[] = {&H->d_perm, &H->d_adm, &H->d_near, &H->d_rank, &H->d_uoff, &H->d_voff,
                           &H->d_coff, &H->d_noff, &H->d_leaf, &H->d_lf_base, &H->d_lf_ptr,
                           &H->d_lf_items, &H->d_lf_src, &H->d_ln_base, &H->d_ln_ptr, &H->d_ln_items,
-                          &H->d_ln_src, &H->d_vb_base, &H->d_vb_ld, &H->d_vb_coff, &H->fdesc, &H->d_groups, &H->d_units, &H->d_multi, &H->d_big, &H->d_small, &H->d_fwd_all, &H->d_work, &H->d_pos_prefix, &H->d_mesh[0], &H->d_mesh[1], &H->d_mesh[2],
+                          &H->d_ln_src, &H->d_vb_base, &H->d_vb_ld, &H->d_vb_coff, &H->fdesc, &H->d_groups, &H->d_units, &H->d_tcunits, &H->d_multi, &H->d_big, &H->d_small, &H->d_fwd_all, &H->d_work, &H->d_pos_prefix, &H->d_mesh[0], &H->d_mesh[1], &H->d_mesh[2],
                           &H->d_mesh[3], &H->d_counters, &H->d_err, &H->U64, &H->V64, &H->N64,
                           &H->Ul[0], &H->Ul[1], &H->Ul[2], &H->Ul[3], &H->Vr[0], &H->Vr[1],
                           &H->Vr[2], &H->Vr[3], &H->Nl64, &H->Nl32, &H->SU, &H->SV, &H->xg, &H->wb, &H->zb,

@@ -104,8 +104,8 @@ struct FwdRec {
     uint64_t kpack;  // rank of kernel q in bits 8q .. 8q+7
 };
 // the blocks that share a column cluster: V of all of them as one n x Cs
-// matrix at element offset vbase (row-major, or 8 x 8 tiles for the 16-bit
-// forms); records first .. first + nrec - 1; the column descriptors of the
+// matrix at element offset vbase (row-major, or unit-contiguous 8 x 8 tiles
+// for the 16-bit forms); records first .. first + nrec - 1; the column descriptors of the
 // 16-bit tensor-core forward pass at dbase .. dbase + Cs - 1
 struct FwdGroup {
     int64_t vbase;
@@ -137,6 +137,18 @@ struct FwdMulti {
 };
 constexpr int kFwdUnitRows = 256;
 constexpr int kFwdUnitCols = 256;
+// a unit as the tensor-core forward pass reads it: one load, no dependent
+// load of its group (the fields are mesh relative but z0)
+struct FwdTcUnit {
+    int64_t v0;   // element offset in the mesh's V of the unit's contiguous 8 x 8 tiles
+    int64_t z0;   // z column of the unit's first column, -1 for a one-unit group
+    int32_t x0;   // first gathered-x position (group s0 + j0)
+    int32_t d0;   // first column descriptor (group dbase + c0)
+    int32_t ld8;  // elements from one 8-row core row of the unit to the next (ncols * 8)
+    int16_t nrows, ncols;
+    int32_t mesh, pad;
+};
+std::vector<FwdTcUnit> tc_units(const std::vector<FwdUnit>& units, const std::vector<FwdGroup>& groups);
 
 // Device-side description of one mesh taking part in a product (a single
 // matrix is a product over one mesh; a batch concatenates several).  Stream
@@ -175,6 +187,7 @@ struct Plan {
     const FwdRec* fwd;          // the block records of every group
     const FwdGroup* groups;     // forward groups (records indexed over all meshes)
     const FwdUnit* units;       // nunits CTAs of the forward pass
+    const FwdTcUnit* tcu;       // the same units for the tensor-core forward pass
     int64_t nunits;
     const FwdMulti* multi;      // nmulti groups added by the second pass
     int64_t nmulti;
@@ -233,6 +246,7 @@ struct hm_matrix {
     hm::DevBuf d_fwd_all;                // FwdRec of every block, group by group
     hm::DevBuf d_groups;                 // FwdGroup
     hm::DevBuf d_units, d_multi;         // FwdUnit (the most data first), FwdMulti
+    hm::DevBuf d_tcunits;                // FwdTcUnit of d_units
     hm::DevBuf d_big, d_small;           // record indices by block height, the most data first
     std::vector<int32_t> big_h, small_h;
     std::vector<hm::FwdUnit> unit_h;

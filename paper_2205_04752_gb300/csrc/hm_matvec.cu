@@ -108,16 +108,24 @@ struct Vec16<__nv_bfloat16, TA> {
     }
 };
 
-// element offset of V[j, c] (c a multiple of 8) in a forward group of Cs
-// columns: row-major for FP64 / FP32, 8 x 8 tiles (row j / 8, column c / 8)
-// for the 16-bit forms, the layout of a tensor-core operand
+// element offset of V[j, c] (c a multiple of 8 for the vector loads) in a
+// forward group of n rows and Cs columns: row-major for FP64 / FP32; for the
+// 16-bit forms the group is cut into the units of the forward pass (rows
+// 256 k .., columns 256 m ..), each unit stored contiguously in 8 x 8 tiles
+// (row j / 8, column c / 8 of the unit), the units of a row chunk side by
+// side: one stage of 32 rows of a unit is one contiguous range, the operand
+// layout of the tensor cores
 template <class TF>
-__device__ __forceinline__ size_t vel(int j, int c, int Cs)
+__device__ __forceinline__ size_t vel(int j, int c, int Cs, int n)
 {
-    if constexpr (sizeof(TF) == 2)
-        return ((size_t)(j >> 3) * (size_t)(Cs >> 3) + (size_t)(c >> 3)) * 64 + (size_t)(j & 7) * 8;
-    else
+    if constexpr (sizeof(TF) == 2) {
+        const int k = j >> 8, jl = j & 255, c0 = c & ~255, cl = c & 255;
+        const int cu = min(256, Cs - c0), n16 = (min(256, n - (k << 8)) + 15) & ~15;
+        return (size_t)k * 256 * (size_t)Cs + (size_t)n16 * c0 +
+               ((size_t)(jl >> 3) * (size_t)(cu >> 3) + (size_t)(cl >> 3)) * 64 + (size_t)(jl & 7) * 8 + (cl & 7);
+    } else {
         return (size_t)j * (size_t)Cs + (size_t)c;
+    }
 }
 
 // R consecutive values of type T (R * sizeof(T) a multiple of 16)
@@ -315,7 +323,7 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_group_kernel(
 #pragma unroll 4
                 for (int jj = g; jj < nrows; jj += GG) {
                     TA v[VEC];
-                    Vec16<TF, TA>::load(Vg + vel<TF>(un.j0 + j0 + jj, cq, Cs), v);
+                    Vec16<TF, TA>::load(Vg + vel<TF>(un.j0 + j0 + jj, cq, Cs, gp.n), v);
                     const TA* xr = xs + ((size_t)jj * G + c * RC) * 4;
 #pragma unroll
                     for (int k = 0; k < RC; ++k) {
@@ -405,6 +413,89 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_group_kernel(
 
 constexpr int kThreads = 128;  // per-block forward kernels
 
+// One vector, 16-bit forms: the forward pass of a unit on the CUDA cores,
+// reading the unit's contiguous 8 x 8 tiles.  Lane (jr, qq) of a warp takes
+// row jr of every 8-row core row of column vector q = q0 + qq (eight
+// columns), so that a warp load covers four whole tiles (512 contiguous
+// bytes); the eight partial sums of a column vector are added across the
+// lanes (a fixed butterfly) and lane jr writes column 8 q + jr.  x of the
+// unit's rows is staged in shared memory once.
+template <class TF, bool ONE>
+__global__ void __launch_bounds__(kFwdThreads) fwd_tile1_kernel(
+    const FwdUnit* __restrict__ units, const FwdTcUnit* __restrict__ tcu, const FwdGroup* __restrict__ groups,
+    const FwdRec* __restrict__ recs, const __grid_constant__ MeshDev m0, const MeshDev* __restrict__ meshes,
+    const float* __restrict__ xg, float* __restrict__ w, float* __restrict__ z)
+{
+    __shared__ float4 xs[kFwdUnitRows];
+    __shared__ FwdRec srec[kMaxGroupRecs];
+    const FwdTcUnit tu = tcu[blockIdx.x];
+    const FwdUnit un = units[blockIdx.x];
+    const FwdGroup gp = groups[un.group];
+    const MeshDev& md = ONE ? m0 : meshes[tu.mesh];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, jr = lane & 7, qq = lane >> 3;
+    for (int i = tid; i < gp.nrec; i += kFwdThreads) srec[i] = recs[gp.first + i];
+    const float4* xsrc = reinterpret_cast<const float4*>(xg) + md.xgoff + tu.x0;
+    const int nrows = tu.nrows, n16 = (nrows + 15) & ~15;
+    for (int j = tid; j < n16; j += kFwdThreads) xs[j] = j < nrows ? xsrc[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    const TF* Vu = static_cast<const TF*>(md.Vr) + tu.v0;
+    const int cu = tu.ncols, nq = cu >> 3, nkr = n16 >> 3;
+    float* wr = w + (size_t)md.woff * 4;
+    const float c1 = (float)md.c1, c2 = (float)md.c2;
+    for (int q0 = warp * 4; q0 < nq; q0 += 16) {
+        const int q = q0 + qq;
+        float acc[8][3];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c][0] = acc[c][1] = acc[c][2] = 0.0f;
+        if (q < nq) {
+            const TF* p = Vu + (size_t)q * 64 + jr * 8;
+#pragma unroll 4
+            for (int kr = 0; kr < nkr; ++kr) {
+                float v[8];
+                Vec16<TF, float>::load(p + (size_t)kr * cu * 8, v);
+                const float4 x = xs[kr * 8 + jr];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    acc[c][0] += v[c] * x.x;
+                    acc[c][1] += v[c] * x.y;
+                    acc[c][2] += v[c] * x.z;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) acc[c][a] += __shfl_xor_sync(0xffffffffu, acc[c][a], o);
+        if (q >= nq) continue;
+        float z0 = 0.0f, z1 = 0.0f, z2 = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (c == jr) {
+                z0 = acc[c][0];
+                z1 = acc[c][1];
+                z2 = acc[c][2];
+            }
+        const int col = un.c0 + q * 8 + jr;  // column of the group
+        if (un.zcol0 >= 0) {
+            float* d = z + (size_t)(un.zcol0 + (int64_t)un.chunk * gp.Cs + col) * 4;
+            d[0] = z0;
+            d[1] = z1;
+            d[2] = z2;
+        } else {
+            int lo = 0, hi = gp.nrec - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (srec[mid].coff <= col) lo = mid;
+                else hi = mid - 1;
+            }
+            const FwdRec& rec = srec[lo];
+            if (col - rec.coff < rec.C) write_w<float>(rec, col - rec.coff, z0, z1, z2, md.SU, wr, c1, c2, 1, 0);
+        }
+    }
+}
+
 }  // namespace
 }  // namespace hm
 
@@ -477,7 +568,7 @@ __device__ __forceinline__ void fwd_multi_block(const FwdRec& rec, const FwdArgs
 #pragma unroll 2
             for (int j = g; j < rec.n; j += GG) {
                 TA v[VEC];
-                Vec16<TF, TA>::load(fa.Vb + vel<TF>(j, cq, fa.ld), v);
+                Vec16<TF, TA>::load(fa.Vb + vel<TF>(j, cq, fa.ld, rec.n), v);
                 const TA* xr = xp + (size_t)j * G * 4;
 #pragma unroll
                 for (int k = 0; k < RC; ++k) {
@@ -728,11 +819,8 @@ __global__ void pack_ul_kernel(const int32_t* __restrict__ leaf, const int64_t* 
 }
 
 // V in its forward group (ld[b] = the group's Cs columns, the block at
-// column vb_coff[b]): one CTA per block.  16-bit forms: 8 x 8 tiles, row group
-// j / 8 and column group c / 8 at ((j / 8) * Cs / 8 + c / 8) * 64 + (j % 8) * 8
-// + c % 8 (eight columns of one row stay 16 contiguous bytes; the tiles are
-// the core matrices of an MN-major tensor-core operand).  Other forms:
-// row-major, j * Cs + c.
+// column vb_coff[b]; the layout of vel: unit-contiguous 8 x 8 tiles for the
+// 16-bit forms, row-major otherwise): one CTA per block.
 template <class T>
 __global__ void pack_vr_kernel(const Blk* __restrict__ blks, const int32_t* __restrict__ rank,
                                const int64_t* __restrict__ voff, const int64_t* __restrict__ coff,
@@ -764,9 +852,7 @@ __global__ void pack_vr_kernel(const Blk* __restrict__ blks, const int32_t* __re
             if (SV) v /= (double)SV[col0 + c];
         }
         const int64_t cc = cb + c;
-        const size_t o = sizeof(T) == 2 ? ((size_t)(j >> 3) * (size_t)(ld >> 3) + (size_t)(cc >> 3)) * 64 + (j & 7) * 8 + (cc & 7)
-                                        : (size_t)j * ld + cc;
-        dst[o] = cvt<T>(v);
+        dst[vel<T>(j, (int)cc, (int)ld, bk.n)] = cvt<T>(v);
     }
 }
 
@@ -840,19 +926,17 @@ int stream_launch(StreamLaunch& out)
     return HM_OK;
 }
 
-// fewest vectors of a launch that take the forward pass of the 16-bit forms
-// to the tensor cores
-constexpr int kFwdTcMinG = 2;
-
+// a launch of several vectors of a 16-bit form takes its forward pass to
+// the tensor cores (and needs max |x| of each vector)
 template <class TF>
 constexpr bool fwd_on_tc(int G)
 {
-    return sizeof(TF) == 2 && G >= kFwdTcMinG;
+    return sizeof(TF) == 2 && G >= 2;
 }
 
 // The forward pass of the 16-bit forms on the tensor cores: one persistent
-// launch over every unit per 16 vectors, then the second pass of the tall
-// groups.  xmax holds max |xg| of each vector (from the gather).
+// launch over every unit for up to 16 vectors, then the second pass of the
+// tall groups.  xmax holds max |xg| of each vector (from the gather).
 template <class TF>
 int run_forward_tc(const Plan& P, const float* xg, float* w, float* z, int G, const int* xmax, cudaStream_t s)
 {
@@ -869,13 +953,12 @@ int run_forward_tc(const Plan& P, const float* xg, float* w, float* z, int G, co
         if (dev < kMaxDevices) nsm_cache[dev][one] = nsm;
     }
     if (P.nunits > INT32_MAX) return fail(HM_EINVAL, "forward pass: too many units");
+    if (G > stream::kTcMaxG) return fail(HM_EINVAL, "forward pass: %d vectors in one tensor-core launch", G);
     const MeshDev m0 = one ? P.mesh0 : MeshDev{};
     const unsigned grid = (unsigned)std::min<int64_t>(P.nunits, nsm);  // one CTA per SM (all of its TMEM)
-    for (int r0 = 0; r0 < G; r0 += stream::kTcMaxG) {
-        kern<<<grid, stream::kFpThreads, stream::fp_smem(), s>>>(P.units, (int)P.nunits, P.groups, m0, P.meshes, xg,
-                                                                 w, z, G, r0, xmax, P.err);
-        HM_CUDA(cudaGetLastError());
-    }
+    kern<<<grid, stream::kFpThreads, stream::fp_smem(), s>>>(P.tcu, (int)P.nunits, m0, P.meshes, P.nmesh, xg, w, z,
+                                                             G, xmax, P.err);
+    HM_CUDA(cudaGetLastError());
     if (P.nmulti > 0) {
         auto red = one ? fwd_reduce_kernel<float, true> : fwd_reduce_kernel<float, false>;
         red<<<(unsigned)P.nmulti, kFwdThreads, 0, s>>>(P.multi, P.groups, P.fwd, m0, P.meshes, z, w, G);
@@ -884,15 +967,58 @@ int run_forward_tc(const Plan& P, const float* xg, float* w, float* z, int G, co
     return HM_OK;
 }
 
+// One vector of a 16-bit form on the CUDA cores: one CTA per unit (with a
+// fork schedule the unit list is split in two halves on two streams), then
+// the second pass of the tall groups.
+template <class TF>
+int run_forward_tile1(const Plan& P, const float* xg, float* w, float* z, cudaStream_t s, const Sched& sc)
+{
+    const bool one = P.nmesh == 1;
+    const MeshDev m0 = one ? P.mesh0 : MeshDev{};
+    const bool fork = sc.side && P.nunits > 1;
+    const int64_t half = fork ? P.nunits / 2 : P.nunits;
+    auto launch = [&](int64_t first, int64_t n, cudaStream_t st) -> int {
+        if (n <= 0) return HM_OK;
+        auto kt = one ? fwd_tile1_kernel<TF, true> : fwd_tile1_kernel<TF, false>;
+        kt<<<(unsigned)n, kFwdThreads, 0, st>>>(P.units + first, P.tcu + first, P.groups, P.fwd, m0, P.meshes, xg, w,
+                                                z);
+        HM_CUDA(cudaGetLastError());
+        return HM_OK;
+    };
+    if (fork) {
+        HM_CUDA(cudaEventRecord(sc.fork, s));
+        HM_CUDA(cudaStreamWaitEvent(sc.side, sc.fork, 0));
+        int rc = launch(half, P.nunits - half, sc.side);
+        if (rc) return rc;
+    }
+    {
+        int rc = launch(0, half, s);
+        if (rc) return rc;
+    }
+    if (fork) {
+        HM_CUDA(cudaEventRecord(sc.join, sc.side));
+        HM_CUDA(cudaStreamWaitEvent(s, sc.join, 0));
+    }
+    if (P.nmulti > 0) {
+        auto red = one ? fwd_reduce_kernel<float, true> : fwd_reduce_kernel<float, false>;
+        red<<<(unsigned)P.nmulti, kFwdThreads, 0, s>>>(P.multi, P.groups, P.fwd, m0, P.meshes, z, w, 1);
+        HM_CUDA(cudaGetLastError());
+    }
+    return HM_OK;
+}
+
 // The forward pass over every unit of the plan (with a fork schedule the
 // unit list is split in two halves on two streams), then the second pass of
-// the tall groups.  Several vectors of a 16-bit form go to the tensor cores.
+// the tall groups.  The 16-bit forms read their tiles (CUDA or tensor cores).
 template <class TF, class TA, int RC>
 int run_forward(const Plan& P, TA* xg, TA* w, TA* z, int G, const int* xmax, cudaStream_t s, const Sched& sc)
 {
     if (P.nunits <= 0) return HM_OK;
     if constexpr (sizeof(TF) == 2 && std::is_same<TA, float>::value) {
-        if (fwd_on_tc<TF>(G)) return run_forward_tc<TF>(P, xg, w, z, G, xmax, s);
+        // the tiles of V: one vector on the CUDA cores, several (up to 16) on
+        // the tensor cores
+        if (G == 1) return run_forward_tile1<TF>(P, xg, w, z, s, sc);
+        return run_forward_tc<TF>(P, xg, w, z, G, xmax, s);
     }
     const bool one = P.nmesh == 1;
     const MeshDev m0 = one ? P.mesh0 : MeshDev{};
@@ -920,18 +1046,28 @@ int run_forward(const Plan& P, TA* xg, TA* w, TA* z, int G, const int* xmax, cud
         }
         return HM_OK;
     }
-    auto kern = one ? fwd_group_kernel<TF, TA, RC, true> : fwd_group_kernel<TF, TA, RC, false>;
     const bool fork = sc.side && P.nunits > 1;
     const int64_t half = fork ? P.nunits / 2 : P.nunits;
     if (fork) {
         HM_CUDA(cudaEventRecord(sc.fork, s));
         HM_CUDA(cudaStreamWaitEvent(sc.side, sc.fork, 0));
-        kern<<<(unsigned)(P.nunits - half), kFwdThreads, 0, sc.side>>>(P.units + half, P.groups, P.fwd, m0, P.meshes,
-                                                                       xg, w, z, G);
-        HM_CUDA(cudaGetLastError());
     }
-    kern<<<(unsigned)half, kFwdThreads, 0, s>>>(P.units, P.groups, P.fwd, m0, P.meshes, xg, w, z, G);
-    HM_CUDA(cudaGetLastError());
+    // the unit lists [0, half) on s and [half, nunits) on the side stream
+    auto launch = [&](int64_t first, int64_t n, cudaStream_t st) -> int {
+        if (n <= 0) return HM_OK;
+        auto kern = one ? fwd_group_kernel<TF, TA, RC, true> : fwd_group_kernel<TF, TA, RC, false>;
+        kern<<<(unsigned)n, kFwdThreads, 0, st>>>(P.units + first, P.groups, P.fwd, m0, P.meshes, xg, w, z, G);
+        HM_CUDA(cudaGetLastError());
+        return HM_OK;
+    };
+    if (fork) {
+        int rc = launch(half, P.nunits - half, sc.side);
+        if (rc) return rc;
+    }
+    {
+        int rc = launch(0, half, s);
+        if (rc) return rc;
+    }
     if (fork) {
         HM_CUDA(cudaEventRecord(sc.join, sc.side));
         HM_CUDA(cudaStreamWaitEvent(s, sc.join, 0));
@@ -1228,6 +1364,7 @@ int matvec_device_scratch(const hm_matrix& H, const double* x, double* y, int32_
     P.fwd = H.d_fwd_all.as<FwdRec>();
     P.groups = H.d_groups.as<FwdGroup>();
     P.units = H.d_units.as<FwdUnit>();
+    P.tcu = H.d_tcunits.as<FwdTcUnit>();
     P.nunits = (int64_t)H.unit_h.size();
     P.multi = H.d_multi.as<FwdMulti>();
     P.nmulti = (int64_t)H.multi_h.size();
