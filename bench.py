@@ -235,7 +235,9 @@ def run_ours(args):
     form = args.form
     H.pack(form)
     st = H.stats()
-    x = torch.tensor(inputs.uniform_rhs(3 * M, 0), device="cuda")[0]
+    x = torch.tensor(inputs.uniform_rhs(3 * M, 0, nrhs=args.nrhs), device="cuda")
+    if args.nrhs == 1:
+        x = x[0]
     y = torch.empty_like(x)
     y64 = torch.empty_like(x)
     binding.hmatvec(H, x, y64, "fp64")
@@ -276,7 +278,8 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": round(value, 3), "unit": UNIT,
                               "ms_per_step": round(ms_step, 4), "steps": args.steps,
-                              "warmup": args.warmup, "config": dict(w, form=form),
+                              "warmup": args.warmup, "config": dict(w, form=form, nrhs=args.nrhs),
+                              "vectors_per_s": round(value * args.nrhs, 2),
                               "minimal": True, "rel_err_vs_fp64_form": err_mixed}), flush=True)
         if ws > 1:
             dist.barrier()
@@ -560,10 +563,17 @@ def main():
     ap.add_argument("--minimal", action="store_true",
                     help="profiling runs: assemble, pack and time the headline product only "
                          "(no e2e, context forms, clock sampling or CPU baseline)")
+    ap.add_argument("--nrhs", type=int, default=1,
+                    help="with --minimal: right-hand sides per timed product (profiling the several-vector "
+                         "kernels)")
     ap.add_argument("--level", type=int, default=6,
                     help="icosphere level; 6 is the benchmark workload, smaller levels are for "
                          "profiling captures")
     args = ap.parse_args()
+    if args.nrhs != 1 and not args.minimal:
+        ap.error("--nrhs applies to --minimal profiling runs only")
+    if not 1 <= args.nrhs <= 32:
+        ap.error("--nrhs must be in 1..32")
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -425,31 +425,37 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
                 __syncwarp();
                 const int c = jj * 32 + lane;  // this lane's column of the unit
                 const float* bp = B + lane * kFpBld;
-                if (c < cu && zb) {
-                    for (int k = 0; k < nk; ++k)
-                        *reinterpret_cast<float4*>(zb + ((size_t)c * G + vb + k) * 4) =
-                            make_float4(bp[4 * k] * invk[k], bp[4 * k + 1] * invk[k], bp[4 * k + 2] * invk[k], 0.0f);
-                } else if (c < cu && dsc[jj].x != kFdSkip) {
-                    // the column's kernel, decoded once for the quarter's vectors:
-                    // V_pq enters y_p with x_q and (p != q) y_q with x_p
-                    const uint32_t x = dsc[jj].x;
-                    const int p = (int)((x >> 28) & 3u), pq = (int)(x >> 30);
-                    const float f = __uint_as_float(dsc[jj].y);
-                    float* d = wr + ((size_t)(x & 0x0fffffffu) * G + vb) * 4;
-                    for (int k = 0; k < nk; ++k) {
-                        const float fk = f * invk[k];
-                        const float z0 = bp[4 * k], z1 = bp[4 * k + 1], z2 = bp[4 * k + 2];
-                        float4 o;
-                        if (p == 3) {
-                            o = make_float4(fk * z0, fk * z1, fk * z2, 0.0f);
-                        } else {
-                            const float zp = p == 0 ? z0 : (p == 1 ? z1 : z2);
-                            const float zq = pq == 0 ? z0 : (pq == 1 ? z1 : z2);
-                            o = make_float4(p == 0 ? fk * zq : (pq == 0 ? fk * zp : 0.0f),
-                                            p == 1 ? fk * zq : (pq == 1 ? fk * zp : 0.0f),
-                                            p == 2 ? fk * zq : (pq == 2 ? fk * zp : 0.0f), 0.0f);
+                if (c < cu && (zb || dsc[jj].x != kFdSkip)) {
+                    // the column, decoded once for the quarter's vectors: output
+                    // component a takes component s_a of z times f_a (V_pq enters
+                    // y_p with x_q and, p != q, y_q with x_p; the third is zero)
+                    int s0 = 0, s1 = 1, s2 = 2;
+                    bool m0 = true, m1 = true, m2 = true;
+                    float f = 1.0f;
+                    float* d;
+                    if (zb) {
+                        d = zb + ((size_t)c * G + vb) * 4;
+                    } else {
+                        const uint32_t x = dsc[jj].x;
+                        const int p = (int)((x >> 28) & 3u), pq = (int)(x >> 30);
+                        f = __uint_as_float(dsc[jj].y);
+                        if (p != 3) {
+                            m0 = p == 0 || pq == 0;
+                            m1 = p == 1 || pq == 1;
+                            m2 = p == 2 || pq == 2;
+                            s0 = p == 0 ? pq : p;
+                            s1 = p == 1 ? pq : p;
+                            s2 = p == 2 ? pq : p;
                         }
-                        *reinterpret_cast<float4*>(d + 4 * k) = o;
+                        d = wr + ((size_t)(x & 0x0fffffffu) * G + vb) * 4;
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (k >= nk) break;
+                        const float fk = f * invk[k];  // a power of two times f: exact
+                        const float* bk = bp + 4 * k;
+                        *reinterpret_cast<float4*>(d + 4 * k) =
+                            make_float4(m0 ? fk * bk[s0] : 0.0f, m1 ? fk * bk[s1] : 0.0f, m2 ? fk * bk[s2] : 0.0f, 0.0f);
                     }
                 }
                 __syncwarp();

@@ -132,7 +132,8 @@ def test_multi_rhs_launches_match_single_vector_products(form):
         c.H.pack(form)
     tol = 1e-13 if form == "fp64" else 2e-6
     # 16-bit forms: 32 = two tensor-core launches of 16; 20 = one of 16 and
-    # 4 vectors on the CUDA cores; 2 and 7 on the CUDA cores only
+    # one of 4 vectors with the leaf product on the CUDA cores; 2 and 7: the
+    # forward pass on the tensor cores, the leaf product on the CUDA cores
     for nrhs in (2, 7, 20, 32):
         x = inputs.uniform_rhs(3 * c.M, 40 + nrhs, nrhs=nrhs)
         y = c.matvec(x, form)
@@ -142,27 +143,29 @@ def test_multi_rhs_launches_match_single_vector_products(form):
             assert _rel(y[r], ys) <= tol, (nrhs, r)
 
 
-@pytest.mark.parametrize("form", ["fp16", "bf16"])
-def test_tensor_core_far_field_scales_exactly(form):
-    """The tensor-core far field scales W by a power of two chosen from
-    max|x| of each vector: scaling x by 2^40 or 2^-40 scales y exactly, a zero
-    vector gives zero, and vectors of very different size share a launch."""
+@pytest.mark.parametrize("form,nrhs", [("fp16", 16), ("bf16", 16), ("fp16", 3), ("bf16", 6), ("fp16", 11)])
+def test_tensor_core_far_field_scales_exactly(form, nrhs):
+    """The tensor-core forward pass (2-16 vectors) and far field (12-16)
+    scale x and W by a power of two chosen from max|x| of each vector:
+    scaling x by 2^40 or 2^-40 scales y exactly, a zero vector gives zero,
+    and vectors of very different size share a launch.  3, 6 and 11 vectors
+    cover the lane quarters holding four, two and one copy of the vectors."""
     if "c32" not in _cache:
         V, T = inputs.icosphere(3)
         _cache["c32"] = Case(V, T, 32, max_rhs=32)
     c = _cache["c32"]
     c.H.pack(form)
-    x = inputs.uniform_rhs(3 * c.M, 91, nrhs=16)
+    x = inputs.uniform_rhs(3 * c.M, 91, nrhs=nrhs)
     y = c.matvec(x, form)
     for k in (40, -40):
         f = 2.0 ** k
         np.testing.assert_array_equal(c.matvec(x * f, form), y * f)
     xm = x.copy()
-    xm[3] = 0.0
-    xm[5] *= 2.0 ** 30
+    xm[1] = 0.0
+    xm[nrhs - 1] *= 2.0 ** 30
     ym = c.matvec(xm, form)
-    assert np.all(ym[3] == 0.0)
-    for r in (0, 5, 15):
+    assert np.all(ym[1] == 0.0)
+    for r in sorted({0, nrhs // 2, nrhs - 1} - {1}):
         ref = c.matvec(xm[r], form)[0]
         assert _rel(ym[r], ref) <= 2e-6, r
 
