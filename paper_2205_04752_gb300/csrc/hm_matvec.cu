@@ -413,47 +413,74 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_group_kernel(
 
 constexpr int kThreads = 128;  // per-block forward kernels
 
-// One vector, 16-bit forms: the forward pass of a unit on the CUDA cores,
-// reading the unit's contiguous 8 x 8 tiles.  Lane (jr, qq) of a warp takes
-// row jr of every 8-row core row of column vector q = q0 + qq (eight
-// columns), so that a warp load covers four whole tiles (512 contiguous
-// bytes); the eight partial sums of a column vector are added across the
-// lanes (a fixed butterfly) and lane jr writes column 8 q + jr.  x of the
-// unit's rows is staged in shared memory once.
+// One vector, 16-bit forms: the forward pass of a unit on the CUDA cores.
+// The unit's tiles are contiguous, so thread 0 streams them into shared
+// memory in stages of 32 rows by bulk copies (two stages in flight per CTA,
+// several CTAs per SM).  Lane (jr, qq) of warp w takes row jr of every 8-row
+// core row of column vector q = 4 w + qq, so a warp reads four whole tiles
+// (512 contiguous bytes); the eight partial sums of a column are added by a
+// fixed butterfly and lane jr writes column 8 q + jr.  x of the unit's rows
+// is staged in shared memory once.  Every wait is bounded; a CTA that gives
+// up drains its copies in flight before it returns.
+constexpr int kTile1Threads = 256;
+constexpr int kTile1Rows = 32;
+constexpr int kTile1Stage = kTile1Rows * kFwdUnitCols * 2;  // bytes of a stage (16-bit V)
+
 template <class TF, bool ONE>
-__global__ void __launch_bounds__(kFwdThreads) fwd_tile1_kernel(
+__global__ void __launch_bounds__(kTile1Threads) fwd_tile1_kernel(
     const FwdUnit* __restrict__ units, const FwdTcUnit* __restrict__ tcu, const FwdGroup* __restrict__ groups,
     const FwdRec* __restrict__ recs, const __grid_constant__ MeshDev m0, const MeshDev* __restrict__ meshes,
-    const float* __restrict__ xg, float* __restrict__ w, float* __restrict__ z)
+    const float* __restrict__ xg, float* __restrict__ w, float* __restrict__ z, int* __restrict__ err)
 {
+    __shared__ __align__(128) unsigned char vs[2][kTile1Stage];
     __shared__ float4 xs[kFwdUnitRows];
     __shared__ FwdRec srec[kMaxGroupRecs];
+    __shared__ __align__(8) uint64_t vbar[2];
     const FwdTcUnit tu = tcu[blockIdx.x];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, jr = lane & 7;
+    const int nrows = tu.nrows, n16 = (nrows + 15) & ~15, cu = tu.ncols, nq = cu >> 3;
+    const int nst = (n16 + kTile1Rows - 1) / kTile1Rows;
+    const MeshDev& md = ONE ? m0 : meshes[tu.mesh];
+    const TF* Vu = static_cast<const TF*>(md.Vr) + tu.v0;
+    auto issue = [&](int q) {
+        const uint32_t bytes = (uint32_t)(min(kTile1Rows, n16 - q * kTile1Rows) * cu * 2);
+        stream::mbar_arrive_expect_tx(&vbar[q & 1], bytes);
+        stream::bulk_g2s(vs[q & 1], Vu + (size_t)q * kTile1Rows * cu, bytes, &vbar[q & 1]);
+    };
+    if (tid == 0) {
+        stream::mbar_init(&vbar[0], 1);
+        stream::mbar_init(&vbar[1], 1);
+        stream::mbar_fence_init();
+        issue(0);
+        if (nst > 1) issue(1);
+    }
     const FwdUnit un = units[blockIdx.x];
     const FwdGroup gp = groups[un.group];
-    const MeshDev& md = ONE ? m0 : meshes[tu.mesh];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, jr = lane & 7, qq = lane >> 3;
-    for (int i = tid; i < gp.nrec; i += kFwdThreads) srec[i] = recs[gp.first + i];
+    for (int i = tid; i < gp.nrec; i += kTile1Threads) srec[i] = recs[gp.first + i];
     const float4* xsrc = reinterpret_cast<const float4*>(xg) + md.xgoff + tu.x0;
-    const int nrows = tu.nrows, n16 = (nrows + 15) & ~15;
-    for (int j = tid; j < n16; j += kFwdThreads) xs[j] = j < nrows ? xsrc[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int j = tid; j < n16; j += kTile1Threads) xs[j] = j < nrows ? xsrc[j] : make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
-    const TF* Vu = static_cast<const TF*>(md.Vr) + tu.v0;
-    const int cu = tu.ncols, nq = cu >> 3, nkr = n16 >> 3;
-    float* wr = w + (size_t)md.woff * 4;
-    const float c1 = (float)md.c1, c2 = (float)md.c2;
-    for (int q0 = warp * 4; q0 < nq; q0 += 16) {
-        const int q = q0 + qq;
-        float acc[8][3];
+    const int q = 4 * warp + (lane >> 3);  // this lane's column vector
+    float acc[8][3];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c][0] = acc[c][1] = acc[c][2] = 0.0f;
+    for (int c = 0; c < 8; ++c) acc[c][0] = acc[c][1] = acc[c][2] = 0.0f;
+    int failed = -1;  // the stage whose wait ran out
+    for (int st = 0; st < nst; ++st) {
+        const bool got = stream::mbar_wait(&vbar[st & 1], (uint32_t)(st >> 1) & 1u, err, 20, st);
+        if (!__syncthreads_and(got ? 1 : 0)) {
+            failed = st;
+            break;
+        }
         if (q < nq) {
-            const TF* p = Vu + (size_t)q * 64 + jr * 8;
-#pragma unroll 4
-            for (int kr = 0; kr < nkr; ++kr) {
+            const int nkr = min(kTile1Rows, n16 - st * kTile1Rows) >> 3;
+            const unsigned char* base = vs[st & 1];
+#pragma unroll
+            for (int kr = 0; kr < kTile1Rows / 8; ++kr) {
+                if (kr >= nkr) break;
                 float v[8];
-                Vec16<TF, float>::load(p + (size_t)kr * cu * 8, v);
-                const float4 x = xs[kr * 8 + jr];
+                stream::Smem16<TF, float>::load(
+                    reinterpret_cast<const TF*>(base) + ((size_t)(kr * nq + q) * 64 + jr * 8), v);
+                const float4 x = xs[st * kTile1Rows + kr * 8 + jr];
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     acc[c][0] += v[c] * x.x;
@@ -462,37 +489,49 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_tile1_kernel(
                 }
             }
         }
+        __syncthreads();  // the stage is consumed
+        if (tid == 0 && st + 2 < nst) issue(st + 2);
+    }
+    if (failed >= 0) {
+        // the copies in flight (stages failed and failed + 1) land before the
+        // CTA returns (bounded)
+        if (tid == 0)
+            for (int st = failed; st < min(nst, failed + 2); ++st)
+                stream::mbar_wait(&vbar[st & 1], (uint32_t)(st >> 1) & 1u, err, 21, st);
+        return;
+    }
 #pragma unroll
-        for (int o = 1; o < 8; o <<= 1)
-#pragma unroll
-            for (int c = 0; c < 8; ++c)
-#pragma unroll
-                for (int a = 0; a < 3; ++a) acc[c][a] += __shfl_xor_sync(0xffffffffu, acc[c][a], o);
-        if (q >= nq) continue;
-        float z0 = 0.0f, z1 = 0.0f, z2 = 0.0f;
+    for (int o = 1; o < 8; o <<= 1)
 #pragma unroll
         for (int c = 0; c < 8; ++c)
-            if (c == jr) {
-                z0 = acc[c][0];
-                z1 = acc[c][1];
-                z2 = acc[c][2];
-            }
-        const int col = un.c0 + q * 8 + jr;  // column of the group
-        if (un.zcol0 >= 0) {
-            float* d = z + (size_t)(un.zcol0 + (int64_t)un.chunk * gp.Cs + col) * 4;
-            d[0] = z0;
-            d[1] = z1;
-            d[2] = z2;
-        } else {
-            int lo = 0, hi = gp.nrec - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (srec[mid].coff <= col) lo = mid;
-                else hi = mid - 1;
-            }
-            const FwdRec& rec = srec[lo];
-            if (col - rec.coff < rec.C) write_w<float>(rec, col - rec.coff, z0, z1, z2, md.SU, wr, c1, c2, 1, 0);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc[c][a] += __shfl_xor_sync(0xffffffffu, acc[c][a], o);
+    if (q >= nq) return;
+    float z0 = 0.0f, z1 = 0.0f, z2 = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        if (c == jr) {
+            z0 = acc[c][0];
+            z1 = acc[c][1];
+            z2 = acc[c][2];
         }
+    const int col = un.c0 + q * 8 + jr;  // column of the group
+    if (un.zcol0 >= 0) {
+        float* d = z + (size_t)(un.zcol0 + (int64_t)un.chunk * gp.Cs + col) * 4;
+        d[0] = z0;
+        d[1] = z1;
+        d[2] = z2;
+    } else {
+        int lo = 0, hi = gp.nrec - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (srec[mid].coff <= col) lo = mid;
+            else hi = mid - 1;
+        }
+        const FwdRec& rec = srec[lo];
+        float* wr = w + (size_t)md.woff * 4;
+        if (col - rec.coff < rec.C)
+            write_w<float>(rec, col - rec.coff, z0, z1, z2, md.SU, wr, (float)md.c1, (float)md.c2, 1, 0);
     }
 }
 
@@ -980,8 +1019,8 @@ int run_forward_tile1(const Plan& P, const float* xg, float* w, float* z, cudaSt
     auto launch = [&](int64_t first, int64_t n, cudaStream_t st) -> int {
         if (n <= 0) return HM_OK;
         auto kt = one ? fwd_tile1_kernel<TF, true> : fwd_tile1_kernel<TF, false>;
-        kt<<<(unsigned)n, kFwdThreads, 0, st>>>(P.units + first, P.tcu + first, P.groups, P.fwd, m0, P.meshes, xg, w,
-                                                z);
+        kt<<<(unsigned)n, kTile1Threads, 0, st>>>(P.units + first, P.tcu + first, P.groups, P.fwd, m0, P.meshes, xg,
+                                                  w, z, P.err);
         HM_CUDA(cudaGetLastError());
         return HM_OK;
     };
