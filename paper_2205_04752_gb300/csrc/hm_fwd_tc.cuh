@@ -13,13 +13,13 @@
 //       unit is stored contiguously in 8 x 8 tiles);
 //   A = x(s) of the G vectors, scaled by a power of two t_r per vector (from
 //       max|x_r|, so that every value fits FP16) and split into hi = fp16(x
-//       t_r) and lo = fp16(x t_r - hi), in a K-major core-matrix layout.  A
-//       lane quarter q (32 rows) holds four vectors: row 32 q + 16 h + 4 k + a
-//       is component a of vector 4 (q mod nq) + k, h = 0 for hi and 1 for lo
-//       (nq = ceil(G / 4) distinct quarters; with G <= 8 the quarters repeat,
-//       and the warps that read copies of the same vectors split the
-//       columns).  The hi and lo rows of a value sit 16 TMEM lanes apart in
-//       one quarter, so each epilogue warp finishes its vectors alone.
+//       t_r) and lo = fp16(x t_r - hi): two K-major core-matrix tiles whose
+//       MMAs accumulate into the same rows (hi and lo stacked along K), so a
+//       TMEM row holds t_r times the result.  A lane quarter q (32 rows) holds
+//       eight vectors: row 32 q + 4 k + a is component a of vector
+//       8 (q mod nq) + k (nq = ceil(G / 8) distinct quarters; the quarters
+//       repeat, and the warps that read copies of the same vectors split the
+//       columns).
 // Persistent CTAs (one per SM) take the units round-robin (largest first)
 // with specialised warps:
 //   warp 0      producer: the V of every stage of every unit through a ring
@@ -51,12 +51,13 @@ constexpr int kFpThreads = 448;
 constexpr int kFpRows = 32;                          // rows (K) per stage: two MMA K steps
 constexpr int kFpCols = 256;                         // columns per unit at most (one N tile)
 constexpr int kFpVBytes = kFpRows * kFpCols * 2;     // V of a stage
-constexpr int kFpABytes = 128 * kFpRows * 2;         // A of a stage
+constexpr int kFpAHalf = 128 * kFpRows * 2;          // the hi (or lo) tile of a stage
+constexpr int kFpABytes = 2 * kFpAHalf;              // A of a stage: hi tile, lo tile
 constexpr int kFpVSlots = 7;
-constexpr int kFpASlots = 8;
+constexpr int kFpASlots = 4;
 constexpr int kFpSbo = (kFpRows / 8) * 128;          // M-direction core stride of an A tile
-constexpr int kFpBld = 17;                           // row stride of an epilogue warp's buffer
-constexpr int kFpBBytes = 32 * kFpBld * 4;           // one epilogue warp's buffer: 32 columns x 16 rows
+constexpr int kFpBld = 33;                           // row stride of an epilogue warp's buffer
+constexpr int kFpBBytes = 32 * kFpBld * 4;           // one epilogue warp's buffer: 32 columns x 32 rows
 constexpr size_t fp_smem()
 {
     return (size_t)kFpVSlots * kFpVBytes + (size_t)kFpASlots * kFpABytes + 8 * (size_t)kFpBBytes;
@@ -142,6 +143,7 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
     __shared__ __align__(8) uint64_t acce[2];            // an accumulator is read out (4 warps)
     __shared__ __align__(8) uint64_t fbar;               // drain after an abort
     __shared__ float tsc[kTcMaxG];
+    __shared__ float tinv[kTcMaxG];  // 1 / tsc (powers of two)
     __shared__ FpMesh smesh[kFpMeshes];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_sh;
@@ -149,8 +151,8 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ng = min(kTcMaxG, G);  // vectors of this launch
-    const int nq = (ng + 3) >> 2;    // distinct quarter contents
-    const int rep = 4 / nq;          // copies of each (1, 2 or 4; one quarter idle for nq = 3)
+    const int nq = (ng + 7) >> 3;    // distinct quarter contents
+    const int rep = 4 / nq;          // copies of each (4 or 2)
     auto slot_v = [&](int s) { return smem + (size_t)s * kFpVBytes; };
     auto slot_a = [&](int s) { return smem + (size_t)kFpVSlots * kFpVBytes + (size_t)s * kFpABytes; };
     if (tid == 0) {
@@ -177,6 +179,7 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
             if (xm > 0.0f && isfinite(xm)) t = exp2f(floorf(log2f(32768.0f / xm)));
         }
         tsc[tid] = t;
+        tinv[tid] = 1.0f / t;
     }
     for (int m = tid; m < (ONE ? 1 : min(nmesh, kFpMeshes)); m += kFpThreads) {
         const MeshDev& md = ONE ? m0 : meshes[m];
@@ -262,9 +265,11 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
                     const uint32_t a0 = smem_addr(slot_a(as)), b0 = smem_addr(slot_v(vs));
                     const int steps = min(kFpRows / 16, (n16 >> 4) - q * (kFpRows / 16));
                     for (int ks = 0; ks < steps; ++ks) {
-                        const uint64_t ad = tc_desc(a0 + (uint32_t)ks * 256, 128, kFpSbo);
+                        const uint64_t ah = tc_desc(a0 + (uint32_t)ks * 256, 128, kFpSbo);
+                        const uint64_t al = tc_desc(a0 + kFpAHalf + (uint32_t)ks * 256, 128, kFpSbo);
                         const uint64_t bd = tc_desc(b0 + (uint32_t)ks * 2 * kstride, kstride, 128);
-                        tc_mma(d, ad, bd, idesc, (q > 0 || ks > 0) ? 1u : 0u);
+                        tc_mma(d, ah, bd, idesc, (q > 0 || ks > 0) ? 1u : 0u);
+                        tc_mma(d, al, bd, idesc, 1u);
                     }
                     tc_commit(&vempty[vs]);
                     tc_commit(&aempty[as]);
@@ -326,15 +331,15 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
                             lw[a][i >> 1] = l0 | (l1 << 16);
                         }
                     }
-                    const int k = r & 3;
-                    for (int qq = r >> 2; qq < rep * nq; qq += nq)
+                    const int k = r & 7;
+                    for (int qq = r >> 3; qq < rep * nq; qq += nq)
 #pragma unroll
                         for (int a = 0; a < 3; ++a) {
-                            const int mh = 32 * qq + 4 * k + a, ml = mh + 16;
-                            *reinterpret_cast<uint4*>(A + (size_t)((mh >> 3) * (kFpRows / 8) + kb) * 128 +
-                                                      (mh & 7) * 16) = make_uint4(hw[a][0], hw[a][1], hw[a][2], hw[a][3]);
-                            *reinterpret_cast<uint4*>(A + (size_t)((ml >> 3) * (kFpRows / 8) + kb) * 128 +
-                                                      (ml & 7) * 16) = make_uint4(lw[a][0], lw[a][1], lw[a][2], lw[a][3]);
+                            const int m = 32 * qq + 4 * k + a;
+                            const size_t o = (size_t)((m >> 3) * (kFpRows / 8) + kb) * 128 + (m & 7) * 16;
+                            *reinterpret_cast<uint4*>(A + o) = make_uint4(hw[a][0], hw[a][1], hw[a][2], hw[a][3]);
+                            *reinterpret_cast<uint4*>(A + kFpAHalf + o) =
+                                make_uint4(lw[a][0], lw[a][1], lw[a][2], lw[a][3]);
                         }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -345,18 +350,15 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
     } else {
         // ---- epilogue: warps 6-9 take the units with an even local index
         // (accumulator 0), warps 10-13 the odd ones (accumulator 1).  The warp
-        // of quarter q reads vectors 4 (q mod nq) + k (lane l holds hi (l <
-        // 16) or lo (l >= 16) of component l % 4 of k = (l / 4) % 4) and, of
-        // the 32-column rounds of the unit, those with index = q / nq mod rep.
+        // of quarter q reads vectors 8 (q mod nq) + k (lane l holds component
+        // l % 4 of k = l / 4) and, of the 32-column rounds of the unit, those
+        // with index = q / nq mod rep.
         const int e = (warp - 6) >> 2, quarter = warp & 3;
         float* B = reinterpret_cast<float*>(smem + (size_t)kFpVSlots * kFpVBytes + (size_t)kFpASlots * kFpABytes +
                                             (size_t)(warp - 6) * kFpBBytes);
-        const int vb = 4 * (quarter % nq);                                // first vector of the quarter
-        const int nk = quarter < rep * nq ? max(0, min(4, ng - vb)) : 0;  // vectors of the quarter
+        const int vb = 8 * (quarter % nq);                                // first vector of the quarter
+        const int nk = quarter < rep * nq ? max(0, min(8, ng - vb)) : 0;  // vectors of the quarter
         const int sub = quarter / nq;                                     // this warp's share of the rounds
-        float invk[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) invk[k] = 1.0f / tsc[min(vb + k, kTcMaxG - 1)];  // powers of two: exact
         // the descriptors of this lane's columns of a unit, loaded one unit
         // ahead (when the previous unit is done with the registers)
         uint2 dsc[kFpCols / 32];
@@ -403,16 +405,8 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
                 if (jj >= nround) break;
                 if (jj % rep != sub) continue;
                 fp_ld32_wait(rv);
-                // hi + lo: lane l < 16 adds the lo row of lane l + 16
-                float v[32];
 #pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    v[c] = __uint_as_float(rv[c]);
-                    v[c] += __shfl_down_sync(0xffffffffu, v[c], 16);
-                }
-                if (lane < 16)
-#pragma unroll
-                    for (int c = 0; c < 32; ++c) B[c * kFpBld + lane] = v[c];
+                for (int c = 0; c < 32; ++c) B[c * kFpBld + lane] = __uint_as_float(rv[c]);
                 if (jj + rep >= nround) {
                     // this warp's last read of the accumulator
                     tc_fence_before();
@@ -450,9 +444,9 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
                         d = wr + ((size_t)(x & 0x0fffffffu) * G + vb) * 4;
                     }
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
+                    for (int k = 0; k < 8; ++k) {
                         if (k >= nk) break;
-                        const float fk = f * invk[k];  // a power of two times f: exact
+                        const float fk = f * tinv[vb + k];  // a power of two times f: exact
                         const float* bk = bp + 4 * k;
                         *reinterpret_cast<float4*>(d + 4 * k) =
                             make_float4(m0 ? fk * bk[s0] : 0.0f, m1 ? fk * bk[s1] : 0.0f, m2 ? fk * bk[s2] : 0.0f, 0.0f);
