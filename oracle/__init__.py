@@ -11,7 +11,10 @@ adds the pieces for which a library routine is the plain definition:
 * ``svd_rank`` / ``svd_truncate`` -- the truncated singular value
   decomposition, the best rank-k approximation (Section 2, Eckart-Young),
   computed with ``numpy.linalg.svd``;
-* ``dense_matvec`` -- y = A x with ``numpy`` on the dense Kelvin matrix.
+* ``dense_matvec`` -- y = A x with ``numpy`` on the dense Kelvin matrix;
+* ``amvm`` -- Algorithm 2 (adaptive matrix-vector multiplication, Section 3)
+  step by step on the oracle's own ACA factors, with the readings stated in
+  its docstring (per-block products are ``numpy`` matrix products).
 
 Parity unpinned: the absolute accuracy of the near-singular rule on badly
 shaped triangles (only its convergence on well-shaped ones is pinned).
@@ -358,3 +361,135 @@ class HMatrix:
         cols = self.perm[lo_s:hi_s]
         R = scalar_rows(self.V, self.T, rows)[kern]
         return R[:, cols]
+
+
+# --------------------------------------------------------------------------
+# Adaptive matrix-vector multiplication (Algorithm 2)
+# --------------------------------------------------------------------------
+
+# kernel index of the component pair (p, q) of V_pq (V_11, V_12, V_13, V_22, V_23, V_33)
+_KPQ = {1: (0, 0), 2: (0, 1), 3: (0, 2), 4: (1, 1), 5: (1, 2), 6: (2, 2)}
+
+
+def sparsity_constant(Ho: "HMatrix") -> int:
+    """c_sp of the block partition (Section 2.1): the largest number of
+    blocks of P that share a row cluster, or a column cluster."""
+    blocks = np.concatenate([Ho.adm, Ho.near]) if Ho.nnear else Ho.adm
+    rows = np.bincount(blocks[:, 0], minlength=Ho.nnodes)
+    cols = np.bincount(blocks[:, 1], minlength=Ho.nnodes)
+    return int(max(rows.max(), cols.max()))
+
+
+def amvm(Ho: "HMatrix", E: float, nu: float, x, theta: float = 0.7, eps: float = 1e-6,
+         r0: int = 2, look: int = 2, max_iter: int = 1000):
+    """Algorithm 2 (adaptive matrix-vector multiplication, Section 3) on the
+    oracle's own H-matrix, FP64, for one vector x (3M dofs, original order).
+
+    Readings (the paper leaves these open):
+    * A_k keeps, on every admissible block t x s, the first r_b crosses of
+      each of the block's seven ACA sequences (Algorithm 1 as assembled with
+      the matrix's ACA epsilon; a sequence shorter than r_b is used whole);
+      A_0 has r_b = r0 = 2.  The look-ahead A^_k has r_b + look crosses
+      (look = 2, "two steps of ACA ahead").  Near blocks are exact in both.
+    * Marking is per block t x s: a marked block moves all seven kernels to
+      the look-ahead ranks, A_{k+1} = A^_k on it.
+    * Rows are the 3M dofs (component a of cluster position p is row 3p + a)
+      and M = N = 3M in the threshold (1 - theta)(c_sp M N)^{-1/2} gamma_k;
+      rows of equal error are taken in increasing row order.
+    * Step 4 stops when gamma_k <= eps * ||b^_k|| (a relative epsilon) and
+      returns b_k; it also stops when no block can be refined any more.
+
+    Returns a dict: b (A_k x at the last k, original order), b_hat, gamma
+    (gamma_k per iteration), gamma_rest (gamma_k(P_k) per iteration), marked
+    (|P_k| per iteration), ranks (r_b at the end), csp, iterations."""
+    x = _f64(x).reshape(-1)
+    M = Ho.M
+    c1, c2 = lame_coefficients(E, nu)
+    perm = Ho.perm
+    Xc = x.reshape(M, 3)[perm]                                  # cluster order
+    rng = Ho.ranges(Ho.adm)                                     # lo_t, hi_t, lo_s, hi_s
+    nb = Ho.nadm
+    F = [[Ho.factors(b, k) for k in range(7)] for b in range(nb)]
+    full = np.array([[F[b][k][0].shape[1] for k in range(7)] for b in range(nb)], dtype=np.int64)
+
+    def part(b: int, l0: int, l1: int) -> np.ndarray:
+        """The crosses l0 .. l1 - 1 of block b applied to x(s): (|t|, 3)."""
+        lo_t, hi_t, lo_s, hi_s = rng[b]
+        xs = Xc[lo_s:hi_s]
+        out = np.zeros((hi_t - lo_t, 3))
+        for k in range(7):
+            U, Vv = F[b][k]
+            a, z = min(l0, U.shape[1]), min(l1, U.shape[1])
+            if a >= z:
+                continue
+            W = Vv[:, a:z].T @ xs                               # (z - a, 3)
+            if k == 0:
+                out += c1 * (U[:, a:z] @ W)
+            else:
+                p, q = _KPQ[k]
+                out[:, p] += c2 * (U[:, a:z] @ W[:, q])
+                if p != q:
+                    out[:, q] += c2 * (U[:, a:z] @ W[:, p])
+        return out
+
+    # b_0: near field exactly, every admissible block at rank r0
+    near = Ho.matvec(E, nu, x, adm_ids=[])[0].reshape(M, 3)[perm]
+    r = np.full(nb, int(r0), dtype=np.int64)
+    bk = near.copy()
+    for b in range(nb):
+        bk[rng[b, 0]:rng[b, 1]] += part(b, 0, r0)
+    csp = sparsity_constant(Ho)
+    N = 3 * M
+    # blocks whose row cluster holds cluster position p, in block order
+    blocks_of_pos = [[] for _ in range(M)]
+    for b in range(nb):
+        for p in range(rng[b, 0], rng[b, 1]):
+            blocks_of_pos[p].append(b)
+    hist = dict(gamma=[], gamma_rest=[], marked=[])
+    delta = [part(b, r[b], r[b] + look) for b in range(nb)]
+    it = 0
+    while True:
+        e = np.zeros((M, 3))
+        for b in range(nb):
+            e[rng[b, 0]:rng[b, 1]] += delta[b]
+        bhat = bk + e
+        gamma = float(np.linalg.norm(e))
+        hist["gamma"].append(gamma)
+        if gamma <= eps * float(np.linalg.norm(bhat)) or it >= max_iter:
+            break
+        # step 3: Doerfler marking through the rows in decreasing error
+        thr = (1.0 - theta) * gamma / np.sqrt(csp * float(N) * float(N))
+        err = np.abs(e).reshape(-1)
+        order = np.lexsort((np.arange(N), -err))              # decreasing error, then row
+        rest = e.copy()
+        marked = []
+        is_marked = np.zeros(nb, dtype=bool)
+        g_rest = gamma
+        for i in order:
+            p, a = divmod(int(i), 3)
+            for b in blocks_of_pos[p]:
+                if is_marked[b]:
+                    continue
+                if abs(delta[b][p - rng[b, 0], a]) >= thr:
+                    is_marked[b] = True
+                    marked.append(b)
+                    rest[rng[b, 0]:rng[b, 1]] -= delta[b]
+            g_rest = float(np.linalg.norm(rest))
+            if gamma - g_rest >= theta * gamma:
+                break
+        hist["gamma_rest"].append(g_rest)
+        hist["marked"].append(len(marked))
+        if not marked:
+            break
+        # step 4: A_{k+1} = A^_k on the marked blocks
+        for b in marked:
+            bk[rng[b, 0]:rng[b, 1]] += delta[b]
+            r[b] += look
+            delta[b] = part(b, r[b], r[b] + look)
+        it += 1
+    out = np.zeros(3 * M)
+    out.reshape(M, 3)[perm] = bk
+    outh = np.zeros(3 * M)
+    outh.reshape(M, 3)[perm] = bhat
+    return dict(b=out, b_hat=outh, ranks=np.minimum(r[:, None], full), full_ranks=full, csp=csp,
+                iterations=it, **hist)
