@@ -351,6 +351,53 @@ typedef struct {
 int hm_solve(const hm_matrix* H, const double* g, double* t, const hm_solve_params* p,
              hm_solve_info* info, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Adaptive matrix-vector multiplication (Section 3, Algorithm 2), FP64.
+ *
+ * Computes b_k = A_k x for a sequence of approximations A_k of the assembled
+ * H-matrix: A_k keeps, on each admissible block t x s, the first r_b crosses
+ * of every one of its seven ACA sequences (a shorter sequence is used whole),
+ * A_0 has r_b = r0; the look-ahead A^_k has r_b + look crosses; near blocks
+ * are exact in both.  gamma_k = ||A_k x - A^_k x||_2 is the error estimator.
+ * Step 3 marks blocks through the dof rows in decreasing |(A_k x - A^_k x)_i|
+ * (ties: increasing row), adding every block t x s with i in t whose part
+ * satisfies |[(A_k - A^_k)_ts x_s]_i| >= (1 - theta)(c_sp N N)^{-1/2}
+ * gamma_k (N = 3M dofs, c_sp the sparsity constant of Section 2.1), until
+ * gamma_k - gamma_k(P_k) >= theta gamma_k; marked blocks take the
+ * look-ahead ranks.  The loop ends when gamma_k <= eps ||A^_k x||_2, when
+ * no block can be refined, or after max_iter refinements.
+ *   x, y      device, 3M doubles each, original dof order; y = A_k x at exit
+ *   info      optional: iterations, c_sp, last gamma, ||A^_k x||, crosses
+ *             used by A_k and by the assembled ACA, blocks marked in all
+ *   gamma_hist, gamma_rest_hist   optional host arrays of hist_cap entries:
+ *             gamma_k per iteration, gamma_k(P_k) per refinement
+ *   block_ranks  optional host array of nadm ints: r_b at exit
+ * Needs the FP64 factors and near field (HM_EINVAL after hm_compact).
+ * Allocates about 24 (3M) + 24 sum|t| bytes of workspace through the
+ * matrix's allocator for the duration of the call; synchronises `stream`.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    double theta;      /* Doerfler parameter in (0, 1) (0 = 0.7) */
+    double eps;        /* stop when gamma_k <= eps ||A^_k x|| (>= 0) */
+    int32_t r0;        /* crosses per block and kernel in A_0 (0 = 2), at most 32 */
+    int32_t look;      /* look-ahead ACA steps (0 = 2), at most 32 */
+    int32_t max_iter;  /* cap on refinement steps (0 = 1000) */
+    int32_t pad;
+} hm_amvm_params;
+
+typedef struct {
+    int32_t iterations;    /* refinement steps taken */
+    int32_t csp;           /* sparsity constant of the partition */
+    double gamma;          /* gamma_k at exit */
+    double bhat_norm;      /* ||A^_k x|| at exit */
+    int64_t crosses_used;  /* sum over block-kernels of the crosses in A_k */
+    int64_t crosses_full;  /* the same for the assembled ACA */
+    int64_t marked_total;  /* blocks marked over all steps */
+} hm_amvm_info;
+
+int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_amvm_params* p, hm_amvm_info* info,
+            double* gamma_hist, double* gamma_rest_hist, int32_t hist_cap, int32_t* block_ranks, void* stream);
+
 /* Status of the asynchronous products of H: HM_ETIMEOUT if a bounded device
  * wait inside an earlier hm_matvec ran out (its result is then invalid; the
  * flag is cleared), HM_OK otherwise.  Synchronises the device. */

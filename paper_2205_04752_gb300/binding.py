@@ -32,7 +32,7 @@ SYMBOLS = (
     "hm_solve", "hm_batch_create", "hm_batch_layout", "hm_batch_matvec", "hm_batch_autotune",
     "hm_batch_set_schedule", "hm_batch_get_schedule", "hm_batch_check", "hm_batch_destroy",
     "hm_compact", "hm_footprint", "hm_server_create", "hm_server_footprint", "hm_server_run",
-    "hm_server_destroy",
+    "hm_server_destroy", "hm_amvm",
 )
 
 
@@ -67,6 +67,17 @@ class _SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("restarts", ctypes.c_int32),
                 ("refinements", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("rel_residual", ctypes.c_double)]
+
+
+class _AmvmParams(ctypes.Structure):
+    _fields_ = [("theta", ctypes.c_double), ("eps", ctypes.c_double), ("r0", ctypes.c_int32),
+                ("look", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class _AmvmInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("csp", ctypes.c_int32), ("gamma", ctypes.c_double),
+                ("bhat_norm", ctypes.c_double), ("crosses_used", ctypes.c_int64),
+                ("crosses_full", ctypes.c_int64), ("marked_total", ctypes.c_int64)]
 
 
 class _Schedule(ctypes.Structure):
@@ -134,6 +145,8 @@ def load():
         "hm_solve": (ctypes.c_int, [P, P, P, ctypes.POINTER(_SolveParams),
                                     ctypes.POINTER(_SolveInfo), P]),
         "hm_get_stats": (ctypes.c_int, [P, ctypes.POINTER(_Stats)]),
+        "hm_amvm": (ctypes.c_int, [P, P, P, ctypes.POINTER(_AmvmParams), ctypes.POINTER(_AmvmInfo), P, P,
+                                   I32, P, P]),
         "hm_export_factors": (ctypes.c_int, [P, I64, I32, ctypes.POINTER(I32), P, P]),
         "hm_export_near": (ctypes.c_int, [P, I64, P]),
         "hm_matrix_destroy": (None, [P]),
@@ -398,6 +411,34 @@ def solve(H: HMatrix, g, t, tol: float = 1e-8, inner_form="fp16", inner_tol: flo
     elif rc not in (HM_OK, HM_ENOTCONV):
         _check(rc)
     return out
+
+
+def amvm(H: HMatrix, x, y, theta: float = 0.7, eps: float = 1e-6, r0: int = 2, look: int = 2,
+         max_iter: int = 0, stream=None):
+    """``hm_amvm``: adaptive matrix-vector multiplication (Algorithm 2), FP64.
+    x, y: CUDA float64 vectors of 3M (original dof order); y = A_k x at exit.
+    Returns a dict with the iterations, the estimator history (gamma per
+    iteration, gamma_rest per refinement), the final block ranks and the
+    crosses used against the assembled ACA."""
+    import torch
+    if not (x.is_cuda and y.is_cuda and x.dtype == torch.float64 and y.dtype == torch.float64):
+        raise TypeError("amvm: x and y must be CUDA float64 tensors")
+    if x.numel() != 3 * H.M or y.numel() != 3 * H.M or not x.is_contiguous() or not y.is_contiguous():
+        raise ValueError("amvm: x and y must be contiguous vectors of 3M")
+    p = _AmvmParams(float(theta), float(eps), int(r0), int(look), int(max_iter), 0)
+    info = _AmvmInfo()
+    cap = 4096
+    g = np.zeros(cap)
+    gr = np.zeros(cap)
+    ranks = np.zeros(max(H.stats().nadm, 1), dtype=np.int32)
+    _check(load().hm_amvm(H._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                          ctypes.byref(p), ctypes.byref(info), _ptr(g), _ptr(gr), cap, _ptr(ranks),
+                          _stream_handle(stream)))
+    k = info.iterations
+    return dict(iterations=k, csp=info.csp, gamma=list(g[:min(k + 1, cap)]),
+                gamma_rest=list(gr[:min(k, cap)]), bhat_norm=info.bhat_norm,
+                crosses_used=int(info.crosses_used), crosses_full=int(info.crosses_full),
+                marked_total=int(info.marked_total), block_ranks=ranks[:H.stats().nadm].copy())
 
 
 def hmatvec_noalloc(H: HMatrix, x, y, form="fp64", stream=None):

@@ -1,0 +1,468 @@
+// hm_amvm.cu -- adaptive matrix-vector multiplication (Algorithm 2, Section
+// 3) on the device, FP64, from the assembled ACA factors.
+//
+// A_k keeps the first r_b crosses of each of the seven ACA sequences of every
+// admissible block (the whole sequence when it is shorter), the look-ahead
+// A^_k the first r_b + L; near blocks are exact in both.  With b_k = A_k x
+// and the look-ahead parts D_b = (A^_k - A_k)_b x, the estimator is gamma_k =
+// ||sum_b D_b|| = ||b^_k - b_k||.  Marking (step 3) goes through the rows in
+// decreasing |(b^_k - b_k)_i| and adds every block t x s with i in t and
+// |(D_b)_i| >= (1 - theta)(c_sp N N)^{-1/2} gamma_k until gamma_k -
+// gamma_k(P_k) >= theta gamma_k; a marked block takes the look-ahead ranks
+// (step 4).  The loop ends when gamma_k <= eps ||b^_k||.
+//
+// Device work per iteration: the look-ahead parts of the blocks refined in
+// the previous step (one CTA per block: V^T x of the new crosses by warp
+// reductions, then U times them row by row), the row sums of all parts (each
+// position adds the parts of the blocks whose row cluster holds it, in block
+// order: deterministic), and the update of b_k by the marked blocks' parts.
+// The marking itself is a sequential scan (it stops at the first row that
+// meets the condition); it runs on the host over the copied parts.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <vector>
+
+#include "hm_internal.h"
+
+namespace hm {
+namespace {
+
+constexpr int kAmvmThreads = 256;
+constexpr int kAmvmMaxCross = 32;  // crosses of one block part (r0 and the look-ahead)
+
+struct AmvmItem {
+    int32_t b, l0, l1, pad;
+};
+
+__global__ void amvm_gather_kernel(const int32_t* __restrict__ perm, const double* __restrict__ x,
+                                   double* __restrict__ xc, int64_t M)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= M) return;
+    const int64_t o = 3 * (int64_t)perm[p];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) xc[3 * p + a] = x[o + a];
+}
+
+__global__ void amvm_scatter_kernel(const int32_t* __restrict__ perm, const double* __restrict__ bc,
+                                    double* __restrict__ y, int64_t M)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= M) return;
+    const int64_t o = 3 * (int64_t)perm[p];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) y[o + a] = bc[3 * p + a];
+}
+
+// near field, exact: position p adds its near blocks (row cluster = its leaf)
+// in block order; the six stored kernels V_11..V_33 give V_Delta as their
+// trace
+__global__ void amvm_near_kernel(const int32_t* __restrict__ ipos, const int32_t* __restrict__ nptr,
+                                 const int32_t* __restrict__ nidx, const Blk* __restrict__ near,
+                                 const int64_t* __restrict__ noff, const double* __restrict__ N64,
+                                 const double* __restrict__ xc, double c1, double c2, double* __restrict__ out,
+                                 int64_t M)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= M) return;
+    const int I = ipos[p];
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int q = nptr[I]; q < nptr[I + 1]; ++q) {
+        const int b = nidx[q];
+        const Blk bk = near[b];
+        const int64_t i = p - bk.t0, pairs = (int64_t)bk.m * bk.n;
+        const double* Nb = N64 + noff[b];
+        for (int j = 0; j < bk.n; ++j) {
+            const double* xj = xc + 3 * (int64_t)(bk.s0 + j);
+            const int64_t e = (int64_t)j * bk.m + i;
+            const double v11 = Nb[e], v12 = Nb[pairs + e], v13 = Nb[2 * pairs + e];
+            const double v22 = Nb[3 * pairs + e], v23 = Nb[4 * pairs + e], v33 = Nb[5 * pairs + e];
+            const double vd = v11 + v22 + v33;
+            s0 += c1 * vd * xj[0] + c2 * (v11 * xj[0] + v12 * xj[1] + v13 * xj[2]);
+            s1 += c1 * vd * xj[1] + c2 * (v12 * xj[0] + v22 * xj[1] + v23 * xj[2]);
+            s2 += c1 * vd * xj[2] + c2 * (v13 * xj[0] + v23 * xj[1] + v33 * xj[2]);
+        }
+    }
+    out[3 * p] = s0;
+    out[3 * p + 1] = s1;
+    out[3 * p + 2] = s2;
+}
+
+// the crosses l0 .. l1 - 1 of admissible block b applied to x(s): |t| x 3
+// values at D + doff[b] (component fastest).  Kernel k = 0 (V_Delta) acts on
+// each component with c1; V_pq (k = 1..6) adds c2 U (V^T x_q) to y_p and, p !=
+// q, c2 U (V^T x_p) to y_q.
+__global__ void __launch_bounds__(kAmvmThreads) amvm_part_kernel(
+    const AmvmItem* __restrict__ items, const Blk* __restrict__ adm, const int32_t* __restrict__ rank,
+    const int64_t* __restrict__ uoff, const int64_t* __restrict__ voff, const double* __restrict__ U64,
+    const double* __restrict__ V64, const double* __restrict__ xc, double c1, double c2,
+    const int64_t* __restrict__ doff, double* __restrict__ D)
+{
+    __shared__ double W[7][kAmvmMaxCross][3];
+    __shared__ int kk[7];
+    const AmvmItem it = items[blockIdx.x];
+    const Blk bk = adm[it.b];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = kAmvmThreads / 32;
+    if (tid < 7) kk[tid] = max(0, min(it.l1, rank[it.b * 7 + tid]) - it.l0);
+    __syncthreads();
+    // V^T x(s) of every (kernel, cross): one warp each, fixed reduction order
+    for (int pr = warp; pr < 7 * kAmvmMaxCross; pr += nw) {
+        const int k = pr / kAmvmMaxCross, l = pr - k * kAmvmMaxCross;
+        if (l >= kk[k]) continue;
+        const double* v = V64 + voff[it.b * 7 + k] + (int64_t)(it.l0 + l) * bk.n;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int j = lane; j < bk.n; j += 32) {
+            const double* xj = xc + 3 * (int64_t)(bk.s0 + j);
+            a0 += v[j] * xj[0];
+            a1 += v[j] * xj[1];
+            a2 += v[j] * xj[2];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        }
+        if (lane == 0) {
+            W[k][l][0] = a0;
+            W[k][l][1] = a1;
+            W[k][l][2] = a2;
+        }
+    }
+    __syncthreads();
+    double* out = D + doff[it.b];
+    for (int i = tid; i < bk.m; i += kAmvmThreads) {
+        double y[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < 7; ++k) {
+            const double* u = U64 + uoff[it.b * 7 + k] + (int64_t)it.l0 * bk.m + i;
+            double s[3] = {0.0, 0.0, 0.0};
+            for (int l = 0; l < kk[k]; ++l) {
+                const double ul = u[(int64_t)l * bk.m];
+                s[0] += ul * W[k][l][0];
+                s[1] += ul * W[k][l][1];
+                s[2] += ul * W[k][l][2];
+            }
+            if (k == 0) {
+                y[0] += c1 * s[0];
+                y[1] += c1 * s[1];
+                y[2] += c1 * s[2];
+            } else {
+                const int p = k <= 3 ? 0 : (k <= 5 ? 1 : 2);
+                const int q = k <= 3 ? k - 1 : (k <= 5 ? k - 3 : 2);
+                y[p] += c2 * s[q];
+                if (p != q) y[q] += c2 * s[p];
+            }
+        }
+        out[3 * i] = y[0];
+        out[3 * i + 1] = y[1];
+        out[3 * i + 2] = y[2];
+    }
+}
+
+// out[p] = (or +=) sum of the parts of the admissible blocks whose row
+// cluster holds position p, in block order; with flags, the flagged blocks
+// only
+__global__ void amvm_rowsum_kernel(const int32_t* __restrict__ ipos, const int32_t* __restrict__ aptr,
+                                   const int32_t* __restrict__ aidx, const Blk* __restrict__ adm,
+                                   const int64_t* __restrict__ doff, const double* __restrict__ D,
+                                   const uint8_t* __restrict__ flags, int add, double* __restrict__ out,
+                                   int64_t M)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= M) return;
+    const int I = ipos[p];
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int q = aptr[I]; q < aptr[I + 1]; ++q) {
+        const int b = aidx[q];
+        if (flags && !flags[b]) continue;
+        const double* d = D + doff[b] + 3 * (p - adm[b].t0);
+        s0 += d[0];
+        s1 += d[1];
+        s2 += d[2];
+    }
+    if (add) {
+        out[3 * p] += s0;
+        out[3 * p + 1] += s1;
+        out[3 * p + 2] += s2;
+    } else {
+        out[3 * p] = s0;
+        out[3 * p + 1] = s1;
+        out[3 * p + 2] = s2;
+    }
+}
+
+// elementary intervals of cluster positions (between consecutive block row
+// boundaries) and, per interval, the blocks whose row range covers it, in
+// block order
+struct RowLists {
+    std::vector<int32_t> ipos;  // M: interval of each position
+    std::vector<int32_t> ptr, idx;
+};
+
+RowLists row_lists(int64_t M, const std::vector<int64_t>& bounds, const std::vector<Blk>& blks)
+{
+    RowLists r;
+    const int nI = (int)bounds.size() - 1;
+    r.ipos.resize((size_t)M);
+    for (int I = 0; I < nI; ++I)
+        for (int64_t p = bounds[(size_t)I]; p < bounds[(size_t)I + 1]; ++p) r.ipos[(size_t)p] = I;
+    std::vector<int32_t> cnt((size_t)nI + 1, 0);
+    for (const Blk& b : blks)
+        for (int I = r.ipos[(size_t)b.t0]; I < nI && bounds[(size_t)I] < b.t0 + b.m; ++I) cnt[(size_t)I + 1]++;
+    r.ptr.assign((size_t)nI + 1, 0);
+    for (int I = 0; I < nI; ++I) r.ptr[(size_t)I + 1] = r.ptr[(size_t)I] + cnt[(size_t)I + 1];
+    r.idx.resize((size_t)r.ptr[(size_t)nI]);
+    std::vector<int32_t> fill(r.ptr.begin(), r.ptr.end() - 1);
+    for (size_t b = 0; b < blks.size(); ++b)
+        for (int I = r.ipos[(size_t)blks[b].t0]; I < nI && bounds[(size_t)I] < blks[b].t0 + blks[b].m; ++I)
+            r.idx[(size_t)fill[(size_t)I]++] = (int32_t)b;
+    return r;
+}
+
+// device buffers of one call, from the matrix's allocator
+struct Pool {
+    Allocator al;
+    std::vector<std::pair<void*, size_t>> held;
+    ~Pool()
+    {
+        for (auto& h : held) al.release(h.first, h.second);
+    }
+    template <class T>
+    T* get(size_t n)
+    {
+        const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+        void* p = al.alloc(bytes);
+        if (p) held.emplace_back(p, bytes);
+        return static_cast<T*>(p);
+    }
+};
+
+template <class T>
+int put(T* d, const std::vector<T>& h, cudaStream_t s)
+{
+    if (!h.empty()) HM_CUDA(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return HM_OK;
+}
+
+}  // namespace
+}  // namespace hm
+
+using namespace hm;
+
+extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_amvm_params* prm,
+                       hm_amvm_info* info, double* gamma_hist, double* gamma_rest_hist, int32_t hist_cap,
+                       int32_t* block_ranks, void* stream)
+{
+    if (!H || !x || !y || !prm) return fail(HM_EINVAL, "hm_amvm: NULL argument");
+    if (H->compacted || !H->U64.p) return fail(HM_EINVAL, "hm_amvm: the FP64 factors were released (hm_compact)");
+    const double theta = prm->theta == 0.0 ? 0.7 : prm->theta;
+    const double eps = prm->eps;
+    const int r0 = prm->r0 == 0 ? 2 : prm->r0, look = prm->look == 0 ? 2 : prm->look;
+    const int max_iter = prm->max_iter == 0 ? 1000 : prm->max_iter;
+    if (!(theta > 0.0 && theta < 1.0)) return fail(HM_EINVAL, "hm_amvm: theta %g outside (0, 1)", theta);
+    if (!(eps >= 0.0)) return fail(HM_EINVAL, "hm_amvm: eps %g < 0", eps);
+    if (r0 < 1 || look < 1 || r0 > kAmvmMaxCross || look > kAmvmMaxCross || max_iter < 0)
+        return fail(HM_EINVAL, "hm_amvm: r0 %d / look %d outside 1..%d or max_iter %d < 0", r0, look, kAmvmMaxCross,
+                    max_iter);
+    if (hist_cap < 0) return fail(HM_EINVAL, "hm_amvm: hist_cap < 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t M = H->M, nb = H->nadm, N = 3 * M;
+    if (M > INT32_MAX / 3) return fail(HM_EINVAL, "hm_amvm: mesh too large");
+    const double c1 = (1.0 + H->nu) * (3.0 - 4.0 * H->nu) / (2.0 * H->E * (1.0 - H->nu));
+    const double c2 = (1.0 + H->nu) / (2.0 * H->E * (1.0 - H->nu));
+
+    // ---- host tables: row intervals, block lists, part offsets, c_sp
+    std::vector<int64_t> bounds = {0, M};
+    for (const Blk& b : H->adm_h) {
+        bounds.push_back(b.t0);
+        bounds.push_back(b.t0 + b.m);
+    }
+    for (const Blk& b : H->near_h) {
+        bounds.push_back(b.t0);
+        bounds.push_back(b.t0 + b.m);
+    }
+    std::sort(bounds.begin(), bounds.end());
+    bounds.erase(std::unique(bounds.begin(), bounds.end()), bounds.end());
+    const RowLists ra = row_lists(M, bounds, H->adm_h), rn = row_lists(M, bounds, H->near_h);
+    std::vector<int64_t> doff((size_t)nb + 1, 0);
+    for (int64_t b = 0; b < nb; ++b) doff[(size_t)b + 1] = doff[(size_t)b] + 3 * (int64_t)H->adm_h[(size_t)b].m;
+    int csp = 0;
+    {
+        // Section 2.1: the most blocks of P that share a row or a column cluster
+        std::map<std::pair<int32_t, int32_t>, int> rows, cols;
+        for (const auto* L : {&H->adm_h, &H->near_h})
+            for (const Blk& b : *L) {
+                csp = std::max(csp, ++rows[{b.t0, b.m}]);
+                csp = std::max(csp, ++cols[{b.s0, b.n}]);
+            }
+    }
+
+    // ---- device buffers
+    Pool pool;
+    pool.al = H->alloc;
+    pool.al.stream = s;
+    double* xc = pool.get<double>((size_t)N);
+    double* bk = pool.get<double>((size_t)N);
+    double* e = pool.get<double>((size_t)N);
+    double* D = pool.get<double>((size_t)doff[(size_t)nb]);
+    int32_t* d_ipos = pool.get<int32_t>((size_t)M);
+    int32_t* d_aptr = pool.get<int32_t>(ra.ptr.size());
+    int32_t* d_aidx = pool.get<int32_t>(ra.idx.size());
+    int32_t* d_nptr = pool.get<int32_t>(rn.ptr.size());
+    int32_t* d_nidx = pool.get<int32_t>(rn.idx.size());
+    int64_t* d_doff = pool.get<int64_t>(doff.size());
+    AmvmItem* d_items = pool.get<AmvmItem>((size_t)nb);
+    uint8_t* d_flags = pool.get<uint8_t>((size_t)nb);
+    if (!xc || !bk || !e || !D || !d_ipos || !d_aptr || !d_aidx || !d_nptr || !d_nidx || !d_doff || !d_items ||
+        !d_flags)
+        return fail(HM_ENOMEM, "hm_amvm: workspace (%lld parts)", (long long)doff[(size_t)nb]);
+    int rc;
+    if ((rc = put(d_ipos, ra.ipos, s)) || (rc = put(d_aptr, ra.ptr, s)) || (rc = put(d_aidx, ra.idx, s)) ||
+        (rc = put(d_nptr, rn.ptr, s)) || (rc = put(d_nidx, rn.idx, s)) || (rc = put(d_doff, doff, s)))
+        return rc;
+    const unsigned gM = (unsigned)((M + 255) / 256);
+    const Blk* d_adm = H->d_adm.as<Blk>();
+    auto parts = [&](const std::vector<AmvmItem>& items) -> int {
+        if (items.empty()) return HM_OK;
+        int rc2 = put(d_items, items, s);
+        if (rc2) return rc2;
+        amvm_part_kernel<<<(unsigned)items.size(), kAmvmThreads, 0, s>>>(
+            d_items, d_adm, H->d_rank.as<int32_t>(), H->d_uoff.as<int64_t>(), H->d_voff.as<int64_t>(),
+            H->U64.as<double>(), H->V64.as<double>(), xc, c1, c2, d_doff, D);
+        HM_CUDA(cudaGetLastError());
+        return HM_OK;
+    };
+
+    // ---- b_0 = near field + every admissible block at rank r0
+    amvm_gather_kernel<<<gM, 256, 0, s>>>(H->d_perm.as<int32_t>(), x, xc, M);
+    HM_CUDA(cudaGetLastError());
+    amvm_near_kernel<<<gM, 256, 0, s>>>(d_ipos, d_nptr, d_nidx, H->d_near.as<Blk>(), H->d_noff.as<int64_t>(),
+                                       H->N64.as<double>(), xc, c1, c2, bk, M);
+    HM_CUDA(cudaGetLastError());
+    std::vector<int32_t> r((size_t)nb, r0);
+    std::vector<AmvmItem> items((size_t)nb);
+    for (int64_t b = 0; b < nb; ++b) items[(size_t)b] = AmvmItem{(int32_t)b, 0, r0, 0};
+    if ((rc = parts(items))) return rc;
+    if (nb > 0) {
+        amvm_rowsum_kernel<<<gM, 256, 0, s>>>(d_ipos, d_aptr, d_aidx, d_adm, d_doff, D, nullptr, 1, bk, M);
+        HM_CUDA(cudaGetLastError());
+    }
+    // look-ahead parts at the current ranks
+    for (int64_t b = 0; b < nb; ++b) items[(size_t)b] = AmvmItem{(int32_t)b, r0, r0 + look, 0};
+    if ((rc = parts(items))) return rc;
+
+    std::vector<double> he((size_t)N), hb((size_t)N), hD((size_t)doff[(size_t)nb]);
+    std::vector<uint8_t> marked((size_t)nb);
+    std::vector<int64_t> order((size_t)N);
+    int it = 0;
+    int64_t marked_total = 0;
+    double gamma = 0.0, bhat = 0.0;
+    for (;;) {
+        // e = b^_k - b_k
+        if (nb > 0) {
+            amvm_rowsum_kernel<<<gM, 256, 0, s>>>(d_ipos, d_aptr, d_aidx, d_adm, d_doff, D, nullptr, 0, e, M);
+            HM_CUDA(cudaGetLastError());
+        } else {
+            HM_CUDA(cudaMemsetAsync(e, 0, (size_t)N * sizeof(double), s));
+        }
+        HM_CUDA(cudaMemcpyAsync(he.data(), e, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaMemcpyAsync(hb.data(), bk, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaStreamSynchronize(s));
+        double g2 = 0.0, b2 = 0.0;
+        for (int64_t i = 0; i < N; ++i) {
+            g2 += he[(size_t)i] * he[(size_t)i];
+            const double v = hb[(size_t)i] + he[(size_t)i];
+            b2 += v * v;
+        }
+        gamma = std::sqrt(g2);
+        bhat = std::sqrt(b2);
+        if (it < hist_cap && gamma_hist) gamma_hist[it] = gamma;
+        if (gamma <= eps * bhat || it >= max_iter) break;
+        // step 3: Doerfler marking through the rows in decreasing error
+        if (!hD.empty())
+            HM_CUDA(cudaMemcpyAsync(hD.data(), D, hD.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaStreamSynchronize(s));
+        const double thr = (1.0 - theta) * gamma / std::sqrt((double)csp * (double)N * (double)N);
+        std::iota(order.begin(), order.end(), 0);
+        std::sort(order.begin(), order.end(), [&](int64_t a, int64_t c) {
+            const double ea = std::fabs(he[(size_t)a]), ec = std::fabs(he[(size_t)c]);
+            return ea > ec || (ea == ec && a < c);
+        });
+        std::vector<double> rest(he);
+        double n2 = g2, g_rest = gamma;
+        std::fill(marked.begin(), marked.end(), 0);
+        std::vector<int32_t> newly;
+        for (int64_t i : order) {
+            const int64_t p = i / 3, a = i - 3 * p;
+            const int I = ra.ipos[(size_t)p];
+            for (int q = ra.ptr[(size_t)I]; q < ra.ptr[(size_t)I + 1]; ++q) {
+                const int b = ra.idx[(size_t)q];
+                if (marked[(size_t)b]) continue;
+                const Blk& bb = H->adm_h[(size_t)b];
+                const double* Db = hD.data() + doff[(size_t)b];
+                if (std::fabs(Db[3 * (p - bb.t0) + a]) < thr) continue;
+                marked[(size_t)b] = 1;
+                newly.push_back(b);
+                for (int64_t z = 0; z < 3 * (int64_t)bb.m; ++z) {
+                    double& v = rest[(size_t)(3 * (int64_t)bb.t0 + z)];
+                    const double old = v;
+                    v -= Db[z];
+                    n2 += v * v - old * old;
+                }
+            }
+            g_rest = std::sqrt(std::max(n2, 0.0));
+            if (std::fabs(gamma - g_rest - theta * gamma) <= 1e-9 * gamma) {
+                // close to the condition: the exact norm of the rest decides
+                double x2 = 0.0;
+                for (double v : rest) x2 += v * v;
+                n2 = x2;
+                g_rest = std::sqrt(x2);
+            }
+            if (gamma - g_rest >= theta * gamma) break;
+        }
+        {
+            double x2 = 0.0;
+            for (double v : rest) x2 += v * v;
+            g_rest = std::sqrt(x2);
+        }
+        if (it < hist_cap && gamma_rest_hist) gamma_rest_hist[it] = g_rest;
+        if (newly.empty()) break;
+        marked_total += (int64_t)newly.size();
+        // step 4: A_{k+1} = A^_k on the marked blocks, and their next look-ahead
+        HM_CUDA(cudaMemcpyAsync(d_flags, marked.data(), (size_t)nb, cudaMemcpyHostToDevice, s));
+        amvm_rowsum_kernel<<<gM, 256, 0, s>>>(d_ipos, d_aptr, d_aidx, d_adm, d_doff, D, d_flags, 1, bk, M);
+        HM_CUDA(cudaGetLastError());
+        items.clear();
+        for (int32_t b : newly) {
+            r[(size_t)b] += look;
+            items.push_back(AmvmItem{b, r[(size_t)b], r[(size_t)b] + look, 0});
+        }
+        if ((rc = parts(items))) return rc;
+        ++it;
+    }
+    amvm_scatter_kernel<<<gM, 256, 0, s>>>(H->d_perm.as<int32_t>(), bk, y, M);
+    HM_CUDA(cudaGetLastError());
+    HM_CUDA(cudaStreamSynchronize(s));
+    if (info) {
+        info->iterations = it;
+        info->csp = csp;
+        info->gamma = gamma;
+        info->bhat_norm = bhat;
+        int64_t used = 0, full = 0;
+        for (int64_t b = 0; b < nb; ++b)
+            for (int k = 0; k < 7; ++k) {
+                const int32_t K = H->rank_h[(size_t)(b * 7 + k)];
+                used += std::min<int64_t>(K, r[(size_t)b]);
+                full += K;
+            }
+        info->crosses_used = used;
+        info->crosses_full = full;
+        info->marked_total = marked_total;
+    }
+    if (block_ranks)
+        for (int64_t b = 0; b < nb; ++b) block_ranks[b] = r[(size_t)b];
+    return HM_OK;
+}

@@ -74,6 +74,7 @@ def test_invalid_arguments_fail_cleanly():
     assert b"NULL" in lib.hm_last_error() or b"empty" in lib.hm_last_error()
     assert lib.hm_matvec(None, None, None, 1, 3, 0, None) == binding.HM_EINVAL
     assert lib.hm_pack(None, 1, None) == binding.HM_EINVAL
+    assert lib.hm_amvm(None, None, None, None, None, None, None, 0, None, None) == binding.HM_EINVAL
 
 
 def _compare_tree(V, T, leaf, eta):
