@@ -13,9 +13,10 @@ L2, so every step streams it from HBM; no L2 flush is needed.
 Besides the headline the JSON line carries, as context: the FP64 form, 32
 right-hand sides, end-to-end products with host buffers, "batch64" (batched
 products over 64 ellipsoid meshes with 1 and 16 right-hand sides), "solve"
-(GMRES with FP64-residual refinement to 1e-8 on a 196,608-triangle cube) and
+(GMRES with FP64-residual refinement to 1e-8 on a 196,608-triangle cube),
 "serving" (the request loop over 16 resident meshes at swept Poisson rates,
-p50 / p99 latency); --no-batch / --no-solve / --no-serve skip them.
+p50 / p99 latency) and "amvm" (Algorithm 2 on the level-6 matrix, FP64, theta
+0.7, eps 1e-4); --no-batch / --no-solve / --no-serve / --no-amvm skip them.
 
 Under torchrun (N > 1) every rank runs its own replica (the product shards
 into independent problems; no collective on the data path): weak scaling,
@@ -345,6 +346,21 @@ def run_ours(args):
     ms32 = timed(lambda: binding.hmatvec(H, X, Y, form), max(2, args.steps // 4), 1) \
         / max(2, args.steps // 4)
 
+    # ---- context: adaptive matrix-vector multiplication (Algorithm 2, FP64)
+    amvm_ctx = None
+    if not args.no_amvm:
+        ya = torch.empty_like(x)
+        binding.amvm(H, x, ya, theta=0.7, eps=1e-4)  # warm-up (host tables, allocations)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ai = binding.amvm(H, x, ya, theta=0.7, eps=1e-4)
+        torch.cuda.synchronize()
+        amvm_ms = (time.perf_counter() - t0) * 1e3
+        amvm_ctx = {"theta": 0.7, "eps": 1e-4, "ms": round(amvm_ms, 1), "iterations": ai["iterations"],
+                    "crosses_used_fraction": round(ai["crosses_used"] / max(ai["crosses_full"], 1), 4),
+                    "rel_err_vs_fp64_product": float(torch.linalg.norm(ya - y64) / torch.linalg.norm(y64)),
+                    "gamma_over_bhat": ai["gamma"][-1] / ai["bhat_norm"]}
+
     line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -357,6 +373,7 @@ def run_ours(args):
             "rel_err_vs_fp64_form": err_mixed,
             "fp64_form": {"ms_per_matvec": round(ms64, 4), "value": round(1e3 / ms64, 3)},
             "nrhs32": {"ms_per_call": round(ms32, 4), "vectors_per_s": round(32e3 / ms32, 2)},
+            "amvm": amvm_ctx,
             "assembly": {"tree_s": round(t_tree, 3), "assemble_s": round(t_asm, 3),
                          "near_ms": round(st.assemble_ms[0], 1),
                          "aca_ms": round(st.assemble_ms[1], 1),
@@ -558,6 +575,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-mesh batched products")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-loop measurement")
     ap.add_argument("--no-solve", action="store_true", help="skip the 196,608-triangle cube solve")
+    ap.add_argument("--no-amvm", action="store_true", help="skip the adaptive matrix-vector multiplication")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[10.0, 30.0, 100.0])
     ap.add_argument("--serve-seconds", type=float, default=4.0)
     ap.add_argument("--minimal", action="store_true",
