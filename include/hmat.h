@@ -114,6 +114,10 @@ typedef struct {
  * (saves its memory while a matrix is assembled only to be packed into a
  * reduced form and compacted) */
 #define HM_DEFER_FP64 1
+/* hm_params.flags: run no ACA at assembly (tree, partition, near field and
+ * product tables only); such a matrix cannot be packed and serves the
+ * adaptive product with ACA on demand (hm_amvm, HM_AMVM_ACA_ON_DEMAND) */
+#define HM_DEFER_ACA 2
 
 /* ---------------------------------------------------------------------------
  * hm_aca_assemble -- assemble the H-matrix of V_h on the device.
@@ -372,7 +376,8 @@ int hm_solve(const hm_matrix* H, const double* g, double* t, const hm_solve_para
  *   gamma_hist, gamma_rest_hist   optional host arrays of hist_cap entries:
  *             gamma_k per iteration, gamma_k(P_k) per refinement
  *   block_ranks  optional host array of nadm ints: r_b at exit
- * Needs the FP64 factors and near field (HM_EINVAL after hm_compact).
+ * Needs the FP64 factors (or HM_AMVM_ACA_ON_DEMAND) and the near field
+ * (HM_EINVAL after hm_compact).
  * Allocates about 24 (3M) + 24 sum|t| bytes of workspace through the
  * matrix's allocator for the duration of the call; synchronises `stream`.
  * ------------------------------------------------------------------------- */
@@ -382,8 +387,14 @@ typedef struct {
     int32_t r0;        /* crosses per block and kernel in A_0 (0 = 2), at most 32 */
     int32_t look;      /* look-ahead ACA steps (0 = 2), at most 32 */
     int32_t max_iter;  /* cap on refinement steps (0 = 1000) */
-    int32_t pad;
+    int32_t flags;     /* HM_AMVM_ACA_ON_DEMAND */
 } hm_amvm_params;
+
+/* hm_amvm_params.flags: run Algorithm 1 on demand (every block-kernel to
+ * r0 + look crosses, a refined block's kernels on to r_b + look) instead of
+ * taking prefixes of the assembled factors; the matrix may be assembled with
+ * HM_DEFER_ACA.  info->crosses_full then counts the crosses computed. */
+#define HM_AMVM_ACA_ON_DEMAND 1
 
 typedef struct {
     int32_t iterations;    /* refinement steps taken */

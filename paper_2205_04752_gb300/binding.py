@@ -71,7 +71,7 @@ class _SolveInfo(ctypes.Structure):
 
 class _AmvmParams(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_double), ("eps", ctypes.c_double), ("r0", ctypes.c_int32),
-                ("look", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("look", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 class _AmvmInfo(ctypes.Structure):
@@ -274,13 +274,13 @@ class HMatrix:
 
     def __init__(self, tree: ClusterTree, E: float, nu: float, aca_eps: float,
                  aca_eta_stop: float = 0.8, kmax: int = 128, max_rhs: int = 32, stream=None,
-                 torch_memory: bool = True, defer_fp64: bool = False):
+                 torch_memory: bool = True, defer_fp64: bool = False, defer_aca: bool = False):
         import torch
         lib = load()
         self.M = tree.M
         self.device = torch.cuda.current_device()
         prm = _Params(float(E), float(nu), float(aca_eps), float(aca_eta_stop), int(kmax),
-                      int(max_rhs), 1 if defer_fp64 else 0, 0)
+                      int(max_rhs), (1 if defer_fp64 else 0) | (2 if defer_aca else 0), 0)
         self._alloc_keep = None
         ap = None
         if torch_memory:
@@ -414,18 +414,20 @@ def solve(H: HMatrix, g, t, tol: float = 1e-8, inner_form="fp16", inner_tol: flo
 
 
 def amvm(H: HMatrix, x, y, theta: float = 0.7, eps: float = 1e-6, r0: int = 2, look: int = 2,
-         max_iter: int = 0, stream=None):
+         max_iter: int = 0, on_demand: bool = False, stream=None):
     """``hm_amvm``: adaptive matrix-vector multiplication (Algorithm 2), FP64.
     x, y: CUDA float64 vectors of 3M (original dof order); y = A_k x at exit.
     Returns a dict with the iterations, the estimator history (gamma per
     iteration, gamma_rest per refinement), the final block ranks and the
-    crosses used against the assembled ACA."""
+    crosses used against the assembled ACA (``on_demand``: Algorithm 1 run on
+    demand, HM_AMVM_ACA_ON_DEMAND; crosses_full then counts the crosses
+    computed)."""
     import torch
     if not (x.is_cuda and y.is_cuda and x.dtype == torch.float64 and y.dtype == torch.float64):
         raise TypeError("amvm: x and y must be CUDA float64 tensors")
     if x.numel() != 3 * H.M or y.numel() != 3 * H.M or not x.is_contiguous() or not y.is_contiguous():
         raise ValueError("amvm: x and y must be contiguous vectors of 3M")
-    p = _AmvmParams(float(theta), float(eps), int(r0), int(look), int(max_iter), 0)
+    p = _AmvmParams(float(theta), float(eps), int(r0), int(look), int(max_iter), 1 if on_demand else 0)
     info = _AmvmInfo()
     cap = 4096
     g = np.zeros(cap)

@@ -18,6 +18,13 @@
 // order: deterministic), and the update of b_k by the marked blocks' parts.
 // The marking itself is a sequential scan (it stops at the first row that
 // meets the condition); it runs on the host over the copied parts.
+//
+// The crosses come either from the assembled ACA (prefixes of its sequences)
+// or, with HM_AMVM_ACA_ON_DEMAND, from Algorithm 1 run on demand: every
+// block-kernel to r0 + look crosses first, a refined block's kernels again to
+// its new r_b + look (the batched ACA kernel is deterministic, so a longer run
+// repeats the first crosses), so that only the crosses the refinement reaches
+// are ever computed -- the combination of assembly and product of Section 3.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -97,9 +104,8 @@ __global__ void amvm_near_kernel(const int32_t* __restrict__ ipos, const int32_t
 // q, c2 U (V^T x_p) to y_q.
 __global__ void __launch_bounds__(kAmvmThreads) amvm_part_kernel(
     const AmvmItem* __restrict__ items, const Blk* __restrict__ adm, const int32_t* __restrict__ rank,
-    const int64_t* __restrict__ uoff, const int64_t* __restrict__ voff, const double* __restrict__ U64,
-    const double* __restrict__ V64, const double* __restrict__ xc, double c1, double c2,
-    const int64_t* __restrict__ doff, double* __restrict__ D)
+    const double* const* __restrict__ uptr, const double* const* __restrict__ vptr, const double* __restrict__ xc,
+    double c1, double c2, const int64_t* __restrict__ doff, double* __restrict__ D)
 {
     __shared__ double W[7][kAmvmMaxCross][3];
     __shared__ int kk[7];
@@ -112,7 +118,7 @@ __global__ void __launch_bounds__(kAmvmThreads) amvm_part_kernel(
     for (int pr = warp; pr < 7 * kAmvmMaxCross; pr += nw) {
         const int k = pr / kAmvmMaxCross, l = pr - k * kAmvmMaxCross;
         if (l >= kk[k]) continue;
-        const double* v = V64 + voff[it.b * 7 + k] + (int64_t)(it.l0 + l) * bk.n;
+        const double* v = vptr[it.b * 7 + k] + (int64_t)(it.l0 + l) * bk.n;
         double a0 = 0.0, a1 = 0.0, a2 = 0.0;
         for (int j = lane; j < bk.n; j += 32) {
             const double* xj = xc + 3 * (int64_t)(bk.s0 + j);
@@ -137,7 +143,7 @@ __global__ void __launch_bounds__(kAmvmThreads) amvm_part_kernel(
     for (int i = tid; i < bk.m; i += kAmvmThreads) {
         double y[3] = {0.0, 0.0, 0.0};
         for (int k = 0; k < 7; ++k) {
-            const double* u = U64 + uoff[it.b * 7 + k] + (int64_t)it.l0 * bk.m + i;
+            const double* u = uptr[it.b * 7 + k] + (int64_t)it.l0 * bk.m + i;
             double s[3] = {0.0, 0.0, 0.0};
             for (int l = 0; l < kk[k]; ++l) {
                 const double ul = u[(int64_t)l * bk.m];
@@ -257,7 +263,11 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
                        int32_t* block_ranks, void* stream)
 {
     if (!H || !x || !y || !prm) return fail(HM_EINVAL, "hm_amvm: NULL argument");
-    if (H->compacted || !H->U64.p) return fail(HM_EINVAL, "hm_amvm: the FP64 factors were released (hm_compact)");
+    if (prm->flags & ~HM_AMVM_ACA_ON_DEMAND) return fail(HM_EINVAL, "hm_amvm: unknown flags 0x%x", prm->flags);
+    const bool lazy = (prm->flags & HM_AMVM_ACA_ON_DEMAND) != 0;
+    if (H->compacted) return fail(HM_EINVAL, "hm_amvm: the FP64 data were released (hm_compact)");
+    if (!lazy && (H->aca_deferred || !H->U64.p))
+        return fail(HM_EINVAL, "hm_amvm: no assembled ACA factors (HM_DEFER_ACA): use HM_AMVM_ACA_ON_DEMAND");
     const double theta = prm->theta == 0.0 ? 0.7 : prm->theta;
     const double eps = prm->eps;
     const int r0 = prm->r0 == 0 ? 2 : prm->r0, look = prm->look == 0 ? 2 : prm->look;
@@ -269,6 +279,19 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
                     max_iter);
     if (hist_cap < 0) return fail(HM_EINVAL, "hm_amvm: hist_cap < 0");
     cudaStream_t s = (cudaStream_t)stream;
+    hm_matrix& Hm = const_cast<hm_matrix&>(*H);  // on-demand ACA allocates through the matrix's allocator
+    const cudaStream_t saved_stream = Hm.alloc.stream;
+    Hm.alloc.stream = s;
+    struct Restore {
+        hm_matrix& h;
+        cudaStream_t st;
+        std::vector<DevBuf> arenas;
+        ~Restore()
+        {
+            for (DevBuf& a : arenas) h.alloc.release(a.p, a.bytes);
+            h.alloc.stream = st;
+        }
+    } restore{Hm, saved_stream, {}};
     const int64_t M = H->M, nb = H->nadm, N = 3 * M;
     if (M > INT32_MAX / 3) return fail(HM_EINVAL, "hm_amvm: mesh too large");
     const double c1 = (1.0 + H->nu) * (3.0 - 4.0 * H->nu) / (2.0 * H->E * (1.0 - H->nu));
@@ -316,8 +339,11 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
     int64_t* d_doff = pool.get<int64_t>(doff.size());
     AmvmItem* d_items = pool.get<AmvmItem>((size_t)nb);
     uint8_t* d_flags = pool.get<uint8_t>((size_t)nb);
+    const double** d_uptr = pool.get<const double*>((size_t)nb * 7);
+    const double** d_vptr = pool.get<const double*>((size_t)nb * 7);
+    int32_t* d_krank = pool.get<int32_t>((size_t)nb * 7);
     if (!xc || !bk || !e || !D || !d_ipos || !d_aptr || !d_aidx || !d_nptr || !d_nidx || !d_doff || !d_items ||
-        !d_flags)
+        !d_flags || !d_uptr || !d_vptr || !d_krank)
         return fail(HM_ENOMEM, "hm_amvm: workspace (%lld parts)", (long long)doff[(size_t)nb]);
     int rc;
     if ((rc = put(d_ipos, ra.ipos, s)) || (rc = put(d_aptr, ra.ptr, s)) || (rc = put(d_aidx, ra.idx, s)) ||
@@ -325,13 +351,57 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
         return rc;
     const unsigned gM = (unsigned)((M + 255) / 256);
     const Blk* d_adm = H->d_adm.as<Blk>();
+    // the crosses of every block-kernel: pointers to U (k x m) and V (k x n),
+    // and how many there are (krank); on demand, also the kmax of the run
+    // that produced them
+    std::vector<const double*> uptr((size_t)nb * 7, nullptr), vptr((size_t)nb * 7, nullptr);
+    std::vector<int32_t> krank((size_t)nb * 7, 0), kmax_run((size_t)nb * 7, 0);
+    const int kcap = std::max(1, (int)H->prm.kmax);
+    auto run_aca = [&](const std::vector<int32_t>& bkl, int kmax) -> int {
+        if (bkl.empty()) return HM_OK;
+        std::vector<int32_t> rr;
+        std::vector<int64_t> oo;
+        DevBuf arena;
+        int rc2 = aca_on_demand(Hm, bkl, kmax, s, arena, rr, oo);
+        if (arena.p) restore.arenas.push_back(arena);
+        if (rc2) return rc2;
+        for (size_t q = 0; q < bkl.size(); ++q) {
+            const int32_t v = bkl[q];
+            const Blk& bb = H->adm_h[(size_t)(v / 7)];
+            uptr[(size_t)v] = arena.as<double>() + oo[q];
+            vptr[(size_t)v] = uptr[(size_t)v] + (int64_t)rr[q] * bb.m;
+            krank[(size_t)v] = rr[q];
+            kmax_run[(size_t)v] = kmax;
+        }
+        return HM_OK;
+    };
+    auto upload_factors = [&]() -> int {
+        int rc2;
+        if ((rc2 = put(d_uptr, uptr, s)) || (rc2 = put(d_vptr, vptr, s)) || (rc2 = put(d_krank, krank, s)))
+            return rc2;
+        return HM_OK;
+    };
+    if (lazy) {
+        std::vector<int32_t> all;
+        for (int64_t q = 0; q < nb * 7; ++q)
+            if (!(H->flags_h[(size_t)q] & 32)) all.push_back((int32_t)q);  // 32: identically zero kernel
+        if ((rc = run_aca(all, std::min(r0 + look, kcap)))) return rc;
+    } else {
+        for (int64_t q = 0; q < nb * 7; ++q) {
+            const Blk& bb = H->adm_h[(size_t)(q / 7)];
+            uptr[(size_t)q] = H->U64.as<double>() + H->uoff_h[(size_t)q];
+            vptr[(size_t)q] = H->V64.as<double>() + H->voff_h[(size_t)q];
+            krank[(size_t)q] = H->rank_h[(size_t)q];
+            (void)bb;
+        }
+    }
+    if ((rc = upload_factors())) return rc;
     auto parts = [&](const std::vector<AmvmItem>& items) -> int {
         if (items.empty()) return HM_OK;
         int rc2 = put(d_items, items, s);
         if (rc2) return rc2;
-        amvm_part_kernel<<<(unsigned)items.size(), kAmvmThreads, 0, s>>>(
-            d_items, d_adm, H->d_rank.as<int32_t>(), H->d_uoff.as<int64_t>(), H->d_voff.as<int64_t>(),
-            H->U64.as<double>(), H->V64.as<double>(), xc, c1, c2, d_doff, D);
+        amvm_part_kernel<<<(unsigned)items.size(), kAmvmThreads, 0, s>>>(d_items, d_adm, d_krank, d_uptr, d_vptr, xc,
+                                                                        c1, c2, d_doff, D);
         HM_CUDA(cudaGetLastError());
         return HM_OK;
     };
@@ -436,9 +506,23 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
         amvm_rowsum_kernel<<<gM, 256, 0, s>>>(d_ipos, d_aptr, d_aidx, d_adm, d_doff, D, d_flags, 1, bk, M);
         HM_CUDA(cudaGetLastError());
         items.clear();
+        std::map<int, std::vector<int32_t>> rerun;  // on demand: tasks to extend, by their new kmax
         for (int32_t b : newly) {
             r[(size_t)b] += look;
             items.push_back(AmvmItem{b, r[(size_t)b], r[(size_t)b] + look, 0});
+            if (lazy)
+                for (int k = 0; k < 7; ++k) {
+                    const size_t q = (size_t)b * 7 + (size_t)k;
+                    const int want = std::min(r[(size_t)b] + look, kcap);
+                    // a run that stopped before its kmax has the whole sequence
+                    if (kmax_run[q] > 0 && krank[q] == kmax_run[q] && want > kmax_run[q])
+                        rerun[want].push_back((int32_t)q);
+                }
+        }
+        if (!rerun.empty()) {
+            for (auto& kv : rerun)
+                if ((rc = run_aca(kv.second, kv.first))) return rc;
+            if ((rc = upload_factors())) return rc;
         }
         if ((rc = parts(items))) return rc;
         ++it;
@@ -454,7 +538,7 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
         int64_t used = 0, full = 0;
         for (int64_t b = 0; b < nb; ++b)
             for (int k = 0; k < 7; ++k) {
-                const int32_t K = H->rank_h[(size_t)(b * 7 + k)];
+                const int32_t K = lazy ? krank[(size_t)(b * 7 + k)] : H->rank_h[(size_t)(b * 7 + k)];
                 used += std::min<int64_t>(K, r[(size_t)b]);
                 full += K;
             }

@@ -699,6 +699,112 @@ struct TmpBuf {
 }  // namespace
 
 // ------------------------------------------------------------------------
+int aca_on_demand(hm_matrix& H, const std::vector<int32_t>& bk, int kmax, cudaStream_t s, DevBuf& out,
+                  std::vector<int32_t>& rank, std::vector<int64_t>& off)
+{
+    const int64_t nt = (int64_t)bk.size();
+    rank.assign((size_t)nt, 0);
+    off.assign((size_t)nt, 0);
+    if (nt == 0) return HM_OK;
+    if (!H.g_coll.p) return fail(HM_EINVAL, "ACA on demand: the matrix keeps no geometry");
+    if (kmax < 1) return fail(HM_EINVAL, "ACA on demand: kmax %d < 1", kmax);
+    const Geom g{H.g_coll.as<double>(), H.g_tri.as<double>(), H.g_qp.as<double>(), H.g_qw.as<double>(),
+                 H.g_diam.as<double>()};
+    // tasks by decreasing |t| + |s| (as at assembly); ord maps back
+    std::vector<int64_t> ord((size_t)nt);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) {
+        const Blk& a = H.adm_h[(size_t)(bk[(size_t)x] / 7)];
+        const Blk& c = H.adm_h[(size_t)(bk[(size_t)y] / 7)];
+        return (int64_t)a.m + a.n > (int64_t)c.m + c.n;
+    });
+    std::vector<AcaTask> tasks((size_t)nt);
+    unsigned long long cap = 1;  // every task's factors fit: kmax (m + n) each at most
+    for (int64_t q = 0; q < nt; ++q) {
+        const int32_t v = bk[(size_t)ord[(size_t)q]];
+        tasks[(size_t)q] = AcaTask{v / 7, v % 7};
+        const Blk& b = H.adm_h[(size_t)(v / 7)];
+        cap += (unsigned long long)std::min(kmax, std::min(b.m, b.n)) * (unsigned long long)(b.m + b.n);
+    }
+    const double eps = H.prm.aca_eps;
+    const double fac = eps * (1.0 - H.prm.aca_eta_stop) / (1.0 + eps);
+    int dev = 0, nsm = 0, occ = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, aca_kernel, kAcaThreads, 0));
+    const int64_t full_grid = (int64_t)nsm * std::max(1, std::min(occ, 4));
+    struct Cls {
+        int64_t i0, i1, grid;
+        AcaParams prm;
+    };
+    std::vector<Cls> cls;
+    size_t scr_bytes = 0, z_bytes = 0;
+    for (int64_t i0 = 0; i0 < nt;) {
+        const Blk& b0 = H.adm_h[(size_t)tasks[(size_t)i0].blk];
+        const int64_t half = ((int64_t)b0.m + b0.n) / 2;
+        int64_t i1 = i0 + 1;
+        while (i1 < nt) {
+            const Blk& b = H.adm_h[(size_t)tasks[(size_t)i1].blk];
+            if ((int64_t)b.m + b.n <= half) break;
+            ++i1;
+        }
+        Cls c;
+        c.i0 = i0;
+        c.i1 = i1;
+        int mmax = 1, nmax = 1, kc = 1;
+        for (int64_t q = i0; q < i1; ++q) {
+            const Blk& b = H.adm_h[(size_t)tasks[(size_t)q].blk];
+            mmax = std::max(mmax, b.m);
+            nmax = std::max(nmax, b.n);
+            kc = std::max(kc, std::min(b.m, b.n));
+        }
+        c.prm.fac = fac;
+        c.prm.kmax = kmax;
+        c.prm.kcap_all = std::max(1, std::min(kc, kmax));
+        c.prm.mmax = mmax;
+        c.prm.nmax = nmax;
+        const size_t per_cta = (size_t)c.prm.kcap_all * (size_t)(mmax + nmax) * 8;
+        c.grid = std::max<int64_t>(1, std::min<int64_t>({full_grid, i1 - i0, (int64_t)(kAcaScratchBytes / per_cta)}));
+        scr_bytes = std::max(scr_bytes, (size_t)c.grid * per_cta);
+        z_bytes = std::max(z_bytes, (size_t)c.grid * (size_t)mmax);
+        cls.push_back(c);
+        i0 = i1;
+    }
+    int rc;
+    TmpBuf dscr(H), dz(H), dtask(H), dcnt(H), dtop(H), drank(H), doff(H), dflag(H);
+    if ((rc = dalloc(H, dscr.b, scr_bytes))) return rc;
+    if ((rc = dalloc(H, dz.b, z_bytes))) return rc;
+    if ((rc = upload(H, dtask.b, tasks.data(), tasks.size() * sizeof(AcaTask)))) return rc;
+    if ((rc = dalloc(H, dcnt.b, 64))) return rc;
+    if ((rc = dalloc(H, dtop.b, 64))) return rc;
+    if ((rc = dalloc(H, drank.b, (size_t)nt * 4))) return rc;
+    if ((rc = dalloc(H, doff.b, (size_t)nt * 8))) return rc;
+    if ((rc = dalloc(H, dflag.b, (size_t)nt * 4))) return rc;
+    if ((rc = dalloc(H, out, (size_t)cap * 8))) return rc;
+    HM_CUDA(cudaMemsetAsync(dtop.b.p, 0, 64, s));
+    for (const Cls& c : cls) {
+        HM_CUDA(cudaMemsetAsync(dcnt.b.p, 0, 64, s));
+        aca_kernel<<<(unsigned)c.grid, kAcaThreads, 0, s>>>(
+            g, dtask.b.as<AcaTask>() + c.i0, (int)(c.i1 - c.i0), H.d_adm.as<Blk>(), c.prm, dscr.b.as<double>(),
+            dz.b.as<unsigned char>(), dcnt.b.as<int>(), out.as<double>(), dtop.b.as<unsigned long long>(), cap,
+            drank.b.as<int32_t>() + c.i0, doff.b.as<int64_t>() + c.i0, dflag.b.as<int32_t>() + c.i0);
+        HM_CUDA(cudaGetLastError());
+    }
+    std::vector<int32_t> r((size_t)nt), f((size_t)nt);
+    std::vector<int64_t> o((size_t)nt);
+    HM_CUDA(cudaMemcpyAsync(r.data(), drank.b.p, (size_t)nt * 4, cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaMemcpyAsync(o.data(), doff.b.p, (size_t)nt * 8, cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaMemcpyAsync(f.data(), dflag.b.p, (size_t)nt * 4, cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaStreamSynchronize(s));
+    for (int64_t q = 0; q < nt; ++q) {
+        if (f[(size_t)q] & 8) return fail(HM_EDEVICE, "ACA on demand: arena overflow");
+        rank[(size_t)ord[(size_t)q]] = r[(size_t)q];
+        off[(size_t)ord[(size_t)q]] = o[(size_t)q];
+    }
+    return HM_OK;
+}
+
+// ------------------------------------------------------------------------
 std::vector<FwdTcUnit> tc_units(const std::vector<FwdUnit>& units, const std::vector<FwdGroup>& groups)
 {
     std::vector<FwdTcUnit> out(units.size());
@@ -756,21 +862,22 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
     }
     int rc;
     if ((rc = upload(H, H.d_perm, perm32.data(), perm32.size() * 4))) return rc;
-    TmpBuf dV(H), dT(H), dcoll(H), dtri(H), dqp(H), dqw(H), ddiam(H);
+    // the geometry of the entries stays with the matrix (ACA on demand)
+    TmpBuf dV(H), dT(H);
     if ((rc = upload(H, dV.b, tr.V.data(), tr.V.size() * 8))) return rc;
     if ((rc = upload(H, dT.b, tr.T.data(), tr.T.size() * 4))) return rc;
-    if ((rc = upload(H, dcoll.b, coll.data(), coll.size() * 8))) return rc;
-    if ((rc = upload(H, ddiam.b, diam2.data(), diam2.size() * 8))) return rc;
-    if ((rc = dalloc(H, dtri.b, (size_t)M * 9 * 8))) return rc;
-    if ((rc = dalloc(H, dqp.b, (size_t)M * 21 * 8))) return rc;
-    if ((rc = dalloc(H, dqw.b, (size_t)M * 7 * 8))) return rc;
+    if ((rc = upload(H, H.g_coll, coll.data(), coll.size() * 8))) return rc;
+    if ((rc = upload(H, H.g_diam, diam2.data(), diam2.size() * 8))) return rc;
+    if ((rc = dalloc(H, H.g_tri, (size_t)M * 9 * 8))) return rc;
+    if ((rc = dalloc(H, H.g_qp, (size_t)M * 21 * 8))) return rc;
+    if ((rc = dalloc(H, H.g_qw, (size_t)M * 7 * 8))) return rc;
     geom_kernel<<<(unsigned)((M + 127) / 128), 128, 0, s>>>((int)M, H.d_perm.as<int32_t>(),
                                                             dT.b.as<int32_t>(), dV.b.as<double>(),
-                                                            dtri.b.as<double>(), dqp.b.as<double>(),
-                                                            dqw.b.as<double>());
+                                                            H.g_tri.as<double>(), H.g_qp.as<double>(),
+                                                            H.g_qw.as<double>());
     HM_CUDA(cudaGetLastError());
-    Geom g{dcoll.b.as<double>(), dtri.b.as<double>(), dqp.b.as<double>(), dqw.b.as<double>(),
-           ddiam.b.as<double>()};
+    Geom g{H.g_coll.as<double>(), H.g_tri.as<double>(), H.g_qp.as<double>(), H.g_qw.as<double>(),
+           H.g_diam.as<double>()};
 
     // ---- block lists
     auto blk_of = [&](const std::array<int64_t, 2>& ts) {
@@ -838,6 +945,11 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
             else
                 tasks.push_back(AcaTask{(int32_t)b, k});
         }
+    }
+    if (H.prm.flags & HM_DEFER_ACA) {
+        // the adaptive product runs Algorithm 1 on demand (hm_amvm)
+        tasks.clear();
+        H.aca_deferred = true;
     }
     const int64_t ntask = (int64_t)tasks.size();
     std::stable_sort(tasks.begin(), tasks.end(), [&](const AcaTask& x, const AcaTask& y) {
@@ -1298,7 +1410,7 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
     if ((rc = dalloc(H, H.xh, (size_t)H.max_rhs * 3 * M * 8))) return rc;
     if ((rc = dalloc(H, H.yh, (size_t)H.max_rhs * 3 * M * 8))) return rc;
     // the FP64 form, unless deferred to hm_pack
-    if (!(H.prm.flags & HM_DEFER_FP64))
+    if (!(H.prm.flags & (HM_DEFER_FP64 | HM_DEFER_ACA)))
         if ((rc = pack_device(H, HM_FP64, s))) return rc;
     HM_CUDA(cudaStreamSynchronize(s));
     float t01 = 0, t12 = 0, t23 = 0;
@@ -1329,7 +1441,8 @@ extern "C" int hm_aca_assemble(const hm_tree* tree, const hm_params* prm, const 
     if (prm->kmax < 0 || prm->kmax > kKmaxLimit)
         return fail(HM_EINVAL, "hm_aca_assemble: kmax must lie in 0..%d", kKmaxLimit);
     if (prm->max_rhs < 0 || prm->max_rhs > 64) return fail(HM_EINVAL, "hm_aca_assemble: max_rhs must lie in 0..64");
-    if (prm->flags & ~HM_DEFER_FP64) return fail(HM_EINVAL, "hm_aca_assemble: unknown flags 0x%x", prm->flags);
+    if (prm->flags & ~(HM_DEFER_FP64 | HM_DEFER_ACA))
+        return fail(HM_EINVAL, "hm_aca_assemble: unknown flags 0x%x", prm->flags);
     hm_matrix* H = new (std::nothrow) hm_matrix();
     if (!H) return fail(HM_ENOMEM, "hm_aca_assemble: out of host memory");
     H->prm = *prm;

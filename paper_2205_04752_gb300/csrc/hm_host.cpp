@@ -494,7 +494,7 @@ int hm_footprint(const hm_matrix* H, int64_t* bytes)
                                 &H->d_mesh[0], &H->d_mesh[1], &H->d_mesh[2], &H->d_mesh[3], &H->d_counters,
                                 &H->d_err, &H->U64, &H->V64, &H->N64, &H->Ul[0], &H->Ul[1], &H->Ul[2],
                                 &H->Ul[3], &H->Vr[0], &H->Vr[1], &H->Vr[2], &H->Vr[3], &H->Nl64, &H->Nl32,
-                                &H->SU, &H->SV, &H->xg, &H->wb, &H->zb, &H->xh, &H->yh};
+                                &H->SU, &H->SV, &H->xg, &H->wb, &H->zb, &H->xh, &H->yh, &H->g_coll, &H->g_tri, &H->g_qp, &H->g_qw, &H->g_diam};
     int64_t t = 0;
     for (const hm::DevBuf* b : bufs)
         if (b->p) t += (int64_t)b->bytes;
@@ -514,7 +514,7 @@ void hm_matrix_destroy(hm_matrix* H)
                           &H->d_mesh[3], &H->d_counters, &H->d_err, &H->U64, &H->V64, &H->N64,
                           &H->Ul[0], &H->Ul[1], &H->Ul[2], &H->Ul[3], &H->Vr[0], &H->Vr[1],
                           &H->Vr[2], &H->Vr[3], &H->Nl64, &H->Nl32, &H->SU, &H->SV, &H->xg, &H->wb, &H->zb,
-                          &H->xh, &H->yh};
+                          &H->xh, &H->yh, &H->g_coll, &H->g_tri, &H->g_qp, &H->g_qw, &H->g_diam};
     // the assembly stream may be gone by now: drain the device and release
     // on the legacy default stream
     cudaDeviceSynchronize();

@@ -273,6 +273,8 @@ struct hm_matrix {
     bool packed[4] = {false, false, false, false};
     float wbound_su = 0.0f;  // max over factor columns of (U column scale x |s| of its block)
     bool compacted = false;  // FP64 data released (hm_compact)
+    bool aca_deferred = false;  // HM_DEFER_ACA: no ACA at assembly (adaptive product only)
+    hm::DevBuf g_coll, g_tri, g_qp, g_qw, g_diam;  // cluster-order geometry of the entries (ACA on demand)
 
     // workspace
     int32_t max_rhs = 32;
@@ -324,6 +326,14 @@ MeshDev mesh_desc(const hm_matrix& H, int32_t form);
 void prof_mark(const hm_matrix& H, int which, cudaStream_t s);
 // kernels launchers (implemented in the .cu files)
 int assemble_device(const hm_tree& tr, hm_matrix& H);
+// Algorithm 1 on demand: the (block, kernel) tasks bk[q] = block * 7 + kernel,
+// each stopped after kmax crosses at most (or earlier by its stop test), into
+// a new arena `out` from the matrix's allocator; per task its rank and the
+// element offset of its U (k x m) with V (k x n) right after it.  The same
+// task gives the same first crosses for any kmax (the kernel is
+// deterministic).
+int aca_on_demand(hm_matrix& H, const std::vector<int32_t>& bk, int kmax, cudaStream_t s, DevBuf& out,
+                  std::vector<int32_t>& rank, std::vector<int64_t>& off);
 int matvec_device(const hm_matrix& H, const double* x, double* y, int32_t nrhs, int64_t ld,
                   int32_t form, cudaStream_t s);
 int pack_device(hm_matrix& H, int32_t form, cudaStream_t s);

@@ -1533,6 +1533,8 @@ int hm_pack(hm_matrix* H, int32_t form, void* stream)
     if (form < HM_FP64 || form > HM_FP16) return fail(HM_EINVAL, "hm_pack: unknown form %d", form);
     if (H->packed[form]) return HM_OK;
     if (H->compacted) return fail(HM_EINVAL, "hm_pack: FP64 data released (hm_compact); pack before compacting");
+    if (H->aca_deferred)
+        return fail(HM_EINVAL, "hm_pack: ACA deferred (HM_DEFER_ACA): the matrix serves hm_amvm with ACA on demand only");
     cudaStream_t s = (cudaStream_t)stream;
     cudaStream_t saved = H->alloc.stream;
     H->alloc.stream = s;

@@ -125,3 +125,37 @@ def test_amvm_argument_errors():
     Hc.compact()
     with pytest.raises(binding.HMError):
         binding.amvm(Hc, x, y)
+
+
+def test_aca_on_demand_repeats_the_assembled_crosses():
+    """Algorithm 1 run on demand (every block-kernel to r0 + look crosses,
+    refined ones further) computes the same first crosses as the full
+    assembly, so the adaptive product is bitwise the same, with fewer crosses
+    computed than the full ACA holds."""
+    V, T, tree, H, Ho = case()
+    x = inputs.uniform_rhs(3 * Ho.M, 8)[0]
+    y1, i1 = run(H, x, theta=0.7, eps=1e-6)
+    y2, i2 = run(H, x, theta=0.7, eps=1e-6, on_demand=True)
+    assert np.array_equal(y1, y2)
+    assert i1["iterations"] == i2["iterations"] and i1["gamma"] == i2["gamma"]
+    assert np.array_equal(i1["block_ranks"], i2["block_ranks"])
+    assert i2["crosses_used"] == i1["crosses_used"]
+    assert i2["crosses_full"] < i1["crosses_full"]
+
+
+def test_deferred_aca_matrix_serves_the_adaptive_product_only():
+    """HM_DEFER_ACA: no ACA at assembly; the matrix cannot be packed, the
+    prefix mode is refused, and the on-demand adaptive product gives the same
+    bits as on the fully assembled matrix."""
+    V, T, tree, H, Ho = case()
+    Hd = binding.aca_assemble(tree, E, NU, 1e-8, max_rhs=1, defer_aca=True)
+    with pytest.raises(binding.HMError):
+        Hd.pack("fp16")
+    x = inputs.uniform_rhs(3 * Ho.M, 9)[0]
+    xd = torch.tensor(x, device="cuda")
+    with pytest.raises(binding.HMError):
+        binding.amvm(Hd, xd, torch.empty_like(xd))
+    y1, i1 = run(H, x, theta=0.7, eps=1e-6, on_demand=True)
+    y2, i2 = run(Hd, x, theta=0.7, eps=1e-6, on_demand=True)
+    assert np.array_equal(y1, y2)
+    assert i1["crosses_full"] == i2["crosses_full"]
