@@ -21,10 +21,11 @@
 //
 // The crosses come either from the assembled ACA (prefixes of its sequences)
 // or, with HM_AMVM_ACA_ON_DEMAND, from Algorithm 1 run on demand: every
-// block-kernel to r0 + look crosses first, a refined block's kernels again to
-// its new r_b + look (the batched ACA kernel is deterministic, so a longer run
-// repeats the first crosses), so that only the crosses the refinement reaches
-// are ever computed -- the combination of assembly and product of Section 3.
+// block-kernel to r0 + look crosses first, a refined block's kernels on to
+// its new r_b + look, resumed from the state their last run ended in (its
+// crosses, Z, the next row and ||S_k||), so that only the crosses the
+// refinement reaches are ever computed -- the combination of assembly and
+// product of Section 3.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -355,14 +356,38 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
     // and how many there are (krank); on demand, also the kmax of the run
     // that produced them
     std::vector<const double*> uptr((size_t)nb * 7, nullptr), vptr((size_t)nb * 7, nullptr);
-    std::vector<int32_t> krank((size_t)nb * 7, 0), kmax_run((size_t)nb * 7, 0);
+    std::vector<int32_t> krank((size_t)nb * 7, 0), kflags((size_t)nb * 7, 0);
     const int kcap = std::max(1, (int)H->prm.kmax);
+    // resumable ACA state (on demand)
+    AcaResume rs{};
+    std::vector<const double*> prev((size_t)nb * 7, nullptr);
+    const double** d_prev = nullptr;
+    if (lazy) {
+        std::vector<int64_t> zoff((size_t)nb * 7 + 1, 0);
+        for (int64_t q = 0; q < nb * 7; ++q) zoff[(size_t)q + 1] = zoff[(size_t)q] + H->adm_h[(size_t)(q / 7)].m;
+        rs.k = pool.get<int32_t>((size_t)nb * 7);
+        rs.nz = pool.get<int32_t>((size_t)nb * 7);
+        rs.irow = pool.get<int32_t>((size_t)nb * 7);
+        rs.flags = pool.get<int32_t>((size_t)nb * 7);
+        rs.S2 = pool.get<double>((size_t)nb * 7);
+        rs.Z = pool.get<unsigned char>((size_t)zoff[(size_t)nb * 7]);
+        int64_t* d_zoff = pool.get<int64_t>(zoff.size());
+        d_prev = pool.get<const double*>((size_t)nb * 7);
+        if (!rs.k || !rs.nz || !rs.irow || !rs.flags || !rs.S2 || !rs.Z || !d_zoff || !d_prev)
+            return fail(HM_ENOMEM, "hm_amvm: ACA state");
+        if ((rc = put(d_zoff, zoff, s))) return rc;
+        HM_CUDA(cudaMemsetAsync(rs.flags, 0, (size_t)nb * 7 * 4, s));
+        rs.zoff = d_zoff;
+        rs.prevU = d_prev;
+    }
     auto run_aca = [&](const std::vector<int32_t>& bkl, int kmax) -> int {
         if (bkl.empty()) return HM_OK;
         std::vector<int32_t> rr;
         std::vector<int64_t> oo;
         DevBuf arena;
-        int rc2 = aca_on_demand(Hm, bkl, kmax, s, arena, rr, oo);
+        int rc2 = put(d_prev, prev, s);  // resume from these (null: afresh)
+        if (rc2) return rc2;
+        rc2 = aca_on_demand(Hm, bkl, kmax, s, arena, rr, oo, &rs);
         if (arena.p) restore.arenas.push_back(arena);
         if (rc2) return rc2;
         for (size_t q = 0; q < bkl.size(); ++q) {
@@ -371,8 +396,10 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
             uptr[(size_t)v] = arena.as<double>() + oo[q];
             vptr[(size_t)v] = uptr[(size_t)v] + (int64_t)rr[q] * bb.m;
             krank[(size_t)v] = rr[q];
-            kmax_run[(size_t)v] = kmax;
         }
+        // the exit flags: bit 0 = stopped at kmax (the sequence goes on)
+        HM_CUDA(cudaMemcpyAsync(kflags.data(), rs.flags, kflags.size() * 4, cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaStreamSynchronize(s));
         return HM_OK;
     };
     auto upload_factors = [&]() -> int {
@@ -514,12 +541,16 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
                 for (int k = 0; k < 7; ++k) {
                     const size_t q = (size_t)b * 7 + (size_t)k;
                     const int want = std::min(r[(size_t)b] + look, kcap);
-                    // a run that stopped before its kmax has the whole sequence
-                    if (kmax_run[q] > 0 && krank[q] == kmax_run[q] && want > kmax_run[q])
+                    // only a run that stopped at its kmax has more crosses to give
+                    // (an identically zero kernel never ran: flag 32)
+                    if (!(H->flags_h[q] & 32) && (kflags[q] & 1) && want > krank[q])
                         rerun[want].push_back((int32_t)q);
                 }
         }
         if (!rerun.empty()) {
+            std::fill(prev.begin(), prev.end(), nullptr);
+            for (auto& kv : rerun)
+                for (int32_t q : kv.second) prev[(size_t)q] = uptr[(size_t)q];
             for (auto& kv : rerun)
                 if ((rc = run_aca(kv.second, kv.first))) return rc;
             if ((rc = upload_factors())) return rc;

@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(kAcaThreads) aca_kernel(
     AcaParams prm, double* __restrict__ scratch, unsigned char* __restrict__ zscr,
     int* __restrict__ counter, double* __restrict__ arena, unsigned long long* __restrict__ arena_top,
     unsigned long long arena_cap, int32_t* __restrict__ out_rank, int64_t* __restrict__ out_off,
-    int32_t* __restrict__ out_flags)
+    int32_t* __restrict__ out_flags, AcaResume rs)
 {
     __shared__ AcaShared sh;
     const int tid = threadIdx.x;
@@ -481,9 +481,25 @@ __global__ void __launch_bounds__(kAcaThreads) aca_kernel(
         const int ka = kern == 0 ? 0 : (kern <= 3 ? 0 : (kern <= 5 ? 1 : 2));
         const int kb = kern == 0 ? 0 : (kern <= 3 ? kern - 1 : (kern <= 5 ? kern - 3 : 2));
         int kcap = min(prm.kmax, min(m, n));
-        for (int i = tid; i < m; i += B) Z[i] = 0;
         int k = 0, nz = 0, flags = 0, irow = 0;
         double S2 = 0.0;
+        const int64_t q7 = (int64_t)tk.blk * 7 + kern;
+        const double* prevU = rs.k ? rs.prevU[q7] : nullptr;
+        if (prevU) {
+            // resume: the previous run's crosses, Z, next row and ||S||^2
+            k = rs.k[q7];
+            nz = rs.nz[q7];
+            irow = rs.irow[q7];
+            S2 = rs.S2[q7];
+            const double* prevV = prevU + (size_t)k * m;
+            for (int l = 0; l < k; ++l) {
+                for (int i = tid; i < m; i += B) U[(size_t)l * m + i] = prevU[(size_t)l * m + i];
+                for (int j = tid; j < n; j += B) Vf[(size_t)l * n + j] = prevV[(size_t)l * n + j];
+            }
+            for (int i = tid; i < m; i += B) Z[i] = rs.Z[rs.zoff[q7] + i];
+        } else {
+            for (int i = tid; i < m; i += B) Z[i] = 0;
+        }
         __syncthreads();
         for (;;) {
             if (k >= prm.kmax) {
@@ -605,7 +621,10 @@ __global__ void __launch_bounds__(kAcaThreads) aca_kernel(
                 flags |= 2;
                 break;
             }
-            if (k >= kcap) {
+            // at kmax below min(|t|, |s|) a resumable run (ACA on demand) also
+            // finds the next row, so that a later run can go on from it; it
+            // then stops at the top of the loop (flag 1)
+            if (k >= kcap && !(rs.k && kcap == prm.kmax && prm.kmax < min(m, n))) {
                 flags |= 4;
                 break;
             }
@@ -618,6 +637,17 @@ __global__ void __launch_bounds__(kAcaThreads) aca_kernel(
         }
         // append the factors to the arena
         __syncthreads();
+        if (rs.k) {
+            // the state a later run resumes from
+            if (tid == 0) {
+                rs.k[q7] = k;
+                rs.nz[q7] = nz;
+                rs.irow[q7] = irow;
+                rs.flags[q7] = flags;
+                rs.S2[q7] = S2;
+            }
+            for (int i = tid; i < m; i += B) rs.Z[rs.zoff[q7] + i] = Z[i];
+        }
         if (tid == 0) {
             unsigned long long need = (unsigned long long)k * (m + n);
             unsigned long long off = atomicAdd(arena_top, need);
@@ -700,7 +730,7 @@ struct TmpBuf {
 
 // ------------------------------------------------------------------------
 int aca_on_demand(hm_matrix& H, const std::vector<int32_t>& bk, int kmax, cudaStream_t s, DevBuf& out,
-                  std::vector<int32_t>& rank, std::vector<int64_t>& off)
+                  std::vector<int32_t>& rank, std::vector<int64_t>& off, const AcaResume* resume)
 {
     const int64_t nt = (int64_t)bk.size();
     rank.assign((size_t)nt, 0);
@@ -787,7 +817,8 @@ int aca_on_demand(hm_matrix& H, const std::vector<int32_t>& bk, int kmax, cudaSt
         aca_kernel<<<(unsigned)c.grid, kAcaThreads, 0, s>>>(
             g, dtask.b.as<AcaTask>() + c.i0, (int)(c.i1 - c.i0), H.d_adm.as<Blk>(), c.prm, dscr.b.as<double>(),
             dz.b.as<unsigned char>(), dcnt.b.as<int>(), out.as<double>(), dtop.b.as<unsigned long long>(), cap,
-            drank.b.as<int32_t>() + c.i0, doff.b.as<int64_t>() + c.i0, dflag.b.as<int32_t>() + c.i0);
+            drank.b.as<int32_t>() + c.i0, doff.b.as<int64_t>() + c.i0, dflag.b.as<int32_t>() + c.i0,
+            resume ? *resume : AcaResume{});
         HM_CUDA(cudaGetLastError());
     }
     std::vector<int32_t> r((size_t)nt), f((size_t)nt);
@@ -1046,7 +1077,7 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
                 g, dtask.b.as<AcaTask>() + c.i0, (int)(c.i1 - c.i0), H.d_adm.as<Blk>(), c.prm,
                 dscr.b.as<double>(), dz.b.as<unsigned char>(), dcnt.b.as<int>(), darena.b.as<double>(),
                 dtop.b.as<unsigned long long>(), cap, drank.b.as<int32_t>() + c.i0, doff.b.as<int64_t>() + c.i0,
-                dflag.b.as<int32_t>() + c.i0);
+                dflag.b.as<int32_t>() + c.i0, AcaResume{});
             HM_CUDA(cudaGetLastError());
         }
         HM_CUDA(cudaMemcpyAsync(trank.data(), drank.b.p, (size_t)ntask * 4, cudaMemcpyDeviceToHost, s));
@@ -1086,7 +1117,8 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
                 aca_kernel<<<(unsigned)c.grid, kAcaThreads, 0, s>>>(
                     g, t2.b.as<AcaTask>() + c.i0, (int)(c.i1 - c.i0), H.d_adm.as<Blk>(), c.prm, dscr.b.as<double>(),
                     dz.b.as<unsigned char>(), dcnt.b.as<int>(), a2.as<double>(), dtop.b.as<unsigned long long>(),
-                    need + 1, r2.b.as<int32_t>() + c.i0, o2.b.as<int64_t>() + c.i0, f2.b.as<int32_t>() + c.i0);
+                    need + 1, r2.b.as<int32_t>() + c.i0, o2.b.as<int64_t>() + c.i0, f2.b.as<int32_t>() + c.i0,
+                    AcaResume{});
                 HM_CUDA(cudaGetLastError());
             }
             // the re-run results: offsets past `cap` address the second arena

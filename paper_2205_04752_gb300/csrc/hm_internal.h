@@ -332,8 +332,21 @@ int assemble_device(const hm_tree& tr, hm_matrix& H);
 // element offset of its U (k x m) with V (k x n) right after it.  The same
 // task gives the same first crosses for any kmax (the kernel is
 // deterministic).
+// State of resumable ACA tasks (device arrays indexed by block * 7 + kernel):
+// the crosses so far, the rows in Z, the next row, the exit flags of the last
+// run (bit 0: stopped at kmax, so it can go on), ||S_k||_F^2, Z itself (m
+// bytes per task at zoff), and the previous run's U (k x m, V right after) or
+// null to start afresh.  A resumed task takes exactly the steps a fresh run to
+// the same kmax would take after its first k crosses.
+struct AcaResume {
+    int32_t *k, *nz, *irow, *flags;
+    double* S2;
+    unsigned char* Z;
+    const int64_t* zoff;
+    const double* const* prevU;
+};
 int aca_on_demand(hm_matrix& H, const std::vector<int32_t>& bk, int kmax, cudaStream_t s, DevBuf& out,
-                  std::vector<int32_t>& rank, std::vector<int64_t>& off);
+                  std::vector<int32_t>& rank, std::vector<int64_t>& off, const AcaResume* resume = nullptr);
 int matvec_device(const hm_matrix& H, const double* x, double* y, int32_t nrhs, int64_t ld,
                   int32_t form, cudaStream_t s);
 int pack_device(hm_matrix& H, int32_t form, cudaStream_t s);
