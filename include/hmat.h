@@ -367,8 +367,8 @@ int hm_solve(const hm_matrix* H, const double* g, double* t, const hm_solve_para
  * (ties: increasing row), adding every block t x s with i in t whose part
  * satisfies |[(A_k - A^_k)_ts x_s]_i| >= (1 - theta)(c_sp N N)^{-1/2}
  * gamma_k (N = 3M dofs, c_sp the sparsity constant of Section 2.1), until
- * gamma_k - gamma_k(P_k) >= theta gamma_k; marked blocks take the
- * look-ahead ranks.  The loop ends when gamma_k <= eps ||A^_k x||_2, when
+ * gamma_k - gamma_k(P_k) >= theta gamma_k (the stopping row found by
+ * bisection over the sorted rows); marked blocks take the look-ahead ranks.  The loop ends when gamma_k <= eps ||A^_k x||_2, when
  * no block can be refined, or after max_iter refinements.
  *   x, y      device, 3M doubles each, original dof order; y = A_k x at exit
  *   info      optional: iterations, c_sp, last gamma, ||A^_k x||, crosses
@@ -378,8 +378,10 @@ int hm_solve(const hm_matrix* H, const double* g, double* t, const hm_solve_para
  *   block_ranks  optional host array of nadm ints: r_b at exit
  * Needs the FP64 factors (or HM_AMVM_ACA_ON_DEMAND) and the near field
  * (HM_EINVAL after hm_compact).
- * Allocates about 24 (3M) + 24 sum|t| bytes of workspace through the
- * matrix's allocator for the duration of the call; synchronises `stream`.
+ * Allocates about 40 (3M) + 24 sum|t| bytes of workspace (with ACA on demand
+ * also the factors it computes and about 7 sum|t| bytes of ACA state)
+ * through the matrix's allocator for the duration of the call; synchronises
+ * `stream`.
  * ------------------------------------------------------------------------- */
 typedef struct {
     double theta;      /* Doerfler parameter in (0, 1) (0 = 0.7) */

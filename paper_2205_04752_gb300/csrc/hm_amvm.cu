@@ -16,8 +16,9 @@
 // reductions, then U times them row by row), the row sums of all parts (each
 // position adds the parts of the blocks whose row cluster holds it, in block
 // order: deterministic), and the update of b_k by the marked blocks' parts.
-// The marking itself is a sequential scan (it stops at the first row that
-// meets the condition); it runs on the host over the copied parts.
+// The marking runs on the device too: the rows sorted by their error, the
+// row at which each block joins the marked set, and a bisection for the row
+// at which the Doerfler condition holds (see step 3 below).
 //
 // The crosses come either from the assembled ACA (prefixes of its sequences)
 // or, with HM_AMVM_ACA_ON_DEMAND, from Algorithm 1 run on demand: every
@@ -201,6 +202,130 @@ __global__ void amvm_rowsum_kernel(const int32_t* __restrict__ ipos, const int32
     }
 }
 
+// ---- step 3 on the device
+// the rows in decreasing |e_i| (ties: increasing i): a bitonic sort of (key,
+// row) over P = a power of two >= N (padding keys -1 sort last)
+__global__ void amvm_sort_init_kernel(const double* __restrict__ e, int64_t N, int64_t P, double* __restrict__ key,
+                                      int32_t* __restrict__ idx)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    key[i] = i < N ? fabs(e[i]) : -1.0;
+    idx[i] = (int32_t)i;
+}
+
+__global__ void amvm_bitonic_kernel(double* __restrict__ key, int32_t* __restrict__ idx, int64_t P, int64_t j,
+                                    int64_t k)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    const int64_t l = i ^ j;
+    if (l <= i) return;
+    const double ka = key[i], kb = key[l];
+    const int32_t ia = idx[i], ib = idx[l];
+    const bool a_first = ka > kb || (ka == kb && ia < ib);
+    const bool up = (i & k) == 0;
+    if (a_first != up) {
+        key[i] = kb;
+        key[l] = ka;
+        idx[i] = ib;
+        idx[l] = ia;
+    }
+}
+
+__global__ void amvm_rowpos_kernel(const int32_t* __restrict__ idx, int64_t N, int32_t* __restrict__ rowpos)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < N) rowpos[idx[p]] = (int32_t)p;
+}
+
+// first[b]: the earliest position (in the sorted rows) of a row of block b
+// whose part reaches thr, INT_MAX if none; one CTA per block
+__global__ void __launch_bounds__(256) amvm_first_kernel(const Blk* __restrict__ adm,
+                                                         const int64_t* __restrict__ doff,
+                                                         const double* __restrict__ D,
+                                                         const int32_t* __restrict__ rowpos, double thr,
+                                                         int32_t* __restrict__ first)
+{
+    __shared__ int32_t red[8];
+    const int b = blockIdx.x;
+    const Blk bk = adm[b];
+    const double* d = D + doff[b];
+    const int64_t r0 = 3 * (int64_t)bk.t0;
+    int32_t best = INT_MAX;
+    for (int z = threadIdx.x; z < 3 * bk.m; z += blockDim.x)
+        if (fabs(d[z]) >= thr) best = min(best, rowpos[r0 + z]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) best = min(best, red[w]);
+        first[b] = best;
+    }
+}
+
+__global__ void amvm_cut_kernel(const int32_t* __restrict__ first, int64_t nb, int32_t j, uint8_t* __restrict__ flags)
+{
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb) flags[b] = first[b] <= j ? 1 : 0;
+}
+
+// the squares of e - (the flagged parts), summed per CTA (fixed order)
+__global__ void __launch_bounds__(256) amvm_rest_kernel(const int32_t* __restrict__ ipos,
+                                                        const int32_t* __restrict__ aptr,
+                                                        const int32_t* __restrict__ aidx,
+                                                        const Blk* __restrict__ adm,
+                                                        const int64_t* __restrict__ doff,
+                                                        const double* __restrict__ D,
+                                                        const uint8_t* __restrict__ flags,
+                                                        const double* __restrict__ e, int64_t M,
+                                                        double* __restrict__ partial)
+{
+    __shared__ double red[8];
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (p < M) {
+        const int I = ipos[p];
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+        for (int q = aptr[I]; q < aptr[I + 1]; ++q) {
+            const int b = aidx[q];
+            if (!flags[b]) continue;
+            const double* d = D + doff[b] + 3 * (p - adm[b].t0);
+            s0 += d[0];
+            s1 += d[1];
+            s2 += d[2];
+        }
+        const double r0 = e[3 * p] - s0, r1 = e[3 * p + 1] - s1, r2 = e[3 * p + 2] - s2;
+        v = r0 * r0 + r1 * r1 + r2 * r2;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+        partial[blockIdx.x] = v;
+    }
+}
+
+// out = the sum of n partial sums, in a fixed order (one CTA)
+__global__ void __launch_bounds__(256) amvm_sum_kernel(const double* __restrict__ partial, int64_t n,
+                                                       double* __restrict__ out)
+{
+    __shared__ double red[8];
+    double v = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) v += partial[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+        out[0] = v;
+    }
+}
+
 // elementary intervals of cluster positions (between consecutive block row
 // boundaries) and, per interval, the blocks whose row range covers it, in
 // block order
@@ -340,6 +465,16 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
     int64_t* d_doff = pool.get<int64_t>(doff.size());
     AmvmItem* d_items = pool.get<AmvmItem>((size_t)nb);
     uint8_t* d_flags = pool.get<uint8_t>((size_t)nb);
+    int64_t P = 1;
+    while (P < N) P <<= 1;
+    double* d_key = pool.get<double>((size_t)P);
+    int32_t* d_sidx = pool.get<int32_t>((size_t)P);
+    int32_t* d_rowpos = pool.get<int32_t>((size_t)N);
+    int32_t* d_first = pool.get<int32_t>((size_t)nb);
+    double* d_part = pool.get<double>((size_t)(M + 255) / 256 + 1);
+    double* d_norm = pool.get<double>(1);
+    if (!d_key || !d_sidx || !d_rowpos || !d_first || !d_part || !d_norm)
+        return fail(HM_ENOMEM, "hm_amvm: marking workspace");
     const double** d_uptr = pool.get<const double*>((size_t)nb * 7);
     const double** d_vptr = pool.get<const double*>((size_t)nb * 7);
     int32_t* d_krank = pool.get<int32_t>((size_t)nb * 7);
@@ -451,9 +586,8 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
     for (int64_t b = 0; b < nb; ++b) items[(size_t)b] = AmvmItem{(int32_t)b, r0, r0 + look, 0};
     if ((rc = parts(items))) return rc;
 
-    std::vector<double> he((size_t)N), hb((size_t)N), hD((size_t)doff[(size_t)nb]);
+    std::vector<double> he((size_t)N), hb((size_t)N);
     std::vector<uint8_t> marked((size_t)nb);
-    std::vector<int64_t> order((size_t)N);
     int it = 0;
     int64_t marked_total = 0;
     double gamma = 0.0, bhat = 0.0;
@@ -478,58 +612,66 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
         bhat = std::sqrt(b2);
         if (it < hist_cap && gamma_hist) gamma_hist[it] = gamma;
         if (gamma <= eps * bhat || it >= max_iter) break;
-        // step 3: Doerfler marking through the rows in decreasing error
-        if (!hD.empty())
-            HM_CUDA(cudaMemcpyAsync(hD.data(), D, hD.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-        HM_CUDA(cudaStreamSynchronize(s));
+        // step 3: Doerfler marking through the rows in decreasing error, on the
+        // device: first[b] = the earliest sorted row at which block b joins P_k;
+        // the marked set after row j is {b : first[b] <= j}, and the stopping row
+        // is found by bisection on ||rest(j)|| <= (1 - theta) gamma_k (the first
+        // such row when ||rest|| decreases along the scan, as it does when parts
+        // remove error; otherwise a row where the condition holds)
         const double thr = (1.0 - theta) * gamma / std::sqrt((double)csp * (double)N * (double)N);
-        std::iota(order.begin(), order.end(), 0);
-        std::sort(order.begin(), order.end(), [&](int64_t a, int64_t c) {
-            const double ea = std::fabs(he[(size_t)a]), ec = std::fabs(he[(size_t)c]);
-            return ea > ec || (ea == ec && a < c);
-        });
-        std::vector<double> rest(he);
-        double n2 = g2, g_rest = gamma;
-        std::fill(marked.begin(), marked.end(), 0);
-        std::vector<int32_t> newly;
-        for (int64_t i : order) {
-            const int64_t p = i / 3, a = i - 3 * p;
-            const int I = ra.ipos[(size_t)p];
-            for (int q = ra.ptr[(size_t)I]; q < ra.ptr[(size_t)I + 1]; ++q) {
-                const int b = ra.idx[(size_t)q];
-                if (marked[(size_t)b]) continue;
-                const Blk& bb = H->adm_h[(size_t)b];
-                const double* Db = hD.data() + doff[(size_t)b];
-                if (std::fabs(Db[3 * (p - bb.t0) + a]) < thr) continue;
-                marked[(size_t)b] = 1;
-                newly.push_back(b);
-                for (int64_t z = 0; z < 3 * (int64_t)bb.m; ++z) {
-                    double& v = rest[(size_t)(3 * (int64_t)bb.t0 + z)];
-                    const double old = v;
-                    v -= Db[z];
-                    n2 += v * v - old * old;
+        const unsigned gP = (unsigned)((P + 255) / 256), gB = (unsigned)((nb + 255) / 256);
+        amvm_sort_init_kernel<<<gP, 256, 0, s>>>(e, N, P, d_key, d_sidx);
+        HM_CUDA(cudaGetLastError());
+        for (int64_t kk2 = 2; kk2 <= P; kk2 <<= 1)
+            for (int64_t jj = kk2 >> 1; jj > 0; jj >>= 1) {
+                amvm_bitonic_kernel<<<gP, 256, 0, s>>>(d_key, d_sidx, P, jj, kk2);
+                HM_CUDA(cudaGetLastError());
+            }
+        amvm_rowpos_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(d_sidx, N, d_rowpos);
+        HM_CUDA(cudaGetLastError());
+        amvm_first_kernel<<<(unsigned)nb, 256, 0, s>>>(d_adm, d_doff, D, d_rowpos, thr, d_first);
+        HM_CUDA(cudaGetLastError());
+        const int64_t npart = (M + 255) / 256;
+        auto rest2 = [&](int32_t j, double& out) -> int {
+            amvm_cut_kernel<<<gB, 256, 0, s>>>(d_first, nb, j, d_flags);
+            HM_CUDA(cudaGetLastError());
+            amvm_rest_kernel<<<(unsigned)npart, 256, 0, s>>>(d_ipos, d_aptr, d_aidx, d_adm, d_doff, D, d_flags, e,
+                                                            M, d_part);
+            HM_CUDA(cudaGetLastError());
+            amvm_sum_kernel<<<1, 256, 0, s>>>(d_part, npart, d_norm);
+            HM_CUDA(cudaGetLastError());
+            HM_CUDA(cudaMemcpyAsync(&out, d_norm, sizeof(double), cudaMemcpyDeviceToHost, s));
+            HM_CUDA(cudaStreamSynchronize(s));
+            return HM_OK;
+        };
+        const double target2 = (1.0 - theta) * gamma * (1.0 - theta) * gamma;
+        int32_t lo = 0, hi = (int32_t)(N - 1);
+        double f_hi = 0.0;
+        if ((rc = rest2(hi, f_hi))) return rc;
+        if (f_hi <= target2) {
+            while (lo < hi) {
+                const int32_t mid = lo + (hi - lo) / 2;
+                double f_mid = 0.0;
+                if ((rc = rest2(mid, f_mid))) return rc;
+                if (f_mid <= target2) {
+                    hi = mid;
+                    f_hi = f_mid;
+                } else {
+                    lo = mid + 1;
                 }
             }
-            g_rest = std::sqrt(std::max(n2, 0.0));
-            if (std::fabs(gamma - g_rest - theta * gamma) <= 1e-9 * gamma) {
-                // close to the condition: the exact norm of the rest decides
-                double x2 = 0.0;
-                for (double v : rest) x2 += v * v;
-                n2 = x2;
-                g_rest = std::sqrt(x2);
-            }
-            if (gamma - g_rest >= theta * gamma) break;
+            if ((rc = rest2(hi, f_hi))) return rc;  // the flags of the cut
         }
-        {
-            double x2 = 0.0;
-            for (double v : rest) x2 += v * v;
-            g_rest = std::sqrt(x2);
-        }
+        double g_rest = std::sqrt(std::max(f_hi, 0.0));
+        HM_CUDA(cudaMemcpyAsync(marked.data(), d_flags, (size_t)nb, cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaStreamSynchronize(s));
+        std::vector<int32_t> newly;
+        for (int64_t b = 0; b < nb; ++b)
+            if (marked[(size_t)b]) newly.push_back((int32_t)b);
         if (it < hist_cap && gamma_rest_hist) gamma_rest_hist[it] = g_rest;
         if (newly.empty()) break;
         marked_total += (int64_t)newly.size();
-        // step 4: A_{k+1} = A^_k on the marked blocks, and their next look-ahead
-        HM_CUDA(cudaMemcpyAsync(d_flags, marked.data(), (size_t)nb, cudaMemcpyHostToDevice, s));
+        // step 4: A_{k+1} = A^_k on the marked blocks (d_flags), and their next look-ahead
         amvm_rowsum_kernel<<<gM, 256, 0, s>>>(d_ipos, d_aptr, d_aidx, d_adm, d_doff, D, d_flags, 1, bk, M);
         HM_CUDA(cudaGetLastError());
         items.clear();
