@@ -14,7 +14,10 @@ adds the pieces for which a library routine is the plain definition:
 * ``dense_matvec`` -- y = A x with ``numpy`` on the dense Kelvin matrix;
 * ``amvm`` -- Algorithm 2 (adaptive matrix-vector multiplication, Section 3)
   step by step on the oracle's own ACA factors, with the readings stated in
-  its docstring (per-block products are ``numpy`` matrix products).
+  its docstring (per-block products are ``numpy`` matrix products);
+* the evaluation operator ~V_h of Section 5, Eq. (vector_eq) (the displacement at points of
+  the domain): ``points_matvec`` by its definition, and ``HMatrix`` with
+  ``points=`` (a tree of the points for the rows, the same ACA).
 
 Parity unpinned: the absolute accuracy of the near-singular rule on badly
 shaped triangles (only its convergence on well-shaped ones is pinned).
@@ -78,6 +81,11 @@ def _L():
                 "or_kelvin_dense": (None, [P, P, I64, D, D, P]),
                 "or_aca_dense": (I32, [P, I64, I64, D, D, I32, P, P, P, P, P, P]),
                 "or_hmat_create": (P, [P, I64, P, I64, I64, D, D, D, I32]),
+                "or_hmat_points_create": (P, [P, I64, P, I64, I64, P, I64, I64, D, D, D, I32]),
+                "or_hmat_rsizes": (None, [P, P]),
+                "or_hmat_rtree": (None, [P, P, P, P]),
+                "or_kelvin_points_matvec": (None, [P, P, I64, D, D, P, I64, P, I64, P]),
+                "or_scalar_points": (None, [P, P, I64, P, I64, P]),
                 "or_hmat_free": (None, [P]),
                 "or_hmat_sizes": (None, [P, P]),
                 "or_hmat_tree": (None, [P, P, P, P]),
@@ -167,6 +175,27 @@ def scalar_rows(V, T, rows) -> np.ndarray:
     out = np.zeros((7, rows.shape[0], M))
     _L().or_scalar_rows(_p(V), _p(T), M, _p(rows), rows.shape[0], _p(out))
     return out
+
+
+def scalar_points(V, T, P) -> np.ndarray:
+    """(7, len(P), M) scalar-kernel matrix at arbitrary points P (no self pair)."""
+    V, T, P = _f64(V), _i32(T), _f64(P).reshape(-1, 3)
+    M = T.shape[0]
+    out = np.zeros((7, P.shape[0], M))
+    _L().or_scalar_points(_p(V), _p(T), M, _p(P), P.shape[0], _p(out))
+    return out
+
+
+def points_matvec(V, T, E: float, nu: float, P, x) -> np.ndarray:
+    """The evaluation operator of Section 5, Eq. (vector_eq) by its definition: u(x_r) =
+    sum_j int_{tau_j} S_K(x_r - y) ds_y t_j at the points P (np x 3), from
+    Kelvin's tensor.  x: (nrhs, 3M) densities; returns (nrhs, 3 np)."""
+    V, T, P = _f64(V), _i32(T), _f64(P).reshape(-1, 3)
+    x = _f64(np.atleast_2d(x))
+    M = T.shape[0]
+    y = np.zeros((x.shape[0], 3 * P.shape[0]))
+    _L().or_kelvin_points_matvec(_p(V), _p(T), M, E, nu, _p(P), P.shape[0], _p(x), x.shape[0], _p(y))
+    return y
 
 
 def kelvin_dense(V, T, E: float, nu: float) -> np.ndarray:
@@ -262,15 +291,27 @@ def svd_truncate(U: np.ndarray, V: np.ndarray, eps: float):
 
 class HMatrix:
     """Cluster tree, partition, ACA factors and near blocks built by the
-    oracle (FP64), and its H-matrix-vector product."""
+    oracle (FP64), and its H-matrix-vector product.
+
+    With ``points`` (np x 3) the rows are those points instead of the
+    collocation points: the evaluation operator ~V_h of Section 5, Eq. (vector_eq), rows
+    clustered by a tree of the points (leaves of ``leaf_points``)."""
 
     def __init__(self, V, T, leaf: int, eta: float, eps: float, eta_stop: float = 0.8,
-                 kmax: int = 256):
+                 kmax: int = 256, points=None, leaf_points: int | None = None):
         self.V, self.T = _f64(V), _i32(T)
         self.M = self.T.shape[0]
         self.leaf, self.eta, self.eps, self.eta_stop, self.kmax = leaf, eta, eps, eta_stop, kmax
-        self._h = _L().or_hmat_create(_p(self.V), self.V.shape[0], _p(self.T), self.M, leaf,
-                                      eta, eps, eta_stop, kmax)
+        if points is None:
+            self.points = None
+            self._h = _L().or_hmat_create(_p(self.V), self.V.shape[0], _p(self.T), self.M, leaf,
+                                          eta, eps, eta_stop, kmax)
+        else:
+            self.points = _f64(points).reshape(-1, 3)
+            lp = leaf if leaf_points is None else leaf_points
+            self._h = _L().or_hmat_points_create(_p(self.V), self.V.shape[0], _p(self.T), self.M, leaf,
+                                                 _p(self.points), self.points.shape[0], lp, eta, eps,
+                                                 eta_stop, kmax)
         s = np.zeros(4, dtype=np.int64)
         _L().or_hmat_sizes(self._h, _p(s))
         self.nnodes, self.nadm, self.nnear = int(s[0]), int(s[1]), int(s[2])
@@ -281,6 +322,14 @@ class HMatrix:
         self.adm = np.zeros((self.nadm, 2), dtype=np.int64)
         self.near = np.zeros((self.nnear, 2), dtype=np.int64)
         _L().or_hmat_blocks(self._h, _p(self.adm), _p(self.near))
+        # the row tree (the point tree of ~V_h, else the triangle tree)
+        r = np.zeros(2, dtype=np.int64)
+        _L().or_hmat_rsizes(self._h, _p(r))
+        self.nrnodes, self.Mr = int(r[0]), int(r[1])
+        self.rperm = np.zeros(self.Mr, dtype=np.int64)
+        self.rnodes = np.zeros((self.nrnodes, 5), dtype=np.int64)
+        self.rboxes = np.zeros((self.nrnodes, 6))
+        _L().or_hmat_rtree(self._h, _p(self.rperm), _p(self.rnodes), _p(self.rboxes))
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -288,10 +337,10 @@ class HMatrix:
             _L().or_hmat_free(h)
             self._h = None
 
-    # block ranges in cluster order
+    # block ranges in cluster order (rows in the row tree)
     def ranges(self, blocks: np.ndarray) -> np.ndarray:
         t, s = blocks[:, 0], blocks[:, 1]
-        return np.stack([self.nodes[t, 0], self.nodes[t, 1], self.nodes[s, 0],
+        return np.stack([self.rnodes[t, 0], self.rnodes[t, 1], self.nodes[s, 0],
                          self.nodes[s, 1]], 1)
 
     @staticmethod
@@ -326,7 +375,7 @@ class HMatrix:
 
     def factors(self, b: int, kern: int):
         t, s = self.adm[b]
-        m = int(self.nodes[t, 1] - self.nodes[t, 0])
+        m = int(self.rnodes[t, 1] - self.rnodes[t, 0])
         n = int(self.nodes[s, 1] - self.nodes[s, 0])
         k = self.rank(b, kern)
         U = np.zeros((max(k, 0), m))
@@ -337,7 +386,7 @@ class HMatrix:
 
     def near_block(self, b: int) -> np.ndarray:
         t, s = self.near[b]
-        m = int(self.nodes[t, 1] - self.nodes[t, 0])
+        m = int(self.rnodes[t, 1] - self.rnodes[t, 0])
         n = int(self.nodes[s, 1] - self.nodes[s, 0])
         out = np.zeros((7, m, n))
         _L().or_hmat_near_block(self._h, b, _p(out))
@@ -345,7 +394,7 @@ class HMatrix:
 
     def matvec(self, E: float, nu: float, x, adm_ids=None, near_ids=None) -> np.ndarray:
         x = _f64(np.atleast_2d(x))
-        y = np.zeros_like(x)
+        y = np.zeros((x.shape[0], 3 * self.Mr))
         pa, na, ka = self._ids(adm_ids)
         pn, nn, kn = self._ids(near_ids)
         _L().or_hmat_matvec(self._h, E, nu, _p(x), _p(y), x.shape[0], pa, na, pn, nn)
@@ -355,11 +404,14 @@ class HMatrix:
         """The exact (quadrature-contract) scalar-kernel block of admissible
         block b, computed entry by entry."""
         t, s = self.adm[b]
-        lo_t, hi_t = self.nodes[t, :2]
+        lo_t, hi_t = self.rnodes[t, :2]
         lo_s, hi_s = self.nodes[s, :2]
-        rows = self.perm[lo_t:hi_t]
+        rows = self.rperm[lo_t:hi_t]
         cols = self.perm[lo_s:hi_s]
-        R = scalar_rows(self.V, self.T, rows)[kern]
+        if self.points is not None:
+            R = scalar_points(self.V, self.T, self.points[rows])[kern]
+        else:
+            R = scalar_rows(self.V, self.T, rows)[kern]
         return R[:, cols]
 
 
@@ -375,7 +427,7 @@ def sparsity_constant(Ho: "HMatrix") -> int:
     """c_sp of the block partition (Section 2.1): the largest number of
     blocks of P that share a row cluster, or a column cluster."""
     blocks = np.concatenate([Ho.adm, Ho.near]) if Ho.nnear else Ho.adm
-    rows = np.bincount(blocks[:, 0], minlength=Ho.nnodes)
+    rows = np.bincount(blocks[:, 0], minlength=Ho.nrnodes)
     cols = np.bincount(blocks[:, 1], minlength=Ho.nnodes)
     return int(max(rows.max(), cols.max()))
 
@@ -383,7 +435,9 @@ def sparsity_constant(Ho: "HMatrix") -> int:
 def amvm(Ho: "HMatrix", E: float, nu: float, x, theta: float = 0.7, eps: float = 1e-6,
          r0: int = 2, look: int = 2, max_iter: int = 1000):
     """Algorithm 2 (adaptive matrix-vector multiplication, Section 3) on the
-    oracle's own H-matrix, FP64, for one vector x (3M dofs, original order).
+    oracle's own H-matrix, FP64, for one vector x (3M dofs, original order);
+    the rows are the 3 Mr dofs of the row points (Mr = M unless Ho is the
+    evaluation operator of Section 5, Eq. (vector_eq)).
 
     Readings (the paper leaves these open):
     * A_k keeps, on every admissible block t x s, the first r_b crosses of
@@ -393,9 +447,10 @@ def amvm(Ho: "HMatrix", E: float, nu: float, x, theta: float = 0.7, eps: float =
       (look = 2, "two steps of ACA ahead").  Near blocks are exact in both.
     * Marking is per block t x s: a marked block moves all seven kernels to
       the look-ahead ranks, A_{k+1} = A^_k on it.
-    * Rows are the 3M dofs (component a of cluster position p is row 3p + a)
-      and M = N = 3M in the threshold (1 - theta)(c_sp M N)^{-1/2} gamma_k;
-      rows of equal error are taken in increasing row order.
+    * Rows are the 3 Mr dofs (component a of row cluster position p is row
+      3p + a); the threshold (1 - theta)(c_sp M N)^{-1/2} gamma_k takes the
+      paper's M x N as 3 Mr x 3M; rows of equal error are taken in increasing
+      row order.
     * Step 4 stops when gamma_k <= eps * ||b^_k|| (a relative epsilon) and
       returns b_k; it also stops when no block can be refined any more.
 
@@ -403,9 +458,9 @@ def amvm(Ho: "HMatrix", E: float, nu: float, x, theta: float = 0.7, eps: float =
     (gamma_k per iteration), gamma_rest (gamma_k(P_k) per iteration), marked
     (|P_k| per iteration), ranks (r_b at the end), csp, iterations."""
     x = _f64(x).reshape(-1)
-    M = Ho.M
+    M, Mr = Ho.M, Ho.Mr
     c1, c2 = lame_coefficients(E, nu)
-    perm = Ho.perm
+    perm, rperm = Ho.perm, Ho.rperm
     Xc = x.reshape(M, 3)[perm]                                  # cluster order
     rng = Ho.ranges(Ho.adm)                                     # lo_t, hi_t, lo_s, hi_s
     nb = Ho.nadm
@@ -433,15 +488,15 @@ def amvm(Ho: "HMatrix", E: float, nu: float, x, theta: float = 0.7, eps: float =
         return out
 
     # b_0: near field exactly, every admissible block at rank r0
-    near = Ho.matvec(E, nu, x, adm_ids=[])[0].reshape(M, 3)[perm]
+    near = Ho.matvec(E, nu, x, adm_ids=[])[0].reshape(Mr, 3)[rperm]
     r = np.full(nb, int(r0), dtype=np.int64)
     bk = near.copy()
     for b in range(nb):
         bk[rng[b, 0]:rng[b, 1]] += part(b, 0, r0)
     csp = sparsity_constant(Ho)
-    N = 3 * M
+    N, Ncol = 3 * Mr, 3 * M
     # blocks whose row cluster holds cluster position p, in block order
-    blocks_of_pos = [[] for _ in range(M)]
+    blocks_of_pos = [[] for _ in range(Mr)]
     for b in range(nb):
         for p in range(rng[b, 0], rng[b, 1]):
             blocks_of_pos[p].append(b)
@@ -449,7 +504,7 @@ def amvm(Ho: "HMatrix", E: float, nu: float, x, theta: float = 0.7, eps: float =
     delta = [part(b, r[b], r[b] + look) for b in range(nb)]
     it = 0
     while True:
-        e = np.zeros((M, 3))
+        e = np.zeros((Mr, 3))
         for b in range(nb):
             e[rng[b, 0]:rng[b, 1]] += delta[b]
         bhat = bk + e
@@ -458,7 +513,7 @@ def amvm(Ho: "HMatrix", E: float, nu: float, x, theta: float = 0.7, eps: float =
         if gamma <= eps * float(np.linalg.norm(bhat)) or it >= max_iter:
             break
         # step 3: Doerfler marking through the rows in decreasing error
-        thr = (1.0 - theta) * gamma / np.sqrt(csp * float(N) * float(N))
+        thr = (1.0 - theta) * gamma / np.sqrt(csp * float(N) * float(Ncol))
         err = np.abs(e).reshape(-1)
         order = np.lexsort((np.arange(N), -err))              # decreasing error, then row
         rest = e.copy()
@@ -487,9 +542,9 @@ def amvm(Ho: "HMatrix", E: float, nu: float, x, theta: float = 0.7, eps: float =
             r[b] += look
             delta[b] = part(b, r[b], r[b] + look)
         it += 1
-    out = np.zeros(3 * M)
-    out.reshape(M, 3)[perm] = bk
-    outh = np.zeros(3 * M)
-    outh.reshape(M, 3)[perm] = bhat
+    out = np.zeros(3 * Mr)
+    out.reshape(Mr, 3)[rperm] = bk
+    outh = np.zeros(3 * Mr)
+    outh.reshape(Mr, 3)[rperm] = bhat
     return dict(b=out, b_hat=outh, ranks=np.minimum(r[:, None], full), full_ranks=full, csp=csp,
                 iterations=it, **hist)

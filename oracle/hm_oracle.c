@@ -17,6 +17,8 @@
  *   admissibility / partition      Section 2.1, Eq. (adm) and the block-cluster recursion
  *   ACA                            Section 2.2, Algorithm 1 and the cross representation after it
  *   H-matrix-vector product        Section 2 (O(k(M+N)) product of a low-rank block) and Section 2.2
+ *   evaluation operator ~V_h       Section 5, Eq. (vector_eq) (u_h at points x_i of the domain: the collocation
+ *                                  entries with x_i for the centroid; a tree of the points)
  *
  * Quadrature contract (the paper names no rule; this is the reading both the
  * oracle and the CUDA path implement):
@@ -341,6 +343,48 @@ void or_kelvin_rows_matvec(const double* V, const int32_t* T, int64_t M, double 
     }
 }
 
+/* The evaluation operator of Section 5, Eq. (vector_eq) applied by its definition: for each
+ * point x_r and component a, y[3 r + a] = sum_j sum_b int_{tau_j} S_ab(x_r - y)
+ * ds_y x[3 j + b], Kelvin's tensor integrated directly (Section 4.1) with the
+ * same quadrature as the collocation entries (x_r is never a centroid of its
+ * own triangle: no self pair).  x is (nrhs, 3M), y (nrhs, 3 np). */
+void or_kelvin_points_matvec(const double* V, const int32_t* T, int64_t M, double E, double nu,
+                             const double* P, int64_t np, const double* x, int64_t nrhs, double* y)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t r = 0; r < np; ++r) {
+        double K[9];
+        for (int64_t q = 0; q < nrhs; ++q)
+            for (int a = 0; a < 3; ++a) y[q * 3 * np + 3 * r + a] = 0.0;
+        for (int64_t j = 0; j < M; ++j) {
+            or_kelvin_entry(P + 3 * r, V, T + 3 * j, 0, OR_ND, E, nu, K);
+            for (int64_t q = 0; q < nrhs; ++q) {
+                const double* xq = x + q * 3 * M;
+                for (int a = 0; a < 3; ++a) {
+                    double s = 0.0;
+                    for (int b = 0; b < 3; ++b) s += K[3 * a + b] * xq[3 * j + b];
+                    y[q * 3 * np + 3 * r + a] += s;
+                }
+            }
+        }
+    }
+}
+
+/* The seven scalar kernels at points P (np of them) against all M triangles:
+ * out[(v * np + r) * M + j]. */
+void or_scalar_points(const double* V, const int32_t* T, int64_t M, const double* P, int64_t np,
+                      double* out)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t r = 0; r < np; ++r) {
+        double e[7];
+        for (int64_t j = 0; j < M; ++j) {
+            or_scalar_entry(P + 3 * r, V, T + 3 * j, 0, OR_ND, e);
+            for (int v = 0; v < 7; ++v) out[(v * np + r) * M + j] = e[v];
+        }
+    }
+}
+
 /* Dense Kelvin matrix, 3M x 3M row-major, dof 3 i + a. */
 void or_kelvin_dense(const double* V, const int32_t* T, int64_t M, double E, double nu,
                      double* A)
@@ -372,7 +416,8 @@ typedef struct {
     int64_t lo, hi;   /* [lo, hi) in cluster order */
     int64_t son[2];   /* -1 for a leaf */
     int32_t level;
-    double bmin[3], bmax[3]; /* box of all triangle vertices of the cluster */
+    double bmin[3], bmax[3]; /* box of all triangle vertices of the cluster (of
+                                the points, in a tree of points) */
 } or_node;
 
 typedef struct {
@@ -413,6 +458,15 @@ static int64_t build_node(tree_ctx* tc, int64_t lo, int64_t hi, int32_t level)
         nd->bmax[k] = -INFINITY;
     }
     for (int64_t p = lo; p < hi; ++p) {
+        if (!tc->T) {
+            /* a tree of points: the box of the points themselves */
+            for (int k = 0; k < 3; ++k) {
+                double v = tc->C[3 * tc->perm[p] + k];
+                if (v < nd->bmin[k]) nd->bmin[k] = v;
+                if (v > nd->bmax[k]) nd->bmax[k] = v;
+            }
+            continue;
+        }
         const int32_t* t = tc->T + 3 * tc->perm[p];
         for (int c = 0; c < 3; ++c)
             for (int k = 0; k < 3; ++k) {
@@ -456,7 +510,9 @@ static int64_t build_node(tree_ctx* tc, int64_t lo, int64_t hi, int32_t level)
 /* Admissible iff min(diam B_t, diam B_s) < eta dist(B_t, B_s) for the vertex
  * boxes (a superset of X_t, X_s, so the test stays sufficient); compared in
  * squares.  Otherwise split both clusters if neither is a leaf, only the
- * non-leaf one if one is a leaf, and emit a near block if both are leaves. */
+ * non-leaf one if one is a leaf, and emit a near block if both are leaves.
+ * Rows and columns may come from different trees (the evaluation operator of
+ * Section 5, Eq. (vector_eq): a tree of points times the triangle tree). */
 
 typedef struct {
     int64_t t, s;
@@ -503,9 +559,10 @@ static double box_dist2(const or_node* a, const or_node* b)
     return s;
 }
 
-static void partition(const or_node* nodes, int64_t t, int64_t s, double eta, block_lists* bl)
+static void partition(const or_node* rnodes, const or_node* nodes, int64_t t, int64_t s, double eta,
+                      block_lists* bl)
 {
-    const or_node* a = &nodes[t];
+    const or_node* a = &rnodes[t];
     const or_node* b = &nodes[s];
     double da = box_diam2(a), db = box_diam2(b);
     double dmin = da < db ? da : db;
@@ -516,11 +573,11 @@ static void partition(const or_node* nodes, int64_t t, int64_t s, double eta, bl
     int tl = a->son[0] < 0, sl = b->son[0] < 0;
     if (!tl && !sl) {
         for (int p = 0; p < 2; ++p)
-            for (int q = 0; q < 2; ++q) partition(nodes, a->son[p], b->son[q], eta, bl);
+            for (int q = 0; q < 2; ++q) partition(rnodes, nodes, a->son[p], b->son[q], eta, bl);
     } else if (!tl) {
-        for (int p = 0; p < 2; ++p) partition(nodes, a->son[p], s, eta, bl);
+        for (int p = 0; p < 2; ++p) partition(rnodes, nodes, a->son[p], s, eta, bl);
     } else if (!sl) {
-        for (int q = 0; q < 2; ++q) partition(nodes, t, b->son[q], eta, bl);
+        for (int q = 0; q < 2; ++q) partition(rnodes, nodes, t, b->son[q], eta, bl);
     } else {
         push_block(&bl->near, &bl->nnear, &bl->capnear, t, s);
     }
@@ -721,6 +778,14 @@ typedef struct {
     int64_t* perm;   /* cluster position -> original triangle */
     or_node* nodes;
     int64_t nnodes;
+    /* rows: the collocation points themselves (square), or the points x_i of
+     * the evaluation operator ~V_h (Section 5, Eq. (vector_eq)) with their own tree */
+    int square;
+    int64_t Mr;
+    double* X;       /* row points, original order (== C when square) */
+    int64_t* rperm;  /* row cluster position -> original row */
+    or_node* rnodes;
+    int64_t nrnodes;
     block_lists bl;
     double eps, eta, eta_stop;
     int32_t kmax;
@@ -746,8 +811,8 @@ typedef struct {
 
 static void kernel_entry(const or_hmat* h, int64_t pi, int64_t pj, double e[7])
 {
-    int64_t i = h->perm[pi], j = h->perm[pj];
-    or_scalar_entry(h->C + 3 * i, h->V, h->T + 3 * j, i == j, OR_ND, e);
+    int64_t i = h->rperm[pi], j = h->perm[pj];
+    or_scalar_entry(h->X + 3 * i, h->V, h->T + 3 * j, h->square && i == j, OR_ND, e);
 }
 
 static void kernel_row(void* c, int64_t i, double* out)
@@ -770,8 +835,8 @@ static void kernel_col(void* c, int64_t j, double* out)
     }
 }
 
-void* or_hmat_create(const double* V, int64_t nv, const int32_t* T, int64_t M, int64_t leaf,
-                     double eta, double eps, double eta_stop, int32_t kmax)
+/* the triangle tree (columns); rows and partition are set by the callers */
+static or_hmat* hmat_columns(const double* V, int64_t nv, const int32_t* T, int64_t M, int64_t leaf)
 {
     or_hmat* h = (or_hmat*)calloc(1, sizeof(or_hmat));
     h->M = M;
@@ -790,7 +855,13 @@ void* or_hmat_create(const double* V, int64_t nv, const int32_t* T, int64_t M, i
     build_node(&tc, 0, M, 0);
     free(tc.tmp);
     h->nnodes = tc.nn;
-    partition(h->nodes, 0, 0, eta, &h->bl);
+    return h;
+}
+
+/* the block storage once the partition is known */
+static void hmat_blocks(or_hmat* h, double eta, double eps, double eta_stop, int32_t kmax)
+{
+    partition(h->rnodes, h->nodes, 0, 0, eta, &h->bl);
     h->eps = eps;
     h->eta = eta;
     h->eta_stop = eta_stop;
@@ -803,6 +874,45 @@ void* or_hmat_create(const double* V, int64_t nv, const int32_t* T, int64_t M, i
     h->Nf = (double**)calloc((size_t)(nn + 1), sizeof(double*));
     h->adm_done = (unsigned char*)calloc((size_t)(na + 1), 1);
     h->near_done = (unsigned char*)calloc((size_t)(nn + 1), 1);
+}
+
+void* or_hmat_create(const double* V, int64_t nv, const int32_t* T, int64_t M, int64_t leaf,
+                     double eta, double eps, double eta_stop, int32_t kmax)
+{
+    or_hmat* h = hmat_columns(V, nv, T, M, leaf);
+    h->square = 1;
+    h->Mr = M;
+    h->X = h->C;
+    h->rperm = h->perm;
+    h->rnodes = h->nodes;
+    h->nrnodes = h->nnodes;
+    hmat_blocks(h, eta, eps, eta_stop, kmax);
+    return h;
+}
+
+/* The evaluation operator ~V_h of Section 5, Eq. (vector_eq) (the displacement at points
+ * x_1 .. x_np of the domain): rows are the points, clustered by the same
+ * rule as the triangles with the boxes of the points, columns the triangles;
+ * the entries are the collocation entries with x_i in place of a centroid
+ * (never a self pair). */
+void* or_hmat_points_create(const double* V, int64_t nv, const int32_t* T, int64_t M, int64_t leaf,
+                            const double* P, int64_t np, int64_t leaf_pts, double eta, double eps,
+                            double eta_stop, int32_t kmax)
+{
+    or_hmat* h = hmat_columns(V, nv, T, M, leaf);
+    h->square = 0;
+    h->Mr = np;
+    h->X = (double*)malloc((size_t)np * 3 * sizeof(double));
+    memcpy(h->X, P, (size_t)np * 3 * sizeof(double));
+    h->rperm = (int64_t*)malloc((size_t)np * sizeof(int64_t));
+    for (int64_t i = 0; i < np; ++i) h->rperm[i] = i;
+    h->rnodes = (or_node*)malloc((size_t)(2 * np + 1) * sizeof(or_node));
+    tree_ctx tc = {NULL, NULL, h->X, leaf_pts, h->rperm, h->rnodes, 0,
+                   (sort_item*)malloc((size_t)np * sizeof(sort_item))};
+    build_node(&tc, 0, np, 0);
+    free(tc.tmp);
+    h->nrnodes = tc.nn;
+    hmat_blocks(h, eta, eps, eta_stop, kmax);
     return h;
 }
 
@@ -824,6 +934,11 @@ void or_hmat_free(void* hp)
     free(h->near_done);
     free(h->bl.adm);
     free(h->bl.near);
+    if (!h->square) {
+        free(h->X);
+        free(h->rperm);
+        free(h->rnodes);
+    }
     free(h->nodes);
     free(h->perm);
     free(h->C);
@@ -841,23 +956,45 @@ void or_hmat_sizes(const void* hp, int64_t* out4)
     out4[3] = h->M;
 }
 
+/* rows: out2 = (row tree nodes, rows) */
+void or_hmat_rsizes(const void* hp, int64_t* out2)
+{
+    const or_hmat* h = (const or_hmat*)hp;
+    out2[0] = h->nrnodes;
+    out2[1] = h->Mr;
+}
+
+static void export_tree(const or_node* nodes, int64_t nnodes, const int64_t* p, int64_t n, int64_t* perm,
+                        int64_t* nodes5, double* boxes6)
+{
+    memcpy(perm, p, (size_t)n * sizeof(int64_t));
+    for (int64_t q = 0; q < nnodes; ++q) {
+        const or_node* nd = &nodes[q];
+        nodes5[5 * q + 0] = nd->lo;
+        nodes5[5 * q + 1] = nd->hi;
+        nodes5[5 * q + 2] = nd->son[0];
+        nodes5[5 * q + 3] = nd->son[1];
+        nodes5[5 * q + 4] = nd->level;
+        for (int k = 0; k < 3; ++k) {
+            boxes6[6 * q + k] = nd->bmin[k];
+            boxes6[6 * q + 3 + k] = nd->bmax[k];
+        }
+    }
+}
+
+/* the row tree (the point tree of an evaluation operator; the triangle tree
+ * of a square one), as or_hmat_tree */
+void or_hmat_rtree(const void* hp, int64_t* perm, int64_t* nodes5, double* boxes6)
+{
+    const or_hmat* h = (const or_hmat*)hp;
+    export_tree(h->rnodes, h->nrnodes, h->rperm, h->Mr, perm, nodes5, boxes6);
+}
+
 /* perm[M]; nodes as int64 rows [lo, hi, son0, son1, level]; boxes as 6 doubles */
 void or_hmat_tree(const void* hp, int64_t* perm, int64_t* nodes5, double* boxes6)
 {
     const or_hmat* h = (const or_hmat*)hp;
-    memcpy(perm, h->perm, (size_t)h->M * sizeof(int64_t));
-    for (int64_t n = 0; n < h->nnodes; ++n) {
-        const or_node* nd = &h->nodes[n];
-        nodes5[5 * n + 0] = nd->lo;
-        nodes5[5 * n + 1] = nd->hi;
-        nodes5[5 * n + 2] = nd->son[0];
-        nodes5[5 * n + 3] = nd->son[1];
-        nodes5[5 * n + 4] = nd->level;
-        for (int k = 0; k < 3; ++k) {
-            boxes6[6 * n + k] = nd->bmin[k];
-            boxes6[6 * n + 3 + k] = nd->bmax[k];
-        }
-    }
+    export_tree(h->nodes, h->nnodes, h->perm, h->M, perm, nodes5, boxes6);
 }
 
 /* block lists as node ids: adm[2*b], adm[2*b+1] = (t, s) */
@@ -895,7 +1032,7 @@ static int kernel_vanishes(const or_node* t, const or_node* s, int kern)
 
 static void assemble_adm(or_hmat* h, int64_t b)
 {
-    const or_node* t = &h->nodes[h->bl.adm[b].t];
+    const or_node* t = &h->rnodes[h->bl.adm[b].t];
     const or_node* s = &h->nodes[h->bl.adm[b].s];
     int64_t m = t->hi - t->lo, n = s->hi - s->lo;
     for (int kern = 0; kern < 7; ++kern) {
@@ -923,7 +1060,7 @@ static void assemble_adm(or_hmat* h, int64_t b)
 
 static void assemble_near(or_hmat* h, int64_t b)
 {
-    const or_node* t = &h->nodes[h->bl.near[b].t];
+    const or_node* t = &h->rnodes[h->bl.near[b].t];
     const or_node* s = &h->nodes[h->bl.near[b].s];
     int64_t m = t->hi - t->lo, n = s->hi - s->lo;
     double* N = (double*)malloc((size_t)(7 * m * n) * sizeof(double));
@@ -971,7 +1108,7 @@ int32_t or_hmat_aca_flags(const void* hp, int64_t b, int kern)
 void or_hmat_factors(const void* hp, int64_t b, int kern, double* U, double* Vv)
 {
     const or_hmat* h = (const or_hmat*)hp;
-    const or_node* t = &h->nodes[h->bl.adm[b].t];
+    const or_node* t = &h->rnodes[h->bl.adm[b].t];
     const or_node* s = &h->nodes[h->bl.adm[b].s];
     int64_t m = t->hi - t->lo, n = s->hi - s->lo;
     int32_t k = h->rank[b * 7 + kern];
@@ -982,7 +1119,7 @@ void or_hmat_factors(const void* hp, int64_t b, int kern, double* U, double* Vv)
 void or_hmat_near_block(const void* hp, int64_t b, double* out)
 {
     const or_hmat* h = (const or_hmat*)hp;
-    const or_node* t = &h->nodes[h->bl.near[b].t];
+    const or_node* t = &h->rnodes[h->bl.near[b].t];
     const or_node* s = &h->nodes[h->bl.near[b].s];
     int64_t m = t->hi - t->lo, n = s->hi - s->lo;
     memcpy(out, h->Nf[b], (size_t)(7 * m * n) * sizeof(double));
@@ -991,7 +1128,8 @@ void or_hmat_near_block(const void* hp, int64_t b, double* out)
 /* y = V_h x over the assembled blocks (only the listed ones if lists are
  * given), Eq. (Vh): y_a(i) += c1 sum_j V_Delta[i,j] x_a(j) + c2 sum_{j,b} V_ab[i,j] x_b(j),
  * with c1 = (1+nu)(3-4nu)/(2E(1-nu)) and c2 = (1+nu)/(2E(1-nu)).  Low-rank
- * blocks apply U (V^T x).  x, y are (nrhs, 3M) in original order, dof 3 i + a.
+ * blocks apply U (V^T x).  x is (nrhs, 3M), y (nrhs, 3 Mr) in original order,
+ * dof 3 i + a (Mr = M unless rows are the points of ~V_h).
  * Per block row, blocks are summed in list order.  A negative count means all
  * blocks of that kind; blocks that were not assembled must not be listed. */
 static const int kab[3][3] = {{1, 2, 3}, {2, 4, 5}, {3, 5, 6}};
@@ -1001,16 +1139,16 @@ void or_hmat_matvec(const void* hp, double E, double nu, const double* x, double
                     const int64_t* near_ids, int64_t nnear_ids)
 {
     const or_hmat* h = (const or_hmat*)hp;
-    int64_t M = h->M;
+    int64_t M = h->M, Mr = h->Mr;
     double c1 = (1.0 + nu) * (3.0 - 4.0 * nu) / (2.0 * E * (1.0 - nu));
     double c2 = (1.0 + nu) / (2.0 * E * (1.0 - nu));
     int64_t na = nadm_ids < 0 ? h->bl.nadm : nadm_ids;
     int64_t nn = nnear_ids < 0 ? h->bl.nnear : nnear_ids;
     if (nadm_ids < 0) adm_ids = NULL;
     if (nnear_ids < 0) near_ids = NULL;
-    for (int64_t q = 0; q < nrhs * 3 * M; ++q) y[q] = 0.0;
+    for (int64_t q = 0; q < nrhs * 3 * Mr; ++q) y[q] = 0.0;
     /* process blocks grouped by row-cluster node id so that threads own rows */
-    int64_t nnod = h->nnodes;
+    int64_t nnod = h->nrnodes;
     int64_t* cnt = (int64_t*)calloc((size_t)(nnod + 1), sizeof(int64_t));
     for (int64_t q = 0; q < na; ++q) cnt[h->bl.adm[adm_ids ? adm_ids[q] : q].t + 1]++;
     int64_t* ncnt = (int64_t*)calloc((size_t)(nnod + 1), sizeof(int64_t));
@@ -1037,17 +1175,17 @@ void or_hmat_matvec(const void* hp, double E, double nu, const double* x, double
      * other and the clusters of one level in parallel. */
     int32_t maxlev = 0;
     for (int64_t n = 0; n < nnod; ++n)
-        if (h->nodes[n].level > maxlev) maxlev = h->nodes[n].level;
+        if (h->rnodes[n].level > maxlev) maxlev = h->rnodes[n].level;
     for (int32_t lev = 0; lev <= maxlev; ++lev) {
 #pragma omp parallel for schedule(dynamic, 1)
         for (int64_t tn = 0; tn < nnod; ++tn) {
-            const or_node* t = &h->nodes[tn];
+            const or_node* t = &h->rnodes[tn];
             if (t->level != lev) continue;
             int64_t m = t->hi - t->lo;
             double* z = (double*)malloc((size_t)(3 * (h->kmax + 1)) * sizeof(double));
             for (int64_t r = 0; r < nrhs; ++r) {
                 const double* xr = x + r * 3 * M;
-                double* yr = y + r * 3 * M;
+                double* yr = y + r * 3 * Mr;
                 for (int64_t q = cnt[tn]; q < cnt[tn + 1]; ++q) {
                     int64_t b = ord[q];
                     const or_node* s = &h->nodes[h->bl.adm[b].s];
@@ -1065,7 +1203,7 @@ void or_hmat_matvec(const void* hp, double E, double nu, const double* x, double
                                 z[3 * l + c] = sacc;
                             }
                         for (int64_t i = 0; i < m; ++i) {
-                            double* yi = yr + 3 * h->perm[t->lo + i];
+                            double* yi = yr + 3 * h->rperm[t->lo + i];
                             for (int a = 0; a < 3; ++a) {
                                 double sacc = 0.0;
                                 if (kern == 0) {
@@ -1090,7 +1228,7 @@ void or_hmat_matvec(const void* hp, double E, double nu, const double* x, double
                     int64_t n = s->hi - s->lo;
                     const double* N = h->Nf[b];
                     for (int64_t i = 0; i < m; ++i) {
-                        double* yi = yr + 3 * h->perm[t->lo + i];
+                        double* yi = yr + 3 * h->rperm[t->lo + i];
                         for (int64_t j = 0; j < n; ++j) {
                             const double* xj = xr + 3 * h->perm[s->lo + j];
                             double vd = N[(0 * m + i) * n + j];

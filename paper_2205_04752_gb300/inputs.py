@@ -18,6 +18,10 @@ Section 6.1 and the beam of Section 6.2 are not published):
   cut along the same diagonal: 12*n*n triangles.
 * ``ellipsoid(n, a, b, c)`` -- cube-sphere (the cube surface projected to the
   unit sphere) scaled by the semi-axes (a, b, c).
+* ``ball_points`` / ``shell_points`` -- evaluation points inside a ball or in
+  a spherical shell (the points x_i of the domain at which Section 5, Eq. (vector_eq)
+  evaluates the displacement), by rejection from a cube: only comparisons and
+  products, no library function whose last bit could differ between hosts.
 """
 from __future__ import annotations
 
@@ -30,6 +34,8 @@ __all__ = [
     "uniform_rhs",
     "ellipsoid_batch_specs",
     "sample_rows",
+    "ball_points",
+    "shell_points",
 ]
 
 
@@ -148,3 +154,22 @@ def sample_rows(M: int, count: int, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     count = min(count, M)
     return np.sort(rng.choice(M, size=count, replace=False)).astype(np.int64)
+
+
+def shell_points(count: int, r_in: float, r_out: float, seed: int) -> np.ndarray:
+    """``count`` points uniform in the shell r_in <= |x| <= r_out (r_in = 0:
+    the ball), in the order drawn: uniform in [-r_out, r_out]^3, kept when
+    their squared norm lies in [r_in^2, r_out^2].  Shape (count, 3)."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((0, 3), dtype=np.float64)
+    lo2, hi2 = r_in * r_in, r_out * r_out
+    while out.shape[0] < count:
+        p = rng.uniform(-r_out, r_out, (max(2 * count, 64), 3))
+        q = p[:, 0] * p[:, 0] + p[:, 1] * p[:, 1] + p[:, 2] * p[:, 2]
+        out = np.concatenate([out, p[(q >= lo2) & (q <= hi2)]])
+    return np.ascontiguousarray(out[:count])
+
+
+def ball_points(count: int, radius: float, seed: int) -> np.ndarray:
+    """``count`` points uniform in the ball |x| <= radius.  Shape (count, 3)."""
+    return shell_points(count, 0.0, radius, seed)
