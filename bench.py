@@ -15,8 +15,11 @@ right-hand sides, end-to-end products with host buffers, "batch64" (batched
 products over 64 ellipsoid meshes with 1 and 16 right-hand sides), "solve"
 (GMRES with FP64-residual refinement to 1e-8 on a 196,608-triangle cube),
 "serving" (the request loop over 16 resident meshes at swept Poisson rates,
-p50 / p99 latency) and "amvm" (Algorithm 2 on the level-6 matrix, FP64, theta
-0.7, eps 1e-4); --no-batch / --no-solve / --no-serve / --no-amvm skip them.
+p50 / p99 latency), "amvm" (Algorithm 2 on the level-6 matrix, FP64, theta
+0.7, eps 1e-4) and "points" (the evaluation operator of Section 5, Eq.
+(vector_eq): the displacement at 65,536 points inside the level-6 sphere,
+its exact FP64 product and Algorithm 2 on it); --no-batch / --no-solve /
+--no-serve / --no-amvm / --no-points skip them.
 
 Under torchrun (N > 1) every rank runs its own replica (the product shards
 into independent problems; no collective on the data path): weak scaling,
@@ -379,6 +382,13 @@ def run_ours(args):
             "rel_err_vs_fp64_product": float(torch.linalg.norm(ya - y64) / torch.linalg.norm(y64))}
         del Hd
 
+    points_ctx = None
+    if not args.no_points and rank == 0 and ws == 1:
+        try:
+            points_ctx = bench_points(args, tree, w, x, timed)
+        except Exception as e:  # reported, the headline still prints
+            points_ctx = {"error": f"{type(e).__name__}: {e}"}
+
     line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -392,6 +402,7 @@ def run_ours(args):
             "fp64_form": {"ms_per_matvec": round(ms64, 4), "value": round(1e3 / ms64, 3)},
             "nrhs32": {"ms_per_call": round(ms32, 4), "vectors_per_s": round(32e3 / ms32, 2)},
             "amvm": amvm_ctx,
+            "points": points_ctx,
             "assembly": {"tree_s": round(t_tree, 3), "assemble_s": round(t_asm, 3),
                          "near_ms": round(st.assemble_ms[0], 1),
                          "aca_ms": round(st.assemble_ms[1], 1),
@@ -419,6 +430,77 @@ def run_ours(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def bench_points(args, tree, w, x, timed):
+    """The evaluation operator ~V_h (Section 5, Eq. (vector_eq)) for 65,536
+    points uniform in the ball of radius 0.95 inside the level-6 sphere (leaf
+    64): assembly, the exact FP64 product u = ~V_h t (device time, the bytes
+    it must read: every factor and near value once, the parts and vectors),
+    and Algorithm 2 on it (theta 0.7, eps 1e-4) with the assembled ACA and
+    with ACA on demand."""
+    import torch
+    from paper_2205_04752_gb300 import binding, inputs
+    npts = 65536
+    P = inputs.ball_points(npts, 0.95, 7)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pt = binding.build_point_tree(tree, P, 64)
+    t_tree = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Hp = binding.aca_assemble(pt, w["E"], w["nu"], w["aca_eps"], max_rhs=1)
+    torch.cuda.synchronize()
+    t_asm = time.perf_counter() - t0
+    st = Hp.stats()
+    _, nodes, adm, _ = pt.export()
+    rows_far = int(np.sum(nodes[adm[:, 0], 1] - nodes[adm[:, 0], 0])) if len(adm) else 0
+    M = pt.M_src
+    t = x if x.dim() == 1 else x[0]
+    u = torch.empty(3 * npts, dtype=torch.float64, device="cuda")
+    steps = max(5, min(50, args.steps // 8))
+    ms = timed(lambda: binding.eval_points(Hp, t, u), steps, 2) / steps
+    # algorithmic bytes: every factor and near value once, the block parts
+    # written and read once, the densities gathered and the result scattered
+    alg = (st.far_entries + 6 * st.near_pairs) * 8 + 2 * 3 * rows_far * 8 + 2 * 3 * M * 8 + 2 * 3 * npts * 8
+    peak, peak_kind = _peaks()
+    gbs = alg / (ms * 1e-3) / 1e9
+    ya = torch.empty_like(u)
+    binding.amvm(Hp, t, ya, theta=0.7, eps=1e-4)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ai = binding.amvm(Hp, t, ya, theta=0.7, eps=1e-4)
+    torch.cuda.synchronize()
+    amvm_ms = (time.perf_counter() - t0) * 1e3
+    err = float(torch.linalg.norm(ya - u) / torch.linalg.norm(u))
+    del Hp
+    torch.cuda.empty_cache()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Hd = binding.aca_assemble(pt, w["E"], w["nu"], w["aca_eps"], max_rhs=1, defer_aca=True)
+    torch.cuda.synchronize()
+    t_def = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ad = binding.amvm(Hd, t, ya, theta=0.7, eps=1e-4, on_demand=True)
+    torch.cuda.synchronize()
+    t_od = time.perf_counter() - t0
+    err_od = float(torch.linalg.norm(ya - u) / torch.linalg.norm(u))
+    del Hd
+    torch.cuda.empty_cache()
+    return {"points": npts, "region": "ball r <= 0.95 (seed 7)", "leaf": 64, "nadm": st.nadm,
+            "nnear": st.nnear, "tree_s": round(t_tree, 3), "assemble_s": round(t_asm, 3),
+            "rank_mean": [round(r / max(st.nadm, 1), 2) for r in st.rank_sum],
+            "eval": {"ms": round(ms, 3), "evals_per_s": round(1e3 / ms, 2), "alg_bytes": int(alg),
+                     "achieved_GBps": round(gbs, 1), "peak": peak, "peak_kind": peak_kind,
+                     "frac": round(gbs / peak, 4), "steps": steps},
+            "amvm": {"theta": 0.7, "eps": 1e-4, "ms": round(amvm_ms, 1), "iterations": ai["iterations"],
+                     "crosses_used_fraction": round(ai["crosses_used"] / max(ai["crosses_full"], 1), 4),
+                     "rel_err_vs_exact_product": err,
+                     "gamma_over_bhat": ai["gamma"][-1] / max(ai["bhat_norm"], 1e-300)},
+            "amvm_aca_on_demand": {"assemble_without_aca_s": round(t_def, 3), "amvm_s": round(t_od, 3),
+                                   "total_s": round(t_def + t_od, 3), "full_assembly_s": round(t_asm, 3),
+                                   "crosses_computed_fraction":
+                                       round(ad["crosses_full"] / max(ai["crosses_full"], 1), 4),
+                                   "rel_err_vs_exact_product": err_od}}
 
 
 def bench_batch(args):
@@ -594,6 +676,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the request-loop measurement")
     ap.add_argument("--no-solve", action="store_true", help="skip the 196,608-triangle cube solve")
     ap.add_argument("--no-amvm", action="store_true", help="skip the adaptive matrix-vector multiplication")
+    ap.add_argument("--no-points", action="store_true",
+                    help="skip the evaluation operator (displacement at 65,536 interior points)")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[10.0, 30.0, 100.0])
     ap.add_argument("--serve-seconds", type=float, default=4.0)
     ap.add_argument("--minimal", action="store_true",

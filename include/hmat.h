@@ -98,6 +98,48 @@ int hm_tree_export(const hm_tree* tree, int64_t* perm, int64_t* nodes, int64_t* 
 
 void hm_tree_destroy(hm_tree* tree);
 
+/* ---------------------------------------------------------------------------
+ * hm_build_point_tree -- the rows of the evaluation operator ~V_h of
+ * Section 5, Eq. (vector_eq): the displacement
+ *     u_h(x_i) = sum_j int_{tau_j} S(x_i - y) ds_y t_j
+ * at points x_1 .. x_l of the domain; ~V_h[i, j] is the collocation entry of
+ * hm_aca_assemble with x_i in place of the centroid c_i (never a self pair).
+ * Builds the cluster tree of the points (the split rule of
+ * hm_build_cluster_tree; boxes of the points) and the block partition of
+ * (point tree) x (triangle tree of `surface`) under Eq. (adm) with the
+ * surface tree's eta.  Host only.
+ *   surface  a triangle tree (copied; may be destroyed afterwards)
+ *   pts      host, npts x 3 float64 points off the surface (a point on a
+ *            triangle gives non-finite or inaccurate entries: the 7-point rule
+ *            and its subdivision assume x outside tau_j)
+ *   leaf     b_min of the point tree, 1..HM_MAX_LEAF
+ *   out      new tree: hm_tree_sizes / hm_tree_export describe the point tree
+ *            (perm over the points, nodes) and the partition (row node of the
+ *            point tree, column node of the surface tree)
+ * hm_aca_assemble on this tree assembles ~V_h (FP64 factors and near field,
+ * no packed forms); apply it with hm_eval_points, or adaptively with hm_amvm.
+ * Errors: HM_EINVAL (NULL argument, `surface` itself a point tree, npts < 1,
+ * leaf outside 1..HM_MAX_LEAF, non-finite coordinate), HM_ENOMEM.
+ * ------------------------------------------------------------------------- */
+int hm_build_point_tree(const hm_tree* surface, const double* pts, int64_t npts, int32_t leaf,
+                        hm_tree** out);
+
+/* ---------------------------------------------------------------------------
+ * hm_eval_points -- u = ~V_h t (Section 5, Eq. (vector_eq) with W_h u = 0):
+ * the displacement at the points of an evaluation operator for densities t.
+ *   t      device, nrhs rows of 3M float64 (dof 3j + b, original triangle order)
+ *   u      device, nrhs rows of 3 npts float64 (3i + a, original point
+ *          order), overwritten; t and u must not overlap
+ * The exact FP64 product of the assembled H-matrix: every admissible block
+ * applies all its crosses, every near block its entries, and each output
+ * element is summed in a fixed order (repeated calls agree bitwise).
+ * Asynchronous on `stream`; allocates nothing (its workspace was reserved at
+ * assembly); calls on the same operator must not overlap on the device.
+ * Errors: HM_EINVAL (NULL argument, not an evaluation operator, assembled
+ * with HM_DEFER_ACA, nrhs < 1), HM_EDEVICE.
+ * ------------------------------------------------------------------------- */
+int hm_eval_points(const hm_matrix* H, const double* t, double* u, int32_t nrhs, void* stream);
+
 /* Assembly parameters. */
 typedef struct {
     double E;            /* Young modulus > 0 (Section 1) */
@@ -136,7 +178,10 @@ typedef struct {
  *   stream stream for all device work; the call synchronises it before return
  *   out    receives the matrix
  * The FP64 product form is built too unless prm->flags has HM_DEFER_FP64.
- * Returns HM_ERANK (matrix still valid) if a block hit the rank cap.
+ * A tree from hm_build_point_tree gives the evaluation operator ~V_h instead
+ * (rows are its points; HM_DEFER_FP64 has no effect there).
+ * Returns HM_ERANK (matrix still valid) if a block hit the rank cap below
+ * min(|t|, |s|).
  * ------------------------------------------------------------------------- */
 int hm_aca_assemble(const hm_tree* tree, const hm_params* prm, const hm_allocator* alloc,
                     void* stream, hm_matrix** out);
@@ -365,12 +410,16 @@ int hm_solve(const hm_matrix* H, const double* g, double* t, const hm_solve_para
  * are exact in both.  gamma_k = ||A_k x - A^_k x||_2 is the error estimator.
  * Step 3 marks blocks through the dof rows in decreasing |(A_k x - A^_k x)_i|
  * (ties: increasing row), adding every block t x s with i in t whose part
- * satisfies |[(A_k - A^_k)_ts x_s]_i| >= (1 - theta)(c_sp N N)^{-1/2}
- * gamma_k (N = 3M dofs, c_sp the sparsity constant of Section 2.1), until
- * gamma_k - gamma_k(P_k) >= theta gamma_k (the stopping row found by
- * bisection over the sorted rows); marked blocks take the look-ahead ranks.  The loop ends when gamma_k <= eps ||A^_k x||_2, when
- * no block can be refined, or after max_iter refinements.
- *   x, y      device, 3M doubles each, original dof order; y = A_k x at exit
+ * satisfies |[(A_k - A^_k)_ts x_s]_i| >= (1 - theta)(c_sp N_r N_c)^{-1/2}
+ * gamma_k (N_r = N_c = 3M dofs; for an evaluation operator N_r = 3 npts rows;
+ * c_sp the sparsity constant of Section 2.1), until gamma_k - gamma_k(P_k) >=
+ * theta gamma_k (the stopping row found by bisection over the sorted rows);
+ * marked blocks take the look-ahead ranks.  The loop ends when gamma_k <= eps
+ * ||A^_k x||_2, when no block can be refined, or after max_iter refinements.
+ * On an evaluation operator (hm_build_point_tree) this is the adaptive
+ * evaluation of the displacement at the points that Section 5 proposes.
+ *   x, y      device, original dof order: x 3M doubles, y 3M (3 npts for an
+ *             evaluation operator) doubles; y = A_k x at exit
  *   info      optional: iterations, c_sp, last gamma, ||A^_k x||, crosses
  *             used by A_k and by the assembled ACA, blocks marked in all
  *   gamma_hist, gamma_rest_hist   optional host arrays of hist_cap entries:

@@ -8,7 +8,8 @@ The binding is imported lazily so that ``paper_2205_04752_gb300.inputs``
 """
 
 __all__ = ["build_cluster_tree", "aca_assemble", "hmatvec", "hmatvec_host", "solve", "HMatrix",
-           "ClusterTree", "FP64", "FP32", "BF16", "FP16"]
+           "ClusterTree", "PointTree", "build_point_tree", "eval_points", "amvm", "FP64", "FP32", "BF16",
+           "FP16"]
 
 
 def __getattr__(name):

@@ -32,7 +32,7 @@ SYMBOLS = (
     "hm_solve", "hm_batch_create", "hm_batch_layout", "hm_batch_matvec", "hm_batch_autotune",
     "hm_batch_set_schedule", "hm_batch_get_schedule", "hm_batch_check", "hm_batch_destroy",
     "hm_compact", "hm_footprint", "hm_server_create", "hm_server_footprint", "hm_server_run",
-    "hm_server_destroy", "hm_amvm",
+    "hm_server_destroy", "hm_amvm", "hm_build_point_tree", "hm_eval_points",
 )
 
 
@@ -134,6 +134,8 @@ def load():
         "hm_tree_sizes": (ctypes.c_int, [P, P]),
         "hm_tree_export": (ctypes.c_int, [P, P, P, P, P]),
         "hm_tree_destroy": (None, [P]),
+        "hm_build_point_tree": (ctypes.c_int, [P, P, I64, I32, ctypes.POINTER(P)]),
+        "hm_eval_points": (ctypes.c_int, [P, P, P, I32, P]),
         "hm_aca_assemble": (ctypes.c_int, [P, ctypes.POINTER(_Params), ctypes.POINTER(_Allocator),
                                            P, ctypes.POINTER(P)]),
         "hm_set_material": (ctypes.c_int, [P, D, D]),
@@ -232,6 +234,30 @@ def build_cluster_tree(verts, tris, leaf: int, eta: float) -> ClusterTree:
     return ClusterTree(verts, tris, leaf, eta)
 
 
+class PointTree(ClusterTree):
+    """Rows of the evaluation operator ~V_h (Section 5, Eq. (vector_eq)):
+    the cluster tree of points of the domain and the partition (point tree) x
+    (triangle tree of ``surface``), ``hm_build_point_tree``.  ``M`` counts
+    the points, ``M_src`` the triangles."""
+
+    def __init__(self, surface: ClusterTree, points, leaf: int):
+        lib = load()
+        self.points = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+        h = ctypes.c_void_p()
+        _check(lib.hm_build_point_tree(surface._h, _ptr(self.points), self.points.shape[0], int(leaf),
+                                       ctypes.byref(h)))
+        self._h = h
+        c = np.zeros(6, dtype=np.int64)
+        _check(lib.hm_tree_sizes(self._h, _ptr(c)))
+        self.M, self.nnodes, self.nadm, self.nnear, self.nleaves, self.depth = map(int, c)
+        self.leaf, self.eta = int(leaf), surface.eta
+        self.M_src = surface.M
+
+
+def build_point_tree(surface: ClusterTree, points, leaf: int) -> PointTree:
+    return PointTree(surface, points, leaf)
+
+
 def _torch_allocator(device: int):
     import torch
 
@@ -277,7 +303,10 @@ class HMatrix:
                  torch_memory: bool = True, defer_fp64: bool = False, defer_aca: bool = False):
         import torch
         lib = load()
-        self.M = tree.M
+        # columns are triangles; rows are the points of an evaluation operator
+        self.rect = isinstance(tree, PointTree)
+        self.M = tree.M_src if self.rect else tree.M
+        self.Mr = tree.M
         self.device = torch.cuda.current_device()
         prm = _Params(float(E), float(nu), float(aca_eps), float(aca_eta_stop), int(kmax),
                       int(max_rhs), (1 if defer_fp64 else 0) | (2 if defer_aca else 0), 0)
@@ -425,8 +454,8 @@ def amvm(H: HMatrix, x, y, theta: float = 0.7, eps: float = 1e-6, r0: int = 2, l
     import torch
     if not (x.is_cuda and y.is_cuda and x.dtype == torch.float64 and y.dtype == torch.float64):
         raise TypeError("amvm: x and y must be CUDA float64 tensors")
-    if x.numel() != 3 * H.M or y.numel() != 3 * H.M or not x.is_contiguous() or not y.is_contiguous():
-        raise ValueError("amvm: x and y must be contiguous vectors of 3M")
+    if x.numel() != 3 * H.M or y.numel() != 3 * H.Mr or not x.is_contiguous() or not y.is_contiguous():
+        raise ValueError("amvm: x must be a contiguous vector of 3M and y of 3 rows (3M, or 3 points)")
     p = _AmvmParams(float(theta), float(eps), int(r0), int(look), int(max_iter), 1 if on_demand else 0)
     info = _AmvmInfo()
     cap = 4096
@@ -441,6 +470,23 @@ def amvm(H: HMatrix, x, y, theta: float = 0.7, eps: float = 1e-6, r0: int = 2, l
                 gamma_rest=list(gr[:min(k, cap)]), bhat_norm=info.bhat_norm,
                 crosses_used=int(info.crosses_used), crosses_full=int(info.crosses_full),
                 marked_total=int(info.marked_total), block_ranks=ranks[:H.stats().nadm].copy())
+
+
+def eval_points(H: HMatrix, t, u, stream=None):
+    """``hm_eval_points``: u = ~V_h t, the displacement at the points of an
+    evaluation operator (an ``HMatrix`` assembled from a ``PointTree``) for
+    densities t.  t: CUDA float64 (3M,) or (nrhs, 3M); u: (3 npts,) or
+    (nrhs, 3 npts); both contiguous."""
+    import torch
+    if not (t.is_cuda and u.is_cuda and t.dtype == torch.float64 and u.dtype == torch.float64):
+        raise TypeError("eval_points: t and u must be CUDA float64 tensors")
+    nrhs = 1 if t.dim() == 1 else t.shape[0]
+    if (t.shape[-1] != 3 * H.M or u.shape[-1] != 3 * H.Mr or (u.dim() == 2) != (t.dim() == 2)
+            or (t.dim() == 2 and u.shape[0] != nrhs) or not t.is_contiguous() or not u.is_contiguous()):
+        raise ValueError("eval_points: t must be contiguous rows of 3M, u rows of 3 npts")
+    _check(load().hm_eval_points(H._h, ctypes.c_void_p(t.data_ptr()), ctypes.c_void_p(u.data_ptr()), nrhs,
+                                 _stream_handle(stream)))
+    return u
 
 
 def hmatvec_noalloc(H: HMatrix, x, y, form="fp64", stream=None):

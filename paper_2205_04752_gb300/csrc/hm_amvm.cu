@@ -103,7 +103,9 @@ __global__ void amvm_near_kernel(const int32_t* __restrict__ ipos, const int32_t
 // the crosses l0 .. l1 - 1 of admissible block b applied to x(s): |t| x 3
 // values at D + doff[b] (component fastest).  Kernel k = 0 (V_Delta) acts on
 // each component with c1; V_pq (k = 1..6) adds c2 U (V^T x_q) to y_p and, p !=
-// q, c2 U (V^T x_p) to y_q.
+// q, c2 U (V^T x_p) to y_q.  The crosses go kAmvmMaxCross at a time: the
+// first chunk writes the block's values, later ones add theirs (a fixed
+// order, so the result is deterministic).
 __global__ void __launch_bounds__(kAmvmThreads) amvm_part_kernel(
     const AmvmItem* __restrict__ items, const Blk* __restrict__ adm, const int32_t* __restrict__ rank,
     const double* const* __restrict__ uptr, const double* const* __restrict__ vptr, const double* __restrict__ xc,
@@ -114,13 +116,22 @@ __global__ void __launch_bounds__(kAmvmThreads) amvm_part_kernel(
     const AmvmItem it = items[blockIdx.x];
     const Blk bk = adm[it.b];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = kAmvmThreads / 32;
-    if (tid < 7) kk[tid] = max(0, min(it.l1, rank[it.b * 7 + tid]) - it.l0);
+    int rmax = 0;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) rmax = max(rmax, rank[it.b * 7 + k]);
+    // at least one chunk, so that a block without crosses in range writes zeros
+    const int lend = max(it.l0 + 1, min(it.l1, rmax));
+    double* out = D + doff[it.b];
+    for (int l0 = it.l0; l0 < lend; l0 += kAmvmMaxCross) {
+    const int l1 = min(it.l1, l0 + kAmvmMaxCross);
+    __syncthreads();  // the previous chunk's W has been read
+    if (tid < 7) kk[tid] = max(0, min(l1, rank[it.b * 7 + tid]) - l0);
     __syncthreads();
     // V^T x(s) of every (kernel, cross): one warp each, fixed reduction order
     for (int pr = warp; pr < 7 * kAmvmMaxCross; pr += nw) {
         const int k = pr / kAmvmMaxCross, l = pr - k * kAmvmMaxCross;
         if (l >= kk[k]) continue;
-        const double* v = vptr[it.b * 7 + k] + (int64_t)(it.l0 + l) * bk.n;
+        const double* v = vptr[it.b * 7 + k] + (int64_t)(l0 + l) * bk.n;
         double a0 = 0.0, a1 = 0.0, a2 = 0.0;
         for (int j = lane; j < bk.n; j += 32) {
             const double* xj = xc + 3 * (int64_t)(bk.s0 + j);
@@ -141,11 +152,10 @@ __global__ void __launch_bounds__(kAmvmThreads) amvm_part_kernel(
         }
     }
     __syncthreads();
-    double* out = D + doff[it.b];
     for (int i = tid; i < bk.m; i += kAmvmThreads) {
         double y[3] = {0.0, 0.0, 0.0};
         for (int k = 0; k < 7; ++k) {
-            const double* u = uptr[it.b * 7 + k] + (int64_t)it.l0 * bk.m + i;
+            const double* u = uptr[it.b * 7 + k] + (int64_t)l0 * bk.m + i;
             double s[3] = {0.0, 0.0, 0.0};
             for (int l = 0; l < kk[k]; ++l) {
                 const double ul = u[(int64_t)l * bk.m];
@@ -164,9 +174,16 @@ __global__ void __launch_bounds__(kAmvmThreads) amvm_part_kernel(
                 if (p != q) y[q] += c2 * s[p];
             }
         }
-        out[3 * i] = y[0];
-        out[3 * i + 1] = y[1];
-        out[3 * i + 2] = y[2];
+        if (l0 == it.l0) {
+            out[3 * i] = y[0];
+            out[3 * i + 1] = y[1];
+            out[3 * i + 2] = y[2];
+        } else {
+            out[3 * i] += y[0];
+            out[3 * i + 1] += y[1];
+            out[3 * i + 2] += y[2];
+        }
+    }
     }
 }
 
@@ -418,13 +435,15 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
             h.alloc.stream = st;
         }
     } restore{Hm, saved_stream, {}};
-    const int64_t M = H->M, nb = H->nadm, N = 3 * M;
-    if (M > INT32_MAX / 3) return fail(HM_EINVAL, "hm_amvm: mesh too large");
+    // rows: the 3 Mr dofs of the row points (Mr = M unless H is the
+    // evaluation operator); columns: the 3M dofs of the triangles
+    const int64_t M = H->M, Mr = H->Mr, nb = H->nadm, N = 3 * Mr, Ncol = 3 * M;
+    if (M > INT32_MAX / 3 || Mr > INT32_MAX / 3) return fail(HM_EINVAL, "hm_amvm: mesh too large");
     const double c1 = (1.0 + H->nu) * (3.0 - 4.0 * H->nu) / (2.0 * H->E * (1.0 - H->nu));
     const double c2 = (1.0 + H->nu) / (2.0 * H->E * (1.0 - H->nu));
 
     // ---- host tables: row intervals, block lists, part offsets, c_sp
-    std::vector<int64_t> bounds = {0, M};
+    std::vector<int64_t> bounds = {0, Mr};
     for (const Blk& b : H->adm_h) {
         bounds.push_back(b.t0);
         bounds.push_back(b.t0 + b.m);
@@ -435,7 +454,7 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
     }
     std::sort(bounds.begin(), bounds.end());
     bounds.erase(std::unique(bounds.begin(), bounds.end()), bounds.end());
-    const RowLists ra = row_lists(M, bounds, H->adm_h), rn = row_lists(M, bounds, H->near_h);
+    const RowLists ra = row_lists(Mr, bounds, H->adm_h), rn = row_lists(Mr, bounds, H->near_h);
     std::vector<int64_t> doff((size_t)nb + 1, 0);
     for (int64_t b = 0; b < nb; ++b) doff[(size_t)b + 1] = doff[(size_t)b] + 3 * (int64_t)H->adm_h[(size_t)b].m;
     int csp = 0;
@@ -453,11 +472,11 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
     Pool pool;
     pool.al = H->alloc;
     pool.al.stream = s;
-    double* xc = pool.get<double>((size_t)N);
+    double* xc = pool.get<double>((size_t)Ncol);
     double* bk = pool.get<double>((size_t)N);
     double* e = pool.get<double>((size_t)N);
     double* D = pool.get<double>((size_t)doff[(size_t)nb]);
-    int32_t* d_ipos = pool.get<int32_t>((size_t)M);
+    int32_t* d_ipos = pool.get<int32_t>((size_t)Mr);
     int32_t* d_aptr = pool.get<int32_t>(ra.ptr.size());
     int32_t* d_aidx = pool.get<int32_t>(ra.idx.size());
     int32_t* d_nptr = pool.get<int32_t>(rn.ptr.size());
@@ -471,7 +490,7 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
     int32_t* d_sidx = pool.get<int32_t>((size_t)P);
     int32_t* d_rowpos = pool.get<int32_t>((size_t)N);
     int32_t* d_first = pool.get<int32_t>((size_t)nb);
-    double* d_part = pool.get<double>((size_t)(M + 255) / 256 + 1);
+    double* d_part = pool.get<double>((size_t)(Mr + 255) / 256 + 1);
     double* d_norm = pool.get<double>(1);
     if (!d_key || !d_sidx || !d_rowpos || !d_first || !d_part || !d_norm)
         return fail(HM_ENOMEM, "hm_amvm: marking workspace");
@@ -485,7 +504,7 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
     if ((rc = put(d_ipos, ra.ipos, s)) || (rc = put(d_aptr, ra.ptr, s)) || (rc = put(d_aidx, ra.idx, s)) ||
         (rc = put(d_nptr, rn.ptr, s)) || (rc = put(d_nidx, rn.idx, s)) || (rc = put(d_doff, doff, s)))
         return rc;
-    const unsigned gM = (unsigned)((M + 255) / 256);
+    const unsigned gM = (unsigned)((Mr + 255) / 256), gMc = (unsigned)((M + 255) / 256);
     const Blk* d_adm = H->d_adm.as<Blk>();
     // the crosses of every block-kernel: pointers to U (k x m) and V (k x n),
     // and how many there are (krank); on demand, also the kmax of the run
@@ -569,17 +588,17 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
     };
 
     // ---- b_0 = near field + every admissible block at rank r0
-    amvm_gather_kernel<<<gM, 256, 0, s>>>(H->d_perm.as<int32_t>(), x, xc, M);
+    amvm_gather_kernel<<<gMc, 256, 0, s>>>(H->d_perm.as<int32_t>(), x, xc, M);
     HM_CUDA(cudaGetLastError());
     amvm_near_kernel<<<gM, 256, 0, s>>>(d_ipos, d_nptr, d_nidx, H->d_near.as<Blk>(), H->d_noff.as<int64_t>(),
-                                       H->N64.as<double>(), xc, c1, c2, bk, M);
+                                       H->N64.as<double>(), xc, c1, c2, bk, Mr);
     HM_CUDA(cudaGetLastError());
     std::vector<int32_t> r((size_t)nb, r0);
     std::vector<AmvmItem> items((size_t)nb);
     for (int64_t b = 0; b < nb; ++b) items[(size_t)b] = AmvmItem{(int32_t)b, 0, r0, 0};
     if ((rc = parts(items))) return rc;
     if (nb > 0) {
-        amvm_rowsum_kernel<<<gM, 256, 0, s>>>(d_ipos, d_aptr, d_aidx, d_adm, d_doff, D, nullptr, 1, bk, M);
+        amvm_rowsum_kernel<<<gM, 256, 0, s>>>(d_ipos, d_aptr, d_aidx, d_adm, d_doff, D, nullptr, 1, bk, Mr);
         HM_CUDA(cudaGetLastError());
     }
     // look-ahead parts at the current ranks
@@ -594,7 +613,7 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
     for (;;) {
         // e = b^_k - b_k
         if (nb > 0) {
-            amvm_rowsum_kernel<<<gM, 256, 0, s>>>(d_ipos, d_aptr, d_aidx, d_adm, d_doff, D, nullptr, 0, e, M);
+            amvm_rowsum_kernel<<<gM, 256, 0, s>>>(d_ipos, d_aptr, d_aidx, d_adm, d_doff, D, nullptr, 0, e, Mr);
             HM_CUDA(cudaGetLastError());
         } else {
             HM_CUDA(cudaMemsetAsync(e, 0, (size_t)N * sizeof(double), s));
@@ -618,7 +637,8 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
         // is found by bisection on ||rest(j)|| <= (1 - theta) gamma_k (the first
         // such row when ||rest|| decreases along the scan, as it does when parts
         // remove error; otherwise a row where the condition holds)
-        const double thr = (1.0 - theta) * gamma / std::sqrt((double)csp * (double)N * (double)N);
+        // (c_sp M N)^{-1/2} of step 3 with the paper's M x N = 3 Mr x 3M
+        const double thr = (1.0 - theta) * gamma / std::sqrt((double)csp * (double)N * (double)Ncol);
         const unsigned gP = (unsigned)((P + 255) / 256), gB = (unsigned)((nb + 255) / 256);
         amvm_sort_init_kernel<<<gP, 256, 0, s>>>(e, N, P, d_key, d_sidx);
         HM_CUDA(cudaGetLastError());
@@ -631,12 +651,12 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
         HM_CUDA(cudaGetLastError());
         amvm_first_kernel<<<(unsigned)nb, 256, 0, s>>>(d_adm, d_doff, D, d_rowpos, thr, d_first);
         HM_CUDA(cudaGetLastError());
-        const int64_t npart = (M + 255) / 256;
+        const int64_t npart = (Mr + 255) / 256;
         auto rest2 = [&](int32_t j, double& out) -> int {
             amvm_cut_kernel<<<gB, 256, 0, s>>>(d_first, nb, j, d_flags);
             HM_CUDA(cudaGetLastError());
             amvm_rest_kernel<<<(unsigned)npart, 256, 0, s>>>(d_ipos, d_aptr, d_aidx, d_adm, d_doff, D, d_flags, e,
-                                                            M, d_part);
+                                                            Mr, d_part);
             HM_CUDA(cudaGetLastError());
             amvm_sum_kernel<<<1, 256, 0, s>>>(d_part, npart, d_norm);
             HM_CUDA(cudaGetLastError());
@@ -672,7 +692,7 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
         if (newly.empty()) break;
         marked_total += (int64_t)newly.size();
         // step 4: A_{k+1} = A^_k on the marked blocks (d_flags), and their next look-ahead
-        amvm_rowsum_kernel<<<gM, 256, 0, s>>>(d_ipos, d_aptr, d_aidx, d_adm, d_doff, D, d_flags, 1, bk, M);
+        amvm_rowsum_kernel<<<gM, 256, 0, s>>>(d_ipos, d_aptr, d_aidx, d_adm, d_doff, D, d_flags, 1, bk, Mr);
         HM_CUDA(cudaGetLastError());
         items.clear();
         std::map<int, std::vector<int32_t>> rerun;  // on demand: tasks to extend, by their new kmax
@@ -700,7 +720,7 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
         if ((rc = parts(items))) return rc;
         ++it;
     }
-    amvm_scatter_kernel<<<gM, 256, 0, s>>>(H->d_perm.as<int32_t>(), bk, y, M);
+    amvm_scatter_kernel<<<gM, 256, 0, s>>>(H->row_perm(), bk, y, Mr);
     HM_CUDA(cudaGetLastError());
     HM_CUDA(cudaStreamSynchronize(s));
     if (info) {
@@ -721,5 +741,104 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
     }
     if (block_ranks)
         for (int64_t b = 0; b < nb; ++b) block_ranks[b] = r[(size_t)b];
+    return HM_OK;
+}
+
+// ------------------------------------------------------------------------
+// The evaluation operator ~V_h (Section 5, Eq. (vector_eq)): its exact FP64
+// product with the kernels above -- every admissible block with all its
+// crosses, the near field exact, per row position a fixed summation order.
+namespace hm {
+namespace {
+enum { kEvIpos, kEvAptr, kEvAidx, kEvNptr, kEvNidx, kEvDoff, kEvItems, kEvUptr, kEvVptr, kEvXc, kEvYc, kEvD };
+static_assert(kEvD + 1 == hm_matrix::kEvBufs, "evaluation buffers");
+
+template <class T>
+int ev_put(hm_matrix& H, int which, const std::vector<T>& h, size_t n)
+{
+    DevBuf& d = H.ev[which];
+    d.bytes = std::max<size_t>(n, 1) * sizeof(T);
+    d.p = H.alloc.alloc(d.bytes);
+    if (!d.p) return fail(HM_ENOMEM, "evaluation operator: device allocation of %zu bytes failed", d.bytes);
+    if (!h.empty())
+        HM_CUDA(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, H.alloc.stream));
+    return HM_OK;
+}
+}  // namespace
+
+int eval_prepare(hm_matrix& H)
+{
+    const int64_t M = H.M, Mr = H.Mr, nb = H.nadm;
+    std::vector<int64_t> bounds = {0, Mr};
+    for (const auto* L : {&H.adm_h, &H.near_h})
+        for (const Blk& b : *L) {
+            bounds.push_back(b.t0);
+            bounds.push_back(b.t0 + b.m);
+        }
+    std::sort(bounds.begin(), bounds.end());
+    bounds.erase(std::unique(bounds.begin(), bounds.end()), bounds.end());
+    const RowLists ra = row_lists(Mr, bounds, H.adm_h), rn = row_lists(Mr, bounds, H.near_h);
+    std::vector<int64_t> doff((size_t)nb + 1, 0);
+    for (int64_t b = 0; b < nb; ++b) doff[(size_t)b + 1] = doff[(size_t)b] + 3 * (int64_t)H.adm_h[(size_t)b].m;
+    std::vector<AmvmItem> items((size_t)nb);
+    int32_t maxrank = 0;
+    for (int64_t b = 0; b < nb; ++b) items[(size_t)b] = AmvmItem{(int32_t)b, 0, INT32_MAX, 0};
+    std::vector<const double*> uptr((size_t)nb * 7, nullptr), vptr((size_t)nb * 7, nullptr);
+    for (int64_t q = 0; q < nb * 7; ++q) {
+        uptr[(size_t)q] = H.U64.as<double>() + H.uoff_h[(size_t)q];
+        vptr[(size_t)q] = H.V64.as<double>() + H.voff_h[(size_t)q];
+        maxrank = std::max(maxrank, H.rank_h[(size_t)q]);
+    }
+    H.ev_parts = doff[(size_t)nb];
+    H.ev_maxrank = maxrank;
+    int rc;
+    const std::vector<double> none;
+    if ((rc = ev_put(H, kEvIpos, ra.ipos, ra.ipos.size())) || (rc = ev_put(H, kEvAptr, ra.ptr, ra.ptr.size())) ||
+        (rc = ev_put(H, kEvAidx, ra.idx, ra.idx.size())) || (rc = ev_put(H, kEvNptr, rn.ptr, rn.ptr.size())) ||
+        (rc = ev_put(H, kEvNidx, rn.idx, rn.idx.size())) || (rc = ev_put(H, kEvDoff, doff, doff.size())) ||
+        (rc = ev_put(H, kEvItems, items, items.size())) || (rc = ev_put(H, kEvUptr, uptr, uptr.size())) ||
+        (rc = ev_put(H, kEvVptr, vptr, vptr.size())) || (rc = ev_put(H, kEvXc, none, (size_t)(3 * M))) ||
+        (rc = ev_put(H, kEvYc, none, (size_t)(3 * Mr))) || (rc = ev_put(H, kEvD, none, (size_t)doff[(size_t)nb])))
+        return rc;
+    return HM_OK;
+}
+}  // namespace hm
+
+extern "C" int hm_eval_points(const hm_matrix* H, const double* t, double* u, int32_t nrhs, void* stream)
+{
+    if (!H || !t || !u) return fail(HM_EINVAL, "hm_eval_points: NULL argument");
+    if (!H->rect) return fail(HM_EINVAL, "hm_eval_points: not an evaluation operator (use hm_matvec)");
+    if (H->aca_deferred)
+        return fail(HM_EINVAL, "hm_eval_points: assembled with HM_DEFER_ACA (use hm_amvm with HM_AMVM_ACA_ON_DEMAND)");
+    if (nrhs < 1) return fail(HM_EINVAL, "hm_eval_points: nrhs %d < 1", nrhs);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t M = H->M, Mr = H->Mr, nb = H->nadm;
+    const double c1 = (1.0 + H->nu) * (3.0 - 4.0 * H->nu) / (2.0 * H->E * (1.0 - H->nu));
+    const double c2 = (1.0 + H->nu) / (2.0 * H->E * (1.0 - H->nu));
+    const DevBuf* ev = H->ev;
+    double* xc = ev[kEvXc].as<double>();
+    double* yc = ev[kEvYc].as<double>();
+    const unsigned gM = (unsigned)((Mr + 255) / 256), gMc = (unsigned)((M + 255) / 256);
+    for (int32_t r = 0; r < nrhs; ++r) {
+        amvm_gather_kernel<<<gMc, 256, 0, s>>>(H->d_perm.as<int32_t>(), t + (int64_t)r * 3 * M, xc, M);
+        HM_CUDA(cudaGetLastError());
+        amvm_near_kernel<<<gM, 256, 0, s>>>(ev[kEvIpos].as<int32_t>(), ev[kEvNptr].as<int32_t>(),
+                                           ev[kEvNidx].as<int32_t>(), H->d_near.as<Blk>(), H->d_noff.as<int64_t>(),
+                                           H->N64.as<double>(), xc, c1, c2, yc, Mr);
+        HM_CUDA(cudaGetLastError());
+        if (nb > 0) {
+            amvm_part_kernel<<<(unsigned)nb, kAmvmThreads, 0, s>>>(
+                ev[kEvItems].as<AmvmItem>(), H->d_adm.as<Blk>(), H->d_rank.as<int32_t>(),
+                ev[kEvUptr].as<const double*>(), ev[kEvVptr].as<const double*>(), xc, c1, c2,
+                ev[kEvDoff].as<int64_t>(), ev[kEvD].as<double>());
+            HM_CUDA(cudaGetLastError());
+            amvm_rowsum_kernel<<<gM, 256, 0, s>>>(ev[kEvIpos].as<int32_t>(), ev[kEvAptr].as<int32_t>(),
+                                                 ev[kEvAidx].as<int32_t>(), H->d_adm.as<Blk>(),
+                                                 ev[kEvDoff].as<int64_t>(), ev[kEvD].as<double>(), nullptr, 1, yc, Mr);
+            HM_CUDA(cudaGetLastError());
+        }
+        amvm_scatter_kernel<<<gM, 256, 0, s>>>(H->d_rperm.as<int32_t>(), yc, u + (int64_t)r * 3 * Mr, Mr);
+        HM_CUDA(cudaGetLastError());
+    }
     return HM_OK;
 }

@@ -160,6 +160,7 @@ int hm_batch_create(const hm_matrix* const* mats, int32_t nmat, int32_t form, in
     if (max_rhs < 1) return fail(HM_EINVAL, "hm_batch_create: max_rhs must be >= 1");
     for (int32_t m = 0; m < nmat; ++m) {
         if (!mats[m]) return fail(HM_EINVAL, "hm_batch_create: matrix %d is NULL", m);
+        if (mats[m]->rect) return fail(HM_EINVAL, "hm_batch_create: matrix %d: an evaluation operator (hm_build_point_tree) has only hm_eval_points and hm_amvm", m);
         if (!mats[m]->packed[form])
             return fail(HM_EINVAL, "hm_batch_create: matrix %d has form %d not packed (call hm_pack)", m, form);
         for (int32_t q = 0; q < m; ++q)

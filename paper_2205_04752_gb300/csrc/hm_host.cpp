@@ -109,6 +109,15 @@ struct TreeBuilder {
                 nd.bmax[k] = -INFINITY;
             }
             for (int64_t p = lo; p < hi; ++p) {
+                if (tr.T.empty()) {
+                    // a tree of points: the box of the points themselves
+                    for (int k = 0; k < 3; ++k) {
+                        double v = tr.coll[3 * tr.perm[p] + k];
+                        nd.bmin[k] = std::min(nd.bmin[k], v);
+                        nd.bmax[k] = std::max(nd.bmax[k], v);
+                    }
+                    continue;
+                }
                 const int32_t* t = &tr.T[3 * tr.perm[p]];
                 for (int c = 0; c < 3; ++c)
                     for (int k = 0; k < 3; ++k) {
@@ -174,8 +183,10 @@ double box_dist2(const Node& a, const Node& b)
 }
 
 // block-cluster recursion (Section 2.1) with an explicit stack; the visiting
-// order is the recursive pre-order (sons in order (0,0), (0,1), (1,0), (1,1))
-void build_partition(hm_tree& tr)
+// order is the recursive pre-order (sons in order (0,0), (0,1), (1,0), (1,1));
+// rows come from `rows` (the tree itself, or a tree of points) and columns
+// from `cols`
+void build_partition(hm_tree& tr, const std::vector<Node>& rows, const std::vector<Node>& cols)
 {
     const double eta2 = tr.eta * tr.eta;
     std::vector<std::array<int64_t, 2>> st;
@@ -183,8 +194,8 @@ void build_partition(hm_tree& tr)
     while (!st.empty()) {
         auto [t, s] = st.back();
         st.pop_back();
-        const Node& a = tr.nodes[(size_t)t];
-        const Node& b = tr.nodes[(size_t)s];
+        const Node& a = rows[(size_t)t];
+        const Node& b = cols[(size_t)s];
         double dmin = std::min(box_diam2(a), box_diam2(b));
         if (dmin < eta2 * box_dist2(a, b)) {
             tr.adm.push_back({t, s});
@@ -272,7 +283,7 @@ int hm_build_cluster_tree(const double* verts, int64_t nv, const int32_t* tris, 
         tr->nodes.reserve((size_t)(2 * nt));
         TreeBuilder tb{*tr, {}};
         tb.build(0, nt, 0);
-        build_partition(*tr);
+        build_partition(*tr, tr->nodes, tr->nodes);
         for (size_t n = 0; n < tr->nodes.size(); ++n)
             if (tr->nodes[n].son[0] < 0) tr->leaves.push_back((int64_t)n);
         std::sort(tr->leaves.begin(), tr->leaves.end(), [&](int64_t a, int64_t b) {
@@ -281,6 +292,48 @@ int hm_build_cluster_tree(const double* verts, int64_t nv, const int32_t* tris, 
     } catch (const std::bad_alloc&) {
         delete tr;
         return fail(HM_ENOMEM, "hm_build_cluster_tree: out of host memory");
+    }
+    *out = tr;
+    return HM_OK;
+}
+
+int hm_build_point_tree(const hm_tree* surface, const double* pts, int64_t npts, int32_t leaf, hm_tree** out)
+{
+    if (!out) return fail(HM_EINVAL, "hm_build_point_tree: out is NULL");
+    *out = nullptr;
+    if (!surface || !pts) return fail(HM_EINVAL, "hm_build_point_tree: NULL argument");
+    if (surface->src) return fail(HM_EINVAL, "hm_build_point_tree: `surface` must be a triangle tree");
+    if (npts < 1) return fail(HM_EINVAL, "hm_build_point_tree: no points");
+    if (npts > (int64_t)INT32_MAX / 4) return fail(HM_EINVAL, "hm_build_point_tree: too many points");
+    if (leaf < 1 || leaf > HM_MAX_LEAF)
+        return fail(HM_EINVAL, "hm_build_point_tree: leaf must lie in 1..%d", HM_MAX_LEAF);
+    for (int64_t i = 0; i < 3 * npts; ++i)
+        if (!std::isfinite(pts[i])) return fail(HM_EINVAL, "hm_build_point_tree: non-finite point coordinate");
+    hm_tree* tr = new (std::nothrow) hm_tree();
+    if (!tr) return fail(HM_ENOMEM, "hm_build_point_tree: out of host memory");
+    try {
+        auto src = std::make_shared<hm_tree>(*surface);
+        src->adm.clear();
+        src->near_blocks.clear();
+        tr->M = npts;
+        tr->leaf = leaf;
+        tr->eta = surface->eta;
+        tr->coll.assign(pts, pts + 3 * npts);
+        tr->perm.resize((size_t)npts);
+        for (int64_t i = 0; i < npts; ++i) tr->perm[(size_t)i] = i;
+        tr->nodes.reserve((size_t)(2 * npts));
+        TreeBuilder tb{*tr, {}};
+        tb.build(0, npts, 0);
+        build_partition(*tr, tr->nodes, src->nodes);
+        for (size_t n = 0; n < tr->nodes.size(); ++n)
+            if (tr->nodes[n].son[0] < 0) tr->leaves.push_back((int64_t)n);
+        std::sort(tr->leaves.begin(), tr->leaves.end(), [&](int64_t a, int64_t b) {
+            return tr->nodes[(size_t)a].lo < tr->nodes[(size_t)b].lo;
+        });
+        tr->src = std::move(src);
+    } catch (const std::bad_alloc&) {
+        delete tr;
+        return fail(HM_ENOMEM, "hm_build_point_tree: out of host memory");
     }
     *out = tr;
     return HM_OK;
@@ -465,6 +518,7 @@ int hm_profile_read(hm_matrix* H, double ms[4], int64_t* calls)
 int hm_compact(hm_matrix* H)
 {
     if (!H) return fail(HM_EINVAL, "hm_compact: NULL matrix");
+    if (H->rect) return fail(HM_EINVAL, "hm_compact: an evaluation operator has no packed form");
     if (H->compacted) return HM_OK;
     if (!H->packed[HM_FP32] && !H->packed[HM_BF16] && !H->packed[HM_FP16])
         return fail(HM_EINVAL, "hm_compact: pack a reduced form first (hm_pack)");
@@ -494,10 +548,13 @@ int hm_footprint(const hm_matrix* H, int64_t* bytes)
                                 &H->d_mesh[0], &H->d_mesh[1], &H->d_mesh[2], &H->d_mesh[3], &H->d_counters,
                                 &H->d_err, &H->U64, &H->V64, &H->N64, &H->Ul[0], &H->Ul[1], &H->Ul[2],
                                 &H->Ul[3], &H->Vr[0], &H->Vr[1], &H->Vr[2], &H->Vr[3], &H->Nl64, &H->Nl32,
-                                &H->SU, &H->SV, &H->xg, &H->wb, &H->zb, &H->xh, &H->yh, &H->g_coll, &H->g_tri, &H->g_qp, &H->g_qw, &H->g_diam};
+                                &H->SU, &H->SV, &H->xg, &H->wb, &H->zb, &H->xh, &H->yh, &H->g_coll, &H->g_tri, &H->g_qp, &H->g_qw, &H->g_diam,
+                                &H->d_rperm, &H->g_rows};
     int64_t t = 0;
     for (const hm::DevBuf* b : bufs)
         if (b->p) t += (int64_t)b->bytes;
+    for (const hm::DevBuf& b : H->ev)
+        if (b.p) t += (int64_t)b.bytes;
     *bytes = t;
     return HM_OK;
 }
@@ -514,7 +571,8 @@ void hm_matrix_destroy(hm_matrix* H)
                           &H->d_mesh[3], &H->d_counters, &H->d_err, &H->U64, &H->V64, &H->N64,
                           &H->Ul[0], &H->Ul[1], &H->Ul[2], &H->Ul[3], &H->Vr[0], &H->Vr[1],
                           &H->Vr[2], &H->Vr[3], &H->Nl64, &H->Nl32, &H->SU, &H->SV, &H->xg, &H->wb, &H->zb,
-                          &H->xh, &H->yh, &H->g_coll, &H->g_tri, &H->g_qp, &H->g_qw, &H->g_diam};
+                          &H->xh, &H->yh, &H->g_coll, &H->g_tri, &H->g_qp, &H->g_qw, &H->g_diam,
+                          &H->d_rperm, &H->g_rows};
     // the assembly stream may be gone by now: drain the device and release
     // on the legacy default stream
     cudaDeviceSynchronize();
@@ -522,6 +580,10 @@ void hm_matrix_destroy(hm_matrix* H)
     for (hm::DevBuf* b : bufs) {
         H->alloc.release(b->p, b->bytes);
         b->p = nullptr;
+    }
+    for (hm::DevBuf& b : H->ev) {
+        H->alloc.release(b.p, b.bytes);
+        b.p = nullptr;
     }
     cudaDeviceSynchronize();
     delete H;

@@ -6,6 +6,7 @@
 
 #include <array>
 #include <cstdint>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -29,7 +30,7 @@ struct Node {
     int64_t lo, hi;      // [lo, hi) in cluster order
     int64_t son[2];      // -1 for a leaf
     int32_t level;
-    double bmin[3], bmax[3];  // box of all triangle vertices of the cluster
+    double bmin[3], bmax[3];  // box of all triangle vertices of the cluster (of the points in a point tree)
 };
 
 }  // namespace hm
@@ -46,6 +47,11 @@ struct hm_tree {
     std::vector<hm::Node> nodes;  // pre-order
     std::vector<std::array<int64_t, 2>> adm, near_blocks;  // (row node, col node)
     std::vector<int64_t> leaves;  // leaf node ids in cluster order
+    // a tree of points (hm_build_point_tree): `coll` holds the points, V and T
+    // are empty, and the partition pairs its nodes (rows) with the nodes of
+    // the triangle tree `src` (columns) -- the evaluation operator of
+    // Section 5, Eq. (vector_eq)
+    std::shared_ptr<const hm_tree> src;
 };
 
 namespace hm {
@@ -212,7 +218,9 @@ constexpr int kCounterInts = 128;
 
 struct hm_matrix {
     // geometry / partition
-    int64_t M = 0;
+    int64_t M = 0;   // columns: triangles (and rows of a square matrix)
+    int64_t Mr = 0;  // rows: M, or the points of an evaluation operator
+    bool rect = false;  // evaluation operator ~V_h (Section 5, Eq. (vector_eq)): rows are points
     int64_t nadm = 0, nnear = 0, nleaves = 0;
     double E = 1.0, nu = 0.3;
     hm_params prm{};
@@ -275,6 +283,16 @@ struct hm_matrix {
     bool compacted = false;  // FP64 data released (hm_compact)
     bool aca_deferred = false;  // HM_DEFER_ACA: no ACA at assembly (adaptive product only)
     hm::DevBuf g_coll, g_tri, g_qp, g_qw, g_diam;  // cluster-order geometry of the entries (ACA on demand)
+    hm::DevBuf d_rperm;  // evaluation operator: int32 Mr, point cluster position -> original point
+    hm::DevBuf g_rows;   // evaluation operator: Mr x 3 points in cluster order
+    // evaluation operator: tables and workspace of its exact product
+    // (hm_amvm.cu; index names there)
+    static constexpr int kEvBufs = 12;
+    hm::DevBuf ev[kEvBufs];
+    int64_t ev_parts = 0;   // 3 sum |t| over the admissible blocks
+    int32_t ev_maxrank = 0;
+    // rows of an entry: the collocation points, or the points of ~V_h
+    const int32_t* row_perm() const { return rect ? d_rperm.as<int32_t>() : d_perm.as<int32_t>(); }
 
     // workspace
     int32_t max_rhs = 32;
@@ -337,7 +355,9 @@ int assemble_device(const hm_tree& tr, hm_matrix& H);
 // run (bit 0: stopped at kmax, so it can go on), ||S_k||_F^2, Z itself (m
 // bytes per task at zoff), and the previous run's U (k x m, V right after) or
 // null to start afresh.  A resumed task takes exactly the steps a fresh run to
-// the same kmax would take after its first k crosses.
+// the same kmax would take after its first k crosses.  cap_hint (elements,
+// 0 = the exact bound kmax (m + n) per task) sizes a first arena for runs
+// without resume; the batch runs again into an exact arena if it overflows.
 struct AcaResume {
     int32_t *k, *nz, *irow, *flags;
     double* S2;
@@ -346,7 +366,11 @@ struct AcaResume {
     const double* const* prevU;
 };
 int aca_on_demand(hm_matrix& H, const std::vector<int32_t>& bk, int kmax, cudaStream_t s, DevBuf& out,
-                  std::vector<int32_t>& rank, std::vector<int64_t>& off, const AcaResume* resume = nullptr);
+                  std::vector<int32_t>& rank, std::vector<int64_t>& off, const AcaResume* resume = nullptr,
+                  std::vector<int32_t>* flags = nullptr, size_t cap_hint = 0);
+// the evaluation operator (a matrix assembled from a point tree): tables and
+// workspace of its exact FP64 product (hm_amvm.cu), built once at assembly
+int eval_prepare(hm_matrix& H);
 int matvec_device(const hm_matrix& H, const double* x, double* y, int32_t nrhs, int64_t ld,
                   int32_t form, cudaStream_t s);
 int pack_device(hm_matrix& H, int32_t form, cudaStream_t s);

@@ -1530,6 +1530,7 @@ extern "C" {
 int hm_pack(hm_matrix* H, int32_t form, void* stream)
 {
     if (!H) return fail(HM_EINVAL, "hm_pack: NULL matrix");
+    if (H->rect) return fail(HM_EINVAL, "hm_pack: an evaluation operator (hm_build_point_tree) has only hm_eval_points and hm_amvm");
     if (form < HM_FP64 || form > HM_FP16) return fail(HM_EINVAL, "hm_pack: unknown form %d", form);
     if (H->packed[form]) return HM_OK;
     if (H->compacted) return fail(HM_EINVAL, "hm_pack: FP64 data released (hm_compact); pack before compacting");
@@ -1560,6 +1561,7 @@ int hm_matvec(const hm_matrix* H, const double* x, double* y, int32_t nrhs, int6
               void* stream)
 {
     if (!H || !x || !y) return fail(HM_EINVAL, "hm_matvec: NULL argument");
+    if (H->rect) return fail(HM_EINVAL, "hm_matvec: an evaluation operator (hm_build_point_tree) has only hm_eval_points and hm_amvm");
     if (nrhs < 1 || nrhs > H->max_rhs)
         return fail(HM_EINVAL, "hm_matvec: nrhs=%d outside 1..%d", nrhs, H->max_rhs);
     if (ld < 3 * H->M) return fail(HM_EINVAL, "hm_matvec: ld=%lld < 3M=%lld", (long long)ld, (long long)(3 * H->M));
@@ -1576,6 +1578,7 @@ int hm_matvec_host(const hm_matrix* H, const double* x_host, double* y_host, int
                    int32_t form, void* stream)
 {
     if (!H || !x_host || !y_host) return fail(HM_EINVAL, "hm_matvec_host: NULL argument");
+    if (H->rect) return fail(HM_EINVAL, "hm_matvec_host: an evaluation operator (hm_build_point_tree) has only hm_eval_points and hm_amvm");
     if (nrhs < 1 || nrhs > H->max_rhs)
         return fail(HM_EINVAL, "hm_matvec_host: nrhs=%d outside 1..%d", nrhs, H->max_rhs);
     if (ld < 3 * H->M) return fail(HM_EINVAL, "hm_matvec_host: ld too small");

@@ -60,6 +60,7 @@ extern "C" int hm_matvec_noalloc(const hm_matrix* H, const double* x, double* y,
 {
     using namespace hm;
     if (!H || !x || !y) return fail(HM_EINVAL, "hm_matvec_noalloc: NULL argument");
+    if (H->rect) return fail(HM_EINVAL, "hm_matvec_noalloc: an evaluation operator (hm_build_point_tree) has only hm_eval_points and hm_amvm");
     if (nrhs < 1 || nrhs > H->max_rhs)
         return fail(HM_EINVAL, "hm_matvec_noalloc: nrhs=%d outside 1..%d", nrhs, H->max_rhs);
     if (ld < 3 * H->M)

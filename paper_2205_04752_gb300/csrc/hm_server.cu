@@ -260,6 +260,7 @@ int hm_server_create(const hm_matrix* const* mats, int32_t nmat, const hm_server
     for (int32_t m = 0; m < nmat; ++m) {
         const hm_matrix* H = mats[m];
         if (!H) return fail(HM_EINVAL, "hm_server_create: matrix %d is NULL", m);
+        if (H->rect) return fail(HM_EINVAL, "hm_server_create: matrix %d: an evaluation operator (hm_build_point_tree) has only hm_eval_points and hm_amvm", m);
         for (int32_t f : {p.matvec_form, p.inner_form, p.residual_form})
             if (!H->packed[f]) return fail(HM_EINVAL, "hm_server_create: matrix %d has form %d not packed", m, f);
     }

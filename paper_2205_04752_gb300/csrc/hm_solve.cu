@@ -293,6 +293,7 @@ extern "C" int hm_solve(const hm_matrix* H, const double* g, double* t, const hm
                         hm_solve_info* info, void* stream)
 {
     if (!H || !g || !t || !sp) return fail(HM_EINVAL, "hm_solve: NULL argument");
+    if (H->rect) return fail(HM_EINVAL, "hm_solve: an evaluation operator (hm_build_point_tree) has only hm_eval_points and hm_amvm");
     hm_solve_params p = *sp;
     int rc = solve_check_params(H, p);
     if (rc) return rc;

@@ -109,3 +109,48 @@ def test_tree_and_partition_match_oracle_level6():
     V, T = inputs.icosphere(6)
     tr = _compare_tree(V, T, 64, 0.8)
     assert tr.nadm > 100000 and tr.nnear > 50000
+
+
+@pytest.mark.parametrize("level,leaf,leaf_pts,npts,r_in,r_out", [
+    (3, 32, 24, 700, 0.0, 0.95), (2, 16, 7, 333, 0.0, 0.7), (4, 64, 64, 2000, 0.0, 0.9),
+    (1, 8, 1, 5, 0.0, 0.5), (2, 16, 32, 257, 1.2, 3.0), (2, 16, 336, 96, 0.0, 0.8)])
+def test_point_tree_and_partition_match_oracle(level, leaf, leaf_pts, npts, r_in, r_out):
+    """The rows of the evaluation operator (Section 5, Eq. (vector_eq)): the
+    tree of the points and the partition (point tree) x (triangle tree) are
+    the oracle's, bit for bit; the point tree outlives the triangle tree it
+    was built from."""
+    V, T = inputs.icosphere(level)
+    P = inputs.shell_points(npts, r_in, r_out, 3)
+    tr = binding.build_cluster_tree(V, T, leaf, 0.8)
+    pt = binding.build_point_tree(tr, P, leaf_pts)
+    del tr
+    perm, nodes, adm, near = pt.export()
+    Ho = oracle.HMatrix(V, T, leaf, 0.8, 1e-4, points=P, leaf_points=leaf_pts)
+    np.testing.assert_array_equal(perm, Ho.rperm)
+    np.testing.assert_array_equal(nodes, Ho.rnodes)
+    np.testing.assert_array_equal(adm, Ho.adm)
+    np.testing.assert_array_equal(near, Ho.near)
+    assert pt.M == npts and pt.M_src == len(T)
+
+
+def test_point_tree_invalid_arguments():
+    V, T = inputs.icosphere(1)
+    tr = binding.build_cluster_tree(V, T, 8, 0.8)
+    P = inputs.ball_points(20, 0.5, 1)
+    for leaf in (0, 337):
+        with pytest.raises(binding.HMError) as e:
+            binding.build_point_tree(tr, P, leaf)
+        assert e.value.code == binding.HM_EINVAL
+    Pn = P.copy()
+    Pn[3, 2] = np.inf
+    with pytest.raises(binding.HMError):
+        binding.build_point_tree(tr, Pn, 8)
+    with pytest.raises(binding.HMError):
+        binding.build_point_tree(tr, P[:0], 8)
+    pt = binding.build_point_tree(tr, P, 8)
+    with pytest.raises(binding.HMError):
+        binding.build_point_tree(pt, P, 8)  # a point tree is no surface
+    lib = binding.load()
+    out = ctypes.c_void_p()
+    assert lib.hm_build_point_tree(None, None, 0, 8, ctypes.byref(out)) == binding.HM_EINVAL
+    assert lib.hm_eval_points(None, None, None, 1, None) == binding.HM_EINVAL
