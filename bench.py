@@ -232,6 +232,25 @@ def run_ours(args):
     t0 = time.perf_counter()
     tree = binding.build_cluster_tree(V, T, w["leaf"], w["eta"])
     t_tree = time.perf_counter() - t0
+    if args.points_minimal:
+        # profiling runs of the evaluation operator alone
+        xp = torch.tensor(inputs.uniform_rhs(3 * M, 0)[0], device="cuda")
+
+        def timed_p(fn, steps, warmup):
+            for _ in range(warmup):
+                fn()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+        ctx = bench_points(args, tree, w, xp, timed_p, eval_only=True)
+        print(json.dumps({"points_minimal": True, "level": args.level, **ctx}), flush=True)
+        return 0
     t0 = time.perf_counter()
     H = binding.aca_assemble(tree, w["E"], w["nu"], w["aca_eps"], max_rhs=32)
     torch.cuda.synchronize()
@@ -432,7 +451,23 @@ def run_ours(args):
     return 0
 
 
-def bench_points(args, tree, w, x, timed):
+def _fp64_peak():
+    """FP64 (CUDA-core) peak of this GPU: 2 FMA per SM per clock (4 flops),
+    the rate behind NVIDIA's 1.25 TFLOP/s for GB300 (152 SMs at 2.07 GHz),
+    scaled by this device's SM count and maximum SM clock."""
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = 2070.0
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits",
+                              "-i", "0"], capture_output=True, text=True, timeout=10).stdout.split()
+        mhz = float(out[0]) if out else mhz
+    except (OSError, ValueError, subprocess.SubprocessError):
+        pass
+    return round(nsm * 4 * mhz * 1e6 / 1e12, 4), f"{nsm} SMs x 4 FP64 flops/clk x {mhz:.0f} MHz"
+
+
+def bench_points(args, tree, w, x, timed, eval_only=False):
     """The evaluation operator ~V_h (Section 5, Eq. (vector_eq)) for 65,536
     points uniform in the ball of radius 0.95 inside the level-6 sphere (leaf
     64): assembly, the exact FP64 product u = ~V_h t (device time, the bytes
@@ -441,7 +476,7 @@ def bench_points(args, tree, w, x, timed):
     with ACA on demand."""
     import torch
     from paper_2205_04752_gb300 import binding, inputs
-    npts = 65536
+    npts = 65536 if args.level == 6 else 65536 >> (2 * (6 - args.level))
     P = inputs.ball_points(npts, 0.95, 7)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -464,6 +499,20 @@ def bench_points(args, tree, w, x, timed):
     alg = (st.far_entries + 6 * st.near_pairs) * 8 + 2 * 3 * rows_far * 8 + 2 * 3 * M * 8 + 2 * 3 * npts * 8
     peak, peak_kind = _peaks()
     gbs = alg / (ms * 1e-3) / 1e9
+    # FP64 operations the product must execute: per factor entry of kernel k
+    # one FMA per component it needs (V_Delta 3, V_pp 1, V_pq 2) in V^T x and
+    # again in U w; per near pair 12 FMA and 2 additions; an FMA counts 2
+    need = (3, 1, 2, 2, 1, 2, 1)
+    flops = 2 * sum(c * e for c, e in zip(need, st.far_entries_kern)) + 26 * st.near_pairs
+    fp64_peak, fp64_src = _fp64_peak()
+    tf = flops / (ms * 1e-3) / 1e12
+    ev = {"ms": round(ms, 3), "evals_per_s": round(1e3 / ms, 2), "alg_bytes": int(alg),
+          "achieved_GBps": round(gbs, 1), "hbm_peak": peak, "hbm_peak_kind": peak_kind,
+          "hbm_frac": round(gbs / peak, 4), "steps": steps,
+          "roofline": {"bound": "alu", "achieved": round(tf, 4), "peak": fp64_peak, "unit": "TFLOP/s",
+                       "frac": round(tf / fp64_peak, 4), "flops": int(flops), "peak_from": fp64_src}}
+    if eval_only:
+        return {"points": npts, "nadm": st.nadm, "nnear": st.nnear, "assemble_s": round(t_asm, 3), "eval": ev}
     ya = torch.empty_like(u)
     binding.amvm(Hp, t, ya, theta=0.7, eps=1e-4)  # warm-up
     torch.cuda.synchronize()
@@ -489,9 +538,7 @@ def bench_points(args, tree, w, x, timed):
     return {"points": npts, "region": "ball r <= 0.95 (seed 7)", "leaf": 64, "nadm": st.nadm,
             "nnear": st.nnear, "tree_s": round(t_tree, 3), "assemble_s": round(t_asm, 3),
             "rank_mean": [round(r / max(st.nadm, 1), 2) for r in st.rank_sum],
-            "eval": {"ms": round(ms, 3), "evals_per_s": round(1e3 / ms, 2), "alg_bytes": int(alg),
-                     "achieved_GBps": round(gbs, 1), "peak": peak, "peak_kind": peak_kind,
-                     "frac": round(gbs / peak, 4), "steps": steps},
+            "eval": ev,
             "amvm": {"theta": 0.7, "eps": 1e-4, "ms": round(amvm_ms, 1), "iterations": ai["iterations"],
                      "crosses_used_fraction": round(ai["crosses_used"] / max(ai["crosses_full"], 1), 4),
                      "rel_err_vs_exact_product": err,
@@ -686,6 +733,9 @@ def main():
     ap.add_argument("--nrhs", type=int, default=1,
                     help="with --minimal: right-hand sides per timed product (profiling the several-vector "
                          "kernels)")
+    ap.add_argument("--points-minimal", action="store_true",
+                    help="profiling runs of the evaluation operator: assemble it for 65,536 points "
+                         "(4^(level-6) x 65,536 below level 6) and time its exact product only")
     ap.add_argument("--level", type=int, default=6,
                     help="icosphere level; 6 is the benchmark workload, smaller levels are for "
                          "profiling captures")

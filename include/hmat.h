@@ -480,6 +480,7 @@ typedef struct {
     int64_t bytes_fp64;         /* far + near bytes read by one FP64 product */
     int64_t bytes_form[4];      /* same for each form (0 if not packed) */
     double assemble_ms[3];      /* near-field quadrature, ACA, packing (device time) */
+    int64_t far_entries_kern[7]; /* sum over admissible blocks of k(|t|+|s|), per scalar kernel */
 } hm_stats;
 
 int hm_get_stats(const hm_matrix* H, hm_stats* st);

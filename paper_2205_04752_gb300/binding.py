@@ -113,7 +113,8 @@ class _Stats(ctypes.Structure):
                 ("rank_sum", ctypes.c_int64 * 7),
                 ("rank_max", ctypes.c_int32 * 7), ("rank_cap_hits", ctypes.c_int32),
                 ("csp", ctypes.c_int32), ("bytes_fp64", ctypes.c_int64),
-                ("bytes_form", ctypes.c_int64 * 4), ("assemble_ms", ctypes.c_double * 3)]
+                ("bytes_form", ctypes.c_int64 * 4), ("assemble_ms", ctypes.c_double * 3),
+                ("far_entries_kern", ctypes.c_int64 * 7)]
 
 
 _lib = None
@@ -293,6 +294,7 @@ class Stats:
     bytes_fp64: int
     bytes_form: list
     assemble_ms: list
+    far_entries_kern: list
 
 
 class HMatrix:
@@ -343,7 +345,7 @@ class HMatrix:
         _check(load().hm_get_stats(self._h, ctypes.byref(st)))
         return Stats(st.M, st.nadm, st.nnear, st.nleaves, st.near_pairs, st.far_entries,
                      st.far_u_entries, st.far_v_entries, st.factor_columns, list(st.rank_sum), list(st.rank_max), st.rank_cap_hits, st.csp,
-                     st.bytes_fp64, list(st.bytes_form), list(st.assemble_ms))
+                     st.bytes_fp64, list(st.bytes_form), list(st.assemble_ms), list(st.far_entries_kern))
 
     def check(self):
         """Raise if a bounded device wait in an earlier product ran out."""

@@ -154,6 +154,7 @@ __global__ void __launch_bounds__(kAmvmThreads) amvm_part_kernel(
     __syncthreads();
     for (int i = tid; i < bk.m; i += kAmvmThreads) {
         double y[3] = {0.0, 0.0, 0.0};
+#pragma unroll
         for (int k = 0; k < 7; ++k) {
             const double* u = uptr[it.b * 7 + k] + (int64_t)l0 * bk.m + i;
             double s[3] = {0.0, 0.0, 0.0};
@@ -746,12 +747,304 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
 
 // ------------------------------------------------------------------------
 // The evaluation operator ~V_h (Section 5, Eq. (vector_eq)): its exact FP64
-// product with the kernels above -- every admissible block with all its
-// crosses, the near field exact, per row position a fixed summation order.
+// product -- every admissible block with all its crosses, the near field
+// exact, per row position a fixed summation order -- in four passes, each
+// spread over warps so that the factor and near-field streams are read with
+// many loads in flight:
+//   ev_fwd   one warp per (block, kernel): w_c = V_c^T x(s) for its crosses c
+//            (3 components of x gathered component-major; lane-strided sums,
+//            fixed butterfly);
+//   ev_back  one warp per (block, 32 rows): the block's part of the rows,
+//            U w with c1 / c2 as in the adaptive product's part kernel;
+//   ev_near  one warp per (near block, 32 rows): the near block's part;
+//   ev_rowsum  one thread per row position: its admissible parts in block
+//            order, then its near parts in block order.
 namespace hm {
 namespace {
-enum { kEvIpos, kEvAptr, kEvAidx, kEvNptr, kEvNidx, kEvDoff, kEvItems, kEvUptr, kEvVptr, kEvXc, kEvYc, kEvD };
-static_assert(kEvD + 1 == hm_matrix::kEvBufs, "evaluation buffers");
+enum { kEvIpos, kEvAptr, kEvAidx, kEvNptr, kEvNidx, kEvDoff, kEvBack, kEvNear, kEvNdoff, kEvW, kEvXc, kEvYc,
+       kEvD, kEvDn };
+static_assert(kEvDn + 1 == hm_matrix::kEvBufs, "evaluation buffers");
+constexpr int kEvThreads = 256;
+constexpr int kEvWarps = kEvThreads / 32;
+
+__device__ __forceinline__ double ev_sum32(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// x gathered to cluster order, component-major (xs[a M + p]), so that a
+// warp reading 32 consecutive positions of one component is coalesced
+__global__ void ev_gather_kernel(const int32_t* __restrict__ perm, const double* __restrict__ x,
+                                 double* __restrict__ xs, int64_t M)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= M) return;
+    const int64_t o = 3 * (int64_t)perm[p];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) xs[a * M + p] = x[o + a];
+}
+
+// Butterfly sums of 2 or 4 values at once: at the first levels each half (or
+// quarter) of the warp keeps one value and sends the other, so that later
+// levels reduce all of them together.  Every value meets the same partners in
+// the same order as in ev_sum32 (the bits agree); the totals end in lane 0
+// (a), 16 (b), 8 (c) and 24 (d).
+__device__ __forceinline__ double ev_sum32x2(double a, double b, int lane)
+{
+    const bool h = lane & 16;
+    double k = h ? b : a;
+    k += __shfl_xor_sync(0xffffffffu, h ? a : b, 16);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+    return k;
+}
+
+__device__ __forceinline__ double ev_sum32x4(double a, double b, double c, double d, int lane)
+{
+    const bool h = lane & 16, g = lane & 8;
+    double k0 = h ? b : a, k1 = h ? d : c;
+    k0 += __shfl_xor_sync(0xffffffffu, h ? a : b, 16);
+    k1 += __shfl_xor_sync(0xffffffffu, h ? c : d, 16);
+    double k = g ? k1 : k0;
+    k += __shfl_xor_sync(0xffffffffu, g ? k0 : k1, 8);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+    return k;
+}
+
+// the sums of G crosses l .. l + G - 1 (G = 4, 2 or 1): V_l^T x_a for the
+// components a the kernel needs -- all three for V_Delta, p for V_pp, p and
+// q for V_pq (p != q) -- each lane-strided over the columns, then the
+// butterfly; the other slots of w are not written (nor read)
+template <bool A0, bool A1, bool A2, int G>
+__device__ __forceinline__ void ev_fwd_group(const double* __restrict__ v, int l, int n,
+                                             const double* __restrict__ x0, const double* __restrict__ x1,
+                                             const double* __restrict__ x2, double* __restrict__ wq, int lane)
+{
+    const double* vl = v + (int64_t)l * n;
+    double acc[3][G];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int g = 0; g < G; ++g) acc[c][g] = 0.0;
+#pragma unroll 2
+    for (int j = lane; j < n; j += 32) {
+        double vg[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) vg[g] = vl[(int64_t)g * n + j];
+        if (A0) {
+            const double x = x0[j];
+#pragma unroll
+            for (int g = 0; g < G; ++g) acc[0][g] += vg[g] * x;
+        }
+        if (A1) {
+            const double x = x1[j];
+#pragma unroll
+            for (int g = 0; g < G; ++g) acc[1][g] += vg[g] * x;
+        }
+        if (A2) {
+            const double x = x2[j];
+#pragma unroll
+            for (int g = 0; g < G; ++g) acc[2][g] += vg[g] * x;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if ((c == 0 && !A0) || (c == 1 && !A1) || (c == 2 && !A2)) continue;
+        double* wc = wq + 3 * l + c;
+        if (G == 4) {
+            const double t = ev_sum32x4(acc[c][0], acc[c][G > 1 ? 1 : 0], acc[c][G > 2 ? 2 : 0],
+                                        acc[c][G > 3 ? 3 : 0], lane);
+            if (lane == 0) wc[0] = t;
+            if (lane == 16) wc[3] = t;
+            if (lane == 8) wc[6] = t;
+            if (lane == 24) wc[9] = t;
+        } else if (G == 2) {
+            const double t = ev_sum32x2(acc[c][0], acc[c][G > 1 ? 1 : 0], lane);
+            if (lane == 0) wc[0] = t;
+            if (lane == 16) wc[3] = t;
+        } else {
+            const double t = ev_sum32(acc[c][0]);
+            if (lane == 0) wc[0] = t;
+        }
+    }
+}
+
+template <bool A0, bool A1, bool A2>
+__device__ __forceinline__ void ev_fwd_task(const double* __restrict__ v, int r, int n,
+                                            const double* __restrict__ x0, const double* __restrict__ x1,
+                                            const double* __restrict__ x2, double* __restrict__ wq, int lane)
+{
+    int l = 0;
+    for (; l + 4 <= r; l += 4) ev_fwd_group<A0, A1, A2, 4>(v, l, n, x0, x1, x2, wq, lane);
+    if (l + 2 <= r) {
+        ev_fwd_group<A0, A1, A2, 2>(v, l, n, x0, x1, x2, wq, lane);
+        l += 2;
+    }
+    if (l < r) ev_fwd_group<A0, A1, A2, 1>(v, l, n, x0, x1, x2, wq, lane);
+}
+
+__global__ void __launch_bounds__(kEvThreads) ev_fwd_kernel(const Blk* __restrict__ adm,
+                                                            const int32_t* __restrict__ rank,
+                                                            const int64_t* __restrict__ voff,
+                                                            const int64_t* __restrict__ coff,
+                                                            const double* __restrict__ V64,
+                                                            const double* __restrict__ xs, int64_t M,
+                                                            int64_t ntask, double* __restrict__ w)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarp = (int64_t)gridDim.x * kEvWarps;
+    for (int64_t q = (int64_t)blockIdx.x * kEvWarps + (threadIdx.x >> 5); q < ntask; q += nwarp) {
+        const int r = rank[q];
+        if (r == 0) continue;
+        const Blk b = adm[q / 7];
+        const double* v = V64 + voff[q];
+        const double* x0 = xs + b.s0;
+        const double* x1 = x0 + M;
+        const double* x2 = x1 + M;
+        double* wq = w + 3 * coff[q];
+        switch ((int)(q % 7)) {  // V_Delta, V_11, V_12, V_13, V_22, V_23, V_33
+            case 0: ev_fwd_task<true, true, true>(v, r, b.n, x0, x1, x2, wq, lane); break;
+            case 1: ev_fwd_task<true, false, false>(v, r, b.n, x0, x1, x2, wq, lane); break;
+            case 2: ev_fwd_task<true, true, false>(v, r, b.n, x0, x1, x2, wq, lane); break;
+            case 3: ev_fwd_task<true, false, true>(v, r, b.n, x0, x1, x2, wq, lane); break;
+            case 4: ev_fwd_task<false, true, false>(v, r, b.n, x0, x1, x2, wq, lane); break;
+            case 5: ev_fwd_task<false, true, true>(v, r, b.n, x0, x1, x2, wq, lane); break;
+            default: ev_fwd_task<false, false, true>(v, r, b.n, x0, x1, x2, wq, lane); break;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kEvThreads) ev_back_kernel(const int2* __restrict__ items, int64_t nitems,
+                                                             const Blk* __restrict__ adm,
+                                                             const int32_t* __restrict__ rank,
+                                                             const int64_t* __restrict__ uoff,
+                                                             const int64_t* __restrict__ coff,
+                                                             const double* __restrict__ U64,
+                                                             const double* __restrict__ w, double c1, double c2,
+                                                             const int64_t* __restrict__ doff, double* __restrict__ D)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarp = (int64_t)gridDim.x * kEvWarps;
+    for (int64_t it = (int64_t)blockIdx.x * kEvWarps + (threadIdx.x >> 5); it < nitems; it += nwarp) {
+        const int2 item = items[it];
+        const Blk bk = adm[item.x];
+        const int i = item.y * 32 + lane;
+        if (i >= bk.m) continue;
+        double y[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            const int64_t q = (int64_t)item.x * 7 + k;
+            const int r = rank[q];
+            const double* u = U64 + uoff[q] + i;
+            const double* wq = w + 3 * coff[q];
+            // the components this kernel uses (the slots ev_fwd wrote)
+            const bool u0 = k <= 3, u1 = k == 0 || k == 2 || k == 4 || k == 5, u2 = k == 0 || k == 3 || k >= 5;
+            double s[3] = {0.0, 0.0, 0.0};
+#pragma unroll 4
+            for (int l = 0; l < r; ++l) {
+                const double ul = u[(int64_t)l * bk.m];
+                if (u0) s[0] += ul * wq[3 * l];
+                if (u1) s[1] += ul * wq[3 * l + 1];
+                if (u2) s[2] += ul * wq[3 * l + 2];
+            }
+            if (k == 0) {
+                y[0] += c1 * s[0];
+                y[1] += c1 * s[1];
+                y[2] += c1 * s[2];
+            } else {
+                const int p = k <= 3 ? 0 : (k <= 5 ? 1 : 2);
+                const int qq = k <= 3 ? k - 1 : (k <= 5 ? k - 3 : 2);
+                y[p] += c2 * s[qq];
+                if (p != qq) y[qq] += c2 * s[p];
+            }
+        }
+        double* out = D + doff[item.x] + 3 * (int64_t)i;
+        out[0] = y[0];
+        out[1] = y[1];
+        out[2] = y[2];
+    }
+}
+
+__global__ void __launch_bounds__(kEvThreads) ev_near_kernel(const int2* __restrict__ items, int64_t nitems,
+                                                             const Blk* __restrict__ near,
+                                                             const int64_t* __restrict__ noff,
+                                                             const double* __restrict__ N64,
+                                                             const double* __restrict__ xs, int64_t M, double c1,
+                                                             double c2, const int64_t* __restrict__ ndoff,
+                                                             double* __restrict__ Dn)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarp = (int64_t)gridDim.x * kEvWarps;
+    for (int64_t it = (int64_t)blockIdx.x * kEvWarps + (threadIdx.x >> 5); it < nitems; it += nwarp) {
+        const int2 item = items[it];
+        const Blk bk = near[item.x];
+        const int i = item.y * 32 + lane;
+        if (i >= bk.m) continue;
+        const int64_t pairs = (int64_t)bk.m * bk.n;
+        const double* Nb = N64 + noff[item.x];
+        // y_a = c1 sum_j V_Delta x_a + c2 sum_j sum_b V_ab x_b: the two sums
+        // apart, c1 and c2 applied once per row (14 FP64 operations a pair)
+        double d0 = 0.0, d1 = 0.0, d2 = 0.0, s0 = 0.0, s1 = 0.0, s2 = 0.0;
+        const double* x0 = xs + bk.s0;
+#pragma unroll 4
+        for (int j = 0; j < bk.n; ++j) {
+            const double xa = x0[j], xb = x0[M + j], xc = x0[2 * M + j];
+            const int64_t e = (int64_t)j * bk.m + i;
+            const double v11 = Nb[e], v12 = Nb[pairs + e], v13 = Nb[2 * pairs + e];
+            const double v22 = Nb[3 * pairs + e], v23 = Nb[4 * pairs + e], v33 = Nb[5 * pairs + e];
+            const double vd = v11 + v22 + v33;
+            d0 += vd * xa;
+            d1 += vd * xb;
+            d2 += vd * xc;
+            s0 += v11 * xa;
+            s0 += v12 * xb;
+            s0 += v13 * xc;
+            s1 += v12 * xa;
+            s1 += v22 * xb;
+            s1 += v23 * xc;
+            s2 += v13 * xa;
+            s2 += v23 * xb;
+            s2 += v33 * xc;
+        }
+        double* out = Dn + ndoff[item.x] + 3 * (int64_t)i;
+        out[0] = c1 * d0 + c2 * s0;
+        out[1] = c1 * d1 + c2 * s1;
+        out[2] = c1 * d2 + c2 * s2;
+    }
+}
+
+__global__ void ev_rowsum_kernel(const int32_t* __restrict__ ipos, const int32_t* __restrict__ aptr,
+                                 const int32_t* __restrict__ aidx, const Blk* __restrict__ adm,
+                                 const int64_t* __restrict__ doff, const double* __restrict__ D,
+                                 const int32_t* __restrict__ nptr, const int32_t* __restrict__ nidx,
+                                 const Blk* __restrict__ near, const int64_t* __restrict__ ndoff,
+                                 const double* __restrict__ Dn, double* __restrict__ out, int64_t Mr)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= Mr) return;
+    const int I = ipos[p];
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int q = aptr[I]; q < aptr[I + 1]; ++q) {
+        const int b = aidx[q];
+        const double* d = D + doff[b] + 3 * (p - adm[b].t0);
+        s0 += d[0];
+        s1 += d[1];
+        s2 += d[2];
+    }
+    for (int q = nptr[I]; q < nptr[I + 1]; ++q) {
+        const int b = nidx[q];
+        const double* d = Dn + ndoff[b] + 3 * (p - near[b].t0);
+        s0 += d[0];
+        s1 += d[1];
+        s2 += d[2];
+    }
+    out[3 * p] = s0;
+    out[3 * p + 1] = s1;
+    out[3 * p + 2] = s2;
+}
 
 template <class T>
 int ev_put(hm_matrix& H, int which, const std::vector<T>& h, size_t n)
@@ -768,7 +1061,7 @@ int ev_put(hm_matrix& H, int which, const std::vector<T>& h, size_t n)
 
 int eval_prepare(hm_matrix& H)
 {
-    const int64_t M = H.M, Mr = H.Mr, nb = H.nadm;
+    const int64_t M = H.M, Mr = H.Mr, nb = H.nadm, nn = H.nnear;
     std::vector<int64_t> bounds = {0, Mr};
     for (const auto* L : {&H.adm_h, &H.near_h})
         for (const Blk& b : *L) {
@@ -778,27 +1071,37 @@ int eval_prepare(hm_matrix& H)
     std::sort(bounds.begin(), bounds.end());
     bounds.erase(std::unique(bounds.begin(), bounds.end()), bounds.end());
     const RowLists ra = row_lists(Mr, bounds, H.adm_h), rn = row_lists(Mr, bounds, H.near_h);
-    std::vector<int64_t> doff((size_t)nb + 1, 0);
-    for (int64_t b = 0; b < nb; ++b) doff[(size_t)b + 1] = doff[(size_t)b] + 3 * (int64_t)H.adm_h[(size_t)b].m;
-    std::vector<AmvmItem> items((size_t)nb);
-    int32_t maxrank = 0;
-    for (int64_t b = 0; b < nb; ++b) items[(size_t)b] = AmvmItem{(int32_t)b, 0, INT32_MAX, 0};
-    std::vector<const double*> uptr((size_t)nb * 7, nullptr), vptr((size_t)nb * 7, nullptr);
-    for (int64_t q = 0; q < nb * 7; ++q) {
-        uptr[(size_t)q] = H.U64.as<double>() + H.uoff_h[(size_t)q];
-        vptr[(size_t)q] = H.V64.as<double>() + H.voff_h[(size_t)q];
-        maxrank = std::max(maxrank, H.rank_h[(size_t)q]);
+    // parts: 3 values per row of every admissible block (doff) and of every
+    // near block (ndoff); work items (block, 32-row chunk)
+    std::vector<int64_t> doff((size_t)nb + 1, 0), ndoff((size_t)nn + 1, 0);
+    std::vector<int2> back, nearit;
+    for (int64_t b = 0; b < nb; ++b) {
+        const Blk& bk = H.adm_h[(size_t)b];
+        doff[(size_t)b + 1] = doff[(size_t)b] + 3 * (int64_t)bk.m;
+        for (int c = 0; 32 * c < bk.m; ++c) back.push_back(int2{(int)b, c});
     }
+    for (int64_t b = 0; b < nn; ++b) {
+        const Blk& bk = H.near_h[(size_t)b];
+        ndoff[(size_t)b + 1] = ndoff[(size_t)b] + 3 * (int64_t)bk.m;
+        for (int c = 0; 32 * c < bk.m; ++c) nearit.push_back(int2{(int)b, c});
+    }
+    int dev = 0, nsm = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     H.ev_parts = doff[(size_t)nb];
-    H.ev_maxrank = maxrank;
+    H.ev_nback = (int64_t)back.size();
+    H.ev_nnear = (int64_t)nearit.size();
+    H.ev_grid = std::max(1, nsm) * 8;  // 8 CTAs of 256 threads per SM
     int rc;
     const std::vector<double> none;
     if ((rc = ev_put(H, kEvIpos, ra.ipos, ra.ipos.size())) || (rc = ev_put(H, kEvAptr, ra.ptr, ra.ptr.size())) ||
         (rc = ev_put(H, kEvAidx, ra.idx, ra.idx.size())) || (rc = ev_put(H, kEvNptr, rn.ptr, rn.ptr.size())) ||
         (rc = ev_put(H, kEvNidx, rn.idx, rn.idx.size())) || (rc = ev_put(H, kEvDoff, doff, doff.size())) ||
-        (rc = ev_put(H, kEvItems, items, items.size())) || (rc = ev_put(H, kEvUptr, uptr, uptr.size())) ||
-        (rc = ev_put(H, kEvVptr, vptr, vptr.size())) || (rc = ev_put(H, kEvXc, none, (size_t)(3 * M))) ||
-        (rc = ev_put(H, kEvYc, none, (size_t)(3 * Mr))) || (rc = ev_put(H, kEvD, none, (size_t)doff[(size_t)nb])))
+        (rc = ev_put(H, kEvBack, back, back.size())) || (rc = ev_put(H, kEvNear, nearit, nearit.size())) ||
+        (rc = ev_put(H, kEvNdoff, ndoff, ndoff.size())) ||
+        (rc = ev_put(H, kEvW, none, (size_t)(3 * std::max<int64_t>(H.c_total, 1)))) ||
+        (rc = ev_put(H, kEvXc, none, (size_t)(3 * M))) || (rc = ev_put(H, kEvYc, none, (size_t)(3 * Mr))) ||
+        (rc = ev_put(H, kEvD, none, (size_t)doff[(size_t)nb])) || (rc = ev_put(H, kEvDn, none, (size_t)ndoff[(size_t)nn])))
         return rc;
     return HM_OK;
 }
@@ -818,25 +1121,37 @@ extern "C" int hm_eval_points(const hm_matrix* H, const double* t, double* u, in
     const DevBuf* ev = H->ev;
     double* xc = ev[kEvXc].as<double>();
     double* yc = ev[kEvYc].as<double>();
+    double* w = ev[kEvW].as<double>();
     const unsigned gM = (unsigned)((Mr + 255) / 256), gMc = (unsigned)((M + 255) / 256);
+    auto grid = [&](int64_t warps) {
+        return (unsigned)std::max<int64_t>(1, std::min<int64_t>(H->ev_grid, (warps + kEvWarps - 1) / kEvWarps));
+    };
     for (int32_t r = 0; r < nrhs; ++r) {
-        amvm_gather_kernel<<<gMc, 256, 0, s>>>(H->d_perm.as<int32_t>(), t + (int64_t)r * 3 * M, xc, M);
-        HM_CUDA(cudaGetLastError());
-        amvm_near_kernel<<<gM, 256, 0, s>>>(ev[kEvIpos].as<int32_t>(), ev[kEvNptr].as<int32_t>(),
-                                           ev[kEvNidx].as<int32_t>(), H->d_near.as<Blk>(), H->d_noff.as<int64_t>(),
-                                           H->N64.as<double>(), xc, c1, c2, yc, Mr);
+        ev_gather_kernel<<<gMc, 256, 0, s>>>(H->d_perm.as<int32_t>(), t + (int64_t)r * 3 * M, xc, M);
         HM_CUDA(cudaGetLastError());
         if (nb > 0) {
-            amvm_part_kernel<<<(unsigned)nb, kAmvmThreads, 0, s>>>(
-                ev[kEvItems].as<AmvmItem>(), H->d_adm.as<Blk>(), H->d_rank.as<int32_t>(),
-                ev[kEvUptr].as<const double*>(), ev[kEvVptr].as<const double*>(), xc, c1, c2,
+            ev_fwd_kernel<<<grid(nb * 7), kEvThreads, 0, s>>>(H->d_adm.as<Blk>(), H->d_rank.as<int32_t>(),
+                                                              H->d_voff.as<int64_t>(), H->d_coff.as<int64_t>(),
+                                                              H->V64.as<double>(), xc, M, nb * 7, w);
+            HM_CUDA(cudaGetLastError());
+            ev_back_kernel<<<grid(H->ev_nback), kEvThreads, 0, s>>>(
+                ev[kEvBack].as<int2>(), H->ev_nback, H->d_adm.as<Blk>(), H->d_rank.as<int32_t>(),
+                H->d_uoff.as<int64_t>(), H->d_coff.as<int64_t>(), H->U64.as<double>(), w, c1, c2,
                 ev[kEvDoff].as<int64_t>(), ev[kEvD].as<double>());
             HM_CUDA(cudaGetLastError());
-            amvm_rowsum_kernel<<<gM, 256, 0, s>>>(ev[kEvIpos].as<int32_t>(), ev[kEvAptr].as<int32_t>(),
-                                                 ev[kEvAidx].as<int32_t>(), H->d_adm.as<Blk>(),
-                                                 ev[kEvDoff].as<int64_t>(), ev[kEvD].as<double>(), nullptr, 1, yc, Mr);
+        }
+        if (H->ev_nnear > 0) {
+            ev_near_kernel<<<grid(H->ev_nnear), kEvThreads, 0, s>>>(
+                ev[kEvNear].as<int2>(), H->ev_nnear, H->d_near.as<Blk>(), H->d_noff.as<int64_t>(),
+                H->N64.as<double>(), xc, M, c1, c2, ev[kEvNdoff].as<int64_t>(), ev[kEvDn].as<double>());
             HM_CUDA(cudaGetLastError());
         }
+        ev_rowsum_kernel<<<gM, 256, 0, s>>>(ev[kEvIpos].as<int32_t>(), ev[kEvAptr].as<int32_t>(),
+                                           ev[kEvAidx].as<int32_t>(), H->d_adm.as<Blk>(), ev[kEvDoff].as<int64_t>(),
+                                           ev[kEvD].as<double>(), ev[kEvNptr].as<int32_t>(),
+                                           ev[kEvNidx].as<int32_t>(), H->d_near.as<Blk>(),
+                                           ev[kEvNdoff].as<int64_t>(), ev[kEvDn].as<double>(), yc, Mr);
+        HM_CUDA(cudaGetLastError());
         amvm_scatter_kernel<<<gM, 256, 0, s>>>(H->d_rperm.as<int32_t>(), yc, u + (int64_t)r * 3 * Mr, Mr);
         HM_CUDA(cudaGetLastError());
     }

@@ -1676,6 +1676,7 @@ int assemble_points_device(const hm_tree& tr, hm_matrix& H)
     if ((rc = dalloc(H, H.V64, (size_t)std::max<int64_t>(vt, 1) * 8))) return rc;
     if ((rc = upload(H, H.d_uoff, H.uoff_h.data(), (size_t)nbk * 8))) return rc;
     if ((rc = upload(H, H.d_voff, H.voff_h.data(), (size_t)nbk * 8))) return rc;
+    if ((rc = upload(H, H.d_coff, H.coff_h.data(), (size_t)nbk * 8))) return rc;
     if ((rc = upload(H, H.d_rank, H.rank_h.data(), (size_t)nbk * 4))) return rc;
     if (!bk.empty()) {
         std::vector<AcaTask> tasks(bk.size());

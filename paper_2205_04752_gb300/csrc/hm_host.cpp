@@ -410,6 +410,7 @@ int hm_get_stats(const hm_matrix* H, hm_stats* st)
         for (int k = 0; k < 7; ++k) {
             int32_t r = H->rank_h[(size_t)(b * 7 + k)];
             st->far_entries += (int64_t)r * (bk.m + bk.n);
+            st->far_entries_kern[k] += (int64_t)r * (bk.m + bk.n);
             st->far_u_entries += (int64_t)r * bk.m;
             st->far_v_entries += (int64_t)r * bk.n;
             st->rank_sum[k] += r;

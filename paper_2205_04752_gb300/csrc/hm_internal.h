@@ -287,10 +287,11 @@ struct hm_matrix {
     hm::DevBuf g_rows;   // evaluation operator: Mr x 3 points in cluster order
     // evaluation operator: tables and workspace of its exact product
     // (hm_amvm.cu; index names there)
-    static constexpr int kEvBufs = 12;
+    static constexpr int kEvBufs = 14;
     hm::DevBuf ev[kEvBufs];
-    int64_t ev_parts = 0;   // 3 sum |t| over the admissible blocks
-    int32_t ev_maxrank = 0;
+    int64_t ev_parts = 0;              // 3 sum |t| over the admissible blocks
+    int64_t ev_nback = 0, ev_nnear = 0;  // work items (block, 32 rows) of the far and near passes
+    int32_t ev_grid = 0;               // CTAs of the warp-per-item passes
     // rows of an entry: the collocation points, or the points of ~V_h
     const int32_t* row_perm() const { return rect ? d_rperm.as<int32_t>() : d_perm.as<int32_t>(); }
 
