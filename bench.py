@@ -511,8 +511,19 @@ def bench_points(args, tree, w, x, timed, eval_only=False):
           "hbm_frac": round(gbs / peak, 4), "steps": steps,
           "roofline": {"bound": "alu", "achieved": round(tf, 4), "peak": fp64_peak, "unit": "TFLOP/s",
                        "frac": round(tf / fp64_peak, 4), "flops": int(flops), "peak_from": fp64_src}}
+    # the FP32 form: the same passes on FP32 copies, bound by HBM
+    Hp.pack("fp32")
+    u32 = torch.empty_like(u)
+    ms32 = timed(lambda: binding.eval_points(Hp, t, u32, "fp32"), steps, 2) / steps
+    alg32 = (st.far_entries + 6 * st.near_pairs) * 4 + 2 * 3 * rows_far * 4 + 2 * 3 * M * 8 + 2 * 3 * npts * 8
+    gbs32 = alg32 / (ms32 * 1e-3) / 1e9
+    ev32 = {"ms": round(ms32, 3), "evals_per_s": round(1e3 / ms32, 2),
+            "rel_err_vs_fp64_form": float(torch.linalg.norm(u32 - u) / torch.linalg.norm(u)),
+            "roofline": {"bound": "hbm", "achieved": round(gbs32, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(gbs32 / peak, 4), "alg_bytes": int(alg32), "peak_kind": peak_kind}}
     if eval_only:
-        return {"points": npts, "nadm": st.nadm, "nnear": st.nnear, "assemble_s": round(t_asm, 3), "eval": ev}
+        return {"points": npts, "nadm": st.nadm, "nnear": st.nnear, "assemble_s": round(t_asm, 3), "eval": ev,
+                "eval_fp32": ev32}
     ya = torch.empty_like(u)
     binding.amvm(Hp, t, ya, theta=0.7, eps=1e-4)  # warm-up
     torch.cuda.synchronize()
@@ -539,6 +550,7 @@ def bench_points(args, tree, w, x, timed, eval_only=False):
             "nnear": st.nnear, "tree_s": round(t_tree, 3), "assemble_s": round(t_asm, 3),
             "rank_mean": [round(r / max(st.nadm, 1), 2) for r in st.rank_sum],
             "eval": ev,
+            "eval_fp32": ev32,
             "amvm": {"theta": 0.7, "eps": 1e-4, "ms": round(amvm_ms, 1), "iterations": ai["iterations"],
                      "crosses_used_fraction": round(ai["crosses_used"] / max(ai["crosses_full"], 1), 4),
                      "rel_err_vs_exact_product": err,

@@ -116,8 +116,9 @@ void hm_tree_destroy(hm_tree* tree);
  *   out      new tree: hm_tree_sizes / hm_tree_export describe the point tree
  *            (perm over the points, nodes) and the partition (row node of the
  *            point tree, column node of the surface tree)
- * hm_aca_assemble on this tree assembles ~V_h (FP64 factors and near field,
- * no packed forms); apply it with hm_eval_points, or adaptively with hm_amvm.
+ * hm_aca_assemble on this tree assembles ~V_h (FP64 factors and near field;
+ * hm_pack(H, HM_FP32) adds FP32 copies, the only other form); apply it with
+ * hm_eval_points, or adaptively with hm_amvm.
  * Errors: HM_EINVAL (NULL argument, `surface` itself a point tree, npts < 1,
  * leaf outside 1..HM_MAX_LEAF, non-finite coordinate), HM_ENOMEM.
  * ------------------------------------------------------------------------- */
@@ -130,15 +131,19 @@ int hm_build_point_tree(const hm_tree* surface, const double* pts, int64_t npts,
  *   t      device, nrhs rows of 3M float64 (dof 3j + b, original triangle order)
  *   u      device, nrhs rows of 3 npts float64 (3i + a, original point
  *          order), overwritten; t and u must not overlap
- * The exact FP64 product of the assembled H-matrix: every admissible block
- * applies all its crosses, every near block its entries, and each output
- * element is summed in a fixed order (repeated calls agree bitwise).
+ *   form   HM_FP64: the exact product of the assembled H-matrix in FP64;
+ *          HM_FP32 (after hm_pack(H, HM_FP32)): the same product from FP32
+ *          copies of the factors and near field with FP32 arithmetic
+ * Every admissible block applies all its crosses, every near block its
+ * entries, and each output element is summed in a fixed order (repeated
+ * calls agree bitwise).
  * Asynchronous on `stream`; allocates nothing (its workspace was reserved at
  * assembly); calls on the same operator must not overlap on the device.
  * Errors: HM_EINVAL (NULL argument, not an evaluation operator, assembled
- * with HM_DEFER_ACA, nrhs < 1), HM_EDEVICE.
+ * with HM_DEFER_ACA, nrhs < 1, a form other than HM_FP64 or a packed
+ * HM_FP32), HM_EDEVICE.
  * ------------------------------------------------------------------------- */
-int hm_eval_points(const hm_matrix* H, const double* t, double* u, int32_t nrhs, void* stream);
+int hm_eval_points(const hm_matrix* H, const double* t, double* u, int32_t nrhs, int32_t form, void* stream);
 
 /* Assembly parameters. */
 typedef struct {

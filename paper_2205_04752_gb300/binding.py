@@ -136,7 +136,7 @@ def load():
         "hm_tree_export": (ctypes.c_int, [P, P, P, P, P]),
         "hm_tree_destroy": (None, [P]),
         "hm_build_point_tree": (ctypes.c_int, [P, P, I64, I32, ctypes.POINTER(P)]),
-        "hm_eval_points": (ctypes.c_int, [P, P, P, I32, P]),
+        "hm_eval_points": (ctypes.c_int, [P, P, P, I32, I32, P]),
         "hm_aca_assemble": (ctypes.c_int, [P, ctypes.POINTER(_Params), ctypes.POINTER(_Allocator),
                                            P, ctypes.POINTER(P)]),
         "hm_set_material": (ctypes.c_int, [P, D, D]),
@@ -474,11 +474,13 @@ def amvm(H: HMatrix, x, y, theta: float = 0.7, eps: float = 1e-6, r0: int = 2, l
                 marked_total=int(info.marked_total), block_ranks=ranks[:H.stats().nadm].copy())
 
 
-def eval_points(H: HMatrix, t, u, stream=None):
+def eval_points(H: HMatrix, t, u, form="fp64", stream=None):
     """``hm_eval_points``: u = ~V_h t, the displacement at the points of an
     evaluation operator (an ``HMatrix`` assembled from a ``PointTree``) for
     densities t.  t: CUDA float64 (3M,) or (nrhs, 3M); u: (3 npts,) or
-    (nrhs, 3 npts); both contiguous."""
+    (nrhs, 3 npts); both contiguous.  ``form``: "fp64" (exact) or "fp32"
+    (after ``H.pack("fp32")``)."""
+    f = FORMS[form] if isinstance(form, str) else int(form)
     import torch
     if not (t.is_cuda and u.is_cuda and t.dtype == torch.float64 and u.dtype == torch.float64):
         raise TypeError("eval_points: t and u must be CUDA float64 tensors")
@@ -486,7 +488,7 @@ def eval_points(H: HMatrix, t, u, stream=None):
     if (t.shape[-1] != 3 * H.M or u.shape[-1] != 3 * H.Mr or (u.dim() == 2) != (t.dim() == 2)
             or (t.dim() == 2 and u.shape[0] != nrhs) or not t.is_contiguous() or not u.is_contiguous()):
         raise ValueError("eval_points: t must be contiguous rows of 3M, u rows of 3 npts")
-    _check(load().hm_eval_points(H._h, ctypes.c_void_p(t.data_ptr()), ctypes.c_void_p(u.data_ptr()), nrhs,
+    _check(load().hm_eval_points(H._h, ctypes.c_void_p(t.data_ptr()), ctypes.c_void_p(u.data_ptr()), nrhs, f,
                                  _stream_handle(stream)))
     return u
 

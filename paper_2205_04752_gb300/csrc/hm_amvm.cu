@@ -746,9 +746,11 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
 }
 
 // ------------------------------------------------------------------------
-// The evaluation operator ~V_h (Section 5, Eq. (vector_eq)): its exact FP64
-// product -- every admissible block with all its crosses, the near field
-// exact, per row position a fixed summation order -- in four passes, each
+// The evaluation operator ~V_h (Section 5, Eq. (vector_eq)): its product --
+// every admissible block with all its crosses, the near field exact, per row
+// position a fixed summation order -- in FP64 (the exact form) or, after
+// hm_pack(HM_FP32), from FP32 copies of the same block-ordered arenas with
+// FP32 arithmetic (T = double or float below), in four passes, each
 // spread over warps so that the factor and near-field streams are read with
 // many loads in flight:
 //   ev_fwd   one warp per (block, kernel): w_c = V_c^T x(s) for its crosses c
@@ -767,7 +769,8 @@ static_assert(kEvDn + 1 == hm_matrix::kEvBufs, "evaluation buffers");
 constexpr int kEvThreads = 256;
 constexpr int kEvWarps = kEvThreads / 32;
 
-__device__ __forceinline__ double ev_sum32(double v)
+template <class T>
+__device__ __forceinline__ T ev_sum32(T v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -776,14 +779,33 @@ __device__ __forceinline__ double ev_sum32(double v)
 
 // x gathered to cluster order, component-major (xs[a M + p]), so that a
 // warp reading 32 consecutive positions of one component is coalesced
+template <class T>
 __global__ void ev_gather_kernel(const int32_t* __restrict__ perm, const double* __restrict__ x,
-                                 double* __restrict__ xs, int64_t M)
+                                 T* __restrict__ xs, int64_t M)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= M) return;
     const int64_t o = 3 * (int64_t)perm[p];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) xs[a * M + p] = x[o + a];
+    for (int a = 0; a < 3; ++a) xs[a * M + p] = (T)x[o + a];
+}
+
+template <class T>
+__global__ void ev_scatter_kernel(const int32_t* __restrict__ perm, const T* __restrict__ yc,
+                                  double* __restrict__ y, int64_t M)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= M) return;
+    const int64_t o = 3 * (int64_t)perm[p];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) y[o + a] = (double)yc[3 * p + a];
+}
+
+// the FP32 form: element-wise copies of the block-ordered FP64 arenas
+__global__ void ev_to_fp32_kernel(const double* __restrict__ src, float* __restrict__ dst, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
 }
 
 // Butterfly sums of 2 or 4 values at once: at the first levels each half (or
@@ -791,23 +813,25 @@ __global__ void ev_gather_kernel(const int32_t* __restrict__ perm, const double*
 // levels reduce all of them together.  Every value meets the same partners in
 // the same order as in ev_sum32 (the bits agree); the totals end in lane 0
 // (a), 16 (b), 8 (c) and 24 (d).
-__device__ __forceinline__ double ev_sum32x2(double a, double b, int lane)
+template <class T>
+__device__ __forceinline__ T ev_sum32x2(T a, T b, int lane)
 {
     const bool h = lane & 16;
-    double k = h ? b : a;
+    T k = h ? b : a;
     k += __shfl_xor_sync(0xffffffffu, h ? a : b, 16);
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
     return k;
 }
 
-__device__ __forceinline__ double ev_sum32x4(double a, double b, double c, double d, int lane)
+template <class T>
+__device__ __forceinline__ T ev_sum32x4(T a, T b, T c, T d, int lane)
 {
     const bool h = lane & 16, g = lane & 8;
-    double k0 = h ? b : a, k1 = h ? d : c;
+    T k0 = h ? b : a, k1 = h ? d : c;
     k0 += __shfl_xor_sync(0xffffffffu, h ? a : b, 16);
     k1 += __shfl_xor_sync(0xffffffffu, h ? c : d, 16);
-    double k = g ? k1 : k0;
+    T k = g ? k1 : k0;
     k += __shfl_xor_sync(0xffffffffu, g ? k0 : k1, 8);
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
@@ -818,34 +842,34 @@ __device__ __forceinline__ double ev_sum32x4(double a, double b, double c, doubl
 // components a the kernel needs -- all three for V_Delta, p for V_pp, p and
 // q for V_pq (p != q) -- each lane-strided over the columns, then the
 // butterfly; the other slots of w are not written (nor read)
-template <bool A0, bool A1, bool A2, int G>
-__device__ __forceinline__ void ev_fwd_group(const double* __restrict__ v, int l, int n,
-                                             const double* __restrict__ x0, const double* __restrict__ x1,
-                                             const double* __restrict__ x2, double* __restrict__ wq, int lane)
+template <class T, bool A0, bool A1, bool A2, int G>
+__device__ __forceinline__ void ev_fwd_group(const T* __restrict__ v, int l, int n, const T* __restrict__ x0,
+                                             const T* __restrict__ x1, const T* __restrict__ x2,
+                                             T* __restrict__ wq, int lane)
 {
-    const double* vl = v + (int64_t)l * n;
-    double acc[3][G];
+    const T* vl = v + (int64_t)l * n;
+    T acc[3][G];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int g = 0; g < G; ++g) acc[c][g] = 0.0;
+        for (int g = 0; g < G; ++g) acc[c][g] = T(0);
 #pragma unroll 2
     for (int j = lane; j < n; j += 32) {
-        double vg[G];
+        T vg[G];
 #pragma unroll
         for (int g = 0; g < G; ++g) vg[g] = vl[(int64_t)g * n + j];
         if (A0) {
-            const double x = x0[j];
+            const T x = x0[j];
 #pragma unroll
             for (int g = 0; g < G; ++g) acc[0][g] += vg[g] * x;
         }
         if (A1) {
-            const double x = x1[j];
+            const T x = x1[j];
 #pragma unroll
             for (int g = 0; g < G; ++g) acc[1][g] += vg[g] * x;
         }
         if (A2) {
-            const double x = x2[j];
+            const T x = x2[j];
 #pragma unroll
             for (int g = 0; g < G; ++g) acc[2][g] += vg[g] * x;
         }
@@ -853,46 +877,46 @@ __device__ __forceinline__ void ev_fwd_group(const double* __restrict__ v, int l
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         if ((c == 0 && !A0) || (c == 1 && !A1) || (c == 2 && !A2)) continue;
-        double* wc = wq + 3 * l + c;
+        T* wc = wq + 3 * l + c;
         if (G == 4) {
-            const double t = ev_sum32x4(acc[c][0], acc[c][G > 1 ? 1 : 0], acc[c][G > 2 ? 2 : 0],
+            const T t = ev_sum32x4<T>(acc[c][0], acc[c][G > 1 ? 1 : 0], acc[c][G > 2 ? 2 : 0],
                                         acc[c][G > 3 ? 3 : 0], lane);
             if (lane == 0) wc[0] = t;
             if (lane == 16) wc[3] = t;
             if (lane == 8) wc[6] = t;
             if (lane == 24) wc[9] = t;
         } else if (G == 2) {
-            const double t = ev_sum32x2(acc[c][0], acc[c][G > 1 ? 1 : 0], lane);
+            const T t = ev_sum32x2<T>(acc[c][0], acc[c][G > 1 ? 1 : 0], lane);
             if (lane == 0) wc[0] = t;
             if (lane == 16) wc[3] = t;
         } else {
-            const double t = ev_sum32(acc[c][0]);
+            const T t = ev_sum32<T>(acc[c][0]);
             if (lane == 0) wc[0] = t;
         }
     }
 }
 
-template <bool A0, bool A1, bool A2>
-__device__ __forceinline__ void ev_fwd_task(const double* __restrict__ v, int r, int n,
-                                            const double* __restrict__ x0, const double* __restrict__ x1,
-                                            const double* __restrict__ x2, double* __restrict__ wq, int lane)
+template <class T, bool A0, bool A1, bool A2>
+__device__ __forceinline__ void ev_fwd_task(const T* __restrict__ v, int r, int n, const T* __restrict__ x0,
+                                            const T* __restrict__ x1, const T* __restrict__ x2,
+                                            T* __restrict__ wq, int lane)
 {
     int l = 0;
-    for (; l + 4 <= r; l += 4) ev_fwd_group<A0, A1, A2, 4>(v, l, n, x0, x1, x2, wq, lane);
+    for (; l + 4 <= r; l += 4) ev_fwd_group<T, A0, A1, A2, 4>(v, l, n, x0, x1, x2, wq, lane);
     if (l + 2 <= r) {
-        ev_fwd_group<A0, A1, A2, 2>(v, l, n, x0, x1, x2, wq, lane);
+        ev_fwd_group<T, A0, A1, A2, 2>(v, l, n, x0, x1, x2, wq, lane);
         l += 2;
     }
-    if (l < r) ev_fwd_group<A0, A1, A2, 1>(v, l, n, x0, x1, x2, wq, lane);
+    if (l < r) ev_fwd_group<T, A0, A1, A2, 1>(v, l, n, x0, x1, x2, wq, lane);
 }
 
+template <class T>
 __global__ void __launch_bounds__(kEvThreads) ev_fwd_kernel(const Blk* __restrict__ adm,
                                                             const int32_t* __restrict__ rank,
                                                             const int64_t* __restrict__ voff,
                                                             const int64_t* __restrict__ coff,
-                                                            const double* __restrict__ V64,
-                                                            const double* __restrict__ xs, int64_t M,
-                                                            int64_t ntask, double* __restrict__ w)
+                                                            const T* __restrict__ Vf, const T* __restrict__ xs,
+                                                            int64_t M, int64_t ntask, T* __restrict__ w)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarp = (int64_t)gridDim.x * kEvWarps;
@@ -900,31 +924,32 @@ __global__ void __launch_bounds__(kEvThreads) ev_fwd_kernel(const Blk* __restric
         const int r = rank[q];
         if (r == 0) continue;
         const Blk b = adm[q / 7];
-        const double* v = V64 + voff[q];
-        const double* x0 = xs + b.s0;
-        const double* x1 = x0 + M;
-        const double* x2 = x1 + M;
-        double* wq = w + 3 * coff[q];
+        const T* v = Vf + voff[q];
+        const T* x0 = xs + b.s0;
+        const T* x1 = x0 + M;
+        const T* x2 = x1 + M;
+        T* wq = w + 3 * coff[q];
         switch ((int)(q % 7)) {  // V_Delta, V_11, V_12, V_13, V_22, V_23, V_33
-            case 0: ev_fwd_task<true, true, true>(v, r, b.n, x0, x1, x2, wq, lane); break;
-            case 1: ev_fwd_task<true, false, false>(v, r, b.n, x0, x1, x2, wq, lane); break;
-            case 2: ev_fwd_task<true, true, false>(v, r, b.n, x0, x1, x2, wq, lane); break;
-            case 3: ev_fwd_task<true, false, true>(v, r, b.n, x0, x1, x2, wq, lane); break;
-            case 4: ev_fwd_task<false, true, false>(v, r, b.n, x0, x1, x2, wq, lane); break;
-            case 5: ev_fwd_task<false, true, true>(v, r, b.n, x0, x1, x2, wq, lane); break;
-            default: ev_fwd_task<false, false, true>(v, r, b.n, x0, x1, x2, wq, lane); break;
+            case 0: ev_fwd_task<T, true, true, true>(v, r, b.n, x0, x1, x2, wq, lane); break;
+            case 1: ev_fwd_task<T, true, false, false>(v, r, b.n, x0, x1, x2, wq, lane); break;
+            case 2: ev_fwd_task<T, true, true, false>(v, r, b.n, x0, x1, x2, wq, lane); break;
+            case 3: ev_fwd_task<T, true, false, true>(v, r, b.n, x0, x1, x2, wq, lane); break;
+            case 4: ev_fwd_task<T, false, true, false>(v, r, b.n, x0, x1, x2, wq, lane); break;
+            case 5: ev_fwd_task<T, false, true, true>(v, r, b.n, x0, x1, x2, wq, lane); break;
+            default: ev_fwd_task<T, false, false, true>(v, r, b.n, x0, x1, x2, wq, lane); break;
         }
     }
 }
 
+template <class T>
 __global__ void __launch_bounds__(kEvThreads) ev_back_kernel(const int2* __restrict__ items, int64_t nitems,
                                                              const Blk* __restrict__ adm,
                                                              const int32_t* __restrict__ rank,
                                                              const int64_t* __restrict__ uoff,
                                                              const int64_t* __restrict__ coff,
-                                                             const double* __restrict__ U64,
-                                                             const double* __restrict__ w, double c1, double c2,
-                                                             const int64_t* __restrict__ doff, double* __restrict__ D)
+                                                             const T* __restrict__ Uf, const T* __restrict__ w,
+                                                             T c1, T c2, const int64_t* __restrict__ doff,
+                                                             T* __restrict__ D)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarp = (int64_t)gridDim.x * kEvWarps;
@@ -933,22 +958,33 @@ __global__ void __launch_bounds__(kEvThreads) ev_back_kernel(const int2* __restr
         const Blk bk = adm[item.x];
         const int i = item.y * 32 + lane;
         if (i >= bk.m) continue;
-        double y[3] = {0.0, 0.0, 0.0};
+        T y[3] = {T(0), T(0), T(0)};
 #pragma unroll
         for (int k = 0; k < 7; ++k) {
             const int64_t q = (int64_t)item.x * 7 + k;
             const int r = rank[q];
-            const double* u = U64 + uoff[q] + i;
-            const double* wq = w + 3 * coff[q];
+            const T* u = Uf + uoff[q] + i;
+            const T* wq = w + 3 * coff[q];
             // the components this kernel uses (the slots ev_fwd wrote)
             const bool u0 = k <= 3, u1 = k == 0 || k == 2 || k == 4 || k == 5, u2 = k == 0 || k == 3 || k >= 5;
-            double s[3] = {0.0, 0.0, 0.0};
+            T s[3] = {T(0), T(0), T(0)};
+            // loads in flight: eight crosses deep in FP64, four in FP32 (measured best)
+            if (sizeof(T) == 8) {
+#pragma unroll 8
+                for (int l = 0; l < r; ++l) {
+                    const T ul = u[(int64_t)l * bk.m];
+                    if (u0) s[0] += ul * wq[3 * l];
+                    if (u1) s[1] += ul * wq[3 * l + 1];
+                    if (u2) s[2] += ul * wq[3 * l + 2];
+                }
+            } else {
 #pragma unroll 4
-            for (int l = 0; l < r; ++l) {
-                const double ul = u[(int64_t)l * bk.m];
-                if (u0) s[0] += ul * wq[3 * l];
-                if (u1) s[1] += ul * wq[3 * l + 1];
-                if (u2) s[2] += ul * wq[3 * l + 2];
+                for (int l = 0; l < r; ++l) {
+                    const T ul = u[(int64_t)l * bk.m];
+                    if (u0) s[0] += ul * wq[3 * l];
+                    if (u1) s[1] += ul * wq[3 * l + 1];
+                    if (u2) s[2] += ul * wq[3 * l + 2];
+                }
             }
             if (k == 0) {
                 y[0] += c1 * s[0];
@@ -961,20 +997,20 @@ __global__ void __launch_bounds__(kEvThreads) ev_back_kernel(const int2* __restr
                 if (p != qq) y[qq] += c2 * s[p];
             }
         }
-        double* out = D + doff[item.x] + 3 * (int64_t)i;
+        T* out = D + doff[item.x] + 3 * (int64_t)i;
         out[0] = y[0];
         out[1] = y[1];
         out[2] = y[2];
     }
 }
 
+template <class T>
 __global__ void __launch_bounds__(kEvThreads) ev_near_kernel(const int2* __restrict__ items, int64_t nitems,
                                                              const Blk* __restrict__ near,
                                                              const int64_t* __restrict__ noff,
-                                                             const double* __restrict__ N64,
-                                                             const double* __restrict__ xs, int64_t M, double c1,
-                                                             double c2, const int64_t* __restrict__ ndoff,
-                                                             double* __restrict__ Dn)
+                                                             const T* __restrict__ Nf, const T* __restrict__ xs,
+                                                             int64_t M, T c1, T c2,
+                                                             const int64_t* __restrict__ ndoff, T* __restrict__ Dn)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarp = (int64_t)gridDim.x * kEvWarps;
@@ -984,18 +1020,18 @@ __global__ void __launch_bounds__(kEvThreads) ev_near_kernel(const int2* __restr
         const int i = item.y * 32 + lane;
         if (i >= bk.m) continue;
         const int64_t pairs = (int64_t)bk.m * bk.n;
-        const double* Nb = N64 + noff[item.x];
+        const T* Nb = Nf + noff[item.x];
         // y_a = c1 sum_j V_Delta x_a + c2 sum_j sum_b V_ab x_b: the two sums
-        // apart, c1 and c2 applied once per row (14 FP64 operations a pair)
-        double d0 = 0.0, d1 = 0.0, d2 = 0.0, s0 = 0.0, s1 = 0.0, s2 = 0.0;
-        const double* x0 = xs + bk.s0;
+        // apart, c1 and c2 applied once per row (14 operations a pair)
+        T d0 = T(0), d1 = T(0), d2 = T(0), s0 = T(0), s1 = T(0), s2 = T(0);
+        const T* x0 = xs + bk.s0;
 #pragma unroll 4
         for (int j = 0; j < bk.n; ++j) {
-            const double xa = x0[j], xb = x0[M + j], xc = x0[2 * M + j];
+            const T xa = x0[j], xb = x0[M + j], xc = x0[2 * M + j];
             const int64_t e = (int64_t)j * bk.m + i;
-            const double v11 = Nb[e], v12 = Nb[pairs + e], v13 = Nb[2 * pairs + e];
-            const double v22 = Nb[3 * pairs + e], v23 = Nb[4 * pairs + e], v33 = Nb[5 * pairs + e];
-            const double vd = v11 + v22 + v33;
+            const T v11 = Nb[e], v12 = Nb[pairs + e], v13 = Nb[2 * pairs + e];
+            const T v22 = Nb[3 * pairs + e], v23 = Nb[4 * pairs + e], v33 = Nb[5 * pairs + e];
+            const T vd = v11 + v22 + v33;
             d0 += vd * xa;
             d1 += vd * xb;
             d2 += vd * xc;
@@ -1009,34 +1045,35 @@ __global__ void __launch_bounds__(kEvThreads) ev_near_kernel(const int2* __restr
             s2 += v23 * xb;
             s2 += v33 * xc;
         }
-        double* out = Dn + ndoff[item.x] + 3 * (int64_t)i;
+        T* out = Dn + ndoff[item.x] + 3 * (int64_t)i;
         out[0] = c1 * d0 + c2 * s0;
         out[1] = c1 * d1 + c2 * s1;
         out[2] = c1 * d2 + c2 * s2;
     }
 }
 
+template <class T>
 __global__ void ev_rowsum_kernel(const int32_t* __restrict__ ipos, const int32_t* __restrict__ aptr,
                                  const int32_t* __restrict__ aidx, const Blk* __restrict__ adm,
-                                 const int64_t* __restrict__ doff, const double* __restrict__ D,
+                                 const int64_t* __restrict__ doff, const T* __restrict__ D,
                                  const int32_t* __restrict__ nptr, const int32_t* __restrict__ nidx,
                                  const Blk* __restrict__ near, const int64_t* __restrict__ ndoff,
-                                 const double* __restrict__ Dn, double* __restrict__ out, int64_t Mr)
+                                 const T* __restrict__ Dn, T* __restrict__ out, int64_t Mr)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= Mr) return;
     const int I = ipos[p];
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    T s0 = T(0), s1 = T(0), s2 = T(0);
     for (int q = aptr[I]; q < aptr[I + 1]; ++q) {
         const int b = aidx[q];
-        const double* d = D + doff[b] + 3 * (p - adm[b].t0);
+        const T* d = D + doff[b] + 3 * (p - adm[b].t0);
         s0 += d[0];
         s1 += d[1];
         s2 += d[2];
     }
     for (int q = nptr[I]; q < nptr[I + 1]; ++q) {
         const int b = nidx[q];
-        const double* d = Dn + ndoff[b] + 3 * (p - near[b].t0);
+        const T* d = Dn + ndoff[b] + 3 * (p - near[b].t0);
         s0 += d[0];
         s1 += d[1];
         s2 += d[2];
@@ -1105,9 +1142,81 @@ int eval_prepare(hm_matrix& H)
         return rc;
     return HM_OK;
 }
+int eval_pack_fp32(hm_matrix& H, cudaStream_t s)
+{
+    // FP32 copies of the block-ordered arenas, same offsets: factors U, V and
+    // the near field (the FP32 form of the evaluation operator)
+    struct Pair {
+        const DevBuf* src;
+        DevBuf* dst;
+        int64_t n;
+    } pairs[3] = {{&H.U64, &H.Ul[HM_FP32], H.u_total}, {&H.V64, &H.Vr[HM_FP32], H.v_total},
+                  {&H.N64, &H.Nl32, H.n_total}};
+    for (Pair& pr : pairs) {
+        pr.dst->bytes = (size_t)std::max<int64_t>(pr.n, 1) * sizeof(float);
+        pr.dst->p = H.alloc.alloc(pr.dst->bytes);
+        if (!pr.dst->p) return fail(HM_ENOMEM, "hm_pack: FP32 evaluation arenas (%zu bytes)", pr.dst->bytes);
+        if (pr.n > 0) {
+            ev_to_fp32_kernel<<<(unsigned)std::min<int64_t>((pr.n + 255) / 256, 4096), 256, 0, s>>>(
+                pr.src->as<double>(), pr.dst->as<float>(), pr.n);
+            HM_CUDA(cudaGetLastError());
+        }
+    }
+    return HM_OK;
+}
+
+namespace {
+template <class T>
+int eval_run(const hm_matrix& H, const double* t, double* u, int32_t nrhs, const T* Uf, const T* Vf, const T* Nf,
+             cudaStream_t s)
+{
+    const int64_t M = H.M, Mr = H.Mr, nb = H.nadm;
+    const T c1 = (T)((1.0 + H.nu) * (3.0 - 4.0 * H.nu) / (2.0 * H.E * (1.0 - H.nu)));
+    const T c2 = (T)((1.0 + H.nu) / (2.0 * H.E * (1.0 - H.nu)));
+    const DevBuf* ev = H.ev;
+    T* xc = ev[kEvXc].as<T>();
+    T* yc = ev[kEvYc].as<T>();
+    T* w = ev[kEvW].as<T>();
+    T* D = ev[kEvD].as<T>();
+    T* Dn = ev[kEvDn].as<T>();
+    const unsigned gM = (unsigned)((Mr + 255) / 256), gMc = (unsigned)((M + 255) / 256);
+    auto grid = [&](int64_t warps) {
+        return (unsigned)std::max<int64_t>(1, std::min<int64_t>(H.ev_grid, (warps + kEvWarps - 1) / kEvWarps));
+    };
+    for (int32_t r = 0; r < nrhs; ++r) {
+        ev_gather_kernel<T><<<gMc, 256, 0, s>>>(H.d_perm.as<int32_t>(), t + (int64_t)r * 3 * M, xc, M);
+        HM_CUDA(cudaGetLastError());
+        if (nb > 0) {
+            ev_fwd_kernel<T><<<grid(nb * 7), kEvThreads, 0, s>>>(H.d_adm.as<Blk>(), H.d_rank.as<int32_t>(),
+                                                                 H.d_voff.as<int64_t>(), H.d_coff.as<int64_t>(), Vf,
+                                                                 xc, M, nb * 7, w);
+            HM_CUDA(cudaGetLastError());
+            ev_back_kernel<T><<<grid(H.ev_nback), kEvThreads, 0, s>>>(
+                ev[kEvBack].as<int2>(), H.ev_nback, H.d_adm.as<Blk>(), H.d_rank.as<int32_t>(), H.d_uoff.as<int64_t>(),
+                H.d_coff.as<int64_t>(), Uf, w, c1, c2, ev[kEvDoff].as<int64_t>(), D);
+            HM_CUDA(cudaGetLastError());
+        }
+        if (H.ev_nnear > 0) {
+            ev_near_kernel<T><<<grid(H.ev_nnear), kEvThreads, 0, s>>>(
+                ev[kEvNear].as<int2>(), H.ev_nnear, H.d_near.as<Blk>(), H.d_noff.as<int64_t>(), Nf, xc, M, c1, c2,
+                ev[kEvNdoff].as<int64_t>(), Dn);
+            HM_CUDA(cudaGetLastError());
+        }
+        ev_rowsum_kernel<T><<<gM, 256, 0, s>>>(ev[kEvIpos].as<int32_t>(), ev[kEvAptr].as<int32_t>(),
+                                              ev[kEvAidx].as<int32_t>(), H.d_adm.as<Blk>(), ev[kEvDoff].as<int64_t>(),
+                                              D, ev[kEvNptr].as<int32_t>(), ev[kEvNidx].as<int32_t>(),
+                                              H.d_near.as<Blk>(), ev[kEvNdoff].as<int64_t>(), Dn, yc, Mr);
+        HM_CUDA(cudaGetLastError());
+        ev_scatter_kernel<T><<<gM, 256, 0, s>>>(H.d_rperm.as<int32_t>(), yc, u + (int64_t)r * 3 * Mr, Mr);
+        HM_CUDA(cudaGetLastError());
+    }
+    return HM_OK;
+}
+}  // namespace
 }  // namespace hm
 
-extern "C" int hm_eval_points(const hm_matrix* H, const double* t, double* u, int32_t nrhs, void* stream)
+extern "C" int hm_eval_points(const hm_matrix* H, const double* t, double* u, int32_t nrhs, int32_t form,
+                              void* stream)
 {
     if (!H || !t || !u) return fail(HM_EINVAL, "hm_eval_points: NULL argument");
     if (!H->rect) return fail(HM_EINVAL, "hm_eval_points: not an evaluation operator (use hm_matvec)");
@@ -1115,45 +1224,12 @@ extern "C" int hm_eval_points(const hm_matrix* H, const double* t, double* u, in
         return fail(HM_EINVAL, "hm_eval_points: assembled with HM_DEFER_ACA (use hm_amvm with HM_AMVM_ACA_ON_DEMAND)");
     if (nrhs < 1) return fail(HM_EINVAL, "hm_eval_points: nrhs %d < 1", nrhs);
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t M = H->M, Mr = H->Mr, nb = H->nadm;
-    const double c1 = (1.0 + H->nu) * (3.0 - 4.0 * H->nu) / (2.0 * H->E * (1.0 - H->nu));
-    const double c2 = (1.0 + H->nu) / (2.0 * H->E * (1.0 - H->nu));
-    const DevBuf* ev = H->ev;
-    double* xc = ev[kEvXc].as<double>();
-    double* yc = ev[kEvYc].as<double>();
-    double* w = ev[kEvW].as<double>();
-    const unsigned gM = (unsigned)((Mr + 255) / 256), gMc = (unsigned)((M + 255) / 256);
-    auto grid = [&](int64_t warps) {
-        return (unsigned)std::max<int64_t>(1, std::min<int64_t>(H->ev_grid, (warps + kEvWarps - 1) / kEvWarps));
-    };
-    for (int32_t r = 0; r < nrhs; ++r) {
-        ev_gather_kernel<<<gMc, 256, 0, s>>>(H->d_perm.as<int32_t>(), t + (int64_t)r * 3 * M, xc, M);
-        HM_CUDA(cudaGetLastError());
-        if (nb > 0) {
-            ev_fwd_kernel<<<grid(nb * 7), kEvThreads, 0, s>>>(H->d_adm.as<Blk>(), H->d_rank.as<int32_t>(),
-                                                              H->d_voff.as<int64_t>(), H->d_coff.as<int64_t>(),
-                                                              H->V64.as<double>(), xc, M, nb * 7, w);
-            HM_CUDA(cudaGetLastError());
-            ev_back_kernel<<<grid(H->ev_nback), kEvThreads, 0, s>>>(
-                ev[kEvBack].as<int2>(), H->ev_nback, H->d_adm.as<Blk>(), H->d_rank.as<int32_t>(),
-                H->d_uoff.as<int64_t>(), H->d_coff.as<int64_t>(), H->U64.as<double>(), w, c1, c2,
-                ev[kEvDoff].as<int64_t>(), ev[kEvD].as<double>());
-            HM_CUDA(cudaGetLastError());
-        }
-        if (H->ev_nnear > 0) {
-            ev_near_kernel<<<grid(H->ev_nnear), kEvThreads, 0, s>>>(
-                ev[kEvNear].as<int2>(), H->ev_nnear, H->d_near.as<Blk>(), H->d_noff.as<int64_t>(),
-                H->N64.as<double>(), xc, M, c1, c2, ev[kEvNdoff].as<int64_t>(), ev[kEvDn].as<double>());
-            HM_CUDA(cudaGetLastError());
-        }
-        ev_rowsum_kernel<<<gM, 256, 0, s>>>(ev[kEvIpos].as<int32_t>(), ev[kEvAptr].as<int32_t>(),
-                                           ev[kEvAidx].as<int32_t>(), H->d_adm.as<Blk>(), ev[kEvDoff].as<int64_t>(),
-                                           ev[kEvD].as<double>(), ev[kEvNptr].as<int32_t>(),
-                                           ev[kEvNidx].as<int32_t>(), H->d_near.as<Blk>(),
-                                           ev[kEvNdoff].as<int64_t>(), ev[kEvDn].as<double>(), yc, Mr);
-        HM_CUDA(cudaGetLastError());
-        amvm_scatter_kernel<<<gM, 256, 0, s>>>(H->d_rperm.as<int32_t>(), yc, u + (int64_t)r * 3 * Mr, Mr);
-        HM_CUDA(cudaGetLastError());
+    if (form == HM_FP64)
+        return eval_run<double>(*H, t, u, nrhs, H->U64.as<double>(), H->V64.as<double>(), H->N64.as<double>(), s);
+    if (form == HM_FP32) {
+        if (!H->packed[HM_FP32]) return fail(HM_EINVAL, "hm_eval_points: FP32 form not packed (hm_pack)");
+        return eval_run<float>(*H, t, u, nrhs, H->Ul[HM_FP32].as<float>(), H->Vr[HM_FP32].as<float>(),
+                               H->Nl32.as<float>(), s);
     }
-    return HM_OK;
+    return fail(HM_EINVAL, "hm_eval_points: form %d (an evaluation operator has HM_FP64 and HM_FP32)", form);
 }

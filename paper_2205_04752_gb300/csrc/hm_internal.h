@@ -372,6 +372,9 @@ int aca_on_demand(hm_matrix& H, const std::vector<int32_t>& bk, int kmax, cudaSt
 // the evaluation operator (a matrix assembled from a point tree): tables and
 // workspace of its exact FP64 product (hm_amvm.cu), built once at assembly
 int eval_prepare(hm_matrix& H);
+// the FP32 form of an evaluation operator: FP32 copies of its block-ordered
+// U, V and near arenas (in Ul[HM_FP32], Vr[HM_FP32] and Nl32), same offsets
+int eval_pack_fp32(hm_matrix& H, cudaStream_t s);
 int matvec_device(const hm_matrix& H, const double* x, double* y, int32_t nrhs, int64_t ld,
                   int32_t form, cudaStream_t s);
 int pack_device(hm_matrix& H, int32_t form, cudaStream_t s);

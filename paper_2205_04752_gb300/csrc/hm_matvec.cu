@@ -1530,8 +1530,10 @@ extern "C" {
 int hm_pack(hm_matrix* H, int32_t form, void* stream)
 {
     if (!H) return fail(HM_EINVAL, "hm_pack: NULL matrix");
-    if (H->rect) return fail(HM_EINVAL, "hm_pack: an evaluation operator (hm_build_point_tree) has only hm_eval_points and hm_amvm");
     if (form < HM_FP64 || form > HM_FP16) return fail(HM_EINVAL, "hm_pack: unknown form %d", form);
+    if (H->rect && form != HM_FP64 && form != HM_FP32)
+        return fail(HM_EINVAL, "hm_pack: an evaluation operator has the forms HM_FP64 and HM_FP32");
+    if (H->rect && form == HM_FP64) return HM_OK;  // its FP64 arenas are the FP64 form
     if (H->packed[form]) return HM_OK;
     if (H->compacted) return fail(HM_EINVAL, "hm_pack: FP64 data released (hm_compact); pack before compacting");
     if (H->aca_deferred)
@@ -1543,7 +1545,7 @@ int hm_pack(hm_matrix* H, int32_t form, void* stream)
     HM_CUDA(cudaEventCreate(&e0));
     HM_CUDA(cudaEventCreate(&e1));
     cudaEventRecord(e0, s);
-    int rc = pack_device(*H, form, s);
+    int rc = H->rect ? eval_pack_fp32(*H, s) : pack_device(*H, form, s);
     cudaEventRecord(e1, s);
     H->alloc.stream = saved;
     if (rc == HM_OK) rc = cuda_check(cudaStreamSynchronize(s), "hm_pack");

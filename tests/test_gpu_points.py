@@ -43,10 +43,10 @@ class PCase:
         t, s = blocks[b]
         return int(self.nodes[t, 1] - self.nodes[t, 0]), int(self.snodes[s, 1] - self.snodes[s, 0])
 
-    def eval(self, x):
+    def eval(self, x, form="fp64"):
         td = torch.tensor(np.ascontiguousarray(np.atleast_2d(x)), device="cuda")
         ud = torch.full((td.shape[0], 3 * len(self.P)), np.nan, dtype=torch.float64, device="cuda")
-        binding.eval_points(self.H, td, ud)
+        binding.eval_points(self.H, td, ud, form)
         torch.cuda.synchronize()
         return ud.cpu().numpy()
 
@@ -110,6 +110,24 @@ def test_eval_points_matches_oracle_and_definition():
     assert np.array_equal(c.eval(x), u)
 
 
+def test_eval_points_fp32_form():
+    """The FP32 form (FP32 copies of the same factors and near field, FP32
+    arithmetic): refused before hm_pack(HM_FP32), then within 1e-5 of the
+    FP64 form, deterministic; the 16-bit forms do not exist for ~V_h."""
+    c = small()
+    x = inputs.uniform_rhs(3 * c.M, 6, nrhs=2)
+    with pytest.raises(binding.HMError):
+        c.eval(x, "fp32")
+    with pytest.raises(binding.HMError):
+        c.H.pack("bf16")
+    c.H.pack("fp32")
+    u32 = c.eval(x, "fp32")
+    u64 = c.eval(x)
+    for r in range(2):
+        assert _rel(u32[r], u64[r]) <= 1e-5, r
+    assert np.array_equal(c.eval(x, "fp32"), u32)
+
+
 def test_eval_points_with_more_than_32_crosses():
     """Blocks whose ACA sequences exceed one chunk of crosses (level 4, leaf
     64, eps 1e-12: ranks up to about 60) are applied chunk by chunk."""
@@ -119,6 +137,8 @@ def test_eval_points_with_more_than_32_crosses():
     u = c.eval(x)[0]
     uo = c.Ho.matvec(E, NU, x)[0]
     assert _rel(u, uo) <= 1e-12
+    c.H.pack("fp32")
+    assert _rel(c.eval(x, "fp32")[0], uo) <= 1e-5
 
 
 @pytest.mark.parametrize("npts,leaf_pts,r_in,r_out", [(1, 8, 0.0, 0.5), (333, 7, 0.0, 0.9),
@@ -214,3 +234,7 @@ def test_level6_points_sampled():
     idx = inputs.sample_rows(len(c.P), 48, 8)
     uo = oracle.points_matvec(c.V, c.T, E, NU, c.P[idx], x)[0].reshape(-1, 3)
     assert np.linalg.norm(u[idx] - uo) <= 1e-4 * np.linalg.norm(uo)
+    c.H.pack("fp32")
+    u32 = c.eval(x, "fp32")[0].reshape(-1, 3)
+    assert np.linalg.norm(u32[idx] - uo) <= 1e-4 * np.linalg.norm(uo)
+    assert np.linalg.norm(u32 - u) <= 1e-5 * np.linalg.norm(u)
