@@ -15,6 +15,10 @@ adds the pieces for which a library routine is the plain definition:
 * ``amvm`` -- Algorithm 2 (adaptive matrix-vector multiplication, Section 3)
   step by step on the oracle's own ACA factors, with the readings stated in
   its docstring (per-block products are ``numpy`` matrix products);
+* ``baca`` -- Algorithm 3 (Section 5) restricted to the single layer: the
+  solve interleaved with block refinement, on a dense A_k formed from the
+  oracle's factors, with a plain restarted GMRES (``numpy.linalg.lstsq`` for
+  its small least-squares problems);
 * the evaluation operator ~V_h of Section 5, Eq. (vector_eq) (the displacement at points of
   the domain): ``points_matvec`` by its definition, and ``HMatrix`` with
   ``points=`` (a tree of the points for the rows, the same ACA).
@@ -548,3 +552,183 @@ def amvm(Ho: "HMatrix", E: float, nu: float, x, theta: float = 0.7, eps: float =
     outh.reshape(Mr, 3)[rperm] = bhat
     return dict(b=out, b_hat=outh, ranks=np.minimum(r[:, None], full), full_ranks=full, csp=csp,
                 iterations=it, **hist)
+
+
+# --------------------------------------------------------------------------
+# Block-adaptive ACA for the single layer (Algorithm 3, branch (iii))
+# --------------------------------------------------------------------------
+
+def _dense_block(Ho: "HMatrix", F, rng, b: int, l0: int, l1: int, c1: float, c2: float) -> np.ndarray:
+    """The crosses l0 .. l1 - 1 of admissible block b as a dense (3|t|, 3|s|)
+    block of V_h, rows 3i + a and columns 3j + c in cluster order:
+    c1 U V^T on the diagonal components for V_Delta, c2 U V^T at (p, q) and
+    (q, p) for V_pq (Eq. (Vh))."""
+    lo_t, hi_t, lo_s, hi_s = rng[b]
+    m, n = hi_t - lo_t, hi_s - lo_s
+    out = np.zeros((3 * m, 3 * n))
+    for k in range(7):
+        U, Vv = F[b][k]
+        a, z = min(l0, U.shape[1]), min(l1, U.shape[1])
+        if a >= z:
+            continue
+        S = U[:, a:z] @ Vv[:, a:z].T
+        if k == 0:
+            for p in range(3):
+                out[p::3, p::3] += c1 * S
+        else:
+            p, q = _KPQ[k]
+            out[p::3, q::3] += c2 * S
+            if p != q:
+                out[q::3, p::3] += c2 * S
+    return out
+
+
+def _gmres(A, b, x, tol_of, restart: int, max_it: int, floor: float):
+    """Restarted GMRES(m) on the dense matrix A (plain: Arnoldi with
+    modified Gram-Schmidt, the small least-squares problem by
+    numpy.linalg.lstsq).  A cycle ends early when its residual estimate is
+    <= tol, tol = tol_of(x) at the cycle's start; after each cycle the solve
+    ends when ||b - A x|| <= tol_of(x) (or <= floor, or at max_it
+    iterations).  Returns (x, iterations)."""
+    its = 0
+    while True:
+        r = b - A @ x
+        beta = float(np.linalg.norm(r))
+        tol = tol_of(x)
+        if beta <= tol or beta <= floor or its >= max_it:
+            return x, its
+        Q = [r / beta]
+        Hh = np.zeros((restart + 1, restart))
+        j_end = 0
+        for j in range(restart):
+            w = A @ Q[j]
+            for i in range(j + 1):
+                Hh[i, j] = float(Q[i] @ w)
+                w = w - Hh[i, j] * Q[i]
+            Hh[j + 1, j] = float(np.linalg.norm(w))
+            its += 1
+            j_end = j + 1
+            e1 = np.zeros(j + 2)
+            e1[0] = beta
+            y, *_ = np.linalg.lstsq(Hh[:j + 2, :j + 1], e1, rcond=None)
+            est = float(np.linalg.norm(e1 - Hh[:j + 2, :j + 1] @ y))
+            if est <= tol or Hh[j + 1, j] <= 1e-300 or its >= max_it:
+                break
+            Q.append(w / Hh[j + 1, j])
+        x = x + np.stack(Q[:j_end], 1) @ y
+
+
+def baca(Ho: "HMatrix", E: float, nu: float, b, theta: float = 0.8, alpha: float = 10.0,
+         eps: float = 1e-4, r0: int = 8, look: int = 2, tol0: float = 0.1, restart: int = 50,
+         max_it: int = 100000, max_steps: int = 1000):
+    """Algorithm 3 of Section 5 restricted to the single layer (branch (iii)):
+    solve V_h t = b while the H-matrix approximation is refined block by
+    block, FP64, on the oracle's own ACA factors.
+
+    Readings (the paper leaves these open; it runs Bramble-Pasciak CG on the
+    saddle system):
+    * A_k keeps the first r_b crosses of each of the seven ACA sequences of
+      block b (A_0: r_b = r0); the look-ahead A^_k has r_b + look; near blocks
+      exact in both.  A block of P_adm is a block t x s of V_h (all seven
+      kernels); refining it sets A_{k+1} = A^_k on it.
+    * Step 2 is restarted GMRES(m) from x_{k-1} (x_{-1} = 0): a cycle ends
+      early when its residual estimate falls to tau = alpha ||(A_k - A^_k) x||
+      at the cycle's start (tau = tol0 ||b|| while x = 0); after each cycle the
+      solve ends when ||b - A_k x|| <= alpha ||(A_k - A^_k) x|| (Eq. (solvCond))
+      or the residual is below 1e-13 ||b||.
+    * E_k^2 = sum_b ||(A_k - A^_k)_b x_k||^2; step 3 marks the fewest blocks
+      with E_k(M_k) >= theta E_k: blocks in decreasing ||(A_k - A^_k)_b x_k||
+      (ties: lower block index first) until the condition holds.
+    * The loop stops when E_k <= eps ||b|| (a relative epsilon) after a
+      solve, returning x_k, or when no block can be refined.
+
+    Returns a dict: x (original order), E (per step), iterations (GMRES per
+    step), marked (per step), ranks (r_b at the end, capped by the sequences),
+    steps, and per step the final residual ||b - A_k x_k||, ||(A_k - A^_k)
+    x_k||, the squared block parts and the marked blocks."""
+    b = _f64(b).reshape(-1)
+    M = Ho.M
+    N = 3 * M
+    c1, c2 = lame_coefficients(E, nu)
+    perm = Ho.perm
+    rng = Ho.ranges(Ho.adm)
+    nrng = Ho.ranges(Ho.near) if Ho.nnear else np.zeros((0, 4), dtype=np.int64)
+    nb = Ho.nadm
+    F = [[Ho.factors(bb, k) for k in range(7)] for bb in range(nb)]
+    full = np.array([[F[bb][k][0].shape[1] for k in range(7)] for bb in range(nb)], dtype=np.int64)
+    # cluster order, component fastest: row 3p + a
+    bc = b.reshape(M, 3)[perm].reshape(-1)
+    A0 = np.zeros((N, N))
+    for q in range(Ho.nnear):
+        lo_t, hi_t, lo_s, hi_s = nrng[q]
+        Nb = Ho.near_block(q)
+        blk = np.zeros((3 * (hi_t - lo_t), 3 * (hi_s - lo_s)))
+        for p in range(3):
+            blk[p::3, p::3] += c1 * Nb[0]
+        for k in range(1, 7):
+            p, qq = _KPQ[k]
+            blk[p::3, qq::3] += c2 * Nb[k]
+            if p != qq:
+                blk[qq::3, p::3] += c2 * Nb[k]
+        A0[3 * lo_t:3 * hi_t, 3 * lo_s:3 * hi_s] += blk
+    r = np.full(nb, int(r0), dtype=np.int64)
+    Ak = A0.copy()
+    for bb in range(nb):
+        lo_t, hi_t, lo_s, hi_s = rng[bb]
+        Ak[3 * lo_t:3 * hi_t, 3 * lo_s:3 * hi_s] += _dense_block(Ho, F, rng, bb, 0, r0, c1, c2)
+    look_blk = [_dense_block(Ho, F, rng, bb, r0, r0 + look, c1, c2) for bb in range(nb)]
+
+    def parts(x):
+        """(A^_k - A_k)_b x for every block, and their sum."""
+        P = []
+        e = np.zeros(N)
+        for bb in range(nb):
+            lo_t, hi_t, lo_s, hi_s = rng[bb]
+            d = look_blk[bb] @ x[3 * lo_s:3 * hi_s]
+            P.append(d)
+            e[3 * lo_t:3 * hi_t] += d
+        return P, e
+
+    bnorm = float(np.linalg.norm(bc))
+    x = np.zeros(N)
+    hist = dict(E=[], iterations=[], marked=[], residual=[], lookahead=[], parts=[], marked_sets=[])
+    k = 0
+    while True:
+        def tol_of(xx):
+            if not np.any(xx):
+                return tol0 * bnorm
+            return alpha * float(np.linalg.norm(parts(xx)[1]))
+        x, its = _gmres(Ak, bc, x, tol_of, restart, max_it, 1e-13 * bnorm)
+        hist["iterations"].append(its)
+        P, e = parts(x)
+        hist["residual"].append(float(np.linalg.norm(bc - Ak @ x)))
+        hist["lookahead"].append(float(np.linalg.norm(e)))
+        bn2 = np.array([float(d @ d) for d in P])
+        hist["parts"].append(bn2)
+        Ek = float(np.sqrt(bn2.sum()))
+        hist["E"].append(Ek)
+        if Ek <= eps * bnorm or k >= max_steps:
+            break
+        order = np.lexsort((np.arange(nb), -bn2))
+        acc, marked = 0.0, []
+        target = (theta * Ek) ** 2
+        for bb in order:
+            if acc >= target:
+                break
+            if bn2[bb] == 0.0:
+                break
+            marked.append(int(bb))
+            acc += bn2[bb]
+        hist["marked"].append(len(marked))
+        hist["marked_sets"].append(marked)
+        if not marked:
+            break
+        for bb in marked:
+            lo_t, hi_t, lo_s, hi_s = rng[bb]
+            Ak[3 * lo_t:3 * hi_t, 3 * lo_s:3 * hi_s] += look_blk[bb]
+            r[bb] += look
+            look_blk[bb] = _dense_block(Ho, F, rng, bb, r[bb], r[bb] + look, c1, c2)
+        k += 1
+    out = np.zeros(N)
+    out.reshape(M, 3)[perm] = x.reshape(M, 3)
+    return dict(x=out, ranks=np.minimum(r[:, None], full), full_ranks=full, steps=k, **hist)
