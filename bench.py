@@ -16,10 +16,11 @@ products over 64 ellipsoid meshes with 1 and 16 right-hand sides), "solve"
 (GMRES with FP64-residual refinement to 1e-8 on a 196,608-triangle cube),
 "serving" (the request loop over 16 resident meshes at swept Poisson rates,
 p50 / p99 latency), "amvm" (Algorithm 2 on the level-6 matrix, FP64, theta
-0.7, eps 1e-4) and "points" (the evaluation operator of Section 5, Eq.
+0.7, eps 1e-4), "points" (the evaluation operator of Section 5, Eq.
 (vector_eq): the displacement at 65,536 points inside the level-6 sphere,
-its exact FP64 product and Algorithm 2 on it); --no-batch / --no-solve /
---no-serve / --no-amvm / --no-points skip them.
+its exact FP64 product and Algorithm 2 on it) and "baca" (Algorithm 3 on the
+single layer: the level-6 solve with block-adaptive refinement); --no-batch /
+--no-solve / --no-serve / --no-amvm / --no-points / --no-baca skip them.
 
 Under torchrun (N > 1) every rank runs its own replica (the product shards
 into independent problems; no collective on the data path): weak scaling,
@@ -401,6 +402,31 @@ def run_ours(args):
             "rel_err_vs_fp64_product": float(torch.linalg.norm(ya - y64) / torch.linalg.norm(y64))}
         del Hd
 
+    # ---- context: block-adaptive ACA solve of the single layer (Algorithm 3,
+    # the paper's parameters theta 0.8, alpha 10, eps 1e-4, 8 starting ACA steps)
+    baca_ctx = None
+    if not args.no_baca:
+        g = np.tile([1.0, 0.0, 0.0], M) + inputs.uniform_rhs(3 * M, 2)[0]
+        gd = torch.tensor(g, device="cuda")
+        td = torch.empty_like(gd)
+        yv = torch.empty_like(gd)
+        baca_ctx = {"rhs": "(1,0,0) + U[-1,1] per dof (seed 2)", "theta": 0.8, "alpha": 10.0, "eps": 1e-4,
+                    "look": 2}
+        for r0 in (8, 2):  # the paper's starting rank, and a coarse start that the refinement must lift
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            bi = binding.baca(H, gd, td, theta=0.8, alpha=10.0, eps=1e-4, r0=r0, look=2)
+            torch.cuda.synchronize()
+            t_baca = time.perf_counter() - t0
+            binding.hmatvec(H, td, yv, "fp64")
+            torch.cuda.synchronize()
+            baca_ctx[f"r0_{r0}"] = {
+                "s": round(t_baca, 3), "steps": bi["steps"], "gmres_iterations": bi["gmres_iterations"],
+                "marked_total": bi["marked_total"],
+                "crosses_used_fraction": round(bi["crosses_used"] / max(bi["crosses_full"], 1), 4),
+                "E_over_b": bi["E"] / max(bi["b_norm"], 1e-300), "rel_residual_A_k": bi["rel_residual"],
+                "rel_residual_full_fp64": float(torch.linalg.norm(gd - yv) / torch.linalg.norm(gd))}
+
     points_ctx = None
     if not args.no_points and rank == 0 and ws == 1:
         try:
@@ -422,6 +448,7 @@ def run_ours(args):
             "nrhs32": {"ms_per_call": round(ms32, 4), "vectors_per_s": round(32e3 / ms32, 2)},
             "amvm": amvm_ctx,
             "points": points_ctx,
+            "baca": baca_ctx,
             "assembly": {"tree_s": round(t_tree, 3), "assemble_s": round(t_asm, 3),
                          "near_ms": round(st.assemble_ms[0], 1),
                          "aca_ms": round(st.assemble_ms[1], 1),
@@ -735,6 +762,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the request-loop measurement")
     ap.add_argument("--no-solve", action="store_true", help="skip the 196,608-triangle cube solve")
     ap.add_argument("--no-amvm", action="store_true", help="skip the adaptive matrix-vector multiplication")
+    ap.add_argument("--no-baca", action="store_true",
+                    help="skip the block-adaptive ACA solve (Algorithm 3 on the single layer)")
     ap.add_argument("--no-points", action="store_true",
                     help="skip the evaluation operator (displacement at 65,536 interior points)")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[10.0, 30.0, 100.0])

@@ -465,6 +465,73 @@ typedef struct {
 int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_amvm_params* p, hm_amvm_info* info,
             double* gamma_hist, double* gamma_rest_hist, int32_t hist_cap, int32_t* block_ranks, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Block-adaptive ACA for the single layer (Section 5, Algorithm 3 with only
+ * the V blocks, branch (iii)), FP64: solves V_h t = b while the H-matrix
+ * approximation A_k is refined block by block.
+ *
+ * A_k keeps, on each admissible block, the first r_b crosses of all seven ACA
+ * sequences (A_0: r_b = r0; a shorter sequence is used whole); the look-ahead
+ * A^_k has r_b + look; near blocks are exact in both.  Each step k:
+ *   2. restarted GMRES(restart) on A_k t = b from the previous t (0 at
+ *      first): a cycle ends early when its residual estimate reaches
+ *      tau = alpha ||(A_k - A^_k) t|| at the cycle's start (tau = tol0 ||b||
+ *      while t = 0); the solve ends when ||b - A_k t|| <= alpha ||(A_k - A^_k)
+ *      t|| (Eq. (solvCond)) or below 1e-13 ||b|| (or after max_iter GMRES
+ *      iterations in all);
+ *   3. E_k^2 = sum_b ||(A_k - A^_k)_b t||^2; if E_k <= eps ||b|| stop;
+ *      otherwise mark the fewest blocks with E_k(M_k) >= theta E_k (the
+ *      largest parts first, ties by block index) and set A_{k+1} = A^_k on
+ *      them (r_b += look).
+ *   b, t     device, 3M doubles each, original dof order; t is overwritten
+ *   info     optional: steps, GMRES iterations, final E, ||b - A_k t|| / ||b||,
+ *            ||b||, crosses used by A_k and held by the assembled ACA, blocks
+ *            marked in all
+ *   hist     optional host array of hist_cap steps (E_k, ||b - A_k t||,
+ *            ||(A_k - A^_k) t||, GMRES iterations, blocks marked)
+ *   block_ranks  optional host array of nadm ints: r_b at exit
+ * Needs the assembled FP64 factors and near field (not HM_DEFER_ACA, not
+ * after hm_compact); not for an evaluation operator.  Allocates
+ * (restart + 6) 3M doubles and about 24 sum|t| bytes of workspace through
+ * the matrix's allocator for the call (and, at the first call, the product
+ * tables it keeps); synchronises `stream`.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    double theta;      /* Doerfler parameter in (0, 1) (0 = 0.8) */
+    double alpha;      /* solve accuracy factor of Eq. (solvCond), > 0 (0 = 10) */
+    double eps;        /* stop when E_k <= eps ||b|| (>= 0) */
+    double tol0;       /* first solve: relative residual tol0 (0 = 0.1) */
+    int32_t r0;        /* crosses per block and kernel in A_0 (0 = 8) */
+    int32_t look;      /* look-ahead ACA steps, 1..32 (0 = 2) */
+    int32_t restart;   /* GMRES restart length, 1..200 (0 = 50) */
+    int32_t max_iter;  /* GMRES iterations in all (0 = 100000) */
+    int32_t max_steps; /* refinement steps (0 = 1000) */
+    int32_t flags;     /* 0 */
+} hm_baca_params;
+
+typedef struct {
+    int32_t steps;             /* refinement steps taken */
+    int32_t pad;
+    int64_t gmres_iterations;  /* in all */
+    double E;                  /* E_k at exit */
+    double rel_residual;       /* ||b - A_k t|| / ||b|| at exit */
+    double b_norm;
+    int64_t crosses_used;      /* sum over block-kernels of the crosses in A_k */
+    int64_t crosses_full;      /* the same for the assembled ACA */
+    int64_t marked_total;      /* blocks marked over all steps */
+} hm_baca_info;
+
+typedef struct {
+    double E;           /* E_k after the solve of step k */
+    double residual;    /* ||b - A_k t_k|| */
+    double lookahead;   /* ||(A_k - A^_k) t_k|| */
+    int32_t iterations; /* GMRES iterations of the step */
+    int32_t marked;     /* blocks refined after it */
+} hm_baca_step;
+
+int hm_baca(const hm_matrix* H, const double* b, double* t, const hm_baca_params* p, hm_baca_info* info,
+            hm_baca_step* hist, int32_t hist_cap, int32_t* block_ranks, void* stream);
+
 /* Status of the asynchronous products of H: HM_ETIMEOUT if a bounded device
  * wait inside an earlier hm_matvec ran out (its result is then invalid; the
  * flag is cleared), HM_OK otherwise.  Synchronises the device. */

@@ -32,7 +32,7 @@ SYMBOLS = (
     "hm_solve", "hm_batch_create", "hm_batch_layout", "hm_batch_matvec", "hm_batch_autotune",
     "hm_batch_set_schedule", "hm_batch_get_schedule", "hm_batch_check", "hm_batch_destroy",
     "hm_compact", "hm_footprint", "hm_server_create", "hm_server_footprint", "hm_server_run",
-    "hm_server_destroy", "hm_amvm", "hm_build_point_tree", "hm_eval_points",
+    "hm_server_destroy", "hm_amvm", "hm_build_point_tree", "hm_eval_points", "hm_baca",
 )
 
 
@@ -78,6 +78,25 @@ class _AmvmInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("csp", ctypes.c_int32), ("gamma", ctypes.c_double),
                 ("bhat_norm", ctypes.c_double), ("crosses_used", ctypes.c_int64),
                 ("crosses_full", ctypes.c_int64), ("marked_total", ctypes.c_int64)]
+
+
+class _BacaParams(ctypes.Structure):
+    _fields_ = [("theta", ctypes.c_double), ("alpha", ctypes.c_double), ("eps", ctypes.c_double),
+                ("tol0", ctypes.c_double), ("r0", ctypes.c_int32), ("look", ctypes.c_int32),
+                ("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("max_steps", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
+
+
+class _BacaInfo(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int32), ("pad", ctypes.c_int32), ("gmres_iterations", ctypes.c_int64),
+                ("E", ctypes.c_double), ("rel_residual", ctypes.c_double), ("b_norm", ctypes.c_double),
+                ("crosses_used", ctypes.c_int64), ("crosses_full", ctypes.c_int64),
+                ("marked_total", ctypes.c_int64)]
+
+
+class _BacaStep(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_double), ("residual", ctypes.c_double), ("lookahead", ctypes.c_double),
+                ("iterations", ctypes.c_int32), ("marked", ctypes.c_int32)]
 
 
 class _Schedule(ctypes.Structure):
@@ -150,6 +169,8 @@ def load():
         "hm_get_stats": (ctypes.c_int, [P, ctypes.POINTER(_Stats)]),
         "hm_amvm": (ctypes.c_int, [P, P, P, ctypes.POINTER(_AmvmParams), ctypes.POINTER(_AmvmInfo), P, P,
                                    I32, P, P]),
+        "hm_baca": (ctypes.c_int, [P, P, P, ctypes.POINTER(_BacaParams), ctypes.POINTER(_BacaInfo), P, I32, P,
+                                   P]),
         "hm_export_factors": (ctypes.c_int, [P, I64, I32, ctypes.POINTER(I32), P, P]),
         "hm_export_near": (ctypes.c_int, [P, I64, P]),
         "hm_matrix_destroy": (None, [P]),
@@ -491,6 +512,36 @@ def eval_points(H: HMatrix, t, u, form="fp64", stream=None):
     _check(load().hm_eval_points(H._h, ctypes.c_void_p(t.data_ptr()), ctypes.c_void_p(u.data_ptr()), nrhs, f,
                                  _stream_handle(stream)))
     return u
+
+
+def baca(H: HMatrix, b, t, theta: float = 0.8, alpha: float = 10.0, eps: float = 1e-4, tol0: float = 0.1,
+         r0: int = 8, look: int = 2, restart: int = 50, max_iter: int = 0, max_steps: int = 0, stream=None):
+    """``hm_baca``: solve V_h t = b with block-adaptive ACA (Algorithm 3,
+    single layer), FP64.  b, t: contiguous CUDA float64 vectors of 3M.
+    Returns a dict with steps, GMRES iterations, the final estimator and
+    residual, the crosses used against the assembled ACA, per-step history
+    (E, residual, lookahead, iterations, marked) and the final block ranks."""
+    import torch
+    if not (b.is_cuda and t.is_cuda and b.dtype == torch.float64 and t.dtype == torch.float64):
+        raise TypeError("baca: b and t must be CUDA float64 tensors")
+    if b.numel() != 3 * H.M or t.numel() != 3 * H.M or not b.is_contiguous() or not t.is_contiguous():
+        raise ValueError("baca: b and t must be contiguous vectors of 3M")
+    p = _BacaParams(float(theta), float(alpha), float(eps), float(tol0), int(r0), int(look), int(restart),
+                    int(max_iter), int(max_steps), 0)
+    info = _BacaInfo()
+    cap = 4096
+    hist = (_BacaStep * cap)()
+    ranks = np.zeros(max(H.stats().nadm, 1), dtype=np.int32)
+    _check(load().hm_baca(H._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(t.data_ptr()), ctypes.byref(p),
+                          ctypes.byref(info), ctypes.cast(hist, ctypes.c_void_p), cap, _ptr(ranks),
+                          _stream_handle(stream)))
+    n = min(info.steps + 1, cap)
+    steps = [dict(E=hist[i].E, residual=hist[i].residual, lookahead=hist[i].lookahead,
+                  iterations=hist[i].iterations, marked=hist[i].marked) for i in range(n)]
+    return dict(steps=info.steps, gmres_iterations=int(info.gmres_iterations), E=info.E,
+                rel_residual=info.rel_residual, b_norm=info.b_norm, crosses_used=int(info.crosses_used),
+                crosses_full=int(info.crosses_full), marked_total=int(info.marked_total), history=steps,
+                block_ranks=ranks[:H.stats().nadm].copy())
 
 
 def hmatvec_noalloc(H: HMatrix, x, y, form="fp64", stream=None):

@@ -154,3 +154,4 @@ def test_point_tree_invalid_arguments():
     out = ctypes.c_void_p()
     assert lib.hm_build_point_tree(None, None, 0, 8, ctypes.byref(out)) == binding.HM_EINVAL
     assert lib.hm_eval_points(None, None, None, 1, 0, None) == binding.HM_EINVAL
+    assert lib.hm_baca(None, None, None, None, None, None, 0, None, None) == binding.HM_EINVAL
