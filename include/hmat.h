@@ -490,8 +490,9 @@ int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_amvm_params
  *   hist     optional host array of hist_cap steps (E_k, ||b - A_k t||,
  *            ||(A_k - A^_k) t||, GMRES iterations, blocks marked)
  *   block_ranks  optional host array of nadm ints: r_b at exit
- * Needs the assembled FP64 factors and near field (not HM_DEFER_ACA, not
- * after hm_compact); not for an evaluation operator.  Allocates
+ * Needs the FP64 near field and either the assembled factors or
+ * HM_BACA_ACA_ON_DEMAND (not after hm_compact); not for an evaluation
+ * operator.  Allocates
  * (restart + 6) 3M doubles and about 24 sum|t| bytes of workspace through
  * the matrix's allocator for the call (and, at the first call, the product
  * tables it keeps); synchronises `stream`.
@@ -506,8 +507,16 @@ typedef struct {
     int32_t restart;   /* GMRES restart length, 1..200 (0 = 50) */
     int32_t max_iter;  /* GMRES iterations in all (0 = 100000) */
     int32_t max_steps; /* refinement steps (0 = 1000) */
-    int32_t flags;     /* 0 */
+    int32_t flags;     /* HM_BACA_ACA_ON_DEMAND */
 } hm_baca_params;
+
+/* hm_baca_params.flags: run Algorithm 1 on demand -- every block-kernel to
+ * r0 + look crosses, a refined block's kernels on to r_b + look, resumed from
+ * their saved state -- instead of taking prefixes of the assembled factors
+ * (the adaptive construction of A_k together with the solve); the matrix may
+ * be assembled with HM_DEFER_ACA.  info->crosses_full then counts the
+ * crosses computed. */
+#define HM_BACA_ACA_ON_DEMAND 1
 
 typedef struct {
     int32_t steps;             /* refinement steps taken */

@@ -515,19 +515,22 @@ def eval_points(H: HMatrix, t, u, form="fp64", stream=None):
 
 
 def baca(H: HMatrix, b, t, theta: float = 0.8, alpha: float = 10.0, eps: float = 1e-4, tol0: float = 0.1,
-         r0: int = 8, look: int = 2, restart: int = 50, max_iter: int = 0, max_steps: int = 0, stream=None):
+         r0: int = 8, look: int = 2, restart: int = 50, max_iter: int = 0, max_steps: int = 0,
+         on_demand: bool = False, stream=None):
     """``hm_baca``: solve V_h t = b with block-adaptive ACA (Algorithm 3,
     single layer), FP64.  b, t: contiguous CUDA float64 vectors of 3M.
     Returns a dict with steps, GMRES iterations, the final estimator and
-    residual, the crosses used against the assembled ACA, per-step history
-    (E, residual, lookahead, iterations, marked) and the final block ranks."""
+    residual, the crosses used against the assembled ACA (``on_demand``:
+    Algorithm 1 run on demand, HM_BACA_ACA_ON_DEMAND; crosses_full then counts
+    the crosses computed), per-step history (E, residual, lookahead,
+    iterations, marked) and the final block ranks."""
     import torch
     if not (b.is_cuda and t.is_cuda and b.dtype == torch.float64 and t.dtype == torch.float64):
         raise TypeError("baca: b and t must be CUDA float64 tensors")
     if b.numel() != 3 * H.M or t.numel() != 3 * H.M or not b.is_contiguous() or not t.is_contiguous():
         raise ValueError("baca: b and t must be contiguous vectors of 3M")
     p = _BacaParams(float(theta), float(alpha), float(eps), float(tol0), int(r0), int(look), int(restart),
-                    int(max_iter), int(max_steps), 0)
+                    int(max_iter), int(max_steps), 1 if on_demand else 0)
     info = _BacaInfo()
     cap = 4096
     hist = (_BacaStep * cap)()

@@ -915,8 +915,10 @@ __global__ void __launch_bounds__(kEvThreads) ev_fwd_kernel(const Blk* __restric
                                                             const int32_t* __restrict__ rank,
                                                             const int64_t* __restrict__ voff,
                                                             const int64_t* __restrict__ coff,
-                                                            const T* __restrict__ Vf, const T* __restrict__ xs,
-                                                            int64_t M, int64_t ntask, T* __restrict__ w)
+                                                            const T* __restrict__ Vf,
+                                                            const T* const* __restrict__ vptr,
+                                                            const T* __restrict__ xs, int64_t M, int64_t ntask,
+                                                            T* __restrict__ w)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarp = (int64_t)gridDim.x * kEvWarps;
@@ -924,7 +926,7 @@ __global__ void __launch_bounds__(kEvThreads) ev_fwd_kernel(const Blk* __restric
         const int r = rank[q];
         if (r == 0) continue;
         const Blk b = adm[q / 7];
-        const T* v = Vf + voff[q];
+        const T* v = vptr ? vptr[q] : Vf + voff[q];  // per-task pointers: factors of ACA on demand
         const T* x0 = xs + b.s0;
         const T* x1 = x0 + M;
         const T* x2 = x1 + M;
@@ -947,7 +949,9 @@ __global__ void __launch_bounds__(kEvThreads) ev_back_kernel(const int2* __restr
                                                              const int32_t* __restrict__ rank,
                                                              const int64_t* __restrict__ uoff,
                                                              const int64_t* __restrict__ coff,
-                                                             const T* __restrict__ Uf, const T* __restrict__ w,
+                                                             const T* __restrict__ Uf,
+                                                             const T* const* __restrict__ uptr,
+                                                             const T* __restrict__ w,
                                                              T c1, T c2, const int64_t* __restrict__ doff,
                                                              T* __restrict__ D)
 {
@@ -963,7 +967,7 @@ __global__ void __launch_bounds__(kEvThreads) ev_back_kernel(const int2* __restr
         for (int k = 0; k < 7; ++k) {
             const int64_t q = (int64_t)item.x * 7 + k;
             const int r = rank[q];
-            const T* u = Uf + uoff[q] + i;
+            const T* u = (uptr ? uptr[q] : Uf + uoff[q]) + i;
             const T* wq = w + 3 * coff[q];
             // the components this kernel uses (the slots ev_fwd wrote)
             const bool u0 = k <= 3, u1 = k == 0 || k == 2 || k == 4 || k == 5, u2 = k == 0 || k == 3 || k >= 5;
@@ -1189,11 +1193,11 @@ int eval_run(const hm_matrix& H, const double* t, double* u, int32_t nrhs, const
         if (nb > 0) {
             ev_fwd_kernel<T><<<grid(nb * 7), kEvThreads, 0, s>>>(H.d_adm.as<Blk>(), H.d_rank.as<int32_t>(),
                                                                  H.d_voff.as<int64_t>(), H.d_coff.as<int64_t>(), Vf,
-                                                                 xc, M, nb * 7, w);
+                                                                 nullptr, xc, M, nb * 7, w);
             HM_CUDA(cudaGetLastError());
             ev_back_kernel<T><<<grid(H.ev_nback), kEvThreads, 0, s>>>(
                 ev[kEvBack].as<int2>(), H.ev_nback, H.d_adm.as<Blk>(), H.d_rank.as<int32_t>(), H.d_uoff.as<int64_t>(),
-                H.d_coff.as<int64_t>(), Uf, w, c1, c2, ev[kEvDoff].as<int64_t>(), D);
+                H.d_coff.as<int64_t>(), Uf, nullptr, w, c1, c2, ev[kEvDoff].as<int64_t>(), D);
             HM_CUDA(cudaGetLastError());
         }
         if (H.ev_nnear > 0) {
@@ -1330,9 +1334,11 @@ extern "C" int hm_baca(const hm_matrix* H, const double* b, double* x, const hm_
 {
     if (!H || !b || !x || !prm) return fail(HM_EINVAL, "hm_baca: NULL argument");
     if (H->rect) return fail(HM_EINVAL, "hm_baca: an evaluation operator is not a system matrix");
-    if (H->compacted || H->aca_deferred || !H->U64.p)
-        return fail(HM_EINVAL, "hm_baca: needs the assembled FP64 factors (no hm_compact, no HM_DEFER_ACA)");
-    if (prm->flags != 0) return fail(HM_EINVAL, "hm_baca: unknown flags 0x%x", prm->flags);
+    if (prm->flags & ~HM_BACA_ACA_ON_DEMAND) return fail(HM_EINVAL, "hm_baca: unknown flags 0x%x", prm->flags);
+    const bool lazy = (prm->flags & HM_BACA_ACA_ON_DEMAND) != 0;
+    if (H->compacted) return fail(HM_EINVAL, "hm_baca: the FP64 data were released (hm_compact)");
+    if (!lazy && (H->aca_deferred || !H->U64.p))
+        return fail(HM_EINVAL, "hm_baca: no assembled ACA factors (HM_DEFER_ACA): use HM_BACA_ACA_ON_DEMAND");
     const double theta = prm->theta == 0.0 ? 0.8 : prm->theta;
     const double alpha = prm->alpha == 0.0 ? 10.0 : prm->alpha;
     const double tol0 = prm->tol0 == 0.0 ? 0.1 : prm->tol0;
@@ -1355,8 +1361,13 @@ extern "C" int hm_baca(const hm_matrix* H, const double* b, double* x, const hm_
     struct Restore {
         hm_matrix& h;
         cudaStream_t st;
-        ~Restore() { h.alloc.stream = st; }
-    } restore{Hm, saved_stream};
+        std::vector<DevBuf> arenas;  // factors of ACA on demand
+        ~Restore()
+        {
+            for (DevBuf& a : arenas) h.alloc.release(a.p, a.bytes);
+            h.alloc.stream = st;
+        }
+    } restore{Hm, saved_stream, {}};
     int rc;
     if (!Hm.ev[kEvXc].p && (rc = eval_prepare(Hm))) return rc;
     const int64_t M = H->M, N = 3 * M, nb = H->nadm;
@@ -1386,14 +1397,91 @@ extern "C" int hm_baca(const hm_matrix* H, const double* b, double* x, const hm_
     if (!Q || !bc || !xc || !rv || !yv || !ev_e || !Dl || !bn || !partial || !dots || !coef || !rk || !items ||
         !uptr || !vptr)
         return fail(HM_ENOMEM, "hm_baca: workspace (%d Krylov vectors of %lld)", m + 1, (long long)N);
-    {
-        std::vector<const double*> up((size_t)nb * 7), vp((size_t)nb * 7);
+    // the crosses of every block-kernel: pointers to U (k x m) and V (k x n)
+    // and how many there are (krank): the assembled factors, or, on demand,
+    // the arenas of the ACA runs so far (with the w slot offsets coff)
+    std::vector<const double*> up((size_t)nb * 7, nullptr), vp((size_t)nb * 7, nullptr);
+    std::vector<int32_t> krank((size_t)nb * 7, 0), kflags((size_t)nb * 7, 0);
+    std::vector<int64_t> hcoff((size_t)nb * 7, 0);
+    int32_t* d_krank = pool.get<int32_t>((size_t)nb * 7);
+    int64_t* d_coff = pool.get<int64_t>((size_t)nb * 7);
+    double* w_od = nullptr;  // w of the on-demand factors
+    int64_t w_od_cap = 0;
+    if (!d_krank || !d_coff) return fail(HM_ENOMEM, "hm_baca: rank tables");
+    const int kcap = std::max(1, (int)H->prm.kmax);
+    AcaResume rs{};
+    std::vector<const double*> prev((size_t)nb * 7, nullptr);
+    const double** d_prev = nullptr;
+    if (lazy) {
+        std::vector<int64_t> zoff((size_t)nb * 7 + 1, 0);
+        for (int64_t q = 0; q < nb * 7; ++q) zoff[(size_t)q + 1] = zoff[(size_t)q] + H->adm_h[(size_t)(q / 7)].m;
+        rs.k = pool.get<int32_t>((size_t)nb * 7);
+        rs.nz = pool.get<int32_t>((size_t)nb * 7);
+        rs.irow = pool.get<int32_t>((size_t)nb * 7);
+        rs.flags = pool.get<int32_t>((size_t)nb * 7);
+        rs.S2 = pool.get<double>((size_t)nb * 7);
+        rs.Z = pool.get<unsigned char>((size_t)zoff[(size_t)nb * 7]);
+        int64_t* d_zoff = pool.get<int64_t>(zoff.size());
+        d_prev = pool.get<const double*>((size_t)nb * 7);
+        if (!rs.k || !rs.nz || !rs.irow || !rs.flags || !rs.S2 || !rs.Z || !d_zoff || !d_prev)
+            return fail(HM_ENOMEM, "hm_baca: ACA state");
+        if ((rc = put(d_zoff, zoff, s))) return rc;
+        HM_CUDA(cudaMemsetAsync(rs.flags, 0, (size_t)nb * 7 * 4, s));
+        rs.zoff = d_zoff;
+        rs.prevU = d_prev;
+    } else {
         for (int64_t q = 0; q < nb * 7; ++q) {
             up[(size_t)q] = H->U64.as<double>() + H->uoff_h[(size_t)q];
             vp[(size_t)q] = H->V64.as<double>() + H->voff_h[(size_t)q];
+            krank[(size_t)q] = H->rank_h[(size_t)q];
         }
-        if ((rc = put(uptr, up, s)) || (rc = put(vptr, vp, s))) return rc;
     }
+    // Algorithm 1 on demand for the tasks bkl to kmax crosses, resumed where a
+    // task ran before (prev), then the tables of the product
+    auto run_aca = [&](const std::vector<int32_t>& bkl, int kmax) -> int {
+        if (bkl.empty()) return HM_OK;
+        std::vector<int32_t> rr;
+        std::vector<int64_t> oo;
+        DevBuf arena;
+        int rc2 = put(d_prev, prev, s);
+        if (rc2) return rc2;
+        rc2 = aca_on_demand(Hm, bkl, kmax, s, arena, rr, oo, &rs);
+        if (arena.p) restore.arenas.push_back(arena);
+        if (rc2) return rc2;
+        for (size_t q = 0; q < bkl.size(); ++q) {
+            const int32_t v = bkl[q];
+            up[(size_t)v] = arena.as<double>() + oo[q];
+            vp[(size_t)v] = up[(size_t)v] + (int64_t)rr[q] * H->adm_h[(size_t)(v / 7)].m;
+            krank[(size_t)v] = rr[q];
+        }
+        HM_CUDA(cudaMemcpyAsync(kflags.data(), rs.flags, kflags.size() * 4, cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaStreamSynchronize(s));
+        return HM_OK;
+    };
+    auto upload_factors = [&]() -> int {
+        int64_t c = 0;
+        for (int64_t q = 0; q < nb * 7; ++q) {
+            hcoff[(size_t)q] = c;
+            c += krank[(size_t)q];
+        }
+        if (lazy && c > w_od_cap) {
+            w_od_cap = c + c / 2 + 1;
+            w_od = pool.get<double>((size_t)(3 * w_od_cap));
+            if (!w_od) return fail(HM_ENOMEM, "hm_baca: w of %lld crosses", (long long)w_od_cap);
+        }
+        int rc2;
+        if ((rc2 = put(uptr, up, s)) || (rc2 = put(vptr, vp, s)) || (rc2 = put(d_krank, krank, s)) ||
+            (rc2 = put(d_coff, hcoff, s)))
+            return rc2;
+        return HM_OK;
+    };
+    if (lazy) {
+        std::vector<int32_t> all;
+        for (int64_t q = 0; q < nb * 7; ++q)
+            if (!(H->flags_h[(size_t)q] & 32)) all.push_back((int32_t)q);  // 32: identically zero kernel
+        if ((rc = run_aca(all, std::min(r0 + look, kcap)))) return rc;
+    }
+    if ((rc = upload_factors())) return rc;
     const unsigned gM = (unsigned)((M + 255) / 256), gN = (unsigned)((N + 255) / 256);
     auto grid = [&](int64_t warps) {
         return (unsigned)std::max<int64_t>(1, std::min<int64_t>(H->ev_grid, (warps + kEvWarps - 1) / kEvWarps));
@@ -1410,14 +1498,14 @@ extern "C" int hm_baca(const hm_matrix* H, const double* b, double* x, const hm_
             HM_CUDA(cudaGetLastError());
         }
         if (nb > 0) {
+            double* w = lazy ? w_od : ev[kEvW].as<double>();
             ev_fwd_kernel<double><<<grid(nb * 7), kEvThreads, 0, s>>>(H->d_adm.as<Blk>(), rk, H->d_voff.as<int64_t>(),
-                                                                      H->d_coff.as<int64_t>(), H->V64.as<double>(),
-                                                                      xs, M, nb * 7, ev[kEvW].as<double>());
+                                                                      d_coff, H->V64.as<double>(), vptr, xs, M,
+                                                                      nb * 7, w);
             HM_CUDA(cudaGetLastError());
             ev_back_kernel<double><<<grid(H->ev_nback), kEvThreads, 0, s>>>(
-                ev[kEvBack].as<int2>(), H->ev_nback, H->d_adm.as<Blk>(), rk, H->d_uoff.as<int64_t>(),
-                H->d_coff.as<int64_t>(), H->U64.as<double>(), ev[kEvW].as<double>(), c1, c2,
-                ev[kEvDoff].as<int64_t>(), ev[kEvD].as<double>());
+                ev[kEvBack].as<int2>(), H->ev_nback, H->d_adm.as<Blk>(), rk, H->d_uoff.as<int64_t>(), d_coff,
+                H->U64.as<double>(), uptr, w, c1, c2, ev[kEvDoff].as<int64_t>(), ev[kEvD].as<double>());
             HM_CUDA(cudaGetLastError());
         }
         ev_rowsum_kernel<double><<<gM, 256, 0, s>>>(ev[kEvIpos].as<int32_t>(), ev[kEvAptr].as<int32_t>(),
@@ -1457,8 +1545,8 @@ extern "C" int hm_baca(const hm_matrix* H, const double* b, double* x, const hm_
             if (norms) std::fill(hbn.begin(), hbn.end(), 0.0);
             return HM_OK;
         }
-        amvm_part_kernel<<<(unsigned)nb, kAmvmThreads, 0, s>>>(items, H->d_adm.as<Blk>(), H->d_rank.as<int32_t>(),
-                                                              uptr, vptr, xin, c1, c2, ev[kEvDoff].as<int64_t>(), Dl);
+        amvm_part_kernel<<<(unsigned)nb, kAmvmThreads, 0, s>>>(items, H->d_adm.as<Blk>(), d_krank, uptr, vptr, xin,
+                                                              c1, c2, ev[kEvDoff].as<int64_t>(), Dl);
         HM_CUDA(cudaGetLastError());
         amvm_rowsum_kernel<<<gM, 256, 0, s>>>(ev[kEvIpos].as<int32_t>(), ev[kEvAptr].as<int32_t>(),
                                              ev[kEvAidx].as<int32_t>(), H->d_adm.as<Blk>(), ev[kEvDoff].as<int64_t>(),
@@ -1478,7 +1566,7 @@ extern "C" int hm_baca(const hm_matrix* H, const double* b, double* x, const hm_
         std::vector<int32_t> hrk((size_t)nb * 7);
         for (int64_t bb = 0; bb < nb; ++bb) {
             for (int k = 0; k < 7; ++k)
-                hrk[(size_t)(bb * 7 + k)] = std::min(r[(size_t)bb], H->rank_h[(size_t)(bb * 7 + k)]);
+                hrk[(size_t)(bb * 7 + k)] = std::min(r[(size_t)bb], krank[(size_t)(bb * 7 + k)]);
             hitems[(size_t)bb] = AmvmItem{(int32_t)bb, r[(size_t)bb], r[(size_t)bb] + look, 0};
         }
         int rc2;
@@ -1591,11 +1679,28 @@ extern "C" int hm_baca(const hm_matrix* H, const double* b, double* x, const hm_
             });
             const double target = theta * Ek * theta * Ek;
             double acc = 0.0;
+            std::map<int, std::vector<int32_t>> rerun;  // on demand: tasks to extend, by their new kmax
             for (int64_t bb : ord) {
                 if (acc >= target || hbn[(size_t)bb] == 0.0) break;
                 acc += hbn[(size_t)bb];
                 r[(size_t)bb] += look;  // step 4: A_{k+1} = A^_k on the block
                 ++nmarked;
+                if (lazy)
+                    for (int kk = 0; kk < 7; ++kk) {
+                        const size_t q = (size_t)bb * 7 + (size_t)kk;
+                        const int want = std::min(r[(size_t)bb] + look, kcap);
+                        // only a run that stopped at its kmax has more crosses to give
+                        if (!(H->flags_h[q] & 32) && (kflags[q] & 1) && want > krank[q])
+                            rerun[want].push_back((int32_t)q);
+                    }
+            }
+            if (!rerun.empty()) {
+                std::fill(prev.begin(), prev.end(), nullptr);
+                for (auto& kv : rerun)
+                    for (int32_t q : kv.second) prev[(size_t)q] = up[(size_t)q];
+                for (auto& kv : rerun)
+                    if ((rc = run_aca(kv.second, kv.first))) return rc;
+                if ((rc = upload_factors())) return rc;
             }
         }
         if (k < hist_cap && hist)
@@ -1617,7 +1722,7 @@ extern "C" int hm_baca(const hm_matrix* H, const double* b, double* x, const hm_
         int64_t used = 0, full = 0;
         for (int64_t bb = 0; bb < nb; ++bb)
             for (int kk = 0; kk < 7; ++kk) {
-                const int32_t K = H->rank_h[(size_t)(bb * 7 + kk)];
+                const int32_t K = krank[(size_t)(bb * 7 + kk)];  // on demand: the crosses computed
                 used += std::min<int64_t>(K, r[(size_t)bb]);
                 full += K;
             }

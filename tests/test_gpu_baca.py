@@ -95,6 +95,26 @@ def test_baca_full_refinement_solves_the_full_system():
     assert np.linalg.norm(b - y) <= 1e-11 * np.linalg.norm(b)
 
 
+def test_baca_with_aca_on_demand():
+    """HM_BACA_ACA_ON_DEMAND: Algorithm 1 runs only to the crosses the
+    refinement reaches (resumed tasks); the solve is bitwise the prefix mode's,
+    on the fully assembled matrix and on one assembled without ACA, with fewer
+    crosses computed than the full ACA holds."""
+    V, T, tree, H, Ho = case()
+    b = rhs(Ho.M, 3)
+    kw = dict(theta=0.8, alpha=10.0, eps=1e-4, r0=2, look=2)
+    t1, i1 = run(H, b, **kw)
+    t2, i2 = run(H, b, on_demand=True, **kw)
+    assert np.array_equal(t1, t2)
+    assert i1["steps"] == i2["steps"] and np.array_equal(i1["block_ranks"], i2["block_ranks"])
+    assert i2["crosses_used"] == i1["crosses_used"]
+    assert i2["crosses_full"] < i1["crosses_full"]
+    Hd = binding.aca_assemble(tree, E, NU, 1e-8, max_rhs=1, defer_aca=True)
+    t3, i3 = run(Hd, b, on_demand=True, **kw)
+    assert np.array_equal(t1, t3)
+    assert i3["crosses_full"] == i2["crosses_full"]
+
+
 def test_baca_zero_rhs_and_errors():
     V, T, tree, H, Ho = case()
     t, info = run(H, np.zeros(3 * Ho.M))
