@@ -495,7 +495,8 @@ int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_amvm_params
  * operator.  Allocates
  * (restart + 6) 3M doubles and about 24 sum|t| bytes of workspace through
  * the matrix's allocator for the call (and, at the first call, the product
- * tables it keeps); synchronises `stream`.
+ * tables and workspace it keeps with the matrix, so that calls on the same
+ * matrix must not overlap); synchronises `stream`.
  * ------------------------------------------------------------------------- */
 typedef struct {
     double theta;      /* Doerfler parameter in (0, 1) (0 = 0.8) */

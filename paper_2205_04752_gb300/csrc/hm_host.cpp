@@ -387,7 +387,9 @@ int hm_set_material(hm_matrix* H, double E, double nu)
     if (!(nu > 0.0 && nu < 0.5)) return fail(HM_EINVAL, "hm_set_material: nu must lie in (0, 1/2)");
     H->E = E;
     H->nu = nu;
-    for (int f = 0; f < 4; ++f)
+    // an evaluation operator reads E and nu at each call; the square matrix's
+    // packed forms keep c1, c2 in their device tables
+    for (int f = 0; f < 4 && !H->rect; ++f)
         if (H->packed[f]) {
             int rc = write_mesh_table(*H, f, nullptr);
             if (rc) return rc;
@@ -426,7 +428,14 @@ int hm_get_stats(const hm_matrix* H, hm_stats* st)
     // bytes one product streams in each packed form (padded layouts; the
     // 16-bit forms add one float scale per factor column of U)
     const int64_t stream_elems = H->ul_total + H->vr_total;
-    for (int f = 0; f < 4; ++f) {
+    if (H->rect) {
+        // the evaluation operator reads its block-ordered arenas (FP64, and
+        // the FP32 copies once packed)
+        const int64_t elems = H->u_total + H->v_total + H->n_total;
+        st->bytes_form[HM_FP64] = elems * 8;
+        if (H->packed[HM_FP32]) st->bytes_form[HM_FP32] = elems * 4;
+    }
+    for (int f = 0; f < 4 && !H->rect; ++f) {
         if (!H->packed[f]) continue;
         int64_t wf = f == HM_FP64 ? 8 : (f == HM_FP32 ? 4 : 2);
         int64_t wn = f == HM_FP64 ? 8 : 4;

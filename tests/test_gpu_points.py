@@ -126,6 +126,8 @@ def test_eval_points_fp32_form():
     for r in range(2):
         assert _rel(u32[r], u64[r]) <= 1e-5, r
     assert np.array_equal(c.eval(x, "fp32"), u32)
+    st = c.H.stats()
+    assert st.bytes_form[1] * 2 == st.bytes_form[0] > 0
 
 
 def test_eval_points_with_more_than_32_crosses():
@@ -164,10 +166,13 @@ def test_eval_points_closed_form_and_material():
     u = c.eval(x)[0].reshape(-1, 3)
     exact = (1 + NU) * (5 - 6 * NU) / (3 * E * (1 - NU)) * f
     assert np.abs(u - exact).max() <= 1.5e-3 * np.abs(exact).max()
+    c.H.pack("fp32")
     c.H.set_material(2.0, 0.25)
     u2 = c.eval(x)[0].reshape(-1, 3)
     exact2 = (1.25) * (5 - 1.5) / (3 * 2.0 * 0.75) * f
     assert np.abs(u2 - exact2).max() <= 1.5e-3 * np.abs(exact2).max()
+    u3 = c.eval(x, "fp32")[0].reshape(-1, 3)
+    assert np.abs(u3 - exact2).max() <= 1.5e-3 * np.abs(exact2).max()
 
 
 def test_point_amvm_follows_the_oracle():
