@@ -23,8 +23,11 @@ adds the pieces for which a library routine is the plain definition:
   the domain): ``points_matvec`` by its definition, and ``HMatrix`` with
   ``points=`` (a tree of the points for the rows, the same ACA).
 
-Parity unpinned: the absolute accuracy of the near-singular rule on badly
-shaped triangles (only its convergence on well-shaped ones is pinned).
+Accuracy of the quadrature contract on badly shaped triangles (pinned in
+``tests/test_oracle_pins.py``): the near-singular rule stays within 5e-6 up to
+aspect ratio 30; the self term is within 5e-5 up to aspect ratio 4 (the
+workloads' meshes) and degrades on slivers (1e-2 at 10:1), a limit of the
+contract's 32-point angular rule.
 """
 from __future__ import annotations
 
@@ -157,7 +160,10 @@ def centroids(V, T) -> np.ndarray:
 
 def scalar_entry(x, V, tri, self_pair: bool, nd: int = ND) -> np.ndarray:
     """Seven scalar kernels (Eq. (Vh), collocation, 1/(4 pi) prefactor) of
-    point x against triangle ``tri`` (3 vertex ids into V)."""
+    point x against triangle ``tri`` (3 vertex ids into V); the self term
+    takes 1 <= nd <= 64 Gauss-Legendre points."""
+    if not 1 <= nd <= 64:
+        raise ValueError("nd must lie in 1..64")
     x, V, tri = _f64(x), _f64(V), _i32(tri)
     out = np.zeros(7)
     _L().or_scalar_entry(_p(x), _p(V), _p(tri), int(self_pair), nd, _p(out))
@@ -165,7 +171,10 @@ def scalar_entry(x, V, tri, self_pair: bool, nd: int = ND) -> np.ndarray:
 
 
 def kelvin_entry(x, V, tri, self_pair: bool, E: float, nu: float, nd: int = ND) -> np.ndarray:
-    """int_tau S_K(x - y) ds_y from Kelvin's tensor directly, 3 x 3."""
+    """int_tau S_K(x - y) ds_y from Kelvin's tensor directly, 3 x 3 (the
+    self term with 1 <= nd <= 64 Gauss-Legendre points)."""
+    if not 1 <= nd <= 64:
+        raise ValueError("nd must lie in 1..64")
     x, V, tri = _f64(x), _f64(V), _i32(tri)
     out = np.zeros(9)
     _L().or_kelvin_entry(_p(x), _p(V), _p(tri), int(self_pair), nd, E, nu, _p(out))

@@ -241,6 +241,11 @@ static void self_term(const integrand* g, const double* x, const double* p0, con
                       const double* p2, int nd, double* acc)
 {
     double vq[64], wq[64];
+    if (nd < 1 || nd > 64) {
+        /* outside the node tables: no value rather than an overrun */
+        for (int v = 0; v < g->nval; ++v) acc[v] = NAN;
+        return;
+    }
     or_gauss_legendre01(nd, vq, wq);
     const double* P[3] = {p0, p1, p2};
     double zero[3] = {0.0, 0.0, 0.0};

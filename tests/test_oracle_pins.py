@@ -510,3 +510,50 @@ def test_kelvin_rows_matvec_matches_dense_rows():
     dofs = (3 * rows[:, None] + np.arange(3)[None, :]).ravel()
     np.testing.assert_allclose(ys, oracle.dense_matvec(A, x)[:, dofs], rtol=1e-12,
                                atol=1e-14)
+
+
+@pytest.mark.parametrize("ar", [4.0, 30.0])
+def test_near_rule_on_badly_shaped_triangles(ar):
+    """The quadrature contract's near-singular rule on elongated triangles
+    (aspect ratio 4 and 30): points above the triangle (0.05 and 0.3 of its
+    diameter) and in its plane just beyond an edge or a vertex, as the
+    centroids of neighbouring triangles lie, agree with an independent
+    adaptive integral to 5e-6 of the V_Delta scale."""
+    P = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.5, 1.0 / ar, 0.0]])
+    T0 = np.array([0, 1, 2], dtype=np.int32)
+    c = P.mean(0)
+    pts = [c + [0.2, 0.1 / ar, 0.05], c + [-0.3, 0.0, 0.3], [0.5, -0.05, 0.0], [1.05, 0.0, 0.0],
+           [0.5, 1.0 / ar + 0.02, 0.0]]
+    for x in pts:
+        x = np.asarray(x, dtype=np.float64)
+        s = oracle.scalar_entry(x, P, T0, False)
+        for kern in range(7):
+            ref = _dblquad_entry(x, P, kern)
+            assert abs(s[kern] - ref) <= 5e-6 * abs(s[0]), (x, kern)
+
+
+def test_self_rule_on_elongated_triangles():
+    """The self term (Duffy map, n_D = 32 angular points per edge
+    sub-triangle) against the closed-form V_Delta and the polar integrals:
+    within 5e-5 at aspect ratio 4 (the most elongated triangles of the
+    workloads' meshes); at 10 it is off by up to 1e-2 and improves with n_D,
+    the documented limit of the contract on slivers."""
+    T0 = np.array([0, 1, 2], dtype=np.int32)
+    kl = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+
+    def worst(P, nd):
+        s = oracle.scalar_entry(P.mean(0), P, T0, True, nd)
+        ref0 = _self_analytic_vdelta(P)
+        e = abs(s[0] - ref0) / abs(ref0)
+        for idx, (k, l) in enumerate(kl):
+            ref = _self_polar(P, lambda v, k=k, l=l: v[k] * v[l])
+            e = max(e, abs(s[1 + idx] - ref) / abs(ref0))
+        return e
+
+    P4 = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.5, 0.25, 0.0]])
+    assert worst(P4, 32) <= 5e-5
+    P10 = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.5, 0.1, 0.0]])
+    w32, w64 = worst(P10, 32), worst(P10, 64)
+    assert w32 <= 2e-2 and w64 < 0.1 * w32
+    with pytest.raises(ValueError):
+        oracle.scalar_entry(P4.mean(0), P4, T0, True, 65)
