@@ -19,6 +19,9 @@ adds the pieces for which a library routine is the plain definition:
   solve interleaved with block refinement, on a dense A_k formed from the
   oracle's factors, with a plain restarted GMRES (``numpy.linalg.lstsq`` for
   its small least-squares problems);
+* the double-layer operator K_h of Eq. (Kh) in collocation form
+  (``double_layer_dense``: K_Delta with hat functions, the surface curls T_h,
+  V_Delta T_h and E/(1+nu) V_h T_h; matrix products by numpy);
 * the evaluation operator ~V_h of Section 5, Eq. (vector_eq) (the displacement at points of
   the domain): ``points_matvec`` by its definition, and ``HMatrix`` with
   ``points=`` (a tree of the points for the rows, the same ACA).
@@ -93,6 +96,8 @@ def _L():
                 "or_hmat_rtree": (None, [P, P, P, P]),
                 "or_kelvin_points_matvec": (None, [P, P, I64, D, D, P, I64, P, I64, P]),
                 "or_scalar_points": (None, [P, P, I64, P, I64, P]),
+                "or_dl_entry": (None, [P, P, P, ctypes.c_int, P]),
+                "or_dl_dense": (None, [P, I64, P, I64, P]),
                 "or_hmat_free": (None, [P]),
                 "or_hmat_sizes": (None, [P, P]),
                 "or_hmat_tree": (None, [P, P, P, P]),
@@ -741,3 +746,65 @@ def baca(Ho: "HMatrix", E: float, nu: float, b, theta: float = 0.8, alpha: float
     out = np.zeros(N)
     out.reshape(M, 3)[perm] = x.reshape(M, 3)
     return dict(x=out, ranks=np.minimum(r[:, None], full), full_ranks=full, steps=k, **hist)
+
+
+# --------------------------------------------------------------------------
+# The double-layer operator K_h (Section 4.2, Eq. (Kh)), collocation form
+# --------------------------------------------------------------------------
+
+def dl_dense(V, T) -> np.ndarray:
+    """K_Delta of Eq. (Kh) at the centroids: (M, nv), column p the hat
+    function of vertex p, (1/(4 pi)) int (c_i - y).n / |c_i - y|^3 psi_p(y) ds_y
+    (the triangle's own flat panel gives 0)."""
+    V, T = _f64(V), _i32(T)
+    out = np.zeros((T.shape[0], V.shape[0]))
+    _L().or_dl_dense(_p(V), V.shape[0], _p(T), T.shape[0], _p(out))
+    return out
+
+
+def surface_curls(V, T) -> np.ndarray:
+    """T_kl,h of Eq. (Kh): (3, 3, M, nv) with T[k, l][i, p] = n_l d_k psi_p -
+    n_k d_l psi_p on triangle i (constant there; psi_p the hat function of
+    vertex p, n the unit normal from the vertex order).  Reading of the
+    boundary operators T_kl: the tangential (Guenter) derivative n_l d_k -
+    n_k d_l, antisymmetric in (k, l) as the block structure of T_h requires.
+    d psi_a on (p0, p1, p2) is n x (p_{a+2} - p_{a+1}) / (2 area)."""
+    V, T = _f64(V), _i32(T)
+    M, nv = T.shape[0], V.shape[0]
+    out = np.zeros((3, 3, M, nv))
+    for i in range(M):
+        P = V[T[i]]
+        c = np.cross(P[1] - P[0], P[2] - P[0])
+        A2 = float(np.linalg.norm(c))
+        n = c / A2
+        for a in range(3):
+            g = np.cross(n, P[(a + 2) % 3] - P[(a + 1) % 3]) / A2
+            for k in range(3):
+                for l in range(3):
+                    out[k, l, i, T[i, a]] += n[l] * g[k] - n[k] * g[l]
+    return out
+
+
+def double_layer_dense(V, T, E: float, nu: float) -> np.ndarray:
+    """K_h of Eq. (Kh) in collocation form, (3M, 3 nv), rows 3i + a (centroid
+    i, component a), columns 3p + b (vertex p, component b):
+        K_h = diag(K_Delta) - diag(V_Delta) T_h + E / (1 + nu) V_h T_h,
+    with T_h the 3 x 3 block matrix [[0, T12, T13], [-T12, 0, T23],
+    [-T13, -T23, 0]] of the surface curls (matrix products by numpy)."""
+    V, T = _f64(V), _i32(T)
+    M, nv = T.shape[0], V.shape[0]
+    KD = dl_dense(V, T)
+    S = surface_curls(V, T)
+    Th = np.zeros((3 * M, 3 * nv))
+    for a, b in ((0, 1), (0, 2), (1, 2)):
+        Th[a::3, b::3] = S[a, b]
+        Th[b::3, a::3] = -S[a, b]
+    VD = scalar_rows(V, T, np.arange(M))[0]
+    Vh = kelvin_dense(V, T, E, nu)
+    K = np.zeros((3 * M, 3 * nv))
+    for a in range(3):
+        K[a::3, a::3] = KD
+    VDT = np.zeros((3 * M, 3 * nv))
+    for a in range(3):
+        VDT[a::3, :] = VD @ Th[a::3, :]
+    return K - VDT + (E / (1.0 + nu)) * (Vh @ Th)

@@ -17,6 +17,8 @@
  *   admissibility / partition      Section 2.1, Eq. (adm) and the block-cluster recursion
  *   ACA                            Section 2.2, Algorithm 1 and the cross representation after it
  *   H-matrix-vector product        Section 2 (O(k(M+N)) product of a low-rank block) and Section 2.2
+ *   double layer K_h               Section 4.2, Eq. (Kh) (K_Delta with hat functions, the surface curls
+ *                                  T_h, V_Delta T_h and V_h T_h; collocation at the centroids)
  *   evaluation operator ~V_h       Section 5, Eq. (vector_eq) (u_h at points x_i of the domain: the collocation
  *                                  entries with x_i for the centroid; a tree of the points)
  *
@@ -179,14 +181,40 @@ static void kelvin_at(const double* x, const double* y, double E, double nu, dou
 /* A generic "value at a source point" so that the same quadrature serves the
  * seven scalar kernels and the Kelvin tensor. */
 typedef struct {
-    int nval;     /* 7 scalar kernels or 9 tensor entries */
+    int nval;     /* 7 scalar kernels, 9 tensor entries, or 3 hat-weighted double-layer values */
     double E, nu; /* used by the tensor */
+    /* the double layer: the triangle tau (vertices p[0..2]) whose hat
+     * functions weight the kernel, its unit normal and (p1-p0)x(p2-p0).n */
+    const double* p[3];
+    double n[3], twice_area;
 } integrand;
+
+/* The double-layer kernel of Section 4.1's K (the Laplace part, K_Delta):
+ * (x - y).n(y) / |x - y|^3 times the three barycentric coordinates of y in
+ * tau (the hat functions psi_j of tau's vertices), without 1/(4 pi). */
+static void double_layer_at(const integrand* g, const double* x, const double* y, double f[3])
+{
+    double d[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    double r = sqrt(r2);
+    double k = (d[0] * g->n[0] + d[1] * g->n[1] + d[2] * g->n[2]) / (r2 * r);
+    for (int a = 0; a < 3; ++a) {
+        const double* q1 = g->p[(a + 1) % 3];
+        const double* q2 = g->p[(a + 2) % 3];
+        double u[3] = {q1[0] - y[0], q1[1] - y[1], q1[2] - y[2]};
+        double v[3] = {q2[0] - y[0], q2[1] - y[1], q2[2] - y[2]};
+        double c0 = u[1] * v[2] - u[2] * v[1], c1 = u[2] * v[0] - u[0] * v[2], c2 = u[0] * v[1] - u[1] * v[0];
+        double lam = (c0 * g->n[0] + c1 * g->n[1] + c2 * g->n[2]) / g->twice_area;
+        f[a] = k * lam;
+    }
+}
 
 static void eval_at(const integrand* g, const double* x, const double* y, double* f)
 {
     if (g->nval == 7)
         scalar_kernels_at(x, y, f);
+    else if (g->nval == 3)
+        double_layer_at(g, x, y, f);
     else
         kelvin_at(x, y, g->E, g->nu, f);
 }
@@ -386,6 +414,54 @@ void or_scalar_points(const double* V, const int32_t* T, int64_t M, const double
         for (int64_t j = 0; j < M; ++j) {
             or_scalar_entry(P + 3 * r, V, T + 3 * j, 0, OR_ND, e);
             for (int v = 0; v < 7; ++v) out[(v * np + r) * M + j] = e[v];
+        }
+    }
+}
+
+/* The double-layer block of Eq. (Kh), collocation at x (reading: the outer
+ * integral over tau_i dropped, as for V_h):
+ *   out[a] = (1/(4 pi)) int_{tau_j} (x - y).n_j / |x - y|^3 psi_a(y) ds_y
+ * for the three vertices a of tau_j (psi_a the hat function of vertex a),
+ * n_j the unit normal of tau_j from its vertex order.  self != 0 means x lies
+ * in tau_j (its centroid): (x - y).n_j = 0 on the flat triangle, so the
+ * values are exactly 0. */
+void or_dl_entry(const double* x, const double* V, const int32_t* tj, int self, double out[3])
+{
+    for (int a = 0; a < 3; ++a) out[a] = 0.0;
+    if (self) return;
+    const double* p0 = V + 3 * tj[0];
+    const double* p1 = V + 3 * tj[1];
+    const double* p2 = V + 3 * tj[2];
+    integrand g;
+    memset(&g, 0, sizeof g);
+    g.nval = 3;
+    g.p[0] = p0;
+    g.p[1] = p1;
+    g.p[2] = p2;
+    double e1[3] = {p1[0] - p0[0], p1[1] - p0[1], p1[2] - p0[2]};
+    double e2[3] = {p2[0] - p0[0], p2[1] - p0[1], p2[2] - p0[2]};
+    double c[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    double len = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    for (int k = 0; k < 3; ++k) g.n[k] = c[k] / len;
+    g.twice_area = len;
+    adaptive(&g, x, p0, p1, p2, 0, out);
+    for (int a = 0; a < 3; ++a) out[a] *= 1.0 / (4.0 * OR_PI);
+}
+
+/* Dense K_Delta of Eq. (Kh) at the collocation points: M x nv row-major,
+ * out[i * nv + p] = sum over the triangles tau_j holding vertex p of the
+ * entry of or_dl_entry(c_i, tau_j) for that vertex. */
+void or_dl_dense(const double* V, int64_t nv, const int32_t* T, int64_t M, double* out)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < M; ++i) {
+        double x[3], e[3];
+        centroid(V + 3 * T[3 * i], V + 3 * T[3 * i + 1], V + 3 * T[3 * i + 2], x);
+        double* row = out + i * nv;
+        for (int64_t p = 0; p < nv; ++p) row[p] = 0.0;
+        for (int64_t j = 0; j < M; ++j) {
+            or_dl_entry(x, V, T + 3 * j, i == j, e);
+            for (int a = 0; a < 3; ++a) row[T[3 * j + a]] += e[a];
         }
     }
 }

@@ -1,0 +1,136 @@
+"""Pins of the oracle's double-layer operator K_h (Section 4.2, Eq. (Kh),
+collocation at the centroids) against what the mathematics fixes (CPU only).
+
+Facts used (not printed in the paper):
+* Gauss's solid-angle formula: (1/(4 pi)) int (x - y).n / |x - y|^3 ds_y = -1/2
+  for x on a face of a closed polyhedron (outward normals), so every row of
+  K_Delta sums to -1/2;
+* the double layer of the unit sphere has the spherical harmonics of degree n
+  as eigenfunctions with eigenvalue -1/(2(2n + 1)): K_Delta applied to a
+  linear function y_k gives -y_k / 6 at O(h^2);
+* the tangential derivatives of a linear field are exact on flat triangles;
+* Lame's double layer maps every rigid motion r to -r/2 on the surface
+  (the interior limit of the traction double layer), which involves every
+  term of Eq. (Kh): K_Delta, V_Delta T_h and E/(1+nu) V_h T_h."""
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle
+from paper_2205_04752_gb300 import inputs
+
+E, NU = 1.0, 0.3
+
+
+def test_self_panel_is_zero_and_entry_against_adaptive_quadrature():
+    """The collocation point's own flat triangle contributes nothing; a
+    neighbour's hat-weighted entries agree with an independent adaptive
+    integral to 5e-6 (the kernel is one order more singular than V_Delta's;
+    measured 2e-6 with the contract's subdivision)."""
+    V, T = inputs.icosphere(2)
+    C = oracle.centroids(V, T)
+    i = 11
+    out = np.zeros(3)
+    lib = oracle._L()
+    tri = np.ascontiguousarray(T[i], dtype=np.int32)
+    lib.or_dl_entry(oracle._p(C[i]), oracle._p(V), oracle._p(tri), 1, oracle._p(out))
+    assert not np.any(out)
+    nbr = [j for j in range(len(T)) if j != i and len(set(T[j]) & set(T[i])) == 2][0]
+    P = V[T[nbr]]
+    tri = np.ascontiguousarray(T[nbr], dtype=np.int32)
+    lib.or_dl_entry(oracle._p(C[i]), oracle._p(V), oracle._p(tri), 0, oracle._p(out))
+    e1, e2 = P[1] - P[0], P[2] - P[0]
+    c = np.cross(e1, e2)
+    n = c / np.linalg.norm(c)
+    for a in range(3):
+        def f(v, u, a=a):
+            y = P[0] + u * e1 + v * e2
+            d = C[i] - y
+            lam = (1.0 - u - v, u, v)[a]
+            return (d @ n) / np.linalg.norm(d) ** 3 * lam
+        ref, _ = integrate.dblquad(f, 0.0, 1.0, lambda u: 0.0, lambda u: 1.0 - u, epsabs=1e-14, epsrel=1e-11)
+        ref *= np.linalg.norm(c) / (4 * np.pi)
+        assert abs(out[a] - ref) <= 5e-6 * np.abs(out).max(), (a, out[a], ref)
+
+
+@pytest.mark.parametrize("level", [1, 2, 3])
+def test_row_sums_are_minus_half(level):
+    """Solid angle: every row of K_Delta (the hat functions sum to one) is
+    -1/2 to the accuracy of the quadrature contract."""
+    V, T = inputs.icosphere(level)
+    KD = oracle.dl_dense(V, T)
+    assert np.abs(KD.sum(1) + 0.5).max() <= 1e-6
+
+
+def test_linear_data_give_the_sphere_eigenvalue():
+    """K_Delta applied to the vertex values of y_k tends to -c_k / 6 at the
+    centroids at O(h^2) (errors shrink by more than 3 per level)."""
+    errs = []
+    for level in (1, 2, 3):
+        V, T = inputs.icosphere(level)
+        KD = oracle.dl_dense(V, T)
+        C = oracle.centroids(V, T)
+        errs.append(max(np.abs(KD @ V[:, k] + C[:, k] / 6.0).max() for k in range(3)))
+    assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 3.0, errs
+    assert errs[2] <= 1e-3
+
+
+def test_surface_curls_exact_on_linear_fields():
+    """T_kl u = n_l d_k u - n_k d_l u is exact for a linear field u(y) = A y on
+    flat triangles; T_kl = -T_lk, T_kk = 0 and constants are annihilated."""
+    V, T = inputs.icosphere(2)
+    S = oracle.surface_curls(V, T)
+    A = np.array([[0.3, -1.2, 0.5], [2.0, 0.1, -0.7], [-0.4, 0.9, 1.5]])
+    for i in range(0, len(T), 17):
+        P = V[T[i]]
+        c = np.cross(P[1] - P[0], P[2] - P[0])
+        n = c / np.linalg.norm(c)
+        # the tangential part of the gradient of u_b = A[b] . y
+        for b in range(3):
+            g = A[b] - (A[b] @ n) * n
+            for k in range(3):
+                for l in range(3):
+                    val = S[k, l, i] @ (V @ A[b])
+                    assert abs(val - (n[l] * g[k] - n[k] * g[l])) <= 1e-12 * np.abs(A).max(), (i, b, k, l)
+    for k in range(3):
+        assert not np.any(S[k, k])
+        for l in range(3):
+            np.testing.assert_allclose(S[k, l], -S[l, k], rtol=0, atol=1e-14)
+            assert np.abs(S[k, l].sum(1)).max() <= 1e-12
+
+
+@pytest.mark.parametrize("level", [1, 2])
+def test_rigid_motions_are_mapped_to_minus_half(level):
+    """Translations and rotations u(y) = omega x y give -u/2 at every
+    centroid to the quadrature accuracy; the tangential derivative with the
+    opposite sign (the printed T_ij is garbled), a dropped V_h T_h term or
+    mu in place of 2 mu = E/(1+nu) miss it by more than 50%."""
+    V, T = inputs.icosphere(level)
+    M, nv = len(T), len(V)
+    C = oracle.centroids(V, T)
+    K = oracle.double_layer_dense(V, T, E, NU)
+    c = np.array([1.0, -2.0, 0.5])
+    assert np.abs((K @ np.tile(c, nv)).reshape(M, 3) + 0.5 * c).max() <= 2e-6
+    om = np.array([0.3, -0.5, 0.8])
+    ref = -0.5 * np.cross(om, C)
+    u = np.cross(om, V).reshape(-1)
+    assert np.abs((K @ u).reshape(M, 3) - ref).max() <= 2e-6 * np.abs(ref).max()
+    # the alternatives
+    S = oracle.surface_curls(V, T)
+    Th = np.zeros((3 * M, 3 * nv))
+    for a, b in ((0, 1), (0, 2), (1, 2)):
+        Th[a::3, b::3] = S[a, b]
+        Th[b::3, a::3] = -S[a, b]
+    Vh = oracle.kelvin_dense(V, T, E, NU)
+    Kd = np.zeros_like(K)
+    KD = oracle.dl_dense(V, T)
+    VD = oracle.scalar_rows(V, T, np.arange(M))[0]
+    for a in range(3):
+        Kd[a::3, a::3] = KD
+    VDT = np.zeros_like(K)
+    for a in range(3):
+        VDT[a::3, :] = VD @ Th[a::3, :]
+    for Kw in (Kd + VDT - (E / (1 + NU)) * (Vh @ Th),          # opposite sign of T
+               Kd - VDT,                                       # V_h T_h dropped
+               Kd - VDT + 0.5 * (E / (1 + NU)) * (Vh @ Th)):    # mu instead of 2 mu
+        assert np.abs((Kw @ u).reshape(M, 3) - ref).max() > 0.5 * np.abs(ref).max()
