@@ -55,8 +55,14 @@ int eval_prepare(hm_matrix& H)
         (rc = ev_put(H, kEvNdoff, ndoff, ndoff.size())) ||
         (rc = ev_put(H, kEvW, none, (size_t)(3 * std::max<int64_t>(H.c_total, 1)))) ||
         (rc = ev_put(H, kEvXc, none, (size_t)(3 * M))) || (rc = ev_put(H, kEvYc, none, (size_t)(3 * Mr))) ||
-        (rc = ev_put(H, kEvD, none, (size_t)doff[(size_t)nb])) || (rc = ev_put(H, kEvDn, none, (size_t)ndoff[(size_t)nn])))
+        (rc = ev_put(H, kEvD, none, (size_t)doff[(size_t)nb])) || (rc = ev_put(H, kEvDn, none, (size_t)ndoff[(size_t)nn]))) {
+        // all or nothing: a later call must not find half of the tables
+        for (DevBuf& b : H.ev) {
+            H.alloc.release(b.p, b.bytes);
+            b = DevBuf{};
+        }
         return rc;
+    }
     return HM_OK;
 }
 int eval_pack_fp32(hm_matrix& H, cudaStream_t s)
@@ -142,6 +148,7 @@ extern "C" int hm_eval_points(const hm_matrix* H, const double* t, double* u, in
     if (H->aca_deferred)
         return fail(HM_EINVAL, "hm_eval_points: assembled with HM_DEFER_ACA (use hm_amvm with HM_AMVM_ACA_ON_DEMAND)");
     if (nrhs < 1) return fail(HM_EINVAL, "hm_eval_points: nrhs %d < 1", nrhs);
+    if (!H->ev[kEvXc].p) return fail(HM_EINVAL, "hm_eval_points: the operator has no product tables");
     cudaStream_t s = (cudaStream_t)stream;
     if (form == HM_FP64)
         return eval_run<double>(*H, t, u, nrhs, H->U64.as<double>(), H->V64.as<double>(), H->N64.as<double>(), s);

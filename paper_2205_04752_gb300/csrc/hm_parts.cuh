@@ -607,7 +607,11 @@ int ev_put(hm_matrix& H, int which, const std::vector<T>& h, size_t n)
     DevBuf& d = H.ev[which];
     d.bytes = std::max<size_t>(n, 1) * sizeof(T);
     d.p = H.alloc.alloc(d.bytes);
-    if (!d.p) return fail(HM_ENOMEM, "evaluation operator: device allocation of %zu bytes failed", d.bytes);
+    if (!d.p) {
+        d.bytes = 0;
+        return fail(HM_ENOMEM, "evaluation operator: device allocation of %zu bytes failed",
+                    std::max<size_t>(n, 1) * sizeof(T));
+    }
     if (!h.empty())
         HM_CUDA(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, H.alloc.stream));
     return HM_OK;
