@@ -155,3 +155,20 @@ def test_point_tree_invalid_arguments():
     assert lib.hm_build_point_tree(None, None, 0, 8, ctypes.byref(out)) == binding.HM_EINVAL
     assert lib.hm_eval_points(None, None, None, 1, 0, None) == binding.HM_EINVAL
     assert lib.hm_baca(None, None, None, None, None, None, 0, None, None) == binding.HM_EINVAL
+
+
+@pytest.mark.slow
+def test_point_tree_and_partition_match_oracle_level6():
+    """The evaluation operator's benchmark workload: 65,536 points in the ball
+    of radius 0.95 inside the level-6 icosphere, leaves of 64 on both sides."""
+    V, T = inputs.icosphere(6)
+    P = inputs.ball_points(65536, 0.95, 7)
+    tr = binding.build_cluster_tree(V, T, 64, 0.8)
+    pt = binding.build_point_tree(tr, P, 64)
+    perm, nodes, adm, near = pt.export()
+    Ho = oracle.HMatrix(V, T, 64, 0.8, 1e-4, points=P, leaf_points=64)
+    np.testing.assert_array_equal(perm, Ho.rperm)
+    np.testing.assert_array_equal(nodes, Ho.rnodes)
+    np.testing.assert_array_equal(adm, Ho.adm)
+    np.testing.assert_array_equal(near, Ho.near)
+    assert pt.nadm == 121407 and pt.nnear == 30638
