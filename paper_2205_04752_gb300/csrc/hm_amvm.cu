@@ -7,13 +7,15 @@
 // and the look-ahead parts D_b = (A^_k - A_k)_b x, the estimator is gamma_k =
 // ||sum_b D_b|| = ||b^_k - b_k||.  Marking (step 3) goes through the rows in
 // decreasing |(b^_k - b_k)_i| and adds every block t x s with i in t and
-// |(D_b)_i| >= (1 - theta)(c_sp N N)^{-1/2} gamma_k until gamma_k -
-// gamma_k(P_k) >= theta gamma_k; a marked block takes the look-ahead ranks
-// (step 4).  The loop ends when gamma_k <= eps ||b^_k||.
+// |(D_b)_i| >= (1 - theta)(c_sp N_r N_c)^{-1/2} gamma_k (N_r rows, N_c
+// columns: 3M each, or 3 points x 3M for the evaluation operator) until
+// gamma_k - gamma_k(P_k) >= theta gamma_k; a marked block takes the
+// look-ahead ranks (step 4).  The loop ends when gamma_k <= eps ||b^_k||.
 //
-// Device work per iteration: the look-ahead parts of the blocks refined in
-// the previous step (one CTA per block: V^T x of the new crosses by warp
-// reductions, then U times them row by row), the row sums of all parts (each
+// Device work per iteration (kernels shared with the other block products in
+// hm_parts.cuh): the look-ahead parts of the blocks refined in the previous
+// step (one CTA per block: V^T x of the new crosses by warp reductions, then
+// U times them row by row), the row sums of all parts (each
 // position adds the parts of the blocks whose row cluster holds it, in block
 // order: deterministic), and the update of b_k by the marked blocks' parts.
 // The marking runs on the device too: the rows sorted by their error, the

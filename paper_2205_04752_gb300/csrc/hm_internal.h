@@ -286,7 +286,7 @@ struct hm_matrix {
     hm::DevBuf d_rperm;  // evaluation operator: int32 Mr, point cluster position -> original point
     hm::DevBuf g_rows;   // evaluation operator: Mr x 3 points in cluster order
     // evaluation operator: tables and workspace of its exact product
-    // (hm_amvm.cu; index names there)
+    // (hm_eval.cu; index names in hm_parts.cuh)
     static constexpr int kEvBufs = 14;
     hm::DevBuf ev[kEvBufs];
     int64_t ev_parts = 0;              // 3 sum |t| over the admissible blocks
@@ -370,7 +370,8 @@ int aca_on_demand(hm_matrix& H, const std::vector<int32_t>& bk, int kmax, cudaSt
                   std::vector<int32_t>& rank, std::vector<int64_t>& off, const AcaResume* resume = nullptr,
                   std::vector<int32_t>* flags = nullptr, size_t cap_hint = 0);
 // the evaluation operator (a matrix assembled from a point tree): tables and
-// workspace of its exact FP64 product (hm_amvm.cu), built once at assembly
+// workspace of its product (hm_eval.cu), built once at assembly (and by
+// hm_baca for a square matrix at its first call)
 int eval_prepare(hm_matrix& H);
 // the FP32 form of an evaluation operator: FP32 copies of its block-ordered
 // U, V and near arenas (in Ul[HM_FP32], Vr[HM_FP32] and Nl32), same offsets
