@@ -126,6 +126,27 @@ int hm_build_point_tree(const hm_tree* surface, const double* pts, int64_t npts,
                         hm_tree** out);
 
 /* ---------------------------------------------------------------------------
+ * hm_build_vertex_tree -- the column side of the double layer's K_Delta
+ * (Section 4.2, Eq. (Kh): rows the collocation points, columns the hat
+ * functions psi_p of the mesh vertices).  Builds the cluster tree of the
+ * vertices (the split rule of hm_build_cluster_tree on the vertex
+ * coordinates) whose boxes are the unions of the vertices' stars (the boxes
+ * of all triangles holding the vertex, the support of psi_p), and the block
+ * partition of (triangle tree of `surface`) x (vertex tree) under Eq. (adm)
+ * with the surface tree's eta.  Host only.
+ *   surface  a triangle tree (copied)
+ *   leaf     b_min of the vertex tree, 1..HM_MAX_LEAF
+ *   out      new tree: hm_tree_sizes / hm_tree_export describe the vertex
+ *            tree (perm over the vertices, nodes) and the partition (row node
+ *            of the surface tree, column node of the vertex tree)
+ * The device assembly of the double layer is not built yet: hm_aca_assemble
+ * refuses this tree (HM_EINVAL).
+ * Errors: HM_EINVAL (NULL, `surface` not a triangle tree, leaf out of range,
+ * a vertex in no triangle), HM_ENOMEM.
+ * ------------------------------------------------------------------------- */
+int hm_build_vertex_tree(const hm_tree* surface, int32_t leaf, hm_tree** out);
+
+/* ---------------------------------------------------------------------------
  * hm_eval_points -- u = ~V_h t (Section 5, Eq. (vector_eq) with W_h u = 0):
  * the displacement at the points of an evaluation operator for densities t.
  *   t      device, nrhs rows of 3M float64 (dof 3j + b, original triangle order)

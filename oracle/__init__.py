@@ -97,6 +97,11 @@ def _L():
                 "or_kelvin_points_matvec": (None, [P, P, I64, D, D, P, I64, P, I64, P]),
                 "or_scalar_points": (None, [P, P, I64, P, I64, P]),
                 "or_dl_entry": (None, [P, P, P, ctypes.c_int, P]),
+                "or_vpart_create": (P, [P, I64, P, I64, I64, I64, D]),
+                "or_vpart_sizes": (None, [P, P]),
+                "or_vpart_tree": (None, [P, P, P, P]),
+                "or_vpart_blocks": (None, [P, P, P]),
+                "or_vpart_free": (None, [P]),
                 "or_dl_dense": (None, [P, I64, P, I64, P]),
                 "or_hmat_free": (None, [P]),
                 "or_hmat_sizes": (None, [P, P]),
@@ -808,3 +813,30 @@ def double_layer_dense(V, T, E: float, nu: float) -> np.ndarray:
     for a in range(3):
         VDT[a::3, :] = VD @ Th[a::3, :]
     return K - VDT + (E / (1.0 + nu)) * (Vh @ Th)
+
+
+class VertexPartition:
+    """The block partition of the double layer's K_Delta (Eq. (Kh)): rows the
+    triangle tree (``HMatrix``'s), columns a tree of the vertices whose boxes
+    are the unions of the vertices' stars (the supports of their hat
+    functions), Eq. (adm) with eta."""
+
+    def __init__(self, V, T, leaf: int, leaf_v: int, eta: float):
+        self.V, self.T = _f64(V), _i32(T)
+        self._h = _L().or_vpart_create(_p(self.V), self.V.shape[0], _p(self.T), self.T.shape[0], leaf, leaf_v, eta)
+        s = np.zeros(4, dtype=np.int64)
+        _L().or_vpart_sizes(self._h, _p(s))
+        self.nnodes, self.nadm, self.nnear, self.nv = map(int, s)
+        self.perm = np.zeros(self.nv, dtype=np.int64)
+        self.nodes = np.zeros((self.nnodes, 5), dtype=np.int64)
+        self.boxes = np.zeros((self.nnodes, 6))
+        _L().or_vpart_tree(self._h, _p(self.perm), _p(self.nodes), _p(self.boxes))
+        self.adm = np.zeros((self.nadm, 2), dtype=np.int64)
+        self.near = np.zeros((self.nnear, 2), dtype=np.int64)
+        _L().or_vpart_blocks(self._h, _p(self.adm), _p(self.near))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _L().or_vpart_free(h)
+            self._h = None

@@ -524,6 +524,7 @@ typedef struct {
     or_node* nodes;
     int64_t nn;
     sort_item* tmp;
+    const double* B;  /* without T: a box per item (min xyz, max xyz), else the item is a point */
 } tree_ctx;
 
 static int64_t build_node(tree_ctx* tc, int64_t lo, int64_t hi, int32_t level)
@@ -540,11 +541,13 @@ static int64_t build_node(tree_ctx* tc, int64_t lo, int64_t hi, int32_t level)
     }
     for (int64_t p = lo; p < hi; ++p) {
         if (!tc->T) {
-            /* a tree of points: the box of the points themselves */
+            /* a tree of points: the box of the points themselves; with item
+             * boxes (the supports of hat functions) their union */
             for (int k = 0; k < 3; ++k) {
-                double v = tc->C[3 * tc->perm[p] + k];
-                if (v < nd->bmin[k]) nd->bmin[k] = v;
-                if (v > nd->bmax[k]) nd->bmax[k] = v;
+                double lo = tc->B ? tc->B[6 * tc->perm[p] + k] : tc->C[3 * tc->perm[p] + k];
+                double hi = tc->B ? tc->B[6 * tc->perm[p] + 3 + k] : tc->C[3 * tc->perm[p] + k];
+                if (lo < nd->bmin[k]) nd->bmin[k] = lo;
+                if (hi > nd->bmax[k]) nd->bmax[k] = hi;
             }
             continue;
         }
@@ -1076,6 +1079,119 @@ void or_hmat_tree(const void* hp, int64_t* perm, int64_t* nodes5, double* boxes6
 {
     const or_hmat* h = (const or_hmat*)hp;
     export_tree(h->nodes, h->nnodes, h->perm, h->M, perm, nodes5, boxes6);
+}
+
+/* ------------------------------------------------------------------------ */
+/* The partition of the double layer's K_Delta (Eq. (Kh)): rows are the      */
+/* triangles (collocation points), columns the vertices (hat functions)       */
+/* ------------------------------------------------------------------------ */
+/* The vertices are clustered by the triangles' rule (longest axis of the box
+ * of the vertex coordinates, median of (coordinate, id), first son
+ * floor(n/2), leaves of at most leaf_v); a cluster's box is the union of its
+ * vertices' stars (the boxes of all triangles holding the vertex: the support
+ * of its hat function), so that Eq. (adm) keeps every admissible block away
+ * from the kernel's singularity. */
+typedef struct {
+    int64_t M, nv;
+    int64_t* tperm;
+    or_node* tnodes;
+    int64_t ntn;
+    int64_t* vperm;
+    or_node* vnodes;
+    int64_t nvn;
+    block_lists bl;
+} or_vpart;
+
+void* or_vpart_create(const double* V, int64_t nv, const int32_t* T, int64_t M, int64_t leaf, int64_t leaf_v,
+                      double eta)
+{
+    or_vpart* h = (or_vpart*)calloc(1, sizeof(or_vpart));
+    h->M = M;
+    h->nv = nv;
+    double* C = (double*)malloc((size_t)M * 3 * sizeof(double));
+    or_centroids(V, T, M, C);
+    h->tperm = (int64_t*)malloc((size_t)M * sizeof(int64_t));
+    for (int64_t i = 0; i < M; ++i) h->tperm[i] = i;
+    h->tnodes = (or_node*)malloc((size_t)(2 * M + 1) * sizeof(or_node));
+    tree_ctx tc = {V, T, C, leaf, h->tperm, h->tnodes, 0, (sort_item*)malloc((size_t)M * sizeof(sort_item)), NULL};
+    build_node(&tc, 0, M, 0);
+    free(tc.tmp);
+    h->ntn = tc.nn;
+    /* stars: the box of every triangle, merged into its three vertices */
+    double* B = (double*)malloc((size_t)nv * 6 * sizeof(double));
+    for (int64_t p = 0; p < nv; ++p)
+        for (int k = 0; k < 3; ++k) {
+            B[6 * p + k] = INFINITY;
+            B[6 * p + 3 + k] = -INFINITY;
+        }
+    for (int64_t i = 0; i < M; ++i) {
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int c = 0; c < 3; ++c)
+            for (int k = 0; k < 3; ++k) {
+                double v = V[3 * T[3 * i + c] + k];
+                if (v < lo[k]) lo[k] = v;
+                if (v > hi[k]) hi[k] = v;
+            }
+        for (int c = 0; c < 3; ++c) {
+            int64_t p = T[3 * i + c];
+            for (int k = 0; k < 3; ++k) {
+                if (lo[k] < B[6 * p + k]) B[6 * p + k] = lo[k];
+                if (hi[k] > B[6 * p + 3 + k]) B[6 * p + 3 + k] = hi[k];
+            }
+        }
+    }
+    h->vperm = (int64_t*)malloc((size_t)nv * sizeof(int64_t));
+    for (int64_t p = 0; p < nv; ++p) h->vperm[p] = p;
+    h->vnodes = (or_node*)malloc((size_t)(2 * nv + 1) * sizeof(or_node));
+    tree_ctx tv = {NULL, NULL, V, leaf_v, h->vperm, h->vnodes, 0, (sort_item*)malloc((size_t)nv * sizeof(sort_item)), B};
+    build_node(&tv, 0, nv, 0);
+    free(tv.tmp);
+    h->nvn = tv.nn;
+    partition(h->tnodes, h->vnodes, 0, 0, eta, &h->bl);
+    free(B);
+    free(C);
+    return h;
+}
+
+void or_vpart_sizes(const void* hp, int64_t* out4)
+{
+    const or_vpart* h = (const or_vpart*)hp;
+    out4[0] = h->nvn;
+    out4[1] = h->bl.nadm;
+    out4[2] = h->bl.nnear;
+    out4[3] = h->nv;
+}
+
+void or_vpart_tree(const void* hp, int64_t* perm, int64_t* nodes5, double* boxes6)
+{
+    const or_vpart* h = (const or_vpart*)hp;
+    export_tree(h->vnodes, h->nvn, h->vperm, h->nv, perm, nodes5, boxes6);
+}
+
+void or_vpart_blocks(const void* hp, int64_t* adm, int64_t* nearb)
+{
+    const or_vpart* h = (const or_vpart*)hp;
+    for (int64_t b = 0; b < h->bl.nadm; ++b) {
+        adm[2 * b] = h->bl.adm[b].t;
+        adm[2 * b + 1] = h->bl.adm[b].s;
+    }
+    for (int64_t b = 0; b < h->bl.nnear; ++b) {
+        nearb[2 * b] = h->bl.near[b].t;
+        nearb[2 * b + 1] = h->bl.near[b].s;
+    }
+}
+
+void or_vpart_free(void* hp)
+{
+    or_vpart* h = (or_vpart*)hp;
+    if (!h) return;
+    free(h->bl.adm);
+    free(h->bl.near);
+    free(h->tperm);
+    free(h->tnodes);
+    free(h->vperm);
+    free(h->vnodes);
+    free(h);
 }
 
 /* block lists as node ids: adm[2*b], adm[2*b+1] = (t, s) */

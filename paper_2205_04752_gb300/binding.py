@@ -33,6 +33,7 @@ SYMBOLS = (
     "hm_batch_set_schedule", "hm_batch_get_schedule", "hm_batch_check", "hm_batch_destroy",
     "hm_compact", "hm_footprint", "hm_server_create", "hm_server_footprint", "hm_server_run",
     "hm_server_destroy", "hm_amvm", "hm_build_point_tree", "hm_eval_points", "hm_baca",
+    "hm_build_vertex_tree",
 )
 
 
@@ -155,6 +156,7 @@ def load():
         "hm_tree_export": (ctypes.c_int, [P, P, P, P, P]),
         "hm_tree_destroy": (None, [P]),
         "hm_build_point_tree": (ctypes.c_int, [P, P, I64, I32, ctypes.POINTER(P)]),
+        "hm_build_vertex_tree": (ctypes.c_int, [P, I32, ctypes.POINTER(P)]),
         "hm_eval_points": (ctypes.c_int, [P, P, P, I32, I32, P]),
         "hm_aca_assemble": (ctypes.c_int, [P, ctypes.POINTER(_Params), ctypes.POINTER(_Allocator),
                                            P, ctypes.POINTER(P)]),
@@ -278,6 +280,28 @@ class PointTree(ClusterTree):
 
 def build_point_tree(surface: ClusterTree, points, leaf: int) -> PointTree:
     return PointTree(surface, points, leaf)
+
+
+class VertexTree(ClusterTree):
+    """Columns of the double layer's K_Delta (Eq. (Kh)): the cluster tree of
+    the mesh vertices with star boxes and the partition (triangle tree of
+    ``surface``) x (vertex tree), ``hm_build_vertex_tree``.  ``M`` counts the
+    vertices, ``M_src`` the triangles.  (Its device assembly is not built.)"""
+
+    def __init__(self, surface: ClusterTree, leaf: int):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.hm_build_vertex_tree(surface._h, int(leaf), ctypes.byref(h)))
+        self._h = h
+        c = np.zeros(6, dtype=np.int64)
+        _check(lib.hm_tree_sizes(self._h, _ptr(c)))
+        self.M, self.nnodes, self.nadm, self.nnear, self.nleaves, self.depth = map(int, c)
+        self.leaf, self.eta = int(leaf), surface.eta
+        self.M_src = surface.M
+
+
+def build_vertex_tree(surface: ClusterTree, leaf: int) -> VertexTree:
+    return VertexTree(surface, leaf)
 
 
 def _torch_allocator(device: int):

@@ -947,7 +947,7 @@ int assemble_points_device(const hm_tree& tr, hm_matrix& H);
 
 int assemble_device(const hm_tree& tr, hm_matrix& H)
 {
-    if (tr.src) return assemble_points_device(tr, H);
+    if (tr.kind == 1) return assemble_points_device(tr, H);
     cudaStream_t s = H.alloc.stream;
     const int64_t M = tr.M;
     H.M = M;
@@ -1729,6 +1729,8 @@ extern "C" int hm_aca_assemble(const hm_tree* tree, const hm_params* prm, const 
     if (prm->max_rhs < 0 || prm->max_rhs > 64) return fail(HM_EINVAL, "hm_aca_assemble: max_rhs must lie in 0..64");
     if (prm->flags & ~(HM_DEFER_FP64 | HM_DEFER_ACA))
         return fail(HM_EINVAL, "hm_aca_assemble: unknown flags 0x%x", prm->flags);
+    if (tree->kind == 2)
+        return fail(HM_EINVAL, "hm_aca_assemble: the double layer's device assembly is not built (vertex tree)");
     hm_matrix* H = new (std::nothrow) hm_matrix();
     if (!H) return fail(HM_ENOMEM, "hm_aca_assemble: out of host memory");
     H->prm = *prm;

@@ -110,11 +110,14 @@ struct TreeBuilder {
             }
             for (int64_t p = lo; p < hi; ++p) {
                 if (tr.T.empty()) {
-                    // a tree of points: the box of the points themselves
+                    // a tree of points: the box of the points themselves; of
+                    // vertices: the union of their stars
                     for (int k = 0; k < 3; ++k) {
-                        double v = tr.coll[3 * tr.perm[p] + k];
-                        nd.bmin[k] = std::min(nd.bmin[k], v);
-                        nd.bmax[k] = std::max(nd.bmax[k], v);
+                        const bool star = !tr.ibox.empty();
+                        double lo = star ? tr.ibox[6 * tr.perm[p] + k] : tr.coll[3 * tr.perm[p] + k];
+                        double hi = star ? tr.ibox[6 * tr.perm[p] + 3 + k] : tr.coll[3 * tr.perm[p] + k];
+                        nd.bmin[k] = std::min(nd.bmin[k], lo);
+                        nd.bmax[k] = std::max(nd.bmax[k], hi);
                     }
                     continue;
                 }
@@ -302,7 +305,7 @@ int hm_build_point_tree(const hm_tree* surface, const double* pts, int64_t npts,
     if (!out) return fail(HM_EINVAL, "hm_build_point_tree: out is NULL");
     *out = nullptr;
     if (!surface || !pts) return fail(HM_EINVAL, "hm_build_point_tree: NULL argument");
-    if (surface->src) return fail(HM_EINVAL, "hm_build_point_tree: `surface` must be a triangle tree");
+    if (surface->kind != 0) return fail(HM_EINVAL, "hm_build_point_tree: `surface` must be a triangle tree");
     if (npts < 1) return fail(HM_EINVAL, "hm_build_point_tree: no points");
     if (npts > (int64_t)INT32_MAX / 4) return fail(HM_EINVAL, "hm_build_point_tree: too many points");
     if (leaf < 1 || leaf > HM_MAX_LEAF)
@@ -316,6 +319,7 @@ int hm_build_point_tree(const hm_tree* surface, const double* pts, int64_t npts,
         src->adm.clear();
         src->near_blocks.clear();
         tr->M = npts;
+        tr->kind = 1;
         tr->leaf = leaf;
         tr->eta = surface->eta;
         tr->coll.assign(pts, pts + 3 * npts);
@@ -334,6 +338,74 @@ int hm_build_point_tree(const hm_tree* surface, const double* pts, int64_t npts,
     } catch (const std::bad_alloc&) {
         delete tr;
         return fail(HM_ENOMEM, "hm_build_point_tree: out of host memory");
+    }
+    *out = tr;
+    return HM_OK;
+}
+
+int hm_build_vertex_tree(const hm_tree* surface, int32_t leaf, hm_tree** out)
+{
+    if (!out) return fail(HM_EINVAL, "hm_build_vertex_tree: out is NULL");
+    *out = nullptr;
+    if (!surface) return fail(HM_EINVAL, "hm_build_vertex_tree: NULL surface");
+    if (surface->kind != 0) return fail(HM_EINVAL, "hm_build_vertex_tree: `surface` must be a triangle tree");
+    if (leaf < 1 || leaf > HM_MAX_LEAF)
+        return fail(HM_EINVAL, "hm_build_vertex_tree: leaf must lie in 1..%d", HM_MAX_LEAF);
+    hm_tree* tr = new (std::nothrow) hm_tree();
+    if (!tr) return fail(HM_ENOMEM, "hm_build_vertex_tree: out of host memory");
+    try {
+        const int64_t nv = surface->nv, M = surface->M;
+        auto src = std::make_shared<hm_tree>(*surface);
+        src->adm.clear();
+        src->near_blocks.clear();
+        tr->M = nv;
+        tr->kind = 2;
+        tr->leaf = leaf;
+        tr->eta = surface->eta;
+        tr->coll = surface->V;
+        // stars: the box of every triangle merged into its three vertices
+        tr->ibox.resize((size_t)(6 * nv));
+        for (int64_t p = 0; p < nv; ++p)
+            for (int k = 0; k < 3; ++k) {
+                tr->ibox[(size_t)(6 * p + k)] = INFINITY;
+                tr->ibox[(size_t)(6 * p + 3 + k)] = -INFINITY;
+            }
+        for (int64_t i = 0; i < M; ++i) {
+            double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+            for (int c = 0; c < 3; ++c)
+                for (int k = 0; k < 3; ++k) {
+                    const double v = surface->V[3 * (size_t)surface->T[(size_t)(3 * i + c)] + k];
+                    lo[k] = std::min(lo[k], v);
+                    hi[k] = std::max(hi[k], v);
+                }
+            for (int c = 0; c < 3; ++c) {
+                const int64_t p = surface->T[(size_t)(3 * i + c)];
+                for (int k = 0; k < 3; ++k) {
+                    tr->ibox[(size_t)(6 * p + k)] = std::min(tr->ibox[(size_t)(6 * p + k)], lo[k]);
+                    tr->ibox[(size_t)(6 * p + 3 + k)] = std::max(tr->ibox[(size_t)(6 * p + 3 + k)], hi[k]);
+                }
+            }
+        }
+        for (int64_t p = 0; p < nv; ++p)
+            if (!(tr->ibox[(size_t)(6 * p)] <= tr->ibox[(size_t)(6 * p + 3)])) {
+                delete tr;
+                return fail(HM_EINVAL, "hm_build_vertex_tree: vertex %lld belongs to no triangle", (long long)p);
+            }
+        tr->perm.resize((size_t)nv);
+        for (int64_t p = 0; p < nv; ++p) tr->perm[(size_t)p] = p;
+        tr->nodes.reserve((size_t)(2 * nv));
+        TreeBuilder tb{*tr, {}};
+        tb.build(0, nv, 0);
+        build_partition(*tr, src->nodes, tr->nodes);
+        for (size_t n = 0; n < tr->nodes.size(); ++n)
+            if (tr->nodes[n].son[0] < 0) tr->leaves.push_back((int64_t)n);
+        std::sort(tr->leaves.begin(), tr->leaves.end(), [&](int64_t a, int64_t b) {
+            return tr->nodes[(size_t)a].lo < tr->nodes[(size_t)b].lo;
+        });
+        tr->src = std::move(src);
+    } catch (const std::bad_alloc&) {
+        delete tr;
+        return fail(HM_ENOMEM, "hm_build_vertex_tree: out of host memory");
     }
     *out = tr;
     return HM_OK;

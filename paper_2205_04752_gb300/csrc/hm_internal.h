@@ -47,10 +47,17 @@ struct hm_tree {
     std::vector<hm::Node> nodes;  // pre-order
     std::vector<std::array<int64_t, 2>> adm, near_blocks;  // (row node, col node)
     std::vector<int64_t> leaves;  // leaf node ids in cluster order
-    // a tree of points (hm_build_point_tree): `coll` holds the points, V and T
-    // are empty, and the partition pairs its nodes (rows) with the nodes of
-    // the triangle tree `src` (columns) -- the evaluation operator of
-    // Section 5, Eq. (vector_eq)
+    // kind 0: a triangle tree (rows and columns the triangles);
+    // kind 1, a tree of points (hm_build_point_tree): `coll` holds the points,
+    //   V and T are empty, and the partition pairs its nodes (rows) with the
+    //   nodes of the triangle tree `src` (columns) -- the evaluation operator
+    //   of Section 5, Eq. (vector_eq);
+    // kind 2, a tree of vertices (hm_build_vertex_tree): `coll` holds the
+    //   vertex coordinates, `ibox` each vertex's star box (6 values), and the
+    //   partition pairs the nodes of the triangle tree `src` (rows) with its
+    //   nodes (columns) -- the double layer's K_Delta of Eq. (Kh)
+    int32_t kind = 0;
+    std::vector<double> ibox;
     std::shared_ptr<const hm_tree> src;
 };
 

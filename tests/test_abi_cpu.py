@@ -172,3 +172,46 @@ def test_point_tree_and_partition_match_oracle_level6():
     np.testing.assert_array_equal(adm, Ho.adm)
     np.testing.assert_array_equal(near, Ho.near)
     assert pt.nadm == 121407 and pt.nnear == 30638
+
+
+@pytest.mark.parametrize("mesh,leaf,leaf_v", [("ico3", 32, 24), ("ico2", 16, 7), ("cube6", 16, 16),
+                                              ("ico4", 64, 64), ("ico1", 8, 336)])
+def test_vertex_tree_and_partition_match_oracle(mesh, leaf, leaf_v):
+    """The columns of the double layer's K_Delta (Eq. (Kh)): the vertex tree
+    with star boxes and the partition triangles x vertices equal the
+    oracle's bit for bit; the blocks tile the M x nv rectangle, every vertex
+    box holds the stars of its vertices, Eq. (adm) holds on every admissible
+    block; the device assembly refuses the tree (not built)."""
+    V, T = inputs.cube_surface(6) if mesh == "cube6" else inputs.icosphere(int(mesh[3:]))
+    tr = binding.build_cluster_tree(V, T, leaf, 0.8)
+    vt = binding.build_vertex_tree(tr, leaf_v)
+    perm, nodes, adm, near = vt.export()
+    op = oracle.VertexPartition(V, T, leaf, leaf_v, 0.8)
+    np.testing.assert_array_equal(perm, op.perm)
+    np.testing.assert_array_equal(nodes, op.nodes)
+    np.testing.assert_array_equal(adm, op.adm)
+    np.testing.assert_array_equal(near, op.near)
+    assert vt.M == len(V) and vt.M_src == len(T)
+    _, tnodes, _, _ = tr.export()
+    cover = np.zeros((len(T), len(V)), dtype=np.int32)
+    for (t, s) in np.concatenate([adm, near]):
+        cover[tnodes[t, 0]:tnodes[t, 1], nodes[s, 0]:nodes[s, 1]] += 1
+    assert np.all(cover == 1)
+    for n in range(op.nnodes):
+        lo, hi = nodes[n, 0], nodes[n, 1]
+        verts = set(perm[lo:hi].tolist())
+        tris = [i for i in range(len(T)) if verts & set(T[i].tolist())]
+        pts = V[T[tris].reshape(-1)]
+        assert np.all(op.boxes[n, :3] <= pts.min(0)) and np.all(op.boxes[n, 3:] >= pts.max(0))
+        if n > 40:
+            break
+    # refused before any device work (the raw ABI: no GPU needed)
+    prm = binding._Params(1.0, 0.3, 1e-4, 0.8, 0, 0, 0, 0)
+    out = ctypes.c_void_p()
+    lib = binding.load()
+    assert lib.hm_aca_assemble(vt._h, ctypes.byref(prm), None, None, ctypes.byref(out)) == binding.HM_EINVAL
+    assert b"vertex tree" in lib.hm_last_error()
+    with pytest.raises(binding.HMError):
+        binding.build_point_tree(vt, inputs.ball_points(4, 0.5, 1), 8)
+    with pytest.raises(binding.HMError):
+        binding.build_vertex_tree(vt, 8)
