@@ -215,3 +215,15 @@ def test_vertex_tree_and_partition_match_oracle(mesh, leaf, leaf_v):
         binding.build_point_tree(vt, inputs.ball_points(4, 0.5, 1), 8)
     with pytest.raises(binding.HMError):
         binding.build_vertex_tree(vt, 8)
+
+
+def test_bench_script_parses_its_arguments():
+    """bench.py (run by the round's measurement) imports and parses its flags
+    on any host; the work itself needs a GPU."""
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--help"], capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 0, r.stderr
+    for flag in ("--no-points", "--no-baca", "--points-minimal", "--impl"):
+        assert flag in r.stdout
