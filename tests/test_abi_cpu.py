@@ -218,8 +218,8 @@ def test_vertex_tree_and_partition_match_oracle(mesh, leaf, leaf_v):
 
 
 def test_bench_script_parses_its_arguments():
-    """bench.py (run by the round's measurement) imports and parses its flags
-    on any host; the work itself needs a GPU."""
+    """bench.py imports and parses its flags on any host; the work itself
+    needs a GPU."""
     import subprocess
     import sys
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--help"], capture_output=True, text=True,
