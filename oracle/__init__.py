@@ -840,3 +840,41 @@ class VertexPartition:
         if h:
             _L().or_vpart_free(h)
             self._h = None
+
+
+class DoubleLayerHMatrix:
+    """The H-matrix of the double layer's K_Delta (Eq. (Kh)) on the partition
+    of ``VertexPartition``: Algorithm 1 (``aca_dense``) on every admissible
+    block of the dense K_Delta (``dl_dense``; small meshes), near blocks
+    dense.  Rows and columns in cluster order (the triangle tree of
+    ``HMatrix`` and the vertex tree)."""
+
+    def __init__(self, V, T, leaf: int, leaf_v: int, eta: float, eps: float, eta_stop: float = 0.8):
+        self.V, self.T = _f64(V), _i32(T)
+        self.vp = VertexPartition(self.V, self.T, leaf, leaf_v, eta)
+        self.tri = HMatrix(self.V, self.T, leaf, eta, eps)  # its triangle tree (rows)
+        KD = dl_dense(self.V, self.T)
+        tn, tp = self.tri.nodes, self.tri.perm
+        vn, vperm = self.vp.nodes, self.vp.perm
+        self.KDc = KD[tp][:, vperm]  # cluster order
+        self.factors = []
+        for (t, s) in self.vp.adm:
+            blk = self.KDc[tn[t, 0]:tn[t, 1], vn[s, 0]:vn[s, 1]]
+            self.factors.append(aca_dense(blk, eps, eta_stop))
+        self.near = [self.KDc[tn[t, 0]:tn[t, 1], vn[s, 0]:vn[s, 1]].copy() for (t, s) in self.vp.near]
+
+    def matvec(self, u) -> np.ndarray:
+        """y = K_Delta u (u over the vertices, y over the triangles, original
+        order): U (V^T u_s) per admissible block, dense near blocks."""
+        u = _f64(u).reshape(-1)
+        tn, tp = self.tri.nodes, self.tri.perm
+        vn, vperm = self.vp.nodes, self.vp.perm
+        uc = u[vperm]
+        yc = np.zeros(self.T.shape[0])
+        for (t, s), f in zip(self.vp.adm, self.factors):
+            yc[tn[t, 0]:tn[t, 1]] += f["U"] @ (f["V"].T @ uc[vn[s, 0]:vn[s, 1]])
+        for (t, s), Nb in zip(self.vp.near, self.near):
+            yc[tn[t, 0]:tn[t, 1]] += Nb @ uc[vn[s, 0]:vn[s, 1]]
+        y = np.zeros_like(yc)
+        y[tp] = yc
+        return y

@@ -134,3 +134,34 @@ def test_rigid_motions_are_mapped_to_minus_half(level):
                Kd - VDT,                                       # V_h T_h dropped
                Kd - VDT + 0.5 * (E / (1 + NU)) * (Vh @ Th)):    # mu instead of 2 mu
         assert np.abs((Kw @ u).reshape(M, 3) - ref).max() > 0.5 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("eps,tol", [(1e-4, 1e-4), (1e-8, 1e-7)])
+def test_double_layer_hmatrix_product(eps, tol):
+    """The H-matrix of K_Delta on the vertex partition (Algorithm 1 per
+    admissible block, near blocks dense) reproduces the dense K_Delta within
+    the ACA accuracy, keeps the solid-angle row sums, and every admissible
+    block's ACA meets its bound within 2 eps (and compresses at eps 1e-4)."""
+    V, T = inputs.icosphere(3)
+    Hd = oracle.DoubleLayerHMatrix(V, T, 32, 24, 0.8, eps)
+    KD = oracle.dl_dense(V, T)
+    u = inputs.uniform_rhs(len(V), 3)[0]
+    y = Hd.matvec(u)
+    yd = KD @ u
+    assert np.linalg.norm(y - yd) <= tol * np.linalg.norm(yd)
+    assert np.abs(Hd.matvec(np.ones(len(V))) + 0.5).max() <= 1e-6 + 10 * eps
+    worst, stored = 0.0, 0
+    tn, vn = Hd.tri.nodes, Hd.vp.nodes
+    for (t, s), f in zip(Hd.vp.adm, Hd.factors):
+        blk = Hd.KDc[tn[t, 0]:tn[t, 1], vn[s, 0]:vn[s, 1]]
+        nb = np.linalg.norm(blk)
+        if nb > 0:
+            worst = max(worst, np.linalg.norm(blk - f["U"] @ f["V"].T) / nb)
+        stored += f["rank"] * (blk.shape[0] + blk.shape[1])
+    assert worst <= 2 * eps
+    far = sum((tn[t, 1] - tn[t, 0]) * (vn[s, 1] - vn[s, 0]) for (t, s) in Hd.vp.adm)
+    # low rank never costs more than twice dense (k <= min(m, n)); at eps 1e-4
+    # the level-3 far field compresses
+    assert stored <= 2 * far
+    if eps >= 1e-4:
+        assert stored < far
