@@ -483,7 +483,7 @@ typedef struct {
     int64_t marked_total;  /* blocks marked over all steps */
 } hm_amvm_info;
 
-int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_amvm_params* p, hm_amvm_info* info,
+int hm_amvm(hm_matrix* H, const double* x, double* y, const hm_amvm_params* p, hm_amvm_info* info,
             double* gamma_hist, double* gamma_rest_hist, int32_t hist_cap, int32_t* block_ranks, void* stream);
 
 /* ---------------------------------------------------------------------------
@@ -560,7 +560,7 @@ typedef struct {
     int32_t marked;     /* blocks refined after it */
 } hm_baca_step;
 
-int hm_baca(const hm_matrix* H, const double* b, double* t, const hm_baca_params* p, hm_baca_info* info,
+int hm_baca(hm_matrix* H, const double* b, double* t, const hm_baca_params* p, hm_baca_info* info,
             hm_baca_step* hist, int32_t hist_cap, int32_t* block_ranks, void* stream);
 
 /* Status of the asynchronous products of H: HM_ETIMEOUT if a bounded device

@@ -171,7 +171,7 @@ using namespace hm;
 
 using namespace hm;
 
-extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_amvm_params* prm,
+extern "C" int hm_amvm(hm_matrix* H, const double* x, double* y, const hm_amvm_params* prm,
                        hm_amvm_info* info, double* gamma_hist, double* gamma_rest_hist, int32_t hist_cap,
                        int32_t* block_ranks, void* stream)
 {
@@ -192,7 +192,7 @@ extern "C" int hm_amvm(const hm_matrix* H, const double* x, double* y, const hm_
                     max_iter);
     if (hist_cap < 0) return fail(HM_EINVAL, "hm_amvm: hist_cap < 0");
     cudaStream_t s = (cudaStream_t)stream;
-    hm_matrix& Hm = const_cast<hm_matrix&>(*H);  // on-demand ACA allocates through the matrix's allocator
+    hm_matrix& Hm = *H;  // on-demand ACA allocates through the matrix's allocator
     const cudaStream_t saved_stream = Hm.alloc.stream;
     Hm.alloc.stream = s;
     struct Restore {

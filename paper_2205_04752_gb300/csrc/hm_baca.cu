@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(256) baca_blocknorm_kernel(const int64_t* __re
 
 using namespace hm;
 
-extern "C" int hm_baca(const hm_matrix* H, const double* b, double* x, const hm_baca_params* prm, hm_baca_info* info,
+extern "C" int hm_baca(hm_matrix* H, const double* b, double* x, const hm_baca_params* prm, hm_baca_info* info,
                        hm_baca_step* hist, int32_t hist_cap, int32_t* block_ranks, void* stream)
 {
     if (!H || !b || !x || !prm) return fail(HM_EINVAL, "hm_baca: NULL argument");
@@ -126,7 +126,7 @@ extern "C" int hm_baca(const hm_matrix* H, const double* b, double* x, const hm_
                     r0, look, kAmvmMaxCross, m);
     if (hist_cap < 0) return fail(HM_EINVAL, "hm_baca: hist_cap < 0");
     cudaStream_t s = (cudaStream_t)stream;
-    hm_matrix& Hm = const_cast<hm_matrix&>(*H);  // the product tables are built once and kept
+    hm_matrix& Hm = *H;  // the product tables are built once and kept
     const cudaStream_t saved_stream = Hm.alloc.stream;
     Hm.alloc.stream = s;
     struct Restore {
