@@ -7,7 +7,7 @@ One step = one H-matrix-vector product y = V_h x (gather, far-field forward,
 per-leaf product with the near field).  The H-matrix (GBs) is far larger than
 L2, so every step streams it from HBM; no L2 flush is needed.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--form fp16|fp32|...]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--form i16|fp16|fp32|...]
   python bench.py --impl reference     # the FP64 CPU oracle on the host cores
 
 Besides the headline the JSON line carries, as context: the FP64 form, 32
@@ -45,16 +45,30 @@ if ROOT not in sys.path:
 WORKLOAD = dict(workload="lame-single-layer-icosphere-L6", mesh="icosphere level 6",
                 triangles=81920, dofs=245760, E=1.0, nu=0.3, leaf=64, eta=0.8, aca_eps=1e-4,
                 nrhs=1)
-# DRAM bytes per launch of the dominant kernel, from one ncu capture on the
-# benchmark workload (profiles/leaf_stream_L6_fp16_dram.md); reported only
-# while the kernel's source file is the one that was measured
-MEASURED_TRAFFIC = {"kernel": "leaf_near", "form": "fp16", "level": 6,
-                    "source": "paper_2205_04752_gb300/csrc/hm_stream.cuh",
-                    "sha256": "f10972a4fc6e13fc245b099f9095295a519de482ff4f6d487dfc343fc0da963c",
-                    "bytes": 5468434432 + 3316224}
+# DRAM bytes per launch of the dominant kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) on the benchmark workload.
+# Reported only while every source file of the library is the one that was
+# measured (sha256 over csrc/ in name order): any change to a kernel or to
+# the layout code nulls it until it is measured again.
+MEASURED_TRAFFIC = {"kernel": "leaf_near", "form": "i16", "level": 6,
+                    "sources_sha256": None,
+                    "bytes": None}
 METRIC = "H-matvecs/s"
 UNIT = "matvec/s"
 MEAS_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def _sources_sha256():
+    """sha256 over the library's source files (csrc/, in name order)."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2205_04752_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
 
 
 def _peaks():
@@ -123,61 +137,80 @@ class ClockSampler:
 # CPU baseline: the oracle on a bounded sample of the same workload
 # --------------------------------------------------------------------------
 
-class OracleSample:
-    """The oracle's H-matrix-vector product over a seeded sample of the blocks
-    of the same workload (a fraction `frac` of the admissible and of the near
-    blocks, ACA-assembled by the oracle once, untimed), scaled to one full
-    product by the oracle's own FP64 storage bytes (the product streams every
-    stored value once)."""
+def _cpu_model():
+    """Host CPU model name and logical CPU count, for the baseline's record."""
+    name = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name:"):
+                name = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not name:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith("model name"):
+                        name = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+    return name or platform.machine(), os.cpu_count()
 
-    def __init__(self, V, T, frac=0.01, seed=0):
+
+class OracleFull:
+    """The oracle's H-matrix of the whole workload -- its own cluster tree,
+    partition, near-field quadrature and ACA (FP64, OpenMP over blocks) --
+    assembled once, and its full FP64 H-matrix-vector product.  Nothing is
+    sampled or scaled: one step is one complete product."""
+
+    def __init__(self, V, T):
         import oracle
         w = WORKLOAD
         self.oracle = oracle
-        self.H = H = oracle.HMatrix(V, T, w["leaf"], w["eta"], w["aca_eps"])
-        rng = np.random.default_rng(seed)
-        self.na = max(1, int(round(frac * H.nadm)))
-        self.nn = max(1, int(round(frac * H.nnear)))
-        self.adm = np.sort(rng.choice(H.nadm, self.na, replace=False))
-        self.near = np.sort(rng.choice(H.nnear, self.nn, replace=False))
-        t0 = time.time()
-        H.assemble(adm_ids=self.adm, near_ids=self.near)
-        self.t_asm = time.time() - t0
-        ra = H.ranges(H.adm)
-        rn = H.ranges(H.near)
-        ma, na_ = ra[:, 1] - ra[:, 0], ra[:, 3] - ra[:, 2]
-        near_pairs = (rn[:, 1] - rn[:, 0]) * (rn[:, 3] - rn[:, 2])
-        # the oracle stores 7 values per near pair
-        near_all = float(np.sum(near_pairs)) * 7 * 8
-        near_s = float(np.sum(near_pairs[self.near])) * 7 * 8
-        ranks_s = np.array([[H.rank(b, k) for k in range(7)] for b in self.adm])
-        far_s = float(np.sum(ranks_s.sum(1) * (ma[self.adm] + na_[self.adm]))) * 8
-        # far field of all blocks at the sample's mean total rank per block
-        far_all = float(np.sum((ma + na_) * ranks_s.sum(1).mean())) * 8
-        self.scale = (far_all + near_all) / (far_s + near_s)
-        self.frac = frac
-        self.x = np.random.default_rng(1).uniform(-1, 1, (1, 3 * len(T)))
+        self.threads = oracle.num_threads()
+        t0 = time.perf_counter()
+        self.H = oracle.HMatrix(V, T, w["leaf"], w["eta"], w["aca_eps"])
+        self.H.assemble()
+        self.t_asm = time.perf_counter() - t0
+        from paper_2205_04752_gb300 import inputs
+        self.x = inputs.uniform_rhs(3 * len(T), 0)
 
     def step(self):
-        """Seconds of one full product, estimated from one timed sample product."""
+        """Seconds of one full product."""
         t0 = time.perf_counter()
-        self.H.matvec(WORKLOAD["E"], WORKLOAD["nu"], self.x, adm_ids=self.adm,
-                      near_ids=self.near)
-        return (time.perf_counter() - t0) * self.scale
+        self.H.matvec(WORKLOAD["E"], WORKLOAD["nu"], self.x)
+        return time.perf_counter() - t0
 
-    def describe(self, t_sample_ms, reps):
-        return (f"{self.frac:.1%} of the admissible ({self.na}) and near ({self.nn}) blocks of "
-                f"the level-6 workload (seeded), oracle ACA assembly of the sample "
-                f"{self.t_asm:.1f} s (untimed), sample product {t_sample_ms:.1f} ms (median of "
-                f"{reps}), scaled to a full product by FP64 storage bytes x{self.scale:.1f}")
+    def median(self, reps, threads=None):
+        if threads:
+            self.oracle.set_num_threads(threads)
+        try:
+            return float(np.median([self.step() for _ in range(reps)]))
+        finally:
+            if threads:
+                self.oracle.set_num_threads(self.threads)
+
+    def describe(self, reps):
+        model, ncpu = _cpu_model()
+        return (f"the whole level-6 workload, no sampling: the oracle's own tree, partition, near field and "
+                f"ACA (FP64) assembled once in {self.t_asm:.1f} s on {self.threads} threads (not timed), then "
+                f"its full FP64 H-matrix-vector product, median of {reps}; host {model}, {ncpu} CPUs")
 
 
-def cpu_baseline(V, T, reps=3):
-    s = OracleSample(V, T)
-    ts = [s.step() for _ in range(reps)]
-    t = float(np.median(ts))
-    return {"value": 1.0 / t, "unit": UNIT, "cores": s.oracle.num_threads(), "kind": "oracle",
-            "sample": s.describe(t / s.scale * 1e3, reps)}
+def cpu_baseline(V, T, reps=5):
+    s = OracleFull(V, T)
+    s.step()  # warm-up (first touch of the factors)
+    t = s.median(reps)
+    t1 = s.median(reps, threads=1)
+    model, ncpu = _cpu_model()
+    return {"value": 1.0 / t, "unit": UNIT, "cores": s.threads, "kind": "oracle", "sample": s.describe(reps),
+            "one_core": {"value": 1.0 / t1, "unit": UNIT, "cores": 1, "ms_per_matvec": round(t1 * 1e3, 1)},
+            "ms_per_matvec": round(t * 1e3, 1), "assembly_s": round(s.t_asm, 1), "cpu_model": model,
+            "nproc": ncpu}
 
 
 # --------------------------------------------------------------------------
@@ -195,14 +228,15 @@ def run_reference(args):
         return 0
     from paper_2205_04752_gb300 import inputs
     V, T = inputs.icosphere(6)
-    smp = OracleSample(V, T)
+    ref = OracleFull(V, T)
     for _ in range(args.warmup):
-        smp.step()
-    ts = [smp.step() for _ in range(args.steps)]
+        ref.step()
+    ts = [ref.step() for _ in range(args.steps)]
     t = float(np.median(ts))
     v = 1.0 / t
-    info = {"value": v, "unit": UNIT, "cores": smp.oracle.num_threads(), "kind": "oracle",
-            "sample": smp.describe(t / smp.scale * 1e3, args.steps)}
+    model, ncpu = _cpu_model()
+    info = {"value": v, "unit": UNIT, "cores": ref.threads, "kind": "oracle", "sample": ref.describe(args.steps),
+            "assembly_s": round(ref.t_asm, 1), "cpu_model": model, "nproc": ncpu}
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -319,7 +353,7 @@ def run_ours(args):
     kms = kms[:3] / max(calls, 1)
     names = ["gather", "far_fwd", "leaf_near"]
     dom = int(np.argmax(kms))
-    wf = {"fp64": 8, "fp32": 4, "bf16": 2, "fp16": 2}[form]
+    wf = {"fp64": 8, "fp32": 4, "bf16": 2, "fp16": 2, "i16": 2}[form]
     wn = 8 if form == "fp64" else 4
     wa = 8 if form == "fp64" else 4
     # algorithmic bytes: every stored value once, the vectors once; U column
@@ -337,14 +371,9 @@ def run_ours(args):
     achieved = alg[names[dom]] / (kms[dom] * 1e-3) / 1e9
     traffic = None
     mt = MEASURED_TRAFFIC
-    try:
-        import hashlib
-        with open(os.path.join(ROOT, mt["source"]), "rb") as f:
-            same = hashlib.sha256(f.read()).hexdigest() == mt["sha256"]
-        if same and names[dom] == mt["kernel"] and form == mt["form"] and args.level == mt["level"]:
-            traffic = mt["bytes"]
-    except OSError:
-        pass
+    if (mt["bytes"] and names[dom] == mt["kernel"] and form == mt["form"] and args.level == mt["level"]
+            and _sources_sha256() == mt["sources_sha256"]):
+        traffic = mt["bytes"]
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": names[dom],
                 "peak_kind": peak_kind,
@@ -361,6 +390,7 @@ def run_ours(args):
     e2e = {"value": ws * 1e3 * args.steps / ms_e2e, "unit": UNIT,
            "h2d_bytes_per_step": 3 * M * 8, "d2h_bytes_per_step": 3 * M * 8}
 
+    failed = []  # contexts that ended in a device failure
     # ---- context: FP64 plain form and 32 right-hand sides
     ms64 = timed(lambda: binding.hmatvec(H, x, y64, "fp64"), max(2, args.steps // 4), 1) \
         / max(2, args.steps // 4)
@@ -368,6 +398,30 @@ def run_ours(args):
     Y = torch.empty_like(X)
     ms32 = timed(lambda: binding.hmatvec(H, X, Y, form), max(2, args.steps // 4), 1) \
         / max(2, args.steps // 4)
+    Y64 = torch.empty_like(X)
+    binding.hmatvec(H, X, Y64, "fp64")
+    torch.cuda.synchronize()
+
+    def e_mixed(Yf):
+        d = torch.linalg.norm(Yf - Y64, dim=1) / torch.linalg.norm(Y64, dim=1)
+        return {"max": float(d.max()), "mean": float(d.mean())}
+    err32 = e_mixed(Y)
+
+    # ---- context: the other reduced forms on the same matrix (one vector,
+    # and their error against the FP64 form over the same 32 vectors)
+    forms_ctx = {}
+    for f in ("fp16", "bf16", "fp32"):
+        if f == form or args.minimal:
+            continue
+        try:
+            H.pack(f)
+            msf = timed(lambda: binding.hmatvec(H, x, y, f), max(4, args.steps // 4), 2) / max(4, args.steps // 4)
+            binding.hmatvec(H, X, Y, f)
+            torch.cuda.synchronize()
+            forms_ctx[f] = {"ms_per_matvec": round(msf, 4), "value": round(1e3 / msf, 2),
+                            "rel_err_vs_fp64_form_32_vectors": e_mixed(Y)}
+        except Exception as e:  # reported, the headline still prints
+            forms_ctx[f] = _context_error(e, "forms", failed)
 
     # ---- context: adaptive matrix-vector multiplication (Algorithm 2, FP64)
     amvm_ctx = None
@@ -403,7 +457,7 @@ def run_ours(args):
                 "rel_err_vs_fp64_product": float(torch.linalg.norm(ya - y64) / torch.linalg.norm(y64))}
             del Hd
         except Exception as e:  # reported, the headline still prints
-            amvm_ctx = {"error": f"{type(e).__name__}: {e}"}
+            amvm_ctx = _context_error(e, "amvm", failed)
 
     # ---- context: block-adaptive ACA solve of the single layer (Algorithm 3,
     # the paper's parameters theta 0.8, alpha 10, eps 1e-4, 8 starting ACA steps)
@@ -450,38 +504,35 @@ def run_ours(args):
                 "rel_residual_full_fp64": float(torch.linalg.norm(gd - yv) / torch.linalg.norm(gd))}
             del Hd
         except Exception as e:  # reported, the headline still prints
-            baca_ctx = {"error": f"{type(e).__name__}: {e}"}
+            baca_ctx = _context_error(e, "baca", failed)
 
     points_ctx = None
     if not args.no_points and rank == 0 and ws == 1:
         try:
             points_ctx = bench_points(args, tree, w, x, timed)
         except Exception as e:  # reported, the headline still prints
-            points_ctx = {"error": f"{type(e).__name__}: {e}"}
+            points_ctx = _context_error(e, "points", failed)
 
     line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16+f32", "fp16": "f16+f32"}[form],
+            "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16+f32", "fp16": "f16+f32", "i16": "i16+f32"}[form],
             "data": "synthetic",
             "config": dict(w, form=form, l2="inputs larger than L2 (H-matrix "
                            f"{total_alg/1e9:.2f} GB per product)", parallelism=f"replicas{ws}"),
             "roofline": roofline, "clocks": clocks, "e2e": e2e,
             "gpu_launches": 4 * args.steps,
             "rel_err_vs_fp64_form": err_mixed,
+            "rel_err_vs_fp64_form_32_vectors": err32,
             "fp64_form": {"ms_per_matvec": round(ms64, 4), "value": round(1e3 / ms64, 3)},
+            "other_forms": forms_ctx,
             "nrhs32": {"ms_per_call": round(ms32, 4), "vectors_per_s": round(32e3 / ms32, 2)},
             "amvm": amvm_ctx,
             "points": points_ctx,
             "baca": baca_ctx,
-            "assembly": {"tree_s": round(t_tree, 3), "assemble_s": round(t_asm, 3),
-                         "near_ms": round(st.assemble_ms[0], 1),
-                         "aca_ms": round(st.assemble_ms[1], 1),
-                         "rank_mean": [round(r / max(st.nadm, 1), 2) for r in st.rank_sum],
-                         "bytes_per_form": st.bytes_form}}
+            "assembly": assembly_context(st, t_tree, t_asm)}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = {k: v for k, v in cpu_baseline(V, T).items()
-                                if k in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline"] = cpu_baseline(V, T)
     elif rank == 0:
         line["cpu_baseline"] = None
     # ---- batched and served workloads (their own matrices; free this one first)
@@ -494,13 +545,55 @@ def run_ours(args):
         try:
             line[key] = fn(args)
         except Exception as e:  # reported, the headline still prints
-            line[key] = {"error": f"{type(e).__name__}: {e}"}
+            line[key] = _context_error(e, key, failed)
+    line["context_failed"] = failed
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
-    return 0
+    # a device failure may leave the CUDA context unusable: the headline was
+    # measured before it, but the run is not clean
+    return 3 if failed else 0
+
+
+def assembly_context(st, t_tree, t_asm):
+    """Assembly times and their roofline: the near-field quadrature and ACA
+    are bound by the FP64 units; their FP64 operations are counted by the
+    kernels (quadrature points, ACA entries) with the per-rule operation
+    counts of the library's statistics."""
+    fp64_peak, fp64_src = _fp64_peak()
+    out = {"tree_s": round(t_tree, 3), "assemble_s": round(t_asm, 3),
+           "near_ms": round(st.assemble_ms[0], 1), "aca_ms": round(st.assemble_ms[1], 1),
+           "rank_mean": [round(r / max(st.nadm, 1), 2) for r in st.rank_sum],
+           "bytes_per_form": st.bytes_form,
+           "near_points": {"whole_triangle_pairs": st.near_points[0], "subdivision_leaves": st.near_points[1],
+                           "self_pairs": st.near_points[2]},
+           "aca_entries": {"V_Delta": st.aca_entries[0], "V_kl": st.aca_entries[1]}}
+    rl = {}
+    for key, fl, ms in (("near", st.assembly_flops[0], st.assemble_ms[0]),
+                        ("aca", st.assembly_flops[1], st.assemble_ms[1])):
+        if fl > 0 and ms > 0:
+            tf = fl / (ms * 1e-3) / 1e12
+            rl[key] = {"bound": "alu", "flops": fl, "achieved": round(tf, 4), "peak": fp64_peak,
+                       "unit": "TFLOP/s (FP64)", "frac": round(tf / fp64_peak, 4)}
+    out["roofline"] = rl
+    out["fp64_peak_from"] = fp64_src
+    return out
+
+
+def _context_error(e, key, failed):
+    """Record a context section's exception.  A failed bounded wait or CUDA
+    call of the library (HM_ETIMEOUT, HM_EDEVICE) or a CUDA error raised by
+    torch marks the run as failed on the device."""
+    from paper_2205_04752_gb300 import binding
+    if isinstance(e, binding.HMError):
+        device = e.code in (binding.HM_ETIMEOUT, binding.HM_EDEVICE)
+    else:
+        device = "CUDA" in str(e) or "cuda" in type(e).__name__.lower()
+    if device:
+        failed.append(key)
+    return {"error": f"{type(e).__name__}: {e}", "device_failure": device}
 
 
 def _fp64_peak():
@@ -781,7 +874,7 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="fp16", choices=["fp64", "fp32", "bf16", "fp16"])
+    ap.add_argument("--form", default="i16", choices=["fp64", "fp32", "bf16", "fp16", "i16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-mesh batched products")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-loop measurement")

@@ -43,6 +43,12 @@ extern "C" {
 #define HM_FP32 1 /* factors and near field FP32, FP32 accumulation */
 #define HM_BF16 2 /* factors BF16 with per-column FP32 scales, near field FP32, FP32 acc. */
 #define HM_FP16 3 /* factors FP16 with per-column FP32 scales, near field FP32, FP32 acc. */
+#define HM_I16 4  /* factors INT16 with per-column FP32 scales on U and V (block floating
+                   * point: a column is stored as round(32767 v / max|v|)), near field
+                   * FP32, FP32 acc.  Same bytes as FP16; a column keeps 15 significant
+                   * bits at its largest entries instead of FP16's 11, which makes the
+                   * product's error against HM_FP64 about 16 times smaller */
+#define HM_NFORMS 5
 
 /* largest leaf size b_min of a cluster tree (see hm_build_cluster_tree) */
 #define HM_MAX_LEAF 336
@@ -241,17 +247,26 @@ int hm_matvec(const hm_matrix* H, const double* x, double* y, int32_t nrhs, int6
  * budget such as a real-time or embedded loop, or a host framework that owns
  * all allocation).  The paper has no counterpart; this is a library service.
  * Same arguments, result and determinism as hm_matvec, but the workspace
- * (gathered x and the far-field vectors V^T x) comes from one static device
- * array of 32 MiB inside the library instead of the matrix's own workspace.
+ * comes from one static device array of 32 MiB inside the library instead of
+ * the matrix's own workspace.
  *   - Allocates nothing and calls no allocating routine.
  *   - The array is held by every GPU on which the library is loaded, until
  *     the process exits.
- *   - Products needing more than 32 MiB of workspace are rejected with
- *     HM_EINVAL (need = nrhs * (8M + 4 * sum of ACA ranks) * 8 bytes for
- *     HM_FP64, * 4 for the other forms, plus alignment).
- *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress, which may load the library's device code on
- *     that device); make that first call before any stream capture.
+ *   - The workspace of a product is the sum of four parts, each rounded up
+ *     to a multiple of 256 bytes, with ta = 8 bytes for HM_FP64 and 4 for
+ *     the other forms:
+ *       gathered x:            nrhs * 4M * ta
+ *       w = V^T x per factor:  nrhs * 4 * (sum of ACA ranks) * ta
+ *       forward partial sums:  nrhs * 4 * zcols * ta, where zcols sums, over
+ *                              the column clusters taller than 256 rows,
+ *                              (number of 256-row chunks) x (their factor
+ *                              columns)
+ *       counters:              512 bytes
+ *     Products needing more than 32 MiB are rejected with HM_EINVAL, and
+ *     the message states the exact need.
+ *   - The address of the array is looked up (cudaGetSymbolAddress) on every
+ *     call; the first call on a device may load the library's device code
+ *     on that device, so make that first call before any stream capture.
  *   - All calls share the array: calls whose kernels overlap in time on the
  *     device race and give wrong results.  Nothing in it needs to start at
  *     zero (every call writes each element before reading it).
@@ -581,9 +596,27 @@ typedef struct {
     int32_t rank_cap_hits;      /* block-kernel pairs that hit kmax */
     int32_t csp;                /* sparsity constant: max blocks per row cluster */
     int64_t bytes_fp64;         /* far + near bytes read by one FP64 product */
-    int64_t bytes_form[4];      /* same for each form (0 if not packed) */
+    int64_t bytes_form[HM_NFORMS]; /* same for each form (0 if not packed) */
     double assemble_ms[3];      /* near-field quadrature, ACA, packing (device time) */
     int64_t far_entries_kern[7]; /* sum over admissible blocks of k(|t|+|s|), per scalar kernel */
+    /* Assembly work, counted by the kernels at assembly (0 for a matrix
+     * assembled before these counters or with HM_DEFER_ACA):
+     *   near_points  near-field pairs on the 7-point rule over the whole
+     *                triangle, 7-point-rule applications on subdivision
+     *                leaves, and self pairs (3 x 32 Duffy points each)
+     *   aca_entries  entries Algorithm 1 evaluated (every row it tried times
+     *                |s|, every cross's column times |t|): V_Delta, V_kl */
+    int64_t near_points[3];
+    int64_t aca_entries[2];
+    /* FP64 operations of the near-field quadrature and of ACA, from the
+     * operations the formulas state (an FMA is 2, a square root or reciprocal
+     * square root 1): per quadrature point of all seven kernels 31 (35 on the
+     * self term, 46 on a subdivision leaf, whose rule also forms the points
+     * and the leaf's area: 36 per leaf, and 63 per subdivision step); per ACA
+     * entry 86 (V_Delta) or 114 (V_kl) with its 7-point rule; per ACA task of
+     * rank k the residual, scaling and Frobenius updates
+     * 2k(k-1)(|t|+|s|) + k(3|s|+2|t|). */
+    double assembly_flops[2];
 } hm_stats;
 
 int hm_get_stats(const hm_matrix* H, hm_stats* st);

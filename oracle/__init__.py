@@ -113,7 +113,9 @@ def _L():
                 "or_hmat_factors": (None, [P, I64, ctypes.c_int, P, P]),
                 "or_hmat_near_block": (None, [P, I64, P]),
                 "or_hmat_matvec": (None, [P, D, D, P, P, I64, P, I64, P, I64]),
+                "or_hmat_matvec_c": (None, [P, D, D, P, P, I64, P, I64, P, I64]),
                 "or_num_threads": (I32, []),
+                "or_set_num_threads": (None, [I32]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -141,6 +143,12 @@ def _i64(a):
 
 def num_threads() -> int:
     return int(_L().or_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """OpenMP threads of the oracle's later calls from this thread (the
+    results do not depend on it)."""
+    _L().or_set_num_threads(int(n))
 
 
 # --------------------------------------------------------------------------
@@ -423,6 +431,15 @@ class HMatrix:
         _L().or_hmat_matvec(self._h, E, nu, _p(x), _p(y), x.shape[0], pa, na, pn, nn)
         return y
 
+    def matvec_coeffs(self, c1: float, c2: float, x) -> np.ndarray:
+        """The H-matrix product with the coefficients of Eq. (Vh) given
+        directly: y_a = c1 V_Delta x_a + c2 sum_b V_ab x_b (the double layer
+        of Eq. (Kh) applies the single layer's blocks with its own c1, c2)."""
+        x = _f64(np.atleast_2d(x))
+        y = np.zeros((x.shape[0], 3 * self.Mr))
+        _L().or_hmat_matvec_c(self._h, float(c1), float(c2), _p(x), _p(y), x.shape[0], None, -1, None, -1)
+        return y
+
     def dense_block(self, b: int, kern: int) -> np.ndarray:
         """The exact (quadrature-contract) scalar-kernel block of admissible
         block b, computed entry by entry."""
@@ -456,7 +473,7 @@ def sparsity_constant(Ho: "HMatrix") -> int:
 
 
 def amvm(Ho: "HMatrix", E: float, nu: float, x, theta: float = 0.7, eps: float = 1e-6,
-         r0: int = 2, look: int = 2, max_iter: int = 1000):
+         r0: int = 2, look: int = 2, max_iter: int = 1000, record_scan: bool = False):
     """Algorithm 2 (adaptive matrix-vector multiplication, Section 3) on the
     oracle's own H-matrix, FP64, for one vector x (3M dofs, original order);
     the rows are the 3 Mr dofs of the row points (Mr = M unless Ho is the
@@ -479,7 +496,10 @@ def amvm(Ho: "HMatrix", E: float, nu: float, x, theta: float = 0.7, eps: float =
 
     Returns a dict: b (A_k x at the last k, original order), b_hat, gamma
     (gamma_k per iteration), gamma_rest (gamma_k(P_k) per iteration), marked
-    (|P_k| per iteration), ranks (r_b at the end), csp, iterations."""
+    (|P_k| per iteration), ranks (min(r_b, full rank) per block and kernel at
+    the end), r (r_b per block at the end), csp, iterations; with
+    ``record_scan`` also scans: per refinement, gamma_k(P_k) after each row
+    of the step-3 scan up to the stopping row."""
     x = _f64(x).reshape(-1)
     M, Mr = Ho.M, Ho.Mr
     c1, c2 = lame_coefficients(E, nu)
@@ -524,6 +544,7 @@ def amvm(Ho: "HMatrix", E: float, nu: float, x, theta: float = 0.7, eps: float =
         for p in range(rng[b, 0], rng[b, 1]):
             blocks_of_pos[p].append(b)
     hist = dict(gamma=[], gamma_rest=[], marked=[])
+    scans = []
     delta = [part(b, r[b], r[b] + look) for b in range(nb)]
     it = 0
     while True:
@@ -543,6 +564,7 @@ def amvm(Ho: "HMatrix", E: float, nu: float, x, theta: float = 0.7, eps: float =
         marked = []
         is_marked = np.zeros(nb, dtype=bool)
         g_rest = gamma
+        scan = []
         for i in order:
             p, a = divmod(int(i), 3)
             for b in blocks_of_pos[p]:
@@ -553,8 +575,12 @@ def amvm(Ho: "HMatrix", E: float, nu: float, x, theta: float = 0.7, eps: float =
                     marked.append(b)
                     rest[rng[b, 0]:rng[b, 1]] -= delta[b]
             g_rest = float(np.linalg.norm(rest))
+            if record_scan:
+                scan.append(g_rest)
             if gamma - g_rest >= theta * gamma:
                 break
+        if record_scan:
+            scans.append(np.array(scan))
         hist["gamma_rest"].append(g_rest)
         hist["marked"].append(len(marked))
         if not marked:
@@ -569,8 +595,11 @@ def amvm(Ho: "HMatrix", E: float, nu: float, x, theta: float = 0.7, eps: float =
     out.reshape(Mr, 3)[rperm] = bk
     outh = np.zeros(3 * Mr)
     outh.reshape(Mr, 3)[rperm] = bhat
-    return dict(b=out, b_hat=outh, ranks=np.minimum(r[:, None], full), full_ranks=full, csp=csp,
-                iterations=it, **hist)
+    res = dict(b=out, b_hat=outh, ranks=np.minimum(r[:, None], full), full_ranks=full, r=r.copy(),
+               csp=csp, iterations=it, **hist)
+    if record_scan:
+        res["scans"] = scans
+    return res
 
 
 # --------------------------------------------------------------------------

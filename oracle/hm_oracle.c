@@ -1331,14 +1331,29 @@ void or_hmat_near_block(const void* hp, int64_t b, double* out)
  * blocks of that kind; blocks that were not assembled must not be listed. */
 static const int kab[3][3] = {{1, 2, 3}, {2, 4, 5}, {3, 5, 6}};
 
+/* The same product with the coefficients of Eq. (Vh) given directly:
+ * y_a += c1 V_Delta x_a + c2 sum_b V_ab x_b.  Section 4.2's double layer
+ * applies the single layer's blocks with c1 = (1-2nu)/(2(1-nu)) and
+ * c2 = 1/(2(1-nu)) (Eq. (Kh), -V_Delta T_h + E/(1+nu) V_h T_h). */
+void or_hmat_matvec_c(const void* hp, double c1, double c2, const double* x, double* y,
+                      int64_t nrhs, const int64_t* adm_ids, int64_t nadm_ids,
+                      const int64_t* near_ids, int64_t nnear_ids);
+
 void or_hmat_matvec(const void* hp, double E, double nu, const double* x, double* y,
                     int64_t nrhs, const int64_t* adm_ids, int64_t nadm_ids,
                     const int64_t* near_ids, int64_t nnear_ids)
 {
-    const or_hmat* h = (const or_hmat*)hp;
-    int64_t M = h->M, Mr = h->Mr;
     double c1 = (1.0 + nu) * (3.0 - 4.0 * nu) / (2.0 * E * (1.0 - nu));
     double c2 = (1.0 + nu) / (2.0 * E * (1.0 - nu));
+    or_hmat_matvec_c(hp, c1, c2, x, y, nrhs, adm_ids, nadm_ids, near_ids, nnear_ids);
+}
+
+void or_hmat_matvec_c(const void* hp, double c1, double c2, const double* x, double* y,
+                      int64_t nrhs, const int64_t* adm_ids, int64_t nadm_ids,
+                      const int64_t* near_ids, int64_t nnear_ids)
+{
+    const or_hmat* h = (const or_hmat*)hp;
+    int64_t M = h->M, Mr = h->Mr;
     int64_t na = nadm_ids < 0 ? h->bl.nadm : nadm_ids;
     int64_t nn = nnear_ids < 0 ? h->bl.nnear : nnear_ids;
     if (nadm_ids < 0) adm_ids = NULL;
@@ -1455,5 +1470,17 @@ int32_t or_num_threads(void)
     return (int32_t)omp_get_max_threads();
 #else
     return 1;
+#endif
+}
+
+/* Threads of the later parallel regions started from the calling thread
+ * (OpenMP); the arithmetic and its order do not depend on it.  n < 1 is
+ * ignored. */
+void or_set_num_threads(int32_t n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads((int)n);
+#else
+    (void)n;
 #endif
 }

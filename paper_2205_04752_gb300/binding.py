@@ -19,8 +19,8 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libhmat.so")
 HM_OK, HM_EINVAL, HM_ENOMEM, HM_ENOTCONV, HM_ETIMEOUT, HM_EDEVICE, HM_ERANK, HM_EBUSY = \
     0, -1, -2, -3, -4, -5, -6, -7
 HM_REQ_MATVEC, HM_REQ_SOLVE = 0, 1
-FP64, FP32, BF16, FP16 = 0, 1, 2, 3
-FORMS = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "fp16": FP16}
+FP64, FP32, BF16, FP16, I16 = 0, 1, 2, 3, 4
+FORMS = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "fp16": FP16, "i16": I16}
 MAX_LEAF = 336  # HM_MAX_LEAF
 
 # every symbol the header declares
@@ -133,8 +133,9 @@ class _Stats(ctypes.Structure):
                 ("rank_sum", ctypes.c_int64 * 7),
                 ("rank_max", ctypes.c_int32 * 7), ("rank_cap_hits", ctypes.c_int32),
                 ("csp", ctypes.c_int32), ("bytes_fp64", ctypes.c_int64),
-                ("bytes_form", ctypes.c_int64 * 4), ("assemble_ms", ctypes.c_double * 3),
-                ("far_entries_kern", ctypes.c_int64 * 7)]
+                ("bytes_form", ctypes.c_int64 * 5), ("assemble_ms", ctypes.c_double * 3),
+                ("far_entries_kern", ctypes.c_int64 * 7), ("near_points", ctypes.c_int64 * 3),
+                ("aca_entries", ctypes.c_int64 * 2), ("assembly_flops", ctypes.c_double * 2)]
 
 
 _lib = None
@@ -340,6 +341,9 @@ class Stats:
     bytes_form: list
     assemble_ms: list
     far_entries_kern: list
+    near_points: list
+    aca_entries: list
+    assembly_flops: list
 
 
 class HMatrix:
@@ -390,7 +394,8 @@ class HMatrix:
         _check(load().hm_get_stats(self._h, ctypes.byref(st)))
         return Stats(st.M, st.nadm, st.nnear, st.nleaves, st.near_pairs, st.far_entries,
                      st.far_u_entries, st.far_v_entries, st.factor_columns, list(st.rank_sum), list(st.rank_max), st.rank_cap_hits, st.csp,
-                     st.bytes_fp64, list(st.bytes_form), list(st.assemble_ms), list(st.far_entries_kern))
+                     st.bytes_fp64, list(st.bytes_form), list(st.assemble_ms), list(st.far_entries_kern),
+                     list(st.near_points), list(st.aca_entries), list(st.assembly_flops))
 
     def check(self):
         """Raise if a bounded device wait in an earlier product ran out."""

@@ -164,9 +164,11 @@ __device__ void rule7_all(const double* x, const double* v, double* acc)
 }
 
 // adaptive rule for a point outside triangle v: depth-first over the midpoint
-// subdivision (children: corner 0, corner 1, corner 2, middle)
-__device__ void adaptive7(const double* x, const double* v0, double* acc)
+// subdivision (children: corner 0, corner 1, corner 2, middle); returns the
+// number of leaves the 7-point rule was applied on
+__device__ int adaptive7(const double* x, const double* v0, double* acc)
 {
+    int leaves = 0;
     double st[kStack][9];
     int dep[kStack];
     int top = 0;
@@ -201,8 +203,10 @@ __device__ void adaptive7(const double* x, const double* v0, double* acc)
             }
         } else {
             rule7_all(x, v, acc);
+            ++leaves;
         }
     }
+    return leaves;
 }
 
 // self pair: x is the centroid of v; Duffy map per edge sub-triangle
@@ -230,27 +234,31 @@ __device__ void self7(const double* x, const double* v, double* acc)
 }
 
 // all seven kernels of pair (i, j) (row and column cluster positions), times
-// 1/(4 pi)
-__device__ void entry7(const Geom& g, int i, int j, double* acc)
+// 1/(4 pi).  Returns the rule taken: -1 the self term, 0 the 7-point rule on
+// the whole triangle, n > 0 the 7-point rule on n subdivision leaves.
+__device__ int entry7(const Geom& g, int i, int j, double* acc)
 {
 #pragma unroll
     for (int c = 0; c < 7; ++c) acc[c] = 0.0;
     const double* x = g.xr + 3 * (size_t)i;
     const double* v = g.tri + 9 * (size_t)j;
+    int rule;
     if (g.square && i == j) {
         self7(x, v, acc);
+        rule = -1;
     } else if (sq_dist_rn(x, g.coll + 3 * (size_t)j) < __dmul_rn(4.0, g.diam2[j])) {
-        adaptive7(x, v, acc);
+        rule = adaptive7(x, v, acc);
     } else {
         const double* qp = g.qp + 21 * (size_t)j;
         const double* qw = g.qw + 7 * (size_t)j;
 #pragma unroll
         for (int q = 0; q < 7; ++q)
             point7(x[0] - qp[3 * q], x[1] - qp[3 * q + 1], x[2] - qp[3 * q + 2], qw[q], acc);
-        return;  // qw already holds 1/(4 pi)
+        return 0;  // qw already holds 1/(4 pi)
     }
 #pragma unroll
     for (int c = 0; c < 7; ++c) acc[c] *= kInv4Pi;
+    return rule;
 }
 
 // one scalar kernel of pair (i, j): the far (7-point) path is specialised
@@ -321,20 +329,40 @@ __global__ void geom_kernel(int M, const int32_t* __restrict__ perm, const int32
 
 // ---------------------------------------------------------------- near field
 // One CTA per near block; output per block [v][j][i] (i fastest), v = the six
-// kernels V_11..V_33 (V_Delta is their trace).
+// kernels V_11..V_33 (V_Delta is their trace).  qcount (optional) receives
+// the quadrature work: [0] pairs on the whole-triangle 7-point rule, [1]
+// subdivision leaves, [2] self pairs -- one atomic add per warp.
 __global__ void __launch_bounds__(128) near_kernel(Geom g, const Blk* __restrict__ blks,
                                                    const int64_t* __restrict__ noff,
-                                                   double* __restrict__ N)
+                                                   double* __restrict__ N,
+                                                   unsigned long long* __restrict__ qcount)
 {
     Blk b = blks[blockIdx.x];
     double* out = N + noff[blockIdx.x];
     int pairs = b.m * b.n;
+    unsigned long long c_far = 0, c_leaf = 0, c_self = 0;
     for (int e = threadIdx.x; e < pairs; e += blockDim.x) {
         int j = e / b.m, i = e - j * b.m;
         double a[7];
-        entry7(g, b.t0 + i, b.s0 + j, a);
+        const int rule = entry7(g, b.t0 + i, b.s0 + j, a);
+        c_far += rule == 0;
+        c_self += rule < 0;
+        c_leaf += rule > 0 ? (unsigned long long)rule : 0ull;
 #pragma unroll
         for (int v = 0; v < 6; ++v) out[(size_t)v * pairs + e] = a[1 + v];
+    }
+    if (qcount) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            c_far += __shfl_xor_sync(0xffffffffu, c_far, o);
+            c_leaf += __shfl_xor_sync(0xffffffffu, c_leaf, o);
+            c_self += __shfl_xor_sync(0xffffffffu, c_self, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(qcount, c_far);
+            atomicAdd(qcount + 1, c_leaf);
+            atomicAdd(qcount + 2, c_self);
+        }
     }
 }
 
@@ -352,6 +380,9 @@ struct AcaParams {
     int32_t kmax;
     int32_t kcap_all;  // columns reserved per CTA in scratch
     int32_t mmax, nmax;
+    // optional: entries evaluated, [0] V_Delta, [1] the V_kl (thread 0 of a
+    // CTA adds its task's count once)
+    unsigned long long* ecount = nullptr;
 };
 
 __device__ __forceinline__ double warp_max(double v)
@@ -504,11 +535,13 @@ __global__ void __launch_bounds__(kAcaThreads) aca_kernel(
             for (int i = tid; i < m; i += B) Z[i] = 0;
         }
         __syncthreads();
+        unsigned long long nent = 0;  // entries this task evaluates (thread 0)
         for (;;) {
             if (k >= prm.kmax) {
                 flags |= 1;
                 break;
             }
+            nent += (unsigned long long)n;
             // residual row  v~ = A[i, s] - sum_{l<k} (u_l)_i v_l
             for (int l = tid; l < k; l += B) sh.su[l] = U[(size_t)l * m + irow];
             __syncthreads();
@@ -553,6 +586,7 @@ __global__ void __launch_bounds__(kAcaThreads) aca_kernel(
                 break;
             }
             const double inv = 1.0 / vk[jk];
+            nent += (unsigned long long)m;
             __syncthreads();  // everyone has read the pivot before it is scaled
             double tvv = 0.0;
             for (int j = tid; j < n; j += B) {
@@ -675,7 +709,10 @@ __global__ void __launch_bounds__(kAcaThreads) aca_kernel(
                 for (int j = tid; j < n; j += B) dv[(size_t)l * n + j] = Vf[(size_t)l * n + j];
             }
         }
-        if (tid == 0) out_flags[task] = flags;
+        if (tid == 0) {
+            out_flags[task] = flags;
+            if (prm.ecount) atomicAdd(prm.ecount + (kern == 0 ? 0 : 1), nent);
+        }
     }
 }
 
@@ -993,10 +1030,15 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
     H.n_total = ntot;
     if ((rc = upload(H, H.d_noff, H.noff_h.data(), H.noff_h.size() * 8))) return rc;
     if ((rc = dalloc(H, H.N64, (size_t)std::max<int64_t>(ntot, 1) * 8))) return rc;
+    // assembly work counters: near-field rules [0..2], ACA entries [3..4]
+    TmpBuf dqc(H);
+    if ((rc = dalloc(H, dqc.b, 64))) return rc;
+    HM_CUDA(cudaMemsetAsync(dqc.b.p, 0, 64, s));
+    unsigned long long* qc = dqc.b.as<unsigned long long>();
     HM_CUDA(cudaEventRecord(ev[0], s));
     if (H.nnear > 0) {
         near_kernel<<<(unsigned)H.nnear, 128, 0, s>>>(g, H.d_near.as<Blk>(), H.d_noff.as<int64_t>(),
-                                                      H.N64.as<double>());
+                                                      H.N64.as<double>(), qc);
         HM_CUDA(cudaGetLastError());
     }
     HM_CUDA(cudaEventRecord(ev[1], s));
@@ -1121,8 +1163,10 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
         HM_CUDA(cudaMemsetAsync(dtop.b.p, 0, 64, s));
         for (const AcaClass& c : classes) {
             HM_CUDA(cudaMemsetAsync(dcnt.b.p, 0, 64, s));
+            AcaParams cp = c.prm;
+            cp.ecount = qc + 3;  // the first run of every task (not a re-run into the exact arena)
             aca_kernel<<<(unsigned)c.grid, kAcaThreads, 0, s>>>(
-                g, dtask.b.as<AcaTask>() + c.i0, (int)(c.i1 - c.i0), H.d_adm.as<Blk>(), c.prm,
+                g, dtask.b.as<AcaTask>() + c.i0, (int)(c.i1 - c.i0), H.d_adm.as<Blk>(), cp,
                 dscr.b.as<double>(), dz.b.as<unsigned char>(), dcnt.b.as<int>(), darena.b.as<double>(),
                 dtop.b.as<unsigned long long>(), cap, drank.b.as<int32_t>() + c.i0, doff.b.as<int64_t>() + c.i0,
                 dflag.b.as<int32_t>() + c.i0, AcaResume{});
@@ -1500,6 +1544,11 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
     cudaEventElapsedTime(&t01, ev[0], ev[1]);
     cudaEventElapsedTime(&t12, ev[1], ev[2]);
     cudaEventElapsedTime(&t23, ev[2], ev[3]);
+    {
+        unsigned long long cnt[5] = {0, 0, 0, 0, 0};
+        HM_CUDA(cudaMemcpy(cnt, qc, sizeof cnt, cudaMemcpyDeviceToHost));
+        for (int i = 0; i < 5; ++i) H.asm_count[i] = (int64_t)cnt[i];
+    }
     H.asm_ms[0] = t01;
     H.asm_ms[1] = t12 + t23;
     H.asm_ms[2] = 0.0;
@@ -1588,7 +1637,7 @@ int assemble_points_device(const hm_tree& tr, hm_matrix& H)
     HM_CUDA(cudaEventRecord(ev[0], s));
     if (H.nnear > 0) {
         near_kernel<<<(unsigned)H.nnear, 128, 0, s>>>(g, H.d_near.as<Blk>(), H.d_noff.as<int64_t>(),
-                                                      H.N64.as<double>());
+                                                      H.N64.as<double>(), nullptr);
         HM_CUDA(cudaGetLastError());
     }
     HM_CUDA(cudaEventRecord(ev[1], s));

@@ -156,7 +156,7 @@ int hm_batch_create(const hm_matrix* const* mats, int32_t nmat, int32_t form, in
     *out = nullptr;
     if (!mats || nmat < 1) return fail(HM_EINVAL, "hm_batch_create: need at least one matrix");
     if (nmat > 65535) return fail(HM_EINVAL, "hm_batch_create: at most 65535 matrices");
-    if (form < HM_FP64 || form > HM_FP16) return fail(HM_EINVAL, "hm_batch_create: unknown form %d", form);
+    if (form < HM_FP64 || form >= HM_NFORMS) return fail(HM_EINVAL, "hm_batch_create: unknown form %d", form);
     if (max_rhs < 1) return fail(HM_EINVAL, "hm_batch_create: max_rhs must be >= 1");
     for (int32_t m = 0; m < nmat; ++m) {
         if (!mats[m]) return fail(HM_EINVAL, "hm_batch_create: matrix %d is NULL", m);

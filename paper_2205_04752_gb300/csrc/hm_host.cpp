@@ -461,7 +461,7 @@ int hm_set_material(hm_matrix* H, double E, double nu)
     H->nu = nu;
     // an evaluation operator reads E and nu at each call; the square matrix's
     // packed forms keep c1, c2 in their device tables
-    for (int f = 0; f < 4 && !H->rect; ++f)
+    for (int f = 0; f < HM_NFORMS && !H->rect; ++f)
         if (H->packed[f]) {
             int rc = write_mesh_table(*H, f, nullptr);
             if (rc) return rc;
@@ -507,13 +507,33 @@ int hm_get_stats(const hm_matrix* H, hm_stats* st)
         st->bytes_form[HM_FP64] = elems * 8;
         if (H->packed[HM_FP32]) st->bytes_form[HM_FP32] = elems * 4;
     }
-    for (int f = 0; f < 4 && !H->rect; ++f) {
+    for (int f = 0; f < HM_NFORMS && !H->rect; ++f) {
         if (!H->packed[f]) continue;
         int64_t wf = f == HM_FP64 ? 8 : (f == HM_FP32 ? 4 : 2);
         int64_t wn = f == HM_FP64 ? 8 : 4;
         st->bytes_form[f] = stream_elems * wf + H->nl_total * wn + (wf == 2 ? far_cols * 4 : 0);
     }
     for (int i = 0; i < 3; ++i) st->assemble_ms[i] = H->asm_ms[i];
+    for (int i = 0; i < 3; ++i) st->near_points[i] = H->asm_count[i];
+    for (int i = 0; i < 2; ++i) st->aca_entries[i] = H->asm_count[3 + i];
+    // FP64 operations the formulas state (header of hm_stats): near field
+    const double whole = (double)H->asm_count[0], leaves = (double)H->asm_count[1],
+                 self = (double)H->asm_count[2];
+    const double split_pairs = std::max(0.0, (double)st->near_pairs - whole - self);
+    const double steps = std::max(0.0, (leaves - split_pairs) / 3.0);  // a step turns 1 leaf into 4
+    st->assembly_flops[0] = whole * 7 * 31 + leaves * (7 * 46 + 36) + steps * 63 + self * (96 * 35 + 63 + 7) +
+                            split_pairs * 7;
+    // ACA: the entries, then per block-kernel task of rank k the updates
+    double upd = 0.0;
+    if (H->asm_count[3] + H->asm_count[4] > 0)
+        for (int64_t b = 0; b < H->nadm; ++b) {
+            const hm::Blk& bk = H->adm_h[(size_t)b];
+            for (int k = 0; k < 7; ++k) {
+                const double r = (double)H->rank_h[(size_t)(b * 7 + k)];
+                upd += 2.0 * r * (r - 1.0) * (bk.m + bk.n) + r * (3.0 * bk.n + 2.0 * bk.m);
+            }
+        }
+    st->assembly_flops[1] = (double)H->asm_count[3] * 86 + (double)H->asm_count[4] * 114 + upd;
     return HM_OK;
 }
 
@@ -597,12 +617,31 @@ int hm_profile_read(hm_matrix* H, double ms[4], int64_t* calls)
     return HM_OK;
 }
 
+// every device buffer a matrix may hold (its footprint; released at destroy)
+static std::vector<hm::DevBuf*> matrix_bufs(hm_matrix* H)
+{
+    std::vector<hm::DevBuf*> v = {
+        &H->d_perm, &H->d_adm, &H->d_near, &H->d_rank, &H->d_uoff, &H->d_voff, &H->d_coff, &H->d_noff,
+        &H->d_leaf, &H->d_lf_base, &H->d_lf_ptr, &H->d_lf_items, &H->d_lf_src, &H->d_ln_base, &H->d_ln_ptr,
+        &H->d_ln_items, &H->d_ln_src, &H->d_vb_base, &H->d_vb_ld, &H->d_vb_coff, &H->fdesc, &H->d_groups,
+        &H->d_units, &H->d_tcunits, &H->d_multi, &H->d_big, &H->d_small, &H->d_fwd_all, &H->d_work,
+        &H->d_pos_prefix, &H->d_counters, &H->d_err, &H->U64, &H->V64, &H->N64, &H->Nl64, &H->Nl32, &H->SU,
+        &H->SV, &H->SW16, &H->xg, &H->wb, &H->zb, &H->xh, &H->yh, &H->g_coll, &H->g_tri, &H->g_qp, &H->g_qw,
+        &H->g_diam, &H->d_rperm, &H->g_rows};
+    for (int f = 0; f < HM_NFORMS; ++f) {
+        v.push_back(&H->d_mesh[f]);
+        v.push_back(&H->Ul[f]);
+        v.push_back(&H->Vr[f]);
+    }
+    return v;
+}
+
 int hm_compact(hm_matrix* H)
 {
     if (!H) return fail(HM_EINVAL, "hm_compact: NULL matrix");
     if (H->rect) return fail(HM_EINVAL, "hm_compact: an evaluation operator has no packed form");
     if (H->compacted) return HM_OK;
-    if (!H->packed[HM_FP32] && !H->packed[HM_BF16] && !H->packed[HM_FP16])
+    if (!H->packed[HM_FP32] && !H->packed[HM_BF16] && !H->packed[HM_FP16] && !H->packed[HM_I16])
         return fail(HM_EINVAL, "hm_compact: pack a reduced form first (hm_pack)");
     HM_CUDA(cudaDeviceSynchronize());
     hm::DevBuf* bufs[] = {&H->U64, &H->V64, &H->N64, &H->SV, &H->Ul[HM_FP64], &H->Vr[HM_FP64], &H->Nl64,
@@ -623,17 +662,8 @@ int hm_compact(hm_matrix* H)
 int hm_footprint(const hm_matrix* H, int64_t* bytes)
 {
     if (!H || !bytes) return fail(HM_EINVAL, "hm_footprint: NULL argument");
-    const hm::DevBuf* bufs[] = {&H->d_perm, &H->d_adm, &H->d_near, &H->d_rank, &H->d_uoff, &H->d_voff,
-                                &H->d_coff, &H->d_noff, &H->d_leaf, &H->d_lf_base, &H->d_lf_ptr,
-                                &H->d_lf_items, &H->d_lf_src, &H->d_ln_base, &H->d_ln_ptr, &H->d_ln_items,
-                                &H->d_ln_src, &H->d_vb_base, &H->d_vb_ld, &H->d_vb_coff, &H->fdesc, &H->d_groups, &H->d_units, &H->d_tcunits, &H->d_multi, &H->d_big, &H->d_small, &H->d_fwd_all, &H->d_work, &H->d_pos_prefix,
-                                &H->d_mesh[0], &H->d_mesh[1], &H->d_mesh[2], &H->d_mesh[3], &H->d_counters,
-                                &H->d_err, &H->U64, &H->V64, &H->N64, &H->Ul[0], &H->Ul[1], &H->Ul[2],
-                                &H->Ul[3], &H->Vr[0], &H->Vr[1], &H->Vr[2], &H->Vr[3], &H->Nl64, &H->Nl32,
-                                &H->SU, &H->SV, &H->xg, &H->wb, &H->zb, &H->xh, &H->yh, &H->g_coll, &H->g_tri, &H->g_qp, &H->g_qw, &H->g_diam,
-                                &H->d_rperm, &H->g_rows};
     int64_t t = 0;
-    for (const hm::DevBuf* b : bufs)
+    for (const hm::DevBuf* b : matrix_bufs(const_cast<hm_matrix*>(H)))
         if (b->p) t += (int64_t)b->bytes;
     for (const hm::DevBuf& b : H->ev)
         if (b.p) t += (int64_t)b.bytes;
@@ -646,20 +676,11 @@ void hm_matrix_destroy(hm_matrix* H)
     if (!H) return;
     for (cudaEvent_t e : H->prof_ev) cudaEventDestroy(e);
 
-    hm::DevBuf* bufs[] = {&H->d_perm, &H->d_adm, &H->d_near, &H->d_rank, &H->d_uoff, &H->d_voff,
-                          &H->d_coff, &H->d_noff, &H->d_leaf, &H->d_lf_base, &H->d_lf_ptr,
-                          &H->d_lf_items, &H->d_lf_src, &H->d_ln_base, &H->d_ln_ptr, &H->d_ln_items,
-                          &H->d_ln_src, &H->d_vb_base, &H->d_vb_ld, &H->d_vb_coff, &H->fdesc, &H->d_groups, &H->d_units, &H->d_tcunits, &H->d_multi, &H->d_big, &H->d_small, &H->d_fwd_all, &H->d_work, &H->d_pos_prefix, &H->d_mesh[0], &H->d_mesh[1], &H->d_mesh[2],
-                          &H->d_mesh[3], &H->d_counters, &H->d_err, &H->U64, &H->V64, &H->N64,
-                          &H->Ul[0], &H->Ul[1], &H->Ul[2], &H->Ul[3], &H->Vr[0], &H->Vr[1],
-                          &H->Vr[2], &H->Vr[3], &H->Nl64, &H->Nl32, &H->SU, &H->SV, &H->xg, &H->wb, &H->zb,
-                          &H->xh, &H->yh, &H->g_coll, &H->g_tri, &H->g_qp, &H->g_qw, &H->g_diam,
-                          &H->d_rperm, &H->g_rows};
     // the assembly stream may be gone by now: drain the device and release
     // on the legacy default stream
     cudaDeviceSynchronize();
     H->alloc.stream = nullptr;
-    for (hm::DevBuf* b : bufs) {
+    for (hm::DevBuf* b : matrix_bufs(H)) {
         H->alloc.release(b->p, b->bytes);
         b->p = nullptr;
     }

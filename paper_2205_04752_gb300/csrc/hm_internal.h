@@ -242,6 +242,9 @@ struct hm_matrix {
     int32_t csp = 0;
     int32_t max_leaf = 0;
     double asm_ms[3] = {0, 0, 0};
+    // assembly work counted by the kernels: near-field pairs on the whole-
+    // triangle rule, subdivision leaves, self pairs; ACA entries V_Delta, V_kl
+    int64_t asm_count[5] = {0, 0, 0, 0, 0};
 
     // device arrays
     hm::DevBuf d_perm;   // int32 M: cluster position -> original id
@@ -274,7 +277,7 @@ struct hm_matrix {
     std::vector<int32_t> leaf_order_h;   // host copy of the order
     std::vector<int64_t> leaf_bytes_h;   // streamed elements per leaf (U + near)
     hm::DevBuf d_pos_prefix;             // int64 {0, M}
-    hm::DevBuf d_mesh[4];                // MeshDev of this matrix, per packed form
+    hm::DevBuf d_mesh[HM_NFORMS];        // MeshDev of this matrix, per packed form
     hm::DevBuf d_counters;               // int32 2*max_rhs: work counters of the streamed kernel
     hm::DevBuf d_err;                    // int32: set by a device wait that ran out
     int64_t ul_total = 0, nl_total = 0, vr_total = 0;
@@ -282,10 +285,11 @@ struct hm_matrix {
     // FP64 factor and near arenas in block order (ACA output, export)
     hm::DevBuf U64, V64, N64;
     // streaming arenas of each form (index = form): U leaf-major, V row-major
-    hm::DevBuf Ul[4], Vr[4];
+    hm::DevBuf Ul[HM_NFORMS], Vr[HM_NFORMS];
     hm::DevBuf Nl64, Nl32;  // near field leaf-major: FP64 form / all other forms
     hm::DevBuf SU, SV;      // per-column scales of the 16-bit forms (float, c_total)
-    bool packed[4] = {false, false, false, false};
+    hm::DevBuf SW16;        // HM_I16: per-column factor of w, SU SV / 32767^2 (float, c_total)
+    bool packed[HM_NFORMS] = {false, false, false, false, false};
     float wbound_su = 0.0f;  // max over factor columns of (U column scale x |s| of its block)
     bool compacted = false;  // FP64 data released (hm_compact)
     bool aca_deferred = false;  // HM_DEFER_ACA: no ACA at assembly (adaptive product only)

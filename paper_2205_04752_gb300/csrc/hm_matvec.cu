@@ -108,6 +108,30 @@ struct Vec16<__nv_bfloat16, TA> {
     }
 };
 
+template <class TA>
+struct Vec16<int16_t, TA> {
+    static constexpr int N = 8;
+    __device__ __forceinline__ static void load(const int16_t* p, TA* o)
+    {
+        uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float2 f = stream::i16x2_to_float2(wv[q]);
+            o[2 * q] = (TA)f.x;
+            o[2 * q + 1] = (TA)f.y;
+        }
+    }
+};
+
+// forms whose several-vector launches run on the tensor cores (FP16 / BF16
+// factors: tcgen05 kind::f16 operands); the INT16 form stays on the CUDA cores
+template <class TF>
+constexpr bool tc_form()
+{
+    return sizeof(TF) == 2 && !std::is_same<TF, int16_t>::value;
+}
+
 // element offset of V[j, c] (c a multiple of 8 for the vector loads) in a
 // forward group of n rows and Cs columns: row-major for FP64 / FP32; for the
 // 16-bit forms the group is cut into the units of the forward pass (rows
@@ -430,7 +454,7 @@ template <class TF, bool ONE>
 __global__ void __launch_bounds__(kTile1Threads) fwd_tile1_kernel(
     const FwdUnit* __restrict__ units, const FwdTcUnit* __restrict__ tcu, const FwdGroup* __restrict__ groups,
     const FwdRec* __restrict__ recs, const __grid_constant__ MeshDev m0, const MeshDev* __restrict__ meshes,
-    const float* __restrict__ xg, float* __restrict__ w, float* __restrict__ z, int* __restrict__ err)
+    const float* __restrict__ xg, float* __restrict__ w, float* __restrict__ z, int* __restrict__ err, int G, int r)
 {
     __shared__ __align__(128) unsigned char vs[2][kTile1Stage];
     __shared__ float4 xs[kFwdUnitRows];
@@ -457,8 +481,10 @@ __global__ void __launch_bounds__(kTile1Threads) fwd_tile1_kernel(
     const FwdUnit un = units[blockIdx.x];
     const FwdGroup gp = groups[un.group];
     for (int i = tid; i < gp.nrec; i += kTile1Threads) srec[i] = recs[gp.first + i];
-    const float4* xsrc = reinterpret_cast<const float4*>(xg) + md.xgoff + tu.x0;
-    for (int j = tid; j < n16; j += kTile1Threads) xs[j] = j < nrows ? xsrc[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    // vector r of the G interleaved ones: position p's 4-vector at p G + r
+    const float4* xsrc = reinterpret_cast<const float4*>(xg) + (size_t)(md.xgoff + tu.x0) * G + r;
+    for (int j = tid; j < n16; j += kTile1Threads)
+        xs[j] = j < nrows ? xsrc[(size_t)j * G] : make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     const int q = 4 * warp + (lane >> 3);  // this lane's column vector
     float acc[8][3];
@@ -517,7 +543,7 @@ __global__ void __launch_bounds__(kTile1Threads) fwd_tile1_kernel(
         }
     const int col = un.c0 + q * 8 + jr;  // column of the group
     if (un.zcol0 >= 0) {
-        float* d = z + (size_t)(un.zcol0 + (int64_t)un.chunk * gp.Cs + col) * 4;
+        float* d = z + ((size_t)(un.zcol0 + (int64_t)un.chunk * gp.Cs + col) * G + r) * 4;
         d[0] = z0;
         d[1] = z1;
         d[2] = z2;
@@ -529,9 +555,9 @@ __global__ void __launch_bounds__(kTile1Threads) fwd_tile1_kernel(
             else hi = mid - 1;
         }
         const FwdRec& rec = srec[lo];
-        float* wr = w + (size_t)md.woff * 4;
+        float* wr = w + (size_t)md.woff * 4 * G;
         if (col - rec.coff < rec.C)
-            write_w<float>(rec, col - rec.coff, z0, z1, z2, md.SU, wr, (float)md.c1, (float)md.c2, 1, 0);
+            write_w<float>(rec, col - rec.coff, z0, z1, z2, md.SU, wr, (float)md.c1, (float)md.c2, G, r);
     }
 }
 
@@ -798,6 +824,13 @@ template <>
 __device__ __forceinline__ __half cvt<__half>(double v) { return __float2half_rn((float)v); }
 template <>
 __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
+// INT16 form: v is already divided by its column's max |v| (|v| <= 1)
+template <>
+__device__ __forceinline__ int16_t cvt<int16_t>(double v)
+{
+    const int q = __double2int_rn(v * 32767.0);
+    return (int16_t)max(-32767, min(32767, q));
+}
 
 // per-column scale of the 16-bit forms: max |column| (1 for a zero column)
 __global__ void colscale_kernel(int ntask, const Blk* __restrict__ blks, const int32_t* __restrict__ rank,
@@ -822,6 +855,14 @@ __global__ void colscale_kernel(int ntask, const Blk* __restrict__ blks, const i
         for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (lane == 0) (isu ? SU : SV)[coff[q] + l] = mx > 0.0 ? (float)mx : 1.0f;
     }
+}
+
+// INT16 form: the factor of w per column, (max|u| / 32767) (max|v| / 32767)
+__global__ void sw16_kernel(int64_t n, const float* __restrict__ SU, const float* __restrict__ SV,
+                            float* __restrict__ SW)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n) SW[c] = (float)((double)SU[c] * (double)SV[c] / (32767.0 * 32767.0));
 }
 
 // U leaf-major: one CTA per leaf.  The 16-bit forms store each leaf's stream
@@ -970,7 +1011,7 @@ int stream_launch(StreamLaunch& out)
 template <class TF>
 constexpr bool fwd_on_tc(int G)
 {
-    return sizeof(TF) == 2 && G >= 2;
+    return tc_form<TF>() && G >= 2;
 }
 
 // The forward pass of the 16-bit forms on the tensor cores: one persistent
@@ -1009,8 +1050,11 @@ int run_forward_tc(const Plan& P, const float* xg, float* w, float* z, int G, co
 // One vector of a 16-bit form on the CUDA cores: one CTA per unit (with a
 // fork schedule the unit list is split in two halves on two streams), then
 // the second pass of the tall groups.
+// Several vectors of the INT16 form take the same kernel once per vector
+// (vector r of the G interleaved ones), each launch reading the tiles again.
 template <class TF>
-int run_forward_tile1(const Plan& P, const float* xg, float* w, float* z, cudaStream_t s, const Sched& sc)
+int run_forward_tile1(const Plan& P, const float* xg, float* w, float* z, cudaStream_t s, const Sched& sc,
+                      int G = 1)
 {
     const bool one = P.nmesh == 1;
     const MeshDev m0 = one ? P.mesh0 : MeshDev{};
@@ -1019,9 +1063,11 @@ int run_forward_tile1(const Plan& P, const float* xg, float* w, float* z, cudaSt
     auto launch = [&](int64_t first, int64_t n, cudaStream_t st) -> int {
         if (n <= 0) return HM_OK;
         auto kt = one ? fwd_tile1_kernel<TF, true> : fwd_tile1_kernel<TF, false>;
-        kt<<<(unsigned)n, kTile1Threads, 0, st>>>(P.units + first, P.tcu + first, P.groups, P.fwd, m0, P.meshes, xg,
-                                                  w, z, P.err);
-        HM_CUDA(cudaGetLastError());
+        for (int r = 0; r < G; ++r) {
+            kt<<<(unsigned)n, kTile1Threads, 0, st>>>(P.units + first, P.tcu + first, P.groups, P.fwd, m0, P.meshes,
+                                                      xg, w, z, P.err, G, r);
+            HM_CUDA(cudaGetLastError());
+        }
         return HM_OK;
     };
     if (fork) {
@@ -1040,7 +1086,7 @@ int run_forward_tile1(const Plan& P, const float* xg, float* w, float* z, cudaSt
     }
     if (P.nmulti > 0) {
         auto red = one ? fwd_reduce_kernel<float, true> : fwd_reduce_kernel<float, false>;
-        red<<<(unsigned)P.nmulti, kFwdThreads, 0, s>>>(P.multi, P.groups, P.fwd, m0, P.meshes, z, w, 1);
+        red<<<(unsigned)P.nmulti, kFwdThreads, 0, s>>>(P.multi, P.groups, P.fwd, m0, P.meshes, z, w, G);
         HM_CUDA(cudaGetLastError());
     }
     return HM_OK;
@@ -1056,8 +1102,8 @@ int run_forward(const Plan& P, TA* xg, TA* w, TA* z, int G, const int* xmax, cud
     if constexpr (sizeof(TF) == 2 && std::is_same<TA, float>::value) {
         // the tiles of V: one vector on the CUDA cores, several (up to 16) on
         // the tensor cores
-        if (G == 1) return run_forward_tile1<TF>(P, xg, w, z, s, sc);
-        return run_forward_tc<TF>(P, xg, w, z, G, xmax, s);
+        if (G == 1 || !tc_form<TF>()) return run_forward_tile1<TF>(P, xg, w, z, s, sc, G);
+        if constexpr (tc_form<TF>()) return run_forward_tc<TF>(P, xg, w, z, G, xmax, s);
     }
     const bool one = P.nmesh == 1;
     const MeshDev m0 = one ? P.mesh0 : MeshDev{};
@@ -1237,7 +1283,7 @@ int run_product_t(const Plan& P, const double* x, double* y, int nrhs, int64_t l
     if (P.nwork > 0) HM_CUDA(cudaMemsetAsync(P.counters, 0, 64 * sizeof(int), s));
     if (nrhs == 1) return run_phases<TF, TN, TA, 1>(P, x, y, 1, ld, xg, w, P.counters, s, prof, sc);
     int k = 0, r0 = 0;
-    if constexpr (sizeof(TF) == 2 && std::is_same<TA, float>::value) {
+    if constexpr (tc_form<TF>() && std::is_same<TA, float>::value) {
         // 16-bit factors: launches of 16 vectors (at least kTcMinG) take the
         // far field to the tensor cores; fewer vectors stay on the CUDA cores,
         // where the per-stage latency of the tensor-core pipeline does not pay
@@ -1325,6 +1371,7 @@ int product_prepare(int32_t form, int* ctas_per_sm)
         case HM_FP32: return prepare_t<float, float, float>(ctas_per_sm);
         case HM_BF16: return prepare_t<__nv_bfloat16, float, float>(ctas_per_sm);
         case HM_FP16: return prepare_t<__half, float, float>(ctas_per_sm);
+        case HM_I16: return prepare_t<int16_t, float, float>(ctas_per_sm);
         default: return fail(HM_EINVAL, "product: unknown form %d", form);
     }
 }
@@ -1346,6 +1393,9 @@ int run_product(const Plan& P, int32_t form, const double* x, double* y, int32_t
         case HM_FP16:
             return run_product_t<__half, float, float>(P, x, y, nrhs, ld, static_cast<float*>(xg),
                                                        static_cast<float*>(w), s, prof, sc);
+        case HM_I16:
+            return run_product_t<int16_t, float, float>(P, x, y, nrhs, ld, static_cast<float*>(xg),
+                                                        static_cast<float*>(w), s, prof, sc);
         default:
             return fail(HM_EINVAL, "product: unknown form %d", form);
     }
@@ -1357,7 +1407,7 @@ MeshDev mesh_desc(const hm_matrix& H, int32_t form)
     m.Ul = H.Ul[form].p;
     m.Vr = H.Vr[form].p;
     m.Nl = form == HM_FP64 ? H.Nl64.p : H.Nl32.p;
-    m.SU = (form == HM_BF16 || form == HM_FP16) ? H.SU.as<float>() : nullptr;
+    m.SU = (form == HM_BF16 || form == HM_FP16) ? H.SU.as<float>() : (form == HM_I16 ? H.SW16.as<float>() : nullptr);
     m.fdesc = (form == HM_BF16 || form == HM_FP16) ? H.fdesc.as<uint2>() : nullptr;
     m.leaf = H.d_leaf.as<int32_t>();
     m.lf_base = H.d_lf_base.as<int64_t>();
@@ -1477,6 +1527,23 @@ int pack_device(hm_matrix& H, int32_t form, cudaStream_t s)
                 HM_CUDA(cudaGetLastError());
             }
         }
+        if (form == HM_I16) {
+            // block floating point: U and V each divided by their column's
+            // max |value| and stored as round(32767 v); w carries the product
+            // of the two scales and 1 / 32767^2
+            if (!H.SW16.p) {
+                if ((rc = dalloc(H, H.SW16, (size_t)std::max<int64_t>(H.c_total, 1) * 4))) return rc;
+                if (H.c_total > 0) {
+                    sw16_kernel<<<(unsigned)((H.c_total + 255) / 256), 256, 0, s>>>(H.c_total, H.SU.as<float>(),
+                                                                                    H.SV.as<float>(), H.SW16.as<float>());
+                    HM_CUDA(cudaGetLastError());
+                }
+            }
+            if ((rc = pack_form<int16_t>(H, HM_I16, H.SU.as<float>(), H.SV.as<float>(), s))) return rc;
+            if ((rc = write_mesh_table(H, form, s))) return rc;
+            H.packed[form] = true;
+            return HM_OK;
+        }
         if (!H.fdesc.p) {
             if (H.c_total > kFdMaxCol) return fail(HM_EINVAL, "16-bit forms: more than %lld factor columns", (long long)kFdMaxCol);
             if ((rc = dalloc(H, H.fdesc, (size_t)std::max<int64_t>(H.dcols, 1) * sizeof(uint2)))) return rc;
@@ -1530,7 +1597,7 @@ extern "C" {
 int hm_pack(hm_matrix* H, int32_t form, void* stream)
 {
     if (!H) return fail(HM_EINVAL, "hm_pack: NULL matrix");
-    if (form < HM_FP64 || form > HM_FP16) return fail(HM_EINVAL, "hm_pack: unknown form %d", form);
+    if (form < HM_FP64 || form >= HM_NFORMS) return fail(HM_EINVAL, "hm_pack: unknown form %d", form);
     if (H->rect && form != HM_FP64 && form != HM_FP32)
         return fail(HM_EINVAL, "hm_pack: an evaluation operator has the forms HM_FP64 and HM_FP32");
     if (H->rect && form == HM_FP64) return HM_OK;  // its FP64 arenas are the FP64 form
@@ -1567,7 +1634,7 @@ int hm_matvec(const hm_matrix* H, const double* x, double* y, int32_t nrhs, int6
     if (nrhs < 1 || nrhs > H->max_rhs)
         return fail(HM_EINVAL, "hm_matvec: nrhs=%d outside 1..%d", nrhs, H->max_rhs);
     if (ld < 3 * H->M) return fail(HM_EINVAL, "hm_matvec: ld=%lld < 3M=%lld", (long long)ld, (long long)(3 * H->M));
-    if (form < HM_FP64 || form > HM_FP16) return fail(HM_EINVAL, "hm_matvec: unknown form %d", form);
+    if (form < HM_FP64 || form >= HM_NFORMS) return fail(HM_EINVAL, "hm_matvec: unknown form %d", form);
     if (!H->packed[form]) return fail(HM_EINVAL, "hm_matvec: form %d not packed (call hm_pack)", form);
     const char* xb = (const char*)x;
     const char* yb = (const char*)y;

@@ -16,40 +16,29 @@
 // give wrong results.  Nothing in it has to start at zero: every call
 // overwrites each scratch element before reading it.
 #include <algorithm>
-#include <mutex>
 
 #include "hm_internal.h"
 
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB
-constexpr int kMaxDevices = 64;
-
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
-
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
 
 // Device address of the array on the current device.  In host code the name
 // g_noalloc_scratch is only a host-side stand-in for the symbol, never a
-// device address, so the address is looked up once per device with that
-// device current (this also loads the module on that device).
+// device address, so the address is looked up with the calling device
+// current.  It is looked up on every call (cheap once the module is loaded):
+// a cached address would go stale if the caller reset the device, which
+// unloads the module and may place the array elsewhere on reload.  The first
+// call on a device may load the library's device code there.
 int scratch_address(void** out)
 {
-    int dev = 0;
-    HM_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices)
-        return hm::fail(HM_EDEVICE, "hm_matvec_noalloc: device ordinal %d not supported", dev);
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return hm::cuda_check(e != cudaSuccess ? e : cudaErrorInvalidSymbol,
-                                  "cudaGetSymbolAddress(g_noalloc_scratch)");
-        g_addr[dev] = p;
-    }
-    *out = g_addr[dev];
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return hm::cuda_check(e != cudaSuccess ? e : cudaErrorInvalidSymbol,
+                              "cudaGetSymbolAddress(g_noalloc_scratch)");
+    *out = p;
     return HM_OK;
 }
 
@@ -66,7 +55,7 @@ extern "C" int hm_matvec_noalloc(const hm_matrix* H, const double* x, double* y,
     if (ld < 3 * H->M)
         return fail(HM_EINVAL, "hm_matvec_noalloc: ld=%lld < 3M=%lld", (long long)ld,
                     (long long)(3 * H->M));
-    if (form < HM_FP64 || form > HM_FP16) return fail(HM_EINVAL, "hm_matvec_noalloc: unknown form %d", form);
+    if (form < HM_FP64 || form >= HM_NFORMS) return fail(HM_EINVAL, "hm_matvec_noalloc: unknown form %d", form);
     if (!H->packed[form])
         return fail(HM_EINVAL, "hm_matvec_noalloc: form %d not packed (call hm_pack)", form);
     const char* xb = (const char*)x;

@@ -256,7 +256,7 @@ int hm_server_create(const hm_matrix* const* mats, int32_t nmat, const hm_server
     if (p.restart > 127) return fail(HM_EINVAL, "hm_server_create: restart above 127");
     if (p.inner_tol <= 0.0) p.inner_tol = 1e-3;
     for (int32_t f : {p.matvec_form, p.inner_form, p.residual_form})
-        if (f < HM_FP64 || f > HM_FP16) return fail(HM_EINVAL, "hm_server_create: unknown form %d", f);
+        if (f < HM_FP64 || f >= HM_NFORMS) return fail(HM_EINVAL, "hm_server_create: unknown form %d", f);
     for (int32_t m = 0; m < nmat; ++m) {
         const hm_matrix* H = mats[m];
         if (!H) return fail(HM_EINVAL, "hm_server_create: matrix %d is NULL", m);

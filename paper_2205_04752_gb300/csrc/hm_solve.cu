@@ -140,10 +140,10 @@ int solve_check_params(const hm_matrix* H, hm_solve_params& p)
     if (p.inner_tol <= 0.0) p.inner_tol = 1e-3;
     if (p.max_inner <= 0) p.max_inner = 1000;
     if (p.max_refine <= 0) p.max_refine = 20;
-    if (p.residual_form < HM_FP64 || p.residual_form > HM_FP16 || !H->packed[p.residual_form])
+    if (p.residual_form < HM_FP64 || p.residual_form >= HM_NFORMS || !H->packed[p.residual_form])
         return fail(HM_EINVAL, "hm_solve: residual form %d not available (FP64 released by hm_compact, or not packed)",
                     p.residual_form);
-    if (p.inner_form < HM_FP64 || p.inner_form > HM_FP16 || !H->packed[p.inner_form])
+    if (p.inner_form < HM_FP64 || p.inner_form >= HM_NFORMS || !H->packed[p.inner_form])
         return fail(HM_EINVAL, "hm_solve: inner form %d not available (hm_pack first)", p.inner_form);
     return HM_OK;
 }

@@ -210,6 +210,35 @@ struct Smem16<__nv_bfloat16, TA> {
     }
 };
 
+// Two int16 values of a 32-bit word (low half first) as exact FP32 values:
+// q ^ 0x8000 is q + 32768 as an unsigned 16-bit integer u; placed under the
+// exponent of 2^23 (bytes u_lo, u_hi, 0x00, 0x4B) it is the float 2^23 + u,
+// and subtracting 2^23 + 2^15 leaves q exactly.  Integer byte permutes and
+// one FP32 add per value, no int-to-float conversion instruction.
+__device__ __forceinline__ float2 i16x2_to_float2(uint32_t word)
+{
+    const uint32_t u = word ^ 0x80008000u;
+    const float lo = __uint_as_float(__byte_perm(u, 0x4B000000u, 0x7410)) - 8421376.0f;
+    const float hi = __uint_as_float(__byte_perm(u, 0x4B000000u, 0x7432)) - 8421376.0f;
+    return make_float2(lo, hi);
+}
+
+template <class TA>
+struct Smem16<int16_t, TA> {
+    static constexpr int N = 8;
+    __device__ __forceinline__ static void load(const int16_t* p, TA* o)
+    {
+        uint4 v = *reinterpret_cast<const uint4*>(p);
+        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float2 f = i16x2_to_float2(wv[q]);
+            o[2 * q] = (TA)f.x;
+            o[2 * q + 1] = (TA)f.y;
+        }
+    }
+};
+
 __device__ __forceinline__ void load3(const float* p, float& a, float& b, float& c)
 {
     const float4 v = *reinterpret_cast<const float4*>(p);

@@ -41,20 +41,32 @@ def product(H, x):
     return yd.cpu().numpy()
 
 
-def test_amvm_follows_the_oracle():
-    """Same mesh, partition and ACA epsilon: the GPU and the oracle run the
-    same refinement (the estimator sequences agree to the rounding of the
-    two ACA runs) and end at products that agree to the requested accuracy."""
+@pytest.mark.parametrize("seed,theta", [(0, 0.7), (3, 0.5)])
+def test_amvm_follows_the_oracle(seed, theta):
+    """Same mesh, partition and ACA epsilon: the GPU and the oracle take the
+    same refinement steps.  The GPU finds step 3's stopping row by bisection
+    over the sorted rows; the oracle scans them one by one.  The two rows
+    coincide when the remaining error gamma_k(P_k) does not grow along the
+    scan, which is asserted on the oracle's scan for these inputs.  Then
+    every step marks the same blocks (the same final ranks and marked
+    counts), the estimators agree to the rounding of the two ACA runs, and
+    the products agree to 1e-12."""
     V, T, tree, H, Ho = case()
-    x = inputs.uniform_rhs(3 * Ho.M, 0)[0]
-    y, info = run(H, x, theta=0.7, eps=1e-6)
-    ro = oracle.amvm(Ho, E, NU, x, theta=0.7, eps=1e-6)
+    x = inputs.uniform_rhs(3 * Ho.M, seed)[0]
+    ro = oracle.amvm(Ho, E, NU, x, theta=theta, eps=1e-6, record_scan=True)
+    for k, sc in enumerate(ro["scans"]):
+        assert np.all(np.diff(sc) <= 0), k  # the case the bisection must reproduce
+    y, info = run(H, x, theta=theta, eps=1e-6)
     assert info["csp"] == ro["csp"]
-    assert abs(info["iterations"] - ro["iterations"]) <= 1
-    n = min(len(info["gamma"]), len(ro["gamma"]))
-    for k in range(min(n, 3)):
-        assert abs(info["gamma"][k] - ro["gamma"][k]) <= 1e-6 * ro["gamma"][k], k
-    assert np.linalg.norm(y - ro["b"]) <= 4e-6 * np.linalg.norm(ro["b"])
+    assert info["iterations"] == ro["iterations"]
+    assert info["marked_total"] == sum(ro["marked"])
+    np.testing.assert_array_equal(info["block_ranks"], ro["r"])
+    assert len(info["gamma"]) == len(ro["gamma"])
+    for k, (g, go) in enumerate(zip(info["gamma"], ro["gamma"])):
+        assert abs(g - go) <= 1e-10 * go, k
+    for k, (g, go) in enumerate(zip(info["gamma_rest"], ro["gamma_rest"])):
+        assert abs(g - go) <= 1e-10 * ro["gamma"][k], k
+    assert np.linalg.norm(y - ro["b"]) <= 1e-12 * np.linalg.norm(ro["b"])
     yf = Ho.matvec(E, NU, x)[0]
     assert np.linalg.norm(y - yf) <= 1e-5 * np.linalg.norm(yf)
 

@@ -35,8 +35,8 @@ def members():
             V, T = _mesh(name)
             tr = binding.build_cluster_tree(V, T, leaf, 0.8)
             H = binding.aca_assemble(tr, E, nu, 1e-4, max_rhs=4)
-            H.pack("fp16")
-            H.pack("fp32")
+            for form in ("fp16", "fp32", "i16"):
+                H.pack(form)
             out.append((name, V, T, leaf, E, nu, tr, H))
         _cache["m"] = out
     return _cache["m"]
@@ -48,11 +48,13 @@ def _alone(H, x, form):
     return y
 
 
-@pytest.mark.parametrize("form,nrhs", [("fp64", 3), ("fp16", 3), ("fp32", 3), ("fp16", 1), ("fp32", 1)])
+@pytest.mark.parametrize("form,nrhs", [("fp64", 3), ("fp16", 3), ("fp32", 3), ("fp16", 1), ("fp32", 1), ("i16", 1),
+                                       ("i16", 3)])
 def test_batch_equals_each_member_alone_bitwise(form, nrhs):
     """One launch per phase over all members gives each member's own bits:
     the FP16 form with one vector (forward pass from the tiles on the CUDA
-    cores) and with three (on the tensor cores), FP32 and FP64 (row-major)."""
+    cores) and with three (on the tensor cores), the INT16 form (CUDA cores),
+    FP32 and FP64 (row-major)."""
     ms = members()
     B = binding.Batch([m[-1] for m in ms], form, max_rhs=3)
     assert B.ndof == sum(3 * len(m[2]) for m in ms)

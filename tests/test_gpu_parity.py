@@ -96,15 +96,24 @@ def test_hmatvec_fp64_matches_oracle_and_dense():
         assert _rel(y[r], yd[r]) <= 1e-4
 
 
-@pytest.mark.parametrize("form,tol", [("fp32", 1e-5), ("bf16", 1e-2), ("fp16", 2e-3)])
-def test_packed_forms_against_fp64_form(form, tol):
+# Relative error of each packed form against the FP64 form at C1, bounded at
+# about twice what the forms reach there (measured on GB300 with these
+# inputs: FP32 2.7e-7, BF16 3.3e-4, FP16 4.1e-5, INT16 3.0e-6); the errors
+# follow each storage type's rounding of the factors (unit roundoff 2^-24,
+# 2^-8, 2^-11, and 2^-16 of each column's largest entry)
+C1_BOUNDS = {"fp32": 6e-7, "bf16": 7e-4, "fp16": 8e-5, "i16": 6e-6}
+
+
+@pytest.mark.parametrize("form", ["fp32", "bf16", "fp16", "i16"])
+def test_packed_forms_against_fp64_form(form):
     c = c1()
     c.H.pack(form)
     x = inputs.uniform_rhs(3 * c.M, 1, nrhs=2)
     y64 = c.matvec(x)
     y = c.matvec(x, form)
-    for r in range(2):
-        assert _rel(y[r], y64[r]) <= tol
+    errs = [_rel(y[r], y64[r]) for r in range(2)]
+    print(f"C1 {form}: {max(errs):.3e}")
+    assert max(errs) <= C1_BOUNDS[form]
 
 
 def test_deterministic_and_multi_rhs_consistent():
@@ -118,7 +127,7 @@ def test_deterministic_and_multi_rhs_consistent():
         np.testing.assert_allclose(ys[0], y1[r], rtol=0, atol=1e-14 * np.abs(y1[r]).max())
 
 
-@pytest.mark.parametrize("form", ["fp16", "fp32", "bf16", "fp64"])
+@pytest.mark.parametrize("form", ["fp16", "fp32", "bf16", "i16", "fp64"])
 def test_multi_rhs_launches_match_single_vector_products(form):
     """Several right-hand sides share one pass over the factors (interleaved
     vectors, up to 32 per launch): each row agrees with the single-vector
@@ -234,27 +243,69 @@ def test_small_and_ragged_meshes(mesh, leaf):
         assert (c.Ho.ranks() == 0).any()
 
 
+def l6():
+    """The benchmark workload: level-6 icosphere (81,920 triangles, 245,760
+    dofs), leaf 64, eta 0.8, eps 1e-4, assembled with room for 32 vectors
+    per call as bench.py does."""
+    if "l6" not in _cache:
+        V, T = inputs.icosphere(6)
+        tree = binding.build_cluster_tree(V, T, 64, 0.8)
+        H = binding.aca_assemble(tree, E, NU, 1e-4, max_rhs=32)
+        _cache["l6"] = (V, T, tree, H)
+    return _cache["l6"]
+
+
+def _l6_products(H, M, form, nrhs, seed):
+    x = torch.tensor(inputs.uniform_rhs(3 * M, seed, nrhs=nrhs), device="cuda")
+    y64 = torch.empty_like(x)
+    y = torch.full_like(x, float("nan"))
+    binding.hmatvec(H, x, y64, "fp64")
+    binding.hmatvec(H, x, y, form)
+    torch.cuda.synchronize()
+    d = torch.linalg.norm(y - y64, dim=1) / torch.linalg.norm(y64, dim=1)
+    return d.cpu().numpy()
+
+
+# E_mixed = ||y_form - y_fp64|| / ||y_fp64|| over the full 245,760-dof vector
+# of every right-hand side, at the benchmark workload, one vector and 32 in
+# one call.  INT16 (the form the benchmark times) is gated at the metric's
+# 1e-4.  FP16 does not meet it at this size (8.2e-5 for seed 0 alone but up to
+# 1.21e-4 over 32 vectors): it is kept, bounded at its own measured level, as
+# the form of the tensor-core kernels.  BF16 keeps three fewer mantissa bits
+# than FP16 (unit roundoff 2^-8 against 2^-11), about 8x FP16's error, and
+# serves as an inner form of the refined solve.  FP32 is gated far below
+# (measured on GB300: INT16 7.9e-6, FP16 1.21e-4, BF16 9.7e-4, FP32 1.4e-6).
+L6_BOUNDS = {"i16": 1e-4, "fp16": 1.5e-4, "bf16": 1.5e-3, "fp32": 3e-6}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("form", ["i16", "fp16", "bf16", "fp32"])
+def test_level6_mixed_form_error_against_fp64_form(form):
+    V, T, tree, H = l6()
+    H.pack(form)
+    M = len(T)
+    e1 = _l6_products(H, M, form, 1, 0)
+    e32 = _l6_products(H, M, form, 32, 0)
+    print(f"E_mixed {form}: R=1 {e1.max():.3e}, R=32 max {e32.max():.3e} mean {e32.mean():.3e}")
+    assert e1.max() <= L6_BOUNDS[form]
+    assert e32.max() <= L6_BOUNDS[form]
+
+
 @pytest.mark.slow
 def test_level6_sampled_rows_and_blocks():
     """The benchmark workload (level-6 icosphere, 245,760 dofs, leaf 64,
     eta 0.8, eps 1e-4) in the configuration the benchmark times: the FP64
     product against exact rows of the dense product at 384 sampled triangles
-    (relative error <= 1e-4), the FP32 form against the FP64 form on the full
-    vector (<= 1e-4), and ACA parity on 60 sampled admissible blocks."""
-    V, T = inputs.icosphere(6)
+    (relative error <= 1e-4), and ACA parity on 60 sampled admissible
+    blocks."""
+    V, T, tree, H = l6()
     M = len(T)
-    tree = binding.build_cluster_tree(V, T, 64, 0.8)
-    H = binding.aca_assemble(tree, E, NU, 1e-4, max_rhs=1)
-    H.pack("fp32")
     x = inputs.uniform_rhs(3 * M, 0)
     xd = torch.tensor(x, device="cuda")
     y64 = torch.empty_like(xd)
-    y32 = torch.empty_like(xd)
     binding.hmatvec(H, xd[0], y64[0], "fp64")
-    binding.hmatvec(H, xd[0], y32[0], "fp32")
     torch.cuda.synchronize()
-    y64, y32 = y64.cpu().numpy(), y32.cpu().numpy()
-    assert _rel(y32[0], y64[0]) <= 1e-4
+    y64 = y64.cpu().numpy()
     rows = inputs.sample_rows(M, 384, 11)
     yr = oracle.kelvin_rows_matvec(V, T, E, NU, rows, x)[0]
     dofs = (3 * rows[:, None] + np.arange(3)[None, :]).ravel()
@@ -275,3 +326,4 @@ def test_level6_sampled_rows_and_blocks():
             assert Ug.shape[1] == Uo.shape[1], (b, kern)
             So = Uo @ Vo.T
             assert np.linalg.norm(Ug @ Vg.T - So) <= 1e-12 * np.linalg.norm(So), (b, kern)
+    _cache.pop("l6", None)  # release the level-6 matrix (tens of GB) for the later tests
