@@ -145,8 +145,17 @@ int hm_build_point_tree(const hm_tree* surface, const double* pts, int64_t npts,
  *   out      new tree: hm_tree_sizes / hm_tree_export describe the vertex
  *            tree (perm over the vertices, nodes) and the partition (row node
  *            of the surface tree, column node of the vertex tree)
- * The device assembly of the double layer is not built yet: hm_aca_assemble
- * refuses this tree (HM_EINVAL).
+ * hm_aca_assemble on this tree assembles K_Delta (Eq. (Kh) in collocation
+ * form, the collocation point's own flat panel contributing 0):
+ *   K_Delta[i, p] = 1/(4 pi) sum over the triangles tau_j holding vertex p of
+ *                   int_{tau_j} (c_i - y).n_j / |c_i - y|^3 psi_p(y) ds_y,
+ * near blocks entry by entry and one ACA (Algorithm 1) per admissible block,
+ * with the quadrature of the single layer (the 7-point rule, subdivided
+ * near c_i).  The matrix is a rectangular operator (rows the triangles,
+ * columns the vertices): hm_eval_points applies K_Delta to each component
+ * (u of 3 nv values, dof 3p + b), hm_double_layer_matvec the whole K_h.
+ * A block whose triangles all lie in one plane has K_Delta = 0 in exact
+ * arithmetic; its computed entries are rounding noise (not special-cased).
  * Errors: HM_EINVAL (NULL, `surface` not a triangle tree, leaf out of range,
  * a vertex in no triangle), HM_ENOMEM.
  * ------------------------------------------------------------------------- */
@@ -273,6 +282,35 @@ int hm_matvec(const hm_matrix* H, const double* x, double* y, int32_t nrhs, int6
  * ------------------------------------------------------------------------- */
 int hm_matvec_noalloc(const hm_matrix* H, const double* x, double* y, int32_t nrhs, int64_t ld,
                       int32_t form, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * hm_double_layer_matvec -- y = K_h u, the double-layer operator of Section
+ * 4.2, Eq. (Kh), in collocation form:
+ *   K_h = diag(K_Delta) - diag(V_Delta) T_h + E/(1+nu) V_h T_h,
+ * T_h the surface curls T_kl = n_l d_k - n_k d_l of the hat functions
+ * (constant on each flat triangle; the tangential derivative, antisymmetric
+ * in (k, l), T_h = [[0, T12, T13], [-T12, 0, T23], [-T13, -T23, 0]]).  The
+ * last two terms are one single-layer product of w = T_h u with the
+ * coefficients ((1 - 2nu) / (2(1 - nu)), 1 / (2(1 - nu))) in place of
+ * (c1, c2): E cancels.  Rigid motions u (translations, rotations) give
+ * K_h u = -u/2 up to the discretisation error.
+ *   V     the single layer of the mesh (hm_aca_assemble on its triangle
+ *         tree), with `form` packed; its material nu is used.  The first call
+ *         allocates a small mesh table in V (hence non-const).
+ *   K     K_Delta (hm_aca_assemble on hm_build_vertex_tree of the same
+ *         triangle tree); FP64 factors
+ *   u     device, nrhs rows of 3 nv doubles (vertex p, component b at 3p + b,
+ *         original vertex order)
+ *   y     device, nrhs rows of 3M doubles (3i + a, original triangle order),
+ *         overwritten; must not overlap u
+ *   form  the product form of the V_h part (K_Delta is applied in FP64)
+ * Asynchronous on `stream`; calls on the same V or K must not overlap.
+ * Errors: HM_EINVAL (NULL, V not a triangle tree's matrix or K not a vertex
+ * tree's, different meshes, nrhs < 1, form not packed, K without factors),
+ * HM_ENOMEM, HM_EDEVICE.
+ * ------------------------------------------------------------------------- */
+int hm_double_layer_matvec(hm_matrix* V, const hm_matrix* K, const double* u, double* y, int32_t nrhs,
+                           int32_t form, void* stream);
 
 /* Same product with HOST x and y: copies x in, runs hm_matvec, copies y back
  * and synchronises `stream`.  Pinned host memory gives the fastest copies. */

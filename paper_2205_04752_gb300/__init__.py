@@ -8,8 +8,8 @@ The binding is imported lazily so that ``paper_2205_04752_gb300.inputs``
 """
 
 __all__ = ["build_cluster_tree", "aca_assemble", "hmatvec", "hmatvec_host", "solve", "HMatrix",
-           "ClusterTree", "PointTree", "build_point_tree", "eval_points", "amvm", "FP64", "FP32", "BF16",
-           "FP16"]
+           "ClusterTree", "PointTree", "build_point_tree", "eval_points", "amvm", "VertexTree",
+           "build_vertex_tree", "double_layer_matvec", "FP64", "FP32", "BF16", "FP16", "I16"]
 
 
 def __getattr__(name):

@@ -33,7 +33,7 @@ SYMBOLS = (
     "hm_batch_set_schedule", "hm_batch_get_schedule", "hm_batch_check", "hm_batch_destroy",
     "hm_compact", "hm_footprint", "hm_server_create", "hm_server_footprint", "hm_server_run",
     "hm_server_destroy", "hm_amvm", "hm_build_point_tree", "hm_eval_points", "hm_baca",
-    "hm_build_vertex_tree",
+    "hm_build_vertex_tree", "hm_double_layer_matvec",
 )
 
 
@@ -159,6 +159,7 @@ def load():
         "hm_build_point_tree": (ctypes.c_int, [P, P, I64, I32, ctypes.POINTER(P)]),
         "hm_build_vertex_tree": (ctypes.c_int, [P, I32, ctypes.POINTER(P)]),
         "hm_eval_points": (ctypes.c_int, [P, P, P, I32, I32, P]),
+        "hm_double_layer_matvec": (ctypes.c_int, [P, P, P, P, I32, I32, P]),
         "hm_aca_assemble": (ctypes.c_int, [P, ctypes.POINTER(_Params), ctypes.POINTER(_Allocator),
                                            P, ctypes.POINTER(P)]),
         "hm_set_material": (ctypes.c_int, [P, D, D]),
@@ -287,7 +288,7 @@ class VertexTree(ClusterTree):
     """Columns of the double layer's K_Delta (Eq. (Kh)): the cluster tree of
     the mesh vertices with star boxes and the partition (triangle tree of
     ``surface``) x (vertex tree), ``hm_build_vertex_tree``.  ``M`` counts the
-    vertices, ``M_src`` the triangles.  (Its device assembly is not built.)"""
+    vertices, ``M_src`` the triangles.  ``HMatrix`` on it assembles K_Delta."""
 
     def __init__(self, surface: ClusterTree, leaf: int):
         lib = load()
@@ -354,10 +355,15 @@ class HMatrix:
                  torch_memory: bool = True, defer_fp64: bool = False, defer_aca: bool = False):
         import torch
         lib = load()
-        # columns are triangles; rows are the points of an evaluation operator
-        self.rect = isinstance(tree, PointTree)
-        self.M = tree.M_src if self.rect else tree.M
-        self.Mr = tree.M
+        # columns are triangles (the vertices for the double layer's K_Delta);
+        # rows are the triangles (the points of an evaluation operator)
+        self.dl = isinstance(tree, VertexTree)
+        self.rect = isinstance(tree, (PointTree, VertexTree))
+        if self.dl:
+            self.M, self.Mr = tree.M, tree.M_src
+        else:
+            self.M = tree.M_src if self.rect else tree.M
+            self.Mr = tree.M
         self.device = torch.cuda.current_device()
         prm = _Params(float(E), float(nu), float(aca_eps), float(aca_eta_stop), int(kmax),
                       int(max_rhs), (1 if defer_fp64 else 0) | (2 if defer_aca else 0), 0)
@@ -522,6 +528,25 @@ def amvm(H: HMatrix, x, y, theta: float = 0.7, eps: float = 1e-6, r0: int = 2, l
                 gamma_rest=list(gr[:min(k, cap)]), bhat_norm=info.bhat_norm,
                 crosses_used=int(info.crosses_used), crosses_full=int(info.crosses_full),
                 marked_total=int(info.marked_total), block_ranks=ranks[:H.stats().nadm].copy())
+
+
+def double_layer_matvec(V: HMatrix, K: HMatrix, u, y, form="fp64", stream=None):
+    """``hm_double_layer_matvec``: y = K_h u, the double layer of Eq. (Kh) in
+    collocation form.  V: the single layer of the mesh (``form`` packed), K:
+    K_Delta (an ``HMatrix`` of a ``VertexTree`` of the same triangle tree).
+    u: CUDA float64 (3 nv,) or (nrhs, 3 nv) in the original vertex order; y:
+    (3M,) or (nrhs, 3M); both contiguous."""
+    import torch
+    f = FORMS[form] if isinstance(form, str) else int(form)
+    if not (u.is_cuda and y.is_cuda and u.dtype == torch.float64 and y.dtype == torch.float64):
+        raise TypeError("double_layer_matvec: u and y must be CUDA float64 tensors")
+    nrhs = 1 if u.dim() == 1 else u.shape[0]
+    if (u.shape[-1] != 3 * K.M or y.shape[-1] != 3 * V.M or (u.dim() == 2) != (y.dim() == 2)
+            or (u.dim() == 2 and y.shape[0] != nrhs) or not u.is_contiguous() or not y.is_contiguous()):
+        raise ValueError("double_layer_matvec: u must be contiguous rows of 3 nv, y rows of 3M")
+    _check(load().hm_double_layer_matvec(V._h, K._h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                         nrhs, f, _stream_handle(stream)))
+    return y
 
 
 def eval_points(H: HMatrix, t, u, form="fp64", stream=None):

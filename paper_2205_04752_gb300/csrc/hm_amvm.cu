@@ -176,6 +176,7 @@ extern "C" int hm_amvm(hm_matrix* H, const double* x, double* y, const hm_amvm_p
                        int32_t* block_ranks, void* stream)
 {
     if (!H || !x || !y || !prm) return fail(HM_EINVAL, "hm_amvm: NULL argument");
+    if (H->dl) return fail(HM_EINVAL, "hm_amvm: the double layer's K_Delta is applied by hm_double_layer_matvec");
     if (prm->flags & ~HM_AMVM_ACA_ON_DEMAND) return fail(HM_EINVAL, "hm_amvm: unknown flags 0x%x", prm->flags);
     const bool lazy = (prm->flags & HM_AMVM_ACA_ON_DEMAND) != 0;
     if (H->compacted) return fail(HM_EINVAL, "hm_amvm: the FP64 data were released (hm_compact)");

@@ -48,6 +48,10 @@ struct Geom {
     const double* diam2;  // M: max squared edge length
     const double* xr;     // rows: coll, or the points of the evaluation operator (cluster order)
     int square;           // rows are the collocation points: (i, i) is a self pair
+    // the double layer's K_Delta (columns: hat functions of the vertices)
+    const double* nrm = nullptr;        // M x 4: unit normal, twice the area
+    const int32_t* star_ptr = nullptr;  // vertex cluster position -> its star entries
+    const int32_t* star = nullptr;      // triangle position * 4 + local index of the vertex
 };
 
 // ---------------------------------------------------------------- host tables
@@ -294,6 +298,143 @@ __device__ __forceinline__ double entry1(const Geom& g, int i, int j, int kern, 
     return a7[kern];
 }
 
+// ---------------------------------------------------------------- double layer
+// K_Delta of Eq. (Kh) in collocation form: entry (i, p) is
+//   1/(4 pi) sum over the triangles tau_j holding vertex p of
+//   int_{tau_j} (c_i - y).n_j / |c_i - y|^3 psi_p(y) ds_y,
+// psi_p the hat function of p, which on tau_j is the barycentric coordinate
+// of p's corner; the collocation point's own flat panel gives 0.  The same
+// quadrature contract as the single layer: the 7-point rule on tau_j, or on
+// the leaves of its midpoint subdivision when c_i is near.
+
+// the 7-point rule on sub-triangle s of triangle v (normal nr[0..2], twice
+// its area nr[3]) for the corner a of v: area(s) sum_q w_q k(x - y_q) lambda_a(y_q)
+__device__ double dl_rule7(const double* x, const double* s, const double* v, const double* nr, int a)
+{
+    double u[3], w[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        u[k] = s[3 + k] - s[k];
+        w[k] = s[6 + k] - s[k];
+    }
+    const double n0 = u[1] * w[2] - u[2] * w[1], n1 = u[2] * w[0] - u[0] * w[2], n2 = u[0] * w[1] - u[1] * w[0];
+    const double area = 0.5 * sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+    const double* q1 = v + 3 * ((a + 1) % 3);
+    const double* q2 = v + 3 * ((a + 2) % 3);
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        double y[3], d[3], e1[3], e2[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            y[k] = c_lam[3 * q] * s[k] + c_lam[3 * q + 1] * s[3 + k] + c_lam[3 * q + 2] * s[6 + k];
+            d[k] = x[k] - y[k];
+            e1[k] = q1[k] - y[k];
+            e2[k] = q2[k] - y[k];
+        }
+        const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        const double r = sqrt(r2);
+        const double kv = (d[0] * nr[0] + d[1] * nr[1] + d[2] * nr[2]) / (r2 * r);
+        const double c0 = e1[1] * e2[2] - e1[2] * e2[1], c1 = e1[2] * e2[0] - e1[0] * e2[2],
+                     c2 = e1[0] * e2[1] - e1[1] * e2[0];
+        const double lam = (c0 * nr[0] + c1 * nr[1] + c2 * nr[2]) / nr[3];
+        acc += c_w7[q] * kv * lam;
+    }
+    return area * acc;
+}
+
+// the subdivision of adaptive7 (same test, same order) with the double-layer
+// integrand for corner a of v
+__device__ double dl_adaptive(const double* x, const double* v0, const double* nr, int a)
+{
+    double st[kStack][9];
+    int dep[kStack];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) st[0][c] = v0[c];
+    dep[0] = 0;
+    int top = 1;
+    double acc = 0.0;
+    while (top > 0) {
+        --top;
+        double v[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) v[c] = st[top][c];
+        const int d = dep[top];
+        if (d < kMaxDepth && is_near_rn(x, v)) {
+            double ab[3], bc[3], ca[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                ab[k] = __dmul_rn(__dadd_rn(v[k], v[3 + k]), 0.5);
+                bc[k] = __dmul_rn(__dadd_rn(v[3 + k], v[6 + k]), 0.5);
+                ca[k] = __dmul_rn(__dadd_rn(v[6 + k], v[k]), 0.5);
+            }
+            const double* kids[4][3] = {{ab, bc, ca}, {ca, bc, v + 6}, {ab, v + 3, bc}, {v, ab, ca}};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+#pragma unroll
+                for (int p = 0; p < 3; ++p)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) st[top][3 * p + k] = kids[q][p][k];
+                dep[top] = d + 1;
+                ++top;
+            }
+        } else {
+            acc += dl_rule7(x, v, v0, nr, a);
+        }
+    }
+    return acc;
+}
+
+// corner a of triangle j (cluster position) at point x, times 1/(4 pi)
+__device__ double dl_pair(const Geom& g, const double* x, int j, int a)
+{
+    if (sq_dist_rn(x, g.coll + 3 * (size_t)j) < __dmul_rn(4.0, g.diam2[j]))
+        return dl_adaptive(x, g.tri + 9 * (size_t)j, g.nrm + 4 * (size_t)j, a) * kInv4Pi;
+    // far: the rule's nodes and weights (area / (4 pi) folded in) of the
+    // geometry tables; lambda_a at node q is the rule's own coordinate
+    const double* qp = g.qp + 21 * (size_t)j;
+    const double* qw = g.qw + 7 * (size_t)j;
+    const double* nr = g.nrm + 4 * (size_t)j;
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        const double d0 = x[0] - qp[3 * q], d1 = x[1] - qp[3 * q + 1], d2 = x[2] - qp[3 * q + 2];
+        const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+        const double r = sqrt(r2);
+        acc += qw[q] * ((d0 * nr[0] + d1 * nr[1] + d2 * nr[2]) / (r2 * r)) * c_lam[3 * q + a];
+    }
+    return acc;
+}
+
+// K_Delta (i, p): row i (triangle position), column p (vertex position)
+__device__ double dl_entry(const Geom& g, int i, int p)
+{
+    const double* x = g.xr + 3 * (size_t)i;
+    double acc = 0.0;
+    for (int e = g.star_ptr[p]; e < g.star_ptr[p + 1]; ++e) {
+        const int sj = g.star[e], j = sj >> 2, a = sj & 3;
+        if (j != i) acc += dl_pair(g, x, j, a);
+    }
+    return acc;
+}
+
+// near blocks of K_Delta: one CTA per block; stored as the six values of the
+// single layer's layout with K_Delta in the first and zeros elsewhere (the
+// product's trace is then K_Delta itself)
+__global__ void __launch_bounds__(128) dl_near_kernel(Geom g, const Blk* __restrict__ blks,
+                                                      const int64_t* __restrict__ noff, double* __restrict__ N)
+{
+    Blk b = blks[blockIdx.x];
+    double* out = N + noff[blockIdx.x];
+    const int pairs = b.m * b.n;
+    for (int e = threadIdx.x; e < pairs; e += blockDim.x) {
+        const int j = e / b.m, i = e - j * b.m;
+        out[e] = dl_entry(g, b.t0 + i, b.s0 + j);
+#pragma unroll
+        for (int v = 1; v < 6; ++v) out[(size_t)v * pairs + e] = 0.0;
+    }
+}
+
 // ---------------------------------------------------------------- geometry kernel
 __global__ void geom_kernel(int M, const int32_t* __restrict__ perm, const int32_t* __restrict__ T,
                             const double* __restrict__ V, double* __restrict__ tri,
@@ -489,6 +630,8 @@ __device__ int next_row(AcaShared& sh, const double* u, const unsigned char* Z, 
 // with its U / V columns in its own slice of `scratch`; the finished factors
 // (U: m x k, then V: n x k, both column-major) are appended to `arena` at an
 // offset taken with atomicAdd and repacked in block order afterwards.
+// DL: the entries are the double layer's K_Delta (task kernel 0 only)
+template <bool DL>
 __global__ void __launch_bounds__(kAcaThreads) aca_kernel(
     Geom g, const AcaTask* __restrict__ tasks, int ntask, const Blk* __restrict__ blks,
     AcaParams prm, double* __restrict__ scratch, unsigned char* __restrict__ zscr,
@@ -548,7 +691,7 @@ __global__ void __launch_bounds__(kAcaThreads) aca_kernel(
             double* vk = Vf + (size_t)k * n;
             double mraw = 0.0, mres = 0.0;
             for (int j = tid; j < n; j += B) {
-                double a = entry1(g, b.t0 + irow, b.s0 + j, kern, ka, kb);
+                double a = DL ? dl_entry(g, b.t0 + irow, b.s0 + j) : entry1(g, b.t0 + irow, b.s0 + j, kern, ka, kb);
                 double s = a;
                 for (int l = 0; l < k; ++l) s -= sh.su[l] * Vf[(size_t)l * n + j];
                 vk[j] = s;
@@ -600,7 +743,7 @@ __global__ void __launch_bounds__(kAcaThreads) aca_kernel(
             double* uk = U + (size_t)k * m;
             double tuu = 0.0;
             for (int i = tid; i < m; i += B) {
-                double a = entry1(g, b.t0 + i, b.s0 + jk, kern, ka, kb);
+                double a = DL ? dl_entry(g, b.t0 + i, b.s0 + jk) : entry1(g, b.t0 + i, b.s0 + jk, kern, ka, kb);
                 double s = a;
                 for (int l = 0; l < k; ++l) s -= sh.sv[l] * U[(size_t)l * m + i];
                 uk[i] = s;
@@ -780,8 +923,14 @@ int aca_on_demand(hm_matrix& H, const std::vector<int32_t>& bk, int kmax, cudaSt
     if (nt == 0) return HM_OK;
     if (!H.g_coll.p) return fail(HM_EINVAL, "ACA on demand: the matrix keeps no geometry");
     if (kmax < 1) return fail(HM_EINVAL, "ACA on demand: kmax %d < 1", kmax);
-    const Geom g{H.g_coll.as<double>(), H.g_tri.as<double>(), H.g_qp.as<double>(), H.g_qw.as<double>(),
-                 H.g_diam.as<double>(), H.rect ? H.g_rows.as<double>() : H.g_coll.as<double>(), H.rect ? 0 : 1};
+    Geom g{H.g_coll.as<double>(), H.g_tri.as<double>(), H.g_qp.as<double>(), H.g_qw.as<double>(),
+           H.g_diam.as<double>(), H.rect ? H.g_rows.as<double>() : H.g_coll.as<double>(), H.rect ? 0 : 1};
+    if (H.dl) {
+        g.nrm = H.g_nrm.as<double>();
+        g.star_ptr = H.d_star_ptr.as<int32_t>();
+        g.star = H.d_star.as<int32_t>();
+    }
+    auto aca = H.dl ? aca_kernel<true> : aca_kernel<false>;
     // tasks by decreasing |t| + |s| (as at assembly); ord maps back
     std::vector<int64_t> ord((size_t)nt);
     std::iota(ord.begin(), ord.end(), 0);
@@ -803,7 +952,7 @@ int aca_on_demand(hm_matrix& H, const std::vector<int32_t>& bk, int kmax, cudaSt
     int dev = 0, nsm = 0, occ = 0;
     HM_CUDA(cudaGetDevice(&dev));
     HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, aca_kernel, kAcaThreads, 0));
+    HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, aca, kAcaThreads, 0));
     const int64_t full_grid = (int64_t)nsm * std::max(1, std::min(occ, 4));
     struct Cls {
         int64_t i0, i1, grid;
@@ -860,7 +1009,7 @@ int aca_on_demand(hm_matrix& H, const std::vector<int32_t>& bk, int kmax, cudaSt
         HM_CUDA(cudaMemsetAsync(dtop.b.p, 0, 64, s));
         for (const Cls& c : cls) {
             HM_CUDA(cudaMemsetAsync(dcnt.b.p, 0, 64, s));
-            aca_kernel<<<(unsigned)c.grid, kAcaThreads, 0, s>>>(
+            aca<<<(unsigned)c.grid, kAcaThreads, 0, s>>>(
                 g, dtask.b.as<AcaTask>() + c.i0, (int)(c.i1 - c.i0), H.d_adm.as<Blk>(), c.prm, dscr.b.as<double>(),
                 dz.b.as<unsigned char>(), dcnt.b.as<int>(), out.as<double>(), dtop.b.as<unsigned long long>(),
                 arena_cap, drank.b.as<int32_t>() + c.i0, doff.b.as<int64_t>() + c.i0, dflag.b.as<int32_t>() + c.i0,
@@ -981,10 +1130,89 @@ static int upload_geometry(const hm_tree& tr, hm_matrix& H)
 }
 
 int assemble_points_device(const hm_tree& tr, hm_matrix& H);
+// FNV-1a over the mesh's vertex coordinates and triangles: matrices built on
+// the same mesh (the double layer's two operators) carry the same value
+static uint64_t mesh_fingerprint(const hm_tree& tr)
+{
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void* p, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(p);
+        for (size_t i = 0; i < n; ++i) {
+            h ^= b[i];
+            h *= 1099511628211ull;
+        }
+    };
+    mix(tr.V.data(), tr.V.size() * sizeof(double));
+    mix(tr.T.data(), tr.T.size() * sizeof(int32_t));
+    return h;
+}
+
+// The double layer's columns (Section 4.2, Eq. (Kh)): the vertex tree `tr`
+// over the triangles of tr.src.  Rows are the triangles' collocation points
+// (cluster order of tr.src, whose geometry upload_geometry has placed);
+// columns the vertices in tr's cluster order.  Per triangle its unit normal
+// and twice its area (the cross product (p1 - p0) x (p2 - p0) in the
+// triangle's own vertex order), per vertex its star sorted by triangle id,
+// and the triangles' vertex ids for the surface curls.
+static int upload_dl_geometry(const hm_tree& tr, hm_matrix& H)
+{
+    const hm_tree& src = *tr.src;
+    const int64_t M = src.M, nv = tr.M;
+    int rc;
+    // rows: the triangle perm (upload_geometry put it in d_perm) and the
+    // centroids in cluster order
+    std::vector<int32_t> rperm((size_t)M), vperm((size_t)nv), tpos((size_t)M);
+    std::vector<double> rows((size_t)(3 * M)), nrm((size_t)(4 * M));
+    for (int64_t p = 0; p < M; ++p) {
+        const int64_t t = src.perm[(size_t)p];
+        rperm[(size_t)p] = (int32_t)t;
+        tpos[(size_t)t] = (int32_t)p;
+        for (int k = 0; k < 3; ++k) rows[(size_t)(3 * p + k)] = src.coll[(size_t)(3 * t + k)];
+        const double* p0 = &src.V[3 * (size_t)src.T[(size_t)(3 * t)]];
+        const double* p1 = &src.V[3 * (size_t)src.T[(size_t)(3 * t + 1)]];
+        const double* p2 = &src.V[3 * (size_t)src.T[(size_t)(3 * t + 2)]];
+        const double e1[3] = {p1[0] - p0[0], p1[1] - p0[1], p1[2] - p0[2]};
+        const double e2[3] = {p2[0] - p0[0], p2[1] - p0[1], p2[2] - p0[2]};
+        const double c[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                             e1[0] * e2[1] - e1[1] * e2[0]};
+        const double len = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        if (!(len > 0.0)) return fail(HM_EINVAL, "double layer: triangle %lld is degenerate", (long long)t);
+        for (int k = 0; k < 3; ++k) nrm[(size_t)(4 * p + k)] = c[k] / len;
+        nrm[(size_t)(4 * p + 3)] = len;
+    }
+    // stars: for the vertex at cluster position q, (triangle position, corner)
+    // of every triangle holding it, by increasing triangle id
+    std::vector<int32_t> vpos((size_t)nv), cnt((size_t)nv + 1, 0);
+    for (int64_t q = 0; q < nv; ++q) {
+        vperm[(size_t)q] = (int32_t)tr.perm[(size_t)q];
+        vpos[(size_t)tr.perm[(size_t)q]] = (int32_t)q;
+    }
+    for (int64_t t = 0; t < M; ++t)
+        for (int c = 0; c < 3; ++c) ++cnt[(size_t)vpos[(size_t)src.T[(size_t)(3 * t + c)]] + 1];
+    for (int64_t q = 0; q < nv; ++q) cnt[(size_t)q + 1] += cnt[(size_t)q];
+    std::vector<int32_t> star((size_t)cnt[(size_t)nv]), fill(cnt.begin(), cnt.end() - 1);
+    for (int64_t t = 0; t < M; ++t)
+        for (int c = 0; c < 3; ++c) {
+            const int32_t q = vpos[(size_t)src.T[(size_t)(3 * t + c)]];
+            star[(size_t)fill[(size_t)q]++] = tpos[(size_t)t] * 4 + c;
+        }
+    if ((rc = upload(H, H.d_rperm, rperm.data(), rperm.size() * 4))) return rc;
+    H.alloc.release(H.d_perm.p, H.d_perm.bytes);
+    H.d_perm = DevBuf{};
+    if ((rc = upload(H, H.d_perm, vperm.data(), vperm.size() * 4))) return rc;
+    if ((rc = upload(H, H.g_rows, rows.data(), rows.size() * 8))) return rc;
+    if ((rc = upload(H, H.g_nrm, nrm.data(), nrm.size() * 8))) return rc;
+    if ((rc = upload(H, H.d_star_ptr, cnt.data(), cnt.size() * 4))) return rc;
+    if ((rc = upload(H, H.d_star, star.data(), star.size() * 4))) return rc;
+    if ((rc = upload(H, H.d_tris, src.T.data(), src.T.size() * 4))) return rc;
+    if ((rc = dalloc(H, H.dl_w, (size_t)(3 * M) * 8))) return rc;
+    return HM_OK;
+}
+
 
 int assemble_device(const hm_tree& tr, hm_matrix& H)
 {
-    if (tr.kind == 1) return assemble_points_device(tr, H);
+    if (tr.kind == 1 || tr.kind == 2) return assemble_points_device(tr, H);
     cudaStream_t s = H.alloc.stream;
     const int64_t M = tr.M;
     H.M = M;
@@ -992,6 +1220,7 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
     int rc;
     if ((rc = upload_tables(s))) return rc;
     if ((rc = upload_geometry(tr, H))) return rc;
+    H.mesh_fp = mesh_fingerprint(tr);
     Geom g{H.g_coll.as<double>(), H.g_tri.as<double>(), H.g_qp.as<double>(), H.g_qw.as<double>(),
            H.g_diam.as<double>(), H.g_coll.as<double>(), 1};
 
@@ -1099,7 +1328,7 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
         int dev = 0, nsm = 0, occ = 0;
         HM_CUDA(cudaGetDevice(&dev));
         HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, aca_kernel, kAcaThreads, 0));
+        HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, aca_kernel<false>, kAcaThreads, 0));
         const int64_t full_grid = (int64_t)nsm * std::max(1, std::min(occ, 4));
         // Launch classes over the tasks (sorted by decreasing |t| + |s|): a
         // class ends where blocks are half the size of its first one.  Each
@@ -1165,7 +1394,7 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
             HM_CUDA(cudaMemsetAsync(dcnt.b.p, 0, 64, s));
             AcaParams cp = c.prm;
             cp.ecount = qc + 3;  // the first run of every task (not a re-run into the exact arena)
-            aca_kernel<<<(unsigned)c.grid, kAcaThreads, 0, s>>>(
+            aca_kernel<false><<<(unsigned)c.grid, kAcaThreads, 0, s>>>(
                 g, dtask.b.as<AcaTask>() + c.i0, (int)(c.i1 - c.i0), H.d_adm.as<Blk>(), cp,
                 dscr.b.as<double>(), dz.b.as<unsigned char>(), dcnt.b.as<int>(), darena.b.as<double>(),
                 dtop.b.as<unsigned long long>(), cap, drank.b.as<int32_t>() + c.i0, doff.b.as<int64_t>() + c.i0,
@@ -1206,7 +1435,7 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
                 c.grid = std::max<int64_t>(1, std::min<int64_t>({c.grid, (int64_t)(dscr.b.bytes / per_cta),
                                                                  (int64_t)(dz.b.bytes / (size_t)c.prm.mmax)}));
                 HM_CUDA(cudaMemsetAsync(dcnt.b.p, 0, 64, s));
-                aca_kernel<<<(unsigned)c.grid, kAcaThreads, 0, s>>>(
+                aca_kernel<false><<<(unsigned)c.grid, kAcaThreads, 0, s>>>(
                     g, t2.b.as<AcaTask>() + c.i0, (int)(c.i1 - c.i0), H.d_adm.as<Blk>(), c.prm, dscr.b.as<double>(),
                     dz.b.as<unsigned char>(), dcnt.b.as<int>(), a2.as<double>(), dtop.b.as<unsigned long long>(),
                     need + 1, r2.b.as<int32_t>() + c.i0, o2.b.as<int64_t>() + c.i0, f2.b.as<int32_t>() + c.i0,
@@ -1566,15 +1795,22 @@ int assemble_points_device(const hm_tree& tr, hm_matrix& H)
 {
     cudaStream_t s = H.alloc.stream;
     const hm_tree& src = *tr.src;
-    const int64_t M = src.M, Mr = tr.M;
+    // kind 1: rows the points of tr, columns the triangles of src (~V_h);
+    // kind 2: rows the triangles of src, columns the vertices of tr (K_Delta)
+    const bool dl = tr.kind == 2;
+    const std::vector<Node>& rnodes = dl ? src.nodes : tr.nodes;
+    const std::vector<Node>& cnodes = dl ? tr.nodes : src.nodes;
+    const int64_t M = dl ? tr.M : src.M, Mr = dl ? src.M : tr.M;
     H.M = M;
     H.Mr = Mr;
     H.rect = true;
-    H.nleaves = (int64_t)tr.leaves.size();
+    H.dl = dl;
+    H.mesh_fp = mesh_fingerprint(src);
+    H.nleaves = (int64_t)(dl ? src.leaves.size() : tr.leaves.size());
     int rc;
     if ((rc = upload_tables(s))) return rc;
     if ((rc = upload_geometry(src, H))) return rc;
-    {
+    if (!dl) {
         std::vector<int32_t> rperm((size_t)Mr);
         std::vector<double> rows((size_t)(3 * Mr));
         for (int64_t p = 0; p < Mr; ++p) {
@@ -1584,14 +1820,21 @@ int assemble_points_device(const hm_tree& tr, hm_matrix& H)
         }
         if ((rc = upload(H, H.d_rperm, rperm.data(), rperm.size() * 4))) return rc;
         if ((rc = upload(H, H.g_rows, rows.data(), rows.size() * 8))) return rc;
+    } else if ((rc = upload_dl_geometry(tr, H))) {
+        return rc;
     }
-    const Geom g{H.g_coll.as<double>(), H.g_tri.as<double>(), H.g_qp.as<double>(), H.g_qw.as<double>(),
-                 H.g_diam.as<double>(), H.g_rows.as<double>(), 0};
+    Geom g{H.g_coll.as<double>(), H.g_tri.as<double>(), H.g_qp.as<double>(), H.g_qw.as<double>(),
+           H.g_diam.as<double>(), H.g_rows.as<double>(), 0};
+    if (dl) {
+        g.nrm = H.g_nrm.as<double>();
+        g.star_ptr = H.d_star_ptr.as<int32_t>();
+        g.star = H.d_star.as<int32_t>();
+    }
 
-    // ---- block lists: row nodes of the point tree, column nodes of the triangle tree
+    // ---- block lists: (row node, column node) of the partition
     auto blk_of = [&](const std::array<int64_t, 2>& ts) {
-        const Node& a = tr.nodes[(size_t)ts[0]];
-        const Node& c = src.nodes[(size_t)ts[1]];
+        const Node& a = rnodes[(size_t)ts[0]];
+        const Node& c = cnodes[(size_t)ts[1]];
         return Blk{(int32_t)a.lo, (int32_t)(a.hi - a.lo), (int32_t)c.lo, (int32_t)(c.hi - c.lo)};
     };
     H.nadm = (int64_t)tr.adm.size();
@@ -1604,7 +1847,7 @@ int assemble_points_device(const hm_tree& tr, hm_matrix& H)
     if ((rc = upload(H, H.d_near, H.near_h.data(), H.near_h.size() * sizeof(Blk)))) return rc;
     {
         // c_sp (Section 2.1): the most blocks sharing a row or a column cluster
-        std::vector<int32_t> rc_cnt(tr.nodes.size(), 0), cc_cnt(src.nodes.size(), 0);
+        std::vector<int32_t> rc_cnt(rnodes.size(), 0), cc_cnt(cnodes.size(), 0);
         int32_t csp = 0;
         for (const auto* L : {&tr.adm, &tr.near_blocks})
             for (const auto& ts : *L) {
@@ -1636,8 +1879,12 @@ int assemble_points_device(const hm_tree& tr, hm_matrix& H)
     if ((rc = dalloc(H, H.N64, (size_t)std::max<int64_t>(ntot, 1) * 8))) return rc;
     HM_CUDA(cudaEventRecord(ev[0], s));
     if (H.nnear > 0) {
-        near_kernel<<<(unsigned)H.nnear, 128, 0, s>>>(g, H.d_near.as<Blk>(), H.d_noff.as<int64_t>(),
-                                                      H.N64.as<double>(), nullptr);
+        if (dl)
+            dl_near_kernel<<<(unsigned)H.nnear, 128, 0, s>>>(g, H.d_near.as<Blk>(), H.d_noff.as<int64_t>(),
+                                                             H.N64.as<double>());
+        else
+            near_kernel<<<(unsigned)H.nnear, 128, 0, s>>>(g, H.d_near.as<Blk>(), H.d_noff.as<int64_t>(),
+                                                          H.N64.as<double>(), nullptr);
         HM_CUDA(cudaGetLastError());
     }
     HM_CUDA(cudaEventRecord(ev[1], s));
@@ -1651,6 +1898,11 @@ int assemble_points_device(const hm_tree& tr, hm_matrix& H)
     static const int kp[7] = {-1, 0, 0, 0, 1, 1, 2}, kq[7] = {-1, 0, 1, 2, 1, 2, 2};
     std::vector<int32_t> bk;
     for (int64_t b = 0; b < H.nadm; ++b) {
+        if (dl) {
+            // K_Delta is one scalar kernel: slot 0 (the other six keep rank 0)
+            bk.push_back((int32_t)(b * 7));
+            continue;
+        }
         const Node& nt = tr.nodes[(size_t)tr.adm[(size_t)b][0]];
         const Node& ns = src.nodes[(size_t)tr.adm[(size_t)b][1]];
         for (int k = 0; k < 7; ++k) {
@@ -1778,8 +2030,6 @@ extern "C" int hm_aca_assemble(const hm_tree* tree, const hm_params* prm, const 
     if (prm->max_rhs < 0 || prm->max_rhs > 64) return fail(HM_EINVAL, "hm_aca_assemble: max_rhs must lie in 0..64");
     if (prm->flags & ~(HM_DEFER_FP64 | HM_DEFER_ACA))
         return fail(HM_EINVAL, "hm_aca_assemble: unknown flags 0x%x", prm->flags);
-    if (tree->kind == 2)
-        return fail(HM_EINVAL, "hm_aca_assemble: the double layer's device assembly is not built (vertex tree)");
     hm_matrix* H = new (std::nothrow) hm_matrix();
     if (!H) return fail(HM_ENOMEM, "hm_aca_assemble: out of host memory");
     H->prm = *prm;

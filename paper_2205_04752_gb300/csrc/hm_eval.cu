@@ -91,11 +91,13 @@ int eval_pack_fp32(hm_matrix& H, cudaStream_t s)
 namespace {
 template <class T>
 int eval_run(const hm_matrix& H, const double* t, double* u, int32_t nrhs, const T* Uf, const T* Vf, const T* Nf,
-             cudaStream_t s)
+             cudaStream_t s, bool accumulate = false)
 {
     const int64_t M = H.M, Mr = H.Mr, nb = H.nadm;
-    const T c1 = (T)((1.0 + H.nu) * (3.0 - 4.0 * H.nu) / (2.0 * H.E * (1.0 - H.nu)));
-    const T c2 = (T)((1.0 + H.nu) / (2.0 * H.E * (1.0 - H.nu)));
+    // the double layer's K_Delta is one scalar kernel in slot 0, applied to
+    // each component: c1 = 1, c2 = 0
+    const T c1 = H.dl ? (T)1 : (T)((1.0 + H.nu) * (3.0 - 4.0 * H.nu) / (2.0 * H.E * (1.0 - H.nu)));
+    const T c2 = H.dl ? (T)0 : (T)((1.0 + H.nu) / (2.0 * H.E * (1.0 - H.nu)));
     const DevBuf* ev = H.ev;
     T* xc = ev[kEvXc].as<T>();
     T* yc = ev[kEvYc].as<T>();
@@ -130,12 +132,25 @@ int eval_run(const hm_matrix& H, const double* t, double* u, int32_t nrhs, const
                                               D, ev[kEvNptr].as<int32_t>(), ev[kEvNidx].as<int32_t>(),
                                               H.d_near.as<Blk>(), ev[kEvNdoff].as<int64_t>(), Dn, yc, Mr);
         HM_CUDA(cudaGetLastError());
-        ev_scatter_kernel<T><<<gM, 256, 0, s>>>(H.d_rperm.as<int32_t>(), yc, u + (int64_t)r * 3 * Mr, Mr);
+        if (accumulate)
+            ev_scatter_add_kernel<T><<<gM, 256, 0, s>>>(H.d_rperm.as<int32_t>(), yc, u + (int64_t)r * 3 * Mr, Mr);
+        else
+            ev_scatter_kernel<T><<<gM, 256, 0, s>>>(H.d_rperm.as<int32_t>(), yc, u + (int64_t)r * 3 * Mr, Mr);
         HM_CUDA(cudaGetLastError());
     }
     return HM_OK;
 }
 }  // namespace
+
+int eval_apply(const hm_matrix& H, const double* t, double* u, int32_t nrhs, int32_t form, bool accumulate,
+               cudaStream_t s)
+{
+    if (form == HM_FP32)
+        return eval_run<float>(H, t, u, nrhs, H.Ul[HM_FP32].as<float>(), H.Vr[HM_FP32].as<float>(),
+                               H.Nl32.as<float>(), s, accumulate);
+    return eval_run<double>(H, t, u, nrhs, H.U64.as<double>(), H.V64.as<double>(), H.N64.as<double>(), s,
+                            accumulate);
+}
 }  // namespace hm
 
 using namespace hm;

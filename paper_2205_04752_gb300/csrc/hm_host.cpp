@@ -627,7 +627,8 @@ static std::vector<hm::DevBuf*> matrix_bufs(hm_matrix* H)
         &H->d_units, &H->d_tcunits, &H->d_multi, &H->d_big, &H->d_small, &H->d_fwd_all, &H->d_work,
         &H->d_pos_prefix, &H->d_counters, &H->d_err, &H->U64, &H->V64, &H->N64, &H->Nl64, &H->Nl32, &H->SU,
         &H->SV, &H->SW16, &H->xg, &H->wb, &H->zb, &H->xh, &H->yh, &H->g_coll, &H->g_tri, &H->g_qp, &H->g_qw,
-        &H->g_diam, &H->d_rperm, &H->g_rows};
+        &H->g_diam, &H->d_rperm, &H->g_rows, &H->g_nrm, &H->d_star_ptr, &H->d_star, &H->d_tris, &H->d_mesh_k,
+        &H->dl_w};
     for (int f = 0; f < HM_NFORMS; ++f) {
         v.push_back(&H->d_mesh[f]);
         v.push_back(&H->Ul[f]);

@@ -228,6 +228,11 @@ struct hm_matrix {
     int64_t M = 0;   // columns: triangles (and rows of a square matrix)
     int64_t Mr = 0;  // rows: M, or the points of an evaluation operator
     bool rect = false;  // evaluation operator ~V_h (Section 5, Eq. (vector_eq)): rows are points
+    // the double layer's K_Delta (Section 4.2, Eq. (Kh)), a rectangular
+    // operator too: rows the collocation points (triangles), columns the hat
+    // functions of the vertices; one scalar kernel (slot 0), c1 = 1, c2 = 0
+    bool dl = false;
+    uint64_t mesh_fp = 0;  // fingerprint of the mesh (vertices and triangles) the matrix was built on
     int64_t nadm = 0, nnear = 0, nleaves = 0;
     double E = 1.0, nu = 0.3;
     hm_params prm{};
@@ -296,6 +301,12 @@ struct hm_matrix {
     hm::DevBuf g_coll, g_tri, g_qp, g_qw, g_diam;  // cluster-order geometry of the entries (ACA on demand)
     hm::DevBuf d_rperm;  // evaluation operator: int32 Mr, point cluster position -> original point
     hm::DevBuf g_rows;   // evaluation operator: Mr x 3 points in cluster order
+    // double layer: per triangle (cluster order) the unit normal and twice the
+    // area; per vertex (cluster order) its star as (triangle position * 4 +
+    // local vertex index), CSR; the triangles' vertex ids (original order)
+    hm::DevBuf g_nrm, d_star_ptr, d_star, d_tris;
+    hm::DevBuf d_mesh_k;  // square matrix: the mesh table with the double layer's coefficients
+    hm::DevBuf dl_w;      // double layer: T_h u (3 x rows doubles)
     // evaluation operator: tables and workspace of its exact product
     // (hm_eval.cu; index names in hm_parts.cuh)
     static constexpr int kEvBufs = 14;
@@ -387,6 +398,14 @@ int eval_prepare(hm_matrix& H);
 // the FP32 form of an evaluation operator: FP32 copies of its block-ordered
 // U, V and near arenas (in Ul[HM_FP32], Vr[HM_FP32] and Nl32), same offsets
 int eval_pack_fp32(hm_matrix& H, cudaStream_t s);
+// the product of a rectangular operator (evaluation operator or the double
+// layer's K_Delta) in HM_FP64 or a packed HM_FP32; accumulate: u += instead of u =
+int eval_apply(const hm_matrix& H, const double* t, double* u, int32_t nrhs, int32_t form, bool accumulate,
+               cudaStream_t s);
+// the single-layer product of a square matrix with the coefficients of
+// Eq. (Vh) replaced by (c1, c2) (one vector; its mesh table in d_mesh_k)
+int matvec_device_coeffs(hm_matrix& H, const double* x, double* y, int32_t form, double c1, double c2,
+                         cudaStream_t s);
 int matvec_device(const hm_matrix& H, const double* x, double* y, int32_t nrhs, int64_t ld,
                   int32_t form, cudaStream_t s);
 int pack_device(hm_matrix& H, int32_t form, cudaStream_t s);

@@ -1471,6 +1471,44 @@ int matvec_device_scratch(const hm_matrix& H, const double* x, double* y, int32_
     return run_product(P, form, x, y, nrhs, ld, scr.xg, scr.w, s, scr.profile ? &H : nullptr);
 }
 
+int matvec_device_coeffs(hm_matrix& H, const double* x, double* y, int32_t form, double c1, double c2,
+                         cudaStream_t s)
+{
+    int rc;
+    if (!H.d_mesh_k.p)
+        if ((rc = dalloc(H, H.d_mesh_k, sizeof(MeshDev)))) return rc;
+    MeshDev m = mesh_desc(H, form);
+    m.c1 = c1;
+    m.c2 = c2;
+    // a pageable source: the copy is staged before the call returns
+    HM_CUDA(cudaMemcpyAsync(H.d_mesh_k.p, &m, sizeof m, cudaMemcpyHostToDevice, s));
+    Plan P{};
+    P.meshes = H.d_mesh_k.as<MeshDev>();
+    P.mesh0 = m;
+    P.nmesh = 1;
+    P.pos_prefix = H.d_pos_prefix.as<int64_t>();
+    P.npos = H.M;
+    P.fwd = H.d_fwd_all.as<FwdRec>();
+    P.groups = H.d_groups.as<FwdGroup>();
+    P.units = H.d_units.as<FwdUnit>();
+    P.tcu = H.d_tcunits.as<FwdTcUnit>();
+    P.nunits = (int64_t)H.unit_h.size();
+    P.multi = H.d_multi.as<FwdMulti>();
+    P.nmulti = (int64_t)H.multi_h.size();
+    P.zcols = H.zcols;
+    P.z = H.zb.p;
+    P.big = H.d_big.as<int32_t>();
+    P.nbig = (int64_t)H.big_h.size();
+    P.small = H.d_small.as<int32_t>();
+    P.nsmall = (int64_t)H.small_h.size();
+    P.work = H.d_work.as<int2>();
+    P.nwork = H.nleaves;
+    P.max_leaf = H.max_leaf;
+    P.counters = H.d_counters.as<int>();
+    P.err = H.d_err.as<int>();
+    return run_product(P, form, x, y, 1, 3 * H.M, H.xg.p, H.wb.p, s, nullptr);
+}
+
 int matvec_device(const hm_matrix& H, const double* x, double* y, int32_t nrhs, int64_t ld,
                   int32_t form, cudaStream_t s)
 {

@@ -315,6 +315,17 @@ __global__ void ev_scatter_kernel(const int32_t* __restrict__ perm, const T* __r
     for (int a = 0; a < 3; ++a) y[o + a] = (double)yc[3 * p + a];
 }
 
+template <class T>
+__global__ void ev_scatter_add_kernel(const int32_t* __restrict__ perm, const T* __restrict__ yc,
+                                      double* __restrict__ y, int64_t M)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= M) return;
+    const int64_t o = 3 * (int64_t)perm[p];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) y[o + a] += (double)yc[3 * p + a];
+}
+
 // the FP32 form: element-wise copies of the block-ordered FP64 arenas
 __global__ void ev_to_fp32_kernel(const double* __restrict__ src, float* __restrict__ dst, int64_t n)
 {

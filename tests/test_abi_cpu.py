@@ -205,12 +205,7 @@ def test_vertex_tree_and_partition_match_oracle(mesh, leaf, leaf_v):
         assert np.all(op.boxes[n, :3] <= pts.min(0)) and np.all(op.boxes[n, 3:] >= pts.max(0))
         if n > 40:
             break
-    # refused before any device work (the raw ABI: no GPU needed)
-    prm = binding._Params(1.0, 0.3, 1e-4, 0.8, 0, 0, 0, 0)
-    out = ctypes.c_void_p()
-    lib = binding.load()
-    assert lib.hm_aca_assemble(vt._h, ctypes.byref(prm), None, None, ctypes.byref(out)) == binding.HM_EINVAL
-    assert b"vertex tree" in lib.hm_last_error()
+    # a vertex tree cannot stand in for a triangle tree (host checks, no GPU needed)
     with pytest.raises(binding.HMError):
         binding.build_point_tree(vt, inputs.ball_points(4, 0.5, 1), 8)
     with pytest.raises(binding.HMError):
