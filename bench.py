@@ -362,10 +362,20 @@ def run_ours(args):
     nvals = st.near_pairs * 6
     xvec = 4 * M * wa
     wvec = 4 * st.factor_columns * wa
+    near_bytes = nvals * wn
+    if form == "i16":
+        # the leaves' diagonal blocks stay FP32; every other near column is
+        # six INT16 segments and six FP32 scales
+        _, nodes, _, near = tree.export()
+        nsz = nodes[:, 1] - nodes[:, 0]
+        diag = near[:, 0] == near[:, 1]
+        pairs = nsz[near[:, 0]] * nsz[near[:, 1]]
+        near_bytes = int(pairs[diag].sum()) * 6 * 4 + int(pairs[~diag].sum()) * 6 * 2 + \
+            int(nsz[near[~diag, 1]].sum()) * 6 * 4
     alg = {
         "gather": 3 * M * 8 + M * 4 + xvec,
         "far_fwd": st.far_v_entries * wf + scales + xvec + wvec,
-        "leaf_near": st.far_u_entries * wf + nvals * wn + wvec + xvec + 3 * M * 8,
+        "leaf_near": st.far_u_entries * wf + near_bytes + wvec + xvec + 3 * M * 8,
     }
     peak, peak_kind = _peaks()
     achieved = alg[names[dom]] / (kms[dom] * 1e-3) / 1e9

@@ -1541,7 +1541,9 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
         std::vector<PackSrc> lf_src;
         std::vector<LeafNearItem> ln_items;
         std::vector<NearSrc> ln_src;
-        int64_t ul = 0, nl = 0;
+        std::vector<int64_t> ln16_base;   // byte offsets in the INT16 near stream
+        std::vector<int32_t> ln16_diag;   // columns of the leaf's diagonal block
+        int64_t ul = 0, nl = 0, nl16 = 0, nl_diag = 0;
         int32_t maxleaf = 0;
         for (int64_t lf : tr.leaves) {
             const Node& L = tr.nodes[(size_t)lf];
@@ -1575,8 +1577,16 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
             ul += (int64_t)((seg + 15) & ~15) * mp;
             int32_t col = 0;
             ln_base.push_back(nl);
-            for (int32_t b : near_by_row[(size_t)lf]) {
+            // the leaf's diagonal block (tau, tau) first: it holds the singular
+            // and near-singular pairs, which the INT16 form keeps in FP32
+            std::vector<int32_t> nb_order(near_by_row[(size_t)lf].begin(), near_by_row[(size_t)lf].end());
+            std::stable_partition(nb_order.begin(), nb_order.end(), [&](int32_t b) {
+                return H.near_h[(size_t)b].s0 == (int32_t)L.lo && H.near_h[(size_t)b].n == mt;
+            });
+            int32_t ndiag = 0;
+            for (int32_t b : nb_order) {
                 const Blk& bk = H.near_h[(size_t)b];
+                if (col == 0 && bk.s0 == (int32_t)L.lo && bk.n == mt) ndiag = bk.n;
                 ln_items.push_back(LeafNearItem{col, bk.s0});
                 ln_src.push_back(NearSrc{H.noff_h[(size_t)b], bk.n, 0});
                 col += bk.n;
@@ -1585,10 +1595,18 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
             ln_src.push_back(NearSrc{0, 0, 0});
             ln_ptr.push_back((int32_t)ln_items.size());
             nl += (int64_t)col * 6 * mp;
+            // the INT16 near stream: the columns after the diagonal block, each a
+            // 32-byte header (six FP32 scales) and six segments of mp int16
+            ln16_base.push_back(nl16);
+            ln16_diag.push_back(ndiag);
+            nl_diag += (int64_t)ndiag * 6 * mp;
+            nl16 += (int64_t)(col - ndiag) * (kNear16Head + 12 * mp);
         }
         H.max_leaf = maxleaf;
         H.ul_total = ul;
         H.nl_total = nl;
+        H.nl16_bytes = nl16;
+        H.nl_diag_total = nl_diag;
         H.nleaves = (int64_t)tr.leaves.size();
         {
             // streamed kernel: leaves with the most bytes first
@@ -1619,6 +1637,8 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
         if ((rc = upload(H, H.d_ln_ptr, ln_ptr.data(), ln_ptr.size() * 4))) return rc;
         if ((rc = upload(H, H.d_ln_items, ln_items.data(), ln_items.size() * sizeof(LeafNearItem)))) return rc;
         if ((rc = upload(H, H.d_ln_src, ln_src.data(), ln_src.size() * sizeof(NearSrc)))) return rc;
+        if ((rc = upload(H, H.d_ln16_base, ln16_base.data(), ln16_base.size() * 8))) return rc;
+        if ((rc = upload(H, H.d_ln16_diag, ln16_diag.data(), ln16_diag.size() * 4))) return rc;
     }
     {
         // forward-pass groups: the admissible blocks that share a column

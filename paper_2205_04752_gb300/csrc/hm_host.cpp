@@ -512,6 +512,8 @@ int hm_get_stats(const hm_matrix* H, hm_stats* st)
         int64_t wf = f == HM_FP64 ? 8 : (f == HM_FP32 ? 4 : 2);
         int64_t wn = f == HM_FP64 ? 8 : 4;
         st->bytes_form[f] = stream_elems * wf + H->nl_total * wn + (wf == 2 ? far_cols * 4 : 0);
+        // INT16: the diagonal blocks from the FP32 near stream, the rest INT16
+        if (f == HM_I16) st->bytes_form[f] = stream_elems * 2 + far_cols * 4 + H->nl_diag_total * 4 + H->nl16_bytes;
     }
     for (int i = 0; i < 3; ++i) st->assemble_ms[i] = H->asm_ms[i];
     for (int i = 0; i < 3; ++i) st->near_points[i] = H->asm_count[i];
@@ -627,6 +629,7 @@ static std::vector<hm::DevBuf*> matrix_bufs(hm_matrix* H)
         &H->d_units, &H->d_tcunits, &H->d_multi, &H->d_big, &H->d_small, &H->d_fwd_all, &H->d_work,
         &H->d_pos_prefix, &H->d_counters, &H->d_err, &H->U64, &H->V64, &H->N64, &H->Nl64, &H->Nl32, &H->SU,
         &H->SV, &H->SW16, &H->xg, &H->wb, &H->zb, &H->xh, &H->yh, &H->g_coll, &H->g_tri, &H->g_qp, &H->g_qw,
+        &H->Nl16, &H->d_ln16_base, &H->d_ln16_diag,
         &H->g_diam, &H->d_rperm, &H->g_rows, &H->g_nrm, &H->d_star_ptr, &H->d_star, &H->d_tris, &H->d_mesh_k,
         &H->dl_w};
     for (int f = 0; f < HM_NFORMS; ++f) {

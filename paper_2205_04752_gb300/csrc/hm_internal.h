@@ -105,6 +105,10 @@ struct NearSrc {
     int64_t src;  // element offset of the block in the block-ordered FP64 near arena
     int32_t n, pad;
 };
+// INT16 near stream (the INT16 form): a column is a header of kNear16Head
+// bytes (six FP32 scales, max |value| / 32767 of V_11 .. V_33 over the
+// leaf's rows, then padding) and six segments of mp int16, 32 + 12 mp bytes
+constexpr int kNear16Head = 32;
 // one admissible block of the far-field forward pass (32 bytes): column
 // cluster start and size, first factor column, total rank, mesh, column offset
 // of its V inside its group's row-major matrix, the group, and the rank of
@@ -182,6 +186,12 @@ struct MeshDev {
     const int64_t* ln_base;
     const int32_t* ln_ptr;
     const LeafNearItem* ln_items;
+    // INT16 form: the near columns after each leaf's diagonal block in the
+    // INT16 near stream (null for the other forms, which stream every
+    // column from Nl); the diagonal block's columns still come from Nl (FP32)
+    const unsigned char* Nl16;
+    const int64_t* ln16_base;   // byte offset of each leaf's INT16 columns
+    const int32_t* ln16_diag;   // columns of each leaf's diagonal block
     const int32_t* perm;
     int64_t xoff, xgoff, woff;
     int32_t M, max_leaf;
@@ -261,6 +271,7 @@ struct hm_matrix {
     hm::DevBuf d_leaf;   // int32 2*nleaves (t0, m)
     hm::DevBuf d_lf_base, d_lf_ptr, d_lf_items, d_lf_src;  // far stream per leaf
     hm::DevBuf d_ln_base, d_ln_ptr, d_ln_items, d_ln_src;  // near stream per leaf
+    hm::DevBuf d_ln16_base, d_ln16_diag;                   // INT16 near stream per leaf
     hm::DevBuf d_vb_base;                 // int64 nadm+1: V of each block (first row) in its group
     hm::DevBuf d_vb_ld;                   // int64 nadm+1: row stride of that V (its group's Cs)
     hm::DevBuf d_vb_coff;                 // int64 nadm+1: column offset of the block in its group
@@ -286,6 +297,8 @@ struct hm_matrix {
     hm::DevBuf d_counters;               // int32 2*max_rhs: work counters of the streamed kernel
     hm::DevBuf d_err;                    // int32: set by a device wait that ran out
     int64_t ul_total = 0, nl_total = 0, vr_total = 0;
+    int64_t nl16_bytes = 0;  // bytes of the INT16 near stream
+    int64_t nl_diag_total = 0;  // elements of the leaves' diagonal blocks in the near stream
 
     // FP64 factor and near arenas in block order (ACA output, export)
     hm::DevBuf U64, V64, N64;
@@ -294,6 +307,7 @@ struct hm_matrix {
     hm::DevBuf Nl64, Nl32;  // near field leaf-major: FP64 form / all other forms
     hm::DevBuf SU, SV;      // per-column scales of the 16-bit forms (float, c_total)
     hm::DevBuf SW16;        // HM_I16: per-column factor of w, SU SV / 32767^2 (float, c_total)
+    hm::DevBuf Nl16;        // HM_I16: INT16 near stream (nl16_bytes)
     bool packed[HM_NFORMS] = {false, false, false, false, false};
     float wbound_su = 0.0f;  // max over factor columns of (U column scale x |s| of its block)
     bool compacted = false;  // FP64 data released (hm_compact)

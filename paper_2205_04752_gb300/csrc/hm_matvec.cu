@@ -960,6 +960,42 @@ __global__ void pack_nl_kernel(const int32_t* __restrict__ leaf, const int64_t* 
     }
 }
 
+// INT16 near stream of the INT16 form: one CTA per leaf, one thread per
+// (column, value) segment of the columns after the leaf's diagonal block.
+// Header float v of a column = max |V_v| over the leaf's rows / 32767 (0 for
+// a zero segment); the segment stores round(32767 V_v / max |V_v|).
+__global__ void pack_nl16_kernel(const int32_t* __restrict__ leaf, const int64_t* __restrict__ ln16_base,
+                                 const int32_t* __restrict__ ln16_diag, const int32_t* __restrict__ ln_ptr,
+                                 const LeafNearItem* __restrict__ items, const NearSrc* __restrict__ src,
+                                 const double* __restrict__ N, unsigned char* __restrict__ out)
+{
+    const int lf = blockIdx.x;
+    const int mt = leaf[2 * lf + 1], mp = (mt + 7) & ~7;
+    const int ndiag = ln16_diag[lf];
+    const size_t colB = (size_t)kNear16Head + 12 * (size_t)mp;
+    unsigned char* base = out + ln16_base[lf];
+    for (int q = ln_ptr[lf]; q < ln_ptr[lf + 1] - 1; ++q) {
+        const NearSrc ns = src[q];
+        const int c0 = items[q].col_start;
+        if (c0 < ndiag) continue;  // the diagonal block streams from the FP32 near stream
+        for (int e = threadIdx.x; e < ns.n * 6; e += blockDim.x) {
+            const int j = e / 6, v = e - 6 * j;
+            const double* seg = N + ns.src + ((size_t)v * ns.n + j) * mt;
+            double mx = 0.0;
+            for (int i = 0; i < mt; ++i) mx = fmax(mx, fabs(seg[i]));
+            unsigned char* col = base + (size_t)(c0 + j - ndiag) * colB;
+            reinterpret_cast<float*>(col)[v] = (float)(mx / 32767.0);
+            if (v == 0) reinterpret_cast<float*>(col)[6] = reinterpret_cast<float*>(col)[7] = 0.0f;
+            int16_t* d = reinterpret_cast<int16_t*>(col + kNear16Head) + (size_t)v * mp;
+            for (int i = 0; i < mp; ++i) {
+                int qv = 0;
+                if (i < mt && mx > 0.0) qv = max(-32767, min(32767, __double2int_rn(seg[i] / mx * 32767.0)));
+                d[i] = (int16_t)qv;
+            }
+        }
+    }
+}
+
 int dalloc(hm_matrix& H, DevBuf& d, size_t bytes)
 {
     d.bytes = std::max<size_t>(bytes, 256);
@@ -1416,6 +1452,11 @@ MeshDev mesh_desc(const hm_matrix& H, int32_t form)
     m.ln_base = H.d_ln_base.as<int64_t>();
     m.ln_ptr = H.d_ln_ptr.as<int32_t>();
     m.ln_items = H.d_ln_items.as<LeafNearItem>();
+    if (form == HM_I16) {
+        m.Nl16 = H.Nl16.as<unsigned char>();
+        m.ln16_base = H.d_ln16_base.as<int64_t>();
+        m.ln16_diag = H.d_ln16_diag.as<int32_t>();
+    }
     m.perm = H.d_perm.as<int32_t>();
     m.xoff = m.xgoff = m.woff = 0;
     m.M = (int32_t)H.M;
@@ -1578,6 +1619,16 @@ int pack_device(hm_matrix& H, int32_t form, cudaStream_t s)
                 }
             }
             if ((rc = pack_form<int16_t>(H, HM_I16, H.SU.as<float>(), H.SV.as<float>(), s))) return rc;
+            if (!H.Nl16.p) {
+                if ((rc = dalloc(H, H.Nl16, (size_t)std::max<int64_t>(H.nl16_bytes, 16)))) return rc;
+                if (H.nleaves > 0) {
+                    pack_nl16_kernel<<<(unsigned)H.nleaves, 256, 0, s>>>(
+                        H.d_leaf.as<int32_t>(), H.d_ln16_base.as<int64_t>(), H.d_ln16_diag.as<int32_t>(),
+                        H.d_ln_ptr.as<int32_t>(), H.d_ln_items.as<LeafNearItem>(), H.d_ln_src.as<NearSrc>(),
+                        H.N64.as<double>(), H.Nl16.as<unsigned char>());
+                    HM_CUDA(cudaGetLastError());
+                }
+            }
             if ((rc = write_mesh_table(H, form, s))) return rc;
             H.packed[form] = true;
             return HM_OK;

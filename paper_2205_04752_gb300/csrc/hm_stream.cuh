@@ -43,7 +43,7 @@ constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 struct StageMeta {
     int32_t leaf;   // leaf index (into its mesh's leaf table)
-    int32_t kind;   // 0 far segments, 1 near columns, 2 no more work
+    int32_t kind;   // 0 far segments, 1 near columns, 2 no more work, 3 INT16 near columns
     int32_t first;  // first segment / column of the stage within the leaf's stream
     int32_t count;  // segments / columns in the stage
     int32_t last;   // 1 if this is the last stage of the leaf
@@ -364,7 +364,7 @@ __device__ __forceinline__ void leaf_producer(const int2* __restrict__ work, int
                 meta[slot] = m;
             }
             __syncwarp();
-            if (kind < 2) {
+            if (kind != 2) {
                 // bytes of this lane's copies that go through the bulk engine
                 uint32_t bulk = 0;
                 auto copy = [&](TA* dst, const TA* srcp, uint32_t nb) {
@@ -486,11 +486,24 @@ __device__ __forceinline__ void leaf_producer(const int2* __restrict__ work, int
                           fitems, fi1 - fi0, &cur, wvec, g + cnt == S ? 1 : 0);
             }
             cur = 0;
-            for (int g = 0; g < Sn && ok; g += perN) {
-                const int cnt = min(perN, Sn - g);
+            // the INT16 form streams the leaf's diagonal block from the FP32
+            // near stream and its other columns from the INT16 one (kind 3)
+            const int nd = md.Nl16 ? min(md.ln16_diag[lf], Sn) : Sn;
+            for (int g = 0; g < nd && ok; g += perN) {
+                const int cnt = min(perN, nd - g);
                 const TN* src = Nl + md.ln_base[lf] + (size_t)g * 6 * mp;
                 ok = emit(wk.x, lf, 1, g, cnt, (g + cnt == Sn) ? 1 : 0, src, (uint32_t)(cnt * colB), nitems,
                           ni1 - ni0, &cur, xvec, 0);
+            }
+            if (md.Nl16 && nd < Sn && ok) {
+                const int colB16 = kNear16Head + 12 * mp;
+                const int perN16 = min(kStage / colB16, perV);
+                const unsigned char* n16 = md.Nl16 + md.ln16_base[lf];
+                for (int g = nd; g < Sn && ok; g += perN16) {
+                    const int cnt = min(perN16, Sn - g);
+                    ok = emit(wk.x, lf, 3, g, cnt, (g + cnt == Sn) ? 1 : 0, n16 + (size_t)(g - nd) * colB16,
+                              (uint32_t)(cnt * colB16), nitems, ni1 - ni0, &cur, xvec, 0);
+                }
             }
         }
         if (ok) ok = emit(0, -1, 2, 0, 0, 0, nullptr, 0, nullptr, 0, nullptr, nullptr, 0);
@@ -620,6 +633,56 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
                                 acc[e][q][0] += ua[e] * w0;
                                 acc[e][q][1] += ua[e] * w1;
                                 acc[e][q][2] += ua[e] * w2;
+                            }
+                        }
+                    }
+                }
+            } else if (m.kind == 3) {
+                // INT16 near columns: header of six scales, then six segments
+                // of int16; the scales are folded into the coefficients of x,
+                // so that each row costs the 15 FMAs of the FP32 columns:
+                // V_aa enters y_a with (c1 + c2) x_a and the other two
+                // components with c1 x_b; V_ab (a != b) enters y_a with c2 x_b
+                // and y_b with c2 x_a
+                const unsigned char* sb3 = sdata(slot);
+                const int colB16 = kNear16Head + 12 * mp;
+                const TA c12 = c1 + c2;
+                for (int s = h; s < m.count; s += H) {
+                    const unsigned char* col = sb3 + (size_t)s * colB16;
+                    const float4 sa = *reinterpret_cast<const float4*>(col);        // s11 s12 s13 s22
+                    const float2 sz = *reinterpret_cast<const float2*>(col + 16);   // s23 s33
+                    const TA sc[6] = {(TA)sa.x, (TA)sa.y, (TA)sa.z, (TA)sa.w, (TA)sz.x, (TA)sz.y};
+                    const int16_t* e0 = reinterpret_cast<const int16_t*>(col + kNear16Head) + p * Rr;
+#pragma unroll
+                    for (int q = 0; q < RC; ++q) {
+                        if (RC > 1 && c * RC + q >= G) break;
+                        TA x0, x1, x2;
+                        load3(av + ((size_t)s * G + q) * 4, x0, x1, x2);
+                        const TA xs3[3] = {x0, x1, x2};
+#pragma unroll
+                        for (int v = 0; v < 6; ++v) {
+                            // (a, b) of value v: 11, 12, 13, 22, 23, 33
+                            const int va = v < 3 ? 0 : (v < 5 ? 1 : 2);
+                            const int vb = v < 3 ? v : (v < 5 ? v - 2 : 2);
+                            TA val[Rr];
+                            smem_rows<int16_t, TA, Rr>(e0 + v * mp, val);
+                            if (va == vb) {
+                                const TA f0 = (va == 0 ? c12 : c1) * sc[v] * xs3[0];
+                                const TA f1 = (va == 1 ? c12 : c1) * sc[v] * xs3[1];
+                                const TA f2 = (va == 2 ? c12 : c1) * sc[v] * xs3[2];
+#pragma unroll
+                                for (int e = 0; e < Rr; ++e) {
+                                    acc[e][q][0] += f0 * val[e];
+                                    acc[e][q][1] += f1 * val[e];
+                                    acc[e][q][2] += f2 * val[e];
+                                }
+                            } else {
+                                const TA fa = c2 * sc[v] * xs3[vb], fb = c2 * sc[v] * xs3[va];
+#pragma unroll
+                                for (int e = 0; e < Rr; ++e) {
+                                    acc[e][q][va] += fa * val[e];
+                                    acc[e][q][vb] += fb * val[e];
+                                }
                             }
                         }
                     }

@@ -98,10 +98,11 @@ def test_hmatvec_fp64_matches_oracle_and_dense():
 
 # Relative error of each packed form against the FP64 form at C1, bounded at
 # about twice what the forms reach there (measured on GB300 with these
-# inputs: FP32 2.7e-7, BF16 3.3e-4, FP16 4.1e-5, INT16 3.0e-6); the errors
+# inputs: FP32 3.2e-7, BF16 3.3e-4, FP16 4.1e-5, INT16 9.5e-6); the errors
 # follow each storage type's rounding of the factors (unit roundoff 2^-24,
-# 2^-8, 2^-11, and 2^-16 of each column's largest entry)
-C1_BOUNDS = {"fp32": 6e-7, "bf16": 7e-4, "fp16": 8e-5, "i16": 6e-6}
+# 2^-8, 2^-11, and 2^-16 of each column's largest entry; INT16 also stores
+# the near field outside the leaves' diagonal blocks in INT16)
+C1_BOUNDS = {"fp32": 6e-7, "bf16": 7e-4, "fp16": 8e-5, "i16": 2e-5}
 
 
 @pytest.mark.parametrize("form", ["fp32", "bf16", "fp16", "i16"])
@@ -274,7 +275,8 @@ def _l6_products(H, M, form, nrhs, seed):
 # the form of the tensor-core kernels.  BF16 keeps three fewer mantissa bits
 # than FP16 (unit roundoff 2^-8 against 2^-11), about 8x FP16's error, and
 # serves as an inner form of the refined solve.  FP32 is gated far below
-# (measured on GB300: INT16 7.9e-6, FP16 1.21e-4, BF16 9.7e-4, FP32 1.4e-6).
+# (measured on GB300 over 32 vectors: INT16 1.28e-5, FP16 1.21e-4, BF16 9.7e-4,
+# FP32 1.7e-6).
 L6_BOUNDS = {"i16": 1e-4, "fp16": 1.5e-4, "bf16": 1.5e-3, "fp32": 3e-6}
 
 
