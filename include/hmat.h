@@ -384,8 +384,10 @@ void hm_batch_destroy(hm_batch* B);
  * a fixed arena of budget_bytes (its vectors, the product workspace and, for
  * a solve, the Krylov basis); admitted requests run concurrently on their
  * own streams, so their kernels overlap on the device while later arrivals
- * keep being admitted.  Arrivals that find queue_cap requests waiting, or
- * whose footprint exceeds the arena, are rejected (HM_EBUSY).
+ * keep being admitted.  Requests of one kind are admitted in arrival order;
+ * a solve that waits for one of its solve_slots does not hold back the
+ * matvec requests behind it.  Arrivals that find queue_cap requests waiting,
+ * or whose footprint exceeds the arena, are rejected (HM_EBUSY).
  * Every request runs the kernels it would run alone, with its own
  * workspace: its result is bitwise the same alone and in any mix.
  * The matrices must stay alive and unchanged while the server exists; the
@@ -406,7 +408,9 @@ typedef struct {
     int32_t restart;        /* solve: GMRES restart (0 = 30) */
     double inner_tol;       /* solve: residual reduction per GMRES solve (0 = 1e-3) */
     int32_t max_inner;      /* solve: cap on inner products (0 = 1000) */
-    int32_t pad;
+    int32_t solve_slots;    /* at most this many slots run solves at once (0 = any slot); the
+                               other slots are kept for matvec requests, so that long solves
+                               cannot hold every slot */
 } hm_server_params;
 
 typedef struct {

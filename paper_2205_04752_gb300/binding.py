@@ -110,7 +110,7 @@ class _ServerParams(ctypes.Structure):
                 ("budget_bytes", ctypes.c_int64), ("matvec_form", ctypes.c_int32),
                 ("inner_form", ctypes.c_int32), ("residual_form", ctypes.c_int32),
                 ("restart", ctypes.c_int32), ("inner_tol", ctypes.c_double),
-                ("max_inner", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("max_inner", ctypes.c_int32), ("solve_slots", ctypes.c_int32)]
 
 
 class _Request(ctypes.Structure):
@@ -713,12 +713,13 @@ class Server:
     host arrays x / y) and returns one result dict per request."""
 
     def __init__(self, mats, slots=8, queue_cap=1024, budget_bytes=8 << 30, matvec_form="fp16",
-                 inner_form="fp16", residual_form="fp32", restart=30, inner_tol=1e-3, max_inner=0):
+                 inner_form="fp16", residual_form="fp32", restart=30, inner_tol=1e-3, max_inner=0,
+                 solve_slots=0):
         lib = load()
         self.mats = list(mats)
         f = lambda v: FORMS[v] if isinstance(v, str) else int(v)
         p = _ServerParams(int(slots), int(queue_cap), int(budget_bytes), f(matvec_form), f(inner_form),
-                          f(residual_form), int(restart), float(inner_tol), int(max_inner), 0)
+                          f(residual_form), int(restart), float(inner_tol), int(max_inner), int(solve_slots))
         arr = (ctypes.c_void_p * len(self.mats))(*[m._h.value for m in self.mats])
         h = ctypes.c_void_p()
         _check(lib.hm_server_create(arr, len(self.mats), ctypes.byref(p), ctypes.byref(h)))

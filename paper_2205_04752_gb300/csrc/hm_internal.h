@@ -107,8 +107,11 @@ struct NearSrc {
 };
 // INT16 near stream (the INT16 form): a column is a header of kNear16Head
 // bytes (six FP32 scales, max |value| / 32767 of V_11 .. V_33 over the
-// leaf's rows, then padding) and six segments of mp int16, 32 + 12 mp bytes
-constexpr int kNear16Head = 32;
+// leaf's rows, then padding) and six segments of mp 16-bit values (offset
+// binary, see cvt<int16_t>), 48 + 12 mp bytes: an odd number of 16-byte
+// chunks, so that the columns read by eight consecutive consumer threads
+// start in different shared-memory banks
+constexpr int kNear16Head = 48;
 // one admissible block of the far-field forward pass (32 bytes): column
 // cluster start and size, first factor column, total rank, mesh, column offset
 // of its V inside its group's row-major matrix, the group, and the rank of

@@ -466,10 +466,12 @@ __global__ void __launch_bounds__(kTile1Threads) fwd_tile1_kernel(
     const int nst = (n16 + kTile1Rows - 1) / kTile1Rows;
     const MeshDev& md = ONE ? m0 : meshes[tu.mesh];
     const TF* Vu = static_cast<const TF*>(md.Vr) + tu.v0;
+    // V is read once per product: evict it from L2 first (x and w stay)
+    const uint64_t pol = stream::l2_evict_first_policy();
     auto issue = [&](int q) {
         const uint32_t bytes = (uint32_t)(min(kTile1Rows, n16 - q * kTile1Rows) * cu * 2);
         stream::mbar_arrive_expect_tx(&vbar[q & 1], bytes);
-        stream::bulk_g2s(vs[q & 1], Vu + (size_t)q * kTile1Rows * cu, bytes, &vbar[q & 1]);
+        stream::bulk_g2s_hint(vs[q & 1], Vu + (size_t)q * kTile1Rows * cu, bytes, &vbar[q & 1], pol);
     };
     if (tid == 0) {
         stream::mbar_init(&vbar[0], 1);
@@ -824,12 +826,17 @@ template <>
 __device__ __forceinline__ __half cvt<__half>(double v) { return __float2half_rn((float)v); }
 template <>
 __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
-// INT16 form: v is already divided by its column's max |v| (|v| <= 1)
+// INT16 form: v is already divided by its column's max |v| (|v| <= 1);
+// q = round(32767 v) is stored in offset binary, q + 32768 as an unsigned
+// 16-bit pattern (see stream::i16x2_to_float2)
+__device__ __forceinline__ int16_t i16_store(int q)
+{
+    return (int16_t)(uint16_t)(max(-32767, min(32767, q)) + 32768);
+}
 template <>
 __device__ __forceinline__ int16_t cvt<int16_t>(double v)
 {
-    const int q = __double2int_rn(v * 32767.0);
-    return (int16_t)max(-32767, min(32767, q));
+    return i16_store(__double2int_rn(v * 32767.0));
 }
 
 // per-column scale of the 16-bit forms: max |column| (1 for a zero column)
@@ -985,12 +992,13 @@ __global__ void pack_nl16_kernel(const int32_t* __restrict__ leaf, const int64_t
             for (int i = 0; i < mt; ++i) mx = fmax(mx, fabs(seg[i]));
             unsigned char* col = base + (size_t)(c0 + j - ndiag) * colB;
             reinterpret_cast<float*>(col)[v] = (float)(mx / 32767.0);
-            if (v == 0) reinterpret_cast<float*>(col)[6] = reinterpret_cast<float*>(col)[7] = 0.0f;
+            if (v == 0)
+                for (int z = 6; z < kNear16Head / 4; ++z) reinterpret_cast<float*>(col)[z] = 0.0f;
             int16_t* d = reinterpret_cast<int16_t*>(col + kNear16Head) + (size_t)v * mp;
             for (int i = 0; i < mp; ++i) {
                 int qv = 0;
-                if (i < mt && mx > 0.0) qv = max(-32767, min(32767, __double2int_rn(seg[i] / mx * 32767.0)));
-                d[i] = (int16_t)qv;
+                if (i < mt && mx > 0.0) qv = __double2int_rn(seg[i] / mx * 32767.0);
+                d[i] = i16_store(qv);
             }
         }
     }

@@ -255,6 +255,8 @@ int hm_server_create(const hm_matrix* const* mats, int32_t nmat, const hm_server
     if (p.restart <= 0) p.restart = 30;
     if (p.restart > 127) return fail(HM_EINVAL, "hm_server_create: restart above 127");
     if (p.inner_tol <= 0.0) p.inner_tol = 1e-3;
+    if (p.solve_slots < 0 || p.solve_slots > p.slots)
+        return fail(HM_EINVAL, "hm_server_create: solve_slots must lie in 0..slots");
     for (int32_t f : {p.matvec_form, p.inner_form, p.residual_form})
         if (f < HM_FP64 || f >= HM_NFORMS) return fail(HM_EINVAL, "hm_server_create: unknown form %d", f);
     for (int32_t m = 0; m < nmat; ++m) {
@@ -328,6 +330,8 @@ int hm_server_run(hm_server* S, const hm_request* reqs, int32_t n, int32_t realt
     int32_t next = 0, finished = 0;
     std::vector<int> idle;
     for (int w = S->prm.slots - 1; w >= 0; --w) idle.push_back(w);
+    const int solve_cap = S->prm.solve_slots;
+    int solves_running = 0;
     std::vector<size_t> fp((size_t)n);
     for (int32_t i = 0; i < n; ++i) fp[(size_t)i] = up(footprint(*S, reqs[i]).total);
     {
@@ -352,17 +356,28 @@ int hm_server_run(hm_server* S, const hm_request* reqs, int32_t n, int32_t realt
                 Slot& sl = R.slots[w];
                 if (sl.done) {
                     sl.done = false;
+                    if (reqs[sl.idx].kind == HM_REQ_SOLVE) --solves_running;
                     arena.release(sl.off, sl.bytes);
                     idle.push_back((int)w);
                     ++finished;
                 }
             }
-            // admission in arrival order: a free slot and room in the arena
-            while (!queue.empty() && !idle.empty()) {
-                const int i = queue.front();
+            // admission: each kind in arrival order, a free slot (a solve also
+            // one of its solve_slots) and room in the arena; a solve that must
+            // wait does not hold back the matvec requests behind it
+            bool blocked[2] = {false, false};
+            for (auto it = queue.begin(); it != queue.end() && !idle.empty();) {
+                const int i = *it;
+                const int kind = reqs[i].kind == HM_REQ_SOLVE ? 1 : 0;
+                if (blocked[kind] || (kind == 1 && solve_cap > 0 && solves_running >= solve_cap)) {
+                    blocked[kind] = true;
+                    ++it;
+                    if (blocked[0] && blocked[1]) break;
+                    continue;
+                }
                 const size_t off = arena.alloc(fp[(size_t)i]);
-                if (off == SIZE_MAX) break;
-                queue.pop_front();
+                if (off == SIZE_MAX) break;  // memory: admit nothing out of order
+                it = queue.erase(it);
                 const int w = idle.back();
                 idle.pop_back();
                 Slot& sl = R.slots[(size_t)w];
@@ -370,6 +385,7 @@ int hm_server_run(hm_server* S, const hm_request* reqs, int32_t n, int32_t realt
                 sl.off = off;
                 sl.bytes = fp[(size_t)i];
                 sl.has_job = true;
+                if (kind == 1) ++solves_running;
                 out[i].start_s = R.now();
                 R.cv_work.notify_all();
             }

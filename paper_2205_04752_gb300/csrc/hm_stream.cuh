@@ -36,7 +36,7 @@ namespace stream {
 
 constexpr int kThreads = 256;             // warp 0 producer + 7 consumer warps
 constexpr int kConsumers = kThreads - 32;
-constexpr int kStages = 4;
+constexpr int kStages = 5;
 constexpr int kStageBytes = 16384;
 constexpr int kMaxSeg = 256;              // segments / columns per stage at most
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
@@ -118,6 +118,38 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
             smem_addr(dst)),
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
+}
+
+// the same with an L2 cache policy (the streamed factors and near field are
+// read once per product: evict them first, so that the vectors and tables the
+// kernels read repeatedly stay in L2)
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                              uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+        : "memory");
+}
+
+__device__ __forceinline__ uint64_t l2_evict_first_policy()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// prefetch [p, p + bytes) into L2: only the 16-byte-aligned interior, so that
+// nothing outside the range is touched
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes)
+{
+    const uintptr_t a = (uintptr_t)p, b = a + bytes;
+    const uintptr_t a16 = (a + 15) & ~(uintptr_t)15, b16 = b & ~(uintptr_t)15;
+    for (uintptr_t q = a16; q < b16; q += 65536) {
+        const uint32_t n = (uint32_t)min((uintptr_t)65536, b16 - q);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(q), "r"(n) : "memory");
+    }
 }
 
 // 16-byte asynchronous copy global -> shared through the load/store path
@@ -210,16 +242,16 @@ struct Smem16<__nv_bfloat16, TA> {
     }
 };
 
-// Two int16 values of a 32-bit word (low half first) as exact FP32 values:
-// q ^ 0x8000 is q + 32768 as an unsigned 16-bit integer u; placed under the
-// exponent of 2^23 (bytes u_lo, u_hi, 0x00, 0x4B) it is the float 2^23 + u,
-// and subtracting 2^23 + 2^15 leaves q exactly.  Integer byte permutes and
-// one FP32 add per value, no int-to-float conversion instruction.
+// Two values of the INT16 form from a 32-bit word (low half first) as exact
+// FP32 values.  The form stores q in [-32767, 32767] in offset binary,
+// u = q + 32768 as an unsigned 16-bit integer; placed under the exponent of
+// 2^23 (bytes u_lo, u_hi, 0x00, 0x4B) it is the float 2^23 + u, and
+// subtracting 2^23 + 2^15 leaves q exactly.  One byte permute and one FP32
+// add per value, no int-to-float conversion instruction.
 __device__ __forceinline__ float2 i16x2_to_float2(uint32_t word)
 {
-    const uint32_t u = word ^ 0x80008000u;
-    const float lo = __uint_as_float(__byte_perm(u, 0x4B000000u, 0x7410)) - 8421376.0f;
-    const float hi = __uint_as_float(__byte_perm(u, 0x4B000000u, 0x7432)) - 8421376.0f;
+    const float lo = __uint_as_float(__byte_perm(word, 0x4B000000u, 0x7410)) - 8421376.0f;
+    const float hi = __uint_as_float(__byte_perm(word, 0x4B000000u, 0x7432)) - 8421376.0f;
     return make_float2(lo, hi);
 }
 
@@ -268,20 +300,22 @@ __device__ __forceinline__ void smem_rows(const T* p, TA* o)
 // consumer thread holds Rr rows (16 bytes of U) for RC right-hand sides.
 // RC = 1 is the single-vector kernel; RC * Rr = 16 otherwise.
 // A slot is kStageBytes of stream data followed by kAuxBytes of staged 4-vectors.
-// The single-vector kernel keeps 4 slots and a separate reduction area
-// (about 100 KB, two CTAs per SM); the multi-vector kernel keeps 3 slots of
-// 32 KB and reduces a finished leaf inside the slot of its last stage, one
-// RHS-chunk position at a time, so that it too fits two CTAs per SM.
+// A finished leaf is reduced inside the slot of its last stage (released
+// afterwards): the single-vector kernel one output component at a time, the
+// multi-vector kernel one RHS-chunk position at a time.  The single-vector
+// kernel keeps 5 slots of 20 KB, the multi-vector kernel 3 of 48 KB: two CTAs
+// per SM either way, and ten 16 KB stages in flight per SM for one vector
+// (the copy pipeline, not the arithmetic, bounds that kernel).
 template <class TF, class TA, int RC>
 struct LeafCfg {
     static constexpr int Rr = Smem16<TF, TA>::N;
-    static constexpr int kS = RC == 1 ? 4 : 3;
+    static constexpr int kS = RC == 1 ? 5 : 3;
     static constexpr int kAuxBytes = RC == 1 ? kMaxSeg * 4 * (int)sizeof(TA) : 16384;
     static constexpr int kSlotBytes = kStageBytes + kAuxBytes;
-    static constexpr int kRedBytes = kConsumers * Rr * 3 * (int)sizeof(TA) * (RC == 1 ? 1 : 0);
-    static_assert(RC == 1 || kConsumers * Rr * 3 * (int)sizeof(TA) <= kSlotBytes,
-                  "one RHS position of the leaf reduction must fit a slot");
-    static constexpr size_t smem() { return (size_t)kS * kSlotBytes + (size_t)kRedBytes; }
+    static_assert(kS <= kStages, "the barrier arrays hold kStages slots");
+    static_assert(kConsumers * Rr * (RC == 1 ? 1 : 3) * (int)sizeof(TA) <= kSlotBytes,
+                  "one pass of the leaf reduction must fit a slot");
+    static constexpr size_t smem() { return (size_t)kS * kSlotBytes; }
 };
 
 // ---------------------------------------------------------------- producer
@@ -309,6 +343,7 @@ __device__ __forceinline__ void leaf_producer(const int2* __restrict__ work, int
     uint32_t near_parity = 0u;   // bit q: parity of the next near release of slot q
     constexpr int kSlotBytes = kStage + kAuxBytes;
     const int lane = threadIdx.x & 31;
+    const uint64_t stream_policy = l2_evict_first_policy();
     const int vecG = 4 * G;
     auto sdata = [&](int q) { return smem + (size_t)q * kSlotBytes; };
     auto saux = [&](int q) { return smem + (size_t)q * kSlotBytes + kStage; };
@@ -434,7 +469,7 @@ __device__ __forceinline__ void leaf_producer(const int2* __restrict__ work, int
                 __syncwarp();
                 if (lane == 0) {
                     mbar_arrive_expect_tx(&full[slot], bytes + bulk);
-                    bulk_g2s(sdata(slot), src, bytes, &full[slot]);
+                    bulk_g2s_hint(sdata(slot), src, bytes, &full[slot], stream_policy);
                 }
             } else if (lane == 0) {
                 mbar_arrive(&full[slot]);
@@ -478,6 +513,11 @@ __device__ __forceinline__ void leaf_producer(const int2* __restrict__ work, int
             }
             const int2* fitems = reinterpret_cast<const int2*>(md.lf_items + fi0);
             const int2* nitems = reinterpret_cast<const int2*>(md.ln_items + ni0);
+            // the leaf's item tables, read by every stage's scan, into L2 now
+            if (lane == 0) {
+                prefetch_l2(fitems, (size_t)(fi1 - fi0) * sizeof(int2));
+                prefetch_l2(nitems, (size_t)(ni1 - ni0) * sizeof(int2));
+            }
             int cur = 0;
             for (int g = 0; g < S && ok; g += perF) {
                 const int cnt = min(perF, S - g);
@@ -529,7 +569,6 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
     // slot q: stream data at smem + q * kSlotBytes, its 4-vectors kStageBytes later
     auto sdata = [&](int q) { return smem + (size_t)q * Cfg::kSlotBytes; };
     auto saux = [&](int q) { return smem + (size_t)q * Cfg::kSlotBytes + kStageBytes; };
-    TA* red1 = reinterpret_cast<TA*>(smem + (size_t)NS * Cfg::kSlotBytes);  // single-vector kernel only
     __shared__ __align__(8) uint64_t full[kStages];
     __shared__ __align__(8) uint64_t empty[kStages];
     __shared__ StageMeta meta[kStages];
@@ -578,9 +617,21 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
             mp = (mt + 7) & ~7;
             P = mp / Rr;
             H = kConsumers / (P * NRC);
-            p = ctid % P;
-            c = (ctid / P) % NRC;
-            h = ctid / (P * NRC);
+            if (std::is_same<TF, int16_t>::value && RC == 1) {
+                // INT16 form, one vector: segments fastest, so that the eight
+                // threads of a shared-memory phase read eight consecutive
+                // segments (columns) of one row block -- distinct 16-byte
+                // positions of a tile, or columns an odd number of 16-byte
+                // chunks apart -- and no two of them share a bank
+                h = ctid % H;
+                p = ctid / H;
+                c = 0;
+                if (p >= P) h = H;  // idle
+            } else {
+                p = ctid % P;
+                c = (ctid / P) % NRC;
+                h = ctid / (P * NRC);
+            }
 #pragma unroll
             for (int e = 0; e < Rr; ++e)
 #pragma unroll
@@ -756,46 +807,63 @@ __global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
                 }
             }
         }
-        if (RC == 1 || !m.last) {
+        if (!m.last) {
             // the slot may be refilled once every consumer warp is done with it
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[slot]);
-        }
-        if (m.last) {
+        } else {
             // the H partial sums of every (row, vector, component), added in a
-            // fixed order; red[((h * P + p) * NRC + c)][e][a] for one position q
-            // of the RHS chunk at a time (the multi-vector kernel reuses the
-            // slot of this last stage, released afterwards)
-            TA* red = RC == 1 ? red1 : reinterpret_cast<TA*>(sdata(slot));
-            constexpr int kPer = Rr * 3;
-            if (RC > 1) named_barrier_consumers();  // everyone is done reading the slot
+            // fixed order inside the slot of this last stage (released
+            // afterwards): one output component at a time for one vector,
+            // red[(h * P + p) * Rr + e]; one position q of the RHS chunk at a
+            // time for several, red[((h * P + p) * NRC + c)][e][a]
+            TA* red = reinterpret_cast<TA*>(sdata(slot));
+            named_barrier_consumers();  // everyone is done reading the slot
+            if (RC == 1) {
 #pragma unroll
-            for (int q = 0; q < RC; ++q) {
-                if (h < H) {
-                    TA* rp = red + (size_t)((h * P + p) * NRC + c) * kPer;
+                for (int a = 0; a < 3; ++a) {
+                    if (h < H) {
+                        TA* rp = red + (size_t)(h * P + p) * Rr;
 #pragma unroll
-                    for (int e = 0; e < Rr; ++e)
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) rp[e * 3 + a] = acc[e][q][a];
+                        for (int e = 0; e < Rr; ++e) rp[e] = acc[e][0][a];
+                    }
+                    named_barrier_consumers();
+                    for (int i = ctid; i < mt; i += kConsumers) {
+                        const int pp = i / Rr, e = i - pp * Rr;
+                        TA sum = (TA)0;
+                        for (int g = 0; g < H; ++g) sum += red[(size_t)(g * P + pp) * Rr + e];
+                        y[xoff + 3 * (size_t)perm[t0 + i] + a] = (double)sum;
+                    }
+                    named_barrier_consumers();
                 }
-                named_barrier_consumers();
-                const int nvec = (G - q + RC - 1) / RC;  // vectors r = cc * RC + q < G
-                const int per_row = 3 * nvec;
-                for (int idx = ctid; idx < mt * per_row; idx += kConsumers) {
-                    const int i = idx / per_row, rem = idx - i * per_row;
-                    const int cc = rem / 3, a = rem - 3 * cc;
-                    const int pp = i / Rr, e = i - pp * Rr;
-                    TA sum = (TA)0;
-                    for (int g = 0; g < H; ++g) sum += red[(size_t)((g * P + pp) * NRC + cc) * kPer + e * 3 + a];
-                    const int r = cc * RC + q;
-                    y[(size_t)r * ld + xoff + 3 * (size_t)perm[t0 + i] + a] = (double)sum;
+            } else {
+                constexpr int kPer = Rr * 3;
+#pragma unroll
+                for (int q = 0; q < RC; ++q) {
+                    if (h < H) {
+                        TA* rp = red + (size_t)((h * P + p) * NRC + c) * kPer;
+#pragma unroll
+                        for (int e = 0; e < Rr; ++e)
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) rp[e * 3 + a] = acc[e][q][a];
+                    }
+                    named_barrier_consumers();
+                    const int nvec = (G - q + RC - 1) / RC;  // vectors r = cc * RC + q < G
+                    const int per_row = 3 * nvec;
+                    for (int idx = ctid; idx < mt * per_row; idx += kConsumers) {
+                        const int i = idx / per_row, rem = idx - i * per_row;
+                        const int cc = rem / 3, a = rem - 3 * cc;
+                        const int pp = i / Rr, e = i - pp * Rr;
+                        TA sum = (TA)0;
+                        for (int g = 0; g < H; ++g) sum += red[(size_t)((g * P + pp) * NRC + cc) * kPer + e * 3 + a];
+                        const int r = cc * RC + q;
+                        y[(size_t)r * ld + xoff + 3 * (size_t)perm[t0 + i] + a] = (double)sum;
+                    }
+                    named_barrier_consumers();
                 }
-                named_barrier_consumers();
             }
-            if (RC > 1) {
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[slot]);
-            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[slot]);
         }
     }
 }

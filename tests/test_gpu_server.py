@@ -99,3 +99,27 @@ def test_admission_by_footprint_and_queue_cap():
     assert all(r["status"] == binding.HM_OK for r in res)
     iv = sorted((r["start_s"], r["done_s"]) for r in res)
     assert all(iv[i + 1][0] >= iv[i][1] - 1e-9 for i in range(3))
+
+
+def test_solve_slots_keep_a_lane_for_matvecs():
+    """With solve_slots = 1 of 2 slots, solves run one at a time and the
+    matvec requests queued behind them are admitted while they wait; every
+    result still equals the same request run alone."""
+    mats = pool()
+    srv = binding.Server(mats, slots=2, queue_cap=64, budget_bytes=1 << 30, solve_slots=1)
+    solves = [dict(mesh=2, kind="solve", nrhs=1, seed=10 + i, tol=1e-6, y=np.full((1, 3 * mats[2].M), np.nan))
+              for i in range(3)]
+    mvs = [dict(mesh=1, kind="matvec", nrhs=2, seed=20 + i, y=np.full((2, 3 * mats[1].M), np.nan))
+           for i in range(3)]
+    reqs = solves + mvs
+    res = srv.run(reqs, realtime=False)
+    assert all(r["status"] == binding.HM_OK for r in res), [r["status"] for r in res]
+    sv = sorted((r["start_s"], r["done_s"]) for r in res[:3])
+    assert all(sv[i + 1][0] >= sv[i][1] - 1e-9 for i in range(2))   # one solve at a time
+    assert min(r["start_s"] for r in res[3:]) < sv[1][0]            # matvecs did not wait for the solves
+    for q, r in zip(reqs, res):
+        alone = dict(q, y=np.full_like(q["y"], np.nan))
+        assert srv.run([alone], realtime=False)[0]["status"] == binding.HM_OK
+        assert np.array_equal(alone["y"], q["y"]), q["kind"]
+    with pytest.raises(binding.HMError):
+        binding.Server(mats, slots=2, solve_slots=3)
