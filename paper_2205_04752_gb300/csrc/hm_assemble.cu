@@ -1537,7 +1537,8 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
                 if (tr.nodes[n].son[c] >= 0) parent[(size_t)tr.nodes[n].son[c]] = (int64_t)n;
         std::vector<int32_t> leafv, lf_ptr(1, 0), ln_ptr(1, 0);
         std::vector<int64_t> lf_base, ln_base;
-        std::vector<LeafFarItem> lf_items;
+        std::vector<LeafFarItem> lf_items, lr_items;
+        std::vector<int32_t> lr_ptr(1, 0);
         std::vector<PackSrc> lf_src;
         std::vector<LeafNearItem> ln_items;
         std::vector<NearSrc> ln_src;
@@ -1571,6 +1572,17 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
                 }
             lf_items.push_back(LeafFarItem{seg, 0});  // sentinel: number of segments
             lf_src.push_back(PackSrc{0, 0, 0});
+            // w runs: an item continues the previous run when its columns do
+            for (int32_t q = lf_ptr.back(); q + 1 < (int32_t)lf_items.size(); ++q) {
+                const LeafFarItem it = lf_items[(size_t)q];
+                if (q > lf_ptr.back()) {
+                    const LeafFarItem& pv = lf_items[(size_t)q - 1];
+                    if (it.col == pv.col + (it.seg_start - pv.seg_start)) continue;
+                }
+                lr_items.push_back(it);
+            }
+            lr_items.push_back(LeafFarItem{seg, 0});
+            lr_ptr.push_back((int32_t)lr_items.size());
             lf_ptr.push_back((int32_t)lf_items.size());
             // the 16-bit forms take segments 16 at a time (one tensor-core K step):
             // every leaf's U stream holds a multiple of 16 segments, zero padded
@@ -1632,6 +1644,8 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
         if ((rc = upload(H, H.d_lf_base, lf_base.data(), lf_base.size() * 8))) return rc;
         if ((rc = upload(H, H.d_lf_ptr, lf_ptr.data(), lf_ptr.size() * 4))) return rc;
         if ((rc = upload(H, H.d_lf_items, lf_items.data(), lf_items.size() * sizeof(LeafFarItem)))) return rc;
+        if ((rc = upload(H, H.d_lr_ptr, lr_ptr.data(), lr_ptr.size() * 4))) return rc;
+        if ((rc = upload(H, H.d_lr_items, lr_items.data(), lr_items.size() * sizeof(LeafFarItem)))) return rc;
         if ((rc = upload(H, H.d_lf_src, lf_src.data(), lf_src.size() * sizeof(PackSrc)))) return rc;
         if ((rc = upload(H, H.d_ln_base, ln_base.data(), ln_base.size() * 8))) return rc;
         if ((rc = upload(H, H.d_ln_ptr, ln_ptr.data(), ln_ptr.size() * 4))) return rc;

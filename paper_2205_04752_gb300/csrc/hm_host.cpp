@@ -624,7 +624,7 @@ static std::vector<hm::DevBuf*> matrix_bufs(hm_matrix* H)
 {
     std::vector<hm::DevBuf*> v = {
         &H->d_perm, &H->d_adm, &H->d_near, &H->d_rank, &H->d_uoff, &H->d_voff, &H->d_coff, &H->d_noff,
-        &H->d_leaf, &H->d_lf_base, &H->d_lf_ptr, &H->d_lf_items, &H->d_lf_src, &H->d_ln_base, &H->d_ln_ptr,
+        &H->d_leaf, &H->d_lf_base, &H->d_lf_ptr, &H->d_lf_items, &H->d_lf_src, &H->d_lr_ptr, &H->d_lr_items, &H->d_ln_base, &H->d_ln_ptr,
         &H->d_ln_items, &H->d_ln_src, &H->d_vb_base, &H->d_vb_ld, &H->d_vb_coff, &H->fdesc, &H->d_groups,
         &H->d_units, &H->d_tcunits, &H->d_multi, &H->d_big, &H->d_small, &H->d_fwd_all, &H->d_work,
         &H->d_pos_prefix, &H->d_counters, &H->d_err, &H->U64, &H->V64, &H->N64, &H->Nl64, &H->Nl32, &H->SU,

@@ -186,6 +186,11 @@ struct MeshDev {
     const int64_t* lf_base;
     const int32_t* lf_ptr;
     const LeafFarItem* lf_items;
+    // the far items merged into runs whose w columns are contiguous (the
+    // kernels of a block, and blocks with consecutive columns): the w copies
+    // of a stage, lr_items[lr_ptr[leaf] .. lr_ptr[leaf + 1]) with a sentinel
+    const int32_t* lr_ptr;
+    const LeafFarItem* lr_items;
     const int64_t* ln_base;
     const int32_t* ln_ptr;
     const LeafNearItem* ln_items;
@@ -273,6 +278,7 @@ struct hm_matrix {
     hm::DevBuf d_noff;   // int64 nnear
     hm::DevBuf d_leaf;   // int32 2*nleaves (t0, m)
     hm::DevBuf d_lf_base, d_lf_ptr, d_lf_items, d_lf_src;  // far stream per leaf
+    hm::DevBuf d_lr_ptr, d_lr_items;                        // its w runs (MeshDev::lr_items)
     hm::DevBuf d_ln_base, d_ln_ptr, d_ln_items, d_ln_src;  // near stream per leaf
     hm::DevBuf d_ln16_base, d_ln16_diag;                   // INT16 near stream per leaf
     hm::DevBuf d_vb_base;                 // int64 nadm+1: V of each block (first row) in its group

@@ -1457,6 +1457,8 @@ MeshDev mesh_desc(const hm_matrix& H, int32_t form)
     m.lf_base = H.d_lf_base.as<int64_t>();
     m.lf_ptr = H.d_lf_ptr.as<int32_t>();
     m.lf_items = H.d_lf_items.as<LeafFarItem>();
+    m.lr_ptr = H.d_lr_ptr.as<int32_t>();
+    m.lr_items = H.d_lr_items.as<LeafFarItem>();
     m.ln_base = H.d_ln_base.as<int64_t>();
     m.ln_ptr = H.d_ln_ptr.as<int32_t>();
     m.ln_items = H.d_ln_items.as<LeafNearItem>();

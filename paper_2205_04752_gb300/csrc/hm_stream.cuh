@@ -488,9 +488,9 @@ __device__ __forceinline__ void leaf_producer(const int2* __restrict__ work, int
             const int lf = wk.y;
             const int mt = md.leaf[2 * lf + 1];
             const int mp = (mt + 7) & ~7;
-            const int fi0 = md.lf_ptr[lf], fi1 = md.lf_ptr[lf + 1];
+            const int fi0 = md.lr_ptr[lf], fi1 = md.lr_ptr[lf + 1];
             const int ni0 = md.ln_ptr[lf], ni1 = md.ln_ptr[lf + 1];
-            sreal = md.lf_items[fi1 - 1].seg_start;
+            sreal = md.lr_items[fi1 - 1].seg_start;
             // 16-bit streams are tiled in groups of 8 segments (and stored padded
             // to 16, the tensor-core K step); the single-vector kernel takes
             // stages in whole tiles, the multi-vector one in K steps
@@ -511,7 +511,7 @@ __device__ __forceinline__ void leaf_producer(const int2* __restrict__ work, int
                 if (lane == 0) atomicExch(err, 2);
                 break;
             }
-            const int2* fitems = reinterpret_cast<const int2*>(md.lf_items + fi0);
+            const int2* fitems = reinterpret_cast<const int2*>(md.lr_items + fi0);
             const int2* nitems = reinterpret_cast<const int2*>(md.ln_items + ni0);
             // the leaf's item tables, read by every stage's scan, into L2 now
             if (lane == 0) {
