@@ -1,5 +1,6 @@
 // hm_fwd_tc.cuh -- the far-field forward pass z = V^T x on the tensor cores
-// (tcgen05), for the FP16 / BF16 forms and up to 16 right-hand sides a launch.
+// (tcgen05), for the FP16 / BF16 / INT16 forms and up to 16 right-hand sides
+// a launch.
 //
 // A forward group holds the V of the admissible blocks that share a column
 // cluster s, side by side (Section 2: each block contributes w = c V^T x(s)).
@@ -10,7 +11,13 @@
 // MMA, accumulating in tensor memory:
 //   B = V, streamed 32 rows (a stage) at a time by one bulk copy each
 //       straight into the MN-major core-matrix layout (the 16-bit V of a
-//       unit is stored contiguously in 8 x 8 tiles);
+//       unit is stored contiguously in 8 x 8 tiles).  INT16 values (offset
+//       binary q = v + 32768) are split in shared memory into two FP16
+//       operands of the same layout, 256 (q / 256 - 128) and q mod 256, both
+//       exact, whose MMAs accumulate into the same rows;
+// Every ring is used in stage order by each of its waiting threads, or (the
+// A ring, filled by four warps round-robin) has a multiple of four slots, so
+// that no wait can see a barrier's parity of two phases before.
 //   A = x(s) of the G vectors, scaled by a power of two t_r per vector (from
 //       max|x_r|, so that every value fits FP16) and split into hi = fp16(x
 //       t_r) and lo = fp16(x t_r - hi): two K-major core-matrix tiles whose
@@ -26,6 +33,9 @@
 //               of slots (bulk copies);
 //   warps 2-5   build the A tiles from the gathered x into a second ring, a
 //               stage each round-robin, ahead of the V stream;
+//   warp 14     INT16 form: splits every stage's V once it has landed, in
+//               stage order (256 x high bytes in place, the low bytes into a
+//               ring of two buffers that the MMA commits release);
 //   warp 1      one thread issues the MMAs of a stage and commits them to the
 //               release barriers of its V and A slots, and after a unit's last
 //               stage to its accumulator barrier; two accumulators (2 x 256
@@ -47,21 +57,37 @@
 namespace hm {
 namespace stream {
 
-constexpr int kFpThreads = 448;
+constexpr int kFpThreads = 480;
 constexpr int kFpRows = 32;                          // rows (K) per stage: two MMA K steps
 constexpr int kFpCols = 256;                         // columns per unit at most (one N tile)
 constexpr int kFpVBytes = kFpRows * kFpCols * 2;     // V of a stage
 constexpr int kFpAHalf = 128 * kFpRows * 2;          // the hi (or lo) tile of a stage
 constexpr int kFpABytes = 2 * kFpAHalf;              // A of a stage: hi tile, lo tile
-constexpr int kFpVSlots = 7;
+constexpr int kFpVSlots = 7;                         // slots of the ring of V (16-bit floats)
 constexpr int kFpASlots = 4;
 constexpr int kFpSbo = (kFpRows / 8) * 128;          // M-direction core stride of an A tile
 constexpr int kFpBld = 33;                           // row stride of an epilogue warp's buffer
 constexpr int kFpBBytes = 32 * kFpBld * 4;           // one epilogue warp's buffer: 32 columns x 32 rows
+// the rings of a form: INT16 takes fewer V slots (the 256 x high bytes of
+// the split replace the stage) and a ring of LS buffers for the low bytes
+template <class TF>
+struct FpCfg {
+    static constexpr bool kI16 = std::is_same<TF, int16_t>::value;
+    static constexpr int VS = kI16 ? 5 : kFpVSlots;
+    static constexpr int LS = kI16 ? 2 : 0;
+    static constexpr int AS = kFpASlots;
+    static constexpr size_t smem()
+    {
+        return (size_t)(VS + LS) * kFpVBytes + (size_t)AS * kFpABytes + 8 * (size_t)kFpBBytes;
+    }
+};
+static_assert(kFpASlots % 4 == 0, "four builder warps take the A slots round-robin");
+template <class TF>
 constexpr size_t fp_smem()
 {
-    return (size_t)kFpVSlots * kFpVBytes + (size_t)kFpASlots * kFpABytes + 8 * (size_t)kFpBBytes;
+    return FpCfg<TF>::smem();
 }
+
 constexpr int kFpMeshes = 64;                        // meshes whose pointers are kept in shared memory
 static_assert(kFpCols == kFwdUnitCols, "a unit is one N tile");
 static_assert(kFwdUnitRows % kFpRows == 0, "a unit is whole stages, but its last one");
@@ -133,9 +159,15 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
     const MeshDev* __restrict__ meshes, int nmesh, const float* __restrict__ xg, float* __restrict__ w,
     float* __restrict__ z, int G, const int* __restrict__ xmax, int* __restrict__ err)
 {
-    constexpr bool kBf16 = !std::is_same<TF, __half>::value;
+    using Cfg = FpCfg<TF>;
+    constexpr bool kI16 = Cfg::kI16;
+    constexpr int VS = Cfg::VS, AS = Cfg::AS, LS = Cfg::LS;
+    constexpr bool kBf16 = std::is_same<TF, __nv_bfloat16>::value;
+    using TO = typename std::conditional<kBf16, __nv_bfloat16, __half>::type;  // the operand type
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t vfull[kFpVSlots];   // the V of a stage has landed
+    __shared__ __align__(8) uint64_t vconv[kFpVSlots];   // INT16: the V of a stage is split
+    __shared__ __align__(8) uint64_t lempty[2];          // INT16: the MMAs that read a low-byte buffer are done
     __shared__ __align__(8) uint64_t vempty[kFpVSlots];  // the MMAs that read a V slot are done
     __shared__ __align__(8) uint64_t afull[kFpASlots];   // the A of a stage is built
     __shared__ __align__(8) uint64_t aempty[kFpASlots];  // the MMAs that read an A slot are done
@@ -154,13 +186,16 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
     const int nq = (ng + 7) >> 3;    // distinct quarter contents
     const int rep = 4 / nq;          // copies of each (4 or 2)
     auto slot_v = [&](int s) { return smem + (size_t)s * kFpVBytes; };
-    auto slot_a = [&](int s) { return smem + (size_t)kFpVSlots * kFpVBytes + (size_t)s * kFpABytes; };
+    auto slot_l = [&](int s) { return smem + (size_t)(VS + s) * kFpVBytes; };
+    auto slot_a = [&](int s) { return smem + (size_t)(VS + LS) * kFpVBytes + (size_t)s * kFpABytes; };
     if (tid == 0) {
-        for (int s = 0; s < kFpVSlots; ++s) {
+        for (int s = 0; s < VS; ++s) {
             mbar_init(&vfull[s], 1);
+            mbar_init(&vconv[s], 1);
             mbar_init(&vempty[s], 1);
         }
-        for (int s = 0; s < kFpASlots; ++s) {
+        for (int s = 0; s < LS; ++s) mbar_init(&lempty[s], 1);
+        for (int s = 0; s < AS; ++s) {
             mbar_init(&afull[s], 1);
             mbar_init(&aempty[s], 1);
         }
@@ -186,7 +221,7 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
         smesh[m] = FpMesh{md.Vr, md.fdesc, md.xgoff, md.woff};
     }
     // A rows that no stage writes (vectors >= G, the fourth component) stay zero
-    for (int e = tid; e < kFpASlots * kFpABytes / 16; e += kFpThreads)
+    for (int e = tid; e < AS * kFpABytes / 16; e += kFpThreads)
         reinterpret_cast<uint4*>(slot_a(0))[e] = make_uint4(0u, 0u, 0u, 0u);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (warp == 0) {
@@ -221,9 +256,9 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
                 const TF* Vg = static_cast<const TF*>(mesh_of_unit(un.mesh).Vr) + un.v0;
                 const int n16 = (un.nrows + 15) & ~15, cu = un.ncols;
                 for (int q = 0; q * kFpRows < n16; ++q, ++it) {
-                    const int slot = it % kFpVSlots;
-                    if (it >= kFpVSlots &&
-                        !fp_wait(&vempty[slot], (uint32_t)((it / kFpVSlots) - 1) & 1u, abort_flag, err, 7, it)) {
+                    const int slot = it % VS;
+                    if (it >= VS &&
+                        !fp_wait(&vempty[slot], (uint32_t)((it / VS) - 1) & 1u, abort_flag, err, 7, it)) {
                         run = false;
                         break;
                     }
@@ -255,9 +290,9 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
                 const uint32_t idesc = tc_idesc(nN, kBf16);
                 const uint32_t kstride = (uint32_t)cu * 16;  // K-direction core stride of V
                 for (int q = 0; q * kFpRows < n16; ++q, ++it) {
-                    const int vs = it % kFpVSlots, as = it % kFpASlots;
-                    if (!fp_wait(&vfull[vs], (uint32_t)(it / kFpVSlots) & 1u, abort_flag, err, 9, it) ||
-                        !fp_wait(&afull[as], (uint32_t)(it / kFpASlots) & 1u, abort_flag, err, 10, it)) {
+                    const int vs = it % VS, as = it % AS;
+                    if (!fp_wait(kI16 ? &vconv[vs] : &vfull[vs], (uint32_t)(it / VS) & 1u, abort_flag, err, 9, it) ||
+                        !fp_wait(&afull[as], (uint32_t)(it / AS) & 1u, abort_flag, err, 10, it)) {
                         run = false;
                         break;
                     }
@@ -270,9 +305,17 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
                         const uint64_t bd = tc_desc(b0 + (uint32_t)ks * 2 * kstride, kstride, 128);
                         tc_mma(d, ah, bd, idesc, (q > 0 || ks > 0) ? 1u : 0u);
                         tc_mma(d, al, bd, idesc, 1u);
+                        if (kI16) {
+                            // the low bytes of the split, in the stage's buffer
+                            const uint64_t bl = tc_desc(smem_addr(slot_l(it % 2)) + (uint32_t)ks * 2 * kstride,
+                                                        kstride, 128);
+                            tc_mma(d, ah, bl, idesc, 1u);
+                            tc_mma(d, al, bl, idesc, 1u);
+                        }
                     }
                     tc_commit(&vempty[vs]);
                     tc_commit(&aempty[as]);
+                    if (kI16) tc_commit(&lempty[it % 2]);
                 }
                 if (run) tc_commit(&accf[ab]);
             }
@@ -298,10 +341,10 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
             const float* x0 = xg + ((size_t)mesh_of_unit(un.mesh).xgoff + un.x0) * G * 4;
             for (int q = 0; q < nst; ++q, ++it) {
                 if ((it & 3) != bw) continue;
-                const int as = it % kFpASlots;
+                const int as = it % AS;
                 // the lanes of a warp decide together (they meet at __syncwarp)
-                const bool got = it < kFpASlots ||
-                                 fp_wait(&aempty[as], (uint32_t)((it / kFpASlots) - 1) & 1u, abort_flag, err, 11, it);
+                const bool got = it < AS ||
+                                 fp_wait(&aempty[as], (uint32_t)((it / AS) - 1) & 1u, abort_flag, err, 11, it);
                 if (!__all_sync(0xffffffffu, got)) {
                     run = false;
                     break;
@@ -324,9 +367,9 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
                                                 {xv[i + 1].x * t, xv[i + 1].y * t, xv[i + 1].z * t}};
 #pragma unroll
                         for (int a = 0; a < 3; ++a) {
-                            const uint32_t h0 = tc_bits<TF>(va[0][a]), h1 = tc_bits<TF>(va[1][a]);
-                            const uint32_t l0 = tc_bits<TF>(va[0][a] - tc_back<TF>((unsigned short)h0));
-                            const uint32_t l1 = tc_bits<TF>(va[1][a] - tc_back<TF>((unsigned short)h1));
+                            const uint32_t h0 = tc_bits<TO>(va[0][a]), h1 = tc_bits<TO>(va[1][a]);
+                            const uint32_t l0 = tc_bits<TO>(va[0][a] - tc_back<TO>((unsigned short)h0));
+                            const uint32_t l1 = tc_bits<TO>(va[1][a] - tc_back<TO>((unsigned short)h1));
                             hw[a][i >> 1] = h0 | (h1 << 16);
                             lw[a][i >> 1] = l0 | (l1 << 16);
                         }
@@ -347,6 +390,48 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
                 if (lane == 0) mbar_arrive(&afull[as]);
             }
         }
+    } else if (warp == 14) {
+        // ---- INT16: split every stage's V in stage order once it has landed
+        // (and its low-byte buffer is free): 256 x high bytes in place, the
+        // low bytes into the buffer
+        if constexpr (kI16) {
+            int it = 0;
+            bool run = true;
+            FwdTcUnit nx{};
+            if ((int)blockIdx.x < nunits) nx = units[blockIdx.x];
+            for (int u = blockIdx.x; u < nunits && run; u += gridDim.x) {
+                const FwdTcUnit un = nx;
+                if (u + (int)gridDim.x < nunits) nx = units[u + gridDim.x];
+                const int n16 = (un.nrows + 15) & ~15;
+                for (int q = 0; q * kFpRows < n16; ++q, ++it) {
+                    const int vs = it % VS, ls = it % 2;
+                    bool got = fp_wait(&vfull[vs], (uint32_t)(it / VS) & 1u, abort_flag, err, 15, it);
+                    if (got && it >= 2)
+                        got = fp_wait(&lempty[ls], (uint32_t)((it / 2) - 1) & 1u, abort_flag, err, 16, it);
+                    if (!__all_sync(0xffffffffu, got)) {
+                        run = false;
+                        break;
+                    }
+                    uint4* V = reinterpret_cast<uint4*>(slot_v(vs));
+                    uint4* L = reinterpret_cast<uint4*>(slot_l(ls));
+                    const int nkr = min(kFpRows / 8, (n16 >> 3) - q * (kFpRows / 8));
+                    const int nch = nkr * un.ncols;  // 16-byte chunks of the stage
+                    for (int e = lane; e < nch; e += 32) {
+                        const uint4 v = V[e];
+                        uint4 h, l;
+                        i16_split_word(v.x, h.x, l.x);
+                        i16_split_word(v.y, h.y, l.y);
+                        i16_split_word(v.z, h.z, l.z);
+                        i16_split_word(v.w, h.w, l.w);
+                        V[e] = h;
+                        L[e] = l;
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&vconv[vs]);
+                }
+            }
+        }
     } else {
         // ---- epilogue: warps 6-9 take the units with an even local index
         // (accumulator 0), warps 10-13 the odd ones (accumulator 1).  The warp
@@ -354,7 +439,7 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
         // l % 4 of k = l / 4) and, of the 32-column rounds of the unit, those
         // with index = q / nq mod rep.
         const int e = (warp - 6) >> 2, quarter = warp & 3;
-        float* B = reinterpret_cast<float*>(smem + (size_t)kFpVSlots * kFpVBytes + (size_t)kFpASlots * kFpABytes +
+        float* B = reinterpret_cast<float*>(smem + (size_t)(VS + LS) * kFpVBytes + (size_t)AS * kFpABytes +
                                             (size_t)(warp - 6) * kFpBBytes);
         const int vb = 8 * (quarter % nq);                                // first vector of the quarter
         const int nk = quarter < rep * nq ? max(0, min(8, ng - vb)) : 0;  // vectors of the quarter
@@ -462,8 +547,8 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
         // no copy may still write into shared memory and no MMA may still run
         // when the CTA frees its tensor memory and exits
         if (tid == 0)
-            for (int q = max(0, issued - kFpVSlots); q < issued; ++q)
-                mbar_wait(&vfull[q % kFpVSlots], (uint32_t)(q / kFpVSlots) & 1u, err, 13, q);
+            for (int q = max(0, issued - VS); q < issued; ++q)
+                mbar_wait(&vfull[q % VS], (uint32_t)(q / VS) & 1u, err, 13, q);
         if (tid == 32) {
             tc_fence_after();
             tc_commit(&fbar);

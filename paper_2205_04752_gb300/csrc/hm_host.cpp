@@ -628,7 +628,7 @@ static std::vector<hm::DevBuf*> matrix_bufs(hm_matrix* H)
         &H->d_ln_items, &H->d_ln_src, &H->d_vb_base, &H->d_vb_ld, &H->d_vb_coff, &H->fdesc, &H->d_groups,
         &H->d_units, &H->d_tcunits, &H->d_multi, &H->d_big, &H->d_small, &H->d_fwd_all, &H->d_work,
         &H->d_pos_prefix, &H->d_counters, &H->d_err, &H->U64, &H->V64, &H->N64, &H->Nl64, &H->Nl32, &H->SU,
-        &H->SV, &H->SW16, &H->xg, &H->wb, &H->zb, &H->xh, &H->yh, &H->g_coll, &H->g_tri, &H->g_qp, &H->g_qw,
+        &H->SV, &H->SW16, &H->fdesc16, &H->xg, &H->wb, &H->zb, &H->xh, &H->yh, &H->g_coll, &H->g_tri, &H->g_qp, &H->g_qw,
         &H->Nl16, &H->d_ln16_base, &H->d_ln16_diag,
         &H->g_diam, &H->d_rperm, &H->g_rows, &H->g_nrm, &H->d_star_ptr, &H->d_star, &H->d_tris, &H->d_mesh_k,
         &H->dl_w};

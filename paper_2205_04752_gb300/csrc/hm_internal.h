@@ -316,9 +316,11 @@ struct hm_matrix {
     hm::DevBuf Nl64, Nl32;  // near field leaf-major: FP64 form / all other forms
     hm::DevBuf SU, SV;      // per-column scales of the 16-bit forms (float, c_total)
     hm::DevBuf SW16;        // HM_I16: per-column factor of w, SU SV / 32767^2 (float, c_total)
+    hm::DevBuf fdesc16;     // HM_I16: the forward column descriptors (as fdesc, with SW16)
     hm::DevBuf Nl16;        // HM_I16: INT16 near stream (nl16_bytes)
     bool packed[HM_NFORMS] = {false, false, false, false, false};
     float wbound_su = 0.0f;  // max over factor columns of (U column scale x |s| of its block)
+    float wbound_sw16 = 0.0f;  // the same with the INT16 factor SU SV / 32767^2
     bool compacted = false;  // FP64 data released (hm_compact)
     bool aca_deferred = false;  // HM_DEFER_ACA: no ACA at assembly (adaptive product only)
     hm::DevBuf g_coll, g_tri, g_qp, g_qw, g_diam;  // cluster-order geometry of the entries (ACA on demand)

@@ -1,5 +1,5 @@
 // hm_leaf_tc.cuh -- per-leaf product for several right-hand sides with the
-// far field on the tensor cores (tcgen05), for the FP16 / BF16 forms.
+// far field on the tensor cores (tcgen05), for the FP16 / BF16 / INT16 forms.
 //
 // For a leaf tau and G <= 16 right-hand sides the far field is
 //   Y[i, (r, a)] = sum_s U[i, s] W[s, (r, a)]
@@ -8,15 +8,20 @@
 // tcgen05.mma computes D[m, i] += A[m, k] B[k, i] for M = 128, K = 16 and N =
 // the leaf's rows (rounded up to 16), accumulating in tensor memory:
 //   B = U of 16 segments, straight from the stage (the stream is stored in
-//       8 x 8 core-matrix tiles, an MN-major operand);
+//       8 x 8 core-matrix tiles, an MN-major operand).  INT16 stages (offset
+//       binary q = v + 32768) are split into two exact FP16 operands of the
+//       same layout, 256 (q / 256 - 128) in place and q mod 256 in the
+//       slot's 4-vector region (free once A is built); their MMAs accumulate
+//       into the same D;
 //   A = 128 rows (split, r, a): W scaled by a power of two t_r and split into
 //       hi = fp16(W t_r) (split 0) and lo = fp16(W t_r - hi) (split 1), so
 //       that D[(0, r, a)] + D[(1, r, a)] = t_r (U W) to about 2^-22 relative;
 //       rows of vectors r >= G are zero.  The consumer warps build it in a
 //       K-major core-matrix layout from the staged FP32 w.
 // t_r = 2^floor(log2(2^15 / (wbound x max|x_r|))): wbound bounds |w| / max|x|
-// for the mesh (|v| <= 1 after pivot normalisation, so |V^T x| <= |s| max|x|),
-// which keeps every scaled value inside the FP16 range.
+// for the mesh (|v| <= 1 after pivot normalisation, so |V^T x| <= |s| max|x|;
+// INT16: |v| <= 32767 and w carries the scales SU SV / 32767^2), which keeps
+// every scaled value inside the FP16 range.
 // One thread issues the MMAs of a stage and commits them to the barriers that
 // release the A buffer and the stage.  The near field stays on the CUDA cores
 // (as in the multi-vector kernel) and is added to the far result at the end of
@@ -38,7 +43,15 @@ constexpr int kTcK = 48;                   // segments per far stage at most (th
 constexpr int kTcABytes = 128 * kTcK * 2;  // one A tile
 constexpr int kTcSbo = (kTcK / 8) * 128;   // M-direction core stride of an A tile
 constexpr int kTcMaxG = 16;
-constexpr size_t tc_smem() { return (size_t)kTcSlots * kTcSlotBytes + 2 * (size_t)kTcABytes; }
+template <class TF>
+constexpr size_t tc_smem()
+{
+    return (size_t)kTcSlots * kTcSlotBytes + 2 * (size_t)kTcABytes;
+}
+// the low half of an INT16 far stage's split (at most a stage) fits the
+// slot's 4-vector region; an MMA of N = rows rounded up to 16 reads up to
+// 128 bytes past it, still inside shared memory (the next slot or A tiles)
+static_assert(kTcStage <= kTcAux, "the split of a far stage must fit the 4-vector region");
 static_assert(kConsumers * 8 * 3 * 4 <= kTcSlotBytes, "the near reduction must fit a slot");
 static_assert(64 * 64 * 4 <= kTcSlotBytes, "the far epilogue exchange must fit a slot");
 
@@ -115,6 +128,22 @@ __device__ __forceinline__ float tc_back<__nv_bfloat16>(unsigned short b)
     return __bfloat162float(__ushort_as_bfloat16(b));
 }
 
+// two offset-binary int16 values q (one word) -> the exact FP16 pairs
+// 256 (q / 256 - 128) (hi) and q mod 256 (lo): a byte b becomes the FP16
+// number 1024 + b by its bits 0x6400 | b, from which 1024 (or 1024 + 128) is
+// subtracted exactly
+__device__ __forceinline__ void i16_split_word(uint32_t q, uint32_t& hi, uint32_t& lo)
+{
+    const uint32_t lb = (q & 0x00ff00ffu) | 0x64006400u;
+    const uint32_t hb = ((q >> 8) & 0x00ff00ffu) | 0x64006400u;
+    __half2 l2 = *reinterpret_cast<const __half2*>(&lb);
+    __half2 h2 = *reinterpret_cast<const __half2*>(&hb);
+    l2 = __hsub2(l2, __float2half2_rn(1024.0f));
+    h2 = __hmul2(__hsub2(h2, __float2half2_rn(1152.0f)), __float2half2_rn(256.0f));
+    hi = *reinterpret_cast<const uint32_t*>(&h2);
+    lo = *reinterpret_cast<const uint32_t*>(&l2);
+}
+
 // the power-of-two scale of vector r's far-field values on a mesh
 __device__ __forceinline__ float tc_scale(float wbound, const int* xmax, int r)
 {
@@ -134,7 +163,9 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
     using TN = float;
     constexpr int Rr = 8;  // rows per consumer thread in the near field (as for 16-bit U)
     constexpr int RC = 2;
-    constexpr bool kBf16 = sizeof(TF) == 2 && !std::is_same<TF, __half>::value;
+    constexpr bool kI16 = std::is_same<TF, int16_t>::value;
+    constexpr bool kBf16 = std::is_same<TF, __nv_bfloat16>::value;
+    using TO = typename std::conditional<kBf16, __nv_bfloat16, __half>::type;  // the operand type
     extern __shared__ __align__(128) unsigned char smem[];
     auto sdata = [&](int q) { return smem + (size_t)q * kTcSlotBytes; };
     auto saux = [&](int q) { return smem + (size_t)q * kTcSlotBytes + kTcStage; };
@@ -251,9 +282,9 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
                         for (int s2 = 0; s2 < 4; ++s2) {
                             const float v0 = av[((size_t)(kb * 8 + 2 * s2) * G + r) * 4 + a] * t;
                             const float v1 = av[((size_t)(kb * 8 + 2 * s2 + 1) * G + r) * 4 + a] * t;
-                            const uint32_t h0 = tc_bits<TF>(v0), h1 = tc_bits<TF>(v1);
-                            const uint32_t l0 = tc_bits<TF>(v0 - tc_back<TF>((unsigned short)h0));
-                            const uint32_t l1 = tc_bits<TF>(v1 - tc_back<TF>((unsigned short)h1));
+                            const uint32_t h0 = tc_bits<TO>(v0), h1 = tc_bits<TO>(v1);
+                            const uint32_t l0 = tc_bits<TO>(v0 - tc_back<TO>((unsigned short)h0));
+                            const uint32_t l1 = tc_bits<TO>(v1 - tc_back<TO>((unsigned short)h1));
                             hw[s2] = h0 | (h1 << 16);
                             lw[s2] = l0 | (l1 << 16);
                         }
@@ -262,6 +293,24 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
                         make_uint4(hw[0], hw[1], hw[2], hw[3]);
                     *reinterpret_cast<uint4*>(A + (size_t)((mb + 8) * (kTcK / 8) + kb) * 128 + (4 * rr + a) * 16) =
                         make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                }
+            }
+            if constexpr (kI16) {
+                // split the stage's U: 256 x high bytes in place, the low bytes
+                // into the 4-vector region right after the stage, once every
+                // builder is done reading w from it (16-byte chunks)
+                asm volatile("bar.sync 2, %0;" ::"n"(kBuilders) : "memory");
+                uint4* Us = reinterpret_cast<uint4*>(sdata(slot));
+                const int nch = m.count * (mp >> 3);
+                for (int e = ctid; e < nch; e += kBuilders) {
+                    const uint4 v = Us[e];
+                    uint4 hv, lv;
+                    i16_split_word(v.x, hv.x, lv.x);
+                    i16_split_word(v.y, hv.y, lv.y);
+                    i16_split_word(v.z, hv.z, lv.z);
+                    i16_split_word(v.w, hv.w, lv.w);
+                    Us[e] = hv;
+                    Us[e + kTcStage / 16] = lv;
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -278,6 +327,12 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
                         const uint64_t bd = tc_desc(b0 + (uint32_t)ks * 2 * kstride + (uint32_t)(n0 >> 3) * 128,
                                                     kstride, 128);
                         tc_mma(tmem + (uint32_t)n0, ad, bd, tc_idesc(n, kBf16), (!first_far || ks > 0) ? 1u : 0u);
+                        if (kI16) {
+                            const uint64_t bl = tc_desc(b0 + kTcStage + (uint32_t)ks * 2 * kstride +
+                                                            (uint32_t)(n0 >> 3) * 128,
+                                                        kstride, 128);
+                            tc_mma(tmem + (uint32_t)n0, ad, bl, tc_idesc(n, kBf16), 1u);
+                        }
                     }
                 }
                 tc_commit(&abar[buf]);
@@ -288,7 +343,56 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
         }
         // ---- near stage on the CUDA cores (as in the multi-vector kernel)
         const TA* av = reinterpret_cast<const TA*>(saux(slot)) + (size_t)c * RC * 4;
-        if (h < H) {
+        if (kI16 && m.kind == 3 && h < H) {
+            // INT16 near columns: six FP32 scales, then six segments of int16;
+            // the scales are folded into the coefficients of x (V_aa enters y_a
+            // with (c1 + c2) x_a and the other components with c1 x_b; V_ab,
+            // a != b, enters y_a with c2 x_b and y_b with c2 x_a)
+            const unsigned char* sb3 = sdata(slot);
+            const int colB16 = kNear16Head + 12 * mp;
+            const TA c12 = c1 + c2;
+            for (int s = h; s < m.count; s += H) {
+                const unsigned char* col = sb3 + (size_t)s * colB16;
+                const float4 sa = *reinterpret_cast<const float4*>(col);       // s11 s12 s13 s22
+                const float2 sz = *reinterpret_cast<const float2*>(col + 16);  // s23 s33
+                const TA sc[6] = {sa.x, sa.y, sa.z, sa.w, sz.x, sz.y};
+                const int16_t* e0 = reinterpret_cast<const int16_t*>(col + kNear16Head) + p * Rr;
+                TA xs[RC][3];
+#pragma unroll
+                for (int q = 0; q < RC; ++q) {
+                    if (c * RC + q < G) load3(av + ((size_t)s * G + q) * 4, xs[q][0], xs[q][1], xs[q][2]);
+                    else xs[q][0] = xs[q][1] = xs[q][2] = (TA)0;
+                }
+#pragma unroll
+                for (int v = 0; v < 6; ++v) {
+                    const int va = v < 3 ? 0 : (v < 5 ? 1 : 2);
+                    const int vb = v < 3 ? v : (v < 5 ? v - 2 : 2);
+                    TA val[Rr];
+                    smem_rows<int16_t, TA, Rr>(e0 + v * mp, val);
+#pragma unroll
+                    for (int q = 0; q < RC; ++q) {
+                        if (va == vb) {
+                            const TA f0 = (va == 0 ? c12 : c1) * sc[v] * xs[q][0];
+                            const TA f1 = (va == 1 ? c12 : c1) * sc[v] * xs[q][1];
+                            const TA f2 = (va == 2 ? c12 : c1) * sc[v] * xs[q][2];
+#pragma unroll
+                            for (int e = 0; e < Rr; ++e) {
+                                acc[e][q][0] += f0 * val[e];
+                                acc[e][q][1] += f1 * val[e];
+                                acc[e][q][2] += f2 * val[e];
+                            }
+                        } else {
+                            const TA fa = c2 * sc[v] * xs[q][vb], fb = c2 * sc[v] * xs[q][va];
+#pragma unroll
+                            for (int e = 0; e < Rr; ++e) {
+                                acc[e][q][va] += fa * val[e];
+                                acc[e][q][vb] += fb * val[e];
+                            }
+                        }
+                    }
+                }
+            }
+        } else if (h < H) {
             const TN* sb = reinterpret_cast<const TN*>(sdata(slot)) + p * Rr;
             const TA c12 = c1 + c2;
             for (int s = h; s < m.count; s += H) {

@@ -124,12 +124,13 @@ struct Vec16<int16_t, TA> {
     }
 };
 
-// forms whose several-vector launches run on the tensor cores (FP16 / BF16
-// factors: tcgen05 kind::f16 operands); the INT16 form stays on the CUDA cores
+// forms whose several-vector launches run on the tensor cores (tcgen05
+// kind::f16 operands): FP16 and BF16 factors as stored, INT16 factors split
+// in shared memory into two exact FP16 operands
 template <class TF>
 constexpr bool tc_form()
 {
-    return sizeof(TF) == 2 && !std::is_same<TF, int16_t>::value;
+    return sizeof(TF) == 2;
 }
 
 // element offset of V[j, c] (c a multiple of 8 for the vector loads) in a
@@ -1055,7 +1056,9 @@ int stream_launch(StreamLaunch& out)
 template <class TF>
 constexpr bool fwd_on_tc(int G)
 {
-    return tc_form<TF>() && G >= 2;
+    // the INT16 split costs a warp's pass over every stage: below five
+    // vectors the per-vector CUDA-core kernel is faster
+    return tc_form<TF>() && G >= (std::is_same<TF, int16_t>::value ? 5 : 2);
 }
 
 // The forward pass of the 16-bit forms on the tensor cores: one persistent
@@ -1072,7 +1075,7 @@ int run_forward_tc(const Plan& P, const float* xg, float* w, float* z, int G, co
     auto kern = one ? stream::fwd_tc_kernel<TF, true> : stream::fwd_tc_kernel<TF, false>;
     int nsm = dev < kMaxDevices ? nsm_cache[dev][one] : 0;
     if (nsm == 0) {
-        HM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stream::fp_smem()));
+        HM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stream::fp_smem<TF>()));
         HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         if (dev < kMaxDevices) nsm_cache[dev][one] = nsm;
     }
@@ -1080,7 +1083,7 @@ int run_forward_tc(const Plan& P, const float* xg, float* w, float* z, int G, co
     if (G > stream::kTcMaxG) return fail(HM_EINVAL, "forward pass: %d vectors in one tensor-core launch", G);
     const MeshDev m0 = one ? P.mesh0 : MeshDev{};
     const unsigned grid = (unsigned)std::min<int64_t>(P.nunits, nsm);  // one CTA per SM (all of its TMEM)
-    kern<<<grid, stream::kFpThreads, stream::fp_smem(), s>>>(P.tcu, (int)P.nunits, m0, P.meshes, P.nmesh, xg, w, z,
+    kern<<<grid, stream::kFpThreads, stream::fp_smem<TF>(), s>>>(P.tcu, (int)P.nunits, m0, P.meshes, P.nmesh, xg, w, z,
                                                              G, xmax, P.err);
     HM_CUDA(cudaGetLastError());
     if (P.nmulti > 0) {
@@ -1146,7 +1149,7 @@ int run_forward(const Plan& P, TA* xg, TA* w, TA* z, int G, const int* xmax, cud
     if constexpr (sizeof(TF) == 2 && std::is_same<TA, float>::value) {
         // the tiles of V: one vector on the CUDA cores, several (up to 16) on
         // the tensor cores
-        if (G == 1 || !tc_form<TF>()) return run_forward_tile1<TF>(P, xg, w, z, s, sc, G);
+        if (!fwd_on_tc<TF>(G)) return run_forward_tile1<TF>(P, xg, w, z, s, sc, G);
         if constexpr (tc_form<TF>()) return run_forward_tc<TF>(P, xg, w, z, G, xmax, s);
     }
     const bool one = P.nmesh == 1;
@@ -1261,7 +1264,7 @@ int tc_launch(StreamLaunch& out)
         return HM_OK;
     }
     auto kern = stream::leaf_tc_kernel<TF>;
-    const size_t smem = stream::tc_smem();
+    const size_t smem = stream::tc_smem<TF>();
     HM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     StreamLaunch l;
     HM_CUDA(cudaDeviceGetAttribute(&l.nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -1305,7 +1308,7 @@ int run_phases_tc(const Plan& P, const double* x, double* y, int G, int64_t ld, 
         int per_sm = sc.ctas_per_sm > 0 ? std::min(sc.ctas_per_sm, 2) : 2;
         per_sm = std::min(per_sm, (int)(512 / cols));  // never wait for another CTA's columns
         const int64_t ncta = std::min<int64_t>(P.nwork, (int64_t)l.nsm * std::max(per_sm, 1));
-        stream::leaf_tc_kernel<TF><<<(unsigned)ncta, stream::kThreads, stream::tc_smem(), s>>>(
+        stream::leaf_tc_kernel<TF><<<(unsigned)ncta, stream::kThreads, stream::tc_smem<TF>(), s>>>(
             P.work, (int)P.nwork, P.meshes, counter, P.err, xg, w, G, xmax, cols, y, ld);
         HM_CUDA(cudaGetLastError());
     }
@@ -1344,8 +1347,10 @@ int run_product_t(const Plan& P, const double* x, double* y, int nrhs, int64_t l
                                              P.counters + k, s, k == 0 ? prof : nullptr, sc);
     }
     // every (row block, RHS chunk) pair of the largest leaf needs a consumer
-    // thread; at most 32 vectors keep at least 16 segments per slot
-    const int Gmax = std::min(32, RC * (stream::kConsumers / (mpmax / Rr)));
+    // thread; at most 32 vectors keep at least 16 segments per slot (16 where
+    // the forward pass takes them to the tensor cores)
+    int Gmax = std::min(32, RC * (stream::kConsumers / (mpmax / Rr)));
+    if (tc_form<TF>() && std::is_same<TA, float>::value) Gmax = std::min(Gmax, stream::kTcMaxG);
     for (; r0 < nrhs; r0 += Gmax, ++k) {
         const int G = std::min(Gmax, nrhs - r0);
         int rc = run_phases<TF, TN, TA, RC>(P, x + (size_t)r0 * ld, y + (size_t)r0 * ld, G, ld, xg, w,
@@ -1452,7 +1457,8 @@ MeshDev mesh_desc(const hm_matrix& H, int32_t form)
     m.Vr = H.Vr[form].p;
     m.Nl = form == HM_FP64 ? H.Nl64.p : H.Nl32.p;
     m.SU = (form == HM_BF16 || form == HM_FP16) ? H.SU.as<float>() : (form == HM_I16 ? H.SW16.as<float>() : nullptr);
-    m.fdesc = (form == HM_BF16 || form == HM_FP16) ? H.fdesc.as<uint2>() : nullptr;
+    m.fdesc = (form == HM_BF16 || form == HM_FP16) ? H.fdesc.as<uint2>()
+                                                   : (form == HM_I16 ? H.fdesc16.as<uint2>() : nullptr);
     m.leaf = H.d_leaf.as<int32_t>();
     m.lf_base = H.d_lf_base.as<int64_t>();
     m.lf_ptr = H.d_lf_ptr.as<int32_t>();
@@ -1475,7 +1481,8 @@ MeshDev mesh_desc(const hm_matrix& H, int32_t form)
     m.c2 = (1.0 + H.nu) / (2.0 * H.E * (1.0 - H.nu));
     // |w| <= max(c1, c2) x column scale x |s| x max|x| (|v| <= 1); rounded up
     m.wbound = (form == HM_BF16 || form == HM_FP16) ? (float)(std::max(m.c1, m.c2) * (double)H.wbound_su) * 1.0001f
-                                                    : 0.0f;
+               : form == HM_I16 ? (float)(std::max(m.c1, m.c2) * 32767.0 * (double)H.wbound_sw16) * 1.0001f
+                                : 0.0f;
     return m;
 }
 
@@ -1587,6 +1594,27 @@ size_t matvec_scratch_bytes(const hm_matrix& H, int32_t nrhs, int32_t form)
            up((size_t)kCounterInts * sizeof(int)) + up((size_t)nrhs * (size_t)std::max<int64_t>(H.zcols, 1) * 4 * ta);
 }
 
+// max over the factor columns of S[column] x |s| of the column's block (the
+// bound of |w| / max|x| of the tensor-core far field, before the coefficients)
+static int column_bound(hm_matrix& H, const float* S, float& out, cudaStream_t s)
+{
+    int rc;
+    DevBuf wb;
+    if ((rc = dalloc(H, wb, 256))) return rc;
+    HM_CUDA(cudaMemsetAsync(wb.p, 0, 4, s));
+    const int64_t nrec = (int64_t)H.fwd_h.size();
+    if (nrec > 0) {
+        wbound_kernel<<<256, 256, 0, s>>>(H.d_fwd_all.as<FwdRec>(), nrec, S, wb.as<int>());
+        HM_CUDA(cudaGetLastError());
+    }
+    int bits = 0;
+    HM_CUDA(cudaMemcpyAsync(&bits, wb.p, 4, cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaStreamSynchronize(s));
+    H.alloc.release(wb.p, wb.bytes);
+    std::memcpy(&out, &bits, 4);
+    return HM_OK;
+}
+
 // the streaming layouts of one form (and the FP32 near field and the column
 // scales it shares with the other reduced forms), then the form's mesh table
 int pack_device(hm_matrix& H, int32_t form, cudaStream_t s)
@@ -1629,6 +1657,24 @@ int pack_device(hm_matrix& H, int32_t form, cudaStream_t s)
                 }
             }
             if ((rc = pack_form<int16_t>(H, HM_I16, H.SU.as<float>(), H.SV.as<float>(), s))) return rc;
+            if (H.wbound_sw16 == 0.0f)
+                if ((rc = column_bound(H, H.SW16.as<float>(), H.wbound_sw16, s))) return rc;
+            // the column descriptors of the tensor-core forward pass, with
+            // c1 or c2 times the column's SU SV / 32767^2
+            if (!H.fdesc16.p) {
+                if (H.c_total > kFdMaxCol)
+                    return fail(HM_EINVAL, "16-bit forms: more than %lld factor columns", (long long)kFdMaxCol);
+                if ((rc = dalloc(H, H.fdesc16, (size_t)std::max<int64_t>(H.dcols, 1) * sizeof(uint2)))) return rc;
+                const int64_t nrec = (int64_t)H.fwd_h.size();
+                if (nrec > 0) {
+                    const MeshDev m = mesh_desc(H, HM_FP64);
+                    fdesc_kernel<<<(unsigned)((nrec + 7) / 8), 256, 0, s>>>(H.d_fwd_all.as<FwdRec>(), nrec,
+                                                                            H.d_groups.as<FwdGroup>(),
+                                                                            H.SW16.as<float>(), (float)m.c1,
+                                                                            (float)m.c2, H.fdesc16.as<uint2>());
+                    HM_CUDA(cudaGetLastError());
+                }
+            }
             if (!H.Nl16.p) {
                 if ((rc = dalloc(H, H.Nl16, (size_t)std::max<int64_t>(H.nl16_bytes, 16)))) return rc;
                 if (H.nleaves > 0) {
@@ -1656,23 +1702,8 @@ int pack_device(hm_matrix& H, int32_t form, cudaStream_t s)
                 HM_CUDA(cudaGetLastError());
             }
         }
-        if (H.wbound_su == 0.0f) {
-            DevBuf wb;
-            if ((rc = dalloc(H, wb, 256))) return rc;
-            HM_CUDA(cudaMemsetAsync(wb.p, 0, 4, s));
-            const int64_t nrec = (int64_t)H.fwd_h.size();
-            if (nrec > 0) {
-                wbound_kernel<<<256, 256, 0, s>>>(H.d_fwd_all.as<FwdRec>(), nrec, H.SU.as<float>(), wb.as<int>());
-                HM_CUDA(cudaGetLastError());
-            }
-            int bits = 0;
-            HM_CUDA(cudaMemcpyAsync(&bits, wb.p, 4, cudaMemcpyDeviceToHost, s));
-            HM_CUDA(cudaStreamSynchronize(s));
-            H.alloc.release(wb.p, wb.bytes);
-            float f;
-            std::memcpy(&f, &bits, 4);
-            H.wbound_su = f;
-        }
+        if (H.wbound_su == 0.0f)
+            if ((rc = column_bound(H, H.SU.as<float>(), H.wbound_su, s))) return rc;
         // V columns are normalised by their ACA pivot (max |v| = 1), so V is
         // stored without a scale; U carries the magnitudes and gets one scale
         // per column
