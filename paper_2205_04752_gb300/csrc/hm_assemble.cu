@@ -1745,7 +1745,8 @@ int assemble_device(const hm_tree& tr, hm_matrix& H)
             const int32_t nch = (g.n + kFwdUnitRows - 1) / kFwdUnitRows;
             const int64_t z0 = nch > 1 ? zc : -1;
             if (nch > 1) {
-                multi.push_back(FwdMulti{(int32_t)gi, nch, zc});
+                for (int32_t c0 = 0; c0 < g.Cs; c0 += kReduceCols)
+                    multi.push_back(FwdMulti{(int32_t)gi, nch, zc, c0, std::min(kReduceCols, g.Cs - c0)});
                 zc += (int64_t)nch * g.Cs;
             }
             for (int32_t k = 0; k < nch; ++k)

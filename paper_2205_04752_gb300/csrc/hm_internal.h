@@ -150,11 +150,14 @@ struct FwdUnit {
     int32_t c0, ncols;  // the unit's columns of the group (at most kFwdUnitCols)
     int64_t zcol0;
 };
-// the groups with several units: group, units, first z column
+// the second pass of the groups with several units, in column chunks (one
+// CTA each): group, units, first z column of the group, the chunk's columns
 struct FwdMulti {
     int32_t group, nchunk;
     int64_t zcol0;
+    int32_t c0, ncols;
 };
+constexpr int kReduceCols = 128;  // columns of a second-pass chunk
 constexpr int kFwdUnitRows = 256;
 constexpr int kFwdUnitCols = 256;
 // a unit as the tensor-core forward pass reads it: one load, no dependent

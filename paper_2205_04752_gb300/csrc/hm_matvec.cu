@@ -728,7 +728,8 @@ __global__ void __launch_bounds__(kThreads) fwd_big_multi_kernel(
 }
 
 // Second pass for the groups taller than one unit: z of every (column,
-// vector) as the sum of the units' partial sums in chunk order, then w.
+// vector) as the sum of the units' partial sums in chunk order, then w; one
+// CTA per chunk of kReduceCols columns of a group.
 template <class TA, bool ONE>
 __global__ void __launch_bounds__(kFwdThreads) fwd_reduce_kernel(
     const FwdMulti* __restrict__ multi, const FwdGroup* __restrict__ groups, const FwdRec* __restrict__ recs,
@@ -744,8 +745,8 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_reduce_kernel(
     TA* wr = w + (size_t)md.woff * G * 4;
     const TA c1 = (TA)md.c1, c2 = (TA)md.c2;
     const int Cs = gp.Cs;
-    for (int idx = threadIdx.x; idx < Cs * G; idx += blockDim.x) {
-        const int col = idx / G, r = idx - col * G;
+    for (int idx = threadIdx.x; idx < mu.ncols * G; idx += blockDim.x) {
+        const int col = mu.c0 + idx / G, r = idx % G;
         int lo = 0, hi = gp.nrec - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
