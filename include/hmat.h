@@ -386,7 +386,9 @@ void hm_batch_destroy(hm_batch* B);
  * own streams, so their kernels overlap on the device while later arrivals
  * keep being admitted.  Requests of one kind are admitted in arrival order;
  * a solve that waits for one of its solve_slots does not hold back the
- * matvec requests behind it.  Arrivals that find queue_cap requests waiting,
+ * matvec requests behind it, and matvec requests run on streams of the
+ * device's greatest priority (solves on its least), so that their kernels'
+ * CTAs are started first.  Arrivals that find queue_cap requests waiting,
  * or whose footprint exceeds the arena, are rejected (HM_EBUSY).
  * Every request runs the kernels it would run alone, with its own
  * workspace: its result is bitwise the same alone and in any mix.

@@ -3,7 +3,8 @@
 // Matvec and solve requests on any of the server's matrices arrive over time
 // (a trace replayed in real time, or all at once).  A scheduler thread admits
 // them in arrival order as soon as a slot (worker thread with its own CUDA
-// stream) and enough device memory are free: every request's device
+// streams: matvec requests at the greatest stream priority, solves at the
+// least) and enough device memory are free: every request's device
 // footprint -- its vectors, the product workspace and, for a solve, the
 // Krylov basis -- is carved out of one arena of fixed size by a first-fit
 // allocator, so admission is by footprint.  Admitted requests run
@@ -209,8 +210,15 @@ struct Run {
     void worker(int w)
     {
         cudaSetDevice(S.device);
-        cudaStream_t s = nullptr;
-        const bool have_stream = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+        // two streams per worker: matvec requests on the device's greatest
+        // stream priority, solves on its least, so that the block scheduler
+        // starts a matvec's CTAs ahead of those of solves that overlap it (the
+        // kernels and their results are the same on either stream)
+        int least = 0, greatest = 0;
+        cudaStream_t s_mv = nullptr, s_sv = nullptr;
+        bool have_stream = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess;
+        have_stream = have_stream && cudaStreamCreateWithPriority(&s_mv, cudaStreamNonBlocking, greatest) == cudaSuccess;
+        have_stream = have_stream && cudaStreamCreateWithPriority(&s_sv, cudaStreamNonBlocking, least) == cudaSuccess;
         for (;;) {
             int idx;
             size_t off;
@@ -222,6 +230,7 @@ struct Run {
                 off = slots[(size_t)w].off;
             }
             hm_result r{};
+            cudaStream_t s = reqs[idx].kind == HM_REQ_MATVEC ? s_mv : s_sv;
             const int rc = have_stream ? execute(idx, off, s, r) : fail(HM_EDEVICE, "hm_server: no stream");
             const double t = now();
             {
@@ -235,7 +244,8 @@ struct Run {
             }
             cv_sched.notify_one();
         }
-        if (s) cudaStreamDestroy(s);
+        if (s_mv) cudaStreamDestroy(s_mv);
+        if (s_sv) cudaStreamDestroy(s_sv);
     }
 };
 
