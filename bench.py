@@ -823,8 +823,8 @@ def bench_serving(args):
     rates, 80% matvec (1-32 vectors, INT16 form, within 1e-4 of the FP64
     form) / 20% solve (tol 1e-6, GMRES on FP16 with FP32-residual
     refinement), mesh uniform over the pool; 8 slots of which solves may take
-    4, so that matvec requests always find a lane.  Latency percentiles per
-    request kind."""
+    --serve-solve-slots, so that matvec requests always find a lane.  Latency
+    percentiles per request kind."""
     import torch
     from paper_2205_04752_gb300 import binding, inputs
     meshes = [(inputs.icosphere(l), 64, 0.3) for l in (3, 4, 5, 6)]
@@ -843,11 +843,11 @@ def bench_serving(args):
     torch.cuda.synchronize()
     t_asm = time.perf_counter() - t0
     srv = binding.Server(mats, slots=8, queue_cap=256, budget_bytes=24 << 30, matvec_form="i16",
-                         inner_form="fp16", residual_form="fp32", restart=30, solve_slots=4)
+                         inner_form="fp16", residual_form="fp32", restart=30, solve_slots=args.serve_solve_slots)
     out = {"workload": "16 resident meshes (icosphere L3-L6, 12 ellipsoids 1k-200k triangles), "
                        "Poisson arrivals, 80% matvec (1-32 RHS, i16) / 20% solve (tol 1e-6)",
            "triangles": tri, "assemble_s": round(t_asm, 2), "resident_gb": round(resident / 1e9, 2),
-           "slots": 8, "solve_slots": 4, "budget_gb": 24, "rates": []}
+           "slots": 8, "solve_slots": args.serve_solve_slots, "budget_gb": 24, "rates": []}
     # warm the kernels of every form once
     srv.run([dict(mesh=m, kind="matvec", nrhs=1, seed=m) for m in range(len(mats))], realtime=False)
     rng = np.random.default_rng(5)
@@ -905,6 +905,8 @@ def main():
     ap.add_argument("--no-points", action="store_true",
                     help="skip the evaluation operator (displacement at 65,536 interior points)")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[10.0, 30.0, 100.0, 300.0, 1000.0])
+    ap.add_argument("--serve-solve-slots", type=int, default=2,
+                    help="of the 8 request slots, how many solves may hold at once")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
     ap.add_argument("--minimal", action="store_true",
                     help="profiling runs: assemble, pack and time the headline product only "
