@@ -33,9 +33,10 @@
 //               of slots (bulk copies);
 //   warps 2-5   build the A tiles from the gathered x into a second ring, a
 //               stage each round-robin, ahead of the V stream;
-//   warp 14     INT16 form: splits every stage's V once it has landed, in
-//               stage order (256 x high bytes in place, the low bytes into a
-//               ring of two buffers that the MMA commits release);
+//   warps 14-15 INT16 form: split every stage's V once it has landed, in
+//               stage order, each half of its 16-byte chunks (256 x high bytes
+//               in place, the low bytes into a ring of two buffers that the
+//               MMA commits release);
 //   warp 1      one thread issues the MMAs of a stage and commits them to the
 //               release barriers of its V and A slots, and after a unit's last
 //               stage to its accumulator barrier; two accumulators (2 x 256
@@ -57,7 +58,7 @@
 namespace hm {
 namespace stream {
 
-constexpr int kFpThreads = 480;
+constexpr int kFpThreads = 512;
 constexpr int kFpRows = 32;                          // rows (K) per stage: two MMA K steps
 constexpr int kFpCols = 256;                         // columns per unit at most (one N tile)
 constexpr int kFpVBytes = kFpRows * kFpCols * 2;     // V of a stage
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
     if (tid == 0) {
         for (int s = 0; s < VS; ++s) {
             mbar_init(&vfull[s], 1);
-            mbar_init(&vconv[s], 1);
+            mbar_init(&vconv[s], 2);  // one arrival per converter warp
             mbar_init(&vempty[s], 1);
         }
         for (int s = 0; s < LS; ++s) mbar_init(&lempty[s], 1);
@@ -390,10 +391,12 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
                 if (lane == 0) mbar_arrive(&afull[as]);
             }
         }
-    } else if (warp == 14) {
+    } else if (warp >= 14) {
         // ---- INT16: split every stage's V in stage order once it has landed
         // (and its low-byte buffer is free): 256 x high bytes in place, the
-        // low bytes into the buffer
+        // low bytes into the buffer; warp 14 + h takes the groups of 32
+        // 16-byte chunks h, h + 2, h + 4, ...
+        const int cw = warp - 14;
         if constexpr (kI16) {
             int it = 0;
             bool run = true;
@@ -416,7 +419,7 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
                     uint4* L = reinterpret_cast<uint4*>(slot_l(ls));
                     const int nkr = min(kFpRows / 8, (n16 >> 3) - q * (kFpRows / 8));
                     const int nch = nkr * un.ncols;  // 16-byte chunks of the stage
-                    for (int e = lane; e < nch; e += 32) {
+                    for (int e = 32 * cw + lane; e < nch; e += 64) {
                         const uint4 v = V[e];
                         uint4 h, l;
                         i16_split_word(v.x, h.x, l.x);

@@ -303,13 +303,17 @@ __device__ __forceinline__ void smem_rows(const T* p, TA* o)
 // A finished leaf is reduced inside the slot of its last stage (released
 // afterwards): the single-vector kernel one output component at a time, the
 // multi-vector kernel one RHS-chunk position at a time.  The single-vector
-// kernel keeps 5 slots of 20 KB, the multi-vector kernel 3 of 48 KB: two CTAs
-// per SM either way, and ten 16 KB stages in flight per SM for one vector
-// (the copy pipeline, not the arithmetic, bounds that kernel).
+// kernel keeps 3 slots of 20 KB (24 KB in FP64) at three CTAs per SM (at
+// most 85 registers a thread): nine 16 KB stages in flight per SM and 21
+// consumer warps, which measured 11% faster at level 6 (INT16) than 5 slots
+// at two CTAs per SM -- the kernel issues about half of the SM's instruction
+// slots, and the extra warps hide latency.  The multi-vector kernels keep 3
+// slots of 48 KB at two CTAs per SM.
 template <class TF, class TA, int RC>
 struct LeafCfg {
     static constexpr int Rr = Smem16<TF, TA>::N;
-    static constexpr int kS = RC == 1 ? 5 : 3;
+    static constexpr int kMinCtas = RC == 1 ? 3 : 1;  // CTAs per SM the registers must allow
+    static constexpr int kS = 3;
     static constexpr int kAuxBytes = RC == 1 ? kMaxSeg * 4 * (int)sizeof(TA) : 16384;
     static constexpr int kSlotBytes = kStageBytes + kAuxBytes;
     static_assert(kS <= kStages, "the barrier arrays hold kStages slots");
@@ -557,7 +561,7 @@ __device__ __forceinline__ void leaf_producer(const int2* __restrict__ work, int
 }
 
 template <class TF, class TN, class TA, int RC>
-__global__ void __launch_bounds__(kThreads) leaf_stream_kernel(
+__global__ void __launch_bounds__(kThreads, LeafCfg<TF, TA, RC>::kMinCtas) leaf_stream_kernel(
     const int2* __restrict__ work, int nwork, const MeshDev* __restrict__ meshes, int* __restrict__ counter,
     int* __restrict__ err, const TA* __restrict__ xg_base, const TA* __restrict__ w_base, int G,
     double* __restrict__ y, int64_t ld)
