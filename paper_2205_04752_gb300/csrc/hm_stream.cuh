@@ -307,12 +307,14 @@ __device__ __forceinline__ void smem_rows(const T* p, TA* o)
 // most 85 registers a thread): nine 16 KB stages in flight per SM and 21
 // consumer warps, which measured 11% faster at level 6 (INT16) than 5 slots
 // at two CTAs per SM -- the kernel issues about half of the SM's instruction
-// slots, and the extra warps hide latency.  The multi-vector kernels keep 3
-// slots of 48 KB at two CTAs per SM.
+// slots, and the extra warps hide latency (four CTAs of 2 slots, at 64
+// registers, were no faster).  The multi-vector kernels keep 3 slots of
+// 32 KB at two CTAs per SM (at most 128 registers; at one CTA per SM the
+// 4-vector leaf product took 2.52 ms at level 6 against 1.85 ms).
 template <class TF, class TA, int RC>
 struct LeafCfg {
     static constexpr int Rr = Smem16<TF, TA>::N;
-    static constexpr int kMinCtas = RC == 1 ? 3 : 1;  // CTAs per SM the registers must allow
+    static constexpr int kMinCtas = RC == 1 ? 3 : 2;  // CTAs per SM the registers must allow
     static constexpr int kS = 3;
     static constexpr int kAuxBytes = RC == 1 ? kMaxSeg * 4 * (int)sizeof(TA) : 16384;
     static constexpr int kSlotBytes = kStageBytes + kAuxBytes;
