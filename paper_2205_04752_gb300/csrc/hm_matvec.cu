@@ -1250,7 +1250,9 @@ int run_phases(const Plan& P, const double* x, double* y, int G, int64_t ld, TA*
 }
 
 // fewest vectors of a launch that takes the far field to the tensor cores
-constexpr int kTcMinG = 12;
+// (level 6: at 12 vectors the CUDA-core kernel is faster, at 16 the
+// tensor-core one; the two meet near 14 in both 16-bit forms)
+constexpr int kTcMinG = 14;
 
 // per-device launch data of the tensor-core leaf kernel
 template <class TF>

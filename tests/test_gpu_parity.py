@@ -157,7 +157,7 @@ def test_multi_rhs_launches_match_single_vector_products(form):
                                        ("i16", 16), ("i16", 6)])
 def test_tensor_core_far_field_scales_exactly(form, nrhs):
     """The tensor-core forward pass (2-16 vectors; INT16 V split into two
-    exact FP16 operands) and far field (12-16) scale x and W by a power of
+    exact FP16 operands) and far field (14-16) scale x and W by a power of
     two chosen from max|x| of each vector:
     scaling x by 2^40 or 2^-40 scales y exactly, a zero vector gives zero,
     and vectors of very different size share a launch.  3, 6 and 11 vectors
