@@ -22,8 +22,12 @@
 // for the mesh (|v| <= 1 after pivot normalisation, so |V^T x| <= |s| max|x|;
 // INT16: |v| <= 32767 and w carries the scales SU SV / 32767^2), which keeps
 // every scaled value inside the FP16 range.
-// One thread issues the MMAs of a stage and commits them to the barriers that
-// release the A buffer and the stage.  The near field stays on the CUDA cores
+// The three builder warps take the far stages round-robin, each into its own
+// A buffer, so that the builds of consecutive stages overlap.  One thread
+// (lane 0 of warp 1) issues every stage's MMAs in stage order, once its
+// builder has announced the A tile, and commits them to the barriers that
+// release the builder's A buffer and the stage (one issuing thread: the
+// accumulation order is fixed, and every commit tracks all far MMAs).  The near field stays on the CUDA cores
 // (as in the multi-vector kernel) and is added to the far result at the end of
 // the leaf, in a fixed order.  Every wait is bounded.
 #pragma once
@@ -43,11 +47,13 @@ constexpr int kTcK = 48;                   // segments per far stage at most (th
 constexpr int kTcABytes = 128 * kTcK * 2;  // one A tile
 constexpr int kTcSbo = (kTcK / 8) * 128;   // M-direction core stride of an A tile
 constexpr int kTcMaxG = 16;
+constexpr int kTcBuildW = 3;  // builder warps, one A buffer each
 template <class TF>
 constexpr size_t tc_smem()
 {
-    return (size_t)kTcSlots * kTcSlotBytes + 2 * (size_t)kTcABytes;
+    return (size_t)kTcSlots * kTcSlotBytes + kTcBuildW * (size_t)kTcABytes;
 }
+
 // the low half of an INT16 far stage's split (at most a stage) fits the
 // slot's 4-vector region; an MMA of N = rows rounded up to 16 reads up to
 // 128 bytes past it, still inside shared memory (the next slot or A tiles)
@@ -169,13 +175,14 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
     extern __shared__ __align__(128) unsigned char smem[];
     auto sdata = [&](int q) { return smem + (size_t)q * kTcSlotBytes; };
     auto saux = [&](int q) { return smem + (size_t)q * kTcSlotBytes + kTcStage; };
-    unsigned char* abuf = smem + (size_t)kTcSlots * kTcSlotBytes;  // two A tiles
+    unsigned char* abuf = smem + (size_t)kTcSlots * kTcSlotBytes;  // one A tile per builder warp
     __shared__ __align__(8) uint64_t full[kTcSlots];
     __shared__ __align__(8) uint64_t empty[kTcSlots];      // near stages: one arrival per consumer warp
     __shared__ __align__(8) uint64_t empty_far[kTcSlots];  // far stages: the MMA commit
-    __shared__ __align__(8) uint64_t abar[2];
-    __shared__ __align__(8) uint64_t dbar;
-    __shared__ __align__(8) uint64_t fbar;
+    __shared__ __align__(8) uint64_t afull[kTcBuildW];     // a builder's A tile is built
+    __shared__ __align__(8) uint64_t aempty[kTcBuildW];    // a builder's A tile is read by its MMAs
+    __shared__ __align__(8) uint64_t dbar;                 // a leaf's far MMAs are done
+    __shared__ __align__(8) uint64_t fbar;                 // drain
     __shared__ StageMeta meta[kTcSlots];
     __shared__ uint32_t tmem_slot;
 
@@ -186,8 +193,10 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
             mbar_init(&empty[s], kConsumers / 32);
             mbar_init(&empty_far[s], 1);
         }
-        mbar_init(&abar[0], 1);
-        mbar_init(&abar[1], 1);
+        for (int b = 0; b < kTcBuildW; ++b) {
+            mbar_init(&afull[b], 1);
+            mbar_init(&aempty[b], 1);
+        }
         mbar_init(&dbar, 1);
         mbar_init(&fbar, 1);
         mbar_fence_init();
@@ -211,19 +220,19 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
     }
 
     // ---------------------------------------------------------------- consumers
-    // warps 1..3 build the A tiles of the far stages and thread 0 of warp 1
-    // issues the MMAs; warps 4..7 go on to the near stages meanwhile and read
-    // the accumulators (TMEM lane quarters 0..3) in the epilogue
-    constexpr int kBuilders = 96;
+    // warps 2..4 build the A tiles of the far stages (far stage f by warp
+    // 2 + f mod 3), lane 0 of warp 1 issues the MMAs; the other warps go on to
+    // the near stages meanwhile, and warps 4..7 read the accumulators (TMEM
+    // lane quarters 0..3) in the epilogue
     const int ctid = threadIdx.x - 32;
-    const bool builder = ctid < kBuilders;
+    const bool builder = warp >= 2 && warp < 2 + kTcBuildW;
     const int NRC = (G + RC - 1) / RC;
     int cur = -1, cur_mesh = -1, P = 1, H = 0, p = 0, c = 0, h = 0, t0 = 0, mt = 0, mp = 8, mp16 = 16;
     const int32_t* perm = nullptr;
     int64_t xoff = 0;
     TA c1 = 0.f, c2 = 0.f;
     float wbound = 0.f;
-    int fs = 0;   // far stages seen (A buffer, phase of its barrier)
+    int fs = 0;   // far stages seen (the builder, the use of its A tile, the MMA turn)
     int nfl = 0;  // leaves with a far field finished (phase of dbar)
     bool far_started = false;
     TA acc[Rr][RC][3];
@@ -258,18 +267,54 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
         }
         if (m.kind == 0) {
             // ---- far stage on the tensor cores
-            const int buf = fs & 1;
+            const int f = fs++;
             const bool first_far = !far_started;
             far_started = true;
-            ++fs;
-            if (!builder) continue;
-            if (fs > 2 && !mbar_wait(&abar[buf], (uint32_t)(((fs - 1) >> 1) - 1) & 1u, err, 4, it)) break;
-            unsigned char* A = abuf + (size_t)buf * kTcABytes;
+            const int own = f % kTcBuildW;  // its builder: warp 2 + own
+            const int use = f / kTcBuildW;  // that builder's use of its A tile
+            unsigned char* A = abuf + (size_t)own * kTcABytes;
+            if (warp == 1) {
+                // the issuer: the stage's MMAs once its A tile is built
+                int ok = 1;
+                if (lane == 0) {
+                    ok = mbar_wait(&afull[own], (uint32_t)use & 1u, err, 4, it) ? 1 : 0;
+                    if (ok) {
+                        tc_fence_after();
+                        const uint32_t a0 = smem_addr(A), b0 = smem_addr(sdata(slot));
+                        const uint32_t kstride = (uint32_t)(mp >> 3) * 128;  // K-direction core stride of U
+                        for (int ks = 0; ks < (m.count >> 4); ++ks) {
+                            for (int n0 = 0; n0 < mp16; n0 += 256) {
+                                const int n = min(256, mp16 - n0);
+                                const uint64_t ad = tc_desc(a0 + (uint32_t)ks * 256, 128, kTcSbo);
+                                const uint64_t bd = tc_desc(b0 + (uint32_t)ks * 2 * kstride + (uint32_t)(n0 >> 3) * 128,
+                                                            kstride, 128);
+                                tc_mma(tmem + (uint32_t)n0, ad, bd, tc_idesc(n, kBf16),
+                                       (!first_far || ks > 0) ? 1u : 0u);
+                                if (kI16) {
+                                    const uint64_t bl = tc_desc(b0 + kTcStage + (uint32_t)ks * 2 * kstride +
+                                                                    (uint32_t)(n0 >> 3) * 128,
+                                                                kstride, 128);
+                                    tc_mma(tmem + (uint32_t)n0, ad, bl, tc_idesc(n, kBf16), 1u);
+                                }
+                            }
+                        }
+                        tc_commit(&aempty[own]);
+                        tc_commit(&empty_far[slot]);
+                        if (m.pad[1]) tc_commit(&dbar);
+                    }
+                }
+                if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+                continue;
+            }
+            if (!builder || warp - 2 != own) continue;
+            // the builder of this stage: its A tile is free once the MMAs of its
+            // previous use are done
+            if (use > 0 && !mbar_wait(&aempty[own], (uint32_t)(use - 1) & 1u, err, 8, it)) break;
             const float* av = reinterpret_cast<const float*>(saux(slot));
             const int nkb = m.count >> 3;  // core columns of this stage
             // item (mb, kb, rr): vector r = 2 mb + rr, rows 8 mb + 4 rr + a (hi)
             // and 64 + 8 mb + 4 rr + a (lo), segments 8 kb .. 8 kb + 7
-            for (int itm = ctid; itm < 16 * nkb; itm += kBuilders) {
+            for (int itm = lane; itm < 16 * nkb; itm += 32) {
                 const int rr = itm & 1, mb = (itm >> 1) & 7, kb = itm >> 4;
                 const int r = 2 * mb + rr;
                 const float t = r < G ? tc_scale(wbound, xmax, r) : 0.0f;
@@ -297,12 +342,12 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
             }
             if constexpr (kI16) {
                 // split the stage's U: 256 x high bytes in place, the low bytes
-                // into the 4-vector region right after the stage, once every
-                // builder is done reading w from it (16-byte chunks)
-                asm volatile("bar.sync 2, %0;" ::"n"(kBuilders) : "memory");
+                // into the 4-vector region right after the stage, once the warp
+                // is done reading w from it (16-byte chunks)
+                __syncwarp();
                 uint4* Us = reinterpret_cast<uint4*>(sdata(slot));
                 const int nch = m.count * (mp >> 3);
-                for (int e = ctid; e < nch; e += kBuilders) {
+                for (int e = lane; e < nch; e += 32) {
                     const uint4 v = Us[e];
                     uint4 hv, lv;
                     i16_split_word(v.x, hv.x, lv.x);
@@ -315,30 +360,8 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             tc_fence_before();
-            asm volatile("bar.sync 2, %0;" ::"n"(kBuilders) : "memory");
-            if (ctid == 0) {
-                tc_fence_after();
-                const uint32_t a0 = smem_addr(A), b0 = smem_addr(sdata(slot));
-                const uint32_t kstride = (uint32_t)(mp >> 3) * 128;  // K-direction core stride of U
-                for (int ks = 0; ks < (m.count >> 4); ++ks) {
-                    for (int n0 = 0; n0 < mp16; n0 += 256) {
-                        const int n = min(256, mp16 - n0);
-                        const uint64_t ad = tc_desc(a0 + (uint32_t)ks * 256, 128, kTcSbo);
-                        const uint64_t bd = tc_desc(b0 + (uint32_t)ks * 2 * kstride + (uint32_t)(n0 >> 3) * 128,
-                                                    kstride, 128);
-                        tc_mma(tmem + (uint32_t)n0, ad, bd, tc_idesc(n, kBf16), (!first_far || ks > 0) ? 1u : 0u);
-                        if (kI16) {
-                            const uint64_t bl = tc_desc(b0 + kTcStage + (uint32_t)ks * 2 * kstride +
-                                                            (uint32_t)(n0 >> 3) * 128,
-                                                        kstride, 128);
-                            tc_mma(tmem + (uint32_t)n0, ad, bl, tc_idesc(n, kBf16), 1u);
-                        }
-                    }
-                }
-                tc_commit(&abar[buf]);
-                tc_commit(&empty_far[slot]);
-                if (m.pad[1]) tc_commit(&dbar);
-            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&afull[own]);
             continue;
         }
         // ---- near stage on the CUDA cores (as in the multi-vector kernel)
