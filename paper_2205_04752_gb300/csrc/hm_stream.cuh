@@ -6,7 +6,7 @@
 // (see hm_matvec.cu).  A persistent CTA takes (mesh, leaf) work items from a
 // global counter (largest first, over every mesh of the product).  Warp 0 is
 // the producer: for every slot of a ring of kStages shared-memory slots it
-// copies up to kStageBytes of the current leaf's stream and, next to it, the
+// copies up to kStage bytes of the current leaf's stream and, next to it, the
 // 4-vector each segment needs: w of the
 // segment's factor column (far field) or x at the segment's source position
 // (near field).  Consecutive segments of one (block, kernel) item have
@@ -37,7 +37,7 @@ namespace stream {
 constexpr int kThreads = 256;             // warp 0 producer + 7 consumer warps
 constexpr int kConsumers = kThreads - 32;
 constexpr int kStages = 5;
-constexpr int kStageBytes = 16384;
+constexpr int kStageBytes = 16384;        // stream bytes of a slot at least (LeafCfg::kStage)
 constexpr int kMaxSeg = 256;              // segments / columns per stage at most
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
@@ -299,25 +299,30 @@ __device__ __forceinline__ void smem_rows(const T* p, TA* o)
 // interleaved, 4-vector (position or column, r) at index pos * G + r).  A
 // consumer thread holds Rr rows (16 bytes of U) for RC right-hand sides.
 // RC = 1 is the single-vector kernel; RC * Rr = 16 otherwise.
-// A slot is kStageBytes of stream data followed by kAuxBytes of staged 4-vectors.
+// A slot is kStage bytes of stream data followed by kAuxBytes of staged 4-vectors.
 // A finished leaf is reduced inside the slot of its last stage (released
 // afterwards): the single-vector kernel one output component at a time, the
 // multi-vector kernel one RHS-chunk position at a time.  The single-vector
-// kernel keeps 3 slots of 20 KB (24 KB in FP64) at three CTAs per SM (at
-// most 85 registers a thread): nine 16 KB stages in flight per SM and 21
-// consumer warps, which measured 11% faster at level 6 (INT16) than 5 slots
-// at two CTAs per SM -- the kernel issues about half of the SM's instruction
-// slots, and the extra warps hide latency (four CTAs of 2 slots, at 64
-// registers, were no faster).  The multi-vector kernels keep 3 slots of
-// 32 KB at two CTAs per SM (at most 128 registers; at one CTA per SM the
-// 4-vector leaf product took 2.52 ms at level 6 against 1.85 ms).
+// kernel keeps 3 slots of 20 KB stages (16 KB in FP64, whose 4-vectors take
+// twice the room) at three CTAs per SM (at most 85 registers a thread): nine
+// stages in flight per SM and 21 consumer warps.  Measured at level 6
+// (INT16): 5 slots of 16 KB at two CTAs per SM 0.887 ms, 3 of 16 KB at three
+// CTAs 0.793 ms, 3 of 20 KB 0.708 ms -- the kernel issues about half of the
+// SM's instruction slots, and the extra warps and longer stages hide latency
+// (four CTAs of 2 slots, at 64 registers, were no faster; 6 slots of 12 KB
+// at two CTAs took 1.15 ms).  The multi-vector kernels keep 3 slots of 20 KB
+// stages and 16 KB of 4-vectors at two CTAs per SM (at most 128 registers;
+// at one CTA per SM the 4-vector leaf product took 2.52 ms at level 6
+// against 1.85 ms).
 template <class TF, class TA, int RC>
 struct LeafCfg {
     static constexpr int Rr = Smem16<TF, TA>::N;
     static constexpr int kMinCtas = RC == 1 ? 3 : 2;  // CTAs per SM the registers must allow
     static constexpr int kS = 3;
+    static constexpr int kStage = (RC == 1 && sizeof(TA) == 8) ? kStageBytes : 20480;
+    static_assert(kStage >= kStageBytes, "the host admits leaves by the smallest stage");
     static constexpr int kAuxBytes = RC == 1 ? kMaxSeg * 4 * (int)sizeof(TA) : 16384;
-    static constexpr int kSlotBytes = kStageBytes + kAuxBytes;
+    static constexpr int kSlotBytes = kStage + kAuxBytes;
     static_assert(kS <= kStages, "the barrier arrays hold kStages slots");
     static_assert(kConsumers * Rr * (RC == 1 ? 1 : 3) * (int)sizeof(TA) <= kSlotBytes,
                   "one pass of the leaf reduction must fit a slot");
@@ -572,9 +577,9 @@ __global__ void __launch_bounds__(kThreads, LeafCfg<TF, TA, RC>::kMinCtas) leaf_
     constexpr int Rr = Cfg::Rr;
     constexpr int NS = Cfg::kS;
     extern __shared__ __align__(128) unsigned char smem[];
-    // slot q: stream data at smem + q * kSlotBytes, its 4-vectors kStageBytes later
+    // slot q: stream data at smem + q * kSlotBytes, its 4-vectors kStage bytes later
     auto sdata = [&](int q) { return smem + (size_t)q * Cfg::kSlotBytes; };
-    auto saux = [&](int q) { return smem + (size_t)q * Cfg::kSlotBytes + kStageBytes; };
+    auto saux = [&](int q) { return smem + (size_t)q * Cfg::kSlotBytes + Cfg::kStage; };
     __shared__ __align__(8) uint64_t full[kStages];
     __shared__ __align__(8) uint64_t empty[kStages];
     __shared__ StageMeta meta[kStages];
@@ -590,7 +595,7 @@ __global__ void __launch_bounds__(kThreads, LeafCfg<TF, TA, RC>::kMinCtas) leaf_
     __syncthreads();
 
     if (warp == 0) {
-        leaf_producer<TF, TN, TA, NS, kStageBytes, Cfg::kAuxBytes, RC == 1 ? 8 : 16>(
+        leaf_producer<TF, TN, TA, NS, Cfg::kStage, Cfg::kAuxBytes, RC == 1 ? 8 : 16>(
             work, nwork, meshes, counter, err, xg_base, w_base, G, smem, full, empty, meta);
         return;
     }
