@@ -177,8 +177,8 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
     auto saux = [&](int q) { return smem + (size_t)q * kTcSlotBytes + kTcStage; };
     unsigned char* abuf = smem + (size_t)kTcSlots * kTcSlotBytes;  // one A tile per builder warp
     __shared__ __align__(8) uint64_t full[kTcSlots];
-    __shared__ __align__(8) uint64_t empty[kTcSlots];      // near stages: one arrival per consumer warp
-    __shared__ __align__(8) uint64_t empty_far[kTcSlots];  // far stages: the MMA commit
+    __shared__ __align__(8) uint64_t empty[kTcSlots];      // every stage: one arrival per consumer warp
+    __shared__ __align__(8) uint64_t empty_far[kTcSlots];  // far stages, also: the MMA commit
     __shared__ __align__(8) uint64_t afull[kTcBuildW];     // a builder's A tile is built
     __shared__ __align__(8) uint64_t aempty[kTcBuildW];    // a builder's A tile is read by its MMAs
     __shared__ __align__(8) uint64_t dbar;                 // a leaf's far MMAs are done
@@ -304,9 +304,15 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
                     }
                 }
                 if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);  // the warp has passed the stage
                 continue;
             }
-            if (!builder || warp - 2 != own) continue;
+            if (!builder || warp - 2 != own) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+                continue;
+            }
             // the builder of this stage: its A tile is free once the MMAs of its
             // previous use are done
             if (use > 0 && !mbar_wait(&aempty[own], (uint32_t)(use - 1) & 1u, err, 8, it)) break;
@@ -361,7 +367,10 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&afull[own]);
+            if (lane == 0) {
+                mbar_arrive(&afull[own]);
+                mbar_arrive(&empty[slot]);  // the warp has passed the stage
+            }
             continue;
         }
         // ---- near stage on the CUDA cores (as in the multi-vector kernel)

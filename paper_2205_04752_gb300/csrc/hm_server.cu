@@ -409,10 +409,13 @@ int hm_server_run(hm_server* S, const hm_request* reqs, int32_t n, int32_t realt
     R.cv_work.notify_all();
     for (auto& sl : R.slots) sl.th.join();
     // a device wait that ran out in any product invalidates the run
-    for (const hm_matrix* H : S->mats) {
-        int flag = 0;
-        HM_CUDA(cudaMemcpy(&flag, H->d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
-        if (flag) return fail(HM_ETIMEOUT, "hm_server_run: a bounded device wait ran out");
+    for (size_t mi = 0; mi < S->mats.size(); ++mi) {
+        const hm_matrix* H = S->mats[mi];
+        int e[4] = {0, 0, 0, 0};  // flag, site, stage, CTA (as hm_check reports them)
+        HM_CUDA(cudaMemcpy(e, H->d_err.p, sizeof e, cudaMemcpyDeviceToHost));
+        if (e[0])
+            return fail(HM_ETIMEOUT, "hm_server_run: a bounded device wait ran out (matrix %zu, site %d, stage %d, CTA %d)",
+                        mi, e[1], e[2], e[3]);
     }
     return HM_OK;
 }

@@ -336,8 +336,10 @@ struct LeafCfg {
 // (whatever count that barrier was initialised with).  kGran: stage
 // granularity of a tiled 16-bit U stream (8 for the single-vector kernel,
 // 16, the tensor-core K step, otherwise).
-// empty_far (optional): far stages are taken back through this second set of
-// barriers instead (the tensor-core kernel releases them by MMA commit).
+// empty_far (optional): a far stage is taken back once its barrier in this
+// second set completes too (the tensor-core kernel's MMA commit); every stage
+// is taken back through empty[slot] as well, once every consumer warp has
+// passed it, so that no warp can find a full barrier two phases on.
 template <class TF, class TN, class TA, int NS, int kStage, int kAuxBytes, int kGran, int kFarCap = 1 << 20,
           bool kTwoRelease = false>
 __device__ __forceinline__ void leaf_producer(const int2* __restrict__ work, int nwork,
@@ -351,7 +353,6 @@ __device__ __forceinline__ void leaf_producer(const int2* __restrict__ work, int
     // uses of each release barrier, as bit fields of registers
     uint32_t far_mask = 0u;      // bit q: slot q last held a far stage
     uint32_t far_parity = 0u;    // bit q: parity of the next far release of slot q
-    uint32_t near_parity = 0u;   // bit q: parity of the next near release of slot q
     constexpr int kSlotBytes = kStage + kAuxBytes;
     const int lane = threadIdx.x & 31;
     const uint64_t stream_policy = l2_evict_first_policy();
@@ -378,19 +379,17 @@ __device__ __forceinline__ void leaf_producer(const int2* __restrict__ work, int
             const int slot = it % NS;
             if (it >= NS) {
                 bool got;
-                if (kTwoRelease) {
-                    // wait for the release of the slot's previous stage, then
-                    // flip that barrier's expected parity
+                // every consumer warp has taken the slot's previous stage (so that
+                // none can miss a phase of its full barrier)...
+                got = mbar_wait(&empty[slot], (uint32_t)((it / NS) - 1) & 1u, err, 1, it);
+                if (got && kTwoRelease) {
+                    // ...and, for a far stage, its MMAs are done; then flip that
+                    // barrier's expected parity
                     const uint32_t bit = 1u << slot;
                     if (far_mask & bit) {
                         got = mbar_wait(&empty_far[slot], (far_parity & bit) ? 1u : 0u, err, 1, it);
                         far_parity ^= bit;
-                    } else {
-                        got = mbar_wait(&empty[slot], (near_parity & bit) ? 1u : 0u, err, 1, it);
-                        near_parity ^= bit;
                     }
-                } else {
-                    got = mbar_wait(&empty[slot], (uint32_t)((it / NS) - 1) & 1u, err, 1, it);
                 }
                 if (!got) return false;
             }
