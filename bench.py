@@ -51,8 +51,8 @@ WORKLOAD = dict(workload="lame-single-layer-icosphere-L6", mesh="icosphere level
 # measured (sha256 over csrc/ in name order): any change to a kernel or to
 # the layout code nulls it until it is measured again.
 MEASURED_TRAFFIC = {"kernel": "leaf_near", "form": "i16", "level": 6,
-                    "sources_sha256": "decbb7d75e298d16f0a29a4a171774a7262985247882e5af3e876b141ca4cda8",
-                    "bytes": 3925491712 + 1582336}
+                    "sources_sha256": "2dd125fb5c4f474e34a5c93b42fb103f30ee99378158a52205898b39b0fa4411",
+                    "bytes": 3925656832 + 1554432}
 METRIC = "H-matvecs/s"
 UNIT = "matvec/s"
 MEAS_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
