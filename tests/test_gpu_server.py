@@ -123,3 +123,34 @@ def test_solve_slots_keep_a_lane_for_matvecs():
         assert np.array_equal(alone["y"], q["y"]), q["kind"]
     with pytest.raises(binding.HMError):
         binding.Server(mats, slots=2, solve_slots=3)
+
+
+def test_concurrent_tensor_core_matvecs():
+    """Many INT16 requests of 14-20 vectors (the forward pass and the far field
+    of their first 16 on the tensor cores) on two meshes, admitted all at
+    once on 8 slots so that their kernels share the SMs: every request
+    completes (no bounded device wait runs out) and equals the library's
+    product of the same vectors bitwise."""
+    mats = []
+    for (V, T), leaf in [(inputs.icosphere(4), 32), (inputs.ellipsoid(16, 0.7, 1.6, 1.1), 32)]:
+        tr = binding.build_cluster_tree(V, T, leaf, 0.8)
+        H = binding.aca_assemble(tr, 1.0, 0.3, 1e-4, max_rhs=20)
+        H.pack("i16")
+        mats.append(H)
+    srv = binding.Server(mats, slots=8, queue_cap=256, budget_bytes=1 << 31, matvec_form="i16",
+                         inner_form="i16", residual_form="i16")
+    rng = np.random.default_rng(11)
+    reqs = []
+    for i in range(48):
+        m = int(rng.integers(2))
+        nrhs = int(rng.integers(14, 21))
+        x = inputs.uniform_rhs(3 * mats[m].M, 300 + i, nrhs=nrhs)
+        reqs.append(dict(mesh=m, kind="matvec", nrhs=nrhs, x=x, y=np.full_like(x, np.nan)))
+    res = srv.run(reqs, realtime=False)
+    assert all(r["status"] == binding.HM_OK for r in res), [r["status"] for r in res]
+    for q in reqs[:12]:
+        xd = torch.tensor(q["x"], device="cuda")
+        yd = torch.empty_like(xd)
+        binding.hmatvec(mats[q["mesh"]], xd, yd, "i16")
+        torch.cuda.synchronize()
+        assert np.array_equal(yd.cpu().numpy(), q["y"]), (q["mesh"], q["nrhs"])
