@@ -44,10 +44,12 @@ extern "C" {
 #define HM_BF16 2 /* factors BF16 with per-column FP32 scales, near field FP32, FP32 acc. */
 #define HM_FP16 3 /* factors FP16 with per-column FP32 scales, near field FP32, FP32 acc. */
 #define HM_I16 4  /* factors INT16 with per-column FP32 scales on U and V (block floating
-                   * point: a column is stored as round(32767 v / max|v|)), near field
-                   * FP32, FP32 acc.  Same bytes as FP16; a column keeps 15 significant
-                   * bits at its largest entries instead of FP16's 11, which makes the
-                   * product's error against HM_FP64 about 16 times smaller */
+                   * point: a column is stored as round(32767 v / max|v|)); near field:
+                   * the leaves' diagonal blocks FP32, every other near column INT16
+                   * with six FP32 scales; FP32 acc.  Same factor bytes as FP16; a
+                   * column keeps 15 significant bits at its largest entries instead
+                   * of FP16's 11, which makes the product's error against HM_FP64
+                   * about 10 times smaller */
 #define HM_NFORMS 5
 
 /* largest leaf size b_min of a cluster tree (see hm_build_cluster_tree) */

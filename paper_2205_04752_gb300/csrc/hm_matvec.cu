@@ -1148,8 +1148,8 @@ int run_forward(const Plan& P, TA* xg, TA* w, TA* z, int G, const int* xmax, cud
 {
     if (P.nunits <= 0) return HM_OK;
     if constexpr (sizeof(TF) == 2 && std::is_same<TA, float>::value) {
-        // the tiles of V: one vector on the CUDA cores, several (up to 16) on
-        // the tensor cores
+        // the tiles of V: one vector on the CUDA cores, several (up to 16 a
+        // launch; INT16 from 5) on the tensor cores
         if (!fwd_on_tc<TF>(G)) return run_forward_tile1<TF>(P, xg, w, z, s, sc, G);
         if constexpr (tc_form<TF>()) return run_forward_tc<TF>(P, xg, w, z, G, xmax, s);
     }

@@ -5,13 +5,14 @@
 // to the rows of tau) and the near-field columns are contiguous in memory
 // (see hm_matvec.cu).  A persistent CTA takes (mesh, leaf) work items from a
 // global counter (largest first, over every mesh of the product).  Warp 0 is
-// the producer: for every slot of a ring of kStages shared-memory slots it
-// copies up to kStage bytes of the current leaf's stream and, next to it, the
-// 4-vector each segment needs: w of the
-// segment's factor column (far field) or x at the segment's source position
-// (near field).  Consecutive segments of one (block, kernel) item have
-// consecutive factor columns (and of one near block consecutive positions),
-// so these are a few contiguous bulk copies per slot, one per item and lane.
+// the producer: for every slot of a ring of shared-memory slots (LeafCfg::kS)
+// it copies up to kStage bytes of the current leaf's stream and, next to it,
+// the 4-vector each segment needs: w of the segment's factor column (far
+// field) or x at the segment's source position (near field).  The far items
+// of a leaf are merged into runs of consecutive factor columns (the kernels
+// of a block, often consecutive blocks), and one near block's columns are
+// consecutive positions, so these are a few contiguous copies per slot, one
+// per run and lane.
 // Warps 1..7 consume the slots from shared memory only: thread (p, c, h) owns
 // Rr rows (16 bytes of U), a chunk of RC right-hand sides and every H-th
 // segment of a slot; at the end of a leaf the H partial sums of each row are
