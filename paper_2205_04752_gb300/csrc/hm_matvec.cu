@@ -1057,9 +1057,11 @@ int stream_launch(StreamLaunch& out)
 template <class TF>
 constexpr bool fwd_on_tc(int G)
 {
-    // the INT16 split costs a warp's pass over every stage: below five
-    // vectors the per-vector CUDA-core kernel is faster
-    return tc_form<TF>() && G >= (std::is_same<TF, int16_t>::value ? 5 : 2);
+    // the INT16 split costs two warps' pass over every stage: with 2 vectors
+    // the per-vector CUDA-core kernel is faster (level 6: 1.00 against
+    // 1.45 ms), with 3 the two tie, with 4 the tensor cores win (1.57 against
+    // 2.10 ms)
+    return tc_form<TF>() && G >= (std::is_same<TF, int16_t>::value ? 3 : 2);
 }
 
 // The forward pass of the 16-bit forms on the tensor cores: one persistent
@@ -1149,7 +1151,7 @@ int run_forward(const Plan& P, TA* xg, TA* w, TA* z, int G, const int* xmax, cud
     if (P.nunits <= 0) return HM_OK;
     if constexpr (sizeof(TF) == 2 && std::is_same<TA, float>::value) {
         // the tiles of V: one vector on the CUDA cores, several (up to 16 a
-        // launch; INT16 from 5) on the tensor cores
+        // launch; INT16 from 3) on the tensor cores
         if (!fwd_on_tc<TF>(G)) return run_forward_tile1<TF>(P, xg, w, z, s, sc, G);
         if constexpr (tc_form<TF>()) return run_forward_tc<TF>(P, xg, w, z, G, xmax, s);
     }
