@@ -367,13 +367,7 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
                         const float va[2][3] = {{xv[i].x * t, xv[i].y * t, xv[i].z * t},
                                                 {xv[i + 1].x * t, xv[i + 1].y * t, xv[i + 1].z * t}};
 #pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            const uint32_t h0 = tc_bits<TO>(va[0][a]), h1 = tc_bits<TO>(va[1][a]);
-                            const uint32_t l0 = tc_bits<TO>(va[0][a] - tc_back<TO>((unsigned short)h0));
-                            const uint32_t l1 = tc_bits<TO>(va[1][a] - tc_back<TO>((unsigned short)h1));
-                            hw[a][i >> 1] = h0 | (h1 << 16);
-                            lw[a][i >> 1] = l0 | (l1 << 16);
-                        }
+                        for (int a = 0; a < 3; ++a) tc_split2<TO>(va[0][a], va[1][a], hw[a][i >> 1], lw[a][i >> 1]);
                     }
                     const int k = r & 7;
                     for (int qq = r >> 3; qq < rep * nq; qq += nq)

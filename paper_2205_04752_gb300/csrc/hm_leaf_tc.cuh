@@ -13,11 +13,14 @@
 //       same layout, 256 (q / 256 - 128) in place and q mod 256 in the
 //       slot's 4-vector region (free once A is built); their MMAs accumulate
 //       into the same D;
-//   A = 128 rows (split, r, a): W scaled by a power of two t_r and split into
-//       hi = fp16(W t_r) (split 0) and lo = fp16(W t_r - hi) (split 1), so
-//       that D[(0, r, a)] + D[(1, r, a)] = t_r (U W) to about 2^-22 relative;
-//       rows of vectors r >= G are zero.  The consumer warps build it in a
-//       K-major core-matrix layout from the staged FP32 w.
+//   A = 128 rows 64 split + 16 a + r: W scaled by a power of two t_r and
+//       split into hi = fp16(W t_r) (split 0) and lo = fp16(W t_r - hi)
+//       (split 1), so that D[(0, a, r)] + D[(1, a, r)] = t_r (U W) to about
+//       2^-22 relative; the rows of vectors r >= G and of the padding
+//       component a = 3 are zero (never written).  The consumer warps build it
+//       in a K-major core-matrix layout from the staged FP32 w: a lane takes
+//       vector r and eight segments, so that the eight lanes of a shared-memory
+//       phase read 128 contiguous bytes and write the eight rows of one core.
 // t_r = 2^floor(log2(2^15 / (wbound x max|x_r|))): wbound bounds |w| / max|x|
 // for the mesh (|v| <= 1 after pivot normalisation, so |V^T x| <= |s| max|x|;
 // INT16: |v| <= 32767 and w carries the scales SU SV / 32767^2), which keeps
@@ -109,29 +112,27 @@ __device__ __forceinline__ void tc_ld8(uint32_t addr, float* v)
     for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// two FP32 values -> their hi = rn(v) and lo = rn(v - hi) in the operand type,
+// packed (v0 in the low half); each conversion rounds as the scalar one does
 template <class T>
-__device__ __forceinline__ unsigned short tc_bits(float v);
+__device__ __forceinline__ void tc_split2(float v0, float v1, uint32_t& hi, uint32_t& lo);
 template <>
-__device__ __forceinline__ unsigned short tc_bits<__half>(float v)
+__device__ __forceinline__ void tc_split2<__half>(float v0, float v1, uint32_t& hi, uint32_t& lo)
 {
-    return __half_as_ushort(__float2half_rn(v));
+    const __half2 h = __floats2half2_rn(v0, v1);
+    const float2 b = __half22float2(h);
+    const __half2 l = __floats2half2_rn(v0 - b.x, v1 - b.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 template <>
-__device__ __forceinline__ unsigned short tc_bits<__nv_bfloat16>(float v)
+__device__ __forceinline__ void tc_split2<__nv_bfloat16>(float v0, float v1, uint32_t& hi, uint32_t& lo)
 {
-    return __bfloat16_as_ushort(__float2bfloat16_rn(v));
-}
-template <class T>
-__device__ __forceinline__ float tc_back(unsigned short b);
-template <>
-__device__ __forceinline__ float tc_back<__half>(unsigned short b)
-{
-    return __half2float(__ushort_as_half(b));
-}
-template <>
-__device__ __forceinline__ float tc_back<__nv_bfloat16>(unsigned short b)
-{
-    return __bfloat162float(__ushort_as_bfloat16(b));
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+    const float2 b = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - b.x, v1 - b.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
 // two offset-binary int16 values q (one word) -> the exact FP16 pairs
@@ -208,6 +209,10 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    // the rows of the A tiles that no builder writes stay zero
+    for (int e = threadIdx.x; e < kTcBuildW * kTcABytes / 16; e += kThreads)
+        reinterpret_cast<uint4*>(abuf)[e] = make_uint4(0u, 0u, 0u, 0u);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -232,6 +237,7 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
     int64_t xoff = 0;
     TA c1 = 0.f, c2 = 0.f;
     float wbound = 0.f;
+    float tl = 0.f;  // a builder lane's t_r, r = lane mod 16 (0: a vector beyond G)
     int fs = 0;   // far stages seen (the builder, the use of its A tile, the MMA turn)
     int nfl = 0;  // leaves with a far field finished (phase of dbar)
     bool far_started = false;
@@ -252,6 +258,7 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
             c1 = (TA)md.c1;
             c2 = (TA)md.c2;
             wbound = md.wbound;
+            if (builder) tl = (lane & 15) < G ? tc_scale(wbound, xmax, lane & 15) : 0.0f;
             mp = (mt + 7) & ~7;
             mp16 = (mt + 15) & ~15;
             P = mp / Rr;
@@ -318,32 +325,29 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
             if (use > 0 && !mbar_wait(&aempty[own], (uint32_t)(use - 1) & 1u, err, 8, it)) break;
             const float* av = reinterpret_cast<const float*>(saux(slot));
             const int nkb = m.count >> 3;  // core columns of this stage
-            // item (mb, kb, rr): vector r = 2 mb + rr, rows 8 mb + 4 rr + a (hi)
-            // and 64 + 8 mb + 4 rr + a (lo), segments 8 kb .. 8 kb + 7
-            for (int itm = lane; itm < 16 * nkb; itm += 32) {
-                const int rr = itm & 1, mb = (itm >> 1) & 7, kb = itm >> 4;
-                const int r = 2 * mb + rr;
-                const float t = r < G ? tc_scale(wbound, xmax, r) : 0.0f;
+            // item (r, kb): vector r = lane mod 16, segments 8 kb .. 8 kb + 7;
+            // its rows 16 a + r (hi) and 64 + 16 a + r (lo) are row r mod 8 of
+            // the cores 2 a + r / 8 and 8 + 2 a + r / 8 of core column kb
+            const int r = lane & 15;
+            if (r < G) {
+                for (int kb = lane >> 4; kb < nkb; kb += 2) {
+                    uint32_t hw[3][4], lw[3][4];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    // one row of the hi core and of the lo core: 8 segments of (r, a)
-                    uint32_t hw[4] = {0u, 0u, 0u, 0u}, lw[4] = {0u, 0u, 0u, 0u};
-                    if (r < G) {
-#pragma unroll
-                        for (int s2 = 0; s2 < 4; ++s2) {
-                            const float v0 = av[((size_t)(kb * 8 + 2 * s2) * G + r) * 4 + a] * t;
-                            const float v1 = av[((size_t)(kb * 8 + 2 * s2 + 1) * G + r) * 4 + a] * t;
-                            const uint32_t h0 = tc_bits<TO>(v0), h1 = tc_bits<TO>(v1);
-                            const uint32_t l0 = tc_bits<TO>(v0 - tc_back<TO>((unsigned short)h0));
-                            const uint32_t l1 = tc_bits<TO>(v1 - tc_back<TO>((unsigned short)h1));
-                            hw[s2] = h0 | (h1 << 16);
-                            lw[s2] = l0 | (l1 << 16);
-                        }
+                    for (int s2 = 0; s2 < 4; ++s2) {
+                        const float4 x0 = *reinterpret_cast<const float4*>(av + ((size_t)(kb * 8 + 2 * s2) * G + r) * 4);
+                        const float4 x1 =
+                            *reinterpret_cast<const float4*>(av + ((size_t)(kb * 8 + 2 * s2 + 1) * G + r) * 4);
+                        tc_split2<TO>(x0.x * tl, x1.x * tl, hw[0][s2], lw[0][s2]);
+                        tc_split2<TO>(x0.y * tl, x1.y * tl, hw[1][s2], lw[1][s2]);
+                        tc_split2<TO>(x0.z * tl, x1.z * tl, hw[2][s2], lw[2][s2]);
                     }
-                    *reinterpret_cast<uint4*>(A + (size_t)(mb * (kTcK / 8) + kb) * 128 + (4 * rr + a) * 16) =
-                        make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                    *reinterpret_cast<uint4*>(A + (size_t)((mb + 8) * (kTcK / 8) + kb) * 128 + (4 * rr + a) * 16) =
-                        make_uint4(lw[0], lw[1], lw[2], lw[3]);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const size_t o = (size_t)((2 * a + (r >> 3)) * (kTcK / 8) + kb) * 128 + (r & 7) * 16;
+                        *reinterpret_cast<uint4*>(A + o) = make_uint4(hw[a][0], hw[a][1], hw[a][2], hw[a][3]);
+                        *reinterpret_cast<uint4*>(A + o + (size_t)8 * (kTcK / 8) * 128) =
+                            make_uint4(lw[a][0], lw[a][1], lw[a][2], lw[a][3]);
+                    }
                 }
             }
             if constexpr (kI16) {
@@ -490,8 +494,8 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
                     named_barrier_consumers();
                     if (reader && q4 < 2) {
                         const int row = 32 * q4 + lane;
-                        const int r = row >> 2, a = row & 3;
-                        const float inv = 1.0f / tc_scale(wbound, xmax, min(r, kTcMaxG - 1));
+                        const int r = row & 15, a = row >> 4;
+                        const float inv = 1.0f / tc_scale(wbound, xmax, r);
                         for (int cc = 0; cc < nc; cc += 8) {
                             float v[8];
                             tc_ld8(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(c0 + cc), v);
