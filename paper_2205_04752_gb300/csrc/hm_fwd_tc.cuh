@@ -16,8 +16,9 @@
 //       operands of the same layout, 256 (q / 256 - 128) and q mod 256, both
 //       exact, whose MMAs accumulate into the same rows;
 // Every ring is used in stage order by each of its waiting threads, or (the
-// A ring, filled by four warps round-robin) has a multiple of four slots, so
-// that no wait can see a barrier's parity of two phases before.
+// A ring, filled by the builder warps round-robin) has a multiple of their
+// number of slots, so that no wait can see a barrier's parity of two phases
+// before.
 //   A = x(s) of the G vectors, scaled by a power of two t_r per vector (from
 //       max|x_r|, so that every value fits FP16) and split into hi = fp16(x
 //       t_r) and lo = fp16(x t_r - hi): two K-major core-matrix tiles whose
@@ -32,11 +33,13 @@
 //   warp 0      producer: the V of every stage of every unit through a ring
 //               of slots (bulk copies);
 //   warps 2-5   build the A tiles from the gathered x into a second ring, a
-//               stage each round-robin, ahead of the V stream;
-//   warps 14-15 INT16 form: split every stage's V once it has landed, in
-//               stage order, each half of its 16-byte chunks (256 x high bytes
-//               in place, the low bytes into a ring of two buffers that the
-//               MMA commits release);
+//               stage each round-robin, ahead of the V stream (INT16 form
+//               with at most 8 vectors: warps 2-3 only);
+//   warps 14-15 (and 4-5 where they build nothing) INT16 form: split every
+//               stage's V once it has landed, in stage order, each its share
+//               of the 16-byte chunks (256 x high bytes in place, the low
+//               bytes into a ring of two buffers that the MMA commits
+//               release);
 //   warp 1      one thread issues the MMAs of a stage and commits them to the
 //               release barriers of its V and A slots, and after a unit's last
 //               stage to its accumulator barrier; two accumulators (2 x 256
@@ -82,7 +85,19 @@ struct FpCfg {
         return (size_t)(VS + LS) * kFpVBytes + (size_t)AS * kFpABytes + 8 * (size_t)kFpBBytes;
     }
 };
-static_assert(kFpASlots % 4 == 0, "four builder warps take the A slots round-robin");
+static_assert(kFpASlots % 4 == 0, "four (or two) builder warps take the A slots round-robin");
+
+// A-builder warps of a launch (warps 2 .. 1 + nb); the INT16 form splits V
+// on the other warps of 2-5 and on 14-15.  The builds grow with the vectors,
+// the split does not: level 6, INT16, four builders and two converters
+// against two and four: 4 vectors 1.57 against 1.38 ms, 8 vectors 1.83
+// against 1.64 ms, 16 vectors 2.08 against 2.11 ms (one builder and five
+// converters: 2.02, 2.42, 3.19 ms)
+template <class TF>
+__host__ __device__ constexpr int fp_builders(int ng)
+{
+    return std::is_same<TF, int16_t>::value && ng <= 8 ? 2 : 4;
+}
 template <class TF>
 constexpr size_t fp_smem()
 {
@@ -186,13 +201,15 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
     const int ng = min(kTcMaxG, G);  // vectors of this launch
     const int nq = (ng + 7) >> 3;    // distinct quarter contents
     const int rep = 4 / nq;          // copies of each (4 or 2)
+    const int nb = fp_builders<TF>(ng);  // A-builder warps (a power of two dividing AS)
+    const int ncv = kI16 ? 6 - nb : 0;   // INT16 converter warps
     auto slot_v = [&](int s) { return smem + (size_t)s * kFpVBytes; };
     auto slot_l = [&](int s) { return smem + (size_t)(VS + s) * kFpVBytes; };
     auto slot_a = [&](int s) { return smem + (size_t)(VS + LS) * kFpVBytes + (size_t)s * kFpABytes; };
     if (tid == 0) {
         for (int s = 0; s < VS; ++s) {
             mbar_init(&vfull[s], 1);
-            mbar_init(&vconv[s], 2);  // one arrival per converter warp
+            mbar_init(&vconv[s], ncv > 0 ? ncv : 1);  // one arrival per converter warp
             mbar_init(&vempty[s], 1);
         }
         for (int s = 0; s < LS; ++s) mbar_init(&lempty[s], 1);
@@ -321,8 +338,8 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
                 if (run) tc_commit(&accf[ab]);
             }
         }
-    } else if (warp < 6) {
-        // ---- A builders: warp bw builds the stages it with it % 4 == bw; an
+    } else if (warp < 2 + nb) {
+        // ---- A builders: warp bw builds the stages it with it % nb == bw; an
         // item is (8-row K block kb, vector r): 8 rows of x_r -> three hi and
         // three lo rows of 8 K values in every quarter that holds r
         const int bw = warp - 2;
@@ -335,13 +352,13 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
             if (u + (int)gridDim.x < nunits) nx = units[u + gridDim.x];
             const int n16 = (un.nrows + 15) & ~15;
             const int nst = (n16 + kFpRows - 1) / kFpRows;
-            if (((bw - it) & 3) >= nst) {  // no stage of this unit is ours
+            if (((bw - it) & (nb - 1)) >= nst) {  // no stage of this unit is ours
                 it += nst;
                 continue;
             }
             const float* x0 = xg + ((size_t)mesh_of_unit(un.mesh).xgoff + un.x0) * G * 4;
             for (int q = 0; q < nst; ++q, ++it) {
-                if ((it & 3) != bw) continue;
+                if ((it & (nb - 1)) != bw) continue;
                 const int as = it % AS;
                 // the lanes of a warp decide together (they meet at __syncwarp)
                 const bool got = it < AS ||
@@ -385,12 +402,12 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
                 if (lane == 0) mbar_arrive(&afull[as]);
             }
         }
-    } else if (warp >= 14) {
+    } else if (warp < 6 || warp >= 14) {
         // ---- INT16: split every stage's V in stage order once it has landed
         // (and its low-byte buffer is free): 256 x high bytes in place, the
-        // low bytes into the buffer; warp 14 + h takes the groups of 32
-        // 16-byte chunks h, h + 2, h + 4, ...
-        const int cw = warp - 14;
+        // low bytes into the buffer; converter h (warps 2 + nb .. 5, then 14
+        // and 15) takes the groups of 32 16-byte chunks h, h + ncv, ...
+        const int cw = warp < 6 ? warp - 2 - nb : warp - 14 + (4 - nb);
         if constexpr (kI16) {
             int it = 0;
             bool run = true;
@@ -413,7 +430,7 @@ __global__ void __launch_bounds__(kFpThreads, 1) fwd_tc_kernel(
                     uint4* L = reinterpret_cast<uint4*>(slot_l(ls));
                     const int nkr = min(kFpRows / 8, (n16 >> 3) - q * (kFpRows / 8));
                     const int nch = nkr * un.ncols;  // 16-byte chunks of the stage
-                    for (int e = 32 * cw + lane; e < nch; e += 64) {
+                    for (int e = 32 * cw + lane; e < nch; e += 32 * ncv) {
                         const uint4 v = V[e];
                         uint4 h, l;
                         i16_split_word(v.x, h.x, l.x);

@@ -138,11 +138,12 @@ __device__ __forceinline__ void tc_split2<__nv_bfloat16>(float v0, float v1, uin
 // two offset-binary int16 values q (one word) -> the exact FP16 pairs
 // 256 (q / 256 - 128) (hi) and q mod 256 (lo): a byte b becomes the FP16
 // number 1024 + b by its bits 0x6400 | b, from which 1024 (or 1024 + 128) is
-// subtracted exactly
+// subtracted exactly (one byte permute per half: bytes b0, 0x64, b2, 0x64
+// and b1, 0x64, b3, 0x64)
 __device__ __forceinline__ void i16_split_word(uint32_t q, uint32_t& hi, uint32_t& lo)
 {
-    const uint32_t lb = (q & 0x00ff00ffu) | 0x64006400u;
-    const uint32_t hb = ((q >> 8) & 0x00ff00ffu) | 0x64006400u;
+    const uint32_t lb = __byte_perm(q, 0x64646464u, 0x4240);
+    const uint32_t hb = __byte_perm(q, 0x64646464u, 0x4341);
     __half2 l2 = *reinterpret_cast<const __half2*>(&lb);
     __half2 h2 = *reinterpret_cast<const __half2*>(&hb);
     l2 = __hsub2(l2, __float2half2_rn(1024.0f));

@@ -1252,9 +1252,10 @@ int run_phases(const Plan& P, const double* x, double* y, int G, int64_t ld, TA*
 }
 
 // fewest vectors of a launch that takes the far field to the tensor cores
-// (level 6: at 12 vectors the CUDA-core kernel is faster, at 16 the
-// tensor-core one; the two meet near 14 in both 16-bit forms)
-constexpr int kTcMinG = 14;
+// (leaf product at level 6, CUDA against tensor cores: INT16 8 vectors 3.35
+// against 3.72 ms, 10 vectors 4.42 against 4.04 ms; FP16 3.04 against 3.15
+// and 3.88 against 3.23 ms; the two meet near 9 in both 16-bit forms)
+constexpr int kTcMinG = 9;
 
 // per-device launch data of the tensor-core leaf kernel
 template <class TF>
