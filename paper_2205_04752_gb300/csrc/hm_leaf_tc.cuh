@@ -10,9 +10,10 @@
 //   B = U of 16 segments, straight from the stage (the stream is stored in
 //       8 x 8 core-matrix tiles, an MN-major operand).  INT16 stages (offset
 //       binary q = v + 32768) are split into two exact FP16 operands of the
-//       same layout, 256 (q / 256 - 128) in place and q mod 256 in the
-//       slot's 4-vector region (free once A is built); their MMAs accumulate
-//       into the same D;
+//       same layout, 256 (q / 256 - 128) in place and q mod 256 right after
+//       the stage's U when both fit the stage region (split by a second warp
+//       while the builder builds A), otherwise in the slot's 4-vector region
+//       (free once A is built); their MMAs accumulate into the same D;
 //   A = 128 rows 64 split + 16 a + r: W scaled by a power of two t_r and
 //       split into hi = fp16(W t_r) (split 0) and lo = fp16(W t_r - hi)
 //       (split 1), so that D[(0, a, r)] + D[(1, a, r)] = t_r (U W) to about
@@ -26,7 +27,8 @@
 // INT16: |v| <= 32767 and w carries the scales SU SV / 32767^2), which keeps
 // every scaled value inside the FP16 range.
 // The three builder warps take the far stages round-robin, each into its own
-// A buffer, so that the builds of consecutive stages overlap.  One thread
+// A buffer, so that the builds of consecutive stages overlap; INT16: warp
+// 5 + k splits the stages that builder 2 + k builds.  One thread
 // (lane 0 of warp 1) issues every stage's MMAs in stage order, once its
 // builder has announced the A tile, and commits them to the barriers that
 // release the builder's A buffer and the stage (one issuing thread: the
@@ -63,6 +65,7 @@ constexpr size_t tc_smem()
 static_assert(kTcStage <= kTcAux, "the split of a far stage must fit the 4-vector region");
 static_assert(kConsumers * 8 * 3 * 4 <= kTcSlotBytes, "the near reduction must fit a slot");
 static_assert(64 * 64 * 4 <= kTcSlotBytes, "the far epilogue exchange must fit a slot");
+static_assert(2 + 2 * kTcBuildW <= kThreads / 32, "an INT16 splitter warp for every builder warp");
 
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
 {
@@ -161,6 +164,32 @@ __device__ __forceinline__ float tc_scale(float wbound, const int* xmax, int r)
     return exp2f(floorf(log2f(32768.0f / b)));
 }
 
+// where the low bytes of an INT16 far stage's split go: right after its U in
+// the stage region when both halves fit there (then a warp other than the
+// builder splits the stage while the builder builds A), otherwise into the
+// 4-vector region once the builder has read w from it
+__device__ __forceinline__ uint32_t tc_lo_offset(int count, int mp)
+{
+    const int ub = count * mp * 2;  // bytes of the stage's U (a multiple of 256)
+    return 2 * ub <= kTcStage ? (uint32_t)ub : (uint32_t)kTcStage;
+}
+
+// split an INT16 stage of nch 16-byte chunks: 256 x high bytes in place, the
+// low bytes lo16 chunks further on
+__device__ __forceinline__ void tc_split_stage(uint4* Us, int nch, int lo16, int lane)
+{
+    for (int e = lane; e < nch; e += 32) {
+        const uint4 v = Us[e];
+        uint4 hv, lv;
+        i16_split_word(v.x, hv.x, lv.x);
+        i16_split_word(v.y, hv.y, lv.y);
+        i16_split_word(v.z, hv.z, lv.z);
+        i16_split_word(v.w, hv.w, lv.w);
+        Us[e] = hv;
+        Us[e + lo16] = lv;
+    }
+}
+
 template <class TF>
 __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
     const int2* __restrict__ work, int nwork, const MeshDev* __restrict__ meshes, int* __restrict__ counter,
@@ -196,7 +225,7 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
             mbar_init(&empty_far[s], 1);
         }
         for (int b = 0; b < kTcBuildW; ++b) {
-            mbar_init(&afull[b], 1);
+            mbar_init(&afull[b], kI16 ? 2 : 1);  // INT16: the builder and the splitter
             mbar_init(&aempty[b], 1);
         }
         mbar_init(&dbar, 1);
@@ -290,6 +319,7 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
                         tc_fence_after();
                         const uint32_t a0 = smem_addr(A), b0 = smem_addr(sdata(slot));
                         const uint32_t kstride = (uint32_t)(mp >> 3) * 128;  // K-direction core stride of U
+                        const uint32_t bl0 = b0 + (kI16 ? tc_lo_offset(m.count, mp) : 0u);  // INT16 low bytes
                         for (int ks = 0; ks < (m.count >> 4); ++ks) {
                             for (int n0 = 0; n0 < mp16; n0 += 256) {
                                 const int n = min(256, mp16 - n0);
@@ -299,8 +329,7 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
                                 tc_mma(tmem + (uint32_t)n0, ad, bd, tc_idesc(n, kBf16),
                                        (!first_far || ks > 0) ? 1u : 0u);
                                 if (kI16) {
-                                    const uint64_t bl = tc_desc(b0 + kTcStage + (uint32_t)ks * 2 * kstride +
-                                                                    (uint32_t)(n0 >> 3) * 128,
+                                    const uint64_t bl = tc_desc(bl0 + (uint32_t)ks * 2 * kstride + (uint32_t)(n0 >> 3) * 128,
                                                                 kstride, 128);
                                     tc_mma(tmem + (uint32_t)n0, ad, bl, tc_idesc(n, kBf16), 1u);
                                 }
@@ -317,6 +346,17 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
                 continue;
             }
             if (!builder || warp - 2 != own) {
+                if (kI16 && warp == 2 + kTcBuildW + own) {
+                    // the splitter of this stage (warps 5..7): the split, where
+                    // it goes into the stage region, while the builder builds A
+                    const uint32_t lo = tc_lo_offset(m.count, mp);
+                    if (lo < (uint32_t)kTcStage)
+                        tc_split_stage(reinterpret_cast<uint4*>(sdata(slot)), m.count * (mp >> 3), (int)(lo >> 4),
+                                       lane);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&afull[own]);
+                }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[slot]);
                 continue;
@@ -352,21 +392,12 @@ __global__ void __launch_bounds__(kThreads) leaf_tc_kernel(
                 }
             }
             if constexpr (kI16) {
-                // split the stage's U: 256 x high bytes in place, the low bytes
-                // into the 4-vector region right after the stage, once the warp
-                // is done reading w from it (16-byte chunks)
-                __syncwarp();
-                uint4* Us = reinterpret_cast<uint4*>(sdata(slot));
-                const int nch = m.count * (mp >> 3);
-                for (int e = lane; e < nch; e += 32) {
-                    const uint4 v = Us[e];
-                    uint4 hv, lv;
-                    i16_split_word(v.x, hv.x, lv.x);
-                    i16_split_word(v.y, hv.y, lv.y);
-                    i16_split_word(v.z, hv.z, lv.z);
-                    i16_split_word(v.w, hv.w, lv.w);
-                    Us[e] = hv;
-                    Us[e + kTcStage / 16] = lv;
+                // a stage whose split does not fit its region: the low bytes go
+                // into the 4-vector region right after it, once the warp is done
+                // reading w from it
+                if (tc_lo_offset(m.count, mp) == (uint32_t)kTcStage) {
+                    __syncwarp();
+                    tc_split_stage(reinterpret_cast<uint4*>(sdata(slot)), m.count * (mp >> 3), kTcStage / 16, lane);
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
