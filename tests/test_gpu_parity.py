@@ -183,6 +183,32 @@ def test_tensor_core_far_field_scales_exactly(form, nrhs):
         assert _rel(ym[r], ref) <= 2e-6, r
 
 
+@pytest.mark.parametrize("nrhs", [9, 16])
+def test_tensor_core_far_field_large_leaves(nrhs):
+    """Leaves of more than 64 rows (leaf size 128 on the level-4 icosphere:
+    up to 80): a far stage of 48 segments then holds more U than half the
+    stage region, so the INT16 split goes into the staged-vector region after
+    the A build (leaves of up to 64 rows split beside U, on a second warp).
+    Every vector of the launch matches its own single-vector product within
+    1e-5 (both accumulate the same INT16 product in FP32 and the far field's
+    W carries the 2^-22 of its hi/lo split; the 80-row leaves sum more
+    segments per leaf than the 32-row ones of the 2e-6 tests: 2.5e-6
+    measured), and scaling x by 2^40 scales y exactly."""
+    if "c128" not in _cache:
+        V, T = inputs.icosphere(4)
+        _cache["c128"] = Case(V, T, 128, max_rhs=16)
+    c = _cache["c128"]
+    assert max(c.size(n) for n in range(len(c.nodes)) if c.nodes[n, 2] < 0) > 64
+    c.H.pack("i16")
+    x = inputs.uniform_rhs(3 * c.M, 77, nrhs=nrhs)
+    y = c.matvec(x, "i16")
+    assert np.all(np.isfinite(y))
+    np.testing.assert_array_equal(c.matvec(x * 2.0 ** 40, "i16"), y * 2.0 ** 40)
+    for r in range(nrhs):
+        ys = c.matvec(x[r], "i16")[0]
+        assert _rel(y[r], ys) <= 1e-5, r
+
+
 def test_multi_rhs_split_into_several_launches():
     """Leaves of 300 rows in FP64 leave room for only 4 vectors per launch:
     10 right-hand sides run as launches of 4, 4 and 2; every row matches the
