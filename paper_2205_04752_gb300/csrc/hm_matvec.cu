@@ -756,12 +756,15 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_reduce_kernel(
         const FwdRec& rec = srec[lo];
         const int cb = col - rec.coff;
         if (cb >= rec.C) continue;
+        // the chunks' partial sums in chunk order, one 4-vector load each
         TA zz[3] = {(TA)0, (TA)0, (TA)0};
+#pragma unroll 4
         for (int k = 0; k < mu.nchunk; ++k) {
-            const TA* d = z + ((size_t)(mu.zcol0 + (int64_t)k * Cs + col) * G + r) * 4;
-            zz[0] += d[0];
-            zz[1] += d[1];
-            zz[2] += d[2];
+            TA d0, d1, d2;
+            stream::load3(z + ((size_t)(mu.zcol0 + (int64_t)k * Cs + col) * G + r) * 4, d0, d1, d2);
+            zz[0] += d0;
+            zz[1] += d1;
+            zz[2] += d2;
         }
         write_w<TA>(rec, cb, zz[0], zz[1], zz[2], md.SU, wr, c1, c2, G, r);
     }
