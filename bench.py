@@ -222,6 +222,18 @@ def _dist():
     return ws, rank, local
 
 
+def _slowest(ms, ws, device):
+    """The job's time of a timed region: the slowest rank's (max over the ws
+    ranks of the process group; every rank gets it)."""
+    if ws == 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
@@ -317,12 +329,7 @@ def run_ours(args):
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        if ws > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return _slowest(e0.elapsed_time(e1), ws, "cuda")
 
     # ---- headline: device-resident product in the chosen form
     clk = ClockSampler(local)
